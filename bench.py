@@ -1,0 +1,468 @@
+"""Benchmark of the P3T distant-force path on one B300 (replicas on N GPUs).
+
+Workload (the distant-force benchmark at N = 10^6): a Plummer sphere of
+N = 1,000,000 stars with Kroupa masses (0.08-100, total mass 1) in Henon
+units, theta = 0.4, monopole + quadrupole cells, r_out chosen for ~100 mean
+neighbours (closed form 0.9006 N r^3 = 100 -> r_out = 0.0481), r_in =
+0.1 r_out, r_list = r_out, FP32 interactions on FP64 relative coordinates.
+
+One step = one pass of the whole path: tree build (keys, sort, topology,
+moments, groups), far force, neighbour lists, kick (dt = 1/512) and the drift
+x += dt v that stands in for the Hermite integration, so every step works on
+moved particles.  Inputs are synthetic and seeded (data: "synthetic").
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the context's stream; between steps a 256 MB buffer is written to flush
+the 126 MB L2 (outside the events).  The timed region is bracketed by a
+barrier and a device synchronisation; the reported time is the maximum over
+ranks.  value = particles processed by all ranks / time (far-force evals/s).
+
+--impl reference runs the CPU oracle (plain FP64 C) on the same workload,
+each step a bounded sample (see cpu_sample), on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_DEFAULT = 1_000_000
+THETA = 0.4
+DT = 1.0 / 512
+FLOPS_PER_INTERACTION = 38
+FP32_LANES_PER_SM = 128
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--group-size", type=int, default=64)
+    ap.add_argument("--tile", type=int, default=64)
+    ap.add_argument("--leaf-cap", type=int, default=16)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
+    return ap.parse_args(argv)
+
+
+def workload(n, seed):
+    import synth
+    c = synth.plummer(n, seed, masses="kroupa")
+    r_out = synth.plummer_r_for_mean_neighbours(n, 100.0)
+    return c, {"theta": THETA, "r_out": r_out, "r_in": 0.1 * r_out, "r_list": r_out}
+
+
+# ---------------------------------------------------------------------------- distributed
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("P3T_BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, local, world
+
+
+def dist_barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def dist_max(value, world, device=None):
+    """Maximum of a float over ranks (identity for one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_sum(value, world, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------- peaks
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count, sm_max_mhz):
+    """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flops (FMA) x max SM clock."""
+    return sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+def cpu_sample(c, prm, budget_s, with_neighbours=True):
+    """Time the oracle on a bounded sample of one step; returns step-time estimate.
+
+    The oracle builds the whole tree (all N particles), then evaluates the far
+    force (and the neighbour lists) for the first groups of the tree until
+    `budget_s` is spent, and kicks all particles.  The per-particle force and
+    neighbour cost of the sample is scaled to all N.
+    """
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    tree = oracle.Tree(c.x, c.y, c.z, c.m, prm["theta"], prm["r_out"], leaf_cap=16, group_size=64)
+    t_build = time.perf_counter() - t0
+    ex = tree.export()
+    gcount = ex["g_count"]
+    ng = tree.n_groups
+    done, t_force, t_nbr, parts = 0, 0.0, 0.0, 0
+    chunk = max(1, ng // 1000)
+    while done < ng and t_build + t_force + t_nbr < budget_s:
+        sel = np.arange(done, min(ng, done + chunk))
+        t1 = time.perf_counter()
+        tree.far(prm["r_in"], groups=sel)
+        t2 = time.perf_counter()
+        if with_neighbours:
+            tree.neighbours(prm["r_list"], groups=sel)
+        t3 = time.perf_counter()
+        t_force += t2 - t1
+        t_nbr += t3 - t2
+        parts += int(gcount[sel].sum())
+        done += len(sel)
+        chunk *= 2
+    t4 = time.perf_counter()
+    oracle.kick(DT, c.vx, c.vy, c.vz, c.vx, c.vy, c.vz)
+    t_kick = time.perf_counter() - t4
+    scale = c.n / max(1, parts)
+    step = t_build + (t_force + t_nbr) * scale + t_kick
+    return {"step_s": step, "far_s_per_particle": t_force / max(1, parts), "sampled_particles": parts,
+            "groups": int(done), "build_s": t_build, "wall_s": time.perf_counter() - t0}
+
+
+def omp_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    if v and v.isdigit():
+        return int(v)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_b300(args, rank, local, world):
+    import numpy as np
+    import torch
+
+    import paper_2110_11658_b300 as p3t
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    c, w = workload(args.n, 20211022 + rank)
+    prm = p3t.Params(theta=w["theta"], r_in=w["r_in"], r_out=w["r_out"], r_list=w["r_list"],
+                     leaf_cap=args.leaf_cap, group_size=args.group_size, tile=args.tile,
+                     precision=p3t.P3T_FP32_MIXED, quadrupole=1)
+    stream = torch.cuda.current_stream(dev)
+    ctx = p3t.Context(prm, stream)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    x, y, z, m = t(c.x), t(c.y), t(c.z), t(c.m)
+    vx, vy, vz = t(c.vx), t(c.vy), t(c.vz)
+    n = c.n
+    a = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+    offs = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    tot_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+    n_cell = torch.zeros(1, dtype=torch.int64, device=dev)
+    n_part = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+
+    # size the neighbour buffer from one synchronous step
+    ctx.build_tree(x, y, z, m)
+    ctx.far_force(*a)
+    try:
+        ctx.neighbours(offs, torch.empty(1, dtype=torch.int32, device=dev))
+        first_total = 0
+    except p3t.P3TError as e:
+        if e.code != p3t.P3T_ERR_CAPACITY:
+            raise
+        first_total = e.total
+    idx = torch.empty(int(first_total * 1.3) + 1024, dtype=torch.int32, device=dev)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(record):
+        e0, e1, e2, e3, e4 = (ev(), ev(), ev(), ev(), ev()) if record else (None,) * 5
+        if record:
+            e0.record(stream)
+        ctx.build_tree(x, y, z, m)
+        if record:
+            e1.record(stream)
+        ctx.far_force(*a, n_cell=n_cell, n_part=n_part)
+        if record:
+            e2.record(stream)
+        ctx.neighbours_async(offs, idx, tot_dev)
+        if record:
+            e3.record(stream)
+        ctx.kick(DT, *a, vx, vy, vz)
+        ctx.drift(DT, x, y, z, vx, vy, vz)
+        if record:
+            e4.record(stream)
+        return (e0, e1, e2, e3, e4)
+
+    for _ in range(max(3, args.warmup)):
+        step(False)
+    ctx.check()
+    n_cell.zero_()
+    n_part.zero_()
+    torch.cuda.synchronize(dev)
+    dist_barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall0 = time.perf_counter()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        evs.append(step(True))
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    dist_barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    st = ctx.status()
+    if st != p3t.P3T_OK:
+        raise p3t.P3TError(st, "benchmark step")
+    ph = {"build": 0.0, "far": 0.0, "nbr": 0.0, "kick_drift": 0.0}
+    for e0, e1, e2, e3, e4 in evs:
+        ph["build"] += e0.elapsed_time(e1)
+        ph["far"] += e1.elapsed_time(e2)
+        ph["nbr"] += e2.elapsed_time(e3)
+        ph["kick_drift"] += e3.elapsed_time(e4)
+    step_ms_local = sum(ph.values()) / args.steps
+    step_ms = dist_max(step_ms_local, world, dev)
+    far_ms = dist_max(ph["far"] / args.steps, world, dev)
+    ncell = int(n_cell.item()) / args.steps
+    npart = int(n_part.item()) / args.steps
+    inter = ncell + npart
+    nbr_total = int(tot_dev.item())
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_kind = measured_peaks()
+    fp32_peak = fp32_peak_tflops(props.multi_processor_count, float(peaks.get("sm_max_mhz", 2032.0)))
+    achieved = FLOPS_PER_INTERACTION * inter / (far_ms * 1e-3) / 1e12
+    total_particles = dist_sum(float(n), world, dev)
+    value = total_particles / (step_ms * 1e-3)
+
+    # end-to-end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda q: torch.from_numpy(np.ascontiguousarray(q)).pin_memory()  # noqa: E731
+        hx, hy, hz, hm = pin(c.x), pin(c.y), pin(c.z), pin(c.m)
+        hv = [pin(c.vx), pin(c.vy), pin(c.vz)]
+        ha = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(3)]
+        hoffs = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+        hidx = torch.empty(idx.numel(), dtype=torch.int32).pin_memory()
+        hctx = p3t.Context(prm, stream)
+        for _ in range(2):
+            hctx.step_host(DT, hx, hy, hz, hm, *hv, *ha, hoffs, hidx)
+        k = max(3, min(args.steps, 10))
+        dist_barrier(world, dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        tots = 0
+        for _ in range(k):
+            tots = hctx.step_host(DT, hx, hy, hz, hm, *hv, *ha, hoffs, hidx)
+        torch.cuda.synchronize(dev)
+        te = dist_max((time.perf_counter() - t0) / k, world, dev)
+        hctx.close()
+        e2e = {"value": total_particles / te, "unit": "particles/s",
+               "h2d_bytes_per_step": 7 * 8 * n, "d2h_bytes_per_step": 3 * 4 * n + 3 * 8 * n + 8 * (n + 1) + 4 * tots,
+               "ms_per_step": te * 1e3, "api": "p3t_step_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = cpu_sample(c, w, args.cpu_budget)
+        cpu = {"value": c.n / s["step_s"], "unit": "particles/s", "cores": omp_threads(), "kind": "oracle",
+               "sample": "oracle tree build of all %d particles, far force + neighbour lists of the first %d "
+                         "groups (%d particles) scaled to all N, kick of all N; %.1f s of CPU work"
+                         % (c.n, s["groups"], s["sampled_particles"], s["wall_s"]),
+               "far_force_evals_per_s": 1.0 / s["far_s_per_particle"]}
+
+    line = {
+        "metric": "particle far-force evals/sec & interactions/sec at N=1e6 (FP32 % peak); ensemble p50/p99",
+        "value": value,
+        "unit": "particles/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "plummer_kroupa_n%d_theta%.1f_nbr100" % (n, THETA), "n": n, "theta": THETA,
+                   "r_out": w["r_out"], "r_in": w["r_in"], "r_list": w["r_list"], "leaf_cap": args.leaf_cap,
+                   "group_size": args.group_size, "tile": args.tile, "dt": DT, "quadrupole": True,
+                   "precision": "fp32 interactions, fp64 coordinates, compensated sums",
+                   "step": "build_tree + far_force + neighbours + kick + drift",
+                   "l2": "256 MB buffer written between timed steps (L2 is 126 MB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "far_force_evals_per_s": total_particles / (far_ms * 1e-3),
+        "interactions_per_s": inter / (far_ms * 1e-3) * world,
+        "interactions_per_particle": inter / n,
+        "fp32_pct_of_peak": 100.0 * achieved / fp32_peak,
+        "phase_ms": {k: v / args.steps for k, v in ph.items()},
+        "mean_neighbours": nbr_total / n,
+        "roofline": {"bound": "alu", "kernel": "walk_kernel (p3t_far_force)", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": None,
+                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
+                                    % (float(peaks.get("sm_max_mhz", 2032.0)), peak_kind),
+                     "flops_per_launch": FLOPS_PER_INTERACTION * inter},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * KERNELS_PER_STEP,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    ctx.close()
+    return line
+
+
+# kernels launched by one step (build 57, far force 1, neighbours 4, kick 1, drift 1)
+KERNELS_PER_STEP = 4 + 8 * 3 + 1 + 1 + 21 + 1 + 3 + 1 + 1 + 4 + 1 + 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    c, w = workload(args.n, 20211022)
+    times = []
+    samples = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_sample(c, w, max(2.0, args.cpu_budget / 4))
+        if i >= args.warmup:
+            times.append(s["step_s"])
+            samples.append(s)
+    step = statistics.mean(times)
+    value = c.n / step
+    cores = omp_threads()
+    sample = ("per step: oracle tree build of all %d particles, far force + neighbour lists of the first "
+              "~%d particles' groups scaled to all N, kick of all N" % (c.n, samples[-1]["sampled_particles"]))
+    return {
+        "impl": "reference",
+        "metric": "particle far-force evals/sec & interactions/sec at N=1e6 (FP32 % peak); ensemble p50/p99",
+        "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "plummer_kroupa_n%d_theta%.1f_nbr100" % (c.n, THETA), "n": c.n, "theta": THETA,
+                   "r_out": w["r_out"], "r_in": w["r_in"], "r_list": w["r_list"], "leaf_cap": 16,
+                   "group_size": 64, "dt": DT, "quadrupole": True},
+        "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, local, world = dist_init()
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_b300(args, rank, local, world)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

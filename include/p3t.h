@@ -1,0 +1,185 @@
+/*
+ * p3t.h -- C ABI of the distant-force ("regular force") path of the P3T scheme
+ * (Particle-Particle Particle-Tree; arXiv:2110.11658, Sec. 2) on one NVIDIA
+ * B300 GPU (sm_103a).
+ *
+ * The paper's regular-force step (Sec. 2.2, integration steps 1-2 and 4-5;
+ * Sec. 2.4) takes FP64 positions and masses, builds a Barnes-Hut tree,
+ * returns the regular (far) acceleration F_R of Eq. 3 -- the Newtonian force
+ * weighted by W = 1 - K of Eq. 6 -- and the neighbour lists of the constant
+ * neighbour radius (Sec. 2.3), and applies the leapfrog kick of Eq. 12.
+ *
+ * Conventions shared by every call:
+ *  - G = 1 (Henon units, Sec. 3.1).  Accelerations are attractive:
+ *    a_i = sum_j W(r_ij) m_j (x_j - x_i) / r_ij^3.
+ *  - Array arguments are DEVICE pointers owned by the caller (except the
+ *    *_host variants), indexed by the caller's ORIGINAL particle order, in
+ *    structure-of-arrays form (one array per component).
+ *  - Work is enqueued on the context's CUDA stream and is asynchronous unless
+ *    a call says it synchronises.  Errors found on the device (non-finite or
+ *    negative inputs, capacity, a bounded wait that ran out) are latched in the
+ *    context and returned by the next synchronising call (p3t_status,
+ *    p3t_neighbours, p3t_tree_info, p3t_step_host).
+ *  - Every call returns P3T_OK (0) or one of the P3T_ERR_* codes; no call
+ *    throws across the ABI.  Contexts are independent (no global state).
+ *  - A context is not thread-safe: use one per host thread.
+ */
+#ifndef P3T_H
+#define P3T_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define P3T_OK 0
+#define P3T_ERR_INVALID_ARG 1   /* n <= 0, theta < 0, r_in >= r_out, null pointer, bad tuning value */
+#define P3T_ERR_INVALID_INPUT 2 /* a non-finite position or mass, or a negative mass */
+#define P3T_ERR_OOM 3           /* device allocation failed */
+#define P3T_ERR_CAPACITY 4      /* caller buffer too small; the required size is reported */
+#define P3T_ERR_ORDER 5         /* a call that needs a tree came before p3t_build_tree */
+#define P3T_ERR_TIMEOUT 6       /* a bounded device-side wait ran out */
+#define P3T_ERR_CUDA 7          /* a CUDA runtime call failed */
+#define P3T_ERR_INTERNAL 8      /* a device-side consistency check failed (tree walk aborted) */
+
+#define P3T_FP32_MIXED 0 /* FP32 interactions on FP64-subtracted relative coordinates, compensated sums */
+#define P3T_FP64 1       /* every interaction in FP64 */
+
+/* Tuning and physics parameters.
+ *  theta        opening angle of the Barnes-Hut test (Sec. 2.4); 0 opens every cell.
+ *  r_in, r_out  inner and outer radii of the changeover W (Eqs. 6, 8-10; r_out is
+ *               the paper's r_cut).  0 <= r_in < r_out.
+ *  r_list       neighbour-list radius (Sec. 2.3); a pair is listed iff |r| < r_list.
+ *  leaf_cap     a node holding more than leaf_cap particles is split (below level 21).
+ *  group_size   G, the largest particle group that walks the tree together (32, 64 or 128).
+ *  tile         interaction-list tile: a group evaluates its buffered cells and
+ *               particles once `tile` of them are queued (32..256, multiple of 32).
+ *  threads_per_group  threads that evaluate one group (32).
+ *  precision    P3T_FP32_MIXED or P3T_FP64.
+ *  quadrupole   1: monopole + quadrupole cell terms; 0: monopole only. */
+typedef struct {
+    double theta, r_in, r_out, r_list;
+    int32_t leaf_cap, group_size, tile, threads_per_group, precision, quadrupole;
+} p3t_params;
+
+typedef struct p3t_ctx p3t_ctx; /* opaque; owns the tree and all scratch memory */
+
+/* Fill *p with defaults: theta 0.5, r_in 0.005, r_out 0.05, r_list 0.05, leaf_cap 16,
+ * group_size 64, tile 64, threads_per_group 32, P3T_FP32_MIXED, quadrupole 1. */
+int p3t_default_params(p3t_params *p);
+
+/* Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the handle. */
+int p3t_create(p3t_ctx **out, const p3t_params *p, void *cuda_stream);
+
+/* Free every device buffer of the context (synchronises its stream). */
+int p3t_destroy(p3t_ctx *c);
+
+/* Replace the parameters; they take effect at the next p3t_build_tree. */
+int p3t_set_params(p3t_ctx *c, const p3t_params *p);
+
+/* Build the tree of n particles (Sec. 2.4): bounding cube, 63-bit Morton keys,
+ * stable radix sort by (key, index), canonical octree, centre-of-mass,
+ * quadrupole and bounding-box moments, walk groups.  x, y, z, m: device FP64
+ * arrays of length n, read only; they are copied in sorted order, so the
+ * caller may change them afterwards.  Grows the context's scratch if n
+ * exceeds every earlier n (that growth allocates and synchronises).
+ * Errors: P3T_ERR_INVALID_ARG (n <= 0 or n >= 2^31, null pointer);
+ * non-finite coordinates or masses and negative masses are reported later
+ * as P3T_ERR_INVALID_INPUT. */
+int p3t_build_tree(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                   const double *m);
+
+/* Far (regular) acceleration F_R of Eq. 3 for every particle of the last built
+ * tree: the group-wise walk opens a cell iff it fails the opening-angle test
+ * or lies within r_out of the group's box; accepted cells give monopole (+
+ * quadrupole) terms, opened leaves give particle terms weighted by W (Eq. 6).
+ * ax, ay, az: device arrays of n float (P3T_FP32_MIXED) or double (P3T_FP64),
+ * written in original order.  pot: nullable device double[n], the unsplit
+ * Newtonian potential -sum m_j / r_ij (for energy diagnostics).
+ * n_cell_inter, n_part_inter: nullable device int64 counters; the call ADDS
+ * the number of particle-cell and particle-particle interactions evaluated.
+ * Errors: P3T_ERR_ORDER if no tree was built; P3T_ERR_INVALID_ARG for a null
+ * acceleration pointer. */
+int p3t_far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *n_cell_inter,
+                  int64_t *n_part_inter);
+
+/* Neighbour lists of the last built tree (Sec. 2.3): for each particle i all
+ * j != i with |x_i - x_j| < r_list, the distance formed and compared in FP64,
+ * as original indices in ascending order.  Rows may be empty.  CSR layout:
+ * offsets: device int64[n + 1], row i is idx[offsets[i] .. offsets[i+1]);
+ * idx: device int32[capacity].  *total (host) receives the number of entries.
+ * Synchronises the stream once to read the total.  If total > capacity the
+ * call returns P3T_ERR_CAPACITY with *total and offsets set and idx untouched. */
+int p3t_neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *total);
+
+/* As p3t_neighbours without the synchronisation: *total_dev is a device
+ * int64 written on the stream.  If the total exceeds capacity no entry is
+ * written and P3T_ERR_CAPACITY is latched for the next synchronising call. */
+int p3t_neighbours_async(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t capacity,
+                         int64_t *total_dev);
+
+/* Leapfrog kick of Eq. 12, v += (dt/2) a, for the n particles of the last
+ * built tree.  dt is the regular step Delta t_reg.  ax, ay, az: device arrays
+ * of float (P3T_FP32_MIXED) or double (P3T_FP64) as written by p3t_far_force;
+ * vx, vy, vz: device double[n], updated in place.  Arithmetic in FP64. */
+int p3t_kick(p3t_ctx *c, double dt, const void *ax, const void *ay, const void *az, double *vx,
+             double *vy, double *vz);
+
+/* Drift x += dt v over n particles (device FP64 arrays).  Not part of the
+ * paper's regular step: a stand-in for the Hermite integration that moves
+ * the particles between regular steps in benchmarks. */
+int p3t_drift(p3t_ctx *c, int64_t n, double dt, double *x, double *y, double *z, const double *vx,
+              const double *vy, const double *vz);
+
+/* One whole regular step from HOST memory, the paper's REGF + RKICK boundary
+ * (Sec. 2.4, Eq. 12): copy x, y, z, m, vx, vy, vz (host double[n]) to the
+ * device, build, far force, neighbours, kick, and copy back a_far (host
+ * float or double[n] per precision, SoA ax/ay/az), the kicked velocities
+ * (in place in vx, vy, vz) and the neighbour lists (host int64 offsets[n+1],
+ * int32 idx[capacity]).  Synchronises.  Page-locked host memory gives full
+ * copy bandwidth.  *total receives the neighbour count; P3T_ERR_CAPACITY as
+ * in p3t_neighbours (velocities are then kicked but idx is not written). */
+int p3t_step_host(p3t_ctx *c, int64_t n, double dt, const double *x, const double *y,
+                  const double *z, const double *m, double *vx, double *vy, double *vz, void *ax,
+                  void *ay, void *az, int64_t *offsets, int32_t *idx, int64_t capacity,
+                  int64_t *total);
+
+/* Synchronise the stream and return the first latched device error (then
+ * clear it), or the first CUDA error. */
+int p3t_status(p3t_ctx *c);
+
+/* Sizes of the last built tree (synchronises): particles, nodes, groups and
+ * the deepest level; any pointer may be NULL. */
+int p3t_tree_info(p3t_ctx *c, int64_t *n, int64_t *n_nodes, int64_t *n_groups, int32_t *depth);
+
+/* Copy the last built tree into caller device buffers for inspection (any
+ * pointer may be NULL).  Particle arrays have n entries in sorted order:
+ * keys (uint64), perm (int32 sorted -> original).  Node arrays have n_nodes
+ * entries in breadth-first order: level, first, count, child (first child or
+ * -1), nchild (int32); M (double); com, lo, hi (double, n_nodes x 3
+ * row-major); Q (double, n_nodes x 6 as xx, xy, xz, yy, yz, zz; FP32 values
+ * widened in P3T_FP32_MIXED); ropen2 (double).  Group arrays have n_groups
+ * entries in particle order: g_first, g_count (int32). */
+int p3t_export_tree(p3t_ctx *c, uint64_t *keys, int32_t *perm, int32_t *level, int32_t *first,
+                    int32_t *count, int32_t *child, int32_t *nchild, double *M, double *com,
+                    double *Q, double *lo, double *hi, double *ropen2, int32_t *g_first,
+                    int32_t *g_count);
+
+/* Per-group interaction counts of the last p3t_far_force (device int64
+ * n_groups each, in group order): accepted cells and source particles in
+ * opened leaves.  Filled only when the walk ran after p3t_set_debug(c, 1). */
+int p3t_group_counts(p3t_ctx *c, int64_t *n_cell, int64_t *n_part);
+
+/* 1: record per-group counts in the walk (slightly slower); 0: off (default). */
+int p3t_set_debug(p3t_ctx *c, int on);
+
+/* Static description of an error code. */
+const char *p3t_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P3T_H */

@@ -1,0 +1,291 @@
+"""B300 (sm_103a) library for the distant-force path of the P3T scheme.
+
+arXiv:2110.11658, Sec. 2: the regular (far) force F_R of Eq. 3 -- Newtonian
+gravity weighted by the changeover W = 1 - K of Eq. 6 -- from a Barnes-Hut
+tree with opening angle theta (Sec. 2.4), the constant-radius neighbour lists
+of Sec. 2.3, and the leapfrog kick of Eq. 12.
+
+Everything runs in hand-written CUDA kernels behind the C ABI of
+``include/p3t.h`` (``libp3t.so``).  This package only marshals arguments:
+the low-level functions carry the ABI's names (``p3t_create``,
+``p3t_build_tree``, ...) and take raw pointers; ``Context`` wraps them for
+PyTorch CUDA tensors.  There is no CPU fallback: importing fails if the
+shared library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libp3t.so")
+
+P3T_OK = 0
+P3T_ERR_INVALID_ARG = 1
+P3T_ERR_INVALID_INPUT = 2
+P3T_ERR_OOM = 3
+P3T_ERR_CAPACITY = 4
+P3T_ERR_ORDER = 5
+P3T_ERR_TIMEOUT = 6
+P3T_ERR_CUDA = 7
+P3T_ERR_INTERNAL = 8
+P3T_FP32_MIXED = 0
+P3T_FP64 = 1
+
+EXPORTED = [
+    "p3t_default_params", "p3t_create", "p3t_destroy", "p3t_set_params", "p3t_build_tree",
+    "p3t_far_force", "p3t_neighbours", "p3t_neighbours_async", "p3t_kick", "p3t_drift",
+    "p3t_step_host", "p3t_status", "p3t_tree_info", "p3t_export_tree", "p3t_group_counts",
+    "p3t_set_debug", "p3t_error_string",
+]
+
+
+class p3t_params(C.Structure):
+    _fields_ = [("theta", C.c_double), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("r_list", C.c_double), ("leaf_cap", C.c_int32), ("group_size", C.c_int32),
+                ("tile", C.c_int32), ("threads_per_group", C.c_int32), ("precision", C.c_int32),
+                ("quadrupole", C.c_int32)]
+
+
+class P3TError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__("%s failed: %s (code %d)" % (where, p3t_error_string(code), code))
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libp3t.so is not built (run paper_2110_11658_b300/build.py); "
+                      "there is no CPU fallback")
+_lib = C.CDLL(LIB_PATH)
+
+_vp = C.c_void_p
+_i64 = C.c_int64
+_sig = {
+    "p3t_default_params": [C.POINTER(p3t_params)],
+    "p3t_create": [C.POINTER(_vp), C.POINTER(p3t_params), _vp],
+    "p3t_destroy": [_vp],
+    "p3t_set_params": [_vp, C.POINTER(p3t_params)],
+    "p3t_build_tree": [_vp, _i64, _vp, _vp, _vp, _vp],
+    "p3t_far_force": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "p3t_neighbours": [_vp, _vp, _vp, _i64, C.POINTER(_i64)],
+    "p3t_neighbours_async": [_vp, _vp, _vp, _i64, _vp],
+    "p3t_kick": [_vp, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
+    "p3t_drift": [_vp, _i64, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp],
+    "p3t_step_host": [_vp, _i64, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                      _vp, _vp, _i64, C.POINTER(_i64)],
+    "p3t_status": [_vp],
+    "p3t_tree_info": [_vp, C.POINTER(_i64), C.POINTER(_i64), C.POINTER(_i64), C.POINTER(C.c_int32)],
+    "p3t_export_tree": [_vp] + [_vp] * 15,
+    "p3t_group_counts": [_vp, _vp, _vp],
+    "p3t_set_debug": [_vp, C.c_int],
+    "p3t_error_string": [C.c_int],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_char_p if _name == "p3t_error_string" else C.c_int
+    globals()[_name] = _f
+
+
+def p3t_error_string(code: int) -> str:  # noqa: F811  (str instead of bytes)
+    return _lib.p3t_error_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != P3T_OK:
+        raise P3TError(code, where)
+
+
+@dataclass
+class Params:
+    """Python view of p3t_params (defaults of p3t_default_params)."""
+
+    theta: float = 0.5
+    r_in: float = 0.005
+    r_out: float = 0.05
+    r_list: float = 0.05
+    leaf_cap: int = 16
+    group_size: int = 64
+    tile: int = 64
+    threads_per_group: int = 32
+    precision: int = P3T_FP32_MIXED
+    quadrupole: int = 1
+
+    def to_c(self) -> p3t_params:
+        return p3t_params(self.theta, self.r_in, self.r_out, self.r_list, self.leaf_cap,
+                          self.group_size, self.tile, self.threads_per_group, self.precision,
+                          self.quadrupole)
+
+
+def _ptr(t, dtype=None, n=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (checked), or None."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if n is not None and t.numel() < n:
+        raise ValueError("%s has %d elements, needs %d" % (name, t.numel(), n))
+    return t.data_ptr()
+
+
+class Context:
+    """One p3t_ctx bound to a CUDA stream (torch's current stream by default)."""
+
+    def __init__(self, params: Params | None = None, stream=None):
+        import torch
+        self._torch = torch
+        self.params = params or Params()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        cp = self.params.to_c()
+        _check(_lib.p3t_create(C.byref(h), C.byref(cp), C.c_void_p(stream.cuda_stream)), "p3t_create")
+        self._h = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.p3t_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def acc_dtype(self):
+        t = self._torch
+        return t.float64 if self.params.precision == P3T_FP64 else t.float32
+
+    def set_params(self, params: Params):
+        cp = params.to_c()
+        _check(_lib.p3t_set_params(self._h, C.byref(cp)), "p3t_set_params")
+        self.params = params
+
+    def set_debug(self, on: bool):
+        _check(_lib.p3t_set_debug(self._h, int(bool(on))), "p3t_set_debug")
+
+    def build_tree(self, x, y, z, m):
+        t = self._torch
+        n = x.numel()
+        args = [_ptr(a, t.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")]
+        _check(_lib.p3t_build_tree(self._h, n, *args), "p3t_build_tree")
+        self.n = n
+
+    def far_force(self, ax, ay, az, pot=None, n_cell=None, n_part=None):
+        t = self._torch
+        d = self.acc_dtype
+        _check(_lib.p3t_far_force(self._h, _ptr(ax, d, self.n, "ax"), _ptr(ay, d, self.n, "ay"),
+                                  _ptr(az, d, self.n, "az"), _ptr(pot, t.float64, self.n, "pot"),
+                                  _ptr(n_cell, t.int64, 1, "n_cell"), _ptr(n_part, t.int64, 1, "n_part")),
+               "p3t_far_force")
+
+    def neighbours(self, offsets, idx, capacity=None):
+        """Synchronous: returns the total number of entries (raises on capacity)."""
+        t = self._torch
+        cap = idx.numel() if (idx is not None and capacity is None) else int(capacity or 0)
+        tot = C.c_int64(0)
+        code = _lib.p3t_neighbours(self._h, _ptr(offsets, t.int64, self.n + 1, "offsets"),
+                                   _ptr(idx, t.int32, cap, "idx") if idx is not None else None,
+                                   cap, C.byref(tot))
+        if code == P3T_ERR_CAPACITY:
+            err = P3TError(code, "p3t_neighbours")
+            err.total = tot.value
+            raise err
+        _check(code, "p3t_neighbours")
+        return tot.value
+
+    def neighbours_async(self, offsets, idx, total_dev, capacity=None):
+        t = self._torch
+        cap = idx.numel() if capacity is None else int(capacity)
+        _check(_lib.p3t_neighbours_async(self._h, _ptr(offsets, t.int64, self.n + 1, "offsets"),
+                                         _ptr(idx, t.int32, cap, "idx"), cap,
+                                         _ptr(total_dev, t.int64, 1, "total")),
+               "p3t_neighbours_async")
+
+    def kick(self, dt, ax, ay, az, vx, vy, vz):
+        t = self._torch
+        d = self.acc_dtype
+        _check(_lib.p3t_kick(self._h, float(dt), _ptr(ax, d, self.n, "ax"), _ptr(ay, d, self.n, "ay"),
+                             _ptr(az, d, self.n, "az"), _ptr(vx, t.float64, self.n, "vx"),
+                             _ptr(vy, t.float64, self.n, "vy"), _ptr(vz, t.float64, self.n, "vz")),
+               "p3t_kick")
+
+    def drift(self, dt, x, y, z, vx, vy, vz):
+        t = self._torch
+        n = x.numel()
+        _check(_lib.p3t_drift(self._h, n, float(dt), *[_ptr(a, t.float64, n) for a in (x, y, z, vx, vy, vz)]),
+               "p3t_drift")
+
+    def step_host(self, dt, x, y, z, m, vx, vy, vz, ax, ay, az, offsets, idx):
+        """p3t_step_host on (preferably pinned) CPU tensors; returns the neighbour total."""
+        n = x.numel()
+        for a in (x, y, z, m, vx, vy, vz, ax, ay, az, offsets, idx):
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError("step_host takes contiguous host tensors")
+        tot = C.c_int64(0)
+        code = _lib.p3t_step_host(self._h, n, float(dt), *[a.data_ptr() for a in (x, y, z, m, vx, vy, vz, ax, ay, az, offsets, idx)],
+                                  idx.numel(), C.byref(tot))
+        if code == P3T_ERR_CAPACITY:
+            err = P3TError(code, "p3t_step_host")
+            err.total = tot.value
+            raise err
+        _check(code, "p3t_step_host")
+        self.n = n
+        return tot.value
+
+    def status(self):
+        return _lib.p3t_status(self._h)
+
+    def check(self):
+        _check(self.status(), "p3t_status")
+
+    def tree_info(self):
+        n, nn, ng, d = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()
+        _check(_lib.p3t_tree_info(self._h, C.byref(n), C.byref(nn), C.byref(ng), C.byref(d)),
+               "p3t_tree_info")
+        return {"n": n.value, "n_nodes": nn.value, "n_groups": ng.value, "depth": d.value}
+
+    def export_tree(self):
+        """Copy of the built tree as CUDA tensors (same layout as the ABI)."""
+        t = self._torch
+        info = self.tree_info()
+        n, nn, ng = info["n"], info["n_nodes"], info["n_groups"]
+        dev = t.device("cuda", t.cuda.current_device())
+        o = {
+            "keys": t.empty(n, dtype=t.int64, device=dev), "perm": t.empty(n, dtype=t.int32, device=dev),
+            "level": t.empty(nn, dtype=t.int32, device=dev), "first": t.empty(nn, dtype=t.int32, device=dev),
+            "count": t.empty(nn, dtype=t.int32, device=dev), "child": t.empty(nn, dtype=t.int32, device=dev),
+            "nchild": t.empty(nn, dtype=t.int32, device=dev), "M": t.empty(nn, dtype=t.float64, device=dev),
+            "com": t.empty(nn, 3, dtype=t.float64, device=dev), "Q": t.empty(nn, 6, dtype=t.float64, device=dev),
+            "lo": t.empty(nn, 3, dtype=t.float64, device=dev), "hi": t.empty(nn, 3, dtype=t.float64, device=dev),
+            "ropen2": t.empty(nn, dtype=t.float64, device=dev),
+            "g_first": t.empty(ng, dtype=t.int32, device=dev), "g_count": t.empty(ng, dtype=t.int32, device=dev),
+        }
+        order = ["keys", "perm", "level", "first", "count", "child", "nchild", "M", "com", "Q", "lo", "hi",
+                 "ropen2", "g_first", "g_count"]
+        _check(_lib.p3t_export_tree(self._h, *[o[k].data_ptr() if o[k].numel() else None for k in order]),
+               "p3t_export_tree")
+        self.check()
+        return o
+
+    def group_counts(self):
+        t = self._torch
+        ng = self.tree_info()["n_groups"]
+        c = t.empty(ng, dtype=t.int64, device="cuda")
+        p = t.empty(ng, dtype=t.int64, device="cuda")
+        _check(_lib.p3t_group_counts(self._h, c.data_ptr(), p.data_ptr()), "p3t_group_counts")
+        self.check()
+        return c, p

@@ -1,0 +1,721 @@
+// Tree build of the distant-force path (Sec. 2.4: Barnes-Hut tree).
+//
+// Steps (all on the context's stream, no host synchronisation):
+//   bbox      FP64 min/max over x, y, z (order-preserving integer atomics),
+//             input validation (finite x, y, z, m; m >= 0)
+//   keys      q_d = floor((x_d - min_d) * 2^21/side), clamped, interleaved
+//             into a 63-bit Morton key (bit 3k+2 <- q_x, 3k+1 <- q_y, 3k <- q_z)
+//   sort      stable LSD radix sort of (key, index), 8 passes of 8 bits
+//   gather    particles in key order as double4_32a {x, y, z, m}
+//   topology  canonical octree level by level (a node at level l is split iff
+//             it holds more than leaf_cap particles and l < 21; children are
+//             the non-empty octants, numbered breadth first via a look-back
+//             scan per level); walk-group starts are flagged on the way
+//   groups    flags -> scan -> ranges, tight FP64 boxes
+//   moments   bottom-up: each leaf sums its particles in key order, the last
+//             child to finish combines its parent's children in octant order
+//             (mass, COM, traceless quadrupole, box, opening radius)
+// Every FP64 operation that feeds a decision uses round-to-nearest intrinsics
+// with no contraction, so keys, topology, COMs, boxes and opening radii are
+// reproducible bit for bit.
+#include <cstdint>
+
+#include "p3t_internal.cuh"
+
+namespace p3t {
+
+constexpr int kBuildThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kBuildThreads * kSortItems;
+constexpr unsigned long long kQMax = (1ULL << 21) - 1;
+
+int topo_status_stride(long long n);
+
+// ---------------------------------------------------------------------------
+// metadata reset
+__global__ void init_meta_kernel(Meta *m)
+{
+    int t = threadIdx.x;
+    if (t < kMaxLevelSlots) {
+        m->level_start[t] = 0;
+        m->level_count[t] = 0;
+    }
+    if (t < 32) m->tickets[t] = 0;
+    if (t < 3) {
+        m->minmax[t] = ~0ULL;   // running minimum
+        m->minmax[3 + t] = 0;   // running maximum
+    }
+    if (t == 0) {
+        m->n_nodes = 0;
+        m->n_groups = 0;
+        m->depth = 0;
+        m->fallback_tests = 0;
+    }
+}
+
+// order-preserving map of non-NaN doubles onto unsigned integers
+__device__ __forceinline__ unsigned long long enc_double(double v)
+{
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double dec_double(unsigned long long e)
+{
+    unsigned long long u = (e >> 63) ? (e ^ 0x8000000000000000ULL) : ~e;
+    return __longlong_as_double((long long)u);
+}
+
+__global__ void __launch_bounds__(kBuildThreads)
+    bbox_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
+                const double *__restrict__ z, const double *__restrict__ m, Meta *meta)
+{
+    unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0, 0, 0};
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double p[3] = {x[i], y[i], z[i]};
+        double mi = m[i];
+        bool ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(mi) && mi >= 0.0;
+        bad |= !ok;
+        if (!ok) continue;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            unsigned long long e = enc_double(p[d]);
+            mn[d] = e < mn[d] ? e : mn[d];
+            mx[d] = e > mx[d] ? e : mx[d];
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], o);
+            unsigned long long b = __shfl_xor_sync(0xffffffffu, mx[d], o);
+            mn[d] = a < mn[d] ? a : mn[d];
+            mx[d] = b > mx[d] ? b : mx[d];
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) latch_error(meta, P3T_ERR_INVALID_INPUT);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            atomicMin(&meta->minmax[d], mn[d]);
+            atomicMax(&meta->minmax[3 + d], mx[d]);
+        }
+    }
+}
+
+// rule 1: the bounding cube, and the frame of the FP32 walk filter
+__global__ void cube_kernel(Meta *meta)
+{
+    double lo[3], hi[3], side = 0.0;
+    for (int d = 0; d < 3; d++) {
+        lo[d] = dec_double(meta->minmax[d]);
+        hi[d] = dec_double(meta->minmax[3 + d]);
+        if (meta->minmax[d] == ~0ULL) lo[d] = hi[d] = 0.0;  // no valid particle
+        double ext = dsub(hi[d], lo[d]);
+        if (ext > side) side = ext;
+    }
+    if (side == 0.0) side = 1.0;
+    double R = 0.0;
+    for (int d = 0; d < 3; d++) {
+        meta->cube[d] = lo[d];
+        double o = dmul(0.5, dadd(lo[d], hi[d]));
+        meta->frame[d] = o;
+        R = dmax(R, dmax(dsub(hi[d], o), dsub(o, lo[d])));
+    }
+    meta->cube[3] = side;
+    // |x - O| <= R for every particle; pad for the rounding of O
+    meta->frame[3] = R * (1.0 + 1e-9) + 1e-300;
+}
+
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v)
+{
+    v &= 0x1fffffULL;
+    v = (v | (v << 32)) & 0x1f00000000ffffULL;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+    v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+    v = (v | (v << 2)) & 0x1249249249249249ULL;
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long quantise(double v, double lo, double s)
+{
+    double t = floor(dmul(dsub(v, lo), s));
+    if (!(t >= 0.0)) return 0;  // also NaN
+    if (t > (double)kQMax) return kQMax;
+    return (unsigned long long)t;
+}
+
+__global__ void __launch_bounds__(kBuildThreads)
+    keys_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
+                const double *__restrict__ z, const Meta *__restrict__ meta,
+                uint64_t *__restrict__ keys, int32_t *__restrict__ perm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = ddiv(2097152.0, meta->cube[3]);
+    unsigned long long qx = quantise(x[i], meta->cube[0], s);
+    unsigned long long qy = quantise(y[i], meta->cube[1], s);
+    unsigned long long qz = quantise(z[i], meta->cube[2], s);
+    keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    perm[i] = i;
+}
+
+// ---------------------------------------------------------------------------
+// radix sort: per-block digit histograms, a scan, then a stable scatter
+__global__ void __launch_bounds__(kBuildThreads)
+    sort_hist_kernel(int n, const uint64_t *__restrict__ keys, int shift, int nblocks,
+                     int32_t *__restrict__ hist)
+{
+    __shared__ int cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int k = 0; k < kSortItems; k++) {
+        long long i = base + k * kBuildThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kBuildThreads)
+    sort_scatter_kernel(int n, const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin,
+                        uint64_t *__restrict__ kout, int32_t *__restrict__ vout, int shift,
+                        int nblocks, const int32_t *__restrict__ hist_off)
+{
+    constexpr int W = kBuildThreads / 32;
+    __shared__ int gofs[256];
+    __shared__ int wcnt[W][256];
+    __shared__ int pofs[W][256];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    gofs[tid] = hist_off[tid * nblocks + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < W; w++) wcnt[w][tid] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    const long long base = (long long)blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortItems; r++) {
+        long long i = base + r * kBuildThreads + tid;
+        bool valid = i < n;
+        uint64_t key = valid ? kin[i] : 0;
+        int32_t val = valid ? vin[i] : 0;
+        int d = valid ? (int)((key >> shift) & 255) : 256;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int wrank = __popc(peers & lt);
+        if (valid && wrank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            int s = gofs[tid];
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                int c = wcnt[w][tid];
+                pofs[w][tid] = s;
+                wcnt[w][tid] = 0;
+                s += c;
+            }
+            gofs[tid] = s;
+        }
+        __syncthreads();
+        if (valid) {
+            int pos = pofs[warp][d] + wrank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBuildThreads)
+    gather_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
+                  const double *__restrict__ z, const double *__restrict__ m,
+                  const int32_t *__restrict__ perm, double4_32a *__restrict__ sp)
+{
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int i = perm[s];
+    sp[s] = make_double4_32a(x[i], y[i], z[i], m[i]);
+}
+
+// ---------------------------------------------------------------------------
+// topology
+
+// flag the walk groups a new node starts (rule 7)
+__device__ __forceinline__ void flag_groups(unsigned char *gflag, int first, int count,
+                                            bool parent_big, bool is_leaf, int G)
+{
+    if (!parent_big) return;
+    if (count <= G) {
+        gflag[first] = 1;
+    } else if (is_leaf) {
+        for (int f = 0; f < count; f += G) gflag[first + f] = 1;
+    }
+}
+
+__global__ void topo_root_kernel(Tree T, int n, int leaf_cap, int G)
+{
+    T.topo[0] = make_int4(0, n, -1, 0);
+    T.level[0] = 0;
+    T.parent[0] = -1;
+    T.ready[0] = 0;
+    T.meta->level_start[0] = 0;
+    T.meta->level_count[0] = 1;
+    flag_groups(T.gflag, 0, n, true, n <= leaf_cap, G);
+}
+
+__device__ __forceinline__ int lower_bound_key(const uint64_t *__restrict__ keys, int lo, int hi,
+                                               uint64_t target)
+{
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (keys[mid] < target)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kBuildThreads)
+    topo_level_kernel(Tree T, int l, int leaf_cap, int G, unsigned long long *status,
+                      unsigned int *ticket)
+{
+    __shared__ unsigned int sh_t;
+    __shared__ long long sh_scan[32];
+    __shared__ long long sh_pre;
+    Meta *M = T.meta;
+    const int nl = M->level_count[l];
+    const int base = M->level_start[l];
+    const int ntiles = (nl + kBuildThreads - 1) / kBuildThreads;
+    const int shift = 63 - 3 * (l + 1);
+    while (true) {
+        if (threadIdx.x == 0) sh_t = atomicAdd(ticket, 1u);
+        __syncthreads();
+        const int t = (int)sh_t;
+        __syncthreads();
+        if (t >= ntiles) break;
+        const int node = base + t * kBuildThreads + threadIdx.x;
+        const bool mine = node < base + nl;
+        int bnd[9];
+        int nch = 0;
+        int4 tp = make_int4(0, 0, -1, 0);
+        if (mine) tp = T.topo[node];
+        const bool split = mine && tp.y > leaf_cap && l < kLevels;
+        if (split) {
+            const int b = tp.x, e = tp.x + tp.y;
+            const uint64_t pfx = T.keys[b] >> (shift + 3);
+            bnd[0] = b;
+            bnd[8] = e;
+#pragma unroll
+            for (int o = 1; o < 8; o++)
+                bnd[o] = lower_bound_key(T.keys, bnd[o - 1], e, ((pfx << 3) | (uint64_t)o) << shift);
+#pragma unroll
+            for (int o = 0; o < 8; o++) nch += bnd[o + 1] > bnd[o];
+        }
+        long long tot;
+        long long ex = block_excl_scan<long long>((long long)nch, &tot, sh_scan);
+        long long pre = lookback_prefix(status, t, tot, M, &sh_pre);
+        const int child_base = base + nl + (int)(pre + ex);
+        if (split) {
+            const bool big = tp.y > G;
+            if (child_base + nch > T.cap_nodes) {
+                latch_error(M, P3T_ERR_CAPACITY);
+            } else {
+                int k = 0;
+#pragma unroll
+                for (int o = 0; o < 8; o++) {
+                    int cnt = bnd[o + 1] - bnd[o];
+                    if (cnt > 0) {
+                        int c = child_base + k++;
+                        T.topo[c] = make_int4(bnd[o], cnt, -1, 0);
+                        T.level[c] = l + 1;
+                        T.parent[c] = node;
+                        T.ready[c] = 0;
+                        bool leaf = cnt <= leaf_cap || l + 1 >= kLevels;
+                        flag_groups(T.gflag, bnd[o], cnt, big, leaf, G);
+                    }
+                }
+                T.topo[node] = make_int4(tp.x, tp.y, child_base, nch);
+            }
+        }
+        if (t == ntiles - 1 && threadIdx.x == 0) {
+            M->level_start[l + 1] = base + nl;
+            M->level_count[l + 1] = (int)(pre + tot);
+        }
+    }
+}
+
+__global__ void topo_finish_kernel(Meta *M, int cap_nodes)
+{
+    int total = 0, depth = 0;
+    for (int l = 0; l <= kLevels; l++) {
+        total += M->level_count[l];
+        if (M->level_count[l] > 0) depth = l;
+    }
+    if (total > cap_nodes) latch_error(M, P3T_ERR_CAPACITY);
+    M->n_nodes = total;
+    M->depth = depth;
+}
+
+// ---------------------------------------------------------------------------
+// groups
+__global__ void __launch_bounds__(kBuildThreads)
+    group_first_kernel(int n, const unsigned char *__restrict__ gflag,
+                       const int32_t *__restrict__ gidx, int2 *__restrict__ grp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && gflag[i]) grp[gidx[i]].x = i;
+}
+
+__device__ __forceinline__ double upd_min(double lo, double p) { return p < lo ? p : lo; }
+__device__ __forceinline__ double upd_max(double hi, double p) { return p > hi ? p : hi; }
+
+// one warp per group: count and tight box (exact min/max, order-free)
+__global__ void __launch_bounds__(kBuildThreads) group_finish_kernel(Tree T, int n)
+{
+    const int ng = T.meta->n_groups;
+    const int lane = threadIdx.x & 31;
+    for (int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng;
+         g += (gridDim.x * blockDim.x) >> 5) {
+        const int first = T.grp[g].x;
+        const int end = g + 1 < ng ? T.grp[g + 1].x : n;
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int i = first + lane; i < end; i += 32) {
+            double4_32a p = T.sp[i];
+            lo[0] = upd_min(lo[0], p.x), hi[0] = upd_max(hi[0], p.x);
+            lo[1] = upd_min(lo[1], p.y), hi[1] = upd_max(hi[1], p.y);
+            lo[2] = upd_min(lo[2], p.z), hi[2] = upd_max(hi[2], p.z);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[d] = upd_min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+                hi[d] = upd_max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+            }
+        }
+        if (lane == 0) {
+            T.grp[g].y = end - first;
+            T.glo[g] = make_double4_32a(lo[0], lo[1], lo[2], 0.0);
+            T.ghi[g] = make_double4_32a(hi[0], hi[1], hi[2], 0.0);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// moments (rule 6) and the opening radius (rule 8)
+
+template <bool Q64>
+__device__ void write_node(Tree &T, int k, double M, const double com[3], const double lo[3],
+                           const double hi[3], const double *q, double theta, int4 tp)
+{
+    // opening radius l/theta + delta
+    double l = dsub(hi[0], lo[0]);
+    if (dsub(hi[1], lo[1]) > l) l = dsub(hi[1], lo[1]);
+    if (dsub(hi[2], lo[2]) > l) l = dsub(hi[2], lo[2]);
+    double cx = dsub(dmul(0.5, dadd(lo[0], hi[0])), com[0]);
+    double cy = dsub(dmul(0.5, dadd(lo[1], hi[1])), com[1]);
+    double cz = dsub(dmul(0.5, dadd(lo[2], hi[2])), com[2]);
+    double delta = dsqrt(dadd(dadd(dmul(cx, cx), dmul(cy, cy)), dmul(cz, cz)));
+    double ro2;
+    if (theta > 0.0) {
+        double ro = dadd(ddiv(l, theta), delta);
+        ro2 = dmul(ro, ro);
+    } else {
+        ro2 = INFINITY;
+    }
+    T.comM[k] = make_double4_32a(com[0], com[1], com[2], M);
+    T.lo[k] = make_double4_32a(lo[0], lo[1], lo[2], ro2);
+    T.hi[k] = make_double4_32a(hi[0], hi[1], hi[2], 0.0);
+    if (Q64) {
+        double2 *q2 = reinterpret_cast<double2 *>(T.q64 + 6 * (size_t)k);
+        q2[0] = make_double2(q[0], q[1]);
+        q2[1] = make_double2(q[2], q[3]);
+        q2[2] = make_double2(q[4], q[5]);
+    } else {
+        float2 *q2 = reinterpret_cast<float2 *>(T.q32 + 6 * (size_t)k);
+        q2[0] = make_float2((float)q[0], (float)q[1]);
+        q2[1] = make_float2((float)q[2], (float)q[3]);
+        q2[2] = make_float2((float)q[4], (float)q[5]);
+    }
+    const double *O = T.meta->frame;
+    const bool leaf = tp.z < 0;
+    T.wA[k] = make_float4(__double2float_rn(dsub(com[0], O[0])), __double2float_rn(dsub(com[1], O[1])),
+                          __double2float_rn(dsub(com[2], O[2])), __double2float_rn(ro2));
+    T.wB[k] = make_float4(__double2float_rn(dsub(lo[0], O[0])), __double2float_rn(dsub(lo[1], O[1])),
+                          __double2float_rn(dsub(lo[2], O[2])),
+                          __int_as_float(leaf ? -1 - tp.x : tp.z));
+    T.wC[k] = make_float4(__double2float_rn(dsub(hi[0], O[0])), __double2float_rn(dsub(hi[1], O[1])),
+                          __double2float_rn(dsub(hi[2], O[2])), __int_as_float(leaf ? tp.y : tp.w));
+}
+
+template <bool Q64>
+__device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
+{
+    const int b = tp.x, e = tp.x + tp.y;
+    double M = 0.0, S[3] = {0, 0, 0}, lo[3] = {INFINITY, INFINITY, INFINITY},
+           hi[3] = {-INFINITY, -INFINITY, -INFINITY}, com[3];
+    for (int i = b; i < e; i++) {
+        double4_32a p = T.sp[i];
+        M = dadd(M, p.w);
+        S[0] = dadd(S[0], dmul(p.w, p.x));
+        S[1] = dadd(S[1], dmul(p.w, p.y));
+        S[2] = dadd(S[2], dmul(p.w, p.z));
+        lo[0] = upd_min(lo[0], p.x), hi[0] = upd_max(hi[0], p.x);
+        lo[1] = upd_min(lo[1], p.y), hi[1] = upd_max(hi[1], p.y);
+        lo[2] = upd_min(lo[2], p.z), hi[2] = upd_max(hi[2], p.z);
+    }
+    for (int d = 0; d < 3; d++) com[d] = M > 0.0 ? ddiv(S[d], M) : dmul(0.5, dadd(lo[d], hi[d]));
+    double q[6];
+    if (Q64) {
+        double Q[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = b; i < e; i++) {
+            double4_32a p = T.sp[i];
+            double m = p.w;
+            double dx = dsub(p.x, com[0]), dy = dsub(p.y, com[1]), dz = dsub(p.z, com[2]);
+            double r2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+            Q[0] = dadd(Q[0], dmul(m, dsub(dmul(dmul(3.0, dx), dx), r2)));
+            Q[1] = dadd(Q[1], dmul(m, dmul(dmul(3.0, dx), dy)));
+            Q[2] = dadd(Q[2], dmul(m, dmul(dmul(3.0, dx), dz)));
+            Q[3] = dadd(Q[3], dmul(m, dsub(dmul(dmul(3.0, dy), dy), r2)));
+            Q[4] = dadd(Q[4], dmul(m, dmul(dmul(3.0, dy), dz)));
+            Q[5] = dadd(Q[5], dmul(m, dsub(dmul(dmul(3.0, dz), dz), r2)));
+        }
+        for (int a = 0; a < 6; a++) q[a] = Q[a];
+    } else {
+        // FP32 quadrupole on FP64-subtracted offsets
+        float Q[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = b; i < e; i++) {
+            double4_32a p = T.sp[i];
+            float m = (float)p.w;
+            float dx = __double2float_rn(dsub(p.x, com[0]));
+            float dy = __double2float_rn(dsub(p.y, com[1]));
+            float dz = __double2float_rn(dsub(p.z, com[2]));
+            float r2 = dx * dx + dy * dy + dz * dz;
+            Q[0] += m * (3.f * dx * dx - r2);
+            Q[1] += m * (3.f * dx * dy);
+            Q[2] += m * (3.f * dx * dz);
+            Q[3] += m * (3.f * dy * dy - r2);
+            Q[4] += m * (3.f * dy * dz);
+            Q[5] += m * (3.f * dz * dz - r2);
+        }
+        for (int a = 0; a < 6; a++) q[a] = Q[a];
+    }
+    write_node<Q64>(T, k, M, com, lo, hi, q, theta, tp);
+}
+
+// L2-coherent load of a value written by another block in this kernel
+__device__ __forceinline__ double4_32a ldcg_d4(const double4_32a *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    double2 a = __ldcg(q), b = __ldcg(q + 1);
+    return make_double4_32a(a.x, a.y, b.x, b.y);
+}
+
+template <bool Q64>
+__device__ void internal_moments(Tree &T, int k, int4 tp, double theta)
+{
+    const int c0 = tp.z, c1 = tp.z + tp.w;
+    double M = 0.0, S[3] = {0, 0, 0}, lo[3] = {INFINITY, INFINITY, INFINITY},
+           hi[3] = {-INFINITY, -INFINITY, -INFINITY}, com[3];
+    for (int c = c0; c < c1; c++) {
+        double4_32a cm = ldcg_d4(&T.comM[c]);
+        double4_32a cl = ldcg_d4(&T.lo[c]);
+        double4_32a ch = ldcg_d4(&T.hi[c]);
+        M = dadd(M, cm.w);
+        S[0] = dadd(S[0], dmul(cm.w, cm.x));
+        S[1] = dadd(S[1], dmul(cm.w, cm.y));
+        S[2] = dadd(S[2], dmul(cm.w, cm.z));
+        lo[0] = upd_min(lo[0], cl.x), hi[0] = upd_max(hi[0], ch.x);
+        lo[1] = upd_min(lo[1], cl.y), hi[1] = upd_max(hi[1], ch.y);
+        lo[2] = upd_min(lo[2], cl.z), hi[2] = upd_max(hi[2], ch.z);
+    }
+    for (int d = 0; d < 3; d++) com[d] = M > 0.0 ? ddiv(S[d], M) : dmul(0.5, dadd(lo[d], hi[d]));
+    double q[6];
+    if (Q64) {
+        double Q[6] = {0, 0, 0, 0, 0, 0};
+        for (int c = c0; c < c1; c++) {
+            double4_32a cm = ldcg_d4(&T.comM[c]);
+            const double *Qc = T.q64 + 6 * (size_t)c;
+            double Mc = cm.w;
+            double dx = dsub(cm.x, com[0]), dy = dsub(cm.y, com[1]), dz = dsub(cm.z, com[2]);
+            double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
+            Q[0] = dadd(Q[0], dadd(__ldcg(Qc + 0), dmul(Mc, dsub(dmul(dmul(3.0, dx), dx), d2))));
+            Q[1] = dadd(Q[1], dadd(__ldcg(Qc + 1), dmul(Mc, dmul(dmul(3.0, dx), dy))));
+            Q[2] = dadd(Q[2], dadd(__ldcg(Qc + 2), dmul(Mc, dmul(dmul(3.0, dx), dz))));
+            Q[3] = dadd(Q[3], dadd(__ldcg(Qc + 3), dmul(Mc, dsub(dmul(dmul(3.0, dy), dy), d2))));
+            Q[4] = dadd(Q[4], dadd(__ldcg(Qc + 4), dmul(Mc, dmul(dmul(3.0, dy), dz))));
+            Q[5] = dadd(Q[5], dadd(__ldcg(Qc + 5), dmul(Mc, dsub(dmul(dmul(3.0, dz), dz), d2))));
+        }
+        for (int a = 0; a < 6; a++) q[a] = Q[a];
+    } else {
+        float Q[6] = {0, 0, 0, 0, 0, 0};
+        for (int c = c0; c < c1; c++) {
+            double4_32a cm = ldcg_d4(&T.comM[c]);
+            const float *Qc = T.q32 + 6 * (size_t)c;
+            float Mc = (float)cm.w;
+            float dx = __double2float_rn(dsub(cm.x, com[0]));
+            float dy = __double2float_rn(dsub(cm.y, com[1]));
+            float dz = __double2float_rn(dsub(cm.z, com[2]));
+            float d2 = dx * dx + dy * dy + dz * dz;
+            Q[0] += __ldcg(Qc + 0) + Mc * (3.f * dx * dx - d2);
+            Q[1] += __ldcg(Qc + 1) + Mc * (3.f * dx * dy);
+            Q[2] += __ldcg(Qc + 2) + Mc * (3.f * dx * dz);
+            Q[3] += __ldcg(Qc + 3) + Mc * (3.f * dy * dy - d2);
+            Q[4] += __ldcg(Qc + 4) + Mc * (3.f * dy * dz);
+            Q[5] += __ldcg(Qc + 5) + Mc * (3.f * dz * dz - d2);
+        }
+        for (int a = 0; a < 6; a++) q[a] = Q[a];
+    }
+    write_node<Q64>(T, k, M, com, lo, hi, q, theta, tp);
+}
+
+template <bool Q64>
+__global__ void __launch_bounds__(kBuildThreads) moments_kernel(Tree T, double theta)
+{
+    const int nn = T.meta->n_nodes;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
+        int4 tp = T.topo[k];
+        if (tp.z >= 0) continue;  // internal nodes are finished by their last child
+        leaf_moments<Q64>(T, k, tp, theta);
+        int p = T.parent[k];
+        int hops = 0;
+        while (p >= 0) {
+            if (++hops > kLevels + 1 || p >= nn) {  // a valid chain has at most 21 parents
+                latch_error(T.meta, P3T_ERR_INTERNAL);
+                break;
+            }
+            __threadfence();
+            int4 pt = T.topo[p];
+            int old = atomicAdd(&T.ready[p], 1);
+            if (old != pt.w - 1) break;
+            __threadfence();
+            internal_moments<Q64>(T, p, pt, theta);
+            p = T.parent[p];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+int build_tree(p3t_ctx *c, int n, const double *x, const double *y, const double *z,
+               const double *m)
+{
+    cudaStream_t s = c->stream;
+    Tree &T = c->tree;
+    Meta *M = c->meta;
+    const p3t_params &P = c->prm;
+    T.n = n;
+    const int grid_n = (n + kBuildThreads - 1) / kBuildThreads;
+    const int persistent = 4 * c->sm_count;
+
+    init_meta_kernel<<<1, 64, 0, s>>>(M);
+    bbox_kernel<<<persistent, kBuildThreads, 0, s>>>(n, x, y, z, m, M);
+    cube_kernel<<<1, 1, 0, s>>>(M);
+    keys_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, M, c->keys_buf[0], c->perm_buf[0]);
+    if (check_launch(c)) return P3T_ERR_CUDA;
+
+    // 8 passes of 8 bits: the result lands back in buffer 0
+    const int nb = (n + kSortTile - 1) / kSortTile;
+    for (int pass = 0; pass < 8; pass++) {
+        const int shift = 8 * pass;
+        uint64_t *kin = c->keys_buf[pass & 1], *kout = c->keys_buf[(pass + 1) & 1];
+        int32_t *vin = c->perm_buf[pass & 1], *vout = c->perm_buf[(pass + 1) & 1];
+        sort_hist_kernel<<<nb, kBuildThreads, 0, s>>>(n, kin, shift, nb, c->sort_hist);
+        if (check_launch(c)) return P3T_ERR_CUDA;
+        int e = scan_excl_i32_to_i32(c->sort_hist, c->sort_hist, 256 * nb, c->scan_status,
+                                     &M->tickets[31], M, s);
+        if (e) return e;
+        sort_scatter_kernel<<<nb, kBuildThreads, 0, s>>>(n, kin, vin, kout, vout, shift, nb,
+                                                         c->sort_hist);
+        if (check_launch(c)) return P3T_ERR_CUDA;
+    }
+    T.keys = c->keys_buf[0];
+    T.perm = c->perm_buf[0];
+    gather_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, m, T.perm, T.sp);
+
+    // topology, level by level
+    unsigned long long *topo_status = c->scan_status + (n / 256 + 64 + 256 * nb / 256);
+    const int stride = topo_status_stride(n);
+    if (cudaMemsetAsync(topo_status, 0, sizeof(unsigned long long) * stride * kMaxLevelSlots, s) !=
+            cudaSuccess ||
+        cudaMemsetAsync(T.gflag, 0, n, s) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    topo_root_kernel<<<1, 1, 0, s>>>(T, n, P.leaf_cap, P.group_size);
+    const int topo_grid = 2 * c->sm_count;
+    for (int l = 0; l < kLevels; l++)
+        topo_level_kernel<<<topo_grid, kBuildThreads, 0, s>>>(
+            T, l, P.leaf_cap, P.group_size, topo_status + (size_t)l * stride, &M->tickets[l]);
+    topo_finish_kernel<<<1, 1, 0, s>>>(M, T.cap_nodes);
+    if (check_launch(c)) return P3T_ERR_CUDA;
+
+    // groups
+    int e = scan_excl_u8_to_i32(T.gflag, T.gidx, n, &M->n_groups, c->scan_status, &M->tickets[30],
+                                M, s);
+    if (e) return e;
+    group_first_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, T.gflag, T.gidx, T.grp);
+    group_finish_kernel<<<persistent, kBuildThreads, 0, s>>>(T, n);
+
+    // moments
+    if (P.precision == P3T_FP64)
+        moments_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
+    else
+        moments_kernel<false><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
+    return check_launch(c);
+}
+
+// ---------------------------------------------------------------------------
+// export (inspection)
+__global__ void export_nodes_kernel(Tree T, bool q64, int32_t *level, int32_t *first,
+                                    int32_t *count, int32_t *child, int32_t *nchild, double *M,
+                                    double *com, double *Q, double *lo, double *hi, double *ropen2)
+{
+    const int nn = T.meta->n_nodes;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
+        int4 tp = T.topo[k];
+        if (level) level[k] = T.level[k];
+        if (first) first[k] = tp.x;
+        if (count) count[k] = tp.y;
+        if (child) child[k] = tp.z;
+        if (nchild) nchild[k] = tp.w;
+        double4_32a cm = T.comM[k], l = T.lo[k], h = T.hi[k];
+        if (M) M[k] = cm.w;
+        if (com) com[3 * k] = cm.x, com[3 * k + 1] = cm.y, com[3 * k + 2] = cm.z;
+        if (lo) lo[3 * k] = l.x, lo[3 * k + 1] = l.y, lo[3 * k + 2] = l.z;
+        if (hi) hi[3 * k] = h.x, hi[3 * k + 1] = h.y, hi[3 * k + 2] = h.z;
+        if (ropen2) ropen2[k] = l.w;
+        if (Q)
+            for (int a = 0; a < 6; a++)
+                Q[6 * k + a] = q64 ? T.q64[6 * (size_t)k + a] : (double)T.q32[6 * (size_t)k + a];
+    }
+}
+
+__global__ void export_groups_kernel(Tree T, int32_t *g_first, int32_t *g_count)
+{
+    const int ng = T.meta->n_groups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        if (g_first) g_first[g] = T.grp[g].x;
+        if (g_count) g_count[g] = T.grp[g].y;
+    }
+}
+
+int export_tree(p3t_ctx *c, uint64_t *keys, int32_t *perm, int32_t *level, int32_t *first,
+                int32_t *count, int32_t *child, int32_t *nchild, double *M, double *com,
+                double *Q, double *lo, double *hi, double *ropen2, int32_t *g_first,
+                int32_t *g_count)
+{
+    cudaStream_t s = c->stream;
+    const Tree &T = c->tree;
+    if (keys && cudaMemcpyAsync(keys, T.keys, 8 * (size_t)c->n, cudaMemcpyDeviceToDevice, s))
+        return P3T_ERR_CUDA;
+    if (perm && cudaMemcpyAsync(perm, T.perm, 4 * (size_t)c->n, cudaMemcpyDeviceToDevice, s))
+        return P3T_ERR_CUDA;
+    export_nodes_kernel<<<4 * c->sm_count, kBuildThreads, 0, s>>>(
+        T, c->built_precision == P3T_FP64, level, first, count, child, nchild, M, com, Q, lo, hi,
+        ropen2);
+    export_groups_kernel<<<4 * c->sm_count, kBuildThreads, 0, s>>>(T, g_first, g_count);
+    return check_launch(c);
+}
+
+}  // namespace p3t

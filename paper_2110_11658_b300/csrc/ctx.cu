@@ -1,0 +1,340 @@
+// Context management and the exported C ABI of the P3T distant-force library.
+// Each entry point validates its arguments, enqueues kernels on the context's
+// stream (build_tree.cu, walk.cu, neighbours.cu, kick.cu) and maps CUDA
+// failures to P3T_ERR_CUDA.  Nothing here throws.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "p3t_internal.cuh"
+
+namespace p3t {
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+long long node_capacity(long long n, int leaf_cap)
+{
+    // leaves are disjoint and non-empty (<= n); internal nodes hold more than
+    // leaf_cap particles and are disjoint within a level (<= n/(leaf_cap+1) per
+    // level, levels 0..20)
+    return n + (long long)kLevels * (n / (leaf_cap + 1)) + 1;
+}
+
+int topo_status_stride(long long n) { return (int)(n / 256 + 4); }
+
+int ensure_capacity(p3t_ctx *c, long long n)
+{
+    const int L = c->prm.leaf_cap;
+    long long need_nodes = node_capacity(n, L);
+    if (c->blob && n <= c->cap_n && need_nodes <= c->cap_nodes) return P3T_OK;
+    if (c->blob) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->blob);
+        c->blob = nullptr;
+    }
+    long long N = n;
+    long long NN = need_nodes;
+    long long sort_blocks = (N + 4095) / 4096;
+    long long scan_words = N / 256 + 64 + 256 * sort_blocks / 256;
+    long long topo_words = (long long)kMaxLevelSlots * topo_status_stride(N);
+    struct Item {
+        void **ptr;
+        size_t bytes;
+    };
+    Tree &T = c->tree;
+    Item items[] = {
+        {(void **)&c->meta, sizeof(Meta)},
+        {(void **)&c->keys_buf[0], 8 * (size_t)N},
+        {(void **)&c->keys_buf[1], 8 * (size_t)N},
+        {(void **)&c->perm_buf[0], 4 * (size_t)N},
+        {(void **)&c->perm_buf[1], 4 * (size_t)N},
+        {(void **)&T.sp, 32 * (size_t)N},
+        {(void **)&T.gflag, (size_t)N + 16},
+        {(void **)&T.gidx, 4 * (size_t)N},
+        {(void **)&T.grp, 8 * (size_t)N},
+        {(void **)&T.glo, 32 * (size_t)N},
+        {(void **)&T.ghi, 32 * (size_t)N},
+        {(void **)&c->nbr_count, 4 * (size_t)N},
+        {(void **)&c->grp_cells, 8 * (size_t)N},
+        {(void **)&c->grp_parts, 8 * (size_t)N},
+        {(void **)&c->sort_hist, 4 * 256 * (size_t)sort_blocks},
+        {(void **)&c->scan_status, 8 * (size_t)(scan_words + topo_words)},
+        {(void **)&T.topo, 16 * (size_t)NN},
+        {(void **)&T.level, 4 * (size_t)NN},
+        {(void **)&T.parent, 4 * (size_t)NN},
+        {(void **)&T.ready, 4 * (size_t)NN},
+        {(void **)&T.comM, 32 * (size_t)NN},
+        {(void **)&T.lo, 32 * (size_t)NN},
+        {(void **)&T.hi, 32 * (size_t)NN},
+        {(void **)&T.q32, 24 * (size_t)NN},
+        {(void **)&T.q64, 48 * (size_t)NN},
+        {(void **)&T.wA, 16 * (size_t)NN},
+        {(void **)&T.wB, 16 * (size_t)NN},
+        {(void **)&T.wC, 16 * (size_t)NN},
+    };
+    size_t total = 0;
+    for (auto &it : items) total += align_up(it.bytes, 256);
+    void *blob = nullptr;
+    if (cudaMalloc(&blob, total) != cudaSuccess) {
+        cudaGetLastError();
+        c->cap_n = 0;
+        c->cap_nodes = 0;
+        return P3T_ERR_OOM;
+    }
+    char *p = (char *)blob;
+    for (auto &it : items) {
+        *it.ptr = p;
+        p += align_up(it.bytes, 256);
+    }
+    c->blob = blob;
+    c->blob_bytes = total;
+    c->cap_n = N;
+    c->cap_nodes = NN;
+    c->cap_leaf = L;
+    T.meta = c->meta;
+    T.cap_nodes = (int)NN;
+    if (cudaMemsetAsync(c->meta, 0, sizeof(Meta), c->stream) != cudaSuccess) return P3T_ERR_CUDA;
+    return P3T_OK;
+}
+
+int check_launch(p3t_ctx *c)
+{
+    (void)c;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "p3t: CUDA error %s\n", cudaGetErrorString(e));
+        return P3T_ERR_CUDA;
+    }
+    return P3T_OK;
+}
+
+static int validate_params(const p3t_params *p)
+{
+    if (!p) return P3T_ERR_INVALID_ARG;
+    if (!(p->theta >= 0.0) || !std::isfinite(p->theta)) return P3T_ERR_INVALID_ARG;
+    if (!(p->r_in >= 0.0) || !(p->r_out > p->r_in) || !std::isfinite(p->r_out))
+        return P3T_ERR_INVALID_ARG;
+    if (!(p->r_list >= 0.0) || !std::isfinite(p->r_list)) return P3T_ERR_INVALID_ARG;
+    if (p->leaf_cap < 1 || p->leaf_cap > (1 << 20)) return P3T_ERR_INVALID_ARG;
+    if (p->group_size < 1 || p->group_size > 128) return P3T_ERR_INVALID_ARG;
+    if (p->tile < 32 || p->tile > 256 || p->tile % 32) return P3T_ERR_INVALID_ARG;
+    if (p->threads_per_group != 32) return P3T_ERR_INVALID_ARG;
+    if (p->precision != P3T_FP32_MIXED && p->precision != P3T_FP64) return P3T_ERR_INVALID_ARG;
+    if (p->quadrupole != 0 && p->quadrupole != 1) return P3T_ERR_INVALID_ARG;
+    return P3T_OK;
+}
+
+}  // namespace p3t
+
+using namespace p3t;
+
+extern "C" {
+
+int p3t_default_params(p3t_params *p)
+{
+    if (!p) return P3T_ERR_INVALID_ARG;
+    p->theta = 0.5;
+    p->r_in = 0.005;
+    p->r_out = 0.05;
+    p->r_list = 0.05;
+    p->leaf_cap = 16;
+    p->group_size = 64;
+    p->tile = 64;
+    p->threads_per_group = 32;
+    p->precision = P3T_FP32_MIXED;
+    p->quadrupole = 1;
+    return P3T_OK;
+}
+
+int p3t_create(p3t_ctx **out, const p3t_params *p, void *cuda_stream)
+{
+    if (!out) return P3T_ERR_INVALID_ARG;
+    *out = nullptr;
+    int e = validate_params(p);
+    if (e) return e;
+    p3t_ctx *c = new (std::nothrow) p3t_ctx();
+    if (!c) return P3T_ERR_OOM;
+    memset((void *)c, 0, sizeof(*c));
+    c->prm = *p;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return P3T_ERR_CUDA;
+    }
+    *out = c;
+    return P3T_OK;
+}
+
+int p3t_destroy(p3t_ctx *c)
+{
+    if (!c) return P3T_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c->stream);
+    if (c->blob) cudaFree(c->blob);
+    if (c->host_stage) cudaFree(c->host_stage);
+    delete c;
+    return P3T_OK;
+}
+
+int p3t_set_params(p3t_ctx *c, const p3t_params *p)
+{
+    if (!c) return P3T_ERR_INVALID_ARG;
+    int e = validate_params(p);
+    if (e) return e;
+    c->prm = *p;
+    c->built = 0;
+    return P3T_OK;
+}
+
+int p3t_build_tree(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                   const double *m)
+{
+    if (!c || !x || !y || !z || !m) return P3T_ERR_INVALID_ARG;
+    if (n <= 0 || n >= (1LL << 31) - 1) return P3T_ERR_INVALID_ARG;
+    if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 29)) return P3T_ERR_INVALID_ARG;
+    int e = ensure_capacity(c, n);
+    if (e) return e;
+    c->built = 0;
+    e = build_tree(c, (int)n, x, y, z, m);
+    if (e) return e;
+    c->n = (int)n;
+    c->built = 1;
+    c->built_precision = c->prm.precision;
+    return P3T_OK;
+}
+
+int p3t_far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *n_cell_inter,
+                  int64_t *n_part_inter)
+{
+    if (!c || !ax || !ay || !az) return P3T_ERR_INVALID_ARG;
+    if (!c->built) return P3T_ERR_ORDER;
+    return far_force(c, ax, ay, az, pot, n_cell_inter, n_part_inter);
+}
+
+int p3t_neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *total)
+{
+    if (!c || !offsets || !total || capacity < 0 || (capacity > 0 && !idx))
+        return P3T_ERR_INVALID_ARG;
+    if (!c->built) return P3T_ERR_ORDER;
+    return neighbours(c, offsets, idx, capacity, nullptr, true, total);
+}
+
+int p3t_neighbours_async(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t capacity,
+                         int64_t *total_dev)
+{
+    if (!c || !offsets || !total_dev || capacity < 0 || (capacity > 0 && !idx))
+        return P3T_ERR_INVALID_ARG;
+    if (!c->built) return P3T_ERR_ORDER;
+    return neighbours(c, offsets, idx, capacity, total_dev, false, nullptr);
+}
+
+int p3t_kick(p3t_ctx *c, double dt, const void *ax, const void *ay, const void *az, double *vx,
+             double *vy, double *vz)
+{
+    if (!c || !ax || !ay || !az || !vx || !vy || !vz || !std::isfinite(dt))
+        return P3T_ERR_INVALID_ARG;
+    if (!c->built) return P3T_ERR_ORDER;
+    return kick(c, dt, ax, ay, az, vx, vy, vz);
+}
+
+int p3t_drift(p3t_ctx *c, int64_t n, double dt, double *x, double *y, double *z, const double *vx,
+              const double *vy, const double *vz)
+{
+    if (!c || !x || !y || !z || !vx || !vy || !vz || n <= 0 || n >= (1LL << 31) ||
+        !std::isfinite(dt))
+        return P3T_ERR_INVALID_ARG;
+    return drift(c, (int)n, dt, x, y, z, vx, vy, vz);
+}
+
+int p3t_status(p3t_ctx *c)
+{
+    if (!c) return P3T_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return P3T_ERR_CUDA;
+    }
+    if (c->pending_err) {
+        int e = c->pending_err;
+        c->pending_err = 0;
+        return e;
+    }
+    if (!c->meta) return P3T_OK;
+    int err = 0;
+    if (cudaMemcpy(&err, &c->meta->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    if (err) {
+        int zero = 0;
+        cudaMemcpy(&c->meta->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    }
+    return err;
+}
+
+int p3t_tree_info(p3t_ctx *c, int64_t *n, int64_t *n_nodes, int64_t *n_groups, int32_t *depth)
+{
+    if (!c) return P3T_ERR_INVALID_ARG;
+    if (!c->built) return P3T_ERR_ORDER;
+    int e = p3t_status(c);
+    if (e) return e;
+    Meta h;
+    if (cudaMemcpy(&h, c->meta, sizeof(Meta), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    if (n) *n = c->n;
+    if (n_nodes) *n_nodes = h.n_nodes;
+    if (n_groups) *n_groups = h.n_groups;
+    if (depth) *depth = h.depth;
+    return P3T_OK;
+}
+
+int p3t_export_tree(p3t_ctx *c, uint64_t *keys, int32_t *perm, int32_t *level, int32_t *first,
+                    int32_t *count, int32_t *child, int32_t *nchild, double *M, double *com,
+                    double *Q, double *lo, double *hi, double *ropen2, int32_t *g_first,
+                    int32_t *g_count)
+{
+    if (!c) return P3T_ERR_INVALID_ARG;
+    if (!c->built) return P3T_ERR_ORDER;
+    return export_tree(c, keys, perm, level, first, count, child, nchild, M, com, Q, lo, hi,
+                       ropen2, g_first, g_count);
+}
+
+int p3t_group_counts(p3t_ctx *c, int64_t *n_cell, int64_t *n_part)
+{
+    if (!c || !n_cell || !n_part) return P3T_ERR_INVALID_ARG;
+    if (!c->built) return P3T_ERR_ORDER;
+    int64_t ng = 0;
+    int e = p3t_tree_info(c, nullptr, nullptr, &ng, nullptr);
+    if (e) return e;
+    if (cudaMemcpyAsync(n_cell, c->grp_cells, 8 * ng, cudaMemcpyDeviceToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(n_part, c->grp_parts, 8 * ng, cudaMemcpyDeviceToDevice, c->stream) !=
+            cudaSuccess)
+        return P3T_ERR_CUDA;
+    return P3T_OK;
+}
+
+int p3t_set_debug(p3t_ctx *c, int on)
+{
+    if (!c) return P3T_ERR_INVALID_ARG;
+    c->debug = on ? 1 : 0;
+    return P3T_OK;
+}
+
+const char *p3t_error_string(int code)
+{
+    switch (code) {
+    case P3T_OK: return "ok";
+    case P3T_ERR_INVALID_ARG: return "invalid argument";
+    case P3T_ERR_INVALID_INPUT: return "invalid input (non-finite position or mass, or negative mass)";
+    case P3T_ERR_OOM: return "device allocation failed";
+    case P3T_ERR_CAPACITY: return "output capacity too small";
+    case P3T_ERR_ORDER: return "no tree built: call p3t_build_tree first";
+    case P3T_ERR_TIMEOUT: return "a bounded device-side wait ran out";
+    case P3T_ERR_CUDA: return "CUDA runtime error";
+    case P3T_ERR_INTERNAL: return "device-side consistency check failed";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,403 @@
+// Neighbour lists of the constant neighbour radius (Sec. 2.3), handed to the
+// irregular (Hermite) side: row i lists every j != i with |x_i - x_j| < r_list,
+// by ascending original index; empty rows are legal.
+//
+// Three passes over the tree, one warp per walk group:
+//   count  walk opening every cell whose box lies within r_list of the group
+//          box, test each target against the particles of the opened leaves
+//   scan   counts -> int64 row offsets (look-back scan)
+//   fill   the same walk, writing original indices; then each row is sorted.
+// The pair test is defined in FP64 as r2 = (dx*dx + dy*dy) + dz*dz < r_list^2.
+// It is first taken in FP32 on coordinates relative to the group centre
+// (formed in FP64); a pair inside the FP32 error band is re-tested with the
+// exact FP64 operations, so the lists equal the FP64 definition bit for bit.
+#include <climits>
+#include <cstdint>
+
+#include "p3t_internal.cuh"
+
+namespace p3t {
+
+constexpr int kNbrWarps = 4;
+constexpr int kNbrStack = 32 * 22 + 64;
+constexpr int kNbrLeafQ = 96;  // flush threshold 64 + up to 32 leaves from one step
+constexpr float kUn = 5.9604644775390625e-8f;
+
+struct NbrArgs {
+    Tree T;
+    double rl2_d;
+    float rl_f, rl2_f;
+    int32_t *count;        // per particle, original order
+    const int64_t *offs;   // row offsets (fill pass)
+    int32_t *idx;          // entries (fill pass)
+    long long capacity;
+    unsigned int *ticket;
+};
+
+struct NbrSmem {
+    int stk[kNbrStack];
+    int batch[32];
+    int2 lq[kNbrLeafQ];
+    int lqo[kNbrLeafQ + 1];
+    float4 pp[32];
+    int pj[32];
+};
+
+template <int TPL, bool FILL>
+__global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
+{
+    __shared__ NbrSmem sm[kNbrWarps];
+    NbrSmem &W = sm[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const Tree &T = P.T;
+    Meta *meta = T.meta;
+    const int ng = meta->n_groups;
+    const int nn = meta->n_nodes;
+    const double Ox = meta->frame[0], Oy = meta->frame[1], Oz = meta->frame[2];
+    const float Rf = (float)meta->frame[3] * 1.0001f;
+    const bool filter_ok = Rf > 1e-12f && Rf < 1e12f && P.rl2_f > 1e-30f && P.rl2_f < 1e30f;
+    const float k_rel = 8.f * kUn, k_abs = 8.f * kUn * Rf, k_sq = 16.f * kUn * kUn * Rf * Rf;
+    bool allowed = true;
+    if (FILL) allowed = P.offs[T.n] <= P.capacity;
+    if (FILL && !allowed) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) latch_error(meta, P3T_ERR_CAPACITY);
+        return;
+    }
+
+    while (true) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(P.ticket, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ng) break;
+        const int2 gr = T.grp[g];
+        const double4_32a glo = T.glo[g], ghi = T.ghi[g];
+        const double cgx = dmul(0.5, dadd(glo.x, ghi.x));
+        const double cgy = dmul(0.5, dadd(glo.y, ghi.y));
+        const double cgz = dmul(0.5, dadd(glo.z, ghi.z));
+        const float glx = __double2float_rn(dsub(glo.x, Ox)), gly = __double2float_rn(dsub(glo.y, Oy)),
+                    glz = __double2float_rn(dsub(glo.z, Oz));
+        const float ghx = __double2float_rn(dsub(ghi.x, Ox)), ghy = __double2float_rn(dsub(ghi.y, Oy)),
+                    ghz = __double2float_rn(dsub(ghi.z, Oz));
+        float px[TPL], py[TPL], pz[TPL];
+        int si[TPL], cnt[TPL];
+        long long base[TPL];
+        float A = 0.f;
+#pragma unroll
+        for (int t = 0; t < TPL; t++) {
+            int s = gr.x + lane + 32 * t;
+            cnt[t] = 0;
+            base[t] = 0;
+            if (s < gr.x + gr.y) {
+                double4_32a q = T.sp[s];
+                px[t] = __double2float_rn(dsub(q.x, cgx));
+                py[t] = __double2float_rn(dsub(q.y, cgy));
+                pz[t] = __double2float_rn(dsub(q.z, cgz));
+                si[t] = s;
+                A = fmaxf(A, fmaxf(fabsf(px[t]), fmaxf(fabsf(py[t]), fabsf(pz[t]))));
+                if (FILL) base[t] = P.offs[T.perm[s]];
+            } else {
+                px[t] = py[t] = pz[t] = 0.f;
+                si[t] = -1;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) A = fmaxf(A, __shfl_xor_sync(0xffffffffu, A, o));
+        A *= 1.0001f;
+        // band of the pair test (FP32 vs FP64 squared distance), factor ~2 spare
+        const float tpair = kUn * (20.f * P.rl2_f + 16.f * A * P.rl_f) +
+                            32.f * kUn * kUn * (A + 2.f * P.rl_f) * (A + 2.f * P.rl_f);
+        const bool pair_filter = filter_ok && A < 1e12f;
+
+        int sp = 1;
+        if (lane == 0) W.stk[0] = (0 << 3) | 0;
+        __syncwarp();
+        int lqn = 0, lqp = 0;
+        int iters = 0;  // a valid walk pops every node at most once
+        while (true) {
+            if (++iters > nn + 2) {
+                if (lane == 0) latch_error(meta, P3T_ERR_INTERNAL);
+                break;
+            }
+            if (sp > 0) {
+                int e = lane < sp ? W.stk[sp - 1 - lane] : 0;
+                int c = lane < sp ? (e & 7) + 1 : 0;
+                int incl = warp_incl_scan(c);
+                int excl = incl - c;
+                int total = __shfl_sync(0xffffffffu, incl, 31);
+                int take = total < 32 ? total : 32;
+                unsigned full = __ballot_sync(0xffffffffu, lane < sp && incl <= take);
+                __syncwarp();
+                if (lane < sp && excl < take) {
+                    int first = e >> 3;
+                    int mine = c < take - excl ? c : take - excl;
+                    for (int j = 0; j < mine; j++) W.batch[excl + j] = first + j;
+                    if (mine < c) W.stk[sp - 1 - lane] = ((first + mine) << 3) | (c - mine - 1);
+                }
+                __syncwarp();
+                sp -= __popc(full);
+                const int node = lane < take ? W.batch[lane] : -1;
+                __syncwarp();
+                bool open = false, is_leaf = false;
+                int cinfo = 0, ccount = 0;
+                if (node >= 0) {
+                    const float4 b = T.wB[node], cc = T.wC[node];
+                    cinfo = __float_as_int(b.w);
+                    ccount = __float_as_int(cc.w);
+                    is_leaf = cinfo < 0;
+                    int bb = 2;
+                    if (filter_ok) {
+                        float ux = fmaxf(fmaxf(b.x - ghx, glx - cc.x), 0.f);
+                        float uy = fmaxf(fmaxf(b.y - ghy, gly - cc.y), 0.f);
+                        float uz = fmaxf(fmaxf(b.z - ghz, glz - cc.z), 0.f);
+                        float e2 = ux * ux + uy * uy + uz * uz;
+                        float tol = k_rel * (e2 + P.rl2_f) + k_abs * (ux + uy + uz) + k_sq;
+                        bb = e2 < P.rl2_f - tol ? 1 : (e2 > P.rl2_f + tol ? 0 : 2);
+                    }
+                    if (bb == 2) {
+                        bb = dist2_box_box(glo, ghi, T.lo[node], T.hi[node]) < P.rl2_d;
+                        if (filter_ok) atomicAdd((unsigned long long *)&meta->fallback_tests, 1ULL);
+                    }
+                    open = bb == 1;
+                }
+                const bool open_int = open && !is_leaf;
+                const bool open_leaf = open && is_leaf;
+                const bool bad = (open_int && (ccount < 1 || ccount > 8 || cinfo + ccount > nn)) ||
+                                 (open_leaf && (ccount < 1 || -1 - cinfo + ccount > T.n));
+                if (__any_sync(0xffffffffu, bad)) {
+                    if (lane == 0) latch_error(meta, P3T_ERR_INTERNAL);
+                    break;
+                }
+                const unsigned pm = __ballot_sync(0xffffffffu, open_int);
+                const int npush = __popc(pm);
+                if (sp + npush > kNbrStack) {
+                    if (lane == 0) latch_error(meta, P3T_ERR_CAPACITY);
+                    sp = 0;
+                    break;
+                }
+                if (open_int) W.stk[sp + __popc(pm >> lane >> 1)] = (cinfo << 3) | (ccount - 1);
+                sp += npush;
+                const unsigned lm = __ballot_sync(0xffffffffu, open_leaf);
+                int lc = open_leaf ? ccount : 0;
+                if (open_leaf) W.lq[lqn + __popc(lm & lt)] = make_int2(-1 - cinfo, ccount);
+                lqn += __popc(lm);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) lc += __shfl_xor_sync(0xffffffffu, lc, o);
+                lqp += lc;
+                if (lqp < 64 && sp > 0) continue;
+            }
+            if (lqp == 0) break;
+            // ---- test the targets against the queued leaves' particles
+            __syncwarp();
+            {
+                int carry = 0;
+                for (int b0 = 0; b0 < lqn; b0 += 32) {
+                    int i = b0 + lane;
+                    int v = i < lqn ? W.lq[i].y : 0;
+                    int inc = warp_incl_scan(v);
+                    if (i < lqn) W.lqo[i] = carry + inc - v;
+                    carry += __shfl_sync(0xffffffffu, inc, 31);
+                }
+            }
+            __syncwarp();
+            for (int c0 = 0; c0 < lqp; c0 += 32) {
+                int pos = c0 + lane;
+                if (pos < lqp) {
+                    int lo = 0, hi = lqn;
+                    while (hi - lo > 1) {
+                        int mid = (lo + hi) >> 1;
+                        if (W.lqo[mid] <= pos)
+                            lo = mid;
+                        else
+                            hi = mid;
+                    }
+                    int j = W.lq[lo].x + (pos - W.lqo[lo]);
+                    double4_32a q = T.sp[j];
+                    W.pp[lane] = make_float4(__double2float_rn(dsub(q.x, cgx)),
+                                             __double2float_rn(dsub(q.y, cgy)),
+                                             __double2float_rn(dsub(q.z, cgz)), 0.f);
+                    W.pj[lane] = j;
+                }
+                __syncwarp();
+                const int ns = min(32, lqp - c0);
+                for (int k = 0; k < ns; k++) {
+                    const float4 s = W.pp[k];
+                    const int j = W.pj[k];
+#pragma unroll
+                    for (int t = 0; t < TPL; t++) {
+                        if (si[t] < 0 || si[t] == j) continue;
+                        float dx = s.x - px[t], dy = s.y - py[t], dz = s.z - pz[t];
+                        float r2 = dx * dx + dy * dy + dz * dz;
+                        int in = 2;
+                        if (pair_filter) in = r2 < P.rl2_f - tpair ? 1 : (r2 > P.rl2_f + tpair ? 0 : 2);
+                        if (in == 2) {
+                            const double4_32a a = T.sp[si[t]], b = T.sp[j];
+                            double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
+                            double d2 = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez));
+                            in = d2 < P.rl2_d;
+                        }
+                        if (in) {
+                            if (FILL) P.idx[base[t] + cnt[t]] = T.perm[j];
+                            cnt[t]++;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            lqn = lqp = 0;
+            if (sp == 0) break;
+        }
+        if (!FILL) {
+#pragma unroll
+            for (int t = 0; t < TPL; t++)
+                if (si[t] >= 0) P.count[T.perm[si[t]]] = cnt[t];
+        }
+        __syncwarp();
+    }
+}
+
+// ---- per-row ascending sort --------------------------------------------------
+constexpr int kSortWarps = 4;
+constexpr int kRowBuf = 1024;
+
+__device__ void heap_sort_global(int32_t *a, long long n)
+{
+    // single-thread fallback for rows longer than the shared buffer
+    auto sift = [&](long long start, long long end) {
+        long long root = start;
+        while (2 * root + 1 < end) {
+            long long child = 2 * root + 1;
+            if (child + 1 < end && a[child] < a[child + 1]) child++;
+            if (a[root] < a[child]) {
+                int32_t t = a[root];
+                a[root] = a[child];
+                a[child] = t;
+                root = child;
+            } else {
+                return;
+            }
+        }
+    };
+    for (long long s = n / 2 - 1; s >= 0; s--) sift(s, n);
+    for (long long e = n - 1; e > 0; e--) {
+        int32_t t = a[0];
+        a[0] = a[e];
+        a[e] = t;
+        sift(0, e);
+    }
+}
+
+__global__ void __launch_bounds__(kSortWarps * 32)
+    row_sort_kernel(int n, const int64_t *__restrict__ offs, int32_t *idx, long long capacity)
+{
+    __shared__ int32_t buf[kSortWarps][kRowBuf];
+    int32_t *b = buf[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    if (offs[n] > capacity) return;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
+         i += (gridDim.x * blockDim.x) >> 5) {
+        const long long o = offs[i];
+        const int len = (int)(offs[i + 1] - o);
+        if (len <= 1) continue;
+        if (len > kRowBuf) {
+            if (lane == 0) heap_sort_global(idx + o, len);
+            __syncwarp();
+            continue;
+        }
+        int P2 = 32;
+        while (P2 < len) P2 <<= 1;
+        for (int k = lane; k < P2; k += 32) b[k] = k < len ? idx[o + k] : INT_MAX;
+        __syncwarp();
+        for (int k = 2; k <= P2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = lane; t < P2; t += 32) {
+                    int u = t ^ j;
+                    if (u > t) {
+                        bool up = (t & k) == 0;
+                        int32_t x = b[t], y = b[u];
+                        if ((x > y) == up) {
+                            b[t] = y;
+                            b[u] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int k = lane; k < len; k += 32) idx[o + k] = b[k];
+        __syncwarp();
+    }
+}
+
+template <int TPL, bool FILL>
+static int launch_nbr(p3t_ctx *c, const NbrArgs &a)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nbr_kernel<TPL, FILL>,
+                                                      kNbrWarps * 32, 0) != cudaSuccess ||
+        per_sm < 1)
+        return P3T_ERR_CUDA;
+    if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    nbr_kernel<TPL, FILL><<<per_sm * c->sm_count, kNbrWarps * 32, 0, c->stream>>>(a);
+    return check_launch(c);
+}
+
+template <bool FILL>
+static int dispatch_nbr(p3t_ctx *c, const NbrArgs &a)
+{
+    const int G = c->prm.group_size;
+    if (G <= 32) return launch_nbr<1, FILL>(c, a);
+    if (G <= 64) return launch_nbr<2, FILL>(c, a);
+    return launch_nbr<4, FILL>(c, a);
+}
+
+int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, int64_t *total_dev,
+               bool sync, int64_t *total_host)
+{
+    cudaStream_t s = c->stream;
+    const int n = c->n;
+    NbrArgs a;
+    a.T = c->tree;
+    a.rl2_d = c->prm.r_list * c->prm.r_list;
+    a.rl_f = (float)c->prm.r_list;
+    a.rl2_f = (float)a.rl2_d;
+    a.count = c->nbr_count;
+    a.offs = offsets;
+    a.idx = idx;
+    a.capacity = capacity;
+    a.ticket = &c->meta->tickets[23];
+    int e = dispatch_nbr<false>(c, a);
+    if (e) return e;
+    e = scan_excl_i32_to_i64(c->nbr_count, offsets, n, offsets + n, c->scan_status,
+                             &c->meta->tickets[29], c->meta, s);
+    if (e) return e;
+    if (sync) {
+        int64_t tot = 0;
+        if (cudaMemcpyAsync(&tot, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return P3T_ERR_CUDA;
+        *total_host = tot;
+        int err = 0;
+        if (cudaMemcpy(&err, &c->meta->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return P3T_ERR_CUDA;
+        if (err) {
+            int zero = 0;
+            cudaMemcpy(&c->meta->err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+            return err;
+        }
+        if (tot > capacity) return P3T_ERR_CAPACITY;
+    } else {
+        if (cudaMemcpyAsync(total_dev, offsets + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+            return P3T_ERR_CUDA;
+    }
+    if (capacity == 0) return P3T_OK;
+    e = dispatch_nbr<true>(c, a);
+    if (e) return e;
+    row_sort_kernel<<<8 * c->sm_count, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
+    return check_launch(c);
+}
+
+}  // namespace p3t

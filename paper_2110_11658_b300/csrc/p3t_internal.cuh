@@ -1,0 +1,272 @@
+// Internal declarations of the P3T distant-force library (sm_103a).
+//
+// Device layout of one built tree (all in the context's scratch, see ctx.cu):
+//   particles, Morton order:  keys u64[n], perm i32[n] (sorted -> original),
+//                             sp double4_32a[n] = {x, y, z, m}
+//   nodes, breadth-first:     topo int4 = {first, count, child (-1 = leaf), nchild},
+//                             level i32, parent i32,
+//                             comM double4_32a = {com.xyz, M}, lo double4_32a = {lo.xyz, r_open^2},
+//                             hi double4_32a = {hi.xyz, 0}, Q (FP64: double[6] | FP32: float[6]),
+//                             walk filter float4 wA = {com-O, r_open^2}, wB = {lo-O, child/leaf},
+//                             wC = {hi-O, nchild/count}  (O = centre of the bounding cube)
+//   groups, particle order:   grp int2 = {first, count}, glo/ghi double4_32a (tight box)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/p3t.h"
+
+namespace p3t {
+
+constexpr int kLevels = 21;          // key bits per axis = tree depth
+constexpr int kMaxLevelSlots = 24;   // per-level bookkeeping arrays
+constexpr long long kSpinLimit = 1LL << 24;  // bounded waits: ~1 s with backoff
+
+// ---- device metadata block (one per context) -------------------------------
+struct Meta {
+    int err;                       // first latched error code (0 = none)
+    int n_nodes;
+    int n_groups;
+    int depth;
+    int level_start[kMaxLevelSlots];
+    int level_count[kMaxLevelSlots];
+    unsigned int tickets[32];      // work-distribution counters (reset per launch)
+    double cube[4];                // min.xyz, side (rule 1)
+    double frame[4];               // O.xyz (cube centre), R (bound on |x - O| per axis)
+    unsigned long long minmax[6];  // order-preserving encodings for the bbox reduction
+    long long nbr_total;
+    long long fallback_tests;      // FP64 decisions taken after an undecided FP32 filter
+};
+
+// ---- tree view passed by value to kernels ------------------------------------
+struct Tree {
+    int n;
+    int cap_nodes;
+    uint64_t *keys;
+    int32_t *perm;
+    double4_32a *sp;
+    int4 *topo;
+    int32_t *level;
+    int32_t *parent;
+    int32_t *ready;
+    double4_32a *comM;
+    double4_32a *lo;
+    double4_32a *hi;
+    double *q64;   // 6 per node (FP64 form)
+    float *q32;    // 6 per node (mixed form)
+    float4 *wA, *wB, *wC;
+    int2 *grp;
+    double4_32a *glo, *ghi;
+    unsigned char *gflag;  // group-start flags, particle order
+    int32_t *gidx;         // scan of gflag
+    Meta *meta;
+};
+
+// ---- error latch ---------------------------------------------------------------
+__device__ __forceinline__ void latch_error(Meta *m, int code)
+{
+    atomicCAS(&m->err, 0, code);
+}
+
+// ---- exact FP64 arithmetic (never contracted into FMA) -------------------------
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double dsqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
+__device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
+
+// Squared distance from point p to box [lo, hi]: per axis max(0, lo-p, p-hi),
+// summed as (tx*tx + ty*ty) + tz*tz.  Same operation order as the oracle.
+__device__ __forceinline__ double dist2_point_box(double px, double py, double pz, double4_32a lo,
+                                                  double4_32a hi)
+{
+    double tx = dmax(dmax(dsub(lo.x, px), dsub(px, hi.x)), 0.0);
+    double ty = dmax(dmax(dsub(lo.y, py), dsub(py, hi.y)), 0.0);
+    double tz = dmax(dmax(dsub(lo.z, pz), dsub(pz, hi.z)), 0.0);
+    return dadd(dadd(dmul(tx, tx), dmul(ty, ty)), dmul(tz, tz));
+}
+
+// Squared distance between group box g and cell box c: per axis
+// max(0, clo - ghi, glo - chi).
+__device__ __forceinline__ double dist2_box_box(double4_32a glo, double4_32a ghi, double4_32a clo, double4_32a chi)
+{
+    double tx = dmax(dmax(dsub(clo.x, ghi.x), dsub(glo.x, chi.x)), 0.0);
+    double ty = dmax(dmax(dsub(clo.y, ghi.y), dsub(glo.y, chi.y)), 0.0);
+    double tz = dmax(dmax(dsub(clo.z, ghi.z), dsub(glo.z, chi.z)), 0.0);
+    return dadd(dadd(dmul(tx, tx), dmul(ty, ty)), dmul(tz, tz));
+}
+
+// ---- relaxed device-scope loads/stores for cross-block flags ---------------------
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// ---- block-wide exclusive scan (blockDim.x a multiple of 32, <= 1024) --------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Returns the exclusive prefix of v within the block; *total gets the block sum.
+// `sh` must hold 32 elements of T.  Contains __syncthreads.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *total, T *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T inc = warp_incl_scan(v);
+    if (lane == 31) sh[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        T s = lane < nw ? sh[lane] : T(0);
+        s = warp_incl_scan(s);
+        if (lane < nw) sh[lane] = s;
+    }
+    __syncthreads();
+    T base = wid > 0 ? sh[wid - 1] : T(0);
+    *total = sh[nw - 1];
+    __syncthreads();
+    return base + inc - v;
+}
+
+// ---- decoupled look-back across blocks -----------------------------------------
+// status[t]: bits 62-63 = flag (0 none, 1 aggregate, 2 inclusive prefix), bits
+// 0-61 = value.  Called by ALL threads of the block holding ticket t with the
+// block aggregate; returns the exclusive prefix of the block.  The wait on a
+// predecessor is bounded: after kSpinLimit polls the error is latched and the
+// partial prefix is used, so the kernel always terminates.
+constexpr unsigned long long kFlagAgg = 1ULL << 62, kFlagPre = 2ULL << 62,
+                             kValMask = (1ULL << 62) - 1;
+
+__device__ __forceinline__ long long lookback_prefix(unsigned long long *status, int t,
+                                                      long long aggregate, Meta *meta,
+                                                      long long *sh_out)
+{
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        long long excl = 0;
+        if (t == 0) {
+            if (lane == 0) st_relaxed(&status[0], kFlagPre | (unsigned long long)aggregate);
+        } else {
+            if (lane == 0) st_relaxed(&status[t], kFlagAgg | (unsigned long long)aggregate);
+            int j = t - 1;  // this lane inspects j - lane
+            long long spins = 0;
+            while (true) {
+                int idx = j - lane;
+                unsigned long long s = idx >= 0 ? ld_relaxed(&status[idx]) : kFlagPre;
+                unsigned long long flag = s & ~kValMask;
+                // wait until every inspected predecessor published something
+                if (__any_sync(0xffffffffu, flag == 0)) {
+                    if (++spins > kSpinLimit) {
+                        if (lane == 0) latch_error(meta, P3T_ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(spins < 64 ? 32 : 256);
+                    continue;
+                }
+                unsigned pre = __ballot_sync(0xffffffffu, flag == kFlagPre);
+                long long val = (long long)(s & kValMask);
+                if (idx < 0) val = 0;
+                if (pre) {
+                    int first_pre = __ffs(pre) - 1;  // nearest predecessor with a prefix
+                    long long mine = lane <= first_pre ? val : 0;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+                    excl += mine;
+                    break;
+                }
+                long long mine = val;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+                excl += mine;
+                j -= 32;
+            }
+            if (lane == 0)
+                st_relaxed(&status[t], kFlagPre | (unsigned long long)(excl + aggregate));
+        }
+        if (lane == 0) *sh_out = excl;
+    }
+    __syncthreads();
+    long long r = *sh_out;
+    __syncthreads();
+    return r;
+}
+
+// ---- host helpers ----------------------------------------------------------------
+int scan_excl_u8_to_i32(const unsigned char *in, int32_t *out, int n, int32_t *total_dev,
+                        unsigned long long *status, unsigned int *ticket, Meta *meta,
+                        cudaStream_t s);
+int scan_excl_i32_to_i64(const int32_t *in, int64_t *out, int n, int64_t *total_dev,
+                         unsigned long long *status, unsigned int *ticket, Meta *meta,
+                         cudaStream_t s);
+int scan_excl_i32_to_i32(const int32_t *in, int32_t *out, int n, unsigned long long *status,
+                         unsigned int *ticket, Meta *meta, cudaStream_t s);
+int scan_status_words(int n);  // status array length for an n-element scan
+
+}  // namespace p3t
+
+// ---- context ---------------------------------------------------------------------------
+struct p3t_ctx {
+    p3t_params prm;
+    cudaStream_t stream;
+    int device;
+    int debug;
+    int sm_count;
+    // capacities of the current allocation
+    long long cap_n;
+    long long cap_nodes;
+    int cap_leaf;
+    int has_q64;
+    // state
+    int n;
+    int built;
+    int built_precision;
+    int pending_err;  // host-side latched error
+    // device memory
+    p3t::Meta *meta;
+    p3t::Tree tree;
+    uint64_t *keys_buf[2];
+    int32_t *perm_buf[2];
+    int32_t *sort_hist;               // 256 * sort blocks
+    unsigned long long *scan_status;  // look-back status words
+    int32_t *nbr_count;               // per particle (original order)
+    int64_t *grp_cells, *grp_parts;   // per group debug counts
+    void *blob;                       // single allocation backing everything above
+    size_t blob_bytes;
+    void *host_stage;                 // device staging of p3t_step_host
+    size_t host_stage_bytes;
+};
+
+namespace p3t {
+int ensure_capacity(p3t_ctx *c, long long n);
+int check_launch(p3t_ctx *c);
+int build_tree(p3t_ctx *c, int n, const double *x, const double *y, const double *z,
+               const double *m);
+int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc, int64_t *np);
+int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, int64_t *total_dev,
+               bool sync, int64_t *total_host);
+int kick(p3t_ctx *c, double dt, const void *ax, const void *ay, const void *az, double *vx,
+         double *vy, double *vz);
+int drift(p3t_ctx *c, int n, double dt, double *x, double *y, double *z, const double *vx,
+          const double *vy, const double *vz);
+int export_tree(p3t_ctx *c, uint64_t *keys, int32_t *perm, int32_t *level, int32_t *first,
+                int32_t *count, int32_t *child, int32_t *nchild, double *M, double *com,
+                double *Q, double *lo, double *hi, double *ropen2, int32_t *g_first,
+                int32_t *g_count);
+}  // namespace p3t

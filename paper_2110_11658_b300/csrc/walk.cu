@@ -1,0 +1,601 @@
+// Group-wise tree walk and far-force evaluation (Sec. 2.1 Eqs. 1, 3, 6;
+// Sec. 2.4 Barnes-Hut walk with opening angle theta).
+//
+// One warp walks the tree for one group of <= 32*TPL particles (a persistent
+// grid takes groups from an atomic ticket).  The traversal keeps a stack of
+// node ranges in shared memory; each step pops up to 32 nodes, one per lane,
+// and tests them:
+//   open  iff  dist(B_g, com_c)^2 < r_open_c^2   (opening angle, rule 8)
+//         or   dist(B_g, box_c)^2  < r_out^2     (the cell may hold a pair with W < 1)
+// The decision is defined in FP64.  In the mixed form it is first taken in
+// FP32 on coordinates relative to the cube centre O, with an error band that
+// bounds the FP32-vs-FP64 difference; only a test that falls inside the band
+// is recomputed with the exact FP64 operations (counted in meta->fallback_tests).
+// The interaction lists therefore equal the FP64 rule exactly.
+//
+// Accepted cells (monopole + quadrupole, W = 1) and opened leaves (particle
+// terms weighted by W) are queued in shared memory and evaluated once `tile`
+// of them are queued: every lane holds TPL target particles in registers and
+// loops over the queue, read by broadcast.  Relative coordinates are formed
+// in FP64 (x_source - c_g, x_i - c_g, c_g the group-box centre) and rounded to
+// FP32; interactions run in FP32 and each tile's partial sum is added to the
+// running sum with Kahan compensation.  The FP64 form does everything in FP64.
+#include <cstdint>
+
+#include "p3t_internal.cuh"
+
+namespace p3t {
+
+constexpr int kWalkWarps = 4;                // warps per block
+constexpr int kStackCap = 32 * 22 + 64;      // ranges per warp; see the bound below
+constexpr float kU = 5.9604644775390625e-8f;  // 2^-24, FP32 unit round-off
+
+// Stack bound: children ranges are pushed so that the stack stays sorted by
+// level (deepest on top).  Ranges of level l are created only while popping
+// level l-1 nodes, which happens only after every level-l range above them is
+// consumed; so at most 32 ranges per level are live: 32 * 22 in total.
+
+struct WalkArgs {
+    Tree T;
+    float inv_dr_f, rin_dr_f;   // x = r * inv_dr - r_in * inv_dr
+    double inv_dr_d, r_in_d;
+    double rout2_d;
+    float rout2_f;
+    int tile;
+    void *ax, *ay, *az;
+    double *pot;
+    unsigned long long *n_cell, *n_part;
+    long long *grp_cells, *grp_parts;
+    unsigned int *ticket;
+};
+
+template <typename Real>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using T = float4;
+    using T2 = float2;
+};
+template <>
+struct Vec4<double> {
+    using T = double4_32a;
+    using T2 = double2;
+};
+
+template <typename Real>
+__device__ __forceinline__ Real rsqrt_(Real x);
+template <>
+__device__ __forceinline__ float rsqrt_<float>(float x)
+{
+    return rsqrtf(x);
+}
+template <>
+__device__ __forceinline__ double rsqrt_<double>(double x)
+{
+    return 1.0 / sqrt(x);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real to_real(double v);
+template <>
+__device__ __forceinline__ float to_real<float>(double v)
+{
+    return __double2float_rn(v);
+}
+template <>
+__device__ __forceinline__ double to_real<double>(double v)
+{
+    return v;
+}
+
+__device__ __forceinline__ int pack_range(int first, int count) { return (first << 3) | (count - 1); }
+
+// shared-memory carve-up of one warp
+template <typename Real>
+struct WarpSmem {
+    using R4 = typename Vec4<Real>::T;
+    using R2 = typename Vec4<Real>::T2;
+    int *stk;
+    int *batch;
+    R4 *cpos;  // {dx, dy, dz, M} of accepted cells, relative to c_g
+    R4 *cqa;   // {Qxx, Qxy, Qxz, Qyy}
+    R2 *cqb;   // {Qyz, Qzz}
+    int2 *lq;  // opened leaves {first, count}
+    int *lqo;  // exclusive prefix of leaf counts
+    R4 *pp;    // staged source particles {dx, dy, dz, m}
+    static __host__ __device__ size_t bytes(int tile)
+    {
+        size_t cb = tile + 32;
+        size_t b = 4 * kStackCap + 4 * 32;
+        b += cb * (2 * sizeof(R4) + sizeof(R2));
+        b += cb * 8 + (cb + 1) * 4;
+        b = (b + 31) / 32 * 32;
+        b += 32 * sizeof(R4);
+        return (b + 127) / 128 * 128;
+    }
+    __device__ void carve(char *base, int tile)
+    {
+        size_t cb = tile + 32;
+        char *p = base;
+        stk = (int *)p;
+        p += 4 * kStackCap;
+        batch = (int *)p;
+        p += 4 * 32;
+        cpos = (R4 *)p;
+        p += cb * sizeof(R4);
+        cqa = (R4 *)p;
+        p += cb * sizeof(R4);
+        cqb = (R2 *)p;
+        p += cb * sizeof(R2);
+        lq = (int2 *)p;
+        p += cb * 8;
+        lqo = (int *)p;
+        p += (cb + 1) * 4;
+        p = base + ((p - base + 31) / 32 * 32);
+        pp = (R4 *)p;
+    }
+};
+
+// per-lane accumulator of TPL targets
+template <typename Real, int TPL>
+struct Acc {
+    Real s[TPL][4];  // running sums ax, ay, az, phi
+    Real c[TPL][4];  // Kahan compensation (mixed form)
+    Real p[TPL][4];  // partial sums of the current tile
+    __device__ void zero_all()
+    {
+#pragma unroll
+        for (int t = 0; t < TPL; t++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) s[t][k] = c[t][k] = p[t][k] = Real(0);
+    }
+    __device__ void fold()
+    {
+#pragma unroll
+        for (int t = 0; t < TPL; t++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (sizeof(Real) == 4) {
+                    Real y = p[t][k] - c[t][k];
+                    Real u = s[t][k] + y;
+                    c[t][k] = (u - s[t][k]) - y;
+                    s[t][k] = u;
+                } else {
+                    s[t][k] += p[t][k];
+                }
+                p[t][k] = Real(0);
+            }
+    }
+};
+
+template <typename Real, int TPL, bool POT, bool QUAD>
+__device__ __forceinline__ void eval_cells(const WarpSmem<Real> &W, int ncells, const Real (&px)[TPL],
+                                           const Real (&py)[TPL], const Real (&pz)[TPL],
+                                           Acc<Real, TPL> &A)
+{
+    using R4 = typename Vec4<Real>::T;
+    using R2 = typename Vec4<Real>::T2;
+    __syncwarp();
+#pragma unroll 2
+    for (int k = 0; k < ncells; k++) {
+        const R4 s = W.cpos[k];
+        R4 qa;
+        R2 qb;
+        if (QUAD) {
+            qa = W.cqa[k];
+            qb = W.cqb[k];
+        }
+#pragma unroll
+        for (int t = 0; t < TPL; t++) {
+            // r = x_i - com
+            const Real rx = px[t] - s.x, ry = py[t] - s.y, rz = pz[t] - s.z;
+            const Real r2 = rx * rx + ry * ry + rz * rz;
+            const Real ri = rsqrt_<Real>(r2);
+            const Real ri2 = ri * ri;
+            const Real ri3 = ri * ri2;
+            const Real mr3 = s.w * ri3;
+            if (QUAD) {
+                const Real qx = qa.x * rx + qa.y * ry + qa.z * rz;
+                const Real qy = qa.y * rx + qa.w * ry + qb.x * rz;
+                const Real qz = qa.z * rx + qb.x * ry + qb.y * rz;
+                const Real rqr = rx * qx + ry * qy + rz * qz;
+                const Real ri5 = ri3 * ri2;
+                const Real cf = -mr3 - Real(2.5) * rqr * ri5 * ri2;
+                A.p[t][0] += cf * rx + ri5 * qx;
+                A.p[t][1] += cf * ry + ri5 * qy;
+                A.p[t][2] += cf * rz + ri5 * qz;
+                if (POT) A.p[t][3] -= s.w * ri + Real(0.5) * rqr * ri5;
+            } else {
+                A.p[t][0] -= mr3 * rx;
+                A.p[t][1] -= mr3 * ry;
+                A.p[t][2] -= mr3 * rz;
+                if (POT) A.p[t][3] -= s.w * ri;
+            }
+        }
+    }
+    A.fold();
+    __syncwarp();
+}
+
+template <typename Real, int TPL, bool POT>
+__device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkArgs &P, int nleaves,
+                                           int nparts, double cgx, double cgy, double cgz,
+                                           const Real (&px)[TPL], const Real (&py)[TPL],
+                                           const Real (&pz)[TPL], Acc<Real, TPL> &A)
+{
+    using R4 = typename Vec4<Real>::T;
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    // exclusive prefix of the queued leaf counts
+    int carry = 0;
+    for (int b = 0; b < nleaves; b += 32) {
+        int i = b + lane;
+        int v = i < nleaves ? W.lq[i].y : 0;
+        int inc = warp_incl_scan(v);
+        if (i < nleaves) W.lqo[i] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    __syncwarp();
+    const double4_32a *__restrict__ sp = P.T.sp;
+    for (int c0 = 0; c0 < nparts; c0 += 32) {
+        int pos = c0 + lane;
+        if (pos < nparts) {
+            int lo = 0, hi = nleaves;  // last leaf with lqo <= pos
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (W.lqo[mid] <= pos)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            int j = W.lq[lo].x + (pos - W.lqo[lo]);
+            double4_32a q = sp[j];
+            R4 v;
+            v.x = to_real<Real>(dsub(q.x, cgx));
+            v.y = to_real<Real>(dsub(q.y, cgy));
+            v.z = to_real<Real>(dsub(q.z, cgz));
+            v.w = to_real<Real>(q.w);
+            W.pp[lane] = v;
+        }
+        __syncwarp();
+        const int ns = min(32, nparts - c0);
+        const Real inv_dr = sizeof(Real) == 4 ? Real(P.inv_dr_f) : Real(P.inv_dr_d);
+        const Real rin_dr = sizeof(Real) == 4 ? Real(P.rin_dr_f) : Real(P.r_in_d * P.inv_dr_d);
+#pragma unroll 2
+        for (int k = 0; k < ns; k++) {
+            const R4 s = W.pp[k];
+#pragma unroll
+            for (int t = 0; t < TPL; t++) {
+                // d = x_j - x_i
+                const Real dx = s.x - px[t], dy = s.y - py[t], dz = s.z - pz[t];
+                const Real r2 = dx * dx + dy * dy + dz * dz;
+                const Real ri = rsqrt_<Real>(r2);
+                const Real r = r2 * ri;
+                Real x = r * inv_dr - rin_dr;
+                // clamp to [0, 1]; NaN (r2 = 0) maps to 0
+                x = x > Real(0) ? (x < Real(1) ? x : Real(1)) : Real(0);
+                Real w = (Real(-20) * x + Real(70)) * x + Real(-84);
+                w = w * x + Real(35);
+                const Real x2 = x * x;
+                const Real Wt = w * (x2 * x2);
+                Real f = s.w * Wt * (ri * ri * ri);
+                f = Wt > Real(0) ? f : Real(0);
+                A.p[t][0] += f * dx;
+                A.p[t][1] += f * dy;
+                A.p[t][2] += f * dz;
+                if (POT) A.p[t][3] -= r2 > Real(0) ? s.w * ri : Real(0);
+            }
+        }
+        __syncwarp();
+    }
+    A.fold();
+}
+
+template <typename Real, int TPL, bool POT, bool QUAD>
+__global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkArgs P)
+{
+    extern __shared__ __align__(16) char smem[];
+    using R4 = typename Vec4<Real>::T;
+    using R2 = typename Vec4<Real>::T2;
+    constexpr bool kMixed = sizeof(Real) == 4;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    WarpSmem<Real> W;
+    W.carve(smem + (threadIdx.x >> 5) * WarpSmem<Real>::bytes(P.tile), P.tile);
+    const Tree &T = P.T;
+    Meta *meta = T.meta;
+    const int ng = meta->n_groups;
+    const int nn = meta->n_nodes;
+    const double Ox = meta->frame[0], Oy = meta->frame[1], Oz = meta->frame[2];
+    const int tile = P.tile;
+    // FP32 filter band (|FP32 - FP64| of a squared distance, with a factor ~2
+    // to spare): k_rel*(d2 + r2) + k_abs*|t|_1 + k_sq, where every coordinate
+    // relative to O is within R and carries <= 2^-24 R rounding.  Outside a
+    // safe range of scales the filter is off and every test is exact FP64.
+    const float Rf = (float)meta->frame[3] * 1.0001f;
+    const bool filter_ok = Rf > 1e-12f && Rf < 1e12f && P.rout2_f > 1e-30f && P.rout2_f < 1e30f;
+    const float k_rel = 8.f * kU;
+    const float k_abs = 8.f * kU * Rf;
+    const float k_sq = 16.f * kU * kU * Rf * Rf;
+
+    while (true) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(P.ticket, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ng) break;
+        const int2 gr = T.grp[g];
+        const double4_32a glo = T.glo[g], ghi = T.ghi[g];
+        const double cgx = dmul(0.5, dadd(glo.x, ghi.x));
+        const double cgy = dmul(0.5, dadd(glo.y, ghi.y));
+        const double cgz = dmul(0.5, dadd(glo.z, ghi.z));
+        // group box relative to O for the FP32 filter
+        const float glx = __double2float_rn(dsub(glo.x, Ox)), gly = __double2float_rn(dsub(glo.y, Oy)),
+                    glz = __double2float_rn(dsub(glo.z, Oz));
+        const float ghx = __double2float_rn(dsub(ghi.x, Ox)), ghy = __double2float_rn(dsub(ghi.y, Oy)),
+                    ghz = __double2float_rn(dsub(ghi.z, Oz));
+        Real px[TPL], py[TPL], pz[TPL];
+#pragma unroll
+        for (int t = 0; t < TPL; t++) {
+            int s = gr.x + lane + 32 * t;
+            if (s < gr.x + gr.y) {
+                double4_32a q = T.sp[s];
+                px[t] = to_real<Real>(dsub(q.x, cgx));
+                py[t] = to_real<Real>(dsub(q.y, cgy));
+                pz[t] = to_real<Real>(dsub(q.z, cgz));
+            } else {
+                px[t] = py[t] = pz[t] = Real(0);
+            }
+        }
+        Acc<Real, TPL> A;
+        A.zero_all();
+        int sp = 1;
+        if (lane == 0) W.stk[0] = pack_range(0, 1);
+        __syncwarp();
+        int cb = 0, lqn = 0, lqp = 0;
+        long long ncell = 0, npart = 0;
+        int nfallback = 0;
+        int iters = 0;  // a valid walk pops every node at most once
+        while (sp > 0) {
+            if (++iters > nn + 1) {
+                if (lane == 0) latch_error(meta, P3T_ERR_INTERNAL);
+                break;
+            }
+            // ---- pop up to 32 nodes from the top ranges
+            int e = lane < sp ? W.stk[sp - 1 - lane] : 0;
+            int cnt = lane < sp ? (e & 7) + 1 : 0;
+            int incl = warp_incl_scan(cnt);
+            int excl = incl - cnt;
+            int total = __shfl_sync(0xffffffffu, incl, 31);
+            int take = total < 32 ? total : 32;
+            unsigned full = __ballot_sync(0xffffffffu, lane < sp && incl <= take);
+            __syncwarp();
+            if (lane < sp && excl < take) {
+                int first = e >> 3;
+                int mine = cnt < take - excl ? cnt : take - excl;
+                for (int j = 0; j < mine; j++) W.batch[excl + j] = first + j;
+                if (mine < cnt) W.stk[sp - 1 - lane] = pack_range(first + mine, cnt - mine);
+            }
+            __syncwarp();
+            sp -= __popc(full);
+            const int node = lane < take ? W.batch[lane] : -1;
+            __syncwarp();
+
+            // ---- opening test
+            bool open = false, is_leaf = false;
+            int cinfo = 0, ccount = 0;
+            bool fb = false;
+            if (node >= 0) {
+                if (kMixed && filter_ok) {
+                    const float4 a = T.wA[node], b = T.wB[node], c = T.wC[node];
+                    cinfo = __float_as_int(b.w);
+                    ccount = __float_as_int(c.w);
+                    // point-box: COM against the group box
+                    float tx = fmaxf(fmaxf(glx - a.x, a.x - ghx), 0.f);
+                    float ty = fmaxf(fmaxf(gly - a.y, a.y - ghy), 0.f);
+                    float tz = fmaxf(fmaxf(glz - a.z, a.z - ghz), 0.f);
+                    float d2 = tx * tx + ty * ty + tz * tz;
+                    int mac;
+                    if (isinf(a.w)) {
+                        mac = 1;
+                    } else {
+                        float tol = k_rel * (d2 + a.w) + k_abs * (tx + ty + tz) + k_sq;
+                        mac = d2 < a.w - tol ? 1 : (d2 > a.w + tol ? 0 : 2);
+                    }
+                    // box-box against r_out
+                    float ux = fmaxf(fmaxf(b.x - ghx, glx - c.x), 0.f);
+                    float uy = fmaxf(fmaxf(b.y - ghy, gly - c.y), 0.f);
+                    float uz = fmaxf(fmaxf(b.z - ghz, glz - c.z), 0.f);
+                    float e2 = ux * ux + uy * uy + uz * uz;
+                    float tol2 = k_rel * (e2 + P.rout2_f) + k_abs * (ux + uy + uz) + k_sq;
+                    int bb = e2 < P.rout2_f - tol2 ? 1 : (e2 > P.rout2_f + tol2 ? 0 : 2);
+                    if (mac == 1 || bb == 1) {
+                        open = true;
+                    } else if (mac == 0 && bb == 0) {
+                        open = false;
+                    } else {
+                        fb = true;
+                        const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
+                        open = dist2_point_box(cm.x, cm.y, cm.z, glo, ghi) < cl.w ||
+                               dist2_box_box(glo, ghi, cl, ch) < P.rout2_d;
+                    }
+                } else {
+                    const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
+                    const float4 b = T.wB[node], c = T.wC[node];
+                    cinfo = __float_as_int(b.w);
+                    ccount = __float_as_int(c.w);
+                    open = dist2_point_box(cm.x, cm.y, cm.z, glo, ghi) < cl.w ||
+                           dist2_box_box(glo, ghi, cl, ch) < P.rout2_d;
+                }
+                is_leaf = cinfo < 0;
+            }
+            if (kMixed) nfallback += __popc(__ballot_sync(0xffffffffu, fb));
+            const bool accept = node >= 0 && !open;
+            bool open_int = node >= 0 && open && !is_leaf;
+            bool open_leaf = node >= 0 && open && is_leaf;
+            // consistency of the child / particle ranges before following them
+            const bool bad = (open_int && (ccount < 1 || ccount > 8 || cinfo + ccount > nn)) ||
+                             (open_leaf && (ccount < 1 || -1 - cinfo + ccount > T.n));
+            if (__any_sync(0xffffffffu, bad)) {
+                if (lane == 0) latch_error(meta, P3T_ERR_INTERNAL);
+                break;
+            }
+
+            // ---- push child ranges (lane 0's, the deepest, ends on top)
+            const unsigned pm = __ballot_sync(0xffffffffu, open_int);
+            const int npush = __popc(pm);
+            if (sp + npush > kStackCap) {
+                if (lane == 0) latch_error(meta, P3T_ERR_CAPACITY);
+                sp = 0;
+                break;
+            }
+            if (open_int) W.stk[sp + __popc(pm >> lane >> 1)] = pack_range(cinfo, ccount);
+            sp += npush;
+
+            // ---- queue accepted cells
+            const unsigned am = __ballot_sync(0xffffffffu, accept);
+            if (accept) {
+                const int pos = cb + __popc(am & lt);
+                const double4_32a cm = T.comM[node];
+                R4 v;
+                v.x = to_real<Real>(dsub(cm.x, cgx));
+                v.y = to_real<Real>(dsub(cm.y, cgy));
+                v.z = to_real<Real>(dsub(cm.z, cgz));
+                v.w = to_real<Real>(cm.w);
+                W.cpos[pos] = v;
+                if (QUAD) {
+                    R4 qa;
+                    R2 qb;
+                    if (kMixed) {
+                        const float2 *q = reinterpret_cast<const float2 *>(T.q32 + 6 * (size_t)node);
+                        float2 q0 = q[0], q1 = q[1], q2 = q[2];
+                        qa.x = q0.x, qa.y = q0.y, qa.z = q1.x, qa.w = q1.y, qb.x = q2.x, qb.y = q2.y;
+                    } else {
+                        const double2 *q = reinterpret_cast<const double2 *>(T.q64 + 6 * (size_t)node);
+                        double2 q0 = q[0], q1 = q[1], q2 = q[2];
+                        qa.x = q0.x, qa.y = q0.y, qa.z = q1.x, qa.w = q1.y, qb.x = q2.x, qb.y = q2.y;
+                    }
+                    W.cqa[pos] = qa;
+                    W.cqb[pos] = qb;
+                }
+            }
+            cb += __popc(am);
+            ncell += __popc(am);
+
+            // ---- queue opened leaves
+            const unsigned lm = __ballot_sync(0xffffffffu, open_leaf);
+            int lc = open_leaf ? ccount : 0;
+            if (open_leaf) W.lq[lqn + __popc(lm & lt)] = make_int2(-1 - cinfo, ccount);
+            lqn += __popc(lm);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lc += __shfl_xor_sync(0xffffffffu, lc, o);
+            lqp += lc;
+            npart += lc;
+
+            if (cb >= tile) {
+                eval_cells<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
+                cb = 0;
+            }
+            if (lqp >= tile) {
+                eval_parts<Real, TPL, POT>(W, P, lqn, lqp, cgx, cgy, cgz, px, py, pz, A);
+                lqn = lqp = 0;
+            }
+        }
+        if (cb > 0) eval_cells<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
+        if (lqp > 0) eval_parts<Real, TPL, POT>(W, P, lqn, lqp, cgx, cgy, cgz, px, py, pz, A);
+
+        // ---- results, scattered to the original order
+#pragma unroll
+        for (int t = 0; t < TPL; t++) {
+            int s = gr.x + lane + 32 * t;
+            if (s < gr.x + gr.y) {
+                int o = T.perm[s];
+                if (kMixed) {
+                    ((float *)P.ax)[o] = (float)(A.s[t][0] - A.c[t][0]);
+                    ((float *)P.ay)[o] = (float)(A.s[t][1] - A.c[t][1]);
+                    ((float *)P.az)[o] = (float)(A.s[t][2] - A.c[t][2]);
+                    if (POT) P.pot[o] = (double)A.s[t][3] - (double)A.c[t][3];
+                } else {
+                    ((double *)P.ax)[o] = (double)A.s[t][0];
+                    ((double *)P.ay)[o] = (double)A.s[t][1];
+                    ((double *)P.az)[o] = (double)A.s[t][2];
+                    if (POT) P.pot[o] = (double)A.s[t][3];
+                }
+            }
+        }
+        if (lane == 0) {
+            if (P.n_cell) atomicAdd(P.n_cell, (unsigned long long)(ncell * gr.y));
+            if (P.n_part) atomicAdd(P.n_part, (unsigned long long)(npart * gr.y));
+            if (P.grp_cells) {
+                P.grp_cells[g] = ncell;
+                P.grp_parts[g] = npart;
+            }
+            if (nfallback) atomicAdd((unsigned long long *)&meta->fallback_tests,
+                                     (unsigned long long)nfallback);
+        }
+        __syncwarp();
+    }
+}
+
+template <typename Real, int TPL, bool POT, bool QUAD>
+static int launch_walk(p3t_ctx *c, const WalkArgs &a)
+{
+    auto kern = walk_kernel<Real, TPL, POT, QUAD>;
+    const size_t smem = kWalkWarps * WarpSmem<Real>::bytes(a.tile);
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return P3T_ERR_CUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWalkWarps * 32, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return P3T_ERR_CUDA;
+    kern<<<per_sm * c->sm_count, kWalkWarps * 32, smem, c->stream>>>(a);
+    return check_launch(c);
+}
+
+template <typename Real, int TPL>
+static int dispatch_pq(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
+{
+    if (pot)
+        return quad ? launch_walk<Real, TPL, true, true>(c, a) : launch_walk<Real, TPL, true, false>(c, a);
+    return quad ? launch_walk<Real, TPL, false, true>(c, a) : launch_walk<Real, TPL, false, false>(c, a);
+}
+
+template <typename Real>
+static int dispatch_tpl(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
+{
+    const int G = c->prm.group_size;
+    if (G <= 32) return dispatch_pq<Real, 1>(c, a, pot, quad);
+    if (G <= 64) return dispatch_pq<Real, 2>(c, a, pot, quad);
+    return dispatch_pq<Real, 4>(c, a, pot, quad);
+}
+
+int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc, int64_t *np)
+{
+    const p3t_params &P = c->prm;
+    WalkArgs a;
+    a.T = c->tree;
+    const double dr = P.r_out - P.r_in;
+    a.inv_dr_d = 1.0 / dr;
+    a.r_in_d = P.r_in;
+    a.inv_dr_f = (float)a.inv_dr_d;
+    a.rin_dr_f = (float)(P.r_in * a.inv_dr_d);
+    a.rout2_d = P.r_out * P.r_out;
+    a.rout2_f = (float)a.rout2_d;
+    a.tile = P.tile;
+    a.ax = ax, a.ay = ay, a.az = az;
+    a.pot = pot;
+    a.n_cell = (unsigned long long *)nc;
+    a.n_part = (unsigned long long *)np;
+    a.grp_cells = c->debug ? (long long *)c->grp_cells : nullptr;
+    a.grp_parts = c->debug ? (long long *)c->grp_parts : nullptr;
+    a.ticket = &c->meta->tickets[22];
+    if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    const bool quad = P.quadrupole != 0;
+    const bool want_pot = pot != nullptr;
+    if (c->built_precision == P3T_FP64) return dispatch_tpl<double>(c, a, want_pot, quad);
+    return dispatch_tpl<float>(c, a, want_pot, quad);
+}
+
+}  // namespace p3t

@@ -1,0 +1,80 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI
+and the oracle on the same seeded inputs."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+import paper_2110_11658_b300 as p3t
+
+DEV = torch.device("cuda", 0)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def run_gpu(c, prm: p3t.Params, pot=True, nbr=True, debug=True, kick_dt=None):
+    """Build + far force (+ neighbours, + kick) on the GPU; everything back as numpy."""
+    ctx = p3t.Context(prm)
+    ctx.set_debug(debug)
+    x, y, z, m = to_dev(c.x), to_dev(c.y), to_dev(c.z), to_dev(c.m)
+    ctx.build_tree(x, y, z, m)
+    dt = ctx.acc_dtype
+    a = [torch.full((c.n,), float("nan"), dtype=dt, device=DEV) for _ in range(3)]
+    ph = torch.full((c.n,), float("nan"), dtype=torch.float64, device=DEV) if pot else None
+    nc = torch.zeros(1, dtype=torch.int64, device=DEV)
+    np_ = torch.zeros(1, dtype=torch.int64, device=DEV)
+    ctx.far_force(*a, pot=ph, n_cell=nc, n_part=np_)
+    out = {"a": torch.stack(a, 1).double().cpu().numpy(), "n_cell": int(nc.item()),
+           "n_part": int(np_.item())}
+    if pot:
+        out["pot"] = ph.cpu().numpy()
+    ctx.check()
+    out["tree"] = {k: v.cpu().numpy() for k, v in ctx.export_tree().items()}
+    out["tree"]["keys"] = out["tree"]["keys"].view(np.uint64)
+    if debug:
+        gc, gp = ctx.group_counts()
+        out["g_cells"], out["g_parts"] = gc.cpu().numpy(), gp.cpu().numpy()
+    if nbr:
+        offs = torch.empty(c.n + 1, dtype=torch.int64, device=DEV)
+        try:
+            idx = torch.empty(max(1, 8 * c.n), dtype=torch.int32, device=DEV)
+            tot = ctx.neighbours(offs, idx)
+        except p3t.P3TError as e:
+            if e.code != p3t.P3T_ERR_CAPACITY:
+                raise
+            idx = torch.empty(max(1, e.total), dtype=torch.int32, device=DEV)
+            tot = ctx.neighbours(offs, idx)
+        out["offs"] = offs.cpu().numpy()
+        out["idx"] = idx[:tot].cpu().numpy()
+    if kick_dt is not None:
+        vx, vy, vz = to_dev(c.vx), to_dev(c.vy), to_dev(c.vz)
+        ctx.kick(kick_dt, *a, vx, vy, vz)
+        out["v"] = torch.stack([vx, vy, vz], 1).cpu().numpy()
+    ctx.check()
+    ctx.close()
+    return out
+
+
+def rel_err(a, ref):
+    na = np.linalg.norm(ref, axis=1)
+    ok = na > 0
+    return np.linalg.norm(a - ref, axis=1)[ok] / na[ok]
+
+
+def assert_tree_equal(gpu_tree, ref, fp64_moments=True):
+    for k in ("keys", "perm", "level", "first", "count", "child", "nchild", "g_first", "g_count"):
+        g = gpu_tree[k]
+        r = ref[k]
+        assert g.shape == r.shape, (k, g.shape, r.shape)
+        assert np.array_equal(g, r), k
+    for k in ("M", "com", "lo", "hi", "ropen2"):
+        assert np.array_equal(gpu_tree[k], ref[k]), k
+    if fp64_moments:
+        assert np.array_equal(gpu_tree["Q"], ref["Q"]), "Q"
+    else:
+        # FP32 quadrupole: compare against the node's second moment scale
+        qs = np.abs(ref["Q"]).max(axis=1) + 1e-300
+        assert (np.abs(gpu_tree["Q"] - ref["Q"]).max(axis=1) <= 2e-5 * qs + 1e-30).all()

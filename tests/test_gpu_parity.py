@@ -1,0 +1,146 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Bit-exact: Morton keys, sort permutation, node topology, groups, FP64 moments
+(COM, boxes, opening radii), per-group interaction counts, neighbour lists
+and the kick.  Forces: the all-FP64 form within 1e-10 relative of the oracle
+tree; the mixed form within median 1e-5 and 99th percentile 1e-4 (the
+target accuracy of the distant-force path).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2110_11658_b300 as p3t
+import synth
+from gpu_helpers import assert_tree_equal, rel_err, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+MIXED, FP64 = p3t.P3T_FP32_MIXED, p3t.P3T_FP64
+
+CASES = [
+    # id, kind, n, masses, theta, r_out, leaf, G
+    ("plummer4096", "plummer", 4096, "equal", 0.5, 0.05, 16, 64),
+    ("king20k_kroupa", "king", 20000, "kroupa", 0.4, 0.02, 8, 32),
+    ("plummer3333_G128", "plummer", 3333, "kroupa", 0.7, 0.08, 16, 128),
+    ("plummer257_leaf1", "plummer", 257, "equal", 0.3, 0.05, 1, 64),
+    ("plummer33_G50", "plummer", 33, "equal", 0.5, 0.2, 4, 50),
+]
+
+
+def _case(kind, n, masses):
+    return synth.make(kind, n, synth.BASE_SEED + n, masses=masses)
+
+
+def _oracle(c, theta, r_out, leaf, G):
+    return oracle.Tree(c.x, c.y, c.z, c.m, theta, r_out, leaf_cap=leaf, group_size=G)
+
+
+@pytest.mark.parametrize("cid,kind,n,masses,theta,r_out,leaf,G", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_tree_forces_counts_neighbours(cid, kind, n, masses, theta, r_out, leaf, G, precision):
+    c = _case(kind, n, masses)
+    r_in = 0.1 * r_out
+    prm = p3t.Params(theta=theta, r_in=r_in, r_out=r_out, r_list=r_out, leaf_cap=leaf,
+                     group_size=G, precision=precision)
+    g = run_gpu(c, prm, kick_dt=1.0 / 256)
+    t = _oracle(c, theta, r_out, leaf, G)
+    ref = t.export()
+    assert_tree_equal(g["tree"], ref, fp64_moments=precision == FP64)
+    f = t.far(r_in)
+    # identical interaction lists: per-group counts equal the oracle's
+    assert np.array_equal(g["g_cells"], f["n_cell"])
+    assert np.array_equal(g["g_parts"], f["n_part"])
+    gc = ref["g_count"].astype(np.int64)
+    assert g["n_cell"] == int((gc * f["n_cell"]).sum())
+    assert g["n_part"] == int((gc * f["n_part"]).sum())
+    e = rel_err(g["a"], f["a"])
+    ep = np.abs(g["pot"] - f["pot"]) / np.abs(f["pot"])
+    if precision == FP64:
+        assert e.max() < 1e-10, e.max()
+        assert ep.max() < 1e-12
+    else:
+        assert np.median(e) <= 1e-5 and np.percentile(e, 99) <= 1e-4, (np.median(e), np.percentile(e, 99))
+        assert np.median(ep) <= 1e-6 and ep.max() < 1e-4
+    # neighbour lists, bit-exact
+    o2, i2 = oracle.neighbours_brute(c.x, c.y, c.z, r_out)
+    assert np.array_equal(g["offs"], o2)
+    assert np.array_equal(g["idx"], i2)
+    # kick of Eq. 12 on the GPU's own accelerations, bit-exact
+    v = oracle.kick(1.0 / 256, g["a"][:, 0], g["a"][:, 1], g["a"][:, 2], c.vx, c.vy, c.vz)
+    assert np.array_equal(g["v"], np.stack(v, 1))
+
+
+@pytest.mark.parametrize("precision", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_theta_zero_reproduces_direct_sum(precision):
+    c = synth.plummer(512, 77, masses="kroupa")
+    prm = p3t.Params(theta=0.0, r_in=0.005, r_out=0.05, r_list=0.05, leaf_cap=8, group_size=32,
+                     precision=precision)
+    g = run_gpu(c, prm, nbr=False)
+    d = oracle.direct_split(c.x, c.y, c.z, c.m, 0.005, 0.05)
+    e = rel_err(g["a"], d["far"])
+    assert g["n_cell"] == 0 and g["n_part"] == 512 * 512
+    assert e.max() < (1e-11 if precision == FP64 else 1e-5)
+
+
+@pytest.mark.parametrize("r_list", [0.01, 0.05, 0.13])
+def test_neighbour_radius_independent_of_r_out(r_list):
+    c = synth.king(6000, 5, 7.0)
+    prm = p3t.Params(theta=0.5, r_in=0.004, r_out=0.04, r_list=r_list, leaf_cap=16, group_size=64)
+    g = run_gpu(c, prm, pot=False)
+    o2, i2 = oracle.neighbours_brute(c.x, c.y, c.z, r_list)
+    assert np.array_equal(g["offs"], o2) and np.array_equal(g["idx"], i2)
+    assert (np.diff(o2) == 0).any() or r_list > 0.1  # empty rows occur and are legal
+
+
+def test_quadrupole_off_matches_oracle_monopole():
+    c = synth.plummer(4096, 3)
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, quadrupole=0, precision=FP64)
+    g = run_gpu(c, prm, nbr=False)
+    f = _oracle(c, 0.5, 0.05, 16, 64).far(0.005, quadrupole=False)
+    assert rel_err(g["a"], f["a"]).max() < 1e-10
+
+
+def test_edge_cases_tiny_and_degenerate():
+    rng = np.random.default_rng(4)
+    cases = []
+    # one particle: no force, no neighbours
+    cases.append(synth.Cluster(*(np.array([0.3]) for _ in range(3)), np.array([1.0]),
+                               *(np.zeros(1) for _ in range(3))))
+    # two coincident particles: W(0) = 0 -> no far force; they are neighbours
+    cases.append(synth.Cluster(np.array([0.1, 0.1]), np.array([0.2, 0.2]), np.array([0.3, 0.3]),
+                               np.array([0.5, 0.5]), *(np.zeros(2) for _ in range(3))))
+    # all particles at one point: side 0 -> 1, one level-21 leaf, chunked groups
+    n = 300
+    cases.append(synth.Cluster(np.full(n, -1.5), np.full(n, 2.0), np.full(n, 0.25),
+                               np.full(n, 1.0 / n), *(np.zeros(n) for _ in range(3))))
+    # a clump of duplicates inside a Plummer sphere, with some massless particles
+    p = synth.plummer(2000, 9)
+    p.x[:150] = p.x[0]
+    p.y[:150] = p.y[0]
+    p.z[:150] = p.z[0]
+    p.m[rng.choice(2000, 100, replace=False)] = 0.0
+    cases.append(p)
+    for c in cases:
+        for precision in (FP64, MIXED):
+            prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, precision=precision)
+            g = run_gpu(c, prm)
+            t = _oracle(c, 0.5, 0.05, 16, 64)
+            ref = t.export()
+            assert_tree_equal(g["tree"], ref, fp64_moments=precision == FP64)
+            f = t.far(0.005)
+            assert np.array_equal(g["g_cells"], f["n_cell"])
+            assert np.array_equal(g["g_parts"], f["n_part"])
+            scale = np.abs(f["a"]).max() + 1e-300
+            assert np.abs(g["a"] - f["a"]).max() <= (1e-12 if precision == FP64 else 1e-5) * scale
+            o2, i2 = oracle.neighbours_brute(c.x, c.y, c.z, 0.05)
+            assert np.array_equal(g["offs"], o2) and np.array_equal(g["idx"], i2)
+
+
+def test_repeatable_bitwise():
+    c = synth.plummer(30000, 12, masses="kroupa")
+    prm = p3t.Params(theta=0.4, r_in=0.004, r_out=0.04, r_list=0.04)
+    a = run_gpu(c, prm, nbr=True)
+    b = run_gpu(c, prm, nbr=True)
+    assert np.array_equal(a["a"], b["a"]) and np.array_equal(a["pot"], b["pot"])
+    assert np.array_equal(a["idx"], b["idx"])
