@@ -35,8 +35,12 @@
  *      internal nodes combine their children in octant order; COM, traceless
  *      quadrupole Q = sum m (3 d d^T - |d|^2 I), tight AABB; massless nodes
  *      put the COM at the AABB centre.
- *   7. groups: a node with count <= G whose parent has count > G (or the root
- *      if n <= G); a leaf with count > G is cut into consecutive chunks of G.
+ *   7. groups: let B = 16 G.  A node with count <= B whose parent has count > B
+ *      (or the root if n <= B), and a leaf with count > B, are cut into
+ *      consecutive chunks of G particles in key order (the last chunk of a
+ *      node may be smaller); the chunks, ordered by first particle, are the
+ *      walk groups.  Groups therefore stay inside nodes of at most 16 G
+ *      particles and are full except at node ends.
  *   8. opening test of cell c for group g (box B_g): open iff
  *         dist(B_g, com_c)^2 < r_open_c^2,  r_open = l_c/theta + delta_c
  *      (l_c longest side of the cell box, delta_c = |com_c - box centre|,
@@ -58,6 +62,7 @@
 
 #define ORC_LEVELS 21
 #define ORC_QMAX 2097151LL /* 2^21 - 1 */
+#define ORC_GROUP_NODE_FACTOR 16 /* rule 7: groups are cut from nodes of <= 16 G particles */
 
 /* ------------------------------------------------------------------------ */
 /* Part 1: changeover function and the direct split sum                      */
@@ -417,13 +422,12 @@ orc_tree *orc_tree_build(int64_t n, const double *x, const double *y, const doub
     for (int64_t k = nn - 1; k >= 0; k--) orc_node_moments(t, k);
     /* rule 7: groups, then ordered by first particle */
     int64_t gcap = 0;
+    int64_t big = (int64_t)ORC_GROUP_NODE_FACTOR * group_size;
     for (int64_t k = 0; k < nn; k++) {
         int32_t c = t->count[k];
-        int parent_big = (k == 0) || t->count[t->parent[k]] > group_size;
+        int parent_big = (k == 0) || t->count[t->parent[k]] > big;
         if (!parent_big) continue;
-        if (c <= group_size) {
-            orc_group_push(t, t->first[k], c, &gcap);
-        } else if (t->nchild[k] == 0) {
+        if (c <= big || t->nchild[k] == 0) {
             for (int32_t f = 0; f < c; f += group_size)
                 orc_group_push(t, t->first[k] + f, c - f < group_size ? c - f : group_size, &gcap);
         }

@@ -124,21 +124,27 @@ def test_sort_topology_moments(kind, n, leaf):
 
 def test_groups_partition_and_rule():
     c = synth.plummer(5000, synth.BASE_SEED + 5)
-    for g in (32, 64, 128):
+    for g in (8, 32, 64, 128):
         t = oracle.Tree(c.x, c.y, c.z, c.m, 0.5, 0.05, leaf_cap=16, group_size=g)
         d = t.export()
         f, n = d["g_first"], d["g_count"]
         assert f[0] == 0 and np.array_equal(f[1:], (f + n)[:-1]) and f[-1] + n[-1] == 5000
         assert n.max() <= g
-        # each group is a node whose parent holds more than g particles
-        nodes = {(a, b): k for k, (a, b) in enumerate(zip(d["first"], d["count"]))}
-        parent = {}
-        for k in range(t.n_nodes):
+        # rebuild the rule by recursion: chunks of g inside nodes of <= 16 g
+        # particles whose parent holds more (or big leaves)
+        expect = []
+
+        def rec(k):
+            cnt = d["count"][k]
+            if cnt <= 16 * g or d["nchild"][k] == 0:
+                for s0 in range(0, cnt, g):
+                    expect.append((d["first"][k] + s0, min(g, cnt - s0)))
+                return
             for j in range(d["child"][k], d["child"][k] + d["nchild"][k]):
-                parent[j] = k
-        for a, b in zip(f, n):
-            k = nodes[(a, b)]
-            assert k == 0 or d["count"][parent[k]] > g
+                rec(j)
+
+        rec(0)
+        assert sorted(expect) == list(zip(f.tolist(), n.tolist()))
         xs = np.stack([c.x, c.y, c.z], 1)[d["perm"]]
         for i in range(len(f)):
             p = xs[f[i]:f[i] + n[i]]
@@ -146,18 +152,19 @@ def test_groups_partition_and_rule():
 
 
 def test_big_leaf_is_chunked():
-    # 201 coincident particles at 0.5 plus 0, 0.25 (octant 0) and 0.75, 1 (octant 7):
-    # the level-21 leaf of 201 is cut into chunks 64, 64, 64, 9
-    x = np.concatenate([np.full(200, 0.5), np.linspace(0, 1, 5)])
+    # 1201 coincident particles at 0.5 plus 0, 0.25 (octant 0) and 0.75, 1
+    # (octant 7): with G = 64 the level-21 leaf of 1201 > 16 G is cut into 18
+    # chunks of 64 and one of 49; the two 2-particle branches are groups
+    x = np.concatenate([np.full(1200, 0.5), np.linspace(0, 1, 5)])
     m = np.full(x.size, 1.0 / x.size)
     t = oracle.Tree(x, x, x, m, 0.5, 0.01, leaf_cap=16, group_size=64)
     d = t.export()
     assert d["level"].max() == 21
     leaf21 = np.nonzero((d["level"] == 21) & (d["count"] > 64))[0]
-    assert d["count"][leaf21].tolist() == [201]
-    assert sorted(d["g_count"].tolist()) == [2, 2, 9, 64, 64, 64]
+    assert d["count"][leaf21].tolist() == [1201]
+    assert sorted(d["g_count"].tolist()) == sorted([2, 2, 49] + [64] * 18)
     f0 = d["first"][leaf21[0]]
-    chunks = [(f0 + 64 * k, 64) for k in range(3)] + [(f0 + 192, 9)]
+    chunks = [(f0 + 64 * k, 64) for k in range(18)] + [(f0 + 1152, 49)]
     assert set(chunks) <= set(zip(d["g_first"].tolist(), d["g_count"].tolist()))
 
 
