@@ -50,7 +50,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
-    ap.add_argument("--group-size", type=int, default=64)
+    ap.add_argument("--group-size", type=int, default=32)
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--leaf-cap", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
@@ -185,7 +185,7 @@ def fp32_peak_tflops(sm_count, sm_max_mhz):
 
 
 # ---------------------------------------------------------------------------- CPU oracle
-def cpu_sample(c, prm, budget_s, with_neighbours=True):
+def cpu_sample(c, prm, budget_s, with_neighbours=True, group_size=32, leaf_cap=16):
     """Time the oracle on a bounded sample of one step; returns step-time estimate.
 
     The oracle builds the whole tree (all N particles), then evaluates the far
@@ -197,7 +197,8 @@ def cpu_sample(c, prm, budget_s, with_neighbours=True):
 
     import oracle
     t0 = time.perf_counter()
-    tree = oracle.Tree(c.x, c.y, c.z, c.m, prm["theta"], prm["r_out"], leaf_cap=16, group_size=64)
+    tree = oracle.Tree(c.x, c.y, c.z, c.m, prm["theta"], prm["r_out"], leaf_cap=leaf_cap,
+                       group_size=group_size)
     t_build = time.perf_counter() - t0
     ex = tree.export()
     gcount = ex["g_count"]
@@ -218,7 +219,8 @@ def cpu_sample(c, prm, budget_s, with_neighbours=True):
         done += len(sel)
         chunk *= 2
     t4 = time.perf_counter()
-    oracle.kick(DT, c.vx, c.vy, c.vz, c.vx, c.vy, c.vz)
+    zeros = np.zeros(c.n)
+    oracle.kick(DT, zeros, zeros, zeros, c.vx, c.vy, c.vz)
     t_kick = time.perf_counter() - t4
     scale = c.n / max(1, parts)
     step = t_build + (t_force + t_nbr) * scale + t_kick
@@ -366,7 +368,7 @@ def run_b300(args, rank, local, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = cpu_sample(c, w, args.cpu_budget)
+        s = cpu_sample(c, w, args.cpu_budget, group_size=args.group_size, leaf_cap=args.leaf_cap)
         cpu = {"value": c.n / s["step_s"], "unit": "particles/s", "cores": omp_threads(), "kind": "oracle",
                "sample": "oracle tree build of all %d particles, far force + neighbour lists of the first %d "
                          "groups (%d particles) scaled to all N, kick of all N; %.1f s of CPU work"
@@ -396,6 +398,8 @@ def run_b300(args, rank, local, world):
         "far_force_evals_per_s": total_particles / (far_ms * 1e-3),
         "interactions_per_s": inter / (far_ms * 1e-3) * world,
         "interactions_per_particle": inter / n,
+        "cell_interactions_per_particle": ncell / n,
+        "particle_interactions_per_particle": npart / n,
         "fp32_pct_of_peak": 100.0 * achieved / fp32_peak,
         "phase_ms": {k: v / args.steps for k, v in ph.items()},
         "mean_neighbours": nbr_total / n,
@@ -426,7 +430,8 @@ def run_reference(args, rank, world):
     times = []
     samples = []
     for i in range(args.warmup + args.steps):
-        s = cpu_sample(c, w, max(2.0, args.cpu_budget / 4))
+        s = cpu_sample(c, w, max(2.0, args.cpu_budget / 4), group_size=args.group_size,
+                       leaf_cap=args.leaf_cap)
         if i >= args.warmup:
             times.append(s["step_s"])
             samples.append(s)
@@ -442,8 +447,8 @@ def run_reference(args, rank, world):
         "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "plummer_kroupa_n%d_theta%.1f_nbr100" % (c.n, THETA), "n": c.n, "theta": THETA,
-                   "r_out": w["r_out"], "r_in": w["r_in"], "r_list": w["r_list"], "leaf_cap": 16,
-                   "group_size": 64, "dt": DT, "quadrupole": True},
+                   "r_out": w["r_out"], "r_in": w["r_in"], "r_list": w["r_list"], "leaf_cap": args.leaf_cap,
+                   "group_size": args.group_size, "dt": DT, "quadrupole": True},
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -66,7 +66,7 @@ typedef struct {
 typedef struct p3t_ctx p3t_ctx; /* opaque; owns the tree and all scratch memory */
 
 /* Fill *p with defaults: theta 0.5, r_in 0.005, r_out 0.05, r_list 0.05, leaf_cap 16,
- * group_size 64, tile 64, threads_per_group 32, P3T_FP32_MIXED, quadrupole 1. */
+ * group_size 32, tile 64, threads_per_group 32, P3T_FP32_MIXED, quadrupole 1. */
 int p3t_default_params(p3t_params *p);
 
 /* Create a context bound to the current CUDA device and to `cuda_stream`

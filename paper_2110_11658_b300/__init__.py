@@ -106,7 +106,7 @@ class Params:
     r_out: float = 0.05
     r_list: float = 0.05
     leaf_cap: int = 16
-    group_size: int = 64
+    group_size: int = 32
     tile: int = 64
     threads_per_group: int = 32
     precision: int = P3T_FP32_MIXED

@@ -228,30 +228,40 @@ __global__ void __launch_bounds__(kBuildThreads)
 }
 
 // ---------------------------------------------------------------------------
+// particles in key order, FP64 and as a double-single split relative to O
 __global__ void __launch_bounds__(kBuildThreads)
     gather_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
                   const double *__restrict__ z, const double *__restrict__ m,
-                  const int32_t *__restrict__ perm, double4_32a *__restrict__ sp)
+                  const int32_t *__restrict__ perm, const Meta *__restrict__ meta,
+                  double4_32a *__restrict__ sp, float4 *__restrict__ ph, float4 *__restrict__ pl)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int i = perm[s];
-    sp[s] = make_double4_32a(x[i], y[i], z[i], m[i]);
+    double px = x[i], py = y[i], pz = z[i], pm = m[i];
+    sp[s] = make_double4_32a(px, py, pz, pm);
+    float hx, hy, hz, lx, ly, lz;
+    ds_split(dsub(px, meta->frame[0]), hx, lx);
+    ds_split(dsub(py, meta->frame[1]), hy, ly);
+    ds_split(dsub(pz, meta->frame[2]), hz, lz);
+    ph[s] = make_float4(hx, hy, hz, __double2float_rn(pm));
+    pl[s] = make_float4(lx, ly, lz, 0.f);
 }
 
 // ---------------------------------------------------------------------------
 // topology
 
-// flag the walk groups a new node starts (rule 7)
+// Walk groups: with B = 16 G, a node holding <= B particles whose parent holds
+// more than B (or the root if n <= B), and a leaf holding more than B, are cut
+// into consecutive chunks of G particles; flag the first particle of each chunk.
+constexpr int kGroupNodeFactor = 16;
+
 __device__ __forceinline__ void flag_groups(unsigned char *gflag, int first, int count,
                                             bool parent_big, bool is_leaf, int G)
 {
     if (!parent_big) return;
-    if (count <= G) {
-        gflag[first] = 1;
-    } else if (is_leaf) {
+    if (count <= kGroupNodeFactor * G || is_leaf)
         for (int f = 0; f < count; f += G) gflag[first + f] = 1;
-    }
 }
 
 __global__ void topo_root_kernel(Tree T, int n, int leaf_cap, int G)
@@ -319,7 +329,7 @@ __global__ void __launch_bounds__(kBuildThreads)
         long long pre = lookback_prefix(status, t, tot, M, &sh_pre);
         const int child_base = base + nl + (int)(pre + ex);
         if (split) {
-            const bool big = tp.y > G;
+            const bool big = tp.y > kGroupNodeFactor * G;
             if (child_base + nch > T.cap_nodes) {
                 latch_error(M, P3T_ERR_CAPACITY);
             } else {
@@ -442,8 +452,12 @@ __device__ void write_node(Tree &T, int k, double M, const double com[3], const 
     }
     const double *O = T.meta->frame;
     const bool leaf = tp.z < 0;
-    T.wA[k] = make_float4(__double2float_rn(dsub(com[0], O[0])), __double2float_rn(dsub(com[1], O[1])),
-                          __double2float_rn(dsub(com[2], O[2])), __double2float_rn(ro2));
+    float chx, chy, chz, clx, cly, clz;
+    ds_split(dsub(com[0], O[0]), chx, clx);
+    ds_split(dsub(com[1], O[1]), chy, cly);
+    ds_split(dsub(com[2], O[2]), chz, clz);
+    T.wA[k] = make_float4(chx, chy, chz, __double2float_rn(ro2));
+    T.wD[k] = make_float4(clx, cly, clz, __double2float_rn(M));
     T.wB[k] = make_float4(__double2float_rn(dsub(lo[0], O[0])), __double2float_rn(dsub(lo[1], O[1])),
                           __double2float_rn(dsub(lo[2], O[2])),
                           __int_as_float(leaf ? -1 - tp.x : tp.z));
@@ -633,7 +647,7 @@ int build_tree(p3t_ctx *c, int n, const double *x, const double *y, const double
     }
     T.keys = c->keys_buf[0];
     T.perm = c->perm_buf[0];
-    gather_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, m, T.perm, T.sp);
+    gather_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, m, T.perm, M, T.sp, T.ph, T.pl);
 
     // topology, level by level
     unsigned long long *topo_status = c->scan_status + (n / 256 + 64 + 256 * nb / 256);

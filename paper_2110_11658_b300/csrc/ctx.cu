@@ -50,6 +50,8 @@ int ensure_capacity(p3t_ctx *c, long long n)
         {(void **)&c->perm_buf[0], 4 * (size_t)N},
         {(void **)&c->perm_buf[1], 4 * (size_t)N},
         {(void **)&T.sp, 32 * (size_t)N},
+        {(void **)&T.ph, 16 * (size_t)N},
+        {(void **)&T.pl, 16 * (size_t)N},
         {(void **)&T.gflag, (size_t)N + 16},
         {(void **)&T.gidx, 4 * (size_t)N},
         {(void **)&T.grp, 8 * (size_t)N},
@@ -72,6 +74,7 @@ int ensure_capacity(p3t_ctx *c, long long n)
         {(void **)&T.wA, 16 * (size_t)NN},
         {(void **)&T.wB, 16 * (size_t)NN},
         {(void **)&T.wC, 16 * (size_t)NN},
+        {(void **)&T.wD, 16 * (size_t)NN},
     };
     size_t total = 0;
     for (auto &it : items) total += align_up(it.bytes, 256);
@@ -139,7 +142,7 @@ int p3t_default_params(p3t_params *p)
     p->r_out = 0.05;
     p->r_list = 0.05;
     p->leaf_cap = 16;
-    p->group_size = 64;
+    p->group_size = 32;
     p->tile = 64;
     p->threads_per_group = 32;
     p->precision = P3T_FP32_MIXED;
@@ -198,6 +201,7 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *x, const double *y, cons
     int e = ensure_capacity(c, n);
     if (e) return e;
     c->built = 0;
+    c->counts_valid = 0;
     e = build_tree(c, (int)n, x, y, z, m);
     if (e) return e;
     c->n = (int)n;

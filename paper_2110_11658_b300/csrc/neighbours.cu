@@ -2,15 +2,18 @@
 // irregular (Hermite) side: row i lists every j != i with |x_i - x_j| < r_list,
 // by ascending original index; empty rows are legal.
 //
-// Three passes over the tree, one warp per walk group:
+// Passes, one warp per walk group:
 //   count  walk opening every cell whose box lies within r_list of the group
 //          box, test each target against the particles of the opened leaves
+//          (skipped when the far-force walk already counted: r_list <= r_out)
 //   scan   counts -> int64 row offsets (look-back scan)
-//   fill   the same walk, writing original indices; then each row is sorted.
+//   fill   the same walk, writing original indices; then each row is sorted
+//          in registers (warp-wide bitonic network).
 // The pair test is defined in FP64 as r2 = (dx*dx + dy*dy) + dz*dz < r_list^2.
 // It is first taken in FP32 on coordinates relative to the group centre
-// (formed in FP64); a pair inside the FP32 error band is re-tested with the
-// exact FP64 operations, so the lists equal the FP64 definition bit for bit.
+// (double-single differences); a pair inside the FP32 error band is re-tested
+// with the exact FP64 operations, so the lists equal the FP64 definition bit
+// for bit.
 #include <climits>
 #include <cstdint>
 
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
     const int nn = meta->n_nodes;
     const double Ox = meta->frame[0], Oy = meta->frame[1], Oz = meta->frame[2];
     const float Rf = (float)meta->frame[3] * 1.0001f;
-    const bool filter_ok = Rf > 1e-12f && Rf < 1e12f && P.rl2_f > 1e-30f && P.rl2_f < 1e30f;
+    const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && P.rl2_f > 1e-20f && P.rl2_f < 1e30f;
     const float k_rel = 8.f * kUn, k_abs = 8.f * kUn * Rf, k_sq = 16.f * kUn * kUn * Rf * Rf;
     bool allowed = true;
     if (FILL) allowed = P.offs[T.n] <= P.capacity;
@@ -75,6 +78,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         const double cgx = dmul(0.5, dadd(glo.x, ghi.x));
         const double cgy = dmul(0.5, dadd(glo.y, ghi.y));
         const double cgz = dmul(0.5, dadd(glo.z, ghi.z));
+        float fhx, fhy, fhz, flx, fly, flz;  // double-single split of c_g - O
+        ds_split(dsub(cgx, Ox), fhx, flx);
+        ds_split(dsub(cgy, Oy), fhy, fly);
+        ds_split(dsub(cgz, Oz), fhz, flz);
         const float glx = __double2float_rn(dsub(glo.x, Ox)), gly = __double2float_rn(dsub(glo.y, Oy)),
                     glz = __double2float_rn(dsub(glo.z, Oz));
         const float ghx = __double2float_rn(dsub(ghi.x, Ox)), ghy = __double2float_rn(dsub(ghi.y, Oy)),
@@ -89,10 +96,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
             cnt[t] = 0;
             base[t] = 0;
             if (s < gr.x + gr.y) {
-                double4_32a q = T.sp[s];
-                px[t] = __double2float_rn(dsub(q.x, cgx));
-                py[t] = __double2float_rn(dsub(q.y, cgy));
-                pz[t] = __double2float_rn(dsub(q.z, cgz));
+                const float4 h = T.ph[s], l = T.pl[s];
+                px[t] = (h.x - fhx) + (l.x - flx);
+                py[t] = (h.y - fhy) + (l.y - fly);
+                pz[t] = (h.z - fhz) + (l.z - flz);
                 si[t] = s;
                 A = fmaxf(A, fmaxf(fabsf(px[t]), fmaxf(fabsf(py[t]), fabsf(pz[t]))));
                 if (FILL) base[t] = P.offs[T.perm[s]];
@@ -104,9 +111,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) A = fmaxf(A, __shfl_xor_sync(0xffffffffu, A, o));
         A *= 1.0001f;
-        // band of the pair test (FP32 vs FP64 squared distance), factor ~2 spare
-        const float tpair = kUn * (20.f * P.rl2_f + 16.f * A * P.rl_f) +
-                            32.f * kUn * kUn * (A + 2.f * P.rl_f) * (A + 2.f * P.rl_f);
+        // band of the pair test (FP32 vs FP64 squared distance), factor ~2 spare:
+        // coordinates relative to c_g carry <= 2.01 u |x - c_g| + 8 u^2 R
+        const float tpair = kUn * (24.f * P.rl2_f + 32.f * A * P.rl_f + 128.f * kUn * Rf * P.rl_f) +
+                            64.f * kUn * kUn * (A + 2.f * P.rl_f) * (A + 2.f * P.rl_f);
         const bool pair_filter = filter_ok && A < 1e12f;
 
         int sp = 1;
@@ -212,10 +220,9 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                             hi = mid;
                     }
                     int j = W.lq[lo].x + (pos - W.lqo[lo]);
-                    double4_32a q = T.sp[j];
-                    W.pp[lane] = make_float4(__double2float_rn(dsub(q.x, cgx)),
-                                             __double2float_rn(dsub(q.y, cgy)),
-                                             __double2float_rn(dsub(q.z, cgz)), 0.f);
+                    const float4 h = T.ph[j], l = T.pl[j];
+                    W.pp[lane] = make_float4((h.x - fhx) + (l.x - flx), (h.y - fhy) + (l.y - fly),
+                                             (h.z - fhz) + (l.z - flz), 0.f);
                     W.pj[lane] = j;
                 }
                 __syncwarp();
@@ -257,12 +264,15 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 }
 
 // ---- per-row ascending sort --------------------------------------------------
+// One warp per row.  Rows of up to 32*K entries sit in registers, element
+// e = 32 r + lane in register r of lane `lane`; a bitonic network sorts them
+// (partners 32 apart or more are in the same lane, closer ones are exchanged
+// by shuffles).  Longer rows fall back to a heap sort by one thread.
 constexpr int kSortWarps = 4;
-constexpr int kRowBuf = 1024;
+constexpr int kRowMaxReg = 1024;
 
 __device__ void heap_sort_global(int32_t *a, long long n)
 {
-    // single-thread fallback for rows longer than the shared buffer
     auto sift = [&](long long start, long long end) {
         long long root = start;
         while (2 * root + 1 < end) {
@@ -287,11 +297,54 @@ __device__ void heap_sort_global(int32_t *a, long long n)
     }
 }
 
+template <int K>
+__device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len)
+{
+    const int lane = threadIdx.x & 31;
+    int v[K];
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        int e = 32 * r + lane;
+        v[r] = e < len ? row[e] : INT_MAX;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32 * K; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int rj = j >> 5;
+#pragma unroll
+                for (int r = 0; r < K; r++) {
+                    const int r2 = r ^ rj;
+                    if (r2 > r) {
+                        const bool up = ((32 * r + lane) & k) == 0;
+                        const int a = v[r], bb = v[r2];
+                        const int lo = min(a, bb), hi = max(a, bb);
+                        v[r] = up ? lo : hi;
+                        v[r2] = up ? hi : lo;
+                    }
+                }
+            } else {
+                const bool lower = (lane & j) == 0;
+#pragma unroll
+                for (int r = 0; r < K; r++) {
+                    const bool up = ((32 * r + lane) & k) == 0;
+                    const int p = __shfl_xor_sync(0xffffffffu, v[r], j);
+                    v[r] = (lower == up) ? min(v[r], p) : max(v[r], p);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        int e = 32 * r + lane;
+        if (e < len) row[e] = v[r];
+    }
+}
+
 __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_kernel(int n, const int64_t *__restrict__ offs, int32_t *idx, long long capacity)
 {
-    __shared__ int32_t buf[kSortWarps][kRowBuf];
-    int32_t *b = buf[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     if (offs[n] > capacity) return;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
@@ -299,32 +352,21 @@ __global__ void __launch_bounds__(kSortWarps * 32)
         const long long o = offs[i];
         const int len = (int)(offs[i + 1] - o);
         if (len <= 1) continue;
-        if (len > kRowBuf) {
-            if (lane == 0) heap_sort_global(idx + o, len);
-            __syncwarp();
-            continue;
-        }
-        int P2 = 32;
-        while (P2 < len) P2 <<= 1;
-        for (int k = lane; k < P2; k += 32) b[k] = k < len ? idx[o + k] : INT_MAX;
-        __syncwarp();
-        for (int k = 2; k <= P2; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int t = lane; t < P2; t += 32) {
-                    int u = t ^ j;
-                    if (u > t) {
-                        bool up = (t & k) == 0;
-                        int32_t x = b[t], y = b[u];
-                        if ((x > y) == up) {
-                            b[t] = y;
-                            b[u] = x;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        for (int k = lane; k < len; k += 32) idx[o + k] = b[k];
+        int32_t *row = idx + o;
+        if (len <= 32)
+            warp_bitonic_row<1>(row, len);
+        else if (len <= 64)
+            warp_bitonic_row<2>(row, len);
+        else if (len <= 128)
+            warp_bitonic_row<4>(row, len);
+        else if (len <= 256)
+            warp_bitonic_row<8>(row, len);
+        else if (len <= 512)
+            warp_bitonic_row<16>(row, len);
+        else if (len <= kRowMaxReg)
+            warp_bitonic_row<32>(row, len);
+        else if (lane == 0)
+            heap_sort_global(row, len);
         __syncwarp();
     }
 }
@@ -367,8 +409,12 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
     a.idx = idx;
     a.capacity = capacity;
     a.ticket = &c->meta->tickets[23];
-    int e = dispatch_nbr<false>(c, a);
-    if (e) return e;
+    int e;
+    if (!c->counts_valid) {  // the far-force walk did not count (r_list > r_out or FP64)
+        e = dispatch_nbr<false>(c, a);
+        if (e) return e;
+        c->counts_valid = 1;
+    }
     e = scan_excl_i32_to_i64(c->nbr_count, offsets, n, offsets + n, c->scan_status,
                              &c->meta->tickets[29], c->meta, s);
     if (e) return e;

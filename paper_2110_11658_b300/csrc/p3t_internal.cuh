@@ -8,7 +8,9 @@
 //                             comM double4_32a = {com.xyz, M}, lo double4_32a = {lo.xyz, r_open^2},
 //                             hi double4_32a = {hi.xyz, 0}, Q (FP64: double[6] | FP32: float[6]),
 //                             walk filter float4 wA = {com-O, r_open^2}, wB = {lo-O, child/leaf},
-//                             wC = {hi-O, nchild/count}  (O = centre of the bounding cube)
+//                             wC = {hi-O, nchild/count}, wD = {lo part of com-O, M}
+//                             (O = centre of the bounding cube; wA.xyz + wD.xyz is
+//                             the double-single split of com - O)
 //   groups, particle order:   grp int2 = {first, count}, glo/ghi double4_32a (tight box)
 #pragma once
 
@@ -46,6 +48,7 @@ struct Tree {
     uint64_t *keys;
     int32_t *perm;
     double4_32a *sp;
+    float4 *ph, *pl;
     int4 *topo;
     int32_t *level;
     int32_t *parent;
@@ -55,7 +58,7 @@ struct Tree {
     double4_32a *hi;
     double *q64;   // 6 per node (FP64 form)
     float *q32;    // 6 per node (mixed form)
-    float4 *wA, *wB, *wC;
+    float4 *wA, *wB, *wC, *wD;
     int2 *grp;
     double4_32a *glo, *ghi;
     unsigned char *gflag;  // group-start flags, particle order
@@ -97,6 +100,13 @@ __device__ __forceinline__ double dist2_box_box(double4_32a glo, double4_32a ghi
     double ty = dmax(dmax(dsub(clo.y, ghi.y), dsub(glo.y, chi.y)), 0.0);
     double tz = dmax(dmax(dsub(clo.z, ghi.z), dsub(glo.z, chi.z)), 0.0);
     return dadd(dadd(dmul(tx, tx), dmul(ty, ty)), dmul(tz, tz));
+}
+
+// Double-single split of an FP64 value: v ~ hi + lo with |v - hi - lo| <= 2^-48 |v|.
+__device__ __forceinline__ void ds_split(double v, float &hi, float &lo)
+{
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(dsub(v, (double)hi));
 }
 
 // ---- relaxed device-scope loads/stores for cross-block flags ---------------------
@@ -237,6 +247,7 @@ struct p3t_ctx {
     int n;
     int built;
     int built_precision;
+    int counts_valid;  // neighbour counts of the current tree already in nbr_count
     int pending_err;  // host-side latched error
     // device memory
     p3t::Meta *meta;

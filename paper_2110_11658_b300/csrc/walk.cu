@@ -16,10 +16,19 @@
 // Accepted cells (monopole + quadrupole, W = 1) and opened leaves (particle
 // terms weighted by W) are queued in shared memory and evaluated once `tile`
 // of them are queued: every lane holds TPL target particles in registers and
-// loops over the queue, read by broadcast.  Relative coordinates are formed
-// in FP64 (x_source - c_g, x_i - c_g, c_g the group-box centre) and rounded to
-// FP32; interactions run in FP32 and each tile's partial sum is added to the
-// running sum with Kahan compensation.  The FP64 form does everything in FP64.
+// loops over the queue, read by broadcast.  Relative coordinates x_source - c_g
+// and x_i - c_g (c_g the group-box centre) are formed from double-single
+// splits of the FP64 coordinates (hi + lo FP32 pairs made once per particle
+// and node in FP64 by the build), which gives the FP32 difference to within
+// 2^-23 of its magnitude without any FP64 instruction in the walk; interactions
+// run in FP32 and each tile's partial sum is added to the running sum with
+// Kahan compensation.  The FP64 form does everything in FP64.
+//
+// When 0 < r_list <= r_out the particle loop also counts, per target, the
+// neighbours of Sec. 2.3 (pairs in opened leaves with |r| < r_list; every pair
+// within r_out of a group particle is in an opened leaf), with the same FP32
+// band + exact FP64 decision as the neighbour kernels, so p3t_neighbours can
+// skip its counting pass.
 #include <cstdint>
 
 #include "p3t_internal.cuh"
@@ -47,6 +56,9 @@ struct WalkArgs {
     unsigned long long *n_cell, *n_part;
     long long *grp_cells, *grp_parts;
     unsigned int *ticket;
+    int32_t *nbr_count;          // fused neighbour count (original order) or null
+    double rl2_d;
+    float rl_f, rl2_f;
 };
 
 template <typename Real>
@@ -73,6 +85,19 @@ template <>
 __device__ __forceinline__ double rsqrt_<double>(double x)
 {
     return 1.0 / sqrt(x);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real sat_(Real x);  // clamp to [0, 1], NaN -> 0
+template <>
+__device__ __forceinline__ float sat_<float>(float x)
+{
+    return __saturatef(x);
+}
+template <>
+__device__ __forceinline__ double sat_<double>(double x)
+{
+    return x > 0.0 ? (x < 1.0 ? x : 1.0) : 0.0;
 }
 
 template <typename Real>
@@ -103,6 +128,7 @@ struct WarpSmem {
     int2 *lq;  // opened leaves {first, count}
     int *lqo;  // exclusive prefix of leaf counts
     R4 *pp;    // staged source particles {dx, dy, dz, m}
+    int *pj;   // their positions in key order
     static __host__ __device__ size_t bytes(int tile)
     {
         size_t cb = tile + 32;
@@ -110,7 +136,7 @@ struct WarpSmem {
         b += cb * (2 * sizeof(R4) + sizeof(R2));
         b += cb * 8 + (cb + 1) * 4;
         b = (b + 31) / 32 * 32;
-        b += 32 * sizeof(R4);
+        b += 32 * sizeof(R4) + 32 * 4;
         return (b + 127) / 128 * 128;
     }
     __device__ void carve(char *base, int tile)
@@ -133,6 +159,8 @@ struct WarpSmem {
         p += (cb + 1) * 4;
         p = base + ((p - base + 31) / 32 * 32);
         pp = (R4 *)p;
+        p += 32 * sizeof(R4);
+        pj = (int *)p;
     }
 };
 
@@ -176,7 +204,7 @@ __device__ __forceinline__ void eval_cells(const WarpSmem<Real> &W, int ncells, 
     using R4 = typename Vec4<Real>::T;
     using R2 = typename Vec4<Real>::T2;
     __syncwarp();
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < ncells; k++) {
         const R4 s = W.cpos[k];
         R4 qa;
@@ -187,25 +215,25 @@ __device__ __forceinline__ void eval_cells(const WarpSmem<Real> &W, int ncells, 
         }
 #pragma unroll
         for (int t = 0; t < TPL; t++) {
-            // r = x_i - com
+            // r = x_i - com;  a = r^-3 [(-M - 5/2 (r.Q.r)/r^4) r + (Q r)/r^2]
+            // (r^-3 applied last keeps every intermediate in FP32 range)
             const Real rx = px[t] - s.x, ry = py[t] - s.y, rz = pz[t] - s.z;
             const Real r2 = rx * rx + ry * ry + rz * rz;
             const Real ri = rsqrt_<Real>(r2);
-            const Real ri2 = ri * ri;
-            const Real ri3 = ri * ri2;
-            const Real mr3 = s.w * ri3;
+            const Real q = ri * ri;
+            const Real ri3 = ri * q;
             if (QUAD) {
-                const Real qx = qa.x * rx + qa.y * ry + qa.z * rz;
-                const Real qy = qa.y * rx + qa.w * ry + qb.x * rz;
-                const Real qz = qa.z * rx + qb.x * ry + qb.y * rz;
-                const Real rqr = rx * qx + ry * qy + rz * qz;
-                const Real ri5 = ri3 * ri2;
-                const Real cf = -mr3 - Real(2.5) * rqr * ri5 * ri2;
-                A.p[t][0] += cf * rx + ri5 * qx;
-                A.p[t][1] += cf * ry + ri5 * qy;
-                A.p[t][2] += cf * rz + ri5 * qz;
-                if (POT) A.p[t][3] -= s.w * ri + Real(0.5) * rqr * ri5;
+                const Real qx = (qa.x * rx + qa.y * ry + qa.z * rz) * q;
+                const Real qy = (qa.y * rx + qa.w * ry + qb.x * rz) * q;
+                const Real qz = (qa.z * rx + qb.x * ry + qb.y * rz) * q;
+                const Real rqr4 = (rx * qx + ry * qy + rz * qz) * q;  // r.Q.r / r^4
+                const Real cf = -s.w - Real(2.5) * rqr4;
+                A.p[t][0] += ri3 * (cf * rx + qx);
+                A.p[t][1] += ri3 * (cf * ry + qy);
+                A.p[t][2] += ri3 * (cf * rz + qz);
+                if (POT) A.p[t][3] -= ri * (s.w + Real(0.5) * rqr4);
             } else {
+                const Real mr3 = s.w * ri3;
                 A.p[t][0] -= mr3 * rx;
                 A.p[t][1] -= mr3 * ry;
                 A.p[t][2] -= mr3 * rz;
@@ -217,13 +245,36 @@ __device__ __forceinline__ void eval_cells(const WarpSmem<Real> &W, int ncells, 
     __syncwarp();
 }
 
-template <typename Real, int TPL, bool POT>
+// Group frame: c_g in FP64 and its double-single split relative to O.
+struct GroupFrame {
+    double cx, cy, cz;       // c_g
+    float hx, hy, hz;        // hi part of c_g - O
+    float lx, ly, lz;        // lo part
+};
+
+// x_j - c_g from the double-single split of x_j - O (mixed form)
+__device__ __forceinline__ float4 ds_rel(float4 h, float4 l, const GroupFrame &F)
+{
+    return make_float4((h.x - F.hx) + (l.x - F.lx), (h.y - F.hy) + (l.y - F.ly),
+                       (h.z - F.hz) + (l.z - F.lz), h.w);
+}
+
+// Per-target neighbour counting state (fused counting in the mixed form).
+template <int TPL>
+struct NbrCount {
+    int si[TPL];   // target positions in key order (-1: empty slot)
+    int cnt[TPL];
+    float lo, hi;  // r2 < lo: neighbour; r2 > hi: not; otherwise decide in FP64
+};
+
+template <typename Real, int TPL, bool POT, bool NBR>
 __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkArgs &P, int nleaves,
-                                           int nparts, double cgx, double cgy, double cgz,
-                                           const Real (&px)[TPL], const Real (&py)[TPL],
-                                           const Real (&pz)[TPL], Acc<Real, TPL> &A)
+                                           int nparts, const GroupFrame &F, const Real (&px)[TPL],
+                                           const Real (&py)[TPL], const Real (&pz)[TPL],
+                                           Acc<Real, TPL> &A, NbrCount<TPL> &NC)
 {
     using R4 = typename Vec4<Real>::T;
+    constexpr bool kMixed = sizeof(Real) == 4;
     const int lane = threadIdx.x & 31;
     __syncwarp();
     // exclusive prefix of the queued leaf counts
@@ -236,7 +287,8 @@ __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkAr
         carry += __shfl_sync(0xffffffffu, inc, 31);
     }
     __syncwarp();
-    const double4_32a *__restrict__ sp = P.T.sp;
+    const Real inv_dr = kMixed ? Real(P.inv_dr_f) : Real(P.inv_dr_d);
+    const Real rin_dr = kMixed ? Real(P.rin_dr_f) : Real(P.r_in_d * P.inv_dr_d);
     for (int c0 = 0; c0 < nparts; c0 += 32) {
         int pos = c0 + lane;
         if (pos < nparts) {
@@ -249,19 +301,23 @@ __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkAr
                     hi = mid;
             }
             int j = W.lq[lo].x + (pos - W.lqo[lo]);
-            double4_32a q = sp[j];
             R4 v;
-            v.x = to_real<Real>(dsub(q.x, cgx));
-            v.y = to_real<Real>(dsub(q.y, cgy));
-            v.z = to_real<Real>(dsub(q.z, cgz));
-            v.w = to_real<Real>(q.w);
+            if (kMixed) {
+                float4 r = ds_rel(P.T.ph[j], P.T.pl[j], F);
+                v.x = r.x, v.y = r.y, v.z = r.z, v.w = r.w;
+            } else {
+                double4_32a q = P.T.sp[j];
+                v.x = to_real<Real>(dsub(q.x, F.cx));
+                v.y = to_real<Real>(dsub(q.y, F.cy));
+                v.z = to_real<Real>(dsub(q.z, F.cz));
+                v.w = to_real<Real>(q.w);
+            }
             W.pp[lane] = v;
+            if (NBR) W.pj[lane] = j;
         }
         __syncwarp();
         const int ns = min(32, nparts - c0);
-        const Real inv_dr = sizeof(Real) == 4 ? Real(P.inv_dr_f) : Real(P.inv_dr_d);
-        const Real rin_dr = sizeof(Real) == 4 ? Real(P.rin_dr_f) : Real(P.r_in_d * P.inv_dr_d);
-#pragma unroll 2
+#pragma unroll 4
         for (int k = 0; k < ns; k++) {
             const R4 s = W.pp[k];
 #pragma unroll
@@ -271,9 +327,8 @@ __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkAr
                 const Real r2 = dx * dx + dy * dy + dz * dz;
                 const Real ri = rsqrt_<Real>(r2);
                 const Real r = r2 * ri;
-                Real x = r * inv_dr - rin_dr;
-                // clamp to [0, 1]; NaN (r2 = 0) maps to 0
-                x = x > Real(0) ? (x < Real(1) ? x : Real(1)) : Real(0);
+                // x = (r - r_in)/(r_out - r_in) clamped to [0, 1]; NaN (r2 = 0) maps to 0
+                const Real x = sat_(r * inv_dr - rin_dr);
                 Real w = (Real(-20) * x + Real(70)) * x + Real(-84);
                 w = w * x + Real(35);
                 const Real x2 = x * x;
@@ -284,6 +339,19 @@ __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkAr
                 A.p[t][1] += f * dy;
                 A.p[t][2] += f * dz;
                 if (POT) A.p[t][3] -= r2 > Real(0) ? s.w * ri : Real(0);
+                if (NBR) {
+                    // neighbour iff |x_j - x_i|^2 < r_list^2 in FP64; the pair with
+                    // itself is counted here (r2 = 0) and removed at the end
+                    const float r2f = (float)r2;
+                    if (r2f < NC.lo) {
+                        NC.cnt[t]++;
+                    } else if (r2f <= NC.hi) {  // inside the band: decide in FP64
+                        const int sj = W.pj[k];
+                        const double4_32a a = P.T.sp[NC.si[t] < 0 ? sj : NC.si[t]], b = P.T.sp[sj];
+                        const double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
+                        NC.cnt[t] += dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < P.rl2_d;
+                    }
+                }
             }
         }
         __syncwarp();
@@ -291,8 +359,8 @@ __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkAr
     A.fold();
 }
 
-template <typename Real, int TPL, bool POT, bool QUAD>
-__global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkArgs P)
+template <typename Real, int TPL, bool POT, bool QUAD, bool NBR>
+__global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel(WalkArgs P)
 {
     extern __shared__ __align__(16) char smem[];
     using R4 = typename Vec4<Real>::T;
@@ -313,7 +381,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkArgs P)
     // relative to O is within R and carries <= 2^-24 R rounding.  Outside a
     // safe range of scales the filter is off and every test is exact FP64.
     const float Rf = (float)meta->frame[3] * 1.0001f;
-    const bool filter_ok = Rf > 1e-12f && Rf < 1e12f && P.rout2_f > 1e-30f && P.rout2_f < 1e30f;
+    const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && P.rout2_f > 1e-20f && P.rout2_f < 1e30f;
     const float k_rel = 8.f * kU;
     const float k_abs = 8.f * kU * Rf;
     const float k_sq = 16.f * kU * kU * Rf * Rf;
@@ -325,26 +393,52 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkArgs P)
         if (g >= ng) break;
         const int2 gr = T.grp[g];
         const double4_32a glo = T.glo[g], ghi = T.ghi[g];
-        const double cgx = dmul(0.5, dadd(glo.x, ghi.x));
-        const double cgy = dmul(0.5, dadd(glo.y, ghi.y));
-        const double cgz = dmul(0.5, dadd(glo.z, ghi.z));
+        GroupFrame F;
+        F.cx = dmul(0.5, dadd(glo.x, ghi.x));
+        F.cy = dmul(0.5, dadd(glo.y, ghi.y));
+        F.cz = dmul(0.5, dadd(glo.z, ghi.z));
+        ds_split(dsub(F.cx, Ox), F.hx, F.lx);
+        ds_split(dsub(F.cy, Oy), F.hy, F.ly);
+        ds_split(dsub(F.cz, Oz), F.hz, F.lz);
         // group box relative to O for the FP32 filter
         const float glx = __double2float_rn(dsub(glo.x, Ox)), gly = __double2float_rn(dsub(glo.y, Oy)),
                     glz = __double2float_rn(dsub(glo.z, Oz));
         const float ghx = __double2float_rn(dsub(ghi.x, Ox)), ghy = __double2float_rn(dsub(ghi.y, Oy)),
                     ghz = __double2float_rn(dsub(ghi.z, Oz));
         Real px[TPL], py[TPL], pz[TPL];
+        NbrCount<TPL> NC;
+        float amax = 0.f;
 #pragma unroll
         for (int t = 0; t < TPL; t++) {
             int s = gr.x + lane + 32 * t;
+            NC.cnt[t] = 0;
+            NC.si[t] = -1;
             if (s < gr.x + gr.y) {
-                double4_32a q = T.sp[s];
-                px[t] = to_real<Real>(dsub(q.x, cgx));
-                py[t] = to_real<Real>(dsub(q.y, cgy));
-                pz[t] = to_real<Real>(dsub(q.z, cgz));
+                if (kMixed) {
+                    float4 r = ds_rel(T.ph[s], T.pl[s], F);
+                    px[t] = r.x, py[t] = r.y, pz[t] = r.z;
+                    amax = fmaxf(amax, fmaxf(fabsf(r.x), fmaxf(fabsf(r.y), fabsf(r.z))));
+                } else {
+                    double4_32a q = T.sp[s];
+                    px[t] = to_real<Real>(dsub(q.x, F.cx));
+                    py[t] = to_real<Real>(dsub(q.y, F.cy));
+                    pz[t] = to_real<Real>(dsub(q.z, F.cz));
+                }
+                NC.si[t] = s;
             } else {
                 px[t] = py[t] = pz[t] = Real(0);
             }
+        }
+        if (NBR) {
+            // band of the neighbour pair test: coordinates relative to c_g carry
+            // <= 2.01 u |x - c_g| + 8 u^2 R (double-single), targets within A of c_g
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            const float A = amax * 1.0001f;
+            const float band = kU * (24.f * P.rl2_f + 32.f * A * P.rl_f + 128.f * kU * Rf * P.rl_f) +
+                               64.f * kU * kU * (A + 2.f * P.rl_f) * (A + 2.f * P.rl_f);
+            NC.lo = filter_ok ? P.rl2_f - band : -1.f;        // filter off: every pair to FP64
+            NC.hi = filter_ok ? P.rl2_f + band : INFINITY;
         }
         Acc<Real, TPL> A;
         A.zero_all();
@@ -384,9 +478,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkArgs P)
             bool open = false, is_leaf = false;
             int cinfo = 0, ccount = 0;
             bool fb = false;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);  // node record, reused when staging
             if (node >= 0) {
                 if (kMixed && filter_ok) {
-                    const float4 a = T.wA[node], b = T.wB[node], c = T.wC[node];
+                    a = T.wA[node];
+                    const float4 b = T.wB[node], c = T.wC[node];
                     cinfo = __float_as_int(b.w);
                     ccount = __float_as_int(c.w);
                     // point-box: COM against the group box
@@ -455,12 +551,20 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkArgs P)
             const unsigned am = __ballot_sync(0xffffffffu, accept);
             if (accept) {
                 const int pos = cb + __popc(am & lt);
-                const double4_32a cm = T.comM[node];
                 R4 v;
-                v.x = to_real<Real>(dsub(cm.x, cgx));
-                v.y = to_real<Real>(dsub(cm.y, cgy));
-                v.z = to_real<Real>(dsub(cm.z, cgz));
-                v.w = to_real<Real>(cm.w);
+                if (kMixed) {
+                    const float4 d = T.wD[node];
+                    if (!filter_ok) a = T.wA[node];
+                    const float4 r = ds_rel(a, d, F);
+                    v.x = r.x, v.y = r.y, v.z = r.z;
+                    v.w = d.w;  // M
+                } else {
+                    const double4_32a cm = T.comM[node];
+                    v.x = to_real<Real>(dsub(cm.x, F.cx));
+                    v.y = to_real<Real>(dsub(cm.y, F.cy));
+                    v.z = to_real<Real>(dsub(cm.z, F.cz));
+                    v.w = to_real<Real>(cm.w);
+                }
                 W.cpos[pos] = v;
                 if (QUAD) {
                     R4 qa;
@@ -496,12 +600,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkArgs P)
                 cb = 0;
             }
             if (lqp >= tile) {
-                eval_parts<Real, TPL, POT>(W, P, lqn, lqp, cgx, cgy, cgz, px, py, pz, A);
+                eval_parts<Real, TPL, POT, NBR>(W, P, lqn, lqp, F, px, py, pz, A, NC);
                 lqn = lqp = 0;
             }
         }
         if (cb > 0) eval_cells<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
-        if (lqp > 0) eval_parts<Real, TPL, POT>(W, P, lqn, lqp, cgx, cgy, cgz, px, py, pz, A);
+        if (lqp > 0) eval_parts<Real, TPL, POT, NBR>(W, P, lqn, lqp, F, px, py, pz, A, NC);
 
         // ---- results, scattered to the original order
 #pragma unroll
@@ -520,6 +624,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkArgs P)
                     ((double *)P.az)[o] = (double)A.s[t][2];
                     if (POT) P.pot[o] = (double)A.s[t][3];
                 }
+                if (NBR) P.nbr_count[o] = NC.cnt[t] - 1;  // minus the pair with itself
             }
         }
         if (lane == 0) {
@@ -536,10 +641,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(WalkArgs P)
     }
 }
 
-template <typename Real, int TPL, bool POT, bool QUAD>
+template <typename Real, int TPL, bool POT, bool QUAD, bool NBR>
 static int launch_walk(p3t_ctx *c, const WalkArgs &a)
 {
-    auto kern = walk_kernel<Real, TPL, POT, QUAD>;
+    auto kern = walk_kernel<Real, TPL, POT, QUAD, NBR>;
     const size_t smem = kWalkWarps * WarpSmem<Real>::bytes(a.tile);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
@@ -553,21 +658,23 @@ static int launch_walk(p3t_ctx *c, const WalkArgs &a)
     return check_launch(c);
 }
 
-template <typename Real, int TPL>
+template <typename Real, int TPL, bool NBR>
 static int dispatch_pq(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
 {
     if (pot)
-        return quad ? launch_walk<Real, TPL, true, true>(c, a) : launch_walk<Real, TPL, true, false>(c, a);
-    return quad ? launch_walk<Real, TPL, false, true>(c, a) : launch_walk<Real, TPL, false, false>(c, a);
+        return quad ? launch_walk<Real, TPL, true, true, NBR>(c, a)
+                    : launch_walk<Real, TPL, true, false, NBR>(c, a);
+    return quad ? launch_walk<Real, TPL, false, true, NBR>(c, a)
+                : launch_walk<Real, TPL, false, false, NBR>(c, a);
 }
 
-template <typename Real>
+template <typename Real, bool NBR>
 static int dispatch_tpl(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
 {
     const int G = c->prm.group_size;
-    if (G <= 32) return dispatch_pq<Real, 1>(c, a, pot, quad);
-    if (G <= 64) return dispatch_pq<Real, 2>(c, a, pot, quad);
-    return dispatch_pq<Real, 4>(c, a, pot, quad);
+    if (G <= 32) return dispatch_pq<Real, 1, NBR>(c, a, pot, quad);
+    if (G <= 64) return dispatch_pq<Real, 2, NBR>(c, a, pot, quad);
+    return dispatch_pq<Real, 4, NBR>(c, a, pot, quad);
 }
 
 int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc, int64_t *np)
@@ -590,12 +697,25 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     a.grp_cells = c->debug ? (long long *)c->grp_cells : nullptr;
     a.grp_parts = c->debug ? (long long *)c->grp_parts : nullptr;
     a.ticket = &c->meta->tickets[22];
+    a.rl2_d = P.r_list * P.r_list;
+    a.rl_f = (float)P.r_list;
+    a.rl2_f = (float)a.rl2_d;
+    // count neighbours in the walk when every neighbour pair lies in an opened leaf
+    const bool fuse_nbr = c->built_precision == P3T_FP32_MIXED && P.r_list > 0.0 && P.r_list <= P.r_out;
+    a.nbr_count = fuse_nbr ? c->nbr_count : nullptr;
     if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
         return P3T_ERR_CUDA;
     const bool quad = P.quadrupole != 0;
     const bool want_pot = pot != nullptr;
-    if (c->built_precision == P3T_FP64) return dispatch_tpl<double>(c, a, want_pot, quad);
-    return dispatch_tpl<float>(c, a, want_pot, quad);
+    int e;
+    if (c->built_precision == P3T_FP64)
+        e = dispatch_tpl<double, false>(c, a, want_pot, quad);
+    else if (fuse_nbr)
+        e = dispatch_tpl<float, true>(c, a, want_pot, quad);
+    else
+        e = dispatch_tpl<float, false>(c, a, want_pot, quad);
+    if (e == P3T_OK && fuse_nbr) c->counts_valid = 1;
+    return e;
 }
 
 }  // namespace p3t

@@ -95,7 +95,7 @@ def test_neighbour_radius_independent_of_r_out(r_list):
 
 def test_quadrupole_off_matches_oracle_monopole():
     c = synth.plummer(4096, 3)
-    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, quadrupole=0, precision=FP64)
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, quadrupole=0, precision=FP64, group_size=64)
     g = run_gpu(c, prm, nbr=False)
     f = _oracle(c, 0.5, 0.05, 16, 64).far(0.005, quadrupole=False)
     assert rel_err(g["a"], f["a"]).max() < 1e-10
@@ -123,9 +123,10 @@ def test_edge_cases_tiny_and_degenerate():
     cases.append(p)
     for c in cases:
         for precision in (FP64, MIXED):
-            prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, precision=precision)
+            prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, precision=precision,
+                             group_size=32)
             g = run_gpu(c, prm)
-            t = _oracle(c, 0.5, 0.05, 16, 64)
+            t = _oracle(c, 0.5, 0.05, 16, 32)
             ref = t.export()
             assert_tree_equal(g["tree"], ref, fp64_moments=precision == FP64)
             f = t.far(0.005)
@@ -144,3 +145,22 @@ def test_repeatable_bitwise():
     b = run_gpu(c, prm, nbr=True)
     assert np.array_equal(a["a"], b["a"]) and np.array_equal(a["pot"], b["pot"])
     assert np.array_equal(a["idx"], b["idx"])
+
+
+@pytest.mark.parametrize("scale", [1e-8, 1e4])
+def test_extreme_scales_switch_filters_off_or_on(scale):
+    # at tiny scales the FP32 filters are switched off and every opening and
+    # neighbour decision is taken in FP64; lists and counts must still match
+    c = synth.plummer(3000, 31, masses="kroupa")
+    c.x, c.y, c.z = c.x * scale, c.y * scale, c.z * scale
+    r_out = 0.05 * scale
+    prm = p3t.Params(theta=0.5, r_in=0.1 * r_out, r_out=r_out, r_list=0.8 * r_out, group_size=32)
+    g = run_gpu(c, prm)
+    t = _oracle(c, 0.5, r_out, 16, 32)
+    assert_tree_equal(g["tree"], t.export(), fp64_moments=False)
+    f = t.far(0.1 * r_out)
+    assert np.array_equal(g["g_cells"], f["n_cell"]) and np.array_equal(g["g_parts"], f["n_part"])
+    e = rel_err(g["a"], f["a"])
+    assert np.median(e) <= 1e-5 and np.percentile(e, 99) <= 1e-4
+    o2, i2 = oracle.neighbours_brute(c.x, c.y, c.z, 0.8 * r_out)
+    assert np.array_equal(g["offs"], o2) and np.array_equal(g["idx"], i2)
