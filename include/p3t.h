@@ -178,6 +178,30 @@ int p3t_set_debug(p3t_ctx *c, int on);
 /* Static description of an error code. */
 const char *p3t_error_string(int code);
 
+/* Morton order of n particles WITHOUT ANY DEVICE ALLOCATION.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc where they need it -- a host whose own memory pool already owns
+ * the GPU's memory and hands out only buffers it allocated, or a loop that
+ * must not allocate once running because an allocation can synchronise the
+ * device and stall other streams.
+ * It computes what p3t_build_tree computes first: the bounding cube, the
+ * 63-bit Morton keys and the stable sort by (key, original index).  Outputs:
+ * keys (device uint64[n], ascending) and perm (device int32[n], sorted
+ * position -> original index); inputs x, y, z, m are device double[n] as in
+ * p3t_build_tree.  All scratch memory lives in one static device array of the
+ * library sized for P3T_NOALLOC_MAX_N particles (about 0.8 MB, held by every
+ * GPU that loads the library until the process exits); n above that returns
+ * P3T_ERR_CAPACITY, n <= 0 or a null pointer P3T_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address on the
+ * current device; make that first call before any stream capture.  The call
+ * runs on `cuda_stream`, synchronises it, and returns P3T_ERR_INVALID_INPUT
+ * for non-finite or negative inputs as p3t_build_tree would.  Every call
+ * shares the one array: calls that overlap on a GPU (other streams or host
+ * threads at the same time) race on it. */
+#define P3T_NOALLOC_MAX_N 65536
+int p3t_morton_order_noalloc(int64_t n, const double *x, const double *y, const double *z,
+                             const double *m, uint64_t *keys, int32_t *perm, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,8 +37,9 @@ EXPORTED = [
     "p3t_default_params", "p3t_create", "p3t_destroy", "p3t_set_params", "p3t_build_tree",
     "p3t_far_force", "p3t_neighbours", "p3t_neighbours_async", "p3t_kick", "p3t_drift",
     "p3t_step_host", "p3t_status", "p3t_tree_info", "p3t_export_tree", "p3t_group_counts",
-    "p3t_set_debug", "p3t_error_string",
+    "p3t_set_debug", "p3t_error_string", "p3t_morton_order_noalloc",
 ]
+P3T_NOALLOC_MAX_N = 65536
 
 
 class p3t_params(C.Structure):
@@ -80,6 +81,7 @@ _sig = {
     "p3t_group_counts": [_vp, _vp, _vp],
     "p3t_set_debug": [_vp, C.c_int],
     "p3t_error_string": [C.c_int],
+    "p3t_morton_order_noalloc": [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
