@@ -419,8 +419,11 @@ def run_b300(args, rank, local, world):
     return line
 
 
-# kernels launched by one step (build 57, far force 1, neighbours 4, kick 1, drift 1)
-KERNELS_PER_STEP = 4 + 8 * 3 + 1 + 1 + 21 + 1 + 3 + 1 + 1 + 4 + 1 + 1
+# kernels launched by one step: build = init, bbox, cube, keys (4) + radix sort 8 x
+# (histogram, scan, scatter) + gather + topology root, 21 levels, finish + group scan,
+# first, finish + moments leaves and 21 levels; far force 1 (it also counts the
+# neighbours); neighbours = offsets scan, fill, row sort; kick 1; drift 1
+KERNELS_PER_STEP = (4 + 8 * 3 + 1 + (1 + 21 + 1) + 3 + (1 + 21)) + 1 + 3 + 1 + 1
 
 
 def run_reference(args, rank, world):

@@ -48,6 +48,7 @@ __global__ void init_meta_kernel(Meta *m)
     if (t == 0) {
         m->n_nodes = 0;
         m->n_groups = 0;
+        m->n_leaves = 0;
         m->depth = 0;
         m->fallback_tests = 0;
     }
@@ -233,11 +234,13 @@ __global__ void __launch_bounds__(kBuildThreads)
     gather_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
                   const double *__restrict__ z, const double *__restrict__ m,
                   const int32_t *__restrict__ perm, const Meta *__restrict__ meta,
-                  double4_32a *__restrict__ sp, float4 *__restrict__ ph, float4 *__restrict__ pl)
+                  double4_32a *__restrict__ sp, float4 *__restrict__ ph, float4 *__restrict__ pl,
+                  int32_t *__restrict__ inv)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int i = perm[s];
+    inv[i] = s;
     double px = x[i], py = y[i], pz = z[i], pm = m[i];
     sp[s] = make_double4_32a(px, py, pz, pm);
     float hx, hy, hz, lx, ly, lz;
@@ -270,6 +273,10 @@ __global__ void topo_root_kernel(Tree T, int n, int leaf_cap, int G)
     T.level[0] = 0;
     T.parent[0] = -1;
     T.ready[0] = 0;
+    if (n <= leaf_cap) {
+        T.leaves[0] = 0;
+        T.meta->n_leaves = 1;
+    }
     T.meta->level_start[0] = 0;
     T.meta->level_count[0] = 1;
     flag_groups(T.gflag, 0, n, true, n <= leaf_cap, G);
@@ -344,6 +351,7 @@ __global__ void __launch_bounds__(kBuildThreads)
                         T.parent[c] = node;
                         T.ready[c] = 0;
                         bool leaf = cnt <= leaf_cap || l + 1 >= kLevels;
+                        if (leaf) T.leaves[atomicAdd(&M->n_leaves, 1)] = c;
                         flag_groups(T.gflag, bnd[o], cnt, big, leaf, G);
                     }
                 }
@@ -381,6 +389,40 @@ __global__ void __launch_bounds__(kBuildThreads)
 
 __device__ __forceinline__ double upd_min(double lo, double p) { return p < lo ? p : lo; }
 __device__ __forceinline__ double upd_max(double hi, double p) { return p > hi ? p : hi; }
+
+// Exact box bounds on the integer pipes: min/max of the order-preserving
+// encodings (no FP64 instruction).  Equal to the FP64 min/max except that -0
+// orders below +0, which changes no distance, extent or centre computed later.
+struct EncBox {
+    unsigned long long lo[3], hi[3];
+    __device__ void reset()
+    {
+        for (int d = 0; d < 3; d++) lo[d] = ~0ULL, hi[d] = 0ULL;
+    }
+    __device__ void add(double x, double y, double z)
+    {
+        unsigned long long e[3] = {enc_double(x), enc_double(y), enc_double(z)};
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            lo[d] = e[d] < lo[d] ? e[d] : lo[d];
+            hi[d] = e[d] > hi[d] ? e[d] : hi[d];
+        }
+    }
+    __device__ void add_box(const double4_32a &l, const double4_32a &h)
+    {
+        unsigned long long a[3] = {enc_double(l.x), enc_double(l.y), enc_double(l.z)};
+        unsigned long long b[3] = {enc_double(h.x), enc_double(h.y), enc_double(h.z)};
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            lo[d] = a[d] < lo[d] ? a[d] : lo[d];
+            hi[d] = b[d] > hi[d] ? b[d] : hi[d];
+        }
+    }
+    __device__ void get(double *l, double *h) const
+    {
+        for (int d = 0; d < 3; d++) l[d] = dec_double(lo[d]), h[d] = dec_double(hi[d]);
+    }
+};
 
 // one warp per group: count and tight box (exact min/max, order-free)
 __global__ void __launch_bounds__(kBuildThreads) group_finish_kernel(Tree T, int n)
@@ -456,31 +498,33 @@ __device__ void write_node(Tree &T, int k, double M, const double com[3], const 
     ds_split(dsub(com[0], O[0]), chx, clx);
     ds_split(dsub(com[1], O[1]), chy, cly);
     ds_split(dsub(com[2], O[2]), chz, clz);
-    T.wA[k] = make_float4(chx, chy, chz, __double2float_rn(ro2));
-    T.wD[k] = make_float4(clx, cly, clz, __double2float_rn(M));
-    T.wB[k] = make_float4(__double2float_rn(dsub(lo[0], O[0])), __double2float_rn(dsub(lo[1], O[1])),
-                          __double2float_rn(dsub(lo[2], O[2])),
-                          __int_as_float(leaf ? -1 - tp.x : tp.z));
-    T.wC[k] = make_float4(__double2float_rn(dsub(hi[0], O[0])), __double2float_rn(dsub(hi[1], O[1])),
-                          __double2float_rn(dsub(hi[2], O[2])), __int_as_float(leaf ? tp.y : tp.w));
+    float4 *w = T.wn + (size_t)kWalkRecord * k;
+    w[0] = make_float4(chx, chy, chz, __double2float_rn(ro2));
+    w[1] = make_float4(__double2float_rn(dsub(lo[0], O[0])), __double2float_rn(dsub(lo[1], O[1])),
+                       __double2float_rn(dsub(lo[2], O[2])), __int_as_float(leaf ? -1 - tp.x : tp.z));
+    w[2] = make_float4(__double2float_rn(dsub(hi[0], O[0])), __double2float_rn(dsub(hi[1], O[1])),
+                       __double2float_rn(dsub(hi[2], O[2])), __int_as_float(leaf ? tp.y : tp.w));
+    w[3] = make_float4(clx, cly, clz, __double2float_rn(M));
+    w[4] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
+    w[5] = make_float4((float)q[4], (float)q[5], 0.f, 0.f);
 }
 
 template <bool Q64>
 __device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
 {
     const int b = tp.x, e = tp.x + tp.y;
-    double M = 0.0, S[3] = {0, 0, 0}, lo[3] = {INFINITY, INFINITY, INFINITY},
-           hi[3] = {-INFINITY, -INFINITY, -INFINITY}, com[3];
+    double M = 0.0, S[3] = {0, 0, 0}, lo[3], hi[3], com[3];
+    EncBox box;
+    box.reset();
     for (int i = b; i < e; i++) {
         double4_32a p = T.sp[i];
         M = dadd(M, p.w);
         S[0] = dadd(S[0], dmul(p.w, p.x));
         S[1] = dadd(S[1], dmul(p.w, p.y));
         S[2] = dadd(S[2], dmul(p.w, p.z));
-        lo[0] = upd_min(lo[0], p.x), hi[0] = upd_max(hi[0], p.x);
-        lo[1] = upd_min(lo[1], p.y), hi[1] = upd_max(hi[1], p.y);
-        lo[2] = upd_min(lo[2], p.z), hi[2] = upd_max(hi[2], p.z);
+        box.add(p.x, p.y, p.z);
     }
+    box.get(lo, hi);
     for (int d = 0; d < 3; d++) com[d] = M > 0.0 ? ddiv(S[d], M) : dmul(0.5, dadd(lo[d], hi[d]));
     double q[6];
     if (Q64) {
@@ -499,14 +543,19 @@ __device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
         }
         for (int a = 0; a < 6; a++) q[a] = Q[a];
     } else {
-        // FP32 quadrupole on FP64-subtracted offsets
+        // FP32 quadrupole on offsets from the double-single splits (x - O) - (com - O)
+        const double *O = T.meta->frame;
+        float chx, chy, chz, clx, cly, clz;
+        ds_split(dsub(com[0], O[0]), chx, clx);
+        ds_split(dsub(com[1], O[1]), chy, cly);
+        ds_split(dsub(com[2], O[2]), chz, clz);
         float Q[6] = {0, 0, 0, 0, 0, 0};
         for (int i = b; i < e; i++) {
-            double4_32a p = T.sp[i];
-            float m = (float)p.w;
-            float dx = __double2float_rn(dsub(p.x, com[0]));
-            float dy = __double2float_rn(dsub(p.y, com[1]));
-            float dz = __double2float_rn(dsub(p.z, com[2]));
+            const float4 h = T.ph[i], l = T.pl[i];
+            const float m = h.w;
+            const float dx = (h.x - chx) + (l.x - clx);
+            const float dy = (h.y - chy) + (l.y - cly);
+            const float dz = (h.z - chz) + (l.z - clz);
             float r2 = dx * dx + dy * dy + dz * dz;
             Q[0] += m * (3.f * dx * dx - r2);
             Q[1] += m * (3.f * dx * dy);
@@ -532,8 +581,9 @@ template <bool Q64>
 __device__ void internal_moments(Tree &T, int k, int4 tp, double theta)
 {
     const int c0 = tp.z, c1 = tp.z + tp.w;
-    double M = 0.0, S[3] = {0, 0, 0}, lo[3] = {INFINITY, INFINITY, INFINITY},
-           hi[3] = {-INFINITY, -INFINITY, -INFINITY}, com[3];
+    double M = 0.0, S[3] = {0, 0, 0}, lo[3], hi[3], com[3];
+    EncBox box;
+    box.reset();
     for (int c = c0; c < c1; c++) {
         double4_32a cm = ldcg_d4(&T.comM[c]);
         double4_32a cl = ldcg_d4(&T.lo[c]);
@@ -542,10 +592,9 @@ __device__ void internal_moments(Tree &T, int k, int4 tp, double theta)
         S[0] = dadd(S[0], dmul(cm.w, cm.x));
         S[1] = dadd(S[1], dmul(cm.w, cm.y));
         S[2] = dadd(S[2], dmul(cm.w, cm.z));
-        lo[0] = upd_min(lo[0], cl.x), hi[0] = upd_max(hi[0], ch.x);
-        lo[1] = upd_min(lo[1], cl.y), hi[1] = upd_max(hi[1], ch.y);
-        lo[2] = upd_min(lo[2], cl.z), hi[2] = upd_max(hi[2], ch.z);
+        box.add_box(cl, ch);
     }
+    box.get(lo, hi);
     for (int d = 0; d < 3; d++) com[d] = M > 0.0 ? ddiv(S[d], M) : dmul(0.5, dadd(lo[d], hi[d]));
     double q[6];
     if (Q64) {
@@ -586,29 +635,26 @@ __device__ void internal_moments(Tree &T, int k, int4 tp, double theta)
     write_node<Q64>(T, k, M, com, lo, hi, q, theta, tp);
 }
 
+// leaves first (one thread per leaf), then the internal nodes level by level,
+// deepest first, each from its children in octant order; every pass keeps
+// whole warps busy (FP64 instructions cost the same for one lane as for 32)
 template <bool Q64>
-__global__ void __launch_bounds__(kBuildThreads) moments_kernel(Tree T, double theta)
+__global__ void __launch_bounds__(kBuildThreads) moments_leaf_kernel(Tree T, double theta)
 {
-    const int nn = T.meta->n_nodes;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
-        int4 tp = T.topo[k];
-        if (tp.z >= 0) continue;  // internal nodes are finished by their last child
-        leaf_moments<Q64>(T, k, tp, theta);
-        int p = T.parent[k];
-        int hops = 0;
-        while (p >= 0) {
-            if (++hops > kLevels + 1 || p >= nn) {  // a valid chain has at most 21 parents
-                latch_error(T.meta, P3T_ERR_INTERNAL);
-                break;
-            }
-            __threadfence();
-            int4 pt = T.topo[p];
-            int old = atomicAdd(&T.ready[p], 1);
-            if (old != pt.w - 1) break;
-            __threadfence();
-            internal_moments<Q64>(T, p, pt, theta);
-            p = T.parent[p];
-        }
+    const int nl = T.meta->n_leaves;
+    for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < nl; li += gridDim.x * blockDim.x) {
+        const int k = T.leaves[li];
+        leaf_moments<Q64>(T, k, T.topo[k], theta);
+    }
+}
+
+template <bool Q64>
+__global__ void __launch_bounds__(kBuildThreads) moments_level_kernel(Tree T, int l, double theta)
+{
+    const int b = T.meta->level_start[l], e = b + T.meta->level_count[l];
+    for (int k = b + blockIdx.x * blockDim.x + threadIdx.x; k < e; k += gridDim.x * blockDim.x) {
+        const int4 tp = T.topo[k];
+        if (tp.z >= 0) internal_moments<Q64>(T, k, tp, theta);
     }
 }
 
@@ -647,7 +693,8 @@ int build_tree(p3t_ctx *c, int n, const double *x, const double *y, const double
     }
     T.keys = c->keys_buf[0];
     T.perm = c->perm_buf[0];
-    gather_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, m, T.perm, M, T.sp, T.ph, T.pl);
+    gather_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, m, T.perm, M, T.sp, T.ph, T.pl,
+                                                    T.inv);
 
     // topology, level by level
     unsigned long long *topo_status = c->scan_status + (n / 256 + 64 + 256 * nb / 256);
@@ -671,11 +718,18 @@ int build_tree(p3t_ctx *c, int n, const double *x, const double *y, const double
     group_first_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, T.gflag, T.gidx, T.grp);
     group_finish_kernel<<<persistent, kBuildThreads, 0, s>>>(T, n);
 
-    // moments
-    if (P.precision == P3T_FP64)
-        moments_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
+    // moments: leaves, then levels 20 .. 0 (a level without internal nodes exits at once)
+    const bool q64 = P.precision == P3T_FP64;
+    if (q64)
+        moments_leaf_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
     else
-        moments_kernel<false><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
+        moments_leaf_kernel<false><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
+    for (int l = kLevels - 1; l >= 0; l--) {
+        if (q64)
+            moments_level_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, l, P.theta);
+        else
+            moments_level_kernel<false><<<persistent, kBuildThreads, 0, s>>>(T, l, P.theta);
+    }
     return check_launch(c);
 }
 

@@ -54,6 +54,8 @@ int ensure_capacity(p3t_ctx *c, long long n)
         {(void **)&T.pl, 16 * (size_t)N},
         {(void **)&T.gflag, (size_t)N + 16},
         {(void **)&T.gidx, 4 * (size_t)N},
+        {(void **)&T.leaves, 4 * (size_t)N},
+        {(void **)&T.inv, 4 * (size_t)N},
         {(void **)&T.grp, 8 * (size_t)N},
         {(void **)&T.glo, 32 * (size_t)N},
         {(void **)&T.ghi, 32 * (size_t)N},
@@ -71,10 +73,7 @@ int ensure_capacity(p3t_ctx *c, long long n)
         {(void **)&T.hi, 32 * (size_t)NN},
         {(void **)&T.q32, 24 * (size_t)NN},
         {(void **)&T.q64, 48 * (size_t)NN},
-        {(void **)&T.wA, 16 * (size_t)NN},
-        {(void **)&T.wB, 16 * (size_t)NN},
-        {(void **)&T.wC, 16 * (size_t)NN},
-        {(void **)&T.wD, 16 * (size_t)NN},
+        {(void **)&T.wn, 16 * (size_t)kWalkRecord * (size_t)NN},
     };
     size_t total = 0;
     for (auto &it : items) total += align_up(it.bytes, 256);

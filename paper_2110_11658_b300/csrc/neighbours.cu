@@ -39,11 +39,11 @@ struct NbrArgs {
 
 struct NbrSmem {
     int stk[kNbrStack];
-    int batch[32];
     int2 lq[kNbrLeafQ];
     int lqo[kNbrLeafQ + 1];
     float4 pp[32];
     int pj[32];
+    int po[32];
 };
 
 template <int TPL, bool FILL>
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         const bool pair_filter = filter_ok && A < 1e12f;
 
         int sp = 1;
-        if (lane == 0) W.stk[0] = (0 << 3) | 0;
+        if (lane == 0) W.stk[0] = pack_range(0, 1);
         __syncwarp();
         int lqn = 0, lqp = 0;
         int iters = 0;  // a valid walk pops every node at most once
@@ -128,28 +128,12 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 break;
             }
             if (sp > 0) {
-                int e = lane < sp ? W.stk[sp - 1 - lane] : 0;
-                int c = lane < sp ? (e & 7) + 1 : 0;
-                int incl = warp_incl_scan(c);
-                int excl = incl - c;
-                int total = __shfl_sync(0xffffffffu, incl, 31);
-                int take = total < 32 ? total : 32;
-                unsigned full = __ballot_sync(0xffffffffu, lane < sp && incl <= take);
-                __syncwarp();
-                if (lane < sp && excl < take) {
-                    int first = e >> 3;
-                    int mine = c < take - excl ? c : take - excl;
-                    for (int j = 0; j < mine; j++) W.batch[excl + j] = first + j;
-                    if (mine < c) W.stk[sp - 1 - lane] = ((first + mine) << 3) | (c - mine - 1);
-                }
-                __syncwarp();
-                sp -= __popc(full);
-                const int node = lane < take ? W.batch[lane] : -1;
-                __syncwarp();
+                const int node = pop_batch(W.stk, sp);
                 bool open = false, is_leaf = false;
                 int cinfo = 0, ccount = 0;
                 if (node >= 0) {
-                    const float4 b = T.wB[node], cc = T.wC[node];
+                    const float4 *rec = T.wn + (size_t)kWalkRecord * node;
+                    const float4 b = rec[1], cc = rec[2];
                     cinfo = __float_as_int(b.w);
                     ccount = __float_as_int(cc.w);
                     is_leaf = cinfo < 0;
@@ -183,15 +167,12 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                     sp = 0;
                     break;
                 }
-                if (open_int) W.stk[sp + __popc(pm >> lane >> 1)] = (cinfo << 3) | (ccount - 1);
+                if (open_int) W.stk[sp + __popc(pm >> lane >> 1)] = pack_range(cinfo, ccount);
                 sp += npush;
                 const unsigned lm = __ballot_sync(0xffffffffu, open_leaf);
-                int lc = open_leaf ? ccount : 0;
                 if (open_leaf) W.lq[lqn + __popc(lm & lt)] = make_int2(-1 - cinfo, ccount);
                 lqn += __popc(lm);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) lc += __shfl_xor_sync(0xffffffffu, lc, o);
-                lqp += lc;
+                lqp += (int)__reduce_add_sync(0xffffffffu, open_leaf ? (unsigned)ccount : 0u);
                 if (lqp < 64 && sp > 0) continue;
             }
             if (lqp == 0) break;
@@ -224,6 +205,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                     W.pp[lane] = make_float4((h.x - fhx) + (l.x - flx), (h.y - fhy) + (l.y - fly),
                                              (h.z - fhz) + (l.z - flz), 0.f);
                     W.pj[lane] = j;
+                    if (FILL) W.po[lane] = T.perm[j];
                 }
                 __syncwarp();
                 const int ns = min(32, lqp - c0);
@@ -244,7 +226,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                             in = d2 < P.rl2_d;
                         }
                         if (in) {
-                            if (FILL) P.idx[base[t] + cnt[t]] = T.perm[j];
+                            if (FILL) P.idx[base[t] + cnt[t]] = W.po[k];
                             cnt[t]++;
                         }
                     }

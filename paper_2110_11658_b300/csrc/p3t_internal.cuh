@@ -7,10 +7,11 @@
 //                             level i32, parent i32,
 //                             comM double4_32a = {com.xyz, M}, lo double4_32a = {lo.xyz, r_open^2},
 //                             hi double4_32a = {hi.xyz, 0}, Q (FP64: double[6] | FP32: float[6]),
-//                             walk filter float4 wA = {com-O, r_open^2}, wB = {lo-O, child/leaf},
-//                             wC = {hi-O, nchild/count}, wD = {lo part of com-O, M}
-//                             (O = centre of the bounding cube; wA.xyz + wD.xyz is
-//                             the double-single split of com - O)
+//                             walk record wn float4[6] per node (96 bytes, one load batch):
+//                               [0] {hi part of com-O, r_open^2}  [1] {lo-O, child | -1-first}
+//                               [2] {hi-O, nchild | count}        [3] {lo part of com-O, M}
+//                               [4] {Qxx, Qxy, Qxz, Qyy}          [5] {Qyz, Qzz, 0, 0}
+//                             (O = centre of the bounding cube; FP32 values)
 //   groups, particle order:   grp int2 = {first, count}, glo/ghi double4_32a (tight box)
 #pragma once
 
@@ -24,6 +25,7 @@ namespace p3t {
 constexpr int kLevels = 21;          // key bits per axis = tree depth
 constexpr int kMaxLevelSlots = 24;   // per-level bookkeeping arrays
 constexpr long long kSpinLimit = 1LL << 24;  // bounded waits: ~1 s with backoff
+constexpr int kWalkRecord = 6;               // float4 per node in Tree::wn
 
 // ---- device metadata block (one per context) -------------------------------
 struct Meta {
@@ -31,6 +33,7 @@ struct Meta {
     int n_nodes;
     int n_groups;
     int depth;
+    int n_leaves;
     int level_start[kMaxLevelSlots];
     int level_count[kMaxLevelSlots];
     unsigned int tickets[32];      // work-distribution counters (reset per launch)
@@ -58,11 +61,13 @@ struct Tree {
     double4_32a *hi;
     double *q64;   // 6 per node (FP64 form)
     float *q32;    // 6 per node (mixed form)
-    float4 *wA, *wB, *wC, *wD;
+    float4 *wn;    // kWalkRecord float4 per node
     int2 *grp;
     double4_32a *glo, *ghi;
     unsigned char *gflag;  // group-start flags, particle order
     int32_t *gidx;         // scan of gflag
+    int32_t *leaves;       // leaf node indices, in creation order (moments work list)
+    int32_t *inv;          // original index -> position in key order
     Meta *meta;
 };
 
@@ -119,6 +124,39 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+// ---- warp traversal stack of node ranges -------------------------------------------
+// Entries pack (first node << 3) | (count - 1), count 1..8 (the children of one
+// node).  pop_batch takes up to 32 nodes from the top entries, one per lane,
+// and returns this lane's node (-1 if none); a partly taken entry is advanced
+// in place.  The prefix sum of the entry sizes is formed from four ballots of
+// the size bits, and the lane -> entry map from the mask of entry starts.
+__device__ __forceinline__ int pack_range(int first, int count) { return (first << 3) | (count - 1); }
+
+__device__ __forceinline__ int pop_batch(int *stk, int &sp)
+{
+    const unsigned full_mask = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int e = lane < sp ? stk[sp - 1 - lane] : 0;
+    const int cnt = lane < sp ? (e & 7) + 1 : 0;
+    const unsigned b0 = __ballot_sync(full_mask, cnt & 1), b1 = __ballot_sync(full_mask, cnt & 2),
+                   b2 = __ballot_sync(full_mask, cnt & 4), b3 = __ballot_sync(full_mask, cnt & 8);
+    const int excl = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) + 8 * __popc(b3 & lt);
+    const int total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
+    const int take = total < 32 ? total : 32;
+    const bool starts = cnt > 0 && excl < take;
+    const unsigned smask = __reduce_or_sync(full_mask, starts ? (1u << excl) : 0u);
+    const unsigned consumed = __ballot_sync(full_mask, cnt > 0 && excl + cnt <= take);
+    if (starts && excl + cnt > take) stk[sp - 1 - lane] = pack_range((e >> 3) + (take - excl), cnt - (take - excl));
+    const unsigned le = lane == 31 ? full_mask : ((2u << lane) - 1u);
+    const int k = (__popc(smask & le) - 1) & 31;
+    const int kfirst = __shfl_sync(full_mask, e >> 3, k);
+    const int kexcl = __shfl_sync(full_mask, excl, k);
+    sp -= __popc(consumed);
+    __syncwarp();
+    return lane < take ? kfirst + (lane - kexcl) : -1;
 }
 
 // ---- block-wide exclusive scan (blockDim.x a multiple of 32, <= 1024) --------------

@@ -113,7 +113,6 @@ __device__ __forceinline__ double to_real<double>(double v)
     return v;
 }
 
-__device__ __forceinline__ int pack_range(int first, int count) { return (first << 3) | (count - 1); }
 
 // shared-memory carve-up of one warp
 template <typename Real>
@@ -121,7 +120,6 @@ struct WarpSmem {
     using R4 = typename Vec4<Real>::T;
     using R2 = typename Vec4<Real>::T2;
     int *stk;
-    int *batch;
     R4 *cpos;  // {dx, dy, dz, M} of accepted cells, relative to c_g
     R4 *cqa;   // {Qxx, Qxy, Qxz, Qyy}
     R2 *cqb;   // {Qyz, Qzz}
@@ -132,7 +130,7 @@ struct WarpSmem {
     static __host__ __device__ size_t bytes(int tile)
     {
         size_t cb = tile + 32;
-        size_t b = 4 * kStackCap + 4 * 32;
+        size_t b = 4 * kStackCap;
         b += cb * (2 * sizeof(R4) + sizeof(R2));
         b += cb * 8 + (cb + 1) * 4;
         b = (b + 31) / 32 * 32;
@@ -145,8 +143,6 @@ struct WarpSmem {
         char *p = base;
         stk = (int *)p;
         p += 4 * kStackCap;
-        batch = (int *)p;
-        p += 4 * 32;
         cpos = (R4 *)p;
         p += cb * sizeof(R4);
         cqa = (R4 *)p;
@@ -454,71 +450,60 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
                 if (lane == 0) latch_error(meta, P3T_ERR_INTERNAL);
                 break;
             }
-            // ---- pop up to 32 nodes from the top ranges
-            int e = lane < sp ? W.stk[sp - 1 - lane] : 0;
-            int cnt = lane < sp ? (e & 7) + 1 : 0;
-            int incl = warp_incl_scan(cnt);
-            int excl = incl - cnt;
-            int total = __shfl_sync(0xffffffffu, incl, 31);
-            int take = total < 32 ? total : 32;
-            unsigned full = __ballot_sync(0xffffffffu, lane < sp && incl <= take);
-            __syncwarp();
-            if (lane < sp && excl < take) {
-                int first = e >> 3;
-                int mine = cnt < take - excl ? cnt : take - excl;
-                for (int j = 0; j < mine; j++) W.batch[excl + j] = first + j;
-                if (mine < cnt) W.stk[sp - 1 - lane] = pack_range(first + mine, cnt - mine);
-            }
-            __syncwarp();
-            sp -= __popc(full);
-            const int node = lane < take ? W.batch[lane] : -1;
-            __syncwarp();
+            // ---- pop up to 32 nodes, one per lane
+            const int node = pop_batch(W.stk, sp);
 
-            // ---- opening test
+            // ---- opening test (test and staging data come in one load batch)
             bool open = false, is_leaf = false;
             int cinfo = 0, ccount = 0;
             bool fb = false;
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);  // node record, reused when staging
+            float4 ra, rd, rq0, rq1;  // node record: COM hi / lo + M / quadrupole
             if (node >= 0) {
-                if (kMixed && filter_ok) {
-                    a = T.wA[node];
-                    const float4 b = T.wB[node], c = T.wC[node];
+                if (kMixed) {
+                    const float4 *rec = T.wn + (size_t)kWalkRecord * node;
+                    ra = rec[0];
+                    const float4 b = rec[1], c = rec[2];
+                    rd = rec[3];
+                    rq0 = rec[4];
+                    rq1 = rec[5];
                     cinfo = __float_as_int(b.w);
                     ccount = __float_as_int(c.w);
-                    // point-box: COM against the group box
-                    float tx = fmaxf(fmaxf(glx - a.x, a.x - ghx), 0.f);
-                    float ty = fmaxf(fmaxf(gly - a.y, a.y - ghy), 0.f);
-                    float tz = fmaxf(fmaxf(glz - a.z, a.z - ghz), 0.f);
-                    float d2 = tx * tx + ty * ty + tz * tz;
-                    int mac;
-                    if (isinf(a.w)) {
-                        mac = 1;
-                    } else {
-                        float tol = k_rel * (d2 + a.w) + k_abs * (tx + ty + tz) + k_sq;
-                        mac = d2 < a.w - tol ? 1 : (d2 > a.w + tol ? 0 : 2);
+                    int mac = 2, bb = 2;
+                    if (filter_ok) {
+                        // point-box: COM against the group box
+                        const float tx = fmaxf(fmaxf(glx - ra.x, ra.x - ghx), 0.f);
+                        const float ty = fmaxf(fmaxf(gly - ra.y, ra.y - ghy), 0.f);
+                        const float tz = fmaxf(fmaxf(glz - ra.z, ra.z - ghz), 0.f);
+                        const float d2 = tx * tx + ty * ty + tz * tz;
+                        if (isinf(ra.w)) {
+                            mac = 1;
+                        } else {
+                            const float tol = k_rel * (d2 + ra.w) + k_abs * (tx + ty + tz) + k_sq;
+                            mac = d2 < ra.w - tol ? 1 : (d2 > ra.w + tol ? 0 : 2);
+                        }
+                        // box-box against r_out
+                        const float ux = fmaxf(fmaxf(b.x - ghx, glx - c.x), 0.f);
+                        const float uy = fmaxf(fmaxf(b.y - ghy, gly - c.y), 0.f);
+                        const float uz = fmaxf(fmaxf(b.z - ghz, glz - c.z), 0.f);
+                        const float e2 = ux * ux + uy * uy + uz * uz;
+                        const float tol2 = k_rel * (e2 + P.rout2_f) + k_abs * (ux + uy + uz) + k_sq;
+                        bb = e2 < P.rout2_f - tol2 ? 1 : (e2 > P.rout2_f + tol2 ? 0 : 2);
                     }
-                    // box-box against r_out
-                    float ux = fmaxf(fmaxf(b.x - ghx, glx - c.x), 0.f);
-                    float uy = fmaxf(fmaxf(b.y - ghy, gly - c.y), 0.f);
-                    float uz = fmaxf(fmaxf(b.z - ghz, glz - c.z), 0.f);
-                    float e2 = ux * ux + uy * uy + uz * uz;
-                    float tol2 = k_rel * (e2 + P.rout2_f) + k_abs * (ux + uy + uz) + k_sq;
-                    int bb = e2 < P.rout2_f - tol2 ? 1 : (e2 > P.rout2_f + tol2 ? 0 : 2);
                     if (mac == 1 || bb == 1) {
                         open = true;
                     } else if (mac == 0 && bb == 0) {
                         open = false;
                     } else {
-                        fb = true;
+                        fb = filter_ok;
                         const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
                         open = dist2_point_box(cm.x, cm.y, cm.z, glo, ghi) < cl.w ||
                                dist2_box_box(glo, ghi, cl, ch) < P.rout2_d;
                     }
                 } else {
                     const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
-                    const float4 b = T.wB[node], c = T.wC[node];
-                    cinfo = __float_as_int(b.w);
-                    ccount = __float_as_int(c.w);
+                    const float4 *rec = T.wn + (size_t)kWalkRecord * node;
+                    cinfo = __float_as_int(rec[1].w);
+                    ccount = __float_as_int(rec[2].w);
                     open = dist2_point_box(cm.x, cm.y, cm.z, glo, ghi) < cl.w ||
                            dist2_box_box(glo, ghi, cl, ch) < P.rout2_d;
                 }
@@ -526,8 +511,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
             }
             if (kMixed) nfallback += __popc(__ballot_sync(0xffffffffu, fb));
             const bool accept = node >= 0 && !open;
-            bool open_int = node >= 0 && open && !is_leaf;
-            bool open_leaf = node >= 0 && open && is_leaf;
+            const bool open_int = node >= 0 && open && !is_leaf;
+            const bool open_leaf = node >= 0 && open && is_leaf;
             // consistency of the child / particle ranges before following them
             const bool bad = (open_int && (ccount < 1 || ccount > 8 || cinfo + ccount > nn)) ||
                              (open_leaf && (ccount < 1 || -1 - cinfo + ccount > T.n));
@@ -552,46 +537,39 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
             if (accept) {
                 const int pos = cb + __popc(am & lt);
                 R4 v;
+                R4 qa;
+                R2 qb;
                 if (kMixed) {
-                    const float4 d = T.wD[node];
-                    if (!filter_ok) a = T.wA[node];
-                    const float4 r = ds_rel(a, d, F);
+                    const float4 r = ds_rel(ra, rd, F);
                     v.x = r.x, v.y = r.y, v.z = r.z;
-                    v.w = d.w;  // M
+                    v.w = rd.w;  // M
+                    qa.x = rq0.x, qa.y = rq0.y, qa.z = rq0.z, qa.w = rq0.w;
+                    qb.x = rq1.x, qb.y = rq1.y;
                 } else {
                     const double4_32a cm = T.comM[node];
                     v.x = to_real<Real>(dsub(cm.x, F.cx));
                     v.y = to_real<Real>(dsub(cm.y, F.cy));
                     v.z = to_real<Real>(dsub(cm.z, F.cz));
                     v.w = to_real<Real>(cm.w);
+                    const double2 *q = reinterpret_cast<const double2 *>(T.q64 + 6 * (size_t)node);
+                    const double2 q0 = q[0], q1 = q[1], q2 = q[2];
+                    qa.x = q0.x, qa.y = q0.y, qa.z = q1.x, qa.w = q1.y, qb.x = q2.x, qb.y = q2.y;
                 }
                 W.cpos[pos] = v;
                 if (QUAD) {
-                    R4 qa;
-                    R2 qb;
-                    if (kMixed) {
-                        const float2 *q = reinterpret_cast<const float2 *>(T.q32 + 6 * (size_t)node);
-                        float2 q0 = q[0], q1 = q[1], q2 = q[2];
-                        qa.x = q0.x, qa.y = q0.y, qa.z = q1.x, qa.w = q1.y, qb.x = q2.x, qb.y = q2.y;
-                    } else {
-                        const double2 *q = reinterpret_cast<const double2 *>(T.q64 + 6 * (size_t)node);
-                        double2 q0 = q[0], q1 = q[1], q2 = q[2];
-                        qa.x = q0.x, qa.y = q0.y, qa.z = q1.x, qa.w = q1.y, qb.x = q2.x, qb.y = q2.y;
-                    }
                     W.cqa[pos] = qa;
                     W.cqb[pos] = qb;
                 }
             }
-            cb += __popc(am);
-            ncell += __popc(am);
+            const int na = __popc(am);
+            cb += na;
+            ncell += na;
 
             // ---- queue opened leaves
             const unsigned lm = __ballot_sync(0xffffffffu, open_leaf);
-            int lc = open_leaf ? ccount : 0;
             if (open_leaf) W.lq[lqn + __popc(lm & lt)] = make_int2(-1 - cinfo, ccount);
             lqn += __popc(lm);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) lc += __shfl_xor_sync(0xffffffffu, lc, o);
+            const int lc = (int)__reduce_add_sync(0xffffffffu, open_leaf ? (unsigned)ccount : 0u);
             lqp += lc;
             npart += lc;
 
