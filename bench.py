@@ -36,6 +36,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# DRAM bytes of one walk_kernel launch per particle, from the ncu capture summarised
+# in profiles/walk_kernel_plummer_kroupa_n262144.md (16.19 MB at N = 2^18; the
+# traffic grows with N).  Valid only for the kernel sources it was measured on:
+# if they change, the roofline's traffic is reported as null until re-measured.
+WALK_TRAFFIC = {"sources": {"walk.cu": "ceb66d06b033c26e", "p3t_internal.cuh": "1041cea4ada2d9c9"},
+                "bytes_per_particle": 16189952 / 262144}
+
 N_DEFAULT = 1_000_000
 THETA = 0.4
 DT = 1.0 / 512
@@ -46,7 +53,7 @@ FP32_LANES_PER_SM = 128
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
@@ -128,7 +135,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -177,6 +184,16 @@ def measured_peaks():
         with open(p) as fh:
             return json.load(fh), "measured"
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def walk_traffic(n):
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2110_11658_b300", "csrc")
+    for name, want in WALK_TRAFFIC["sources"].items():
+        with open(os.path.join(csrc, name), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != want:
+                return None
+    return WALK_TRAFFIC["bytes_per_particle"] * n
 
 
 def fp32_peak_tflops(sm_count, sm_max_mhz):
@@ -405,7 +422,7 @@ def run_b300(args, rank, local, world):
         "mean_neighbours": nbr_total / n,
         "roofline": {"bound": "alu", "kernel": "walk_kernel (p3t_far_force)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": None,
+                     "traffic": walk_traffic(n),
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
                                     % (float(peaks.get("sm_max_mhz", 2032.0)), peak_kind),
                      "flops_per_launch": FLOPS_PER_INTERACTION * inter},
