@@ -63,6 +63,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
+    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m"],
+                    help="plummer1m: the throughput benchmark; king2m: theta sweep of the "
+                         "mixed and FP64 forms against the direct sum (one line per theta)")
+    ap.add_argument("--samples", type=int, default=8192, help="direct-sum targets (king2m)")
     return ap.parse_args(argv)
 
 
@@ -475,8 +479,75 @@ def run_reference(args, rank, world):
     }
 
 
+def king2m_sweep(args):
+    """King W0 = 7, N = 2^21, Kroupa masses, heavy stars scaled by 0.7 (segregated);
+    r_out = the paper's r_cut = 4 tau (Eqs. 21-22), r_in = 0.1 r_out.  For theta in
+    {0.3, 0.5, 0.7}: far-force time of the mixed and all-FP64 GPU forms and their error
+    against the FP64 direct sum on `samples` seeded targets."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2110_11658_b300 as p3t
+    import synth
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n = 2 ** 21 if args.n == N_DEFAULT else args.n
+    c = synth.make("king", n, 20211022, masses="kroupa", w0=7.0, segregated=True)
+    r_out = synth.paper_run_params(n)["r_cut"]
+    r_in = 0.1 * r_out
+    tg = np.random.default_rng(20211022).choice(n, args.samples, replace=False)
+    t0 = time.perf_counter()
+    ref = oracle.direct_split(c.x, c.y, c.z, c.m, r_in, r_out, targets=tg)["far"]
+    t_direct = time.perf_counter() - t0
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    x, y, z, m = t(c.x), t(c.y), t(c.z), t(c.m)
+    lines = []
+    for theta in (0.3, 0.5, 0.7):
+        row = {"theta": theta}
+        for name, prec in (("mixed", p3t.P3T_FP32_MIXED), ("fp64", p3t.P3T_FP64)):
+            prm = p3t.Params(theta=theta, r_in=r_in, r_out=r_out, r_list=r_out, leaf_cap=args.leaf_cap,
+                             group_size=args.group_size, tile=args.tile, precision=prec)
+            ctx = p3t.Context(prm)
+            ctx.build_tree(x, y, z, m)
+            dt = ctx.acc_dtype
+            a = [torch.empty(n, dtype=dt, device=dev) for _ in range(3)]
+            nc = torch.zeros(1, dtype=torch.int64, device=dev)
+            npart = torch.zeros(1, dtype=torch.int64, device=dev)
+            reps = 5 if prec == p3t.P3T_FP32_MIXED else 2
+            times = []
+            for r in range(reps + 1):
+                nc.zero_()
+                npart.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.far_force(*a, n_cell=nc, n_part=npart)
+                e1.record()
+                torch.cuda.synchronize()
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            ctx.check()
+            got = torch.stack(a, 1).double().cpu().numpy()[tg]
+            err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+            inter = (int(nc.item()) + int(npart.item())) / n
+            ms = float(np.median(times))
+            row[name] = {"far_ms": ms, "evals_per_s": n / (ms * 1e-3),
+                         "err_vs_direct_median": float(np.median(err)),
+                         "err_vs_direct_p99": float(np.percentile(err, 99)),
+                         "interactions_per_particle": inter}
+            ctx.close()
+        row["speedup_mixed_over_fp64"] = row["fp64"]["far_ms"] / row["mixed"]["far_ms"]
+        lines.append(row)
+    for row in lines:
+        print(json.dumps({"workload": "king_w0_7_kroupa_segregated_n%d" % n, "n": n, "r_out": r_out,
+                          "r_in": r_in, "samples": args.samples, "direct_sum_s": t_direct, **row}))
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload == "king2m":
+        king2m_sweep(args)
+        return
     rank, local, world = dist_init()
     if args.impl == "reference":
         line = run_reference(args, rank, world)

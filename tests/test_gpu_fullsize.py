@@ -1,0 +1,85 @@
+"""Parity at the benchmark's full size, in the launch configuration bench.py times.
+
+Plummer sphere, N = 10^6, Kroupa masses, theta = 0.4, r_out for ~100 mean
+neighbours, r_in = 0.1 r_out, leaf_cap 16, G = 32, tile 64, mixed precision.
+The oracle builds the whole tree (bit-exact comparison of keys, permutation,
+topology and groups) and evaluates forces, interaction counts and neighbour
+rows for a seeded sample of groups; a sample of targets is also checked
+against the FP64 direct sum.
+"""
+import numpy as np
+import pytest
+import torch
+
+import bench
+import oracle
+import paper_2110_11658_b300 as p3t
+from gpu_helpers import DEV, rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    c, w = bench.workload(bench.N_DEFAULT, 20211022)
+    prm = p3t.Params(theta=w["theta"], r_in=w["r_in"], r_out=w["r_out"], r_list=w["r_list"],
+                     leaf_cap=16, group_size=32, tile=64, precision=p3t.P3T_FP32_MIXED)
+    ctx = p3t.Context(prm)
+    ctx.set_debug(True)
+    ctx.build_tree(to_dev(c.x), to_dev(c.y), to_dev(c.z), to_dev(c.m))
+    a = [torch.empty(c.n, dtype=torch.float32, device=DEV) for _ in range(3)]
+    pot = torch.empty(c.n, dtype=torch.float64, device=DEV)
+    ctx.far_force(*a, pot=pot)
+    offs = torch.empty(c.n + 1, dtype=torch.int64, device=DEV)
+    idx = torch.empty(130 * c.n, dtype=torch.int32, device=DEV)
+    total = ctx.neighbours(offs, idx)
+    gc, gp = ctx.group_counts()
+    tree = {k: v.cpu().numpy() for k, v in ctx.export_tree().items()}
+    tree["keys"] = tree["keys"].view(np.uint64)
+    out = {"c": c, "w": w, "a": torch.stack(a, 1).double().cpu().numpy(), "pot": pot.cpu().numpy(),
+           "offs": offs.cpu().numpy(), "idx": idx[:total].cpu().numpy(), "g_cells": gc.cpu().numpy(),
+           "g_parts": gp.cpu().numpy(), "tree": tree}
+    ctx.check()
+    ctx.close()
+    out["oracle"] = oracle.Tree(c.x, c.y, c.z, c.m, w["theta"], w["r_out"], leaf_cap=16, group_size=32)
+    return out
+
+
+def test_fullsize_tree_bit_exact(c2):
+    ref = c2["oracle"].export()
+    g = c2["tree"]
+    for k in ("keys", "perm", "level", "first", "count", "child", "nchild", "g_first", "g_count"):
+        assert np.array_equal(g[k], ref[k]), k
+    for k in ("M", "com", "lo", "hi", "ropen2"):
+        assert np.array_equal(g[k], ref[k]), k
+
+
+def test_fullsize_sampled_groups_forces_counts_neighbours(c2):
+    t = c2["oracle"]
+    rng = np.random.default_rng(8)
+    sel = np.sort(rng.choice(t.n_groups, 128, replace=False))
+    f = t.far(c2["w"]["r_in"], groups=sel)
+    assert np.array_equal(c2["g_cells"][sel], f["n_cell"])
+    assert np.array_equal(c2["g_parts"][sel], f["n_part"])
+    rows = ~np.isnan(f["a"][:, 0])
+    e = rel_err(c2["a"][rows], f["a"][rows])
+    assert np.median(e) <= 1e-5 and np.percentile(e, 99) <= 1e-4, (np.median(e), np.percentile(e, 99))
+    ep = np.abs(c2["pot"][rows] - f["pot"][rows]) / np.abs(f["pot"][rows])
+    assert np.median(ep) <= 1e-6
+    counts, offs, idx = t.neighbours(c2["w"]["r_list"], groups=sel)
+    mine = np.nonzero(counts >= 0)[0]
+    go, gi = c2["offs"], c2["idx"]
+    for i in mine:
+        assert np.array_equal(gi[go[i]:go[i + 1]], idx[offs[i]:offs[i + 1]]), i
+    # mean neighbour number near the target of the workload (~100)
+    assert 90 < go[-1] / len(go) < 115
+
+
+def test_fullsize_against_direct_sum(c2):
+    # the tree's own approximation error, measured against the FP64 direct sum
+    c, w = c2["c"], c2["w"]
+    rng = np.random.default_rng(9)
+    tg = rng.choice(c.n, 512, replace=False)
+    d = oracle.direct_split(c.x, c.y, c.z, c.m, w["r_in"], w["r_out"], targets=tg)
+    e = rel_err(c2["a"][tg], d["far"])
+    assert np.median(e) < 2e-4 and np.percentile(e, 99) < 1e-3, (np.median(e), np.percentile(e, 99))
