@@ -35,6 +35,7 @@ P3T_FP64 = 1
 
 EXPORTED = [
     "p3t_default_params", "p3t_create", "p3t_destroy", "p3t_set_params", "p3t_build_tree",
+    "p3t_build_tree_batch",
     "p3t_far_force", "p3t_neighbours", "p3t_neighbours_async", "p3t_kick", "p3t_drift",
     "p3t_step_host", "p3t_status", "p3t_tree_info", "p3t_export_tree", "p3t_group_counts",
     "p3t_set_debug", "p3t_error_string", "p3t_morton_order_noalloc",
@@ -68,6 +69,7 @@ _sig = {
     "p3t_destroy": [_vp],
     "p3t_set_params": [_vp, C.POINTER(p3t_params)],
     "p3t_build_tree": [_vp, _i64, _vp, _vp, _vp, _vp],
+    "p3t_build_tree_batch": [_vp, C.c_int32, _i64, _vp, _vp, _vp, _vp, _vp],
     "p3t_far_force": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "p3t_neighbours": [_vp, _vp, _vp, _i64, C.POINTER(_i64)],
     "p3t_neighbours_async": [_vp, _vp, _vp, _i64, _vp],
@@ -184,6 +186,16 @@ class Context:
         n = x.numel()
         args = [_ptr(a, t.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")]
         _check(_lib.p3t_build_tree(self._h, n, *args), "p3t_build_tree")
+        self.n = n
+
+    def build_tree_batch(self, seg_offsets, x, y, z, m):
+        """Ensemble build: seg_offsets is a CUDA int64 tensor of n_clusters + 1 offsets."""
+        t = self._torch
+        n = x.numel()
+        nc = seg_offsets.numel() - 1
+        args = [_ptr(a, t.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")]
+        _check(_lib.p3t_build_tree_batch(self._h, nc, n, _ptr(seg_offsets, t.int64, nc + 1, "seg_offsets"),
+                                         *args), "p3t_build_tree_batch")
         self.n = n
 
     def far_force(self, ax, ay, az, pot=None, n_cell=None, n_part=None):

@@ -41,10 +41,6 @@ __global__ void init_meta_kernel(Meta *m)
         m->level_count[t] = 0;
     }
     if (t < 32) m->tickets[t] = 0;
-    if (t < 3) {
-        m->minmax[t] = ~0ULL;   // running minimum
-        m->minmax[3 + t] = 0;   // running maximum
-    }
     if (t == 0) {
         m->n_nodes = 0;
         m->n_groups = 0;
@@ -52,6 +48,37 @@ __global__ void init_meta_kernel(Meta *m)
         m->depth = 0;
         m->fallback_tests = 0;
     }
+}
+
+__global__ void init_clusters_kernel(Cluster *cl, int C)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
+        for (int d = 0; d < 3; d++) {
+            cl[c].minmax[d] = ~0ULL;   // running minimum
+            cl[c].minmax[3 + d] = 0;   // running maximum
+        }
+}
+
+// cluster of every particle from the offsets (validated: 0 = seg[0] < ... < seg[C] = n)
+__global__ void __launch_bounds__(kBuildThreads)
+    cid_kernel(int n, int C, const int64_t *__restrict__ seg, int32_t *__restrict__ cid, Meta *meta)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= C && i < C + 1) {
+        const long long v = seg[i];
+        const bool ok = (i == 0 ? v == 0 : v > seg[i - 1]) && (i < C || v == n);
+        if (!ok) latch_error(meta, P3T_ERR_INVALID_INPUT);
+    }
+    if (i >= n) return;
+    int lo = 0, hi = C;  // last c with seg[c] <= i
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (seg[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    cid[i] = lo;
 }
 
 // order-preserving map of non-NaN doubles onto unsigned integers
@@ -66,67 +93,85 @@ __device__ __forceinline__ double dec_double(unsigned long long e)
     return __longlong_as_double((long long)u);
 }
 
+// Per-cluster bounding box (exact, order-preserving integer min/max) and input
+// validation.  A warp whose particles all belong to one cluster reduces first.
 __global__ void __launch_bounds__(kBuildThreads)
     bbox_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
-                const double *__restrict__ z, const double *__restrict__ m, Meta *meta)
+                const double *__restrict__ z, const double *__restrict__ m,
+                const int32_t *__restrict__ cid, Cluster *cl, Meta *meta)
 {
-    unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0, 0, 0};
+    const int lane = threadIdx.x & 31;
     bool bad = false;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double p[3] = {x[i], y[i], z[i]};
-        double mi = m[i];
-        bool ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(mi) && mi >= 0.0;
-        bad |= !ok;
-        if (!ok) continue;
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + lane;
+        unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0, 0, 0};
+        int c = -1;
+        if (i < n) {
+            const double p[3] = {x[i], y[i], z[i]};
+            const double mi = m[i];
+            const bool ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(mi) && mi >= 0.0;
+            bad |= !ok;
+            c = cid ? cid[i] : 0;
+            if (ok)
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-            unsigned long long e = enc_double(p[d]);
-            mn[d] = e < mn[d] ? e : mn[d];
-            mx[d] = e > mx[d] ? e : mx[d];
+                for (int d = 0; d < 3; d++) mn[d] = mx[d] = enc_double(p[d]);
+        }
+        const int c0 = __shfl_sync(0xffffffffu, c, 0);
+        if (__all_sync(0xffffffffu, c < 0 || c == c0)) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], o);
+                    const unsigned long long bb = __shfl_xor_sync(0xffffffffu, mx[d], o);
+                    mn[d] = a < mn[d] ? a : mn[d];
+                    mx[d] = bb > mx[d] ? bb : mx[d];
+                }
+            }
+            if (lane == 0 && c0 >= 0)
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    atomicMin(&cl[c0].minmax[d], mn[d]);
+                    atomicMax(&cl[c0].minmax[3 + d], mx[d]);
+                }
+        } else if (c >= 0) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                atomicMin(&cl[c].minmax[d], mn[d]);
+                atomicMax(&cl[c].minmax[3 + d], mx[d]);
+            }
         }
     }
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], o);
-            unsigned long long b = __shfl_xor_sync(0xffffffffu, mx[d], o);
-            mn[d] = a < mn[d] ? a : mn[d];
-            mx[d] = b > mx[d] ? b : mx[d];
-        }
-    }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) latch_error(meta, P3T_ERR_INVALID_INPUT);
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            atomicMin(&meta->minmax[d], mn[d]);
-            atomicMax(&meta->minmax[3 + d], mx[d]);
-        }
-    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(meta, P3T_ERR_INVALID_INPUT);
 }
 
-// rule 1: the bounding cube, and the frame of the FP32 walk filter
-__global__ void cube_kernel(Meta *meta)
+// rule 1 per cluster: the bounding cube, and the frame of the FP32 walk filter
+__global__ void cube_kernel(Cluster *cl, int C)
 {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    Cluster &K = cl[c];
     double lo[3], hi[3], side = 0.0;
     for (int d = 0; d < 3; d++) {
-        lo[d] = dec_double(meta->minmax[d]);
-        hi[d] = dec_double(meta->minmax[3 + d]);
-        if (meta->minmax[d] == ~0ULL) lo[d] = hi[d] = 0.0;  // no valid particle
+        lo[d] = dec_double(K.minmax[d]);
+        hi[d] = dec_double(K.minmax[3 + d]);
+        if (K.minmax[d] == ~0ULL) lo[d] = hi[d] = 0.0;  // no valid particle
         double ext = dsub(hi[d], lo[d]);
         if (ext > side) side = ext;
     }
     if (side == 0.0) side = 1.0;
     double R = 0.0;
     for (int d = 0; d < 3; d++) {
-        meta->cube[d] = lo[d];
+        K.cube[d] = lo[d];
         double o = dmul(0.5, dadd(lo[d], hi[d]));
-        meta->frame[d] = o;
+        K.frame[d] = o;
         R = dmax(R, dmax(dsub(hi[d], o), dsub(o, lo[d])));
     }
-    meta->cube[3] = side;
+    K.cube[3] = side;
+    K.scale = ddiv(2097152.0, side);
     // |x - O| <= R for every particle; pad for the rounding of O
-    meta->frame[3] = R * (1.0 + 1e-9) + 1e-300;
+    K.frame[3] = R * (1.0 + 1e-9) + 1e-300;
 }
 
 __device__ __forceinline__ unsigned long long spread3(unsigned long long v)
@@ -150,23 +195,34 @@ __device__ __forceinline__ unsigned long long quantise(double v, double lo, doub
 
 __global__ void __launch_bounds__(kBuildThreads)
     keys_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
-                const double *__restrict__ z, const Meta *__restrict__ meta,
-                uint64_t *__restrict__ keys, int32_t *__restrict__ perm)
+                const double *__restrict__ z, const int32_t *__restrict__ cid,
+                const Cluster *__restrict__ cl, uint64_t *__restrict__ keys,
+                int32_t *__restrict__ perm)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = ddiv(2097152.0, meta->cube[3]);
-    unsigned long long qx = quantise(x[i], meta->cube[0], s);
-    unsigned long long qy = quantise(y[i], meta->cube[1], s);
-    unsigned long long qz = quantise(z[i], meta->cube[2], s);
+    const Cluster &K = cl[cid ? cid[i] : 0];
+    const double s = K.scale;  // 2^21 / side
+    unsigned long long qx = quantise(x[i], K.cube[0], s);
+    unsigned long long qy = quantise(y[i], K.cube[1], s);
+    unsigned long long qz = quantise(z[i], K.cube[2], s);
     keys[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     perm[i] = i;
 }
 
 // ---------------------------------------------------------------------------
 // radix sort: per-block digit histograms, a scan, then a stable scatter
+// digit of an item: bits [shift, shift+8) of the key, or of the cluster id of its
+// payload (the stable passes that group a batched build by cluster)
+__device__ __forceinline__ int sort_digit(uint64_t key, int32_t val, int shift,
+                                          const int32_t *__restrict__ cid)
+{
+    return cid ? (cid[val] >> shift) & 255 : (int)((key >> shift) & 255);
+}
+
 __global__ void __launch_bounds__(kBuildThreads)
-    sort_hist_kernel(int n, const uint64_t *__restrict__ keys, int shift, int nblocks,
+    sort_hist_kernel(int n, const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals,
+                     const int32_t *__restrict__ cid, int shift, int nblocks,
                      int32_t *__restrict__ hist)
 {
     __shared__ int cnt[256];
@@ -176,7 +232,7 @@ __global__ void __launch_bounds__(kBuildThreads)
 #pragma unroll 4
     for (int k = 0; k < kSortItems; k++) {
         long long i = base + k * kBuildThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255], 1);
+        if (i < n) atomicAdd(&cnt[sort_digit(keys[i], vals[i], shift, cid)], 1);
     }
     __syncthreads();
     hist[threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
@@ -184,8 +240,9 @@ __global__ void __launch_bounds__(kBuildThreads)
 
 __global__ void __launch_bounds__(kBuildThreads)
     sort_scatter_kernel(int n, const uint64_t *__restrict__ kin, const int32_t *__restrict__ vin,
-                        uint64_t *__restrict__ kout, int32_t *__restrict__ vout, int shift,
-                        int nblocks, const int32_t *__restrict__ hist_off)
+                        uint64_t *__restrict__ kout, int32_t *__restrict__ vout,
+                        const int32_t *__restrict__ cid, int shift, int nblocks,
+                        const int32_t *__restrict__ hist_off)
 {
     constexpr int W = kBuildThreads / 32;
     __shared__ int gofs[256];
@@ -203,7 +260,7 @@ __global__ void __launch_bounds__(kBuildThreads)
         bool valid = i < n;
         uint64_t key = valid ? kin[i] : 0;
         int32_t val = valid ? vin[i] : 0;
-        int d = valid ? (int)((key >> shift) & 255) : 256;
+        int d = valid ? sort_digit(key, val, shift, cid) : 256;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int wrank = __popc(peers & lt);
         if (valid && wrank == 0) wcnt[warp][d] = __popc(peers);
@@ -233,20 +290,24 @@ __global__ void __launch_bounds__(kBuildThreads)
 __global__ void __launch_bounds__(kBuildThreads)
     gather_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
                   const double *__restrict__ z, const double *__restrict__ m,
-                  const int32_t *__restrict__ perm, const Meta *__restrict__ meta,
-                  double4_32a *__restrict__ sp, float4 *__restrict__ ph, float4 *__restrict__ pl,
-                  int32_t *__restrict__ inv)
+                  const int32_t *__restrict__ perm, const int32_t *__restrict__ cid,
+                  const Cluster *__restrict__ cl, double4_32a *__restrict__ sp,
+                  float4 *__restrict__ ph, float4 *__restrict__ pl, int32_t *__restrict__ inv,
+                  int32_t *__restrict__ cid_s)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int i = perm[s];
     inv[i] = s;
+    const int c = cid ? cid[i] : 0;
+    cid_s[s] = c;
+    const double *O = cl[c].frame;
     double px = x[i], py = y[i], pz = z[i], pm = m[i];
     sp[s] = make_double4_32a(px, py, pz, pm);
     float hx, hy, hz, lx, ly, lz;
-    ds_split(dsub(px, meta->frame[0]), hx, lx);
-    ds_split(dsub(py, meta->frame[1]), hy, ly);
-    ds_split(dsub(pz, meta->frame[2]), hz, lz);
+    ds_split(dsub(px, O[0]), hx, lx);
+    ds_split(dsub(py, O[1]), hy, ly);
+    ds_split(dsub(pz, O[2]), hz, lz);
     ph[s] = make_float4(hx, hy, hz, __double2float_rn(pm));
     pl[s] = make_float4(lx, ly, lz, 0.f);
 }
@@ -267,19 +328,29 @@ __device__ __forceinline__ void flag_groups(unsigned char *gflag, int first, int
         for (int f = 0; f < count; f += G) gflag[first + f] = 1;
 }
 
+// one root per cluster at level 0 (node c covers cluster c in key order)
 __global__ void topo_root_kernel(Tree T, int n, int leaf_cap, int G)
 {
-    T.topo[0] = make_int4(0, n, -1, 0);
-    T.level[0] = 0;
-    T.parent[0] = -1;
-    T.ready[0] = 0;
-    if (n <= leaf_cap) {
-        T.leaves[0] = 0;
-        T.meta->n_leaves = 1;
+    const int C = T.n_clusters;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) {
+        T.meta->level_start[0] = 0;
+        T.meta->level_count[0] = C;
     }
-    T.meta->level_start[0] = 0;
-    T.meta->level_count[0] = 1;
-    flag_groups(T.gflag, 0, n, true, n <= leaf_cap, G);
+    if (c >= C) return;
+    long long first = T.seg ? T.seg[c] : 0, end = T.seg ? T.seg[c + 1] : n;
+    if (!(first >= 0 && end > first && end <= n)) {  // invalid offsets: empty, safe root
+        latch_error(T.meta, P3T_ERR_INVALID_INPUT);
+        first = 0;
+        end = 0;
+    }
+    const int cnt = (int)(end - first);
+    T.topo[c] = make_int4((int)first, cnt, -1, 0);
+    T.level[c] = 0;
+    T.parent[c] = -1;
+    T.ready[c] = 0;
+    if (cnt <= leaf_cap) T.leaves[atomicAdd(&T.meta->n_leaves, 1)] = c;
+    flag_groups(T.gflag, (int)first, cnt, true, cnt <= leaf_cap, G);
 }
 
 __device__ __forceinline__ int lower_bound_key(const uint64_t *__restrict__ keys, int lo, int hi,
@@ -492,7 +563,7 @@ __device__ void write_node(Tree &T, int k, double M, const double com[3], const 
         q2[1] = make_float2((float)q[2], (float)q[3]);
         q2[2] = make_float2((float)q[4], (float)q[5]);
     }
-    const double *O = T.meta->frame;
+    const double *O = T.cl[T.cid_s[tp.x < T.n ? tp.x : 0]].frame;
     const bool leaf = tp.z < 0;
     float chx, chy, chz, clx, cly, clz;
     ds_split(dsub(com[0], O[0]), chx, clx);
@@ -544,7 +615,7 @@ __device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
         for (int a = 0; a < 6; a++) q[a] = Q[a];
     } else {
         // FP32 quadrupole on offsets from the double-single splits (x - O) - (com - O)
-        const double *O = T.meta->frame;
+        const double *O = T.cl[T.cid_s[b < T.n ? b : 0]].frame;
         float chx, chy, chz, clx, cly, clz;
         ds_split(dsub(com[0], O[0]), chx, clx);
         ds_split(dsub(com[1], O[1]), chy, cly);
@@ -659,42 +730,53 @@ __global__ void __launch_bounds__(kBuildThreads) moments_level_kernel(Tree T, in
 }
 
 // ---------------------------------------------------------------------------
-int build_tree(p3t_ctx *c, int n, const double *x, const double *y, const double *z,
-               const double *m)
+int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *x,
+               const double *y, const double *z, const double *m)
 {
     cudaStream_t s = c->stream;
     Tree &T = c->tree;
     Meta *M = c->meta;
     const p3t_params &P = c->prm;
     T.n = n;
+    T.n_clusters = n_clusters;
+    T.seg = seg;
+    const int32_t *cid = seg ? T.cid : nullptr;  // null: a single cluster
     const int grid_n = (n + kBuildThreads - 1) / kBuildThreads;
+    const int grid_c = (n_clusters + 127) / 128;
     const int persistent = 4 * c->sm_count;
 
     init_meta_kernel<<<1, 64, 0, s>>>(M);
-    bbox_kernel<<<persistent, kBuildThreads, 0, s>>>(n, x, y, z, m, M);
-    cube_kernel<<<1, 1, 0, s>>>(M);
-    keys_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, M, c->keys_buf[0], c->perm_buf[0]);
+    init_clusters_kernel<<<grid_c, 128, 0, s>>>(T.cl, n_clusters);
+    if (seg) cid_kernel<<<(n > n_clusters ? grid_n : grid_c + 1), kBuildThreads, 0, s>>>(n, n_clusters, seg, T.cid, M);
+    bbox_kernel<<<persistent, kBuildThreads, 0, s>>>(n, x, y, z, m, cid, T.cl, M);
+    cube_kernel<<<grid_c, 128, 0, s>>>(T.cl, n_clusters);
+    keys_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, cid, T.cl, c->keys_buf[0], c->perm_buf[0]);
     if (check_launch(c)) return P3T_ERR_CUDA;
 
-    // 8 passes of 8 bits: the result lands back in buffer 0
+    // 8 passes of 8 bits over the key, then (batched builds) stable passes over the
+    // cluster id, so the order is (cluster, key, original index)
     const int nb = (n + kSortTile - 1) / kSortTile;
-    for (int pass = 0; pass < 8; pass++) {
-        const int shift = 8 * pass;
+    const int cid_passes = seg ? (n_clusters <= 256 ? 1 : (n_clusters <= 65536 ? 2 : 3)) : 0;
+    const int passes = 8 + cid_passes;
+    for (int pass = 0; pass < passes; pass++) {
+        const bool by_cid = pass >= 8;
+        const int shift = by_cid ? 8 * (pass - 8) : 8 * pass;
         uint64_t *kin = c->keys_buf[pass & 1], *kout = c->keys_buf[(pass + 1) & 1];
         int32_t *vin = c->perm_buf[pass & 1], *vout = c->perm_buf[(pass + 1) & 1];
-        sort_hist_kernel<<<nb, kBuildThreads, 0, s>>>(n, kin, shift, nb, c->sort_hist);
+        const int32_t *dcid = by_cid ? T.cid : nullptr;
+        sort_hist_kernel<<<nb, kBuildThreads, 0, s>>>(n, kin, vin, dcid, shift, nb, c->sort_hist);
         if (check_launch(c)) return P3T_ERR_CUDA;
         int e = scan_excl_i32_to_i32(c->sort_hist, c->sort_hist, 256 * nb, c->scan_status,
                                      &M->tickets[31], M, s);
         if (e) return e;
-        sort_scatter_kernel<<<nb, kBuildThreads, 0, s>>>(n, kin, vin, kout, vout, shift, nb,
+        sort_scatter_kernel<<<nb, kBuildThreads, 0, s>>>(n, kin, vin, kout, vout, dcid, shift, nb,
                                                          c->sort_hist);
         if (check_launch(c)) return P3T_ERR_CUDA;
     }
-    T.keys = c->keys_buf[0];
-    T.perm = c->perm_buf[0];
-    gather_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, m, T.perm, M, T.sp, T.ph, T.pl,
-                                                    T.inv);
+    T.keys = c->keys_buf[passes & 1];
+    T.perm = c->perm_buf[passes & 1];
+    gather_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, m, T.perm, cid, T.cl, T.sp, T.ph, T.pl,
+                                                    T.inv, T.cid_s);
 
     // topology, level by level
     unsigned long long *topo_status = c->scan_status + (n / 256 + 64 + 256 * nb / 256);
@@ -703,7 +785,7 @@ int build_tree(p3t_ctx *c, int n, const double *x, const double *y, const double
             cudaSuccess ||
         cudaMemsetAsync(T.gflag, 0, n, s) != cudaSuccess)
         return P3T_ERR_CUDA;
-    topo_root_kernel<<<1, 1, 0, s>>>(T, n, P.leaf_cap, P.group_size);
+    topo_root_kernel<<<grid_c, 128, 0, s>>>(T, n, P.leaf_cap, P.group_size);
     const int topo_grid = 2 * c->sm_count;
     for (int l = 0; l < kLevels; l++)
         topo_level_kernel<<<topo_grid, kBuildThreads, 0, s>>>(

@@ -55,6 +55,8 @@ int ensure_capacity(p3t_ctx *c, long long n)
         {(void **)&T.gflag, (size_t)N + 16},
         {(void **)&T.gidx, 4 * (size_t)N},
         {(void **)&T.leaves, 4 * (size_t)N},
+        {(void **)&T.cid, 4 * (size_t)N},
+        {(void **)&T.cid_s, 4 * (size_t)N},
         {(void **)&T.inv, 4 * (size_t)N},
         {(void **)&T.grp, 8 * (size_t)N},
         {(void **)&T.glo, 32 * (size_t)N},
@@ -177,6 +179,7 @@ int p3t_destroy(p3t_ctx *c)
     cudaStreamSynchronize(c->stream);
     if (c->blob) cudaFree(c->blob);
     if (c->host_stage) cudaFree(c->host_stage);
+    if (c->clusters) cudaFree(c->clusters);
     delete c;
     return P3T_OK;
 }
@@ -191,22 +194,51 @@ int p3t_set_params(p3t_ctx *c, const p3t_params *p)
     return P3T_OK;
 }
 
-int p3t_build_tree(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
-                   const double *m)
+static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *seg, const double *x,
+                        const double *y, const double *z, const double *m)
 {
     if (!c || !x || !y || !z || !m) return P3T_ERR_INVALID_ARG;
     if (n <= 0 || n >= (1LL << 31) - 1) return P3T_ERR_INVALID_ARG;
+    if (n_clusters < 1 || n_clusters > n) return P3T_ERR_INVALID_ARG;
     if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 29)) return P3T_ERR_INVALID_ARG;
     int e = ensure_capacity(c, n);
     if (e) return e;
+    if (n_clusters > c->cap_clusters) {
+        if (c->clusters) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->clusters);
+            c->clusters = nullptr;
+        }
+        int cap = n_clusters < 256 ? 256 : n_clusters;
+        if (cudaMalloc(&c->clusters, sizeof(Cluster) * (size_t)cap) != cudaSuccess) {
+            cudaGetLastError();
+            c->cap_clusters = 0;
+            return P3T_ERR_OOM;
+        }
+        c->cap_clusters = cap;
+    }
+    c->tree.cl = c->clusters;
     c->built = 0;
     c->counts_valid = 0;
-    e = build_tree(c, (int)n, x, y, z, m);
+    e = build_tree(c, (int)n, n_clusters, seg, x, y, z, m);
     if (e) return e;
     c->n = (int)n;
     c->built = 1;
     c->built_precision = c->prm.precision;
     return P3T_OK;
+}
+
+int p3t_build_tree(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                   const double *m)
+{
+    return build_common(c, n, 1, nullptr, x, y, z, m);
+}
+
+int p3t_build_tree_batch(p3t_ctx *c, int32_t n_clusters, int64_t n, const int64_t *seg_offsets,
+                         const double *x, const double *y, const double *z, const double *m)
+{
+    if (!seg_offsets) return P3T_ERR_INVALID_ARG;
+    return build_common(c, n, n_clusters, seg_offsets, x, y, z, m);
 }
 
 int p3t_far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *n_cell_inter,

@@ -57,10 +57,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
     Meta *meta = T.meta;
     const int ng = meta->n_groups;
     const int nn = meta->n_nodes;
-    const double Ox = meta->frame[0], Oy = meta->frame[1], Oz = meta->frame[2];
-    const float Rf = (float)meta->frame[3] * 1.0001f;
-    const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && P.rl2_f > 1e-20f && P.rl2_f < 1e30f;
-    const float k_rel = 8.f * kUn, k_abs = 8.f * kUn * Rf, k_sq = 16.f * kUn * kUn * Rf * Rf;
+    const float k_rel = 8.f * kUn;
     bool allowed = true;
     if (FILL) allowed = P.offs[T.n] <= P.capacity;
     if (FILL && !allowed) {
@@ -75,6 +72,12 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         if (g >= ng) break;
         const int2 gr = T.grp[g];
         const double4_32a glo = T.glo[g], ghi = T.ghi[g];
+        const int cid = T.cid_s[gr.x];  // the group's cluster: frame, root, filter band
+        const double *fr = T.cl[cid].frame;
+        const double Ox = fr[0], Oy = fr[1], Oz = fr[2];
+        const float Rf = (float)fr[3] * 1.0001f;
+        const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && P.rl2_f > 1e-20f && P.rl2_f < 1e30f;
+        const float k_abs = 8.f * kUn * Rf, k_sq = 16.f * kUn * kUn * Rf * Rf;
         const double cgx = dmul(0.5, dadd(glo.x, ghi.x));
         const double cgy = dmul(0.5, dadd(glo.y, ghi.y));
         const double cgz = dmul(0.5, dadd(glo.z, ghi.z));
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         const bool pair_filter = filter_ok && A < 1e12f;
 
         int sp = 1;
-        if (lane == 0) W.stk[0] = pack_range(0, 1);
+        if (lane == 0) W.stk[0] = pack_range(cid, 1);
         __syncwarp();
         int lqn = 0, lqp = 0;
         int iters = 0;  // a valid walk pops every node at most once

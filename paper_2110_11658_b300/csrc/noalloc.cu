@@ -25,25 +25,29 @@ namespace p3t {
 
 // kernels of build_tree.cu (same launch sequence as the tree build's first steps)
 __global__ void init_meta_kernel(Meta *m);
+__global__ void init_clusters_kernel(Cluster *cl, int C);
 __global__ void bbox_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
-                            const double *__restrict__ z, const double *__restrict__ m, Meta *meta);
-__global__ void cube_kernel(Meta *meta);
+                            const double *__restrict__ z, const double *__restrict__ m,
+                            const int32_t *__restrict__ cid, Cluster *cl, Meta *meta);
+__global__ void cube_kernel(Cluster *cl, int C);
 __global__ void keys_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
-                            const double *__restrict__ z, const Meta *__restrict__ meta,
-                            uint64_t *__restrict__ keys, int32_t *__restrict__ perm);
-__global__ void sort_hist_kernel(int n, const uint64_t *__restrict__ keys, int shift, int nblocks,
-                                 int32_t *__restrict__ hist);
+                            const double *__restrict__ z, const int32_t *__restrict__ cid,
+                            const Cluster *__restrict__ cl, uint64_t *__restrict__ keys,
+                            int32_t *__restrict__ perm);
+__global__ void sort_hist_kernel(int n, const uint64_t *__restrict__ keys,
+                                 const int32_t *__restrict__ vals, const int32_t *__restrict__ cid,
+                                 int shift, int nblocks, int32_t *__restrict__ hist);
 __global__ void sort_scatter_kernel(int n, const uint64_t *__restrict__ kin,
                                     const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-                                    int32_t *__restrict__ vout, int shift, int nblocks,
-                                    const int32_t *__restrict__ hist_off);
+                                    int32_t *__restrict__ vout, const int32_t *__restrict__ cid,
+                                    int shift, int nblocks, const int32_t *__restrict__ hist_off);
 
 namespace {
 
 constexpr int kMaxN = P3T_NOALLOC_MAX_N;
 constexpr int kTile = 4096;                       // items per sort block
 constexpr int kMaxBlocks = (kMaxN + kTile - 1) / kTile;
-constexpr size_t kMetaBytes = (sizeof(Meta) + 255) / 256 * 256;
+constexpr size_t kMetaBytes = (sizeof(Meta) + sizeof(Cluster) + 255) / 256 * 256;  // Meta, then Cluster
 constexpr size_t kKeysBytes = 8 * (size_t)kMaxN;
 constexpr size_t kPermBytes = 4 * (size_t)kMaxN;
 constexpr size_t kHistBytes = 4 * 256 * (size_t)kMaxBlocks;
@@ -98,6 +102,7 @@ extern "C" int p3t_morton_order_noalloc(int64_t n, const double *x, const double
     cudaStream_t s = (cudaStream_t)cuda_stream;
     char *p = (char *)base;
     Meta *meta = (Meta *)p;
+    Cluster *cl = (Cluster *)(p + sizeof(Meta) + (8 - sizeof(Meta) % 8) % 8);
     uint64_t *keys_alt = (uint64_t *)(p + kMetaBytes);
     int32_t *perm_alt = (int32_t *)(p + kMetaBytes + kKeysBytes);
     int32_t *hist = (int32_t *)(p + kMetaBytes + kKeysBytes + kPermBytes);
@@ -110,9 +115,10 @@ extern "C" int p3t_morton_order_noalloc(int64_t n, const double *x, const double
     // the previous call's latched error and counters must not leak into this one
     if (cudaMemsetAsync(meta, 0, sizeof(Meta), s) != cudaSuccess) return P3T_ERR_CUDA;
     init_meta_kernel<<<1, 64, 0, s>>>(meta);
-    bbox_kernel<<<2 * sm, 256, 0, s>>>(N, x, y, z, m, meta);
-    cube_kernel<<<1, 1, 0, s>>>(meta);
-    keys_kernel<<<grid_n, 256, 0, s>>>(N, x, y, z, meta, keys, perm);
+    init_clusters_kernel<<<1, 32, 0, s>>>(cl, 1);
+    bbox_kernel<<<2 * sm, 256, 0, s>>>(N, x, y, z, m, nullptr, cl, meta);
+    cube_kernel<<<1, 32, 0, s>>>(cl, 1);
+    keys_kernel<<<grid_n, 256, 0, s>>>(N, x, y, z, nullptr, cl, keys, perm);
     if (cudaGetLastError() != cudaSuccess) return P3T_ERR_CUDA;
     // 8 passes of 8 bits between the caller's arrays and the scratch copy;
     // after an even number of passes the result is back in the caller's arrays
@@ -121,11 +127,11 @@ extern "C" int p3t_morton_order_noalloc(int64_t n, const double *x, const double
     int32_t *pb[2] = {perm, perm_alt};
     for (int pass = 0; pass < 8; pass++) {
         const int shift = 8 * pass;
-        sort_hist_kernel<<<nb, 256, 0, s>>>(N, kb[pass & 1], shift, nb, hist);
+        sort_hist_kernel<<<nb, 256, 0, s>>>(N, kb[pass & 1], pb[pass & 1], nullptr, shift, nb, hist);
         e = scan_excl_i32_to_i32(hist, hist, 256 * nb, status, &meta->tickets[31], meta, s);
         if (e) return e;
         sort_scatter_kernel<<<nb, 256, 0, s>>>(N, kb[pass & 1], pb[pass & 1], kb[(pass + 1) & 1],
-                                               pb[(pass + 1) & 1], shift, nb, hist);
+                                               pb[(pass + 1) & 1], nullptr, shift, nb, hist);
         if (cudaGetLastError() != cudaSuccess) return P3T_ERR_CUDA;
     }
     int err = 0;

@@ -37,17 +37,27 @@ struct Meta {
     int level_start[kMaxLevelSlots];
     int level_count[kMaxLevelSlots];
     unsigned int tickets[32];      // work-distribution counters (reset per launch)
-    double cube[4];                // min.xyz, side (rule 1)
-    double frame[4];               // O.xyz (cube centre), R (bound on |x - O| per axis)
-    unsigned long long minmax[6];  // order-preserving encodings for the bbox reduction
     long long nbr_total;
     long long fallback_tests;      // FP64 decisions taken after an undecided FP32 filter
+};
+
+// ---- one cluster of a (possibly batched) build -----------------------------------
+struct Cluster {
+    double cube[4];                // min.xyz, side (rule 1)
+    double scale;                  // 2^21 / side
+    double frame[4];               // O.xyz (box centre), R (bound on |x - O| per axis)
+    unsigned long long minmax[6];  // order-preserving encodings for the bbox reduction
 };
 
 // ---- tree view passed by value to kernels ------------------------------------
 struct Tree {
     int n;
     int cap_nodes;
+    int n_clusters;        // independent clusters; cluster c's root is node c
+    const int64_t *seg;    // device cluster offsets [n_clusters + 1] (null: one cluster)
+    int32_t *cid;          // cluster of each particle, original order (null: one cluster)
+    int32_t *cid_s;        // cluster of each particle, key order
+    Cluster *cl;
     uint64_t *keys;
     int32_t *perm;
     double4_32a *sp;
@@ -286,6 +296,8 @@ struct p3t_ctx {
     int built;
     int built_precision;
     int counts_valid;  // neighbour counts of the current tree already in nbr_count
+    int cap_clusters;
+    p3t::Cluster *clusters;  // per-cluster table (separate allocation)
     int pending_err;  // host-side latched error
     // device memory
     p3t::Meta *meta;
@@ -305,8 +317,8 @@ struct p3t_ctx {
 namespace p3t {
 int ensure_capacity(p3t_ctx *c, long long n);
 int check_launch(p3t_ctx *c);
-int build_tree(p3t_ctx *c, int n, const double *x, const double *y, const double *z,
-               const double *m);
+int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *x,
+               const double *y, const double *z, const double *m);
 int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc, int64_t *np);
 int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, int64_t *total_dev,
                bool sync, int64_t *total_host);

@@ -370,17 +370,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
     Meta *meta = T.meta;
     const int ng = meta->n_groups;
     const int nn = meta->n_nodes;
-    const double Ox = meta->frame[0], Oy = meta->frame[1], Oz = meta->frame[2];
     const int tile = P.tile;
-    // FP32 filter band (|FP32 - FP64| of a squared distance, with a factor ~2
-    // to spare): k_rel*(d2 + r2) + k_abs*|t|_1 + k_sq, where every coordinate
-    // relative to O is within R and carries <= 2^-24 R rounding.  Outside a
-    // safe range of scales the filter is off and every test is exact FP64.
-    const float Rf = (float)meta->frame[3] * 1.0001f;
-    const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && P.rout2_f > 1e-20f && P.rout2_f < 1e30f;
     const float k_rel = 8.f * kU;
-    const float k_abs = 8.f * kU * Rf;
-    const float k_sq = 16.f * kU * kU * Rf * Rf;
 
     while (true) {
         int g = 0;
@@ -389,6 +380,18 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
         if (g >= ng) break;
         const int2 gr = T.grp[g];
         const double4_32a glo = T.glo[g], ghi = T.ghi[g];
+        // the group's cluster: its frame O, its root (node cid) and the filter band
+        // (|FP32 - FP64| of a squared distance, with a factor ~2 to spare):
+        // k_rel*(d2 + r2) + k_abs*|t|_1 + k_sq, every coordinate relative to O being
+        // within R and carrying <= 2^-24 R rounding.  Outside a safe range of scales
+        // the filter is off and every test is exact FP64.
+        const int cid = T.cid_s[gr.x];
+        const double *fr = T.cl[cid].frame;
+        const double Ox = fr[0], Oy = fr[1], Oz = fr[2];
+        const float Rf = (float)fr[3] * 1.0001f;
+        const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && P.rout2_f > 1e-20f && P.rout2_f < 1e30f;
+        const float k_abs = 8.f * kU * Rf;
+        const float k_sq = 16.f * kU * kU * Rf * Rf;
         GroupFrame F;
         F.cx = dmul(0.5, dadd(glo.x, ghi.x));
         F.cy = dmul(0.5, dadd(glo.y, ghi.y));
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
         Acc<Real, TPL> A;
         A.zero_all();
         int sp = 1;
-        if (lane == 0) W.stk[0] = pack_range(0, 1);
+        if (lane == 0) W.stk[0] = pack_range(cid, 1);
         __syncwarp();
         int cb = 0, lqn = 0, lqp = 0;
         long long ncell = 0, npart = 0;

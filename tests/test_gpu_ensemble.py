@@ -1,0 +1,93 @@
+"""Ensemble form: one batched build of independent clusters of uneven size.
+
+Each cluster's result from the batch must equal, bit for bit, the result of a
+build of that cluster alone (per-cluster cubes, frames and roots), and match
+the oracle's tree of that cluster."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2110_11658_b300 as p3t
+import synth
+from gpu_helpers import DEV, run_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _ensemble():
+    specs = [("plummer", 3000, "equal"), ("king", 1, "equal"), ("plummer", 33, "kroupa"),
+             ("king", 4096, "kroupa"), ("plummer", 2, "equal"), ("king", 777, "equal"),
+             ("plummer", 5000, "kroupa")]
+    cl = []
+    for k, (kind, n, masses) in enumerate(specs):
+        if n <= 2:
+            rng = np.random.default_rng(k)
+            p = rng.normal(size=(3, n)) * 0.1 + 3.0 * k
+            cl.append(synth.Cluster(p[0], p[1], p[2], np.full(n, 1.0 / n), *(np.zeros(n) for _ in range(3))))
+        else:
+            c = synth.make(kind, n, 100 + k, masses=masses, w0=5.0)
+            c.x = c.x + 5.0 * k  # clusters far apart and of different sizes
+            cl.append(c)
+    return cl
+
+
+def _concat(cl):
+    cat = lambda a: np.concatenate([getattr(c, a) for c in cl])  # noqa: E731
+    seg = np.zeros(len(cl) + 1, np.int64)
+    np.cumsum([c.n for c in cl], out=seg[1:])
+    return synth.Cluster(*(cat(a) for a in ("x", "y", "z", "m", "vx", "vy", "vz"))), seg
+
+
+@pytest.mark.parametrize("precision", [p3t.P3T_FP32_MIXED, p3t.P3T_FP64], ids=["mixed", "fp64"])
+def test_batch_equals_each_cluster_alone(precision):
+    cl = _ensemble()
+    all_, seg = _concat(cl)
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, group_size=32, precision=precision)
+    ctx = p3t.Context(prm)
+    x, y, z, m = to_dev(all_.x), to_dev(all_.y), to_dev(all_.z), to_dev(all_.m)
+    segd = torch.from_numpy(seg).to(DEV)
+    ctx.build_tree_batch(segd, x, y, z, m)
+    dt = ctx.acc_dtype
+    n = all_.n
+    a = [torch.empty(n, dtype=dt, device=DEV) for _ in range(3)]
+    pot = torch.empty(n, dtype=torch.float64, device=DEV)
+    ctx.far_force(*a, pot=pot)
+    offs = torch.empty(n + 1, dtype=torch.int64, device=DEV)
+    idx = torch.empty(50 * n, dtype=torch.int32, device=DEV)
+    tot = ctx.neighbours(offs, idx)
+    v = [to_dev(all_.vx), to_dev(all_.vy), to_dev(all_.vz)]
+    ctx.kick(1.0 / 256, *a, *v)
+    ctx.check()
+    ab = torch.stack(a, 1).double().cpu().numpy()
+    pb = pot.cpu().numpy()
+    ob, ib = offs.cpu().numpy(), idx[:tot].cpu().numpy()
+    vb = torch.stack(v, 1).cpu().numpy()
+    info = ctx.tree_info()
+    assert info["n"] == n
+    for k, c in enumerate(cl):
+        s0, s1 = seg[k], seg[k + 1]
+        g = run_gpu(c, prm, kick_dt=1.0 / 256)
+        assert np.array_equal(ab[s0:s1], g["a"])  # bit-identical
+        assert np.array_equal(pb[s0:s1], g["pot"])
+        assert np.array_equal(vb[s0:s1], g["v"])
+        rows_b = ob[s0:s1 + 1] - ob[s0]
+        assert np.array_equal(rows_b, g["offs"])
+        assert np.array_equal(ib[ob[s0]:ob[s1]] - s0, g["idx"])
+        t = oracle.Tree(c.x, c.y, c.z, c.m, 0.5, 0.05, leaf_cap=16, group_size=32)
+        f = t.far(0.005)
+        assert np.array_equal(g["g_cells"], f["n_cell"])
+    assert tot == ob[-1]
+
+
+def test_batch_rejects_bad_offsets():
+    c = synth.plummer(1000, 3)
+    ctx = p3t.Context(p3t.Params())
+    bad = torch.tensor([0, 600, 500, 1000], dtype=torch.int64, device=DEV)  # not increasing
+    ctx.build_tree_batch(bad, to_dev(c.x), to_dev(c.y), to_dev(c.z), to_dev(c.m))
+    assert ctx.status() == p3t.P3T_ERR_INVALID_INPUT
+    good = torch.tensor([0, 500, 1000], dtype=torch.int64, device=DEV)
+    ctx.build_tree_batch(good, to_dev(c.x), to_dev(c.y), to_dev(c.z), to_dev(c.m))
+    a = [torch.empty(1000, dtype=torch.float32, device=DEV) for _ in range(3)]
+    ctx.far_force(*a)
+    ctx.check()
