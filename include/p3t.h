@@ -95,16 +95,20 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *x, const double *y, cons
  * form): cluster k holds the particles [seg_offsets[k], seg_offsets[k+1]) of
  * the concatenated arrays x, y, z, m (device double[n]).  seg_offsets is a
  * DEVICE int64 array of n_clusters + 1 entries, 0 = seg_offsets[0] <
- * seg_offsets[1] < ... < seg_offsets[n_clusters] = n (every cluster non-empty;
- * a violation is reported as P3T_ERR_INVALID_INPUT).  Each cluster gets its own
- * bounding cube and tree exactly as p3t_build_tree would build it alone, so
- * every later call (far force, neighbours, kick) gives each cluster the same
- * result, bit for bit, as a build of that cluster alone; neighbour lists never
- * cross clusters.  Original indices in outputs refer to the concatenated order.
- * No host synchronisation: a whole step can be captured in a CUDA graph once
- * the context's scratch has been sized by an earlier build of the same n. */
+ * seg_offsets[1] < ... < seg_offsets[n_clusters] = n (every cluster non-empty).
+ * cluster_params: nullable DEVICE double array of 4 per cluster {theta, r_in,
+ * r_out, r_list} (meaning as in p3t_params); NULL gives every cluster the
+ * context's values.  Invalid offsets or radii are reported as
+ * P3T_ERR_INVALID_INPUT.  Each cluster gets its own bounding cube and tree
+ * exactly as p3t_build_tree would build it alone with its parameters, so every
+ * later call (far force, neighbours, kick) gives each cluster the same result,
+ * bit for bit, as a build of that cluster alone; neighbour lists never cross
+ * clusters.  Original indices in outputs refer to the concatenated order.  No
+ * host synchronisation: a whole step can be captured in a CUDA graph once the
+ * context's scratch has been sized by an earlier build of the same n. */
 int p3t_build_tree_batch(p3t_ctx *c, int32_t n_clusters, int64_t n, const int64_t *seg_offsets,
-                         const double *x, const double *y, const double *z, const double *m);
+                         const double *cluster_params, const double *x, const double *y,
+                         const double *z, const double *m);
 
 /* Far (regular) acceleration F_R of Eq. 3 for every particle of the last built
  * tree: the group-wise walk opens a cell iff it fails the opening-angle test

@@ -69,7 +69,7 @@ _sig = {
     "p3t_destroy": [_vp],
     "p3t_set_params": [_vp, C.POINTER(p3t_params)],
     "p3t_build_tree": [_vp, _i64, _vp, _vp, _vp, _vp],
-    "p3t_build_tree_batch": [_vp, C.c_int32, _i64, _vp, _vp, _vp, _vp, _vp],
+    "p3t_build_tree_batch": [_vp, C.c_int32, _i64, _vp, _vp, _vp, _vp, _vp, _vp],
     "p3t_far_force": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "p3t_neighbours": [_vp, _vp, _vp, _i64, C.POINTER(_i64)],
     "p3t_neighbours_async": [_vp, _vp, _vp, _i64, _vp],
@@ -188,14 +188,16 @@ class Context:
         _check(_lib.p3t_build_tree(self._h, n, *args), "p3t_build_tree")
         self.n = n
 
-    def build_tree_batch(self, seg_offsets, x, y, z, m):
-        """Ensemble build: seg_offsets is a CUDA int64 tensor of n_clusters + 1 offsets."""
+    def build_tree_batch(self, seg_offsets, x, y, z, m, cluster_params=None):
+        """Ensemble build: seg_offsets is a CUDA int64 tensor of n_clusters + 1 offsets;
+        cluster_params an optional CUDA float64 (n_clusters, 4) tensor {theta, r_in, r_out, r_list}."""
         t = self._torch
         n = x.numel()
         nc = seg_offsets.numel() - 1
         args = [_ptr(a, t.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")]
+        cp = _ptr(cluster_params, t.float64, 4 * nc, "cluster_params")
         _check(_lib.p3t_build_tree_batch(self._h, nc, n, _ptr(seg_offsets, t.int64, nc + 1, "seg_offsets"),
-                                         *args), "p3t_build_tree_batch")
+                                         cp, *args), "p3t_build_tree_batch")
         self.n = n
 
     def far_force(self, ax, ay, az, pot=None, n_cell=None, n_part=None):

@@ -59,6 +59,40 @@ __global__ void init_clusters_kernel(Cluster *cl, int C)
         }
 }
 
+// physics of every cluster: the batch's table {theta, r_in, r_out, r_list} or the
+// context's values, with the derived constants the walk and neighbour kernels use
+__global__ void cluster_params_kernel(Cluster *cl, int C, const double *__restrict__ prm,
+                                      double theta, double r_in, double r_out, double r_list,
+                                      Meta *meta)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    double th = theta, ri = r_in, ro = r_out, rl = r_list;
+    if (prm) {
+        th = prm[4 * c], ri = prm[4 * c + 1], ro = prm[4 * c + 2], rl = prm[4 * c + 3];
+        const bool ok = th >= 0.0 && isfinite(th) && ri >= 0.0 && ro > ri && isfinite(ro) &&
+                        rl >= 0.0 && isfinite(rl);
+        if (!ok) {
+            latch_error(meta, P3T_ERR_INVALID_INPUT);
+            th = theta, ri = r_in, ro = r_out, rl = r_list;
+        }
+    }
+    Cluster &K = cl[c];
+    K.theta = th;
+    K.r_in = ri;
+    K.r_out = ro;
+    K.r_list = rl;
+    K.inv_dr_d = ddiv(1.0, dsub(ro, ri));
+    K.rout2_d = dmul(ro, ro);
+    K.rl2_d = dmul(rl, rl);
+    K.inv_dr_f = (float)K.inv_dr_d;
+    K.rin_dr_f = (float)dmul(ri, K.inv_dr_d);
+    K.rout2_f = (float)K.rout2_d;
+    K.rl2_f = (float)K.rl2_d;
+    K.rl_f = (float)rl;
+    K.counted = rl > 0.0 && rl <= ro;
+}
+
 // cluster of every particle from the offsets (validated: 0 = seg[0] < ... < seg[C] = n)
 __global__ void __launch_bounds__(kBuildThreads)
     cid_kernel(int n, int C, const int64_t *__restrict__ seg, int32_t *__restrict__ cid, Meta *meta)
@@ -532,8 +566,10 @@ __global__ void __launch_bounds__(kBuildThreads) group_finish_kernel(Tree T, int
 
 template <bool Q64>
 __device__ void write_node(Tree &T, int k, double M, const double com[3], const double lo[3],
-                           const double hi[3], const double *q, double theta, int4 tp)
+                           const double hi[3], const double *q, double, int4 tp)
 {
+    const Cluster &K = T.cl[T.cid_s[tp.x < T.n ? tp.x : 0]];
+    const double theta = K.theta;
     // opening radius l/theta + delta
     double l = dsub(hi[0], lo[0]);
     if (dsub(hi[1], lo[1]) > l) l = dsub(hi[1], lo[1]);
@@ -563,7 +599,7 @@ __device__ void write_node(Tree &T, int k, double M, const double com[3], const 
         q2[1] = make_float2((float)q[2], (float)q[3]);
         q2[2] = make_float2((float)q[4], (float)q[5]);
     }
-    const double *O = T.cl[T.cid_s[tp.x < T.n ? tp.x : 0]].frame;
+    const double *O = K.frame;
     const bool leaf = tp.z < 0;
     float chx, chy, chz, clx, cly, clz;
     ds_split(dsub(com[0], O[0]), chx, clx);
@@ -730,8 +766,8 @@ __global__ void __launch_bounds__(kBuildThreads) moments_level_kernel(Tree T, in
 }
 
 // ---------------------------------------------------------------------------
-int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *x,
-               const double *y, const double *z, const double *m)
+int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *cprm,
+               const double *x, const double *y, const double *z, const double *m)
 {
     cudaStream_t s = c->stream;
     Tree &T = c->tree;
@@ -747,6 +783,8 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
 
     init_meta_kernel<<<1, 64, 0, s>>>(M);
     init_clusters_kernel<<<grid_c, 128, 0, s>>>(T.cl, n_clusters);
+    cluster_params_kernel<<<grid_c, 128, 0, s>>>(T.cl, n_clusters, cprm, P.theta, P.r_in, P.r_out,
+                                                 P.r_list, M);
     if (seg) cid_kernel<<<(n > n_clusters ? grid_n : grid_c + 1), kBuildThreads, 0, s>>>(n, n_clusters, seg, T.cid, M);
     bbox_kernel<<<persistent, kBuildThreads, 0, s>>>(n, x, y, z, m, cid, T.cl, M);
     cube_kernel<<<grid_c, 128, 0, s>>>(T.cl, n_clusters);

@@ -194,8 +194,9 @@ int p3t_set_params(p3t_ctx *c, const p3t_params *p)
     return P3T_OK;
 }
 
-static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *seg, const double *x,
-                        const double *y, const double *z, const double *m)
+static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *seg,
+                        const double *cprm, const double *x, const double *y, const double *z,
+                        const double *m)
 {
     if (!c || !x || !y || !z || !m) return P3T_ERR_INVALID_ARG;
     if (n <= 0 || n >= (1LL << 31) - 1) return P3T_ERR_INVALID_ARG;
@@ -220,7 +221,9 @@ static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *se
     c->tree.cl = c->clusters;
     c->built = 0;
     c->counts_valid = 0;
-    e = build_tree(c, (int)n, n_clusters, seg, x, y, z, m);
+    c->walk_counted = 0;
+    c->uniform_params = cprm == nullptr;
+    e = build_tree(c, (int)n, n_clusters, seg, cprm, x, y, z, m);
     if (e) return e;
     c->n = (int)n;
     c->built = 1;
@@ -231,14 +234,15 @@ static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *se
 int p3t_build_tree(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
                    const double *m)
 {
-    return build_common(c, n, 1, nullptr, x, y, z, m);
+    return build_common(c, n, 1, nullptr, nullptr, x, y, z, m);
 }
 
 int p3t_build_tree_batch(p3t_ctx *c, int32_t n_clusters, int64_t n, const int64_t *seg_offsets,
-                         const double *x, const double *y, const double *z, const double *m)
+                         const double *cluster_params, const double *x, const double *y,
+                         const double *z, const double *m)
 {
     if (!seg_offsets) return P3T_ERR_INVALID_ARG;
-    return build_common(c, n, n_clusters, seg_offsets, x, y, z, m);
+    return build_common(c, n, n_clusters, seg_offsets, cluster_params, x, y, z, m);
 }
 
 int p3t_far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *n_cell_inter,

@@ -34,6 +34,7 @@ struct NbrArgs {
     const int64_t *offs;   // row offsets (fill pass)
     int32_t *idx;          // entries (fill pass)
     long long capacity;
+    int skip_counted;      // count pass: skip clusters whose neighbours the walk counted
     unsigned int *ticket;
 };
 
@@ -72,11 +73,16 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         if (g >= ng) break;
         const int2 gr = T.grp[g];
         const double4_32a glo = T.glo[g], ghi = T.ghi[g];
-        const int cid = T.cid_s[gr.x];  // the group's cluster: frame, root, filter band
-        const double *fr = T.cl[cid].frame;
+        const int cid = T.cid_s[gr.x];  // the group's cluster: frame, root, radius, band
+        const Cluster &K = T.cl[cid];
+        // counting: clusters the far-force walk already counted are skipped
+        if (!FILL && P.skip_counted && K.counted) continue;
+        const double *fr = K.frame;
         const double Ox = fr[0], Oy = fr[1], Oz = fr[2];
         const float Rf = (float)fr[3] * 1.0001f;
-        const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && P.rl2_f > 1e-20f && P.rl2_f < 1e30f;
+        const float rl_f = K.rl_f, rl2_f = K.rl2_f;
+        const double rl2_d = K.rl2_d;
+        const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && rl2_f > 1e-20f && rl2_f < 1e30f;
         const float k_abs = 8.f * kUn * Rf, k_sq = 16.f * kUn * kUn * Rf * Rf;
         const double cgx = dmul(0.5, dadd(glo.x, ghi.x));
         const double cgy = dmul(0.5, dadd(glo.y, ghi.y));
@@ -116,8 +122,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         A *= 1.0001f;
         // band of the pair test (FP32 vs FP64 squared distance), factor ~2 spare:
         // coordinates relative to c_g carry <= 2.01 u |x - c_g| + 8 u^2 R
-        const float tpair = kUn * (24.f * P.rl2_f + 32.f * A * P.rl_f + 128.f * kUn * Rf * P.rl_f) +
-                            64.f * kUn * kUn * (A + 2.f * P.rl_f) * (A + 2.f * P.rl_f);
+        const float tpair = kUn * (24.f * rl2_f + 32.f * A * rl_f + 128.f * kUn * Rf * rl_f) +
+                            64.f * kUn * kUn * (A + 2.f * rl_f) * (A + 2.f * rl_f);
         const bool pair_filter = filter_ok && A < 1e12f;
 
         int sp = 1;
@@ -146,11 +152,11 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                         float uy = fmaxf(fmaxf(b.y - ghy, gly - cc.y), 0.f);
                         float uz = fmaxf(fmaxf(b.z - ghz, glz - cc.z), 0.f);
                         float e2 = ux * ux + uy * uy + uz * uz;
-                        float tol = k_rel * (e2 + P.rl2_f) + k_abs * (ux + uy + uz) + k_sq;
-                        bb = e2 < P.rl2_f - tol ? 1 : (e2 > P.rl2_f + tol ? 0 : 2);
+                        float tol = k_rel * (e2 + rl2_f) + k_abs * (ux + uy + uz) + k_sq;
+                        bb = e2 < rl2_f - tol ? 1 : (e2 > rl2_f + tol ? 0 : 2);
                     }
                     if (bb == 2) {
-                        bb = dist2_box_box(glo, ghi, T.lo[node], T.hi[node]) < P.rl2_d;
+                        bb = dist2_box_box(glo, ghi, T.lo[node], T.hi[node]) < rl2_d;
                         if (filter_ok) atomicAdd((unsigned long long *)&meta->fallback_tests, 1ULL);
                     }
                     open = bb == 1;
@@ -221,12 +227,12 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                         float dx = s.x - px[t], dy = s.y - py[t], dz = s.z - pz[t];
                         float r2 = dx * dx + dy * dy + dz * dz;
                         int in = 2;
-                        if (pair_filter) in = r2 < P.rl2_f - tpair ? 1 : (r2 > P.rl2_f + tpair ? 0 : 2);
+                        if (pair_filter) in = r2 < rl2_f - tpair ? 1 : (r2 > rl2_f + tpair ? 0 : 2);
                         if (in == 2) {
                             const double4_32a a = T.sp[si[t]], b = T.sp[j];
                             double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
                             double d2 = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez));
-                            in = d2 < P.rl2_d;
+                            in = d2 < rl2_d;
                         }
                         if (in) {
                             if (FILL) P.idx[base[t] + cnt[t]] = W.po[k];
@@ -395,7 +401,8 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
     a.capacity = capacity;
     a.ticket = &c->meta->tickets[23];
     int e;
-    if (!c->counts_valid) {  // the far-force walk did not count (r_list > r_out or FP64)
+    a.skip_counted = c->walk_counted;
+    if (!c->counts_valid) {  // the far-force walk did not count every cluster
         e = dispatch_nbr<false>(c, a);
         if (e) return e;
         c->counts_valid = 1;

@@ -47,7 +47,8 @@ namespace {
 constexpr int kMaxN = P3T_NOALLOC_MAX_N;
 constexpr int kTile = 4096;                       // items per sort block
 constexpr int kMaxBlocks = (kMaxN + kTile - 1) / kTile;
-constexpr size_t kMetaBytes = (sizeof(Meta) + sizeof(Cluster) + 255) / 256 * 256;  // Meta, then Cluster
+constexpr size_t kClusterOff = (sizeof(Meta) + 15) / 16 * 16;                     // Cluster after Meta
+constexpr size_t kMetaBytes = (kClusterOff + sizeof(Cluster) + 255) / 256 * 256;
 constexpr size_t kKeysBytes = 8 * (size_t)kMaxN;
 constexpr size_t kPermBytes = 4 * (size_t)kMaxN;
 constexpr size_t kHistBytes = 4 * 256 * (size_t)kMaxBlocks;
@@ -102,7 +103,7 @@ extern "C" int p3t_morton_order_noalloc(int64_t n, const double *x, const double
     cudaStream_t s = (cudaStream_t)cuda_stream;
     char *p = (char *)base;
     Meta *meta = (Meta *)p;
-    Cluster *cl = (Cluster *)(p + sizeof(Meta) + (8 - sizeof(Meta) % 8) % 8);
+    Cluster *cl = (Cluster *)(p + kClusterOff);
     uint64_t *keys_alt = (uint64_t *)(p + kMetaBytes);
     int32_t *perm_alt = (int32_t *)(p + kMetaBytes + kKeysBytes);
     int32_t *hist = (int32_t *)(p + kMetaBytes + kKeysBytes + kPermBytes);

@@ -47,6 +47,11 @@ struct Cluster {
     double scale;                  // 2^21 / side
     double frame[4];               // O.xyz (box centre), R (bound on |x - O| per axis)
     unsigned long long minmax[6];  // order-preserving encodings for the bbox reduction
+    // physics of this cluster (the context's parameters, or the batch's table)
+    double theta, r_in, r_out, r_list;
+    double rout2_d, rl2_d, inv_dr_d;        // r_out^2, r_list^2, 1/(r_out - r_in)
+    float rout2_f, rl2_f, rl_f, inv_dr_f, rin_dr_f;
+    int counted;                   // 1: the mixed far-force walk counts its neighbours
 };
 
 // ---- tree view passed by value to kernels ------------------------------------
@@ -296,6 +301,8 @@ struct p3t_ctx {
     int built;
     int built_precision;
     int counts_valid;  // neighbour counts of the current tree already in nbr_count
+    int walk_counted;  // the far-force walk counted the neighbours of clusters with `counted`
+    int uniform_params;  // every cluster uses the context's parameters
     int cap_clusters;
     p3t::Cluster *clusters;  // per-cluster table (separate allocation)
     int pending_err;  // host-side latched error
@@ -317,8 +324,8 @@ struct p3t_ctx {
 namespace p3t {
 int ensure_capacity(p3t_ctx *c, long long n);
 int check_launch(p3t_ctx *c);
-int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *x,
-               const double *y, const double *z, const double *m);
+int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *cprm,
+               const double *x, const double *y, const double *z, const double *m);
 int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc, int64_t *np);
 int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, int64_t *total_dev,
                bool sync, int64_t *total_host);

@@ -264,8 +264,9 @@ struct NbrCount {
 };
 
 template <typename Real, int TPL, bool POT, bool NBR>
-__device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkArgs &P, int nleaves,
-                                           int nparts, const GroupFrame &F, const Real (&px)[TPL],
+__device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkArgs &P,
+                                           const Cluster &K, int nleaves, int nparts,
+                                           const GroupFrame &F, const Real (&px)[TPL],
                                            const Real (&py)[TPL], const Real (&pz)[TPL],
                                            Acc<Real, TPL> &A, NbrCount<TPL> &NC)
 {
@@ -283,8 +284,8 @@ __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkAr
         carry += __shfl_sync(0xffffffffu, inc, 31);
     }
     __syncwarp();
-    const Real inv_dr = kMixed ? Real(P.inv_dr_f) : Real(P.inv_dr_d);
-    const Real rin_dr = kMixed ? Real(P.rin_dr_f) : Real(P.r_in_d * P.inv_dr_d);
+    const Real inv_dr = kMixed ? Real(K.inv_dr_f) : Real(K.inv_dr_d);
+    const Real rin_dr = kMixed ? Real(K.rin_dr_f) : Real(K.r_in * K.inv_dr_d);
     for (int c0 = 0; c0 < nparts; c0 += 32) {
         int pos = c0 + lane;
         if (pos < nparts) {
@@ -345,7 +346,7 @@ __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkAr
                         const int sj = W.pj[k];
                         const double4_32a a = P.T.sp[NC.si[t] < 0 ? sj : NC.si[t]], b = P.T.sp[sj];
                         const double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
-                        NC.cnt[t] += dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < P.rl2_d;
+                        NC.cnt[t] += dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < K.rl2_d;
                     }
                 }
             }
@@ -386,10 +387,14 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
         // within R and carrying <= 2^-24 R rounding.  Outside a safe range of scales
         // the filter is off and every test is exact FP64.
         const int cid = T.cid_s[gr.x];
-        const double *fr = T.cl[cid].frame;
+        const Cluster &K = T.cl[cid];
+        const double *fr = K.frame;
         const double Ox = fr[0], Oy = fr[1], Oz = fr[2];
         const float Rf = (float)fr[3] * 1.0001f;
-        const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && P.rout2_f > 1e-20f && P.rout2_f < 1e30f;
+        const float rout2_f = K.rout2_f;
+        const double rout2_d = K.rout2_d;
+        const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && rout2_f > 1e-20f && rout2_f < 1e30f;
+        const bool count_here = NBR && K.counted;
         const float k_abs = 8.f * kU * Rf;
         const float k_sq = 16.f * kU * kU * Rf * Rf;
         GroupFrame F;
@@ -434,10 +439,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
             const float A = amax * 1.0001f;
-            const float band = kU * (24.f * P.rl2_f + 32.f * A * P.rl_f + 128.f * kU * Rf * P.rl_f) +
-                               64.f * kU * kU * (A + 2.f * P.rl_f) * (A + 2.f * P.rl_f);
-            NC.lo = filter_ok ? P.rl2_f - band : -1.f;        // filter off: every pair to FP64
-            NC.hi = filter_ok ? P.rl2_f + band : INFINITY;
+            const float band = kU * (24.f * K.rl2_f + 32.f * A * K.rl_f + 128.f * kU * Rf * K.rl_f) +
+                               64.f * kU * kU * (A + 2.f * K.rl_f) * (A + 2.f * K.rl_f);
+            NC.lo = filter_ok ? K.rl2_f - band : -1.f;        // filter off: every pair to FP64
+            NC.hi = filter_ok ? K.rl2_f + band : INFINITY;
+            if (!count_here) NC.lo = NC.hi = -INFINITY;      // this cluster is counted elsewhere
         }
         Acc<Real, TPL> A;
         A.zero_all();
@@ -489,8 +495,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
                         const float uy = fmaxf(fmaxf(b.y - ghy, gly - c.y), 0.f);
                         const float uz = fmaxf(fmaxf(b.z - ghz, glz - c.z), 0.f);
                         const float e2 = ux * ux + uy * uy + uz * uz;
-                        const float tol2 = k_rel * (e2 + P.rout2_f) + k_abs * (ux + uy + uz) + k_sq;
-                        bb = e2 < P.rout2_f - tol2 ? 1 : (e2 > P.rout2_f + tol2 ? 0 : 2);
+                        const float tol2 = k_rel * (e2 + rout2_f) + k_abs * (ux + uy + uz) + k_sq;
+                        bb = e2 < rout2_f - tol2 ? 1 : (e2 > rout2_f + tol2 ? 0 : 2);
                     }
                     if (mac == 1 || bb == 1) {
                         open = true;
@@ -500,7 +506,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
                         fb = filter_ok;
                         const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
                         open = dist2_point_box(cm.x, cm.y, cm.z, glo, ghi) < cl.w ||
-                               dist2_box_box(glo, ghi, cl, ch) < P.rout2_d;
+                               dist2_box_box(glo, ghi, cl, ch) < rout2_d;
                     }
                 } else {
                     const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
@@ -508,7 +514,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
                     cinfo = __float_as_int(rec[1].w);
                     ccount = __float_as_int(rec[2].w);
                     open = dist2_point_box(cm.x, cm.y, cm.z, glo, ghi) < cl.w ||
-                           dist2_box_box(glo, ghi, cl, ch) < P.rout2_d;
+                           dist2_box_box(glo, ghi, cl, ch) < rout2_d;
                 }
                 is_leaf = cinfo < 0;
             }
@@ -581,12 +587,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
                 cb = 0;
             }
             if (lqp >= tile) {
-                eval_parts<Real, TPL, POT, NBR>(W, P, lqn, lqp, F, px, py, pz, A, NC);
+                eval_parts<Real, TPL, POT, NBR>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
                 lqn = lqp = 0;
             }
         }
         if (cb > 0) eval_cells<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
-        if (lqp > 0) eval_parts<Real, TPL, POT, NBR>(W, P, lqn, lqp, F, px, py, pz, A, NC);
+        if (lqp > 0) eval_parts<Real, TPL, POT, NBR>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
 
         // ---- results, scattered to the original order
 #pragma unroll
@@ -605,7 +611,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
                     ((double *)P.az)[o] = (double)A.s[t][2];
                     if (POT) P.pot[o] = (double)A.s[t][3];
                 }
-                if (NBR) P.nbr_count[o] = NC.cnt[t] - 1;  // minus the pair with itself
+                if (count_here) P.nbr_count[o] = NC.cnt[t] - 1;  // minus the pair with itself
             }
         }
         if (lane == 0) {
@@ -681,8 +687,11 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     a.rl2_d = P.r_list * P.r_list;
     a.rl_f = (float)P.r_list;
     a.rl2_f = (float)a.rl2_d;
-    // count neighbours in the walk when every neighbour pair lies in an opened leaf
-    const bool fuse_nbr = c->built_precision == P3T_FP32_MIXED && P.r_list > 0.0 && P.r_list <= P.r_out;
+    // count neighbours in the walk for the clusters whose neighbour pairs all lie in
+    // opened leaves (0 < r_list <= r_out); with the context's parameters the host
+    // knows whether that holds, with a per-cluster table the walk decides per group
+    const bool fuse_nbr = c->built_precision == P3T_FP32_MIXED &&
+                          (!c->uniform_params || (P.r_list > 0.0 && P.r_list <= P.r_out));
     a.nbr_count = fuse_nbr ? c->nbr_count : nullptr;
     if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
         return P3T_ERR_CUDA;
@@ -695,7 +704,10 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
         e = dispatch_tpl<float, true>(c, a, want_pot, quad);
     else
         e = dispatch_tpl<float, false>(c, a, want_pot, quad);
-    if (e == P3T_OK && fuse_nbr) c->counts_valid = 1;
+    if (e == P3T_OK && fuse_nbr) {
+        c->walk_counted = 1;
+        c->counts_valid = c->uniform_params;  // every cluster counted
+    }
     return e;
 }
 

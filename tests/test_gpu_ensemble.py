@@ -91,3 +91,46 @@ def test_batch_rejects_bad_offsets():
     a = [torch.empty(1000, dtype=torch.float32, device=DEV) for _ in range(3)]
     ctx.far_force(*a)
     ctx.check()
+
+
+@pytest.mark.parametrize("precision", [p3t.P3T_FP32_MIXED, p3t.P3T_FP64], ids=["mixed", "fp64"])
+def test_batch_with_per_cluster_parameters(precision):
+    # radii by the paper's rule per cluster size (Eqs. 20-25); one cluster lists
+    # neighbours beyond r_out (counted by the count pass, not the walk) and one
+    # asks for no neighbours at all
+    cl = _ensemble()
+    all_, seg = _concat(cl)
+    rows = []
+    for k, c in enumerate(cl):
+        rc = synth.paper_run_params(max(c.n, 64))["r_cut"]
+        theta = (0.3, 0.5, 0.7)[k % 3]
+        r_list = rc if k not in (3, 5) else (1.5 * rc if k == 3 else 0.0)
+        rows.append([theta, 0.1 * rc, rc, r_list])
+    cprm = np.array(rows, dtype=np.float64)
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, group_size=32, precision=precision)
+    ctx = p3t.Context(prm)
+    n = all_.n
+    ctx.build_tree_batch(torch.from_numpy(seg).to(DEV), to_dev(all_.x), to_dev(all_.y), to_dev(all_.z),
+                         to_dev(all_.m), cluster_params=torch.from_numpy(cprm).to(DEV))
+    a = [torch.empty(n, dtype=ctx.acc_dtype, device=DEV) for _ in range(3)]
+    ctx.far_force(*a)
+    offs = torch.empty(n + 1, dtype=torch.int64, device=DEV)
+    idx = torch.empty(50 * n, dtype=torch.int32, device=DEV)
+    tot = ctx.neighbours(offs, idx)
+    ctx.check()
+    ab = torch.stack(a, 1).double().cpu().numpy()
+    ob, ib = offs.cpu().numpy(), idx[:tot].cpu().numpy()
+    for k, c in enumerate(cl):
+        th, ri, ro, rl = cprm[k]
+        s0, s1 = seg[k], seg[k + 1]
+        g = run_gpu(c, p3t.Params(theta=th, r_in=ri, r_out=ro, r_list=rl, group_size=32, precision=precision))
+        assert np.array_equal(ab[s0:s1], g["a"])
+        assert np.array_equal(ob[s0:s1 + 1] - ob[s0], g["offs"])
+        assert np.array_equal(ib[ob[s0]:ob[s1]] - s0, g["idx"])
+        o2, i2 = oracle.neighbours_brute(c.x, c.y, c.z, rl)
+        assert np.array_equal(g["offs"], o2) and np.array_equal(g["idx"], i2)
+    bad = cprm.copy()
+    bad[2, 1] = bad[2, 2] * 2  # r_in > r_out
+    ctx.build_tree_batch(torch.from_numpy(seg).to(DEV), to_dev(all_.x), to_dev(all_.y), to_dev(all_.z),
+                         to_dev(all_.m), cluster_params=torch.from_numpy(bad).to(DEV))
+    assert ctx.status() == p3t.P3T_ERR_INVALID_INPUT
