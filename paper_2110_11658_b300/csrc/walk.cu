@@ -16,7 +16,12 @@
 // Accepted cells (monopole + quadrupole, W = 1) and opened leaves (particle
 // terms weighted by W) are queued in shared memory and evaluated once `tile`
 // of them are queued: every lane holds TPL target particles in registers and
-// loops over the queue, read by broadcast.  Relative coordinates x_source - c_g
+// loops over the queue, read by broadcast.  In the mixed form the queue is
+// pair-interleaved ({x_k, x_k+1, y_k, y_k+1}, ...) and two sources are
+// evaluated at once with the packed FP32x2 instructions of sm_100+ (one
+// instruction per two multiply-adds), which halves the issue slots of the
+// arithmetic; an odd tail is padded with a massless copy of its partner,
+// whose terms are exactly zero.  Relative coordinates x_source - c_g
 // and x_i - c_g (c_g the group-box centre) are formed from double-single
 // splits of the FP64 coordinates (hi + lo FP32 pairs made once per particle
 // and node in FP64 by the build), which gives the FP32 difference to within
@@ -30,6 +35,7 @@
 // band + exact FP64 decision as the neighbour kernels, so p3t_neighbours can
 // skip its counting pass.
 #include <cstdint>
+#include <type_traits>
 
 #include "p3t_internal.cuh"
 
@@ -38,6 +44,9 @@ namespace p3t {
 constexpr int kWalkWarps = 4;                // warps per block
 constexpr int kStackCap = 32 * 22 + 64;      // ranges per warp; see the bound below
 constexpr float kU = 5.9604644775390625e-8f;  // 2^-24, FP32 unit round-off
+constexpr int kCellPairUnroll = 2;           // pairs of cells per unrolled iteration
+constexpr int kPartPairUnroll = 2;           // pairs of particles per unrolled iteration
+constexpr int kMinBlocksTpl1 = 5;            // resident blocks per SM at TPL = 1 (96 registers)
 
 // Stack bound: children ranges are pushed so that the stack stays sorted by
 // level (deepest on top).  Ranges of level l are created only while popping
@@ -114,11 +123,38 @@ __device__ __forceinline__ double to_real<double>(double v)
 }
 
 
+// packed FP32x2 arithmetic (per component identical to the scalar fmaf/__fmul_rn/__fadd_rn)
+__device__ __forceinline__ float2 f2(float a)
+{
+    return make_float2(a, a);
+}
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c)
+{
+    return __ffma2_rn(a, b, c);
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b)
+{
+    return __fmul2_rn(a, b);
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b)
+{
+    return __fadd2_rn(a, b);
+}
+
+// r^2 below which 1/r is clamped in the particle loop: keeps (1/r)^3 finite for
+// coincident pairs, whose weight W is then exactly 0 (r = 0 < r_in, or x = 0);
+// for r_in >= 4.5e-13 the clamp never touches a pair with W > 0
+constexpr float kR2Min = 4e-26f;
+
 // shared-memory carve-up of one warp
 template <typename Real>
 struct WarpSmem {
     using R4 = typename Vec4<Real>::T;
     using R2 = typename Vec4<Real>::T2;
+    // mixed form: cpos..cqb hold pairs of cells, 5 float4 per pair:
+    // {-x0, -x1, -y0, -y1} {-z0, -z1, -M0, -M1} {Qxx} {Qxy} / {Qxz} {Qyy} / {Qyz} {Qzz}
+    // (each {} one float2 of the two cells), and pp holds pairs of particles,
+    // 2 float4 per pair: {x0, x1, y0, y1} {z0, z1, m0, m1}
     int *stk;
     R4 *cpos;  // {dx, dy, dz, M} of accepted cells, relative to c_g
     R4 *cqa;   // {Qxx, Qxy, Qxz, Qyy}
@@ -188,6 +224,37 @@ struct Acc {
                     s[t][k] += p[t][k];
                 }
                 p[t][k] = Real(0);
+            }
+    }
+};
+
+// mixed form: partial sums of the current tile as float2 (even / odd sources)
+template <int TPL>
+struct AccX2 {
+    float s[TPL][4];
+    float c[TPL][4];
+    float2 p[TPL][4];
+    __device__ void zero_all()
+    {
+#pragma unroll
+        for (int t = 0; t < TPL; t++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                s[t][k] = c[t][k] = 0.f;
+                p[t][k] = make_float2(0.f, 0.f);
+            }
+    }
+    __device__ void fold()
+    {
+#pragma unroll
+        for (int t = 0; t < TPL; t++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const float y = (p[t][k].x + p[t][k].y) - c[t][k];
+                const float u = s[t][k] + y;
+                c[t][k] = (u - s[t][k]) - y;
+                s[t][k] = u;
+                p[t][k] = make_float2(0.f, 0.f);
             }
     }
 };
@@ -356,8 +423,208 @@ __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkAr
     A.fold();
 }
 
+// Mixed form, two queued cells at a time (layout above); same terms as eval_cells.
+template <int TPL, bool POT, bool QUAD>
+__device__ __forceinline__ void eval_cells_x2(const WarpSmem<float> &W, int ncells, const float (&px)[TPL],
+                                              const float (&py)[TPL], const float (&pz)[TPL],
+                                              AccX2<TPL> &A)
+{
+    const float4 *cq = reinterpret_cast<const float4 *>(W.cpos);
+    __syncwarp();
+    if ((ncells & 1) && (threadIdx.x & 31) == 0) {
+        // pad: the partner's position with M = 0 and Q = 0 adds exactly zero
+        float *b = reinterpret_cast<float *>(W.cpos) + 20 * (ncells >> 1);
+        b[1] = b[0], b[3] = b[2], b[5] = b[4];
+        b[7] = b[9] = b[11] = b[13] = b[15] = b[17] = b[19] = 0.f;
+    }
+    __syncwarp();
+    float2 PX[TPL], PY[TPL], PZ[TPL];
+#pragma unroll
+    for (int t = 0; t < TPL; t++) PX[t] = f2(px[t]), PY[t] = f2(py[t]), PZ[t] = f2(pz[t]);
+    const int npairs = (ncells + 1) >> 1;
+#pragma unroll kCellPairUnroll
+    for (int k = 0; k < npairs; k++) {
+        const float4 a0 = cq[5 * k], a1 = cq[5 * k + 1];
+        const float2 NX = make_float2(a0.x, a0.y), NY = make_float2(a0.z, a0.w);
+        const float2 NZ = make_float2(a1.x, a1.y), NM = make_float2(a1.z, a1.w);
+        float2 Qxx, Qxy, Qxz, Qyy, Qyz, Qzz;
+        if (QUAD) {
+            const float4 a2 = cq[5 * k + 2], a3 = cq[5 * k + 3], a4 = cq[5 * k + 4];
+            Qxx = make_float2(a2.x, a2.y), Qxy = make_float2(a2.z, a2.w);
+            Qxz = make_float2(a3.x, a3.y), Qyy = make_float2(a3.z, a3.w);
+            Qyz = make_float2(a4.x, a4.y), Qzz = make_float2(a4.z, a4.w);
+        }
+#pragma unroll
+        for (int t = 0; t < TPL; t++) {
+            // r = x_i - com;  a = r^-3 [(-M - 5/2 (r.Q.r)/r^4) r + (Q r)/r^2]
+            const float2 rx = fadd2(PX[t], NX), ry = fadd2(PY[t], NY), rz = fadd2(PZ[t], NZ);
+            float2 r2 = fmul2(rx, rx);
+            r2 = ffma2(ry, ry, r2);
+            r2 = ffma2(rz, rz, r2);
+            const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 q = fmul2(ri, ri);
+            const float2 ri3 = fmul2(ri, q);
+            if (QUAD) {
+                float2 qx = fmul2(Qxx, rx), qy = fmul2(Qxy, rx), qz = fmul2(Qxz, rx);
+                qx = ffma2(Qxy, ry, qx), qy = ffma2(Qyy, ry, qy), qz = ffma2(Qyz, ry, qz);
+                qx = ffma2(Qxz, rz, qx), qy = ffma2(Qyz, rz, qy), qz = ffma2(Qzz, rz, qz);
+                qx = fmul2(qx, q), qy = fmul2(qy, q), qz = fmul2(qz, q);
+                float2 rqr4 = fmul2(rx, qx);
+                rqr4 = ffma2(ry, qy, rqr4);
+                rqr4 = ffma2(rz, qz, rqr4);
+                rqr4 = fmul2(rqr4, q);  // r.Q.r / r^4
+                const float2 cf = ffma2(f2(-2.5f), rqr4, NM);
+                A.p[t][0] = ffma2(ri3, ffma2(cf, rx, qx), A.p[t][0]);
+                A.p[t][1] = ffma2(ri3, ffma2(cf, ry, qy), A.p[t][1]);
+                A.p[t][2] = ffma2(ri3, ffma2(cf, rz, qz), A.p[t][2]);
+                if (POT) A.p[t][3] = ffma2(ri, ffma2(f2(-0.5f), rqr4, NM), A.p[t][3]);
+            } else {
+                const float2 mr3 = fmul2(NM, ri3);  // -M / r^3
+                A.p[t][0] = ffma2(mr3, rx, A.p[t][0]);
+                A.p[t][1] = ffma2(mr3, ry, A.p[t][1]);
+                A.p[t][2] = ffma2(mr3, rz, A.p[t][2]);
+                if (POT) A.p[t][3] = ffma2(NM, ri, A.p[t][3]);
+            }
+        }
+    }
+    A.fold();
+    __syncwarp();
+}
+
+// Fused neighbour count of one pair (target t, staged source k), FP32 band + FP64 decision.
+template <int TPL>
+__device__ __forceinline__ void count_pair(const WarpSmem<float> &W, const Tree &T, const Cluster &K,
+                                           NbrCount<TPL> &NC, int t, int k, float r2f)
+{
+    if (r2f < NC.lo) {
+        NC.cnt[t]++;
+    } else if (r2f <= NC.hi) {  // inside the band: decide in FP64
+        const int sj = W.pj[k];
+        const double4_32a a = T.sp[NC.si[t] < 0 ? sj : NC.si[t]], b = T.sp[sj];
+        const double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
+        NC.cnt[t] += dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < K.rl2_d;
+    }
+}
+
+// Mixed form, two staged particles at a time; same terms as eval_parts.
+template <int TPL, bool POT, bool NBR>
+__device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const WalkArgs &P,
+                                              const Cluster &K, int nleaves, int nparts,
+                                              const GroupFrame &F, const float (&px)[TPL],
+                                              const float (&py)[TPL], const float (&pz)[TPL],
+                                              AccX2<TPL> &A, NbrCount<TPL> &NC)
+{
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    int carry = 0;
+    for (int b = 0; b < nleaves; b += 32) {
+        int i = b + lane;
+        int v = i < nleaves ? W.lq[i].y : 0;
+        int inc = warp_incl_scan(v);
+        if (i < nleaves) W.lqo[i] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    __syncwarp();
+    const float inv_dr = K.inv_dr_f, nrin_dr = -K.rin_dr_f;
+    float2 NPX[TPL], NPY[TPL], NPZ[TPL];
+#pragma unroll
+    for (int t = 0; t < TPL; t++) NPX[t] = f2(-px[t]), NPY[t] = f2(-py[t]), NPZ[t] = f2(-pz[t]);
+    const float4 *pq = reinterpret_cast<const float4 *>(W.pp);
+    float *pb = reinterpret_cast<float *>(W.pp) + 8 * (lane >> 1) + (lane & 1);
+    for (int c0 = 0; c0 < nparts; c0 += 32) {
+        int pos = c0 + lane;
+        const int ns = min(32, nparts - c0);
+        if (pos < nparts) {
+            int lo = 0, hi = nleaves;  // last leaf with lqo <= pos
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (W.lqo[mid] <= pos)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const int j = W.lq[lo].x + (pos - W.lqo[lo]);
+            const float4 r = ds_rel(P.T.ph[j], P.T.pl[j], F);
+            pb[0] = r.x, pb[2] = r.y, pb[4] = r.z, pb[6] = r.w;
+            if (NBR) W.pj[lane] = j;
+        }
+        __syncwarp();
+        if ((ns & 1) && lane == 0) {
+            // pad: the partner's position with m = 0 (never counted as a neighbour)
+            float *b = reinterpret_cast<float *>(W.pp) + 8 * (ns >> 1);
+            b[1] = b[0], b[3] = b[2], b[5] = b[4], b[7] = 0.f;
+        }
+        __syncwarp();
+        const int npairs = (ns + 1) >> 1;
+#pragma unroll kPartPairUnroll
+        for (int k = 0; k < npairs; k++) {
+            const float4 b0 = pq[2 * k], b1 = pq[2 * k + 1];
+            const float2 X = make_float2(b0.x, b0.y), Y = make_float2(b0.z, b0.w);
+            const float2 Z = make_float2(b1.x, b1.y), Mj = make_float2(b1.z, b1.w);
+#pragma unroll
+            for (int t = 0; t < TPL; t++) {
+                // d = x_j - x_i
+                const float2 dx = fadd2(X, NPX[t]), dy = fadd2(Y, NPY[t]), dz = fadd2(Z, NPZ[t]);
+                float2 r2 = fmul2(dx, dx);
+                r2 = ffma2(dy, dy, r2);
+                r2 = ffma2(dz, dz, r2);
+                const float2 ri = make_float2(rsqrtf(fmaxf(r2.x, kR2Min)), rsqrtf(fmaxf(r2.y, kR2Min)));
+                const float2 r = fmul2(r2, ri);
+                // x = (r - r_in)/(r_out - r_in) clamped to [0, 1]
+                const float2 x = make_float2(__saturatef(fmaf(r.x, inv_dr, nrin_dr)),
+                                             __saturatef(fmaf(r.y, inv_dr, nrin_dr)));
+                float2 w = ffma2(f2(-20.f), x, f2(70.f));
+                w = ffma2(w, x, f2(-84.f));
+                w = ffma2(w, x, f2(35.f));
+                const float2 x2 = fmul2(x, x);
+                const float2 Wt = fmul2(w, fmul2(x2, x2));
+                const float2 ri3 = fmul2(fmul2(ri, ri), ri);
+                const float2 f = fmul2(fmul2(Mj, Wt), ri3);
+                A.p[t][0] = ffma2(f, dx, A.p[t][0]);
+                A.p[t][1] = ffma2(f, dy, A.p[t][1]);
+                A.p[t][2] = ffma2(f, dz, A.p[t][2]);
+                if (POT) {
+                    A.p[t][3].x -= r2.x > 0.f ? Mj.x * ri.x : 0.f;
+                    A.p[t][3].y -= r2.y > 0.f ? Mj.y * ri.y : 0.f;
+                }
+                if (NBR) {
+                    // neighbour iff |x_j - x_i|^2 < r_list^2 in FP64; the pair with
+                    // itself is counted here (r2 = 0) and removed at the end
+                    count_pair(W, P.T, K, NC, t, 2 * k, r2.x);
+                    if (2 * k + 1 < ns) count_pair(W, P.T, K, NC, t, 2 * k + 1, r2.y);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    A.fold();
+}
+
+// the mixed form evaluates pairs of sources, the FP64 form one at a time
+template <typename Real, int TPL, bool POT, bool QUAD, typename AccT>
+__device__ __forceinline__ void eval_cells_any(const WarpSmem<Real> &W, int ncells, const Real (&px)[TPL],
+                                               const Real (&py)[TPL], const Real (&pz)[TPL], AccT &A)
+{
+    if constexpr (sizeof(Real) == 4)
+        eval_cells_x2<TPL, POT, QUAD>(W, ncells, px, py, pz, A);
+    else
+        eval_cells<Real, TPL, POT, QUAD>(W, ncells, px, py, pz, A);
+}
+
+template <typename Real, int TPL, bool POT, bool NBR, typename AccT>
+__device__ __forceinline__ void eval_parts_any(const WarpSmem<Real> &W, const WalkArgs &P, const Cluster &K,
+                                               int nleaves, int nparts, const GroupFrame &F,
+                                               const Real (&px)[TPL], const Real (&py)[TPL],
+                                               const Real (&pz)[TPL], AccT &A, NbrCount<TPL> &NC)
+{
+    if constexpr (sizeof(Real) == 4)
+        eval_parts_x2<TPL, POT, NBR>(W, P, K, nleaves, nparts, F, px, py, pz, A, NC);
+    else
+        eval_parts<Real, TPL, POT, NBR>(W, P, K, nleaves, nparts, F, px, py, pz, A, NC);
+}
+
 template <typename Real, int TPL, bool POT, bool QUAD, bool NBR>
-__global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel(WalkArgs P)
+__global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3) walk_kernel(WalkArgs P)
 {
     extern __shared__ __align__(16) char smem[];
     using R4 = typename Vec4<Real>::T;
@@ -445,7 +712,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
             NC.hi = filter_ok ? K.rl2_f + band : INFINITY;
             if (!count_here) NC.lo = NC.hi = -INFINITY;      // this cluster is counted elsewhere
         }
-        Acc<Real, TPL> A;
+        typename std::conditional<kMixed, AccX2<TPL>, Acc<double, TPL>>::type A;
         A.zero_all();
         int sp = 1;
         if (lane == 0) W.stk[0] = pack_range(cid, 1);
@@ -549,11 +816,14 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
                 R4 qa;
                 R2 qb;
                 if (kMixed) {
+                    // pair layout: negated position and mass, then the quadrupole
                     const float4 r = ds_rel(ra, rd, F);
-                    v.x = r.x, v.y = r.y, v.z = r.z;
-                    v.w = rd.w;  // M
-                    qa.x = rq0.x, qa.y = rq0.y, qa.z = rq0.z, qa.w = rq0.w;
-                    qb.x = rq1.x, qb.y = rq1.y;
+                    float *b = reinterpret_cast<float *>(W.cpos) + 20 * (pos >> 1) + (pos & 1);
+                    b[0] = -r.x, b[2] = -r.y, b[4] = -r.z, b[6] = -rd.w;
+                    if (QUAD) {
+                        b[8] = rq0.x, b[10] = rq0.y, b[12] = rq0.z, b[14] = rq0.w;
+                        b[16] = rq1.x, b[18] = rq1.y;
+                    }
                 } else {
                     const double4_32a cm = T.comM[node];
                     v.x = to_real<Real>(dsub(cm.x, F.cx));
@@ -563,11 +833,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
                     const double2 *q = reinterpret_cast<const double2 *>(T.q64 + 6 * (size_t)node);
                     const double2 q0 = q[0], q1 = q[1], q2 = q[2];
                     qa.x = q0.x, qa.y = q0.y, qa.z = q1.x, qa.w = q1.y, qb.x = q2.x, qb.y = q2.y;
-                }
-                W.cpos[pos] = v;
-                if (QUAD) {
-                    W.cqa[pos] = qa;
-                    W.cqb[pos] = qb;
+                    W.cpos[pos] = v;
+                    if (QUAD) {
+                        W.cqa[pos] = qa;
+                        W.cqb[pos] = qb;
+                    }
                 }
             }
             const int na = __popc(am);
@@ -583,16 +853,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? 5 : 3) walk_kernel
             npart += lc;
 
             if (cb >= tile) {
-                eval_cells<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
+                eval_cells_any<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
                 cb = 0;
             }
             if (lqp >= tile) {
-                eval_parts<Real, TPL, POT, NBR>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
+                eval_parts_any<Real, TPL, POT, NBR>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
                 lqn = lqp = 0;
             }
         }
-        if (cb > 0) eval_cells<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
-        if (lqp > 0) eval_parts<Real, TPL, POT, NBR>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
+        if (cb > 0) eval_cells_any<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
+        if (lqp > 0) eval_parts_any<Real, TPL, POT, NBR>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
 
         // ---- results, scattered to the original order
 #pragma unroll
