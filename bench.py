@@ -63,9 +63,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
-    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m"],
+    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m", "ensemble64"],
                     help="plummer1m: the throughput benchmark; king2m: theta sweep of the "
-                         "mixed and FP64 forms against the direct sum (one line per theta)")
+                         "mixed and FP64 forms against the direct sum (one line per theta); "
+                         "ensemble64: 64 clusters in one graph-captured batched step, autotuned, "
+                         "against one-cluster-at-a-time launches")
+    ap.add_argument("--no-tune", action="store_true", help="ensemble64: use --group-size/--tile/--leaf-cap")
     ap.add_argument("--samples", type=int, default=8192, help="direct-sum targets (king2m)")
     return ap.parse_args(argv)
 
@@ -440,11 +443,12 @@ def run_b300(args, rank, local, world):
     return line
 
 
-# kernels launched by one step: build = init, bbox, cube, keys (4) + radix sort 8 x
-# (histogram, scan, scatter) + gather + topology root, 21 levels, finish + group scan,
-# first, finish + moments leaves and 21 levels; far force 1 (it also counts the
-# neighbours); neighbours = offsets scan, fill, row sort; kick 1; drift 1
-KERNELS_PER_STEP = (4 + 8 * 3 + 1 + (1 + 21 + 1) + 3 + (1 + 21)) + 1 + 3 + 1 + 1
+# kernels launched by one step: build = metadata, cluster table, cluster parameters,
+# bbox, cube, keys (6) + radix sort 8 x (histogram, scan, scatter) + gather + topology
+# root, 21 levels, finish + group scan, first, finish + moments leaves and 21 levels;
+# far force 1 (it also counts the neighbours); neighbours = offsets scan, fill, row
+# sort; kick 1; drift 1
+KERNELS_PER_STEP = (6 + 8 * 3 + 1 + (1 + 21 + 1) + 3 + (1 + 21)) + 1 + 3 + 1 + 1
 
 
 def run_reference(args, rank, world):
@@ -543,10 +547,217 @@ def king2m_sweep(args):
                           "r_in": r_in, "samples": args.samples, "direct_sum_s": t_direct, **row}))
 
 
+# ---------------------------------------------------------------------------- ensemble
+ENS_CLUSTERS, ENS_N_LO, ENS_N_HI, ENS_THETA = 64, 1e4, 5e5, 0.4
+
+
+def ensemble_params(sizes):
+    """Per-cluster {theta, r_in, r_out, r_list}: r_out = the paper's r_cut = 4 tau(N)
+    (Eqs. 21-22) of each cluster, r_in = 0.1 r_out, r_list = r_out."""
+    import synth
+    rows = []
+    for n in sizes:
+        rc = synth.paper_run_params(int(n))["r_cut"]
+        rows.append([ENS_THETA, 0.1 * rc, rc, rc])
+    return rows
+
+
+def _events_ms(stream, fn, steps, flush):
+    import torch
+    ts = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return ts
+
+
+def _dist(ts):
+    import numpy as np
+    a = np.asarray(ts)
+    return {"mean": float(a.mean()), "p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)),
+            "min": float(a.min()), "max": float(a.max()), "steps": len(ts)}
+
+
+def ensemble_run(args):
+    """64 independent clusters (alternately Plummer and King W0 = 5), N log-uniform in
+    [1e4, 5e5] (~7.8e6 in total), equal masses, theta = 0.4, per-cluster r_out by the
+    paper's rule.  One step = batched build + far force + neighbour lists + kick + drift,
+    captured once into a CUDA graph (one persistent walk launch for every cluster), with
+    the launch shape picked by the autotuner.  Compared with the same step run one
+    cluster at a time (eager calls, and one graph per cluster)."""
+    import numpy as np
+    import torch
+
+    import paper_2110_11658_b300 as p3t
+    import synth
+    from paper_2110_11658_b300 import autotune
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    cl = synth.ensemble(ENS_CLUSTERS, ENS_N_LO, ENS_N_HI, 20211022, masses="equal", w0=5.0)
+    sizes = [c.n for c in cl]
+    allc, segn = synth.concat(cl)
+    n = allc.n
+    rows = ensemble_params(sizes)
+    stream = torch.cuda.Stream(dev)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    init = {k: t(getattr(allc, k)) for k in ("x", "y", "z", "m", "vx", "vy", "vz")}
+    seg = t(segn)
+    cprm = torch.tensor(rows, dtype=torch.float64, device=dev)
+    cap = 16 * n
+    buf = {"a": [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)],
+           "offs": torch.empty(n + 1, dtype=torch.int64, device=dev),
+           "idx": torch.empty(cap, dtype=torch.int32, device=dev),
+           "tot": torch.zeros(1, dtype=torch.int64, device=dev),
+           "nc": torch.zeros(1, dtype=torch.int64, device=dev),
+           "np": torch.zeros(1, dtype=torch.int64, device=dev)}
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+
+    def params(cfg):
+        return p3t.Params(theta=ENS_THETA, r_in=rows[0][1], r_out=rows[0][2], r_list=rows[0][3],
+                          leaf_cap=cfg["leaf_cap"], group_size=cfg["group_size"], tile=cfg["tile"],
+                          precision=p3t.P3T_FP32_MIXED)
+
+    def batched_graph(cfg, st):
+        ctx = p3t.Context(params(cfg), stream)
+        g = ctx.capture_step(st["x"], st["y"], st["z"], st["m"], *buf["a"], seg_offsets=seg, cluster_params=cprm,
+                             vx=st["vx"], vy=st["vy"], vz=st["vz"], kick_dt=DT, drift_dt=DT,
+                             n_cell=buf["nc"], n_part=buf["np"], offsets=buf["offs"], idx=buf["idx"],
+                             total=buf["tot"])
+        return g, ctx
+
+    tune_state = {k: v.clone() for k, v in init.items()}
+    if args.no_tune:
+        best = {"group_size": args.group_size, "tile": args.tile, "leaf_cap": args.leaf_cap}
+        table = []
+    else:
+        res = autotune.Tuner(autotune.time_graph_step(lambda cfg: batched_graph(cfg, tune_state), steps=3),
+                             repeats=1).tune()
+        best, table = res.best, [{"cfg": c, "ms": ms} for c, ms in res.table]
+    del tune_state
+
+    steps = max(3, args.steps)
+    out = {}
+    # (a) batched, graph-captured
+    st = {k: v.clone() for k, v in init.items()}
+    g, ctx = batched_graph(best, st)
+    for _ in range(max(3, args.warmup)):
+        g.launch()
+    ctx.check()
+    buf["nc"].zero_()
+    buf["np"].zero_()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    out["batched_graph"] = _dist(_events_ms(stream, g.launch, steps, flush))
+    clk = clocks.stop()
+    ctx.check()
+    inter = (int(buf["nc"].item()) + int(buf["np"].item())) / steps
+    nbr_total = int(buf["tot"].item())
+    # far force alone (eager, same context and tree) for the walk's roofline
+    far_ts = _events_ms(stream, lambda: ctx.far_force(*buf["a"]), steps, flush)
+    ctx.check()
+    ctx.close()
+    # (b) batched, eager calls
+    st = {k: v.clone() for k, v in init.items()}
+    ctx = p3t.Context(params(best), stream)
+
+    def eager():
+        ctx.build_tree_batch(seg, st["x"], st["y"], st["z"], st["m"], cluster_params=cprm)
+        ctx.far_force(*buf["a"])
+        ctx.neighbours_async(buf["offs"], buf["idx"], buf["tot"])
+        ctx.kick(DT, *buf["a"], st["vx"], st["vy"], st["vz"])
+        ctx.drift(DT, st["x"], st["y"], st["z"], st["vx"], st["vy"], st["vz"])
+
+    for _ in range(2):
+        eager()
+    out["batched_eager"] = _dist(_events_ms(stream, eager, steps, flush))
+    ctx.check()
+    ctx.close()
+    # (c), (d) one cluster at a time: a context per cluster with its own r_out
+    st = {k: v.clone() for k, v in init.items()}
+    per = []
+    for k, c in enumerate(cl):
+        s0, s1 = int(segn[k]), int(segn[k + 1])
+        prm = params(best)
+        prm.r_in, prm.r_out, prm.r_list = rows[k][1], rows[k][2], rows[k][3]
+        cx = p3t.Context(prm, stream)
+        v = {q: st[q][s0:s1] for q in st}
+        a = [buf["a"][i][s0:s1] for i in range(3)]
+        offs = torch.empty(c.n + 1, dtype=torch.int64, device=dev)
+        idx = buf["idx"][16 * s0:16 * s1]
+        tot = torch.zeros(1, dtype=torch.int64, device=dev)
+        per.append((cx, v, a, offs, idx, tot))
+
+    def sequential():
+        for cx, v, a, offs, idx, tot in per:
+            cx.build_tree(v["x"], v["y"], v["z"], v["m"])
+            cx.far_force(*a)
+            cx.neighbours_async(offs, idx, tot)
+            cx.kick(DT, *a, v["vx"], v["vy"], v["vz"])
+            cx.drift(DT, v["x"], v["y"], v["z"], v["vx"], v["vy"], v["vz"])
+
+    for _ in range(2):
+        sequential()
+    out["sequential_eager"] = _dist(_events_ms(stream, sequential, steps, flush))
+    graphs = [cx.capture_step(v["x"], v["y"], v["z"], v["m"], *a, vx=v["vx"], vy=v["vy"], vz=v["vz"],
+                              kick_dt=DT, drift_dt=DT, offsets=offs, idx=idx, total=tot)
+              for cx, v, a, offs, idx, tot in per]
+
+    def sequential_graphs():
+        for gg in graphs:
+            gg.launch()
+
+    for _ in range(2):
+        sequential_graphs()
+    out["sequential_graph"] = _dist(_events_ms(stream, sequential_graphs, steps, flush))
+    for cx, *_ in per:
+        cx.check()
+        cx.close()
+
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_kind = measured_peaks()
+    fp32_peak = fp32_peak_tflops(props.multi_processor_count, float(peaks.get("sm_max_mhz", 2032.0)))
+    far_ms = float(np.median(far_ts))
+    achieved = FLOPS_PER_INTERACTION * inter / (far_ms * 1e-3) / 1e12
+    step_ms = out["batched_graph"]["mean"]
+    return {
+        "metric": "particle far-force evals/sec & interactions/sec at N=1e6 (FP32 % peak); ensemble p50/p99",
+        "value": n / (step_ms * 1e-3), "unit": "particles/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(3, args.warmup), "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "ensemble64_plummer_king5_n1e4-5e5", "n_clusters": len(cl), "n": n,
+                   "sizes": sizes, "theta": ENS_THETA, "r_out": "paper r_cut = 4 tau(N) per cluster",
+                   "r_in": "0.1 r_out", "r_list": "r_out", "dt": DT, "tuned": best,
+                   "step": "batched build + far force + neighbours + kick + drift, one CUDA graph launch",
+                   "l2": "256 MB buffer written between timed steps (L2 is 126 MB)"},
+        "ensemble": {"step_ms": out, "speedup_vs_sequential_eager":
+                     out["sequential_eager"]["mean"] / step_ms,
+                     "speedup_vs_sequential_graph": out["sequential_graph"]["mean"] / step_ms,
+                     "tuner_table": table},
+        "far_ms": far_ms, "interactions_per_particle": inter / n, "mean_neighbours": nbr_total / n,
+        "fp32_pct_of_peak": 100.0 * achieved / fp32_peak,
+        "roofline": {"bound": "alu", "kernel": "walk_kernel (batched far force)", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
+                                    % (float(peaks.get("sm_max_mhz", 2032.0)), peak_kind)},
+        "gpu_launches": None, "clocks": clk,
+    }
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.workload == "king2m":
         king2m_sweep(args)
+        return
+    if args.workload == "ensemble64":
+        print(json.dumps(ensemble_run(args)))
         return
     rank, local, world = dist_init()
     if args.impl == "reference":

@@ -197,6 +197,59 @@ int p3t_set_debug(p3t_ctx *c, int on);
 /* Static description of an error code. */
 const char *p3t_error_string(int code);
 
+/* ---- one whole step as a CUDA graph -------------------------------------
+ * The distant-force step of the P3T scheme (Sec. 2.4, Eq. 12): tree build,
+ * far force, neighbour lists, kick and (optionally) the drift that stands in
+ * for the Hermite side, recorded once into a CUDA graph and replayed with a
+ * single launch per step.  Batching many clusters this way leaves one graph
+ * launch per step for the whole ensemble (one persistent walk kernel inside).
+ *
+ * p3t_step_args (all pointers device pointers owned by the caller; they and
+ * every size are baked into the graph at capture, so replays must use the same
+ * buffers, whose contents may change between launches):
+ *   n_clusters, n, seg_offsets, cluster_params: as p3t_build_tree_batch;
+ *     seg_offsets may be null with n_clusters == 1 (then p3t_build_tree).
+ *   x, y, z, m: positions and masses (drift updates x, y, z in place).
+ *   vx, vy, vz: velocities kicked by kick_dt (Eq. 12), or all null: no kick.
+ *   ax, ay, az, pot, n_cell, n_part: as p3t_far_force.
+ *   offsets, idx, capacity, total: as p3t_neighbours_async; offsets null: no lists.
+ *   drift_dt: x += drift_dt * v after the kick; 0: no drift.
+ * p3t_graph_capture sizes the context's scratch for the step first, then
+ * records the step on a private stream, so nothing runs or allocates during
+ * capture; the graph is launched on the context's stream.  The context's
+ * host-side state after capture is that of before it: launch the graph
+ * before further entry points rely on its tree.  A launch restores the
+ * state the captured step leaves (so p3t_export_tree, p3t_tree_info ...
+ * describe the graph's tree after it).  If the context's scratch is
+ * reallocated later (a larger eager build), the graph's pointers are stale and
+ * p3t_graph_launch returns P3T_ERR_ORDER.  Destroy a context's graphs before
+ * the context.  Errors: those of the captured
+ * calls, P3T_ERR_INVALID_ARG for inconsistent arguments, P3T_ERR_CUDA when
+ * capture or instantiation fails.  Device-side errors (capacity, invalid
+ * input) latch as for the eager calls; read them with p3t_status. */
+typedef struct p3t_graph p3t_graph;
+typedef struct {
+    int32_t n_clusters;
+    int64_t n;
+    const int64_t *seg_offsets;
+    const double *cluster_params;
+    double *x, *y, *z;
+    const double *m;
+    double *vx, *vy, *vz;
+    void *ax, *ay, *az;
+    double *pot;
+    int64_t *n_cell, *n_part;
+    int64_t *offsets;
+    int32_t *idx;
+    int64_t capacity;
+    int64_t *total;
+    double kick_dt;
+    double drift_dt;
+} p3t_step_args;
+int p3t_graph_capture(p3t_ctx *c, const p3t_step_args *a, p3t_graph **out);
+int p3t_graph_launch(p3t_graph *g);
+int p3t_graph_destroy(p3t_graph *g);
+
 /* Morton order of n particles WITHOUT ANY DEVICE ALLOCATION.  The paper has
  * no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc where they need it -- a host whose own memory pool already owns

@@ -39,6 +39,7 @@ EXPORTED = [
     "p3t_far_force", "p3t_neighbours", "p3t_neighbours_async", "p3t_kick", "p3t_drift",
     "p3t_step_host", "p3t_status", "p3t_tree_info", "p3t_export_tree", "p3t_group_counts",
     "p3t_set_debug", "p3t_error_string", "p3t_morton_order_noalloc",
+    "p3t_graph_capture", "p3t_graph_launch", "p3t_graph_destroy",
 ]
 P3T_NOALLOC_MAX_N = 65536
 
@@ -48,6 +49,16 @@ class p3t_params(C.Structure):
                 ("r_list", C.c_double), ("leaf_cap", C.c_int32), ("group_size", C.c_int32),
                 ("tile", C.c_int32), ("threads_per_group", C.c_int32), ("precision", C.c_int32),
                 ("quadrupole", C.c_int32)]
+
+
+class p3t_step_args(C.Structure):
+    _fields_ = [("n_clusters", C.c_int32), ("n", C.c_int64), ("seg_offsets", C.c_void_p),
+                ("cluster_params", C.c_void_p), ("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p),
+                ("m", C.c_void_p), ("vx", C.c_void_p), ("vy", C.c_void_p), ("vz", C.c_void_p),
+                ("ax", C.c_void_p), ("ay", C.c_void_p), ("az", C.c_void_p), ("pot", C.c_void_p),
+                ("n_cell", C.c_void_p), ("n_part", C.c_void_p), ("offsets", C.c_void_p), ("idx", C.c_void_p),
+                ("capacity", C.c_int64), ("total", C.c_void_p), ("kick_dt", C.c_double),
+                ("drift_dt", C.c_double)]
 
 
 class P3TError(RuntimeError):
@@ -84,6 +95,9 @@ _sig = {
     "p3t_set_debug": [_vp, C.c_int],
     "p3t_error_string": [C.c_int],
     "p3t_morton_order_noalloc": [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "p3t_graph_capture": [_vp, C.POINTER(p3t_step_args), C.POINTER(_vp)],
+    "p3t_graph_launch": [_vp],
+    "p3t_graph_destroy": [_vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -152,8 +166,12 @@ class Context:
         _check(_lib.p3t_create(C.byref(h), C.byref(cp), C.c_void_p(stream.cuda_stream)), "p3t_create")
         self._h = h
         self.n = 0
+        self._graphs = []
 
     def close(self):
+        for g in getattr(self, "_graphs", []):
+            g.close()
+        self._graphs = []
         if getattr(self, "_h", None):
             _lib.p3t_destroy(self._h)
             self._h = None
@@ -305,3 +323,50 @@ class Context:
         _check(_lib.p3t_group_counts(self._h, c.data_ptr(), p.data_ptr()), "p3t_group_counts")
         self.check()
         return c, p
+
+    def capture_step(self, x, y, z, m, ax, ay, az, seg_offsets=None, cluster_params=None, vx=None, vy=None,
+                     vz=None, kick_dt=0.0, drift_dt=0.0, pot=None, n_cell=None, n_part=None, offsets=None,
+                     idx=None, total=None, capacity=None):
+        """Record one step (build, far force, neighbour lists, kick, drift) into a CUDA graph
+        (p3t_graph_capture).  The tensors are baked in: replays reuse them."""
+        t = self._torch
+        n = x.numel()
+        nc = 1 if seg_offsets is None else seg_offsets.numel() - 1
+        d = self.acc_dtype
+        cap = (idx.numel() if idx is not None else 0) if capacity is None else int(capacity)
+        a = p3t_step_args(
+            nc, n, _ptr(seg_offsets, t.int64, nc + 1, "seg_offsets"),
+            _ptr(cluster_params, t.float64, 4 * nc, "cluster_params"),
+            *[_ptr(v, t.float64, n, nm) for v, nm in zip((x, y, z, m), "xyzm")],
+            *[_ptr(v, t.float64, n, nm) for v, nm in zip((vx, vy, vz), ("vx", "vy", "vz"))],
+            *[_ptr(v, d, n, nm) for v, nm in zip((ax, ay, az), ("ax", "ay", "az"))],
+            _ptr(pot, t.float64, n, "pot"), _ptr(n_cell, t.int64, 1, "n_cell"),
+            _ptr(n_part, t.int64, 1, "n_part"), _ptr(offsets, t.int64, n + 1, "offsets"),
+            _ptr(idx, t.int32, cap, "idx"), cap, _ptr(total, t.int64, 1, "total"), float(kick_dt),
+            float(drift_dt))
+        h = C.c_void_p()
+        _check(_lib.p3t_graph_capture(self._h, C.byref(a), C.byref(h)), "p3t_graph_capture")
+        g = Graph(self, h, n, (x, y, z, m, ax, ay, az, seg_offsets, cluster_params, vx, vy, vz, pot, n_cell,
+                               n_part, offsets, idx, total))
+        self._graphs.append(g)
+        return g
+
+
+class Graph:
+    """A captured step (p3t_graph_*); keeps its tensors alive while it exists."""
+
+    def __init__(self, ctx: Context, handle, n, keep):
+        self.ctx = ctx
+        self._h = handle
+        self.n = n
+        self._keep = keep
+
+    def launch(self):
+        _check(_lib.p3t_graph_launch(self._h), "p3t_graph_launch")
+        self.ctx.n = self.n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.p3t_graph_destroy(self._h)
+            self._h = None
+            self._keep = None

@@ -93,12 +93,38 @@ int ensure_capacity(p3t_ctx *c, long long n)
     }
     c->blob = blob;
     c->blob_bytes = total;
+    c->gen++;
     c->cap_n = N;
     c->cap_nodes = NN;
     c->cap_leaf = L;
     T.meta = c->meta;
     T.cap_nodes = (int)NN;
     if (cudaMemsetAsync(c->meta, 0, sizeof(Meta), c->stream) != cudaSuccess) return P3T_ERR_CUDA;
+    return P3T_OK;
+}
+
+// Scratch for n particles in n_clusters clusters (no work is enqueued unless
+// memory is (re)allocated).
+int reserve(p3t_ctx *c, long long n, int n_clusters)
+{
+    int e = ensure_capacity(c, n);
+    if (e) return e;
+    if (n_clusters > c->cap_clusters) {
+        if (c->clusters) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->clusters);
+            c->clusters = nullptr;
+        }
+        int cap = n_clusters < 256 ? 256 : n_clusters;
+        if (cudaMalloc(&c->clusters, sizeof(Cluster) * (size_t)cap) != cudaSuccess) {
+            cudaGetLastError();
+            c->cap_clusters = 0;
+            return P3T_ERR_OOM;
+        }
+        c->cap_clusters = cap;
+        c->gen++;
+    }
+    c->tree.cl = c->clusters;
     return P3T_OK;
 }
 
@@ -202,23 +228,8 @@ static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *se
     if (n <= 0 || n >= (1LL << 31) - 1) return P3T_ERR_INVALID_ARG;
     if (n_clusters < 1 || n_clusters > n) return P3T_ERR_INVALID_ARG;
     if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 29)) return P3T_ERR_INVALID_ARG;
-    int e = ensure_capacity(c, n);
+    int e = reserve(c, n, n_clusters);
     if (e) return e;
-    if (n_clusters > c->cap_clusters) {
-        if (c->clusters) {
-            cudaStreamSynchronize(c->stream);
-            cudaFree(c->clusters);
-            c->clusters = nullptr;
-        }
-        int cap = n_clusters < 256 ? 256 : n_clusters;
-        if (cudaMalloc(&c->clusters, sizeof(Cluster) * (size_t)cap) != cudaSuccess) {
-            cudaGetLastError();
-            c->cap_clusters = 0;
-            return P3T_ERR_OOM;
-        }
-        c->cap_clusters = cap;
-    }
-    c->tree.cl = c->clusters;
     c->built = 0;
     c->counts_valid = 0;
     c->walk_counted = 0;

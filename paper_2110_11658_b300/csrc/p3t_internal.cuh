@@ -319,10 +319,32 @@ struct p3t_ctx {
     size_t blob_bytes;
     void *host_stage;                 // device staging of p3t_step_host
     size_t host_stage_bytes;
+    unsigned long long gen;           // bumped whenever blob or clusters move
 };
 
 namespace p3t {
+// Host-side state that the entry points update as they enqueue work; a CUDA
+// graph restores the state of its captured step when it is launched.
+struct HostState {
+    int n, built, built_precision, counts_valid, walk_counted, uniform_params;
+    Tree tree;
+};
+inline HostState save_state(const p3t_ctx *c)
+{
+    return HostState{c->n, c->built, c->built_precision, c->counts_valid, c->walk_counted,
+                     c->uniform_params, c->tree};
+}
+inline void restore_state(p3t_ctx *c, const HostState &h)
+{
+    c->n = h.n, c->built = h.built, c->built_precision = h.built_precision;
+    c->counts_valid = h.counts_valid, c->walk_counted = h.walk_counted;
+    c->uniform_params = h.uniform_params, c->tree = h.tree;
+}
+}  // namespace p3t
+
+namespace p3t {
 int ensure_capacity(p3t_ctx *c, long long n);
+int reserve(p3t_ctx *c, long long n, int n_clusters);
 int check_launch(p3t_ctx *c);
 int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *cprm,
                const double *x, const double *y, const double *z, const double *m);

@@ -261,3 +261,27 @@ def make(kind: str, n: int, seed: int, masses: str = "equal", w0: float = 7.0,
     if segregated:
         c = segregate(c)
     return c
+
+
+def log_uniform_sizes(count: int, n_lo: float, n_hi: float, seed: int) -> np.ndarray:
+    """`count` cluster sizes drawn log-uniformly in [n_lo, n_hi] (rounded)."""
+    rng = np.random.default_rng(seed)
+    s = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), count))
+    return np.clip(np.rint(s), n_lo, n_hi).astype(np.int64)
+
+
+def ensemble(count: int, n_lo: float, n_hi: float, seed: int, masses: str = "equal",
+             w0: float = 5.0) -> list:
+    """Independent clusters of log-uniform size, alternately Plummer and King(w0),
+    each in its own Henon units (total mass 1) and seeded by seed + 1 + index."""
+    sizes = log_uniform_sizes(count, n_lo, n_hi, seed)
+    return [make("plummer" if k % 2 == 0 else "king", int(n), seed + 1 + k, masses=masses, w0=w0)
+            for k, n in enumerate(sizes)]
+
+
+def concat(clusters: list):
+    """One particle set of several clusters, and its segment offsets (int64, count + 1)."""
+    cat = lambda a: np.concatenate([getattr(c, a) for c in clusters])  # noqa: E731
+    seg = np.zeros(len(clusters) + 1, np.int64)
+    np.cumsum([c.n for c in clusters], out=seg[1:])
+    return Cluster(*(cat(a) for a in ("x", "y", "z", "m", "vx", "vy", "vz"))), seg
