@@ -63,11 +63,14 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
-    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m", "ensemble64"],
+    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m", "ensemble64", "serve256"],
                     help="plummer1m: the throughput benchmark; king2m: theta sweep of the "
                          "mixed and FP64 forms against the direct sum (one line per theta); "
                          "ensemble64: 64 clusters in one graph-captured batched step, autotuned, "
-                         "against one-cluster-at-a-time launches")
+                         "against one-cluster-at-a-time launches; serve256: Poisson request stream over "
+                         "256 resident clusters with continuous batching (p50/p99 latency)")
+    ap.add_argument("--requests", type=int, default=10000, help="serve256: requests in the timed stream")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve256: mean arrival rate (requests/s)")
     ap.add_argument("--no-tune", action="store_true", help="ensemble64: use --group-size/--tile/--leaf-cap")
     ap.add_argument("--samples", type=int, default=8192, help="direct-sum targets (king2m)")
     return ap.parse_args(argv)
@@ -350,6 +353,7 @@ def run_b300(args, rank, local, world):
         ph["far"] += e1.elapsed_time(e2)
         ph["nbr"] += e2.elapsed_time(e3)
         ph["kick_drift"] += e3.elapsed_time(e4)
+    per_step = sorted(e0.elapsed_time(e4) for e0, e1, e2, e3, e4 in evs)
     step_ms_local = sum(ph.values()) / args.steps
     step_ms = dist_max(step_ms_local, world, dev)
     far_ms = dist_max(ph["far"] / args.steps, world, dev)
@@ -426,6 +430,8 @@ def run_b300(args, rank, local, world):
         "particle_interactions_per_particle": npart / n,
         "fp32_pct_of_peak": 100.0 * achieved / fp32_peak,
         "phase_ms": {k: v / args.steps for k, v in ph.items()},
+        "step_ms_p50": statistics.median(per_step),
+        "step_ms_p99": per_step[min(len(per_step) - 1, int(round(0.99 * (len(per_step) - 1))))],
         "mean_neighbours": nbr_total / n,
         "roofline": {"bound": "alu", "kernel": "walk_kernel (p3t_far_force)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
@@ -751,13 +757,103 @@ def ensemble_run(args):
     }
 
 
+# ---------------------------------------------------------------------------- serving
+SERVE_CLUSTERS, SERVE_N_LO, SERVE_N_HI, SERVE_THETA = 256, 1e3, 1e6, 0.5
+
+
+def serve_run(args):
+    """256 device-resident clusters (alternately Plummer and King W0 = 7, Kroupa masses),
+    N log-uniform in [1e3, 1e6], theta = 0.5, per-cluster r_out = the paper's r_cut(N).
+    A Poisson stream (mean `rate` requests/s, uniform cluster choice, seeded) of distant-
+    force-step requests is replayed in real time through (a) the continuous-batching server
+    (2 slots), (b) batching on one slot (no overlap), (c) one cluster at a time."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2110_11658_b300.serve import Arena, Server, poisson_arrivals, summary
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t_gen = time.perf_counter()
+    sizes = synth.log_uniform_sizes(SERVE_CLUSTERS, SERVE_N_LO, SERVE_N_HI, 20211022)
+    cl = [synth.make("plummer" if k % 2 == 0 else "king", int(n), 20211022 + 1 + k, masses="kroupa", w0=7.0)
+          for k, n in enumerate(sizes)]
+    rows = []
+    for c in cl:
+        rc = synth.paper_run_params(c.n)["r_cut"]
+        rows.append([SERVE_THETA, 0.1 * rc, rc, rc])
+    t_gen = time.perf_counter() - t_gen
+    warm = poisson_arrivals(args.rate, 200, len(cl), 7)
+    big = int(max(sizes))
+    cont = dict(n_slots=2, budget=8 * big, max_clusters=256)
+    runs = [  # (name, server shape, rate, requests): saturated headline, then lower loads
+        ("continuous_2slots", cont, args.rate, args.requests),
+        ("batched_1slot", dict(n_slots=1, budget=8 * big, max_clusters=256), args.rate, args.requests),
+        ("one_at_a_time", dict(n_slots=1, budget=big, max_clusters=1), args.rate, args.requests),
+        ("continuous_2slots_half_rate", cont, args.rate / 2, args.requests // 2),
+        ("continuous_2slots_low_rate", cont, 300.0, max(500, args.requests // 5)),
+        ("one_at_a_time_low_rate", dict(n_slots=1, budget=big, max_clusters=1), 300.0, max(500, args.requests // 5)),
+    ]
+    results = {}
+    clk = None
+    for name, kw, rate, count in runs:
+        arr = poisson_arrivals(rate, count, len(cl), 20211022)
+        ar = Arena(cl, rows, device=dev)
+        srv = Server(ar, dt=DT, **kw)
+        srv.run(warm)
+        srv.batches = []
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(0) if name == "continuous_2slots" else None
+        if clocks:
+            clocks.start()
+        reqs = srv.run(arr)
+        if clocks:
+            clk = clocks.stop()
+        st = summary(reqs, ar.sizes, srv.batches)
+        st.update({"slots": kw["n_slots"], "slot_budget_particles": srv.budget, "rate_per_s": rate,
+                   "slot_bytes": srv.bytes_per_slot, "arena_bytes": ar.bytes()})
+        results[name] = st
+        srv.close()
+        del srv, ar
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+    main_st = results["continuous_2slots"]
+    return {
+        "metric": "particle far-force evals/sec & interactions/sec at N=1e6 (FP32 % peak); ensemble p50/p99",
+        "value": main_st["particles_per_s"], "unit": "particles/s", "n_gpus": 1, "steps": args.requests,
+        "warmup": 200, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve256_poisson%d_n1e3-1e6" % int(args.rate), "n_clusters": len(cl),
+                   "resident_particles": int(sum(sizes)), "theta": SERVE_THETA,
+                   "r_out": "paper r_cut = 4 tau(N) per cluster", "r_in": "0.1 r_out", "r_list": "r_out",
+                   "masses": "Kroupa", "models": "Plummer / King W0 = 7 alternating", "dt": DT,
+                   "rate_per_s": args.rate, "requests": args.requests, "generation_s": t_gen},
+        "p50_ms": main_st["p50_ms"], "p99_ms": main_st["p99_ms"],
+        "serving": results,
+        "throughput_vs_one_at_a_time": main_st["particles_per_s"] / results["one_at_a_time"]["particles_per_s"],
+        "p99_vs_one_at_a_time": main_st["p99_ms"] / results["one_at_a_time"]["p99_ms"],
+        "clocks": clk,
+    }
+
+
+def _json_default(o):
+    """numpy scalars in result dictionaries."""
+    if hasattr(o, "item"):
+        return o.item()
+    raise TypeError(type(o).__name__)
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload == "serve256":
+        print(json.dumps(serve_run(args), default=_json_default))
+        return
     if args.workload == "king2m":
         king2m_sweep(args)
         return
     if args.workload == "ensemble64":
-        print(json.dumps(ensemble_run(args)))
+        print(json.dumps(ensemble_run(args), default=_json_default))
         return
     rank, local, world = dist_init()
     if args.impl == "reference":

@@ -197,6 +197,17 @@ int p3t_set_debug(p3t_ctx *c, int on);
 /* Static description of an error code. */
 const char *p3t_error_string(int code);
 
+/* Size the context's device scratch for n particles in n_clusters clusters
+ * now, so that later builds up to that size allocate nothing (a serving loop
+ * pre-sizes its contexts this way).  May synchronise the context's stream when
+ * it reallocates.  Errors: P3T_ERR_INVALID_ARG, P3T_ERR_OOM. */
+int p3t_reserve(p3t_ctx *c, int64_t n, int32_t n_clusters);
+
+/* Device bytes a context with parameters p allocates for n particles in
+ * n_clusters clusters (scratch plus cluster table); *bytes is host memory.
+ * For admission by device-memory footprint.  Errors: P3T_ERR_INVALID_ARG. */
+int p3t_scratch_bytes(const p3t_params *p, int64_t n, int32_t n_clusters, int64_t *bytes);
+
 /* ---- one whole step as a CUDA graph -------------------------------------
  * The distant-force step of the P3T scheme (Sec. 2.4, Eq. 12): tree build,
  * far force, neighbour lists, kick and (optionally) the drift that stands in
@@ -249,6 +260,48 @@ typedef struct {
 int p3t_graph_capture(p3t_ctx *c, const p3t_step_args *a, p3t_graph **out);
 int p3t_graph_launch(p3t_graph *g);
 int p3t_graph_destroy(p3t_graph *g);
+
+/* ---- serving: batches of resident clusters --------------------------------
+ * A server keeps many clusters resident in one device arena and steps an
+ * arbitrary subset of them together: their particles are gathered into a
+ * contiguous staging area, stepped with one batched call sequence
+ * (p3t_build_tree_batch ... p3t_kick, one persistent walk for all of them),
+ * and the results scattered back.  A batch of n_seg clusters is described by
+ * batch_off (device int64[n_seg + 1], ascending, batch_off[0] = 0: the
+ * segment offsets in the staging area, i.e. the batch's seg_offsets) and
+ * arena_off (device int64[n_seg]: each cluster's first particle in the arena).
+ * n_batch = batch_off[n_seg] (host copy; it sizes the grid).
+ *
+ * p3t_batch_move copies n_arrays (<= 10) parallel arrays between arena and
+ * staging: element i of the staging area <-> element arena_off[k] + (i -
+ * batch_off[k]) of the arena, k the segment holding i; to_batch = 1 gathers
+ * (arena -> staging), 0 scatters back.  Elements are 4 or 8 bytes
+ * (elem_bytes).  Segments must not overlap in the arena.
+ *
+ * p3t_batch_scatter_neighbours turns the batch's neighbour lists (offsets
+ * int64[n_batch + 1], idx int32 with batch indices, capacity max_entries) into
+ * cluster-local lists in the arena: cluster k's n_k + 1 row offsets start at
+ * arena_offsets[row_arena_off[k]] (from 0), its entries at
+ * arena_idx[ent_arena_off[k]] with indices relative to the cluster (0 .. n_k -
+ * 1).  A cluster whose entries exceed ent_arena_cap[k], or a batch whose
+ * total exceeds max_entries, sets *status (device int32) to P3T_ERR_CAPACITY
+ * and is not copied.
+ * Both run on `cuda_stream` without synchronising; they return
+ * P3T_ERR_INVALID_ARG for bad arguments and P3T_ERR_CUDA for launch errors. */
+typedef struct {
+    void *arena;
+    void *batch;
+    int32_t elem_bytes;
+} p3t_seg_array;
+int p3t_batch_move(void *cuda_stream, int32_t n_seg, int64_t n_batch, const int64_t *batch_off,
+                   const int64_t *arena_off, int32_t n_arrays, const p3t_seg_array *arrays,
+                   int32_t to_batch);
+int p3t_batch_scatter_neighbours(void *cuda_stream, int32_t n_seg, int64_t n_batch,
+                                 int64_t max_entries, const int64_t *batch_off,
+                                 const int64_t *row_arena_off, const int64_t *ent_arena_off,
+                                 const int64_t *ent_arena_cap, const int64_t *offsets,
+                                 const int32_t *idx, int64_t *arena_offsets, int32_t *arena_idx,
+                                 int32_t *status);
 
 /* Morton order of n particles WITHOUT ANY DEVICE ALLOCATION.  The paper has
  * no counterpart: this entry point exists for callers that cannot call

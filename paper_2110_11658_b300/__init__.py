@@ -39,7 +39,8 @@ EXPORTED = [
     "p3t_far_force", "p3t_neighbours", "p3t_neighbours_async", "p3t_kick", "p3t_drift",
     "p3t_step_host", "p3t_status", "p3t_tree_info", "p3t_export_tree", "p3t_group_counts",
     "p3t_set_debug", "p3t_error_string", "p3t_morton_order_noalloc",
-    "p3t_graph_capture", "p3t_graph_launch", "p3t_graph_destroy",
+    "p3t_graph_capture", "p3t_graph_launch", "p3t_graph_destroy", "p3t_reserve", "p3t_scratch_bytes",
+    "p3t_batch_move", "p3t_batch_scatter_neighbours",
 ]
 P3T_NOALLOC_MAX_N = 65536
 
@@ -59,6 +60,10 @@ class p3t_step_args(C.Structure):
                 ("n_cell", C.c_void_p), ("n_part", C.c_void_p), ("offsets", C.c_void_p), ("idx", C.c_void_p),
                 ("capacity", C.c_int64), ("total", C.c_void_p), ("kick_dt", C.c_double),
                 ("drift_dt", C.c_double)]
+
+
+class p3t_seg_array(C.Structure):
+    _fields_ = [("arena", C.c_void_p), ("batch", C.c_void_p), ("elem_bytes", C.c_int32)]
 
 
 class P3TError(RuntimeError):
@@ -98,6 +103,10 @@ _sig = {
     "p3t_graph_capture": [_vp, C.POINTER(p3t_step_args), C.POINTER(_vp)],
     "p3t_graph_launch": [_vp],
     "p3t_graph_destroy": [_vp],
+    "p3t_reserve": [_vp, _i64, C.c_int32],
+    "p3t_scratch_bytes": [C.POINTER(p3t_params), _i64, C.c_int32, C.POINTER(_i64)],
+    "p3t_batch_move": [_vp, C.c_int32, _i64, _vp, _vp, C.c_int32, C.POINTER(p3t_seg_array), C.c_int32],
+    "p3t_batch_scatter_neighbours": [_vp, C.c_int32, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -134,6 +143,34 @@ class Params:
         return p3t_params(self.theta, self.r_in, self.r_out, self.r_list, self.leaf_cap,
                           self.group_size, self.tile, self.threads_per_group, self.precision,
                           self.quadrupole)
+
+
+def scratch_bytes(params: "Params", n: int, n_clusters: int = 1) -> int:
+    """Device bytes a context with these parameters allocates for n particles (p3t_scratch_bytes)."""
+    cp = params.to_c()
+    b = C.c_int64(0)
+    _check(_lib.p3t_scratch_bytes(C.byref(cp), int(n), int(n_clusters), C.byref(b)), "p3t_scratch_bytes")
+    return b.value
+
+
+def batch_move(stream, n_seg, n_batch, batch_off, arena_off, pairs, to_batch):
+    """p3t_batch_move: pairs = [(arena_tensor, batch_tensor), ...] (float64 or float32 CUDA tensors)."""
+    arr = (p3t_seg_array * len(pairs))()
+    for q, (a, b) in enumerate(pairs):
+        if a.dtype != b.dtype or a.element_size() not in (4, 8):
+            raise ValueError("arena and batch arrays must share a 4- or 8-byte dtype")
+        arr[q] = p3t_seg_array(_ptr(a, name="arena"), _ptr(b, name="batch"), a.element_size())
+    _check(_lib.p3t_batch_move(C.c_void_p(stream.cuda_stream), int(n_seg), int(n_batch), _ptr(batch_off),
+                               _ptr(arena_off), len(pairs), arr, int(bool(to_batch))), "p3t_batch_move")
+
+
+def batch_scatter_neighbours(stream, n_seg, n_batch, max_entries, batch_off, row_arena_off, ent_arena_off,
+                             ent_arena_cap, offsets, idx, arena_offsets, arena_idx, status):
+    """p3t_batch_scatter_neighbours on CUDA tensors (see include/p3t.h)."""
+    _check(_lib.p3t_batch_scatter_neighbours(
+        C.c_void_p(stream.cuda_stream), int(n_seg), int(n_batch), int(max_entries), _ptr(batch_off),
+        _ptr(row_arena_off), _ptr(ent_arena_off), _ptr(ent_arena_cap), _ptr(offsets), _ptr(idx),
+        _ptr(arena_offsets), _ptr(arena_idx), _ptr(status)), "p3t_batch_scatter_neighbours")
 
 
 def _ptr(t, dtype=None, n=None, name="tensor"):
@@ -195,6 +232,10 @@ class Context:
         cp = params.to_c()
         _check(_lib.p3t_set_params(self._h, C.byref(cp)), "p3t_set_params")
         self.params = params
+
+    def reserve(self, n: int, n_clusters: int = 1):
+        """Size the scratch for n particles in n_clusters clusters now (p3t_reserve)."""
+        _check(_lib.p3t_reserve(self._h, int(n), int(n_clusters)), "p3t_reserve")
 
     def set_debug(self, on: bool):
         _check(_lib.p3t_set_debug(self._h, int(bool(on))), "p3t_set_debug")

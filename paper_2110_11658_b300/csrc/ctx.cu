@@ -23,62 +23,74 @@ long long node_capacity(long long n, int leaf_cap)
 
 int topo_status_stride(long long n) { return (int)(n / 256 + 4); }
 
+// The scratch layout of a context for n particles: every buffer, in order, each
+// 256-byte aligned.  With base == nullptr only the total is computed.
+static size_t scratch_plan(p3t_ctx *c, long long N, int L, char *base)
+{
+    const long long NN = node_capacity(N, L);
+    const long long sort_blocks = (N + 4095) / 4096;
+    const long long scan_words = N / 256 + 64 + 256 * sort_blocks / 256;
+    const long long topo_words = (long long)kMaxLevelSlots * topo_status_stride(N);
+    Tree &T = c->tree;
+    size_t off = 0;
+    auto put = [&](void *slot, size_t bytes) {
+        if (base) *(void **)slot = base + off;
+        off += align_up(bytes, 256);
+    };
+    put(&c->meta, sizeof(Meta));
+    put(&c->keys_buf[0], 8 * (size_t)N);
+    put(&c->keys_buf[1], 8 * (size_t)N);
+    put(&c->perm_buf[0], 4 * (size_t)N);
+    put(&c->perm_buf[1], 4 * (size_t)N);
+    put(&T.sp, 32 * (size_t)N);
+    put(&T.ph, 16 * (size_t)N);
+    put(&T.pl, 16 * (size_t)N);
+    put(&T.gflag, (size_t)N + 16);
+    put(&T.gidx, 4 * (size_t)N);
+    put(&T.leaves, 4 * (size_t)N);
+    put(&T.cid, 4 * (size_t)N);
+    put(&T.cid_s, 4 * (size_t)N);
+    put(&T.inv, 4 * (size_t)N);
+    put(&T.grp, 8 * (size_t)N);
+    put(&T.glo, 32 * (size_t)N);
+    put(&T.ghi, 32 * (size_t)N);
+    put(&c->nbr_count, 4 * (size_t)N);
+    put(&c->grp_cells, 8 * (size_t)N);
+    put(&c->grp_parts, 8 * (size_t)N);
+    put(&c->sort_hist, 4 * 256 * (size_t)sort_blocks);
+    put(&c->scan_status, 8 * (size_t)(scan_words + topo_words));
+    put(&T.topo, 16 * (size_t)NN);
+    put(&T.level, 4 * (size_t)NN);
+    put(&T.parent, 4 * (size_t)NN);
+    put(&T.ready, 4 * (size_t)NN);
+    put(&T.comM, 32 * (size_t)NN);
+    put(&T.lo, 32 * (size_t)NN);
+    put(&T.hi, 32 * (size_t)NN);
+    put(&T.q32, 24 * (size_t)NN);
+    put(&T.q64, 48 * (size_t)NN);
+    put(&T.wn, 16 * (size_t)kWalkRecord * (size_t)NN);
+    return off;
+}
+
+size_t scratch_bytes(long long n, int leaf_cap, int n_clusters)
+{
+    p3t_ctx dummy;
+    memset((void *)&dummy, 0, sizeof(dummy));
+    const int cap = n_clusters < 256 ? 256 : n_clusters;
+    return scratch_plan(&dummy, n, leaf_cap, nullptr) + sizeof(Cluster) * (size_t)cap;
+}
+
 int ensure_capacity(p3t_ctx *c, long long n)
 {
     const int L = c->prm.leaf_cap;
-    long long need_nodes = node_capacity(n, L);
+    const long long need_nodes = node_capacity(n, L);
     if (c->blob && n <= c->cap_n && need_nodes <= c->cap_nodes) return P3T_OK;
     if (c->blob) {
         cudaStreamSynchronize(c->stream);
         cudaFree(c->blob);
         c->blob = nullptr;
     }
-    long long N = n;
-    long long NN = need_nodes;
-    long long sort_blocks = (N + 4095) / 4096;
-    long long scan_words = N / 256 + 64 + 256 * sort_blocks / 256;
-    long long topo_words = (long long)kMaxLevelSlots * topo_status_stride(N);
-    struct Item {
-        void **ptr;
-        size_t bytes;
-    };
-    Tree &T = c->tree;
-    Item items[] = {
-        {(void **)&c->meta, sizeof(Meta)},
-        {(void **)&c->keys_buf[0], 8 * (size_t)N},
-        {(void **)&c->keys_buf[1], 8 * (size_t)N},
-        {(void **)&c->perm_buf[0], 4 * (size_t)N},
-        {(void **)&c->perm_buf[1], 4 * (size_t)N},
-        {(void **)&T.sp, 32 * (size_t)N},
-        {(void **)&T.ph, 16 * (size_t)N},
-        {(void **)&T.pl, 16 * (size_t)N},
-        {(void **)&T.gflag, (size_t)N + 16},
-        {(void **)&T.gidx, 4 * (size_t)N},
-        {(void **)&T.leaves, 4 * (size_t)N},
-        {(void **)&T.cid, 4 * (size_t)N},
-        {(void **)&T.cid_s, 4 * (size_t)N},
-        {(void **)&T.inv, 4 * (size_t)N},
-        {(void **)&T.grp, 8 * (size_t)N},
-        {(void **)&T.glo, 32 * (size_t)N},
-        {(void **)&T.ghi, 32 * (size_t)N},
-        {(void **)&c->nbr_count, 4 * (size_t)N},
-        {(void **)&c->grp_cells, 8 * (size_t)N},
-        {(void **)&c->grp_parts, 8 * (size_t)N},
-        {(void **)&c->sort_hist, 4 * 256 * (size_t)sort_blocks},
-        {(void **)&c->scan_status, 8 * (size_t)(scan_words + topo_words)},
-        {(void **)&T.topo, 16 * (size_t)NN},
-        {(void **)&T.level, 4 * (size_t)NN},
-        {(void **)&T.parent, 4 * (size_t)NN},
-        {(void **)&T.ready, 4 * (size_t)NN},
-        {(void **)&T.comM, 32 * (size_t)NN},
-        {(void **)&T.lo, 32 * (size_t)NN},
-        {(void **)&T.hi, 32 * (size_t)NN},
-        {(void **)&T.q32, 24 * (size_t)NN},
-        {(void **)&T.q64, 48 * (size_t)NN},
-        {(void **)&T.wn, 16 * (size_t)kWalkRecord * (size_t)NN},
-    };
-    size_t total = 0;
-    for (auto &it : items) total += align_up(it.bytes, 256);
+    const size_t total = scratch_plan(c, n, L, nullptr);
     void *blob = nullptr;
     if (cudaMalloc(&blob, total) != cudaSuccess) {
         cudaGetLastError();
@@ -86,19 +98,15 @@ int ensure_capacity(p3t_ctx *c, long long n)
         c->cap_nodes = 0;
         return P3T_ERR_OOM;
     }
-    char *p = (char *)blob;
-    for (auto &it : items) {
-        *it.ptr = p;
-        p += align_up(it.bytes, 256);
-    }
+    scratch_plan(c, n, L, (char *)blob);
     c->blob = blob;
     c->blob_bytes = total;
     c->gen++;
-    c->cap_n = N;
-    c->cap_nodes = NN;
+    c->cap_n = n;
+    c->cap_nodes = need_nodes;
     c->cap_leaf = L;
-    T.meta = c->meta;
-    T.cap_nodes = (int)NN;
+    c->tree.meta = c->meta;
+    c->tree.cap_nodes = (int)need_nodes;
     if (cudaMemsetAsync(c->meta, 0, sizeof(Meta), c->stream) != cudaSuccess) return P3T_ERR_CUDA;
     return P3T_OK;
 }
@@ -217,6 +225,24 @@ int p3t_set_params(p3t_ctx *c, const p3t_params *p)
     if (e) return e;
     c->prm = *p;
     c->built = 0;
+    return P3T_OK;
+}
+
+int p3t_reserve(p3t_ctx *c, int64_t n, int32_t n_clusters)
+{
+    if (!c || n <= 0 || n >= (1LL << 31) - 1 || n_clusters < 1 || n_clusters > n)
+        return P3T_ERR_INVALID_ARG;
+    if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 29)) return P3T_ERR_INVALID_ARG;
+    return reserve(c, n, n_clusters);
+}
+
+int p3t_scratch_bytes(const p3t_params *p, int64_t n, int32_t n_clusters, int64_t *bytes)
+{
+    if (!bytes) return P3T_ERR_INVALID_ARG;
+    int e = validate_params(p);
+    if (e) return e;
+    if (n <= 0 || n >= (1LL << 31) - 1 || n_clusters < 1 || n_clusters > n) return P3T_ERR_INVALID_ARG;
+    *bytes = (int64_t)scratch_bytes(n, p->leaf_cap, n_clusters);
     return P3T_OK;
 }
 
