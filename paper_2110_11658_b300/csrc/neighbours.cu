@@ -125,6 +125,9 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         const float tpair = kUn * (24.f * rl2_f + 32.f * A * rl_f + 128.f * kUn * Rf * rl_f) +
                             64.f * kUn * kUn * (A + 2.f * rl_f) * (A + 2.f * rl_f);
         const bool pair_filter = filter_ok && A < 1e12f;
+        // r2 < in_lo: neighbour; r2 > in_hi: not; otherwise decide in FP64
+        const float in_lo = pair_filter ? rl2_f - tpair : -1.f;
+        const float in_hi = pair_filter ? rl2_f + tpair : INFINITY;
 
         int sp = 1;
         if (lane == 0) W.stk[0] = pack_range(cid, 1);
@@ -218,26 +221,24 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 }
                 __syncwarp();
                 const int ns = min(32, lqp - c0);
+#pragma unroll 4
                 for (int k = 0; k < ns; k++) {
                     const float4 s = W.pp[k];
                     const int j = W.pj[k];
 #pragma unroll
                     for (int t = 0; t < TPL; t++) {
-                        if (si[t] < 0 || si[t] == j) continue;
-                        float dx = s.x - px[t], dy = s.y - py[t], dz = s.z - pz[t];
-                        float r2 = dx * dx + dy * dy + dz * dz;
-                        int in = 2;
-                        if (pair_filter) in = r2 < rl2_f - tpair ? 1 : (r2 > rl2_f + tpair ? 0 : 2);
-                        if (in == 2) {
+                        const float dx = s.x - px[t], dy = s.y - py[t], dz = s.z - pz[t];
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const bool other = si[t] >= 0 && si[t] != j;
+                        bool in = other && r2 < in_lo;
+                        if (other && r2 >= in_lo && r2 <= in_hi) {  // inside the band (rare)
                             const double4_32a a = T.sp[si[t]], b = T.sp[j];
                             double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
                             double d2 = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez));
                             in = d2 < rl2_d;
                         }
-                        if (in) {
-                            if (FILL) P.idx[base[t] + cnt[t]] = W.po[k];
-                            cnt[t]++;
-                        }
+                        if (FILL && in) P.idx[base[t] + cnt[t]] = W.po[k];
+                        cnt[t] += in;
                     }
                 }
                 __syncwarp();
@@ -255,38 +256,21 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 }
 
 // ---- per-row ascending sort --------------------------------------------------
-// One warp per row.  Rows of up to 32*K entries sit in registers, element
-// e = 32 r + lane in register r of lane `lane`; a bitonic network sorts them
-// (partners 32 apart or more are in the same lane, closer ones are exchanged
-// by shuffles).  Longer rows fall back to a heap sort by one thread.
+// One warp per row.  Rows of up to 128 entries sit in registers (element
+// e = 32 r + lane in register r) and a bitonic network sorts them: partners 32
+// apart or more are in the same lane, closer ones are exchanged by shuffles.
+// Rows of up to 512 entries use the same in-register network with 8 or 16
+// registers per lane.  Longer rows are sorted by a loop-based network in which every
+// compare-exchange puts the smaller value at the lower index (each merge stage
+// starts by comparing mirrored positions of a block), so a row of any length
+// sorts in place as if padded with +infinity: a pair whose upper index is past
+// the end never moves.  Rows of up to kSmemRow entries are sorted in shared
+// memory, longer ones directly in global memory.  The size classes run as
+// separate launches: one kernel holding the fully unrolled networks of every
+// size overflowed the instruction cache.
 constexpr int kSortWarps = 4;
-constexpr int kRowMaxReg = 1024;
-
-__device__ void heap_sort_global(int32_t *a, long long n)
-{
-    auto sift = [&](long long start, long long end) {
-        long long root = start;
-        while (2 * root + 1 < end) {
-            long long child = 2 * root + 1;
-            if (child + 1 < end && a[child] < a[child + 1]) child++;
-            if (a[root] < a[child]) {
-                int32_t t = a[root];
-                a[root] = a[child];
-                a[child] = t;
-                root = child;
-            } else {
-                return;
-            }
-        }
-    };
-    for (long long s = n / 2 - 1; s >= 0; s--) sift(s, n);
-    for (long long e = n - 1; e > 0; e--) {
-        int32_t t = a[0];
-        a[0] = a[e];
-        a[e] = t;
-        sift(0, e);
-    }
-}
+constexpr int kRegRow = 512;    // longest row sorted in registers (16 per lane)
+constexpr int kSmemRow = 2048;  // longest row sorted in shared memory
 
 template <int K>
 __device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len)
@@ -333,31 +317,103 @@ __device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len)
     }
 }
 
-__global__ void __launch_bounds__(kSortWarps * 32)
-    row_sort_kernel(int n, const int64_t *__restrict__ offs, int32_t *idx, long long capacity)
+// ascending compare-exchange of a[i] and a[h] (i < h), skipped past the end
+__device__ __forceinline__ void cmpx(int32_t *a, int i, int h, int len)
+{
+    if (h < len) {
+        const int32_t x = a[i], y = a[h];
+        if (y < x) {
+            a[i] = y;
+            a[h] = x;
+        }
+    }
+}
+
+// Warp-cooperative sort of a[0 .. len) (shared or global memory).
+__device__ void warp_sort_mem(int32_t *a, int len)
 {
     const int lane = threadIdx.x & 31;
+    int P = 1;
+    while (P < len) P <<= 1;
+    const int half = P >> 1;
+    for (int k = 2; k <= P; k <<= 1) {
+        const int hk = k >> 1;
+        for (int i = lane; i < half; i += 32) {  // mirrored pairs within blocks of k
+            const int lo = (i / hk) * k + (i % hk);
+            cmpx(a, lo, lo ^ (k - 1), len);
+        }
+        __syncwarp();
+        for (int j = k >> 2; j > 0; j >>= 1) {
+            for (int i = lane; i < half; i += 32) {
+                const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+                cmpx(a, lo, lo | j, len);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Rows whose length lies in (lo, hi], one warp per row.  Each size class is its
+// own launch so that only one register network is resident in the instruction
+// cache at a time.
+template <int K>
+__global__ void __launch_bounds__(kSortWarps * 32)
+    row_sort_reg_kernel(int n, const int64_t *__restrict__ offs, int32_t *idx, long long capacity)
+{
+    if (offs[n] > capacity) return;
+    constexpr int lo = K == 1 ? 1 : 16 * K, hi = 32 * K;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
+         i += (gridDim.x * blockDim.x) >> 5) {
+        const long long o = offs[i];
+        const int len = (int)(offs[i + 1] - o);
+        if (len > lo && len <= hi) warp_bitonic_row<K>(idx + o, len);
+        __syncwarp();
+    }
+}
+
+// Rows of up to 128 entries (three small networks in one launch).
+__global__ void __launch_bounds__(kSortWarps * 32)
+    row_sort_small_kernel(int n, const int64_t *__restrict__ offs, int32_t *idx, long long capacity)
+{
     if (offs[n] > capacity) return;
     for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
          i += (gridDim.x * blockDim.x) >> 5) {
         const long long o = offs[i];
         const int len = (int)(offs[i + 1] - o);
-        if (len <= 1) continue;
+        if (len <= 1 || len > 128) continue;
         int32_t *row = idx + o;
         if (len <= 32)
             warp_bitonic_row<1>(row, len);
         else if (len <= 64)
             warp_bitonic_row<2>(row, len);
-        else if (len <= 128)
+        else
             warp_bitonic_row<4>(row, len);
-        else if (len <= 256)
-            warp_bitonic_row<8>(row, len);
-        else if (len <= 512)
-            warp_bitonic_row<16>(row, len);
-        else if (len <= kRowMaxReg)
-            warp_bitonic_row<32>(row, len);
-        else if (lane == 0)
-            heap_sort_global(row, len);
+        __syncwarp();
+    }
+}
+
+// Rows longer than kRegRow: shared memory up to kSmemRow, global memory beyond.
+__global__ void __launch_bounds__(kSortWarps * 32)
+    row_sort_mem_kernel(int n, const int64_t *__restrict__ offs, int32_t *idx, long long capacity)
+{
+    __shared__ int32_t sbuf[kSortWarps][kSmemRow];
+    const int lane = threadIdx.x & 31;
+    int32_t *sb = sbuf[threadIdx.x >> 5];
+    if (offs[n] > capacity) return;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
+         i += (gridDim.x * blockDim.x) >> 5) {
+        const long long o = offs[i];
+        const int len = (int)(offs[i + 1] - o);
+        if (len <= kRegRow) continue;
+        int32_t *row = idx + o;
+        if (len <= kSmemRow) {
+            for (int e = lane; e < len; e += 32) sb[e] = row[e];
+            __syncwarp();
+            warp_sort_mem(sb, len);
+            for (int e = lane; e < len; e += 32) row[e] = sb[e];
+        } else {
+            warp_sort_mem(row, len);
+        }
         __syncwarp();
     }
 }
@@ -434,7 +490,11 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
     if (capacity == 0) return P3T_OK;
     e = dispatch_nbr<true>(c, a);
     if (e) return e;
-    row_sort_kernel<<<8 * c->sm_count, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
+    const int grid = 8 * c->sm_count;
+    row_sort_small_kernel<<<grid, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
+    row_sort_reg_kernel<8><<<grid, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
+    row_sort_reg_kernel<16><<<grid, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
+    row_sort_mem_kernel<<<grid, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
     return check_launch(c);
 }
 

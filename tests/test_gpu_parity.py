@@ -164,3 +164,22 @@ def test_extreme_scales_switch_filters_off_or_on(scale):
     assert np.median(e) <= 1e-5 and np.percentile(e, 99) <= 1e-4
     o2, i2 = oracle.neighbours_brute(c.x, c.y, c.z, 0.8 * r_out)
     assert np.array_equal(g["offs"], o2) and np.array_equal(g["idx"], i2)
+
+
+def test_long_neighbour_rows_take_every_sort_path():
+    # short rows (Plummer), rows of ~700 (shared-memory sort) and ~3000 (sorted in
+    # global memory) from two tight clumps; every row must equal the brute force
+    p = synth.plummer(3000, 41)
+    rng = np.random.default_rng(41)
+    xs, ys, zs = [p.x], [p.y], [p.z]
+    for n_c, centre in ((700, 2.0), (3000, -2.0)):
+        q = rng.normal(size=(3, n_c)) * 0.002 + centre
+        xs.append(q[0]), ys.append(q[1]), zs.append(q[2])
+    x, y, z = np.concatenate(xs), np.concatenate(ys), np.concatenate(zs)
+    n = x.size
+    c = synth.Cluster(x, y, z, np.full(n, 1.0 / n), *(np.zeros(n) for _ in range(3)))
+    g = run_gpu(c, p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05), pot=False)
+    o2, i2 = oracle.neighbours_brute(x, y, z, 0.05)
+    lens = np.diff(o2)
+    assert lens.max() > 2048 and ((lens > 128) & (lens <= 2048)).any() and (lens <= 32).any()
+    assert np.array_equal(g["offs"], o2) and np.array_equal(g["idx"], i2)
