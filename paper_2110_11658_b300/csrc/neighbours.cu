@@ -16,6 +16,7 @@
 // for bit.
 #include <climits>
 #include <cstdint>
+#include <type_traits>
 
 #include "p3t_internal.cuh"
 
@@ -42,9 +43,8 @@ struct NbrSmem {
     int stk[kNbrStack];
     int2 lq[kNbrLeafQ];
     int lqo[kNbrLeafQ + 1];
-    float4 pp[32];
-    int pj[32];
-    int po[32];
+    float4 pp[32];  // 16 pairs of staged sources (pair layout)
+    int pj[32];     // their positions in key order
 };
 
 template <int TPL, bool FILL>
@@ -95,8 +95,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                     glz = __double2float_rn(dsub(glo.z, Oz));
         const float ghx = __double2float_rn(dsub(ghi.x, Ox)), ghy = __double2float_rn(dsub(ghi.y, Oy)),
                     ghz = __double2float_rn(dsub(ghi.z, Oz));
+        // targets: coordinates relative to c_g, original index `me`; an empty slot sits
+        // at 1e30 so that no FP32 test counts it (its rare FP64 path checks si < 0)
         float px[TPL], py[TPL], pz[TPL];
-        int si[TPL], cnt[TPL];
+        int si[TPL], cnt[TPL], me[TPL];
         long long base[TPL];
         float A = 0.f;
 #pragma unroll
@@ -111,10 +113,12 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 pz[t] = (h.z - fhz) + (l.z - flz);
                 si[t] = s;
                 A = fmaxf(A, fmaxf(fabsf(px[t]), fmaxf(fabsf(py[t]), fabsf(pz[t]))));
-                if (FILL) base[t] = P.offs[T.perm[s]];
+                me[t] = T.perm[s];
+                if (FILL) base[t] = P.offs[me[t]];
             } else {
-                px[t] = py[t] = pz[t] = 0.f;
+                px[t] = py[t] = pz[t] = 1e30f;
                 si[t] = -1;
+                me[t] = -1;
             }
         }
 #pragma unroll
@@ -128,6 +132,59 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         // r2 < in_lo: neighbour; r2 > in_hi: not; otherwise decide in FP64
         const float in_lo = pair_filter ? rl2_f - tpair : -1.f;
         const float in_hi = pair_filter ? rl2_f + tpair : INFINITY;
+        // |r2 - in_mid| <= in_rad covers [in_lo, in_hi] with a 2x margin (infinite: filter off)
+        const float in_mid = 0.5f * in_lo + 0.5f * in_hi, in_rad = in_hi - in_lo;
+        float2 NPX[TPL], NPY[TPL], NPZ[TPL];
+#pragma unroll
+        for (int t = 0; t < TPL; t++)
+            NPX[t] = make_float2(-px[t], -px[t]), NPY[t] = make_float2(-py[t], -py[t]),
+            NPZ[t] = make_float2(-pz[t], -pz[t]);
+        const float4 *pq = W.pp;
+        float *pb = reinterpret_cast<float *>(W.pp) + 8 * (lane >> 1) + (lane & 1);
+        // one pair of staged sources (pair layout {x0 x1 y0 y1} {z0 z1 o0 o1}, o the
+        // original index) against this lane's targets; FP32x2 distances
+        auto test_pair = [&](int k, int ns, auto tail) {
+            constexpr bool kTail = decltype(tail)::value;
+            const float4 b0 = pq[2 * k], b1 = pq[2 * k + 1];
+            const float2 X = make_float2(b0.x, b0.y), Y = make_float2(b0.z, b0.w);
+            const float2 Z = make_float2(b1.x, b1.y);
+            const int o0 = __float_as_int(b1.z), o1 = __float_as_int(b1.w);
+#pragma unroll
+            for (int t = 0; t < TPL; t++) {
+                const float2 dx = __fadd2_rn(X, NPX[t]), dy = __fadd2_rn(Y, NPY[t]), dz = __fadd2_rn(Z, NPZ[t]);
+                float2 r2 = __fmul2_rn(dx, dx);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                bool in0 = r2.x < in_lo && o0 != me[t];
+                bool in1 = r2.y < in_lo && o1 != me[t];
+                const float2 d = __fadd2_rn(r2, make_float2(-in_mid, -in_mid));
+                if (fminf(fabsf(d.x), fabsf(d.y)) <= in_rad) {  // an undecided pair (rare)
+#pragma unroll
+                    for (int e = 0; e < 2; e++) {
+                        const float r2e = e ? r2.y : r2.x;
+                        const int oe = e ? o1 : o0;
+                        if (si[t] >= 0 && (!kTail || e == 0 || 2 * k + 1 < ns) && oe != me[t] &&
+                            r2e >= in_lo && r2e <= in_hi) {
+                            const double4_32a a = T.sp[si[t]], b = T.sp[W.pj[2 * k + e]];
+                            double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
+                            const bool in = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < rl2_d;
+                            if (e)
+                                in1 = in;
+                            else
+                                in0 = in;
+                        }
+                    }
+                }
+                if (FILL) {
+                    if (in0) P.idx[base[t] + cnt[t]] = o0;
+                    cnt[t] += in0;
+                    if (in1) P.idx[base[t] + cnt[t]] = o1;
+                    cnt[t] += in1;
+                } else {
+                    cnt[t] += (int)in0 + (int)in1;
+                }
+            }
+        };
 
         int sp = 1;
         if (lane == 0) W.stk[0] = pack_range(cid, 1);
@@ -214,33 +271,24 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                     }
                     int j = W.lq[lo].x + (pos - W.lqo[lo]);
                     const float4 h = T.ph[j], l = T.pl[j];
-                    W.pp[lane] = make_float4((h.x - fhx) + (l.x - flx), (h.y - fhy) + (l.y - fly),
-                                             (h.z - fhz) + (l.z - flz), 0.f);
+                    pb[0] = (h.x - fhx) + (l.x - flx);
+                    pb[2] = (h.y - fhy) + (l.y - fly);
+                    pb[4] = (h.z - fhz) + (l.z - flz);
+                    pb[6] = __int_as_float(T.perm[j]);
                     W.pj[lane] = j;
-                    if (FILL) W.po[lane] = T.perm[j];
                 }
                 __syncwarp();
                 const int ns = min(32, lqp - c0);
-#pragma unroll 4
-                for (int k = 0; k < ns; k++) {
-                    const float4 s = W.pp[k];
-                    const int j = W.pj[k];
-#pragma unroll
-                    for (int t = 0; t < TPL; t++) {
-                        const float dx = s.x - px[t], dy = s.y - py[t], dz = s.z - pz[t];
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        const bool other = si[t] >= 0 && si[t] != j;
-                        bool in = other && r2 < in_lo;
-                        if (other && r2 >= in_lo && r2 <= in_hi) {  // inside the band (rare)
-                            const double4_32a a = T.sp[si[t]], b = T.sp[j];
-                            double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
-                            double d2 = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez));
-                            in = d2 < rl2_d;
-                        }
-                        if (FILL && in) P.idx[base[t] + cnt[t]] = W.po[k];
-                        cnt[t] += in;
-                    }
+                if ((ns & 1) && lane == 0) {  // pad: far away, never a neighbour
+                    float *b = reinterpret_cast<float *>(W.pp) + 8 * (ns >> 1);
+                    b[1] = b[3] = b[5] = 1e30f;
+                    b[7] = __int_as_float(-1);
                 }
+                __syncwarp();
+                const int nfull = ns >> 1;
+#pragma unroll 2
+                for (int k = 0; k < nfull; k++) test_pair(k, ns, std::false_type());
+                if (ns & 1) test_pair(nfull, ns, std::true_type());
                 __syncwarp();
             }
             lqn = lqp = 0;

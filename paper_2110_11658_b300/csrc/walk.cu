@@ -46,7 +46,7 @@ constexpr int kStackCap = 32 * 22 + 64;      // ranges per warp; see the bound b
 constexpr float kU = 5.9604644775390625e-8f;  // 2^-24, FP32 unit round-off
 constexpr int kCellPairUnroll = 2;           // pairs of cells per unrolled iteration
 constexpr int kPartPairUnroll = 2;           // pairs of particles per unrolled iteration
-constexpr int kMinBlocksTpl1 = 5;            // resident blocks per SM at TPL = 1 (96 registers)
+constexpr int kMinBlocksTpl1 = 6;            // resident blocks per SM at TPL = 1 (80 registers)
 
 // Stack bound: children ranges are pushed so that the stack stays sorted by
 // level (deepest on top).  Ranges of level l are created only while popping
@@ -328,6 +328,20 @@ struct NbrCount {
     int si[TPL];   // target positions in key order (-1: empty slot)
     int cnt[TPL];
     float lo, hi;  // r2 < lo: neighbour; r2 > hi: not; otherwise decide in FP64
+    // |r2 - mid| <= rad covers [lo, hi] (the rare undecided band) with a 2x margin,
+    // so rounding of mid and of r2 - mid cannot leave a band pair out
+    float mid, rad;
+    __device__ void set(float l, float h)  // l <= h; h infinite: every pair to FP64
+    {
+        lo = l, hi = h;
+        mid = 0.5f * l + 0.5f * h;
+        rad = h - l;
+    }
+    __device__ void off()  // no counting in this walk
+    {
+        lo = hi = -INFINITY;
+        mid = 0.f, rad = -1.f;
+    }
 };
 
 template <typename Real, int TPL, bool POT, bool NBR>
@@ -491,18 +505,62 @@ __device__ __forceinline__ void eval_cells_x2(const WarpSmem<float> &W, int ncel
     __syncwarp();
 }
 
-// Fused neighbour count of one pair (target t, staged source k), FP32 band + FP64 decision.
-template <int TPL>
-__device__ __forceinline__ void count_pair(const WarpSmem<float> &W, const Tree &T, const Cluster &K,
-                                           NbrCount<TPL> &NC, int t, int k, float r2f)
+// One pair of staged particles (k: pair index) against this lane's targets.
+template <int TPL, bool POT, bool NBR, bool TAIL>
+__device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &T, const Cluster &K,
+                                          const float4 *pq, int k, int ns, float inv_dr, float nrin_dr,
+                                          const float2 (&NPX)[TPL], const float2 (&NPY)[TPL],
+                                          const float2 (&NPZ)[TPL], AccX2<TPL> &A, NbrCount<TPL> &NC)
 {
-    if (r2f < NC.lo) {
-        NC.cnt[t]++;
-    } else if (r2f <= NC.hi) {  // inside the band: decide in FP64
-        const int sj = W.pj[k];
-        const double4_32a a = T.sp[NC.si[t] < 0 ? sj : NC.si[t]], b = T.sp[sj];
-        const double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
-        NC.cnt[t] += dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < K.rl2_d;
+    const float4 b0 = pq[2 * k], b1 = pq[2 * k + 1];
+    const float2 X = make_float2(b0.x, b0.y), Y = make_float2(b0.z, b0.w);
+    const float2 Z = make_float2(b1.x, b1.y), Mj = make_float2(b1.z, b1.w);
+#pragma unroll
+    for (int t = 0; t < TPL; t++) {
+        // d = x_j - x_i
+        const float2 dx = fadd2(X, NPX[t]), dy = fadd2(Y, NPY[t]), dz = fadd2(Z, NPZ[t]);
+        float2 r2 = fmul2(dx, dx);
+        r2 = ffma2(dy, dy, r2);
+        r2 = ffma2(dz, dz, r2);
+        const float2 ri = make_float2(rsqrtf(fmaxf(r2.x, kR2Min)), rsqrtf(fmaxf(r2.y, kR2Min)));
+        const float2 r = fmul2(r2, ri);
+        // x = (r - r_in)/(r_out - r_in) clamped to [0, 1]
+        const float2 x = make_float2(__saturatef(fmaf(r.x, inv_dr, nrin_dr)),
+                                     __saturatef(fmaf(r.y, inv_dr, nrin_dr)));
+        float2 w = ffma2(f2(-20.f), x, f2(70.f));
+        w = ffma2(w, x, f2(-84.f));
+        w = ffma2(w, x, f2(35.f));
+        const float2 x2 = fmul2(x, x);
+        const float2 Wt = fmul2(w, fmul2(x2, x2));
+        const float2 ri3 = fmul2(fmul2(ri, ri), ri);
+        const float2 f = fmul2(fmul2(Mj, Wt), ri3);
+        A.p[t][0] = ffma2(f, dx, A.p[t][0]);
+        A.p[t][1] = ffma2(f, dy, A.p[t][1]);
+        A.p[t][2] = ffma2(f, dz, A.p[t][2]);
+        if (POT) {
+            A.p[t][3].x -= r2.x > 0.f ? Mj.x * ri.x : 0.f;
+            A.p[t][3].y -= r2.y > 0.f ? Mj.y * ri.y : 0.f;
+        }
+        if (NBR) {
+            // neighbour iff |x_j - x_i|^2 < r_list^2 in FP64: below the band in FP32
+            // counts at once, inside it (rare) is decided with the FP64 operations; the
+            // pair with itself is counted (r2 = 0) and removed at the end
+            const bool yreal = !TAIL || 2 * k + 1 < ns;
+            NC.cnt[t] += (r2.x < NC.lo) + (yreal && r2.y < NC.lo);
+            const float2 d = fadd2(r2, f2(-NC.mid));
+            if (fminf(fabsf(d.x), fabsf(d.y)) <= NC.rad) {
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const float r2e = e ? r2.y : r2.x;
+                    if ((e == 0 || yreal) && r2e >= NC.lo && r2e <= NC.hi) {
+                        const int sj = W.pj[2 * k + e];
+                        const double4_32a a = T.sp[NC.si[t] < 0 ? sj : NC.si[t]], b = T.sp[sj];
+                        const double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
+                        NC.cnt[t] += dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < K.rl2_d;
+                    }
+                }
+            }
+        }
     }
 }
 
@@ -555,46 +613,12 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
             b[1] = b[0], b[3] = b[2], b[5] = b[4], b[7] = 0.f;
         }
         __syncwarp();
-        const int npairs = (ns + 1) >> 1;
+        const int nfull = ns >> 1;
 #pragma unroll kPartPairUnroll
-        for (int k = 0; k < npairs; k++) {
-            const float4 b0 = pq[2 * k], b1 = pq[2 * k + 1];
-            const float2 X = make_float2(b0.x, b0.y), Y = make_float2(b0.z, b0.w);
-            const float2 Z = make_float2(b1.x, b1.y), Mj = make_float2(b1.z, b1.w);
-#pragma unroll
-            for (int t = 0; t < TPL; t++) {
-                // d = x_j - x_i
-                const float2 dx = fadd2(X, NPX[t]), dy = fadd2(Y, NPY[t]), dz = fadd2(Z, NPZ[t]);
-                float2 r2 = fmul2(dx, dx);
-                r2 = ffma2(dy, dy, r2);
-                r2 = ffma2(dz, dz, r2);
-                const float2 ri = make_float2(rsqrtf(fmaxf(r2.x, kR2Min)), rsqrtf(fmaxf(r2.y, kR2Min)));
-                const float2 r = fmul2(r2, ri);
-                // x = (r - r_in)/(r_out - r_in) clamped to [0, 1]
-                const float2 x = make_float2(__saturatef(fmaf(r.x, inv_dr, nrin_dr)),
-                                             __saturatef(fmaf(r.y, inv_dr, nrin_dr)));
-                float2 w = ffma2(f2(-20.f), x, f2(70.f));
-                w = ffma2(w, x, f2(-84.f));
-                w = ffma2(w, x, f2(35.f));
-                const float2 x2 = fmul2(x, x);
-                const float2 Wt = fmul2(w, fmul2(x2, x2));
-                const float2 ri3 = fmul2(fmul2(ri, ri), ri);
-                const float2 f = fmul2(fmul2(Mj, Wt), ri3);
-                A.p[t][0] = ffma2(f, dx, A.p[t][0]);
-                A.p[t][1] = ffma2(f, dy, A.p[t][1]);
-                A.p[t][2] = ffma2(f, dz, A.p[t][2]);
-                if (POT) {
-                    A.p[t][3].x -= r2.x > 0.f ? Mj.x * ri.x : 0.f;
-                    A.p[t][3].y -= r2.y > 0.f ? Mj.y * ri.y : 0.f;
-                }
-                if (NBR) {
-                    // neighbour iff |x_j - x_i|^2 < r_list^2 in FP64; the pair with
-                    // itself is counted here (r2 = 0) and removed at the end
-                    count_pair(W, P.T, K, NC, t, 2 * k, r2.x);
-                    if (2 * k + 1 < ns) count_pair(W, P.T, K, NC, t, 2 * k + 1, r2.y);
-                }
-            }
-        }
+        for (int k = 0; k < nfull; k++)
+            part_pair<TPL, POT, NBR, false>(W, P.T, K, pq, k, ns, inv_dr, nrin_dr, NPX, NPY, NPZ, A, NC);
+        if (ns & 1)  // the last pair holds the zero-mass pad
+            part_pair<TPL, POT, NBR, true>(W, P.T, K, pq, nfull, ns, inv_dr, nrin_dr, NPX, NPY, NPZ, A, NC);
         __syncwarp();
     }
     A.fold();
@@ -708,9 +732,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
             const float A = amax * 1.0001f;
             const float band = kU * (24.f * K.rl2_f + 32.f * A * K.rl_f + 128.f * kU * Rf * K.rl_f) +
                                64.f * kU * kU * (A + 2.f * K.rl_f) * (A + 2.f * K.rl_f);
-            NC.lo = filter_ok ? K.rl2_f - band : -1.f;        // filter off: every pair to FP64
-            NC.hi = filter_ok ? K.rl2_f + band : INFINITY;
-            if (!count_here) NC.lo = NC.hi = -INFINITY;      // this cluster is counted elsewhere
+            if (!count_here)
+                NC.off();  // this cluster is counted elsewhere
+            else if (filter_ok)
+                NC.set(K.rl2_f - band, K.rl2_f + band);
+            else
+                NC.set(-1.f, INFINITY);  // filter off: every pair decided in FP64
         }
         typename std::conditional<kMixed, AccX2<TPL>, Acc<double, TPL>>::type A;
         A.zero_all();
@@ -770,10 +797,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                     } else if (mac == 0 && bb == 0) {
                         open = false;
                     } else {
+                        // undecided in FP32 (rare): the exact FP64 test; the group box and
+                        // r_out^2 are reloaded so they need no registers during the walk
                         fb = filter_ok;
                         const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
-                        open = dist2_point_box(cm.x, cm.y, cm.z, glo, ghi) < cl.w ||
-                               dist2_box_box(glo, ghi, cl, ch) < rout2_d;
+                        const double4_32a bl = T.glo[g], bh = T.ghi[g];
+                        open = dist2_point_box(cm.x, cm.y, cm.z, bl, bh) < cl.w ||
+                               dist2_box_box(bl, bh, cl, ch) < T.cl[cid].rout2_d;
                     }
                 } else {
                     const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
