@@ -613,7 +613,9 @@ __device__ void write_node(Tree &T, int k, double M, const double com[3], const 
                        __double2float_rn(dsub(hi[2], O[2])), __int_as_float(leaf ? tp.y : tp.w));
     w[3] = make_float4(clx, cly, clz, __double2float_rn(M));
     w[4] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
-    w[5] = make_float4((float)q[4], (float)q[5], 0.f, 0.f);
+    // band of the walk's FP32 opening-angle test (R as the walk rounds it)
+    const Band bm = fp32_band((float)O[3] * 1.0001f, __double2float_rn(ro2));
+    w[5] = make_float4((float)q[4], (float)q[5], bm.a, bm.b);
 }
 
 template <bool Q64>

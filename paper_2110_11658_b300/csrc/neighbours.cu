@@ -58,7 +58,6 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
     Meta *meta = T.meta;
     const int ng = meta->n_groups;
     const int nn = meta->n_nodes;
-    const float k_rel = 8.f * kUn;
     bool allowed = true;
     if (FILL) allowed = P.offs[T.n] <= P.capacity;
     if (FILL && !allowed) {
@@ -83,7 +82,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         const float rl_f = K.rl_f, rl2_f = K.rl2_f;
         const double rl2_d = K.rl2_d;
         const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && rl2_f > 1e-20f && rl2_f < 1e30f;
-        const float k_abs = 8.f * kUn * Rf, k_sq = 16.f * kUn * kUn * Rf * Rf;
+        const Band bl_band = fp32_band(Rf, rl2_f);  // box-box test against r_list
         const double cgx = dmul(0.5, dadd(glo.x, ghi.x));
         const double cgy = dmul(0.5, dadd(glo.y, ghi.y));
         const double cgz = dmul(0.5, dadd(glo.z, ghi.z));
@@ -212,8 +211,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                         float uy = fmaxf(fmaxf(b.y - ghy, gly - cc.y), 0.f);
                         float uz = fmaxf(fmaxf(b.z - ghz, glz - cc.z), 0.f);
                         float e2 = ux * ux + uy * uy + uz * uz;
-                        float tol = k_rel * (e2 + rl2_f) + k_abs * (ux + uy + uz) + k_sq;
-                        bb = e2 < rl2_f - tol ? 1 : (e2 > rl2_f + tol ? 0 : 2);
+                        const float db = e2 - rl2_f;
+                        bb = fabsf(db) > fmaf(bl_band.a, e2, bl_band.b) ? (db < 0.f ? 1 : 0) : 2;
                     }
                     if (bb == 2) {
                         bb = dist2_box_box(glo, ghi, T.lo[node], T.hi[node]) < rl2_d;

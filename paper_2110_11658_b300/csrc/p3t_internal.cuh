@@ -26,6 +26,25 @@ constexpr int kLevels = 21;          // key bits per axis = tree depth
 constexpr int kMaxLevelSlots = 24;   // per-level bookkeeping arrays
 constexpr long long kSpinLimit = 1LL << 24;  // bounded waits: ~1 s with backoff
 constexpr int kWalkRecord = 6;               // float4 per node in Tree::wn
+constexpr float kFp32U = 5.9604644775390625e-8f;  // 2^-24, FP32 unit round-off
+
+// Error band of an FP32 squared-distance test d2 < r2 in a cluster frame of half
+// size R (coordinates relative to the frame centre carry <= 2^-24 R rounding):
+// |d2_fp32 - d2_exact| <= k_rel (d2 + r2) + k_abs |t|_1 + k_sq, with about twice
+// the derived bound in each constant.  With |t|_1 <= sqrt(3 d2) <= sqrt(3)
+// (d2 / 2r + r / 2) this is at most A d2 + B, a band linear in d2 whose two
+// coefficients depend only on the threshold r and R; A and B come rounded up.
+struct Band {
+    float a, b;
+};
+__host__ __device__ inline Band fp32_band(float R, float r2)
+{
+    const float k_rel = 8.f * kFp32U, k_abs = 8.f * kFp32U * R, k_sq = 16.f * kFp32U * kFp32U * R * R;
+    if (!(r2 > 0.f) || r2 > 3e38f) return Band{0.f, 0.f};  // r = 0 or infinite: d2 < r2 is fixed
+    const float r = sqrtf(r2) * 1.0001f;
+    return Band{(k_rel + 0.8661f * k_abs / r) * 1.001f,
+                (k_rel * r2 * 1.0001f + 0.8661f * k_abs * r + k_sq) * 1.001f};
+}
 
 // ---- device metadata block (one per context) -------------------------------
 struct Meta {

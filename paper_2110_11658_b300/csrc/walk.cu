@@ -663,7 +663,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
     const int ng = meta->n_groups;
     const int nn = meta->n_nodes;
     const int tile = P.tile;
-    const float k_rel = 8.f * kU;
 
     while (true) {
         int g = 0;
@@ -672,11 +671,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         if (g >= ng) break;
         const int2 gr = T.grp[g];
         const double4_32a glo = T.glo[g], ghi = T.ghi[g];
-        // the group's cluster: its frame O, its root (node cid) and the filter band
-        // (|FP32 - FP64| of a squared distance, with a factor ~2 to spare):
-        // k_rel*(d2 + r2) + k_abs*|t|_1 + k_sq, every coordinate relative to O being
-        // within R and carrying <= 2^-24 R rounding.  Outside a safe range of scales
-        // the filter is off and every test is exact FP64.
+        // the group's cluster: its frame O, its root (node cid) and the filter bands
+        // (|FP32 - FP64| of a squared distance bounded by A d2 + B, see fp32_band;
+        // every coordinate relative to O is within R and carries <= 2^-24 R
+        // rounding).  Outside a safe range of scales the filter is off and every
+        // test is exact FP64.
         const int cid = T.cid_s[gr.x];
         const Cluster &K = T.cl[cid];
         const double *fr = K.frame;
@@ -686,8 +685,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         const double rout2_d = K.rout2_d;
         const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && rout2_f > 1e-20f && rout2_f < 1e30f;
         const bool count_here = NBR && K.counted;
-        const float k_abs = 8.f * kU * Rf;
-        const float k_sq = 16.f * kU * kU * Rf * Rf;
+        const Band bb_band = fp32_band(Rf, rout2_f);  // the box-box test against r_out
         GroupFrame F;
         F.cx = dmul(0.5, dadd(glo.x, ghi.x));
         F.cy = dmul(0.5, dadd(glo.y, ghi.y));
@@ -759,7 +757,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
             // ---- opening test (test and staging data come in one load batch)
             bool open = false, is_leaf = false;
             int cinfo = 0, ccount = 0;
-            bool fb = false;
             float4 ra, rd, rq0, rq1;  // node record: COM hi / lo + M / quadrupole
             if (node >= 0) {
                 if (kMixed) {
@@ -771,35 +768,35 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                     rq1 = rec[5];
                     cinfo = __float_as_int(b.w);
                     ccount = __float_as_int(c.w);
-                    int mac = 2, bb = 2;
+                    // FP32 tests with the band |d2 - r2| <= A d2 + B: the opening angle's
+                    // A, B per node (record slot 5), r_out's per cluster
+                    bool dec_m = false, dec_b = false, in_m = false, in_b = false;
                     if (filter_ok) {
                         // point-box: COM against the group box
                         const float tx = fmaxf(fmaxf(glx - ra.x, ra.x - ghx), 0.f);
                         const float ty = fmaxf(fmaxf(gly - ra.y, ra.y - ghy), 0.f);
                         const float tz = fmaxf(fmaxf(glz - ra.z, ra.z - ghz), 0.f);
                         const float d2 = tx * tx + ty * ty + tz * tz;
-                        if (isinf(ra.w)) {
-                            mac = 1;
-                        } else {
-                            const float tol = k_rel * (d2 + ra.w) + k_abs * (tx + ty + tz) + k_sq;
-                            mac = d2 < ra.w - tol ? 1 : (d2 > ra.w + tol ? 0 : 2);
-                        }
+                        const float dm = d2 - ra.w;  // -inf for theta = 0: always open
+                        dec_m = fabsf(dm) > fmaf(rq1.z, d2, rq1.w);
+                        in_m = dm < 0.f;
                         // box-box against r_out
                         const float ux = fmaxf(fmaxf(b.x - ghx, glx - c.x), 0.f);
                         const float uy = fmaxf(fmaxf(b.y - ghy, gly - c.y), 0.f);
                         const float uz = fmaxf(fmaxf(b.z - ghz, glz - c.z), 0.f);
                         const float e2 = ux * ux + uy * uy + uz * uz;
-                        const float tol2 = k_rel * (e2 + rout2_f) + k_abs * (ux + uy + uz) + k_sq;
-                        bb = e2 < rout2_f - tol2 ? 1 : (e2 > rout2_f + tol2 ? 0 : 2);
+                        const float db = e2 - rout2_f;
+                        dec_b = fabsf(db) > fmaf(bb_band.a, e2, bb_band.b);
+                        in_b = db < 0.f;
                     }
-                    if (mac == 1 || bb == 1) {
+                    if ((dec_m && in_m) || (dec_b && in_b)) {
                         open = true;
-                    } else if (mac == 0 && bb == 0) {
+                    } else if (dec_m && dec_b) {
                         open = false;
                     } else {
                         // undecided in FP32 (rare): the exact FP64 test; the group box and
                         // r_out^2 are reloaded so they need no registers during the walk
-                        fb = filter_ok;
+                        nfallback += filter_ok;
                         const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
                         const double4_32a bl = T.glo[g], bh = T.ghi[g];
                         open = dist2_point_box(cm.x, cm.y, cm.z, bl, bh) < cl.w ||
@@ -815,7 +812,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                 }
                 is_leaf = cinfo < 0;
             }
-            if (kMixed) nfallback += __popc(__ballot_sync(0xffffffffu, fb));
             const bool accept = node >= 0 && !open;
             const bool open_int = node >= 0 && open && !is_leaf;
             const bool open_leaf = node >= 0 && open && is_leaf;
@@ -914,6 +910,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                 if (count_here) P.nbr_count[o] = NC.cnt[t] - 1;  // minus the pair with itself
             }
         }
+        const unsigned nfb = __reduce_add_sync(0xffffffffu, (unsigned)nfallback);
         if (lane == 0) {
             if (P.n_cell) atomicAdd(P.n_cell, (unsigned long long)(ncell * gr.y));
             if (P.n_part) atomicAdd(P.n_part, (unsigned long long)(npart * gr.y));
@@ -921,8 +918,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                 P.grp_cells[g] = ncell;
                 P.grp_parts[g] = npart;
             }
-            if (nfallback) atomicAdd((unsigned long long *)&meta->fallback_tests,
-                                     (unsigned long long)nfallback);
+            if (nfb) atomicAdd((unsigned long long *)&meta->fallback_tests, (unsigned long long)nfb);
         }
         __syncwarp();
     }
