@@ -191,6 +191,12 @@ int p3t_export_tree(p3t_ctx *c, uint64_t *keys, int32_t *perm, int32_t *level, i
  * opened leaves.  Filled only when the walk ran after p3t_set_debug(c, 1). */
 int p3t_group_counts(p3t_ctx *c, int64_t *n_cell, int64_t *n_part);
 
+/* Number of exact FP64 decisions the FP32 filters have handed over (opening
+ * and box tests that fell inside their error bands) since the last build;
+ * host int64.  A diagnostic of the filters' efficiency: the results do not
+ * depend on it.  Synchronises the context's stream. */
+int p3t_filter_fallbacks(p3t_ctx *c, int64_t *count);
+
 /* 1: record per-group counts in the walk (slightly slower); 0: off (default). */
 int p3t_set_debug(p3t_ctx *c, int on);
 

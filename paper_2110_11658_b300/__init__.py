@@ -40,7 +40,7 @@ EXPORTED = [
     "p3t_step_host", "p3t_status", "p3t_tree_info", "p3t_export_tree", "p3t_group_counts",
     "p3t_set_debug", "p3t_error_string", "p3t_morton_order_noalloc",
     "p3t_graph_capture", "p3t_graph_launch", "p3t_graph_destroy", "p3t_reserve", "p3t_scratch_bytes",
-    "p3t_batch_move", "p3t_batch_scatter_neighbours",
+    "p3t_batch_move", "p3t_batch_scatter_neighbours", "p3t_filter_fallbacks",
 ]
 P3T_NOALLOC_MAX_N = 65536
 
@@ -104,6 +104,7 @@ _sig = {
     "p3t_graph_launch": [_vp],
     "p3t_graph_destroy": [_vp],
     "p3t_reserve": [_vp, _i64, C.c_int32],
+    "p3t_filter_fallbacks": [_vp, C.POINTER(_i64)],
     "p3t_scratch_bytes": [C.POINTER(p3t_params), _i64, C.c_int32, C.POINTER(_i64)],
     "p3t_batch_move": [_vp, C.c_int32, _i64, _vp, _vp, C.c_int32, C.POINTER(p3t_seg_array), C.c_int32],
     "p3t_batch_scatter_neighbours": [_vp, C.c_int32, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -355,6 +356,12 @@ class Context:
                "p3t_export_tree")
         self.check()
         return o
+
+    def filter_fallbacks(self) -> int:
+        """FP64 decisions taken by the FP32 filters since the last build (diagnostic)."""
+        v = C.c_int64(0)
+        _check(_lib.p3t_filter_fallbacks(self._h, C.byref(v)), "p3t_filter_fallbacks")
+        return v.value
 
     def group_counts(self):
         t = self._torch

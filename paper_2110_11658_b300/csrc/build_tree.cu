@@ -128,7 +128,11 @@ __device__ __forceinline__ double dec_double(unsigned long long e)
 }
 
 // Per-cluster bounding box (exact, order-preserving integer min/max) and input
-// validation.  A warp whose particles all belong to one cluster reduces first.
+// validation.  Each warp keeps running minima and maxima for its current cluster
+// in registers across its grid-stride iterations and reduces them into the
+// cluster table (warp shuffle + 6 atomics) only when the cluster changes and at
+// the end; a warp whose 32 particles straddle a cluster boundary updates the
+// table per lane for that iteration.
 __global__ void __launch_bounds__(kBuildThreads)
     bbox_kernel(int n, const double *__restrict__ x, const double *__restrict__ y,
                 const double *__restrict__ z, const double *__restrict__ m,
@@ -136,47 +140,67 @@ __global__ void __launch_bounds__(kBuildThreads)
 {
     const int lane = threadIdx.x & 31;
     bool bad = false;
+    int cur = -1;  // cluster of the running extrema (warp-uniform)
+    unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0, 0, 0};
+    auto flush = [&]() {
+        if (cur < 0) return;
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], o);
+                const unsigned long long bb = __shfl_xor_sync(0xffffffffu, mx[d], o);
+                mn[d] = a < mn[d] ? a : mn[d];
+                mx[d] = bb > mx[d] ? bb : mx[d];
+            }
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                atomicMin(&cl[cur].minmax[d], mn[d]);
+                atomicMax(&cl[cur].minmax[3 + d], mx[d]);
+            }
+#pragma unroll
+        for (int d = 0; d < 3; d++) mn[d] = ~0ULL, mx[d] = 0;
+        cur = -1;
+    };
     for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
          base += (long long)gridDim.x * blockDim.x) {
         const long long i = base + lane;
-        unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0, 0, 0};
+        unsigned long long e[3] = {~0ULL, ~0ULL, ~0ULL};
+        bool ok = false;
         int c = -1;
         if (i < n) {
             const double p[3] = {x[i], y[i], z[i]};
             const double mi = m[i];
-            const bool ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(mi) && mi >= 0.0;
+            ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(mi) && mi >= 0.0;
             bad |= !ok;
             c = cid ? cid[i] : 0;
             if (ok)
 #pragma unroll
-                for (int d = 0; d < 3; d++) mn[d] = mx[d] = enc_double(p[d]);
+                for (int d = 0; d < 3; d++) e[d] = enc_double(p[d]);
         }
         const int c0 = __shfl_sync(0xffffffffu, c, 0);
         if (__all_sync(0xffffffffu, c < 0 || c == c0)) {
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], o);
-                    const unsigned long long bb = __shfl_xor_sync(0xffffffffu, mx[d], o);
-                    mn[d] = a < mn[d] ? a : mn[d];
-                    mx[d] = bb > mx[d] ? bb : mx[d];
-                }
+            if (c0 != cur) {
+                flush();
+                cur = c0;
             }
-            if (lane == 0 && c0 >= 0)
+            if (ok)
 #pragma unroll
                 for (int d = 0; d < 3; d++) {
-                    atomicMin(&cl[c0].minmax[d], mn[d]);
-                    atomicMax(&cl[c0].minmax[3 + d], mx[d]);
+                    mn[d] = e[d] < mn[d] ? e[d] : mn[d];
+                    mx[d] = e[d] > mx[d] ? e[d] : mx[d];
                 }
-        } else if (c >= 0) {
+        } else if (ok) {  // a cluster boundary inside this warp's 32 particles
 #pragma unroll
             for (int d = 0; d < 3; d++) {
-                atomicMin(&cl[c].minmax[d], mn[d]);
-                atomicMax(&cl[c].minmax[3 + d], mx[d]);
+                atomicMin(&cl[c].minmax[d], e[d]);
+                atomicMax(&cl[c].minmax[3 + d], e[d]);
             }
         }
     }
+    flush();
     if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(meta, P3T_ERR_INVALID_INPUT);
 }
 
@@ -613,9 +637,7 @@ __device__ void write_node(Tree &T, int k, double M, const double com[3], const 
                        __double2float_rn(dsub(hi[2], O[2])), __int_as_float(leaf ? tp.y : tp.w));
     w[3] = make_float4(clx, cly, clz, __double2float_rn(M));
     w[4] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
-    // band of the walk's FP32 opening-angle test (R as the walk rounds it)
-    const Band bm = fp32_band((float)O[3] * 1.0001f, __double2float_rn(ro2));
-    w[5] = make_float4((float)q[4], (float)q[5], bm.a, bm.b);
+    w[5] = make_float4((float)q[4], (float)q[5], 0.f, 0.f);
 }
 
 template <bool Q64>

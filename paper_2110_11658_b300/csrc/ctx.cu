@@ -390,6 +390,19 @@ int p3t_group_counts(p3t_ctx *c, int64_t *n_cell, int64_t *n_part)
     return P3T_OK;
 }
 
+int p3t_filter_fallbacks(p3t_ctx *c, int64_t *count)
+{
+    if (!c || !count) return P3T_ERR_INVALID_ARG;
+    if (!c->built) return P3T_ERR_ORDER;
+    int e = p3t_status(c);
+    if (e) return e;
+    long long v = 0;
+    if (cudaMemcpy(&v, &c->meta->fallback_tests, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    *count = v;
+    return P3T_OK;
+}
+
 int p3t_set_debug(p3t_ctx *c, int on)
 {
     if (!c) return P3T_ERR_INVALID_ARG;

@@ -34,6 +34,10 @@ constexpr float kFp32U = 5.9604644775390625e-8f;  // 2^-24, FP32 unit round-off
 // the derived bound in each constant.  With |t|_1 <= sqrt(3 d2) <= sqrt(3)
 // (d2 / 2r + r / 2) this is at most A d2 + B, a band linear in d2 whose two
 // coefficients depend only on the threshold r and R; A and B come rounded up.
+// Tight near d2 = r2 and for r of the order of the distances tested, so it
+// serves the box tests against the cluster radii (r_out, r_list); the opening
+// angle's radius can be arbitrarily small (single-particle nodes), where A
+// would swamp every test, so that test keeps the |t|_1 form.
 struct Band {
     float a, b;
 };

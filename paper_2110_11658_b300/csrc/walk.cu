@@ -672,10 +672,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         const int2 gr = T.grp[g];
         const double4_32a glo = T.glo[g], ghi = T.ghi[g];
         // the group's cluster: its frame O, its root (node cid) and the filter bands
-        // (|FP32 - FP64| of a squared distance bounded by A d2 + B, see fp32_band;
-        // every coordinate relative to O is within R and carries <= 2^-24 R
-        // rounding).  Outside a safe range of scales the filter is off and every
-        // test is exact FP64.
+        // (|FP32 - FP64| of a squared distance <= k_rel (d2 + r2) + k_abs |t|_1 +
+        // k_sq, about twice the derived bound, every coordinate relative to O being
+        // within R and carrying <= 2^-24 R rounding; for a fixed threshold r this is
+        // at most A d2 + B, see fp32_band).  Outside a safe range of scales the
+        // filter is off and every test is exact FP64.
         const int cid = T.cid_s[gr.x];
         const Cluster &K = T.cl[cid];
         const double *fr = K.frame;
@@ -685,6 +686,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         const double rout2_d = K.rout2_d;
         const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && rout2_f > 1e-20f && rout2_f < 1e30f;
         const bool count_here = NBR && K.counted;
+        const float k_rel = 8.f * kU, k_abs = 8.f * kU * Rf, k_sq = 16.f * kU * kU * Rf * Rf;
         const Band bb_band = fp32_band(Rf, rout2_f);  // the box-box test against r_out
         GroupFrame F;
         F.cx = dmul(0.5, dadd(glo.x, ghi.x));
@@ -768,8 +770,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                     rq1 = rec[5];
                     cinfo = __float_as_int(b.w);
                     ccount = __float_as_int(c.w);
-                    // FP32 tests with the band |d2 - r2| <= A d2 + B: the opening angle's
-                    // A, B per node (record slot 5), r_out's per cluster
+                    // FP32 tests with their error bands: the opening angle's band keeps the
+                    // |t|_1 term (it follows sqrt(d2) for nodes of every size, down to
+                    // single particles); the box test against r_out uses A d2 + B
                     bool dec_m = false, dec_b = false, in_m = false, in_b = false;
                     if (filter_ok) {
                         // point-box: COM against the group box
@@ -778,7 +781,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                         const float tz = fmaxf(fmaxf(glz - ra.z, ra.z - ghz), 0.f);
                         const float d2 = tx * tx + ty * ty + tz * tz;
                         const float dm = d2 - ra.w;  // -inf for theta = 0: always open
-                        dec_m = fabsf(dm) > fmaf(rq1.z, d2, rq1.w);
+                        dec_m = isinf(ra.w) ||
+                                fabsf(dm) > k_rel * (d2 + ra.w) + k_abs * (tx + ty + tz) + k_sq;
                         in_m = dm < 0.f;
                         // box-box against r_out
                         const float ux = fmaxf(fmaxf(b.x - ghx, glx - c.x), 0.f);
