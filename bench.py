@@ -37,11 +37,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # DRAM bytes of one walk_kernel launch per particle, from the ncu capture summarised
-# in profiles/walk_kernel_plummer_kroupa_n262144.md (16.19 MB at N = 2^18; the
+# in profiles/walk_kernel_plummer_kroupa_n262144.md (17.25 MB at N = 2^18; the
 # traffic grows with N).  Valid only for the kernel sources it was measured on:
 # if they change, the roofline's traffic is reported as null until re-measured.
-WALK_TRAFFIC = {"sources": {"walk.cu": "ceb66d06b033c26e", "p3t_internal.cuh": "1041cea4ada2d9c9"},
-                "bytes_per_particle": 16189952 / 262144}
+WALK_TRAFFIC = {"sources": {"walk.cu": "e4b071658d0b0e22", "p3t_internal.cuh": "1846c913bb5c5164"},
+                "bytes_per_particle": 17250816 / 262144}
 
 N_DEFAULT = 1_000_000
 THETA = 0.4
