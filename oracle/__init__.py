@@ -49,6 +49,10 @@ def _lib():
         lib.orc_neighbours_brute.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_int64, _I64,
                                              _I64, _I64, _I32]
         lib.orc_kick.argtypes = [C.c_int64, C.c_double, _D, _D, _D, _D, _D, _D]
+        lib.orc_changeover_dWdx.restype = C.c_double
+        lib.orc_changeover_dWdx.argtypes = [C.c_double] * 3
+        lib.orc_irregular.argtypes = [C.c_int64, _D, _D, _D, _D, _D, _D, _D, C.c_double, C.c_double,
+                                      _I64, _I32, _D, _D, _D, _D]
         lib.orc_bounding_cube.argtypes = [C.c_int64, _D, _D, _D, _D]
         lib.orc_interleave.restype = C.c_uint64
         lib.orc_interleave.argtypes = [C.c_int64] * 3
@@ -131,6 +135,31 @@ def kick(dt, ax, ay, az, vx, vy, vz):
     _lib().orc_kick(vx.shape[0], dt, _p(ax, _D), _p(ay, _D), _p(az, _D), _p(vx, _D),
                     _p(vy, _D), _p(vz, _D))
     return vx, vy, vz
+
+
+def changeover_dWdx(r: float, r_in: float, r_out: float) -> float:
+    """dW/dx (the bracket of Eq. 7), 0 outside 0 <= x < 1."""
+    return _lib().orc_changeover_dWdx(r, r_in, r_out)
+
+
+def irregular(x, y, z, m, vx, vy, vz, r_in, r_out, offsets, idx, scales=False):
+    """Irregular force F_I (Eq. 1) and jerk dF_I/dt (Eq. 2) over neighbour rows
+    (offsets int64[n+1], idx int32).  Returns (f (n,3), jerk (n,3)) and, with
+    scales=True, also the per-particle sums of the term magnitudes."""
+    x, y, z, m, vx, vy, vz = map(_f64, (x, y, z, m, vx, vy, vz))
+    n = x.shape[0]
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    if idx.size == 0:
+        idx = np.zeros(1, np.int32)
+    f = np.zeros((n, 3))
+    jerk = np.zeros((n, 3))
+    sf = np.zeros(n) if scales else None
+    sj = np.zeros(n) if scales else None
+    _lib().orc_irregular(n, _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D), _p(vx, _D), _p(vy, _D),
+                         _p(vz, _D), r_in, r_out, _p(offsets, _I64), _p(idx, _I32), _p(f, _D),
+                         _p(jerk, _D), _p(sf, _D), _p(sj, _D))
+    return (f, jerk, sf, sj) if scales else (f, jerk)
 
 
 def bounding_cube(x, y, z):

@@ -167,6 +167,71 @@ void orc_kick(int64_t n, double dt, const double *ax, const double *ay, const do
     }
 }
 
+/* dW/dx of Eq. 6 in the variable x of Eqs. 8-10: the bracket of Eq. 7,
+ * -140 x^6 + 420 x^5 - 420 x^4 + 140 x^3 (= 140 x^3 (1 - x)^3) for 0 <= x < 1,
+ * and 0 outside. */
+double orc_changeover_dWdx(double r, double r_in, double r_out)
+{
+    double y = r / r_out;
+    double gamma = r_in / r_out;
+    double x = (y - gamma) / (1.0 - gamma);
+    if (x < 0.0 || x >= 1.0) return 0.0;
+    double x3 = x * x * x;
+    double x4 = x3 * x, x5 = x4 * x, x6 = x5 * x;
+    return -140.0 * x6 + 420.0 * x5 - 420.0 * x4 + 140.0 * x3;
+}
+
+/* Irregular (neighbour) force of Eq. 1 and its time derivative of Eq. 2 for
+ * every particle, summed over the particle's neighbour row (offsets / idx as
+ * produced by rule 11, original indices):
+ *   F_I,i = sum_j K m_j d / r^3
+ *   dF_I,i/dt = sum_j m_j [K (u / r^3 - 3 (d.u) d / r^5) + Kdot d / r^3]
+ * with d = x_j - x_i, u = v_j - v_i (attraction, as in Part 1) and
+ *   Kdot = dK/dt = -dW/dx (d.u) / (r (r_cut - r_in)),
+ * the chain rule through x = (r/r_cut - gamma)/(1 - gamma).  Readings: Eq. 2
+ * as printed drops m_j and K from its middle term and Eq. 7 prints K' with the
+ * opposite sign; both are taken as the exact derivative of Eq. 1.  Pairs at
+ * r = 0 (singular) and at r >= r_cut (K = K' = 0) contribute nothing.  The
+ * sums run over the row in its order.  scale_f / scale_j (nullable) receive the
+ * sums of the magnitudes of the terms, sum K m / r^2 and
+ * sum m (K |u| / r^2 + 3 K |d.u| / r^3 + |Kdot| / r), per particle. */
+void orc_irregular(int64_t n, const double *x, const double *y, const double *z,
+                   const double *m, const double *vx, const double *vy, const double *vz,
+                   double r_in, double r_out, const int64_t *offsets, const int32_t *idx,
+                   double *f, double *jerk, double *scale_f, double *scale_j)
+{
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; i++) {
+        double F[3] = {0, 0, 0}, J[3] = {0, 0, 0}, sf = 0.0, sj = 0.0;
+        for (int64_t e = offsets[i]; e < offsets[i + 1]; e++) {
+            int64_t j = idx[e];
+            double d[3] = {x[j] - x[i], y[j] - y[i], z[j] - z[i]};
+            double u[3] = {vx[j] - vx[i], vy[j] - vy[i], vz[j] - vz[i]};
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 == 0.0) continue;
+            double r = sqrt(r2);
+            double k = orc_changeover_K(r, r_in, r_out);
+            if (k == 0.0) continue;
+            double du = d[0] * u[0] + d[1] * u[1] + d[2] * u[2];
+            double kdot = -orc_changeover_dWdx(r, r_in, r_out) * du / (r * (r_out - r_in));
+            double f3 = m[j] / (r2 * r);
+            for (int c = 0; c < 3; c++) {
+                F[c] += k * f3 * d[c];
+                J[c] += k * f3 * u[c] - 3.0 * k * f3 * (du / r2) * d[c] + kdot * f3 * d[c];
+            }
+            sf += k * m[j] / r2;
+            sj += m[j] * (k * sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / r2 +
+                          3.0 * k * fabs(du) / (r2 * r) + fabs(kdot) / r);
+        }
+        for (int c = 0; c < 3; c++) {
+            f[3 * i + c] = F[c];
+            jerk[3 * i + c] = J[c];
+        }
+        if (scale_f) scale_f[i] = sf;
+        if (scale_j) scale_j[i] = sj;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Part 2: the reference tree                                                */
 /* ------------------------------------------------------------------------ */
