@@ -191,6 +191,32 @@ int p3t_export_tree(p3t_ctx *c, uint64_t *keys, int32_t *perm, int32_t *level, i
  * opened leaves.  Filled only when the walk ran after p3t_set_debug(c, 1). */
 int p3t_group_counts(p3t_ctx *c, int64_t *n_cell, int64_t *n_part);
 
+/* Irregular (neighbour) force F_I of Eq. 1 and its time derivative (Eq. 2) of
+ * every particle, summed over the particle's neighbour row: the near side of
+ * the changeover (K = 1 - W of Eq. 6) that the Hermite integrator needs.
+ *   F_I,i     = sum_j K m_j d / r^3
+ *   dF_I,i/dt = sum_j m_j [K (u / r^3 - 3 (d.u) d / r^5) + Kdot d / r^3]
+ * with d = x_j - x_i, u = v_j - v_i (attraction), Kdot = dK/dt =
+ * -dW/dx (d.u) / (r (r_out - r_in)) (the exact derivative of Eq. 1; Eq. 2 as
+ * printed drops m_j and K from its middle term and Eq. 7 prints K' with the
+ * opposite sign).  Pairs at r = 0 and at r >= r_out contribute nothing, so rows
+ * must hold every j with r < r_out (r_list >= r_out).
+ * Arguments (device, original order, n particles): offsets int64[n+1] and idx
+ * int32 (row i = idx[offsets[i] .. offsets[i+1]), indices in [0, n)), x, y, z,
+ * m, vx, vy, vz double[n]; outputs f* (F_I) and j* (dF_I/dt) double[n].  r_in
+ * and r_out are the context's, or each particle's cluster radii after a
+ * p3t_build_tree_batch with cluster parameters of these n particles.  The
+ * context's precision selects the arithmetic: P3T_FP64 repeats the FP64
+ * operations of the definition pair by pair; P3T_FP32_MIXED forms d and u in
+ * FP64 and evaluates each pair in FP32.  Positions and velocities may differ
+ * from those the tree was built on (predicted states).  Requires a built tree
+ * (P3T_ERR_ORDER); an index outside [0, n) latches P3T_ERR_INVALID_INPUT and
+ * is skipped.  Asynchronous on the context's stream. */
+int p3t_irregular(p3t_ctx *c, int64_t n, const int64_t *offsets, const int32_t *idx,
+                  const double *x, const double *y, const double *z, const double *m,
+                  const double *vx, const double *vy, const double *vz, double *fx, double *fy,
+                  double *fz, double *jx, double *jy, double *jz);
+
 /* Number of exact FP64 decisions the FP32 filters have handed over (opening
  * and box tests that fell inside their error bands) since the last build;
  * host int64.  A diagnostic of the filters' efficiency: the results do not

@@ -194,7 +194,7 @@ double orc_changeover_dWdx(double r, double r_in, double r_out)
  * r = 0 (singular) and at r >= r_cut (K = K' = 0) contribute nothing.  The
  * sums run over the row in its order.  scale_f / scale_j (nullable) receive the
  * sums of the magnitudes of the terms, sum K m / r^2 and
- * sum m (K |u| / r^2 + 3 K |d.u| / r^3 + |Kdot| / r), per particle. */
+ * sum m (K |u| / r^3 + 3 K |d.u| / r^4 + |Kdot| / r^2), per particle. */
 void orc_irregular(int64_t n, const double *x, const double *y, const double *z,
                    const double *m, const double *vx, const double *vy, const double *vz,
                    double r_in, double r_out, const int64_t *offsets, const int32_t *idx,
@@ -220,8 +220,8 @@ void orc_irregular(int64_t n, const double *x, const double *y, const double *z,
                 J[c] += k * f3 * u[c] - 3.0 * k * f3 * (du / r2) * d[c] + kdot * f3 * d[c];
             }
             sf += k * m[j] / r2;
-            sj += m[j] * (k * sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / r2 +
-                          3.0 * k * fabs(du) / (r2 * r) + fabs(kdot) / r);
+            sj += m[j] * (k * sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / (r2 * r) +
+                          3.0 * k * fabs(du) / (r2 * r2) + fabs(kdot) / r2);
         }
         for (int c = 0; c < 3; c++) {
             f[3 * i + c] = F[c];

@@ -40,7 +40,7 @@ EXPORTED = [
     "p3t_step_host", "p3t_status", "p3t_tree_info", "p3t_export_tree", "p3t_group_counts",
     "p3t_set_debug", "p3t_error_string", "p3t_morton_order_noalloc",
     "p3t_graph_capture", "p3t_graph_launch", "p3t_graph_destroy", "p3t_reserve", "p3t_scratch_bytes",
-    "p3t_batch_move", "p3t_batch_scatter_neighbours", "p3t_filter_fallbacks",
+    "p3t_batch_move", "p3t_batch_scatter_neighbours", "p3t_filter_fallbacks", "p3t_irregular",
 ]
 P3T_NOALLOC_MAX_N = 65536
 
@@ -105,6 +105,7 @@ _sig = {
     "p3t_graph_destroy": [_vp],
     "p3t_reserve": [_vp, _i64, C.c_int32],
     "p3t_filter_fallbacks": [_vp, C.POINTER(_i64)],
+    "p3t_irregular": [_vp, _i64] + [_vp] * 15,
     "p3t_scratch_bytes": [C.POINTER(p3t_params), _i64, C.c_int32, C.POINTER(_i64)],
     "p3t_batch_move": [_vp, C.c_int32, _i64, _vp, _vp, C.c_int32, C.POINTER(p3t_seg_array), C.c_int32],
     "p3t_batch_scatter_neighbours": [_vp, C.c_int32, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -356,6 +357,21 @@ class Context:
                "p3t_export_tree")
         self.check()
         return o
+
+    def irregular(self, offsets, idx, x, y, z, m, vx, vy, vz, f=None, jerk=None):
+        """Irregular force F_I (Eq. 1) and its time derivative (Eq. 2) over neighbour
+        rows (p3t_irregular); returns (f, jerk) as (3, n) float64 CUDA tensors."""
+        t = self._torch
+        n = x.numel()
+        if f is None:
+            f = t.empty(3, n, dtype=t.float64, device=x.device)
+        if jerk is None:
+            jerk = t.empty(3, n, dtype=t.float64, device=x.device)
+        args = [_ptr(a, t.float64, n, nm) for a, nm in zip((x, y, z, m, vx, vy, vz), ("x", "y", "z", "m", "vx", "vy", "vz"))]
+        outs = [_ptr(f[q], t.float64, n, "f") for q in range(3)] + [_ptr(jerk[q], t.float64, n, "jerk") for q in range(3)]
+        _check(_lib.p3t_irregular(self._h, n, _ptr(offsets, t.int64, n + 1, "offsets"), _ptr(idx, t.int32, None, "idx"),
+                                  *args, *outs), "p3t_irregular")
+        return f, jerk
 
     def filter_fallbacks(self) -> int:
         """FP64 decisions taken by the FP32 filters since the last build (diagnostic)."""

@@ -390,6 +390,18 @@ int p3t_group_counts(p3t_ctx *c, int64_t *n_cell, int64_t *n_part)
     return P3T_OK;
 }
 
+int p3t_irregular(p3t_ctx *c, int64_t n, const int64_t *offsets, const int32_t *idx,
+                  const double *x, const double *y, const double *z, const double *m,
+                  const double *vx, const double *vy, const double *vz, double *fx, double *fy,
+                  double *fz, double *jx, double *jy, double *jz)
+{
+    if (!c || !offsets || !idx || !x || !y || !z || !m || !vx || !vy || !vz || !fx || !fy || !fz ||
+        !jx || !jy || !jz || n <= 0 || n >= (1LL << 31) - 1)
+        return P3T_ERR_INVALID_ARG;
+    if (!c->built || !c->meta) return P3T_ERR_ORDER;
+    return irregular(c, (int)n, offsets, idx, x, y, z, m, vx, vy, vz, fx, fy, fz, jx, jy, jz);
+}
+
 int p3t_filter_fallbacks(p3t_ctx *c, int64_t *count)
 {
     if (!c || !count) return P3T_ERR_INVALID_ARG;

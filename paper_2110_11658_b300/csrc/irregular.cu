@@ -1,0 +1,177 @@
+// Irregular (neighbour) force and its time derivative over the neighbour rows
+// (Sec. 2.1, Eqs. 1, 2, 6-10): the other side of the changeover, which the
+// Hermite integrator of the P3T scheme needs at every irregular step:
+//   F_I,i    = sum_j K m_j d / r^3
+//   dF_I,i/dt = sum_j m_j [K (u / r^3 - 3 (d.u) d / r^5) + Kdot d / r^3]
+// with d = x_j - x_i, u = v_j - v_i, K = 1 - W, and Kdot = dK/dt =
+// -dW/dx (d.u) / (r (r_out - r_in)) (the exact derivative of Eq. 1: Eq. 2 as
+// printed drops m_j and K from its middle term and Eq. 7 prints K' with the
+// opposite sign).  Pairs at r = 0 (singular) and at r >= r_out (K = 0)
+// contribute nothing.
+//
+// One warp per target row; lanes take every 32nd entry and their partial sums
+// are reduced by shuffles in FP64.  With a tree of the same particles built,
+// targets are visited in key order, so warps running together share their
+// neighbours in the caches.  The FP64 form repeats the oracle's operations per
+// pair (no contraction); the mixed form takes the position and velocity
+// differences in FP64 and evaluates the pair in FP32 (its relative error per
+// term is that of FP32 on exact differences, ~1e-7).
+#include <cstdint>
+
+#include "p3t_internal.cuh"
+
+namespace p3t {
+
+constexpr int kIrrWarps = 8;
+
+struct IrrArgs {
+    int n;
+    const int64_t *offs;
+    const int32_t *idx;
+    const double *x, *y, *z, *m, *vx, *vy, *vz;
+    double *fx, *fy, *fz, *jx, *jy, *jz;
+    const int32_t *order;   // targets in this order (key order) or null
+    const int32_t *inv;     // original -> key order (per-cluster radii) or null
+    const int32_t *cid_s;   // cluster of each particle, key order
+    const Cluster *cl;      // per-cluster radii (null: r_in, r_out below)
+    double r_in, r_out;
+    Meta *meta;
+};
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(kIrrWarps * 32) irregular_kernel(IrrArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * kIrrWarps;
+    bool bad = false;
+    for (int k = blockIdx.x * kIrrWarps + (threadIdx.x >> 5); k < a.n; k += nw) {
+        const int i = a.order ? a.order[k] : k;
+        double r_in = a.r_in, r_out = a.r_out;
+        if (a.cl) {
+            const Cluster &K = a.cl[a.cid_s[a.inv[i]]];
+            r_in = K.r_in, r_out = K.r_out;
+        }
+        const double dr = dsub(r_out, r_in);
+        const double xi = a.x[i], yi = a.y[i], zi = a.z[i];
+        const double uxi = a.vx[i], uyi = a.vy[i], uzi = a.vz[i];
+        const long long o0 = a.offs[i], o1 = a.offs[i + 1];
+        double F[3] = {0.0, 0.0, 0.0}, J[3] = {0.0, 0.0, 0.0};
+        // mixed form: FP32 constants of the changeover
+        const float inv_dr_f = (float)(1.0 / dr), rin_dr_f = (float)(r_in / dr);
+        float Ff[3] = {0.f, 0.f, 0.f}, Jf[3] = {0.f, 0.f, 0.f};
+        for (long long e = o0 + lane; e < o1; e += 32) {
+            const int j = a.idx[e];
+            if ((unsigned)j >= (unsigned)a.n) {
+                bad = true;
+                continue;
+            }
+            const double d0 = dsub(a.x[j], xi), d1 = dsub(a.y[j], yi), d2 = dsub(a.z[j], zi);
+            const double u0 = dsub(a.vx[j], uxi), u1 = dsub(a.vy[j], uyi), u2 = dsub(a.vz[j], uzi);
+            const double mj = a.m[j];
+            if (MIXED) {
+                const float dx = (float)d0, dy = (float)d1, dz = (float)d2;
+                const float ux = (float)u0, uy = (float)u1, uz = (float)u2;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                const float ri = rsqrtf(fmaxf(r2, 4e-26f));
+                const float r = r2 * ri;
+                const float xx = __saturatef(fmaf(r, inv_dr_f, -rin_dr_f));
+                // K = 1 - W(x) = W(1 - x) (the changeover is symmetric), evaluated as
+                // y^4 (35 - 84 y + 70 y^2 - 20 y^3) with y = 1 - x: no cancellation as
+                // x -> 1, so K keeps FP32's relative accuracy; dW/dx = 140 x^3 y^3
+                const float yy = 1.f - xx;
+                const float y2 = yy * yy;
+                const float Kw = (y2 * y2) * (35.f + yy * (-84.f + yy * (70.f - 20.f * yy)));
+                const float dw = 140.f * (xx * xx * xx) * (y2 * yy);
+                const float du = dx * ux + dy * uy + dz * uz;
+                const float f3 = r2 > 0.f ? (float)mj * ri * ri * ri : 0.f;
+                const float kf = Kw * f3;
+                const float kdot = -dw * du * ri * inv_dr_f;  // dK/dt
+                const float c1 = kdot * f3 - 3.f * kf * du * ri * ri;
+                Ff[0] += kf * dx, Ff[1] += kf * dy, Ff[2] += kf * dz;
+                Jf[0] += kf * ux + c1 * dx;
+                Jf[1] += kf * uy + c1 * dy;
+                Jf[2] += kf * uz + c1 * dz;
+            } else {
+                // the oracle's operations, in its order
+                const double r2 = dadd(dadd(dmul(d0, d0), dmul(d1, d1)), dmul(d2, d2));
+                if (r2 == 0.0) continue;
+                const double r = dsqrt(r2);
+                const double y = ddiv(r, r_out), gamma = ddiv(r_in, r_out);
+                const double x = ddiv(dsub(y, gamma), dsub(1.0, gamma));
+                double W, dw;
+                if (x < 0.0) {
+                    W = 0.0, dw = 0.0;
+                } else if (x >= 1.0) {
+                    continue;  // K = 0, K' = 0
+                } else {
+                    const double x3 = dmul(dmul(x, x), x);
+                    const double x4 = dmul(x3, x), x5 = dmul(x4, x), x6 = dmul(x5, x),
+                                 x7 = dmul(x6, x);
+                    W = dadd(dsub(dadd(dmul(-20.0, x7), dmul(70.0, x6)), dmul(84.0, x5)),
+                             dmul(35.0, x4));
+                    dw = dadd(dsub(dadd(dmul(-140.0, x6), dmul(420.0, x5)), dmul(420.0, x4)),
+                              dmul(140.0, x3));
+                }
+                const double kk = dsub(1.0, W);
+                if (kk == 0.0) continue;
+                const double du = dadd(dadd(dmul(d0, u0), dmul(d1, u1)), dmul(d2, u2));
+                const double kdot = ddiv(dmul(-dw, du), dmul(r, dr));
+                const double f3 = ddiv(mj, dmul(r2, r));
+                const double kf = dmul(kk, f3);
+                const double c3 = dmul(dmul(dmul(3.0, kk), f3), ddiv(du, r2));
+                const double kd = dmul(kdot, f3);
+                const double d[3] = {d0, d1, d2}, u[3] = {u0, u1, u2};
+#pragma unroll
+                for (int q = 0; q < 3; q++) {
+                    F[q] = dadd(F[q], dmul(kf, d[q]));
+                    J[q] = dadd(J[q], dadd(dsub(dmul(kf, u[q]), dmul(c3, d[q])), dmul(kd, d[q])));
+                }
+            }
+        }
+        if (MIXED) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) F[q] = (double)Ff[q], J[q] = (double)Jf[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 3; q++) F[q] = warp_sum_d(F[q]), J[q] = warp_sum_d(J[q]);
+        if (lane == 0) {
+            a.fx[i] = F[0], a.fy[i] = F[1], a.fz[i] = F[2];
+            a.jx[i] = J[0], a.jy[i] = J[1], a.jz[i] = J[2];
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(a.meta, P3T_ERR_INVALID_INPUT);
+}
+
+int irregular(p3t_ctx *c, int n, const int64_t *offs, const int32_t *idx, const double *x,
+              const double *y, const double *z, const double *m, const double *vx,
+              const double *vy, const double *vz, double *fx, double *fy, double *fz, double *jx,
+              double *jy, double *jz)
+{
+    IrrArgs a;
+    a.n = n;
+    a.offs = offs, a.idx = idx;
+    a.x = x, a.y = y, a.z = z, a.m = m, a.vx = vx, a.vy = vy, a.vz = vz;
+    a.fx = fx, a.fy = fy, a.fz = fz, a.jx = jx, a.jy = jy, a.jz = jz;
+    const bool tree = c->built && c->n == n;  // the built tree holds these particles
+    a.order = tree ? c->tree.perm : nullptr;
+    a.inv = tree ? c->tree.inv : nullptr;
+    a.cid_s = tree ? c->tree.cid_s : nullptr;
+    a.cl = (tree && !c->uniform_params) ? c->tree.cl : nullptr;
+    a.r_in = c->prm.r_in, a.r_out = c->prm.r_out;
+    a.meta = c->meta;
+    const int grid = 8 * c->sm_count;
+    if (c->prm.precision == P3T_FP64)
+        irregular_kernel<false><<<grid, kIrrWarps * 32, 0, c->stream>>>(a);
+    else
+        irregular_kernel<true><<<grid, kIrrWarps * 32, 0, c->stream>>>(a);
+    return check_launch(c);
+}
+
+}  // namespace p3t

@@ -367,6 +367,10 @@ inline void restore_state(p3t_ctx *c, const HostState &h)
 
 namespace p3t {
 int ensure_capacity(p3t_ctx *c, long long n);
+int irregular(p3t_ctx *c, int n, const int64_t *offs, const int32_t *idx, const double *x,
+              const double *y, const double *z, const double *m, const double *vx,
+              const double *vy, const double *vz, double *fx, double *fy, double *fz, double *jx,
+              double *jy, double *jz);
 int reserve(p3t_ctx *c, long long n, int n_clusters);
 int check_launch(p3t_ctx *c);
 int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *cprm,

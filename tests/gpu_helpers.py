@@ -85,3 +85,15 @@ def assert_tree_equal(gpu_tree, ref, fp64_moments=True):
         R = 0.5 * (hi - lo).max() + 1e-300
         floor = 1e-12 * ref["M"] * R * R
         assert (np.abs(gpu_tree["Q"] - ref["Q"]).max(axis=1) <= 2e-5 * qs + floor + 1e-300).all()
+
+
+def row_mass_over_r2(x, y, z, m, offs, idx, r_out):
+    """Per particle: sum of m_j / r^2 over its row entries with 0 < r < r_out.  The
+    scale of an error in K of fixed absolute size (FP32 rounding of K), used as a
+    floor when comparing K-weighted sums."""
+    n = len(x)
+    i = np.repeat(np.arange(n), np.diff(offs))
+    j = np.asarray(idx)
+    r2 = (x[j] - x[i]) ** 2 + (y[j] - y[i]) ** 2 + (z[j] - z[i]) ** 2
+    w = np.where((r2 > 0) & (r2 < r_out ** 2), m[j] / np.where(r2 > 0, r2, 1), 0.0)
+    return np.bincount(i, weights=w, minlength=n)

@@ -14,7 +14,7 @@ import torch
 import bench
 import oracle
 import paper_2110_11658_b300 as p3t
-from gpu_helpers import DEV, rel_err, to_dev
+from gpu_helpers import DEV, rel_err, row_mass_over_r2, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -34,12 +34,15 @@ def c2():
     idx = torch.empty(130 * c.n, dtype=torch.int32, device=DEV)
     total = ctx.neighbours(offs, idx)
     fallbacks = ctx.filter_fallbacks()
+    v = [to_dev(c.vx), to_dev(c.vy), to_dev(c.vz)]
+    fi, ji = ctx.irregular(offs, idx, to_dev(c.x), to_dev(c.y), to_dev(c.z), to_dev(c.m), *v)
     gc, gp = ctx.group_counts()
     tree = {k: v.cpu().numpy() for k, v in ctx.export_tree().items()}
     tree["keys"] = tree["keys"].view(np.uint64)
     out = {"c": c, "w": w, "a": torch.stack(a, 1).double().cpu().numpy(), "pot": pot.cpu().numpy(),
            "offs": offs.cpu().numpy(), "idx": idx[:total].cpu().numpy(), "g_cells": gc.cpu().numpy(),
-           "g_parts": gp.cpu().numpy(), "tree": tree, "fallbacks": fallbacks}
+           "g_parts": gp.cpu().numpy(), "tree": tree, "fallbacks": fallbacks,
+           "f_irr": fi.T.cpu().numpy(), "j_irr": ji.T.cpu().numpy()}
     ctx.check()
     ctx.close()
     out["oracle"] = oracle.Tree(c.x, c.y, c.z, c.m, w["theta"], w["r_out"], leaf_cap=16, group_size=32)
@@ -92,3 +95,19 @@ def test_fullsize_fp32_filters_rarely_fall_back(c2):
     # for some node class (e.g. single-particle leaves) shows up here at once
     inter = int(c2["g_cells"].sum() + c2["g_parts"].sum())
     assert c2["fallbacks"] < 2e-5 * inter, (c2["fallbacks"], inter)
+
+
+def test_fullsize_irregular_force_and_jerk(c2):
+    # every row of the 10^6 workload (~10^8 pairs), mixed form, against the oracle
+    c, w = c2["c"], c2["w"]
+    f, j, sf, sj = oracle.irregular(c.x, c.y, c.z, c.m, c.vx, c.vy, c.vz, w["r_in"], w["r_out"],
+                                    c2["offs"], c2["idx"], scales=True)
+    # relative 1e-5 of the term magnitudes, with a floor of FP32 rounding of K times
+    # the unweighted row scale (K = 1 - W is tiny just inside r_out)
+    su = row_mass_over_r2(c.x, c.y, c.z, c.m, c2["offs"], c2["idx"], w["r_out"])
+    ef = np.abs(c2["f_irr"] - f).max(axis=1) / np.maximum(sf + 1e-2 * su, 1e-300)
+    ej = np.abs(c2["j_irr"] - j).max(axis=1) / np.where(sj > 0, sj, 1)
+    assert ef.max() <= 1e-5, ef.max()
+    assert np.median(ef) <= 1e-6 and np.median(ej) <= 1e-6
+    big = sj > 1e-3 * np.median(sj[sj > 0])
+    assert ej[big].max() <= 1e-4, ej[big].max()
