@@ -63,12 +63,13 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
-    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m", "ensemble64", "serve256"],
+    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m", "ensemble64", "serve256", "irregular1m"],
                     help="plummer1m: the throughput benchmark; king2m: theta sweep of the "
                          "mixed and FP64 forms against the direct sum (one line per theta); "
                          "ensemble64: 64 clusters in one graph-captured batched step, autotuned, "
                          "against one-cluster-at-a-time launches; serve256: Poisson request stream over "
-                         "256 resident clusters with continuous batching (p50/p99 latency)")
+                         "256 resident clusters with continuous batching (p50/p99 latency); "
+                         "irregular1m: irregular force and jerk over the neighbour rows of plummer1m")
     ap.add_argument("--requests", type=int, default=10000, help="serve256: requests in the timed stream")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve256: mean arrival rate (requests/s)")
     ap.add_argument("--no-tune", action="store_true", help="ensemble64: use --group-size/--tile/--leaf-cap")
@@ -837,6 +838,70 @@ def serve_run(args):
     }
 
 
+# ---------------------------------------------------------------------------- irregular side
+def irregular_run(args):
+    """Irregular force and jerk (Eqs. 1, 2) over the neighbour rows of the benchmark
+    workload (Plummer 10^6, ~100 neighbours per particle): the mixed and FP64 forms
+    timed with CUDA events (L2 flushed between launches), and the oracle over the
+    same rows on the host cores."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2110_11658_b300 as p3t
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    c, w = workload(args.n, 20211022)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d = {k: t(getattr(c, k)) for k in ("x", "y", "z", "m", "vx", "vy", "vz")}
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    out = {}
+    offs = torch.empty(c.n + 1, dtype=torch.int64, device=dev)
+    idx = None
+    for name, prec in (("mixed", p3t.P3T_FP32_MIXED), ("fp64", p3t.P3T_FP64)):
+        prm = p3t.Params(theta=w["theta"], r_in=w["r_in"], r_out=w["r_out"], r_list=w["r_list"],
+                         leaf_cap=args.leaf_cap, group_size=args.group_size, tile=args.tile, precision=prec)
+        ctx = p3t.Context(prm, stream)
+        ctx.build_tree(d["x"], d["y"], d["z"], d["m"])
+        if idx is None:
+            try:
+                ctx.neighbours(offs, torch.empty(1, dtype=torch.int32, device=dev))
+                total = 0
+            except p3t.P3TError as e:
+                total = e.total
+            idx = torch.empty(max(1, total), dtype=torch.int32, device=dev)
+        pairs = ctx.neighbours(offs, idx)
+        f = torch.empty(3, c.n, dtype=torch.float64, device=dev)
+        jk = torch.empty(3, c.n, dtype=torch.float64, device=dev)
+        run = lambda: ctx.irregular(offs, idx, d["x"], d["y"], d["z"], d["m"], d["vx"], d["vy"], d["vz"], f, jk)  # noqa: E731
+        for _ in range(max(3, args.warmup)):
+            run()
+        ts = _events_ms(stream, run, max(3, args.steps), flush)
+        ctx.check()
+        out[name] = {"ms": float(np.median(ts)), "pairs_per_s": pairs / (float(np.median(ts)) * 1e-3)}
+        ctx.close()
+    ho, hi = offs.cpu().numpy(), idx[:pairs].cpu().numpy()
+    t0 = time.perf_counter()
+    oracle.irregular(c.x, c.y, c.z, c.m, c.vx, c.vy, c.vz, w["r_in"], w["r_out"], ho, hi)
+    t_cpu = time.perf_counter() - t0
+    ms = out["mixed"]["ms"]
+    return {
+        "metric": "irregular force + jerk over the neighbour rows (Eqs. 1, 2)",
+        "value": c.n / (ms * 1e-3), "unit": "particles/s", "n_gpus": 1, "steps": max(3, args.steps),
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 pair arithmetic on f64 differences", "data": "synthetic",
+        "config": {"workload": "plummer_kroupa_n%d_nbr100_irregular" % c.n, "n": c.n, "pairs": int(pairs),
+                   "r_in": w["r_in"], "r_out": w["r_out"],
+                   "l2": "256 MB buffer written between timed launches (L2 is 126 MB)"},
+        "forms": out, "fp64_over_mixed": out["fp64"]["ms"] / ms,
+        "cpu_baseline": {"value": c.n / t_cpu, "unit": "particles/s", "cores": omp_threads(), "kind": "oracle",
+                         "sample": "oracle irregular force and jerk over all %d rows (%d pairs), %.2f s"
+                                   % (c.n, int(pairs), t_cpu)},
+    }
+
+
 def _json_default(o):
     """numpy scalars in result dictionaries."""
     if hasattr(o, "item"):
@@ -846,6 +911,9 @@ def _json_default(o):
 
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload == "irregular1m":
+        print(json.dumps(irregular_run(args), default=_json_default))
+        return
     if args.workload == "serve256":
         print(json.dumps(serve_run(args), default=_json_default))
         return

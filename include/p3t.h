@@ -208,10 +208,13 @@ int p3t_group_counts(p3t_ctx *c, int64_t *n_cell, int64_t *n_part);
  * p3t_build_tree_batch with cluster parameters of these n particles.  The
  * context's precision selects the arithmetic: P3T_FP64 repeats the FP64
  * operations of the definition pair by pair; P3T_FP32_MIXED forms d and u in
- * FP64 and evaluates each pair in FP32.  Positions and velocities may differ
- * from those the tree was built on (predicted states).  Requires a built tree
- * (P3T_ERR_ORDER); an index outside [0, n) latches P3T_ERR_INVALID_INPUT and
- * is skipped.  Asynchronous on the context's stream. */
+ * FP64 and evaluates each pair in FP32 (through double-single splits of every
+ * position and velocity, made once per call in a scratch buffer of the context
+ * of 64 bytes per particle, allocated on first use).  Positions and velocities
+ * may differ from those the tree was built on (predicted states).  Requires a
+ * built tree of the same n particles (P3T_ERR_ORDER); an index outside [0, n)
+ * latches P3T_ERR_INVALID_INPUT and is skipped.  Asynchronous on the context's
+ * stream (except the first mixed call, which allocates). */
 int p3t_irregular(p3t_ctx *c, int64_t n, const int64_t *offsets, const int32_t *idx,
                   const double *x, const double *y, const double *z, const double *m,
                   const double *vx, const double *vy, const double *vz, double *fx, double *fy,

@@ -214,6 +214,7 @@ int p3t_destroy(p3t_ctx *c)
     if (c->blob) cudaFree(c->blob);
     if (c->host_stage) cudaFree(c->host_stage);
     if (c->clusters) cudaFree(c->clusters);
+    if (c->irr_buf) cudaFree(c->irr_buf);
     delete c;
     return P3T_OK;
 }
@@ -398,7 +399,7 @@ int p3t_irregular(p3t_ctx *c, int64_t n, const int64_t *offsets, const int32_t *
     if (!c || !offsets || !idx || !x || !y || !z || !m || !vx || !vy || !vz || !fx || !fy || !fz ||
         !jx || !jy || !jz || n <= 0 || n >= (1LL << 31) - 1)
         return P3T_ERR_INVALID_ARG;
-    if (!c->built || !c->meta) return P3T_ERR_ORDER;
+    if (!c->built || !c->meta || c->n != n) return P3T_ERR_ORDER;  // a tree of these n particles
     return irregular(c, (int)n, offsets, idx, x, y, z, m, vx, vy, vz, fx, fy, fz, jx, jy, jz);
 }
 

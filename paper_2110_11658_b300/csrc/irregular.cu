@@ -10,12 +10,16 @@
 // contribute nothing.
 //
 // One warp per target row; lanes take every 32nd entry and their partial sums
-// are reduced by shuffles in FP64.  With a tree of the same particles built,
-// targets are visited in key order, so warps running together share their
-// neighbours in the caches.  The FP64 form repeats the oracle's operations per
-// pair (no contraction); the mixed form takes the position and velocity
-// differences in FP64 and evaluates the pair in FP32 (its relative error per
-// term is that of FP32 on exact differences, ~1e-7).
+// are reduced by shuffles in FP64.  Targets are visited in key order (the
+// built tree's), so warps running together share their neighbours in the
+// caches.  The FP64 form repeats the oracle's operations per pair (no
+// contraction).  The mixed form first splits every position (relative to its
+// cluster's frame centre O) and velocity into double-single FP32 pairs (hi +
+// lo, made in FP64 once per particle and stored in key order, so a row's
+// neighbours sit close together), then forms each difference as
+// (hi_j - hi_i) + (lo_j - lo_i) and evaluates the pair in FP32: no FP64
+// instruction per pair, and each difference within 2^-23 of its own size plus
+// 2^-46 of the cluster size (the relative error of a term is ~1e-7).
 #include <cstdint>
 
 #include "p3t_internal.cuh"
@@ -23,6 +27,14 @@
 namespace p3t {
 
 constexpr int kIrrWarps = 8;
+
+// double-single state of one particle (mixed form), key order
+struct DsState {
+    float4 ph;  // {hi of x - O, m}
+    float4 pl;  // {lo of x - O, 0}
+    float4 vh;  // {hi of v, 0}
+    float4 vl;  // {lo of v, 0}
+};
 
 struct IrrArgs {
     int n;
@@ -34,9 +46,31 @@ struct IrrArgs {
     const int32_t *inv;     // original -> key order (per-cluster radii) or null
     const int32_t *cid_s;   // cluster of each particle, key order
     const Cluster *cl;      // per-cluster radii (null: r_in, r_out below)
+    const Cluster *cl_frame;  // cluster table (frame centres of the split)
     double r_in, r_out;
     Meta *meta;
+    DsState *ds;            // mixed form: per-particle splits, key order
 };
+
+// mixed form: split position (relative to the cluster's frame centre) and
+// velocity of every particle into hi + lo FP32 pairs, key order
+__global__ void __launch_bounds__(256) irregular_split_kernel(IrrArgs a)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
+        const int i = a.order[k];
+        const double *O = a.cl_frame[a.cid_s[k]].frame;
+        DsState s;
+        ds_split(dsub(a.x[i], O[0]), s.ph.x, s.pl.x);
+        ds_split(dsub(a.y[i], O[1]), s.ph.y, s.pl.y);
+        ds_split(dsub(a.z[i], O[2]), s.ph.z, s.pl.z);
+        ds_split(a.vx[i], s.vh.x, s.vl.x);
+        ds_split(a.vy[i], s.vh.y, s.vl.y);
+        ds_split(a.vz[i], s.vh.z, s.vl.z);
+        s.ph.w = (float)a.m[i];
+        s.pl.w = s.vh.w = s.vl.w = 0.f;
+        a.ds[k] = s;
+    }
+}
 
 __device__ __forceinline__ double warp_sum_d(double v)
 {
@@ -59,8 +93,14 @@ __global__ void __launch_bounds__(kIrrWarps * 32) irregular_kernel(IrrArgs a)
             r_in = K.r_in, r_out = K.r_out;
         }
         const double dr = dsub(r_out, r_in);
-        const double xi = a.x[i], yi = a.y[i], zi = a.z[i];
-        const double uxi = a.vx[i], uyi = a.vy[i], uzi = a.vz[i];
+        double xi = 0.0, yi = 0.0, zi = 0.0, uxi = 0.0, uyi = 0.0, uzi = 0.0;
+        DsState si;
+        if (MIXED) {
+            si = a.ds[k];
+        } else {
+            xi = a.x[i], yi = a.y[i], zi = a.z[i];
+            uxi = a.vx[i], uyi = a.vy[i], uzi = a.vz[i];
+        }
         const long long o0 = a.offs[i], o1 = a.offs[i + 1];
         double F[3] = {0.0, 0.0, 0.0}, J[3] = {0.0, 0.0, 0.0};
         // mixed form: FP32 constants of the changeover
@@ -72,12 +112,15 @@ __global__ void __launch_bounds__(kIrrWarps * 32) irregular_kernel(IrrArgs a)
                 bad = true;
                 continue;
             }
-            const double d0 = dsub(a.x[j], xi), d1 = dsub(a.y[j], yi), d2 = dsub(a.z[j], zi);
-            const double u0 = dsub(a.vx[j], uxi), u1 = dsub(a.vy[j], uyi), u2 = dsub(a.vz[j], uzi);
-            const double mj = a.m[j];
             if (MIXED) {
-                const float dx = (float)d0, dy = (float)d1, dz = (float)d2;
-                const float ux = (float)u0, uy = (float)u1, uz = (float)u2;
+                const DsState sj = a.ds[a.inv[j]];
+                const float dx = (sj.ph.x - si.ph.x) + (sj.pl.x - si.pl.x);
+                const float dy = (sj.ph.y - si.ph.y) + (sj.pl.y - si.pl.y);
+                const float dz = (sj.ph.z - si.ph.z) + (sj.pl.z - si.pl.z);
+                const float ux = (sj.vh.x - si.vh.x) + (sj.vl.x - si.vl.x);
+                const float uy = (sj.vh.y - si.vh.y) + (sj.vl.y - si.vl.y);
+                const float uz = (sj.vh.z - si.vh.z) + (sj.vl.z - si.vl.z);
+                const float mj = sj.ph.w;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 const float ri = rsqrtf(fmaxf(r2, 4e-26f));
                 const float r = r2 * ri;
@@ -90,7 +133,7 @@ __global__ void __launch_bounds__(kIrrWarps * 32) irregular_kernel(IrrArgs a)
                 const float Kw = (y2 * y2) * (35.f + yy * (-84.f + yy * (70.f - 20.f * yy)));
                 const float dw = 140.f * (xx * xx * xx) * (y2 * yy);
                 const float du = dx * ux + dy * uy + dz * uz;
-                const float f3 = r2 > 0.f ? (float)mj * ri * ri * ri : 0.f;
+                const float f3 = r2 > 0.f ? mj * ri * ri * ri : 0.f;
                 const float kf = Kw * f3;
                 const float kdot = -dw * du * ri * inv_dr_f;  // dK/dt
                 const float c1 = kdot * f3 - 3.f * kf * du * ri * ri;
@@ -99,6 +142,10 @@ __global__ void __launch_bounds__(kIrrWarps * 32) irregular_kernel(IrrArgs a)
                 Jf[1] += kf * uy + c1 * dy;
                 Jf[2] += kf * uz + c1 * dz;
             } else {
+                const double d0 = dsub(a.x[j], xi), d1 = dsub(a.y[j], yi), d2 = dsub(a.z[j], zi);
+                const double u0 = dsub(a.vx[j], uxi), u1 = dsub(a.vy[j], uyi),
+                             u2 = dsub(a.vz[j], uzi);
+                const double mj = a.m[j];
                 // the oracle's operations, in its order
                 const double r2 = dadd(dadd(dmul(d0, d0), dmul(d1, d1)), dmul(d2, d2));
                 if (r2 == 0.0) continue;
@@ -159,18 +206,38 @@ int irregular(p3t_ctx *c, int n, const int64_t *offs, const int32_t *idx, const 
     a.offs = offs, a.idx = idx;
     a.x = x, a.y = y, a.z = z, a.m = m, a.vx = vx, a.vy = vy, a.vz = vz;
     a.fx = fx, a.fy = fy, a.fz = fz, a.jx = jx, a.jy = jy, a.jz = jz;
-    const bool tree = c->built && c->n == n;  // the built tree holds these particles
-    a.order = tree ? c->tree.perm : nullptr;
-    a.inv = tree ? c->tree.inv : nullptr;
-    a.cid_s = tree ? c->tree.cid_s : nullptr;
-    a.cl = (tree && !c->uniform_params) ? c->tree.cl : nullptr;
+    // the built tree holds these n particles (checked by the caller): key order,
+    // cluster of every particle, frames and (per-cluster) radii
+    a.order = c->tree.perm;
+    a.inv = c->tree.inv;
+    a.cid_s = c->tree.cid_s;
+    a.cl = c->uniform_params ? nullptr : c->tree.cl;
+    a.cl_frame = c->tree.cl;
     a.r_in = c->prm.r_in, a.r_out = c->prm.r_out;
     a.meta = c->meta;
+    a.ds = nullptr;
     const int grid = 8 * c->sm_count;
-    if (c->prm.precision == P3T_FP64)
+    if (c->prm.precision == P3T_FP64) {
         irregular_kernel<false><<<grid, kIrrWarps * 32, 0, c->stream>>>(a);
-    else
+    } else {
+        const size_t need = sizeof(DsState) * (size_t)n;
+        if (c->irr_bytes < need) {
+            if (c->irr_buf) {
+                cudaStreamSynchronize(c->stream);
+                cudaFree(c->irr_buf);
+                c->irr_buf = nullptr;
+                c->irr_bytes = 0;
+            }
+            if (cudaMalloc(&c->irr_buf, need) != cudaSuccess) {
+                cudaGetLastError();
+                return P3T_ERR_OOM;
+            }
+            c->irr_bytes = need;
+        }
+        a.ds = (DsState *)c->irr_buf;
+        irregular_split_kernel<<<4 * c->sm_count, 256, 0, c->stream>>>(a);
         irregular_kernel<true><<<grid, kIrrWarps * 32, 0, c->stream>>>(a);
+    }
     return check_launch(c);
 }
 

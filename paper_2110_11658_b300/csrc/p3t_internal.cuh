@@ -343,6 +343,8 @@ struct p3t_ctx {
     void *host_stage;                 // device staging of p3t_step_host
     size_t host_stage_bytes;
     unsigned long long gen;           // bumped whenever blob or clusters move
+    void *irr_buf;                    // double-single states of p3t_irregular (mixed)
+    size_t irr_bytes;
 };
 
 namespace p3t {
