@@ -49,6 +49,8 @@ def _lib():
         lib.orc_neighbours_brute.argtypes = [C.c_int64, _D, _D, _D, C.c_double, C.c_int64, _I64,
                                              _I64, _I64, _I32]
         lib.orc_kick.argtypes = [C.c_int64, C.c_double, _D, _D, _D, _D, _D, _D]
+        lib.orc_knn.argtypes = [C.c_int64, _D, _D, _D, C.c_int, C.c_int64, _I32, _I32, _D]
+        lib.orc_core_quantities.argtypes = [C.c_int64, _D, _D, _D, _D, C.c_int64, _I32, _I32, _D, _D, _D]
         lib.orc_changeover_dWdx.restype = C.c_double
         lib.orc_changeover_dWdx.argtypes = [C.c_double] * 3
         lib.orc_irregular.argtypes = [C.c_int64, _D, _D, _D, _D, _D, _D, _D, C.c_double, C.c_double,
@@ -160,6 +162,34 @@ def irregular(x, y, z, m, vx, vy, vz, r_in, r_out, offsets, idx, scales=False):
                          _p(vz, _D), r_in, r_out, _p(offsets, _I64), _p(idx, _I32), _p(f, _D),
                          _p(jerk, _D), _p(sf, _D), _p(sj, _D))
     return (f, jerk, sf, sj) if scales else (f, jerk)
+
+
+def knn(x, y, z, sample, k=6):
+    """k nearest neighbours (FP64 squared distance, ties by index) of the sampled
+    particles by brute force: (idx (s, k) int32, d2 (s, k))."""
+    x, y, z = map(_f64, (x, y, z))
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    s = sample.shape[0]
+    idx = np.zeros((s, k), np.int32)
+    d2 = np.zeros((s, k))
+    _lib().orc_knn(x.shape[0], _p(x, _D), _p(y, _D), _p(z, _D), k, s, _p(sample, _I32), _p(idx, _I32),
+                   _p(d2, _D))
+    return idx, d2
+
+
+def core_quantities(x, y, z, m, sample, idx6, d26):
+    """Core quantities from the 6 nearest neighbours of a sample: (rho (s,),
+    dict(centre, r_core, rho_core, n_core))."""
+    x, y, z, m = map(_f64, (x, y, z, m))
+    sample = np.ascontiguousarray(sample, dtype=np.int32)
+    idx6 = np.ascontiguousarray(idx6, dtype=np.int32)
+    d26 = _f64(d26)
+    s = sample.shape[0]
+    rho = np.zeros(s)
+    out = np.zeros(6)
+    _lib().orc_core_quantities(x.shape[0], _p(x, _D), _p(y, _D), _p(z, _D), _p(m, _D), s, _p(sample, _I32),
+                               _p(idx6, _I32), _p(d26, _D), _p(rho, _D), _p(out, _D))
+    return rho, {"centre": out[:3].copy(), "r_core": out[3], "rho_core": out[4], "n_core": int(out[5])}
 
 
 def bounding_cube(x, y, z):

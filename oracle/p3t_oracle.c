@@ -232,6 +232,98 @@ void orc_irregular(int64_t n, const double *x, const double *y, const double *z,
     }
 }
 
+/* k nearest neighbours of sampled particles by brute force (the core-quantity
+ * search of Sec. 4: a random sample of min(N, sqrt(5000 N)) particles, each
+ * with its 6 nearest neighbours).  For sample t (particle i = sample[t]) the
+ * k particles j != i with the smallest squared distance (dx*dx + dy*dy) + dz*dz
+ * (FP64, as rule 11), ties broken by the smaller original index, in ascending
+ * order: idx[t*k + q], d2[t*k + q].  Fewer than k candidates leave -1 / inf. */
+void orc_knn(int64_t n, const double *x, const double *y, const double *z, int k, int64_t s,
+             const int32_t *sample, int32_t *idx, double *d2)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < s; t++) {
+        int64_t i = sample[t];
+        int32_t *bi = idx + t * k;
+        double *bd = d2 + t * k;
+        for (int q = 0; q < k; q++) {
+            bi[q] = -1;
+            bd[q] = INFINITY;
+        }
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double dx = x[j] - x[i], dy = y[j] - y[i], dz = z[j] - z[i];
+            double r2 = (dx * dx + dy * dy) + dz * dz;
+            /* (r2, j) against the current k-th: j ascends, so ties keep the earlier */
+            if (!(r2 < bd[k - 1])) continue;
+            int q = k - 1;
+            while (q > 0 && r2 < bd[q - 1]) {
+                bd[q] = bd[q - 1];
+                bi[q] = bi[q - 1];
+                q--;
+            }
+            bd[q] = r2;
+            bi[q] = (int32_t)j;
+        }
+    }
+}
+
+/* Core quantities from the 6 nearest neighbours of a sample (the density
+ * estimator and density-weighted averages of Casertano & Hut, which Sec. 4
+ * cites and does not print; this is the reading):
+ *   rho_t   = 3 (m of the 5 nearest) / (4 pi r_6^3)        per sample particle
+ *   x_d     = sum rho_t x_t / sum rho_t                     density centre
+ *   r_core  = sqrt(sum rho_t^2 |x_t - x_d|^2 / sum rho_t^2)
+ *   rho_core = sum rho_t^2 / sum rho_t
+ *   n_core  = #{ all particles j : |x_j - x_d|^2 < r_core^2 }
+ * Sums run over the sample in its order.  out = {x_d, y_d, z_d, r_core,
+ * rho_core, n_core}; rho (s values) may be NULL. */
+void orc_core_quantities(int64_t n, const double *x, const double *y, const double *z,
+                         const double *m, int64_t s, const int32_t *sample, const int32_t *idx6,
+                         const double *d26, double *rho, double *out)
+{
+    const double pi = 3.14159265358979323846;
+    double w = 0.0, w2 = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+    double *r = (double *)malloc(sizeof(double) * (size_t)(s > 0 ? s : 1));
+    for (int64_t t = 0; t < s; t++) {
+        double mass = 0.0;
+        for (int q = 0; q < 5; q++) mass += m[idx6[6 * t + q]];
+        double r6 = sqrt(d26[6 * t + 5]);
+        r[t] = 3.0 * mass / (4.0 * pi * (r6 * r6 * r6));
+        int64_t i = sample[t];
+        w += r[t];
+        w2 += r[t] * r[t];
+        cx += r[t] * x[i];
+        cy += r[t] * y[i];
+        cz += r[t] * z[i];
+    }
+    cx /= w;
+    cy /= w;
+    cz /= w;
+    double a = 0.0;
+    for (int64_t t = 0; t < s; t++) {
+        int64_t i = sample[t];
+        double dx = x[i] - cx, dy = y[i] - cy, dz = z[i] - cz;
+        a += r[t] * r[t] * ((dx * dx + dy * dy) + dz * dz);
+    }
+    double rc = sqrt(a / w2);
+    double rc2 = rc * rc;
+    int64_t cnt = 0;
+    for (int64_t j = 0; j < n; j++) {
+        double dx = x[j] - cx, dy = y[j] - cy, dz = z[j] - cz;
+        if ((dx * dx + dy * dy) + dz * dz < rc2) cnt++;
+    }
+    out[0] = cx;
+    out[1] = cy;
+    out[2] = cz;
+    out[3] = rc;
+    out[4] = w2 / w;
+    out[5] = (double)cnt;
+    if (rho)
+        for (int64_t t = 0; t < s; t++) rho[t] = r[t];
+    free(r);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Part 2: the reference tree                                                */
 /* ------------------------------------------------------------------------ */
