@@ -63,13 +63,14 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
-    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m", "ensemble64", "serve256", "irregular1m"],
+    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m", "ensemble64", "serve256", "irregular1m", "core1m"],
                     help="plummer1m: the throughput benchmark; king2m: theta sweep of the "
                          "mixed and FP64 forms against the direct sum (one line per theta); "
                          "ensemble64: 64 clusters in one graph-captured batched step, autotuned, "
                          "against one-cluster-at-a-time launches; serve256: Poisson request stream over "
                          "256 resident clusters with continuous batching (p50/p99 latency); "
-                         "irregular1m: irregular force and jerk over the neighbour rows of plummer1m")
+                         "irregular1m: irregular force and jerk over the neighbour rows of plummer1m; "
+                         "core1m: 6 nearest neighbours of sqrt(5000 N) sampled particles and core quantities")
     ap.add_argument("--requests", type=int, default=10000, help="serve256: requests in the timed stream")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve256: mean arrival rate (requests/s)")
     ap.add_argument("--no-tune", action="store_true", help="ensemble64: use --group-size/--tile/--leaf-cap")
@@ -902,6 +903,63 @@ def irregular_run(args):
     }
 
 
+def core_run(args):
+    """Core quantities of the benchmark workload (Plummer 10^6): a seeded random sample
+    of min(N, sqrt(5000 N)) particles, their 6 nearest neighbours by brute force over
+    all N, and the density-weighted core radius / density / membership.  The oracle's
+    search is timed on a subsample and scaled (it is O(sample x N))."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2110_11658_b300 as p3t
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    c, w = workload(args.n, 20211022)
+    s = int(min(c.n, math.sqrt(5000 * c.n)))
+    sample = np.random.default_rng(20211022).choice(c.n, s, replace=False).astype(np.int32)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    d = [t(getattr(c, k)) for k in "xyzm"]
+    sm = t(sample)
+    stream = torch.cuda.current_stream(dev)
+    ctx = p3t.Context(p3t.Params(theta=w["theta"], r_in=w["r_in"], r_out=w["r_out"], r_list=w["r_list"]),
+                      stream)
+    ctx.build_tree(*d)
+    res = {}
+
+    def run():
+        res["knn"] = ctx.sample_knn6(sm)
+        res["core"] = ctx.core_quantities(*d, sm, *res["knn"])
+
+    run()
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    ts = _events_ms(stream, lambda: ctx.sample_knn6(sm), max(3, args.steps), flush)
+    ms = float(np.median(ts))
+    ctx.check()
+    q = res["core"][1]
+    sub = sample[:1000]
+    t0 = time.perf_counter()
+    oracle.knn(c.x, c.y, c.z, sub, 6)
+    t_cpu = (time.perf_counter() - t0) * s / len(sub)
+    ctx.close()
+    return {
+        "metric": "6 nearest neighbours of a sqrt(5000 N) sample by brute force (core quantities)",
+        "value": s * c.n / (ms * 1e-3), "unit": "pair tests/s", "n_gpus": 1, "steps": max(3, args.steps),
+        "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 filter, f64 decisions", "data": "synthetic",
+        "config": {"workload": "plummer_kroupa_n%d_core_sample%d" % (c.n, s), "n": c.n, "sample": s,
+                   "l2": "256 MB buffer written between timed launches (L2 is 126 MB)"},
+        "core": {"centre": list(map(float, q["centre"])), "r_core": q["r_core"], "rho_core": q["rho_core"],
+                 "n_core": q["n_core"]},
+        "cpu_baseline": {"value": s * c.n / t_cpu, "unit": "pair tests/s", "cores": omp_threads(),
+                         "kind": "oracle", "sample": "oracle search of 1000 of the %d sampled particles, "
+                                                     "scaled to all" % s},
+    }
+
+
 def _json_default(o):
     """numpy scalars in result dictionaries."""
     if hasattr(o, "item"):
@@ -911,6 +969,9 @@ def _json_default(o):
 
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload == "core1m":
+        print(json.dumps(core_run(args), default=_json_default))
+        return
     if args.workload == "irregular1m":
         print(json.dumps(irregular_run(args), default=_json_default))
         return

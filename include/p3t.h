@@ -220,6 +220,37 @@ int p3t_irregular(p3t_ctx *c, int64_t n, const int64_t *offsets, const int32_t *
                   const double *vx, const double *vy, const double *vz, double *fx, double *fy,
                   double *fz, double *jx, double *jy, double *jz);
 
+/* ---- core quantities (Sec. 4) -------------------------------------------
+ * The core radius, density and membership are estimated from the 6 nearest
+ * neighbours of a random sample of min(N, sqrt(5000 N)) particles found by a
+ * brute-force search (Sec. 4), with the density estimator and density-weighted
+ * averages of Casertano & Hut, which the paper cites without printing.
+ *
+ * p3t_sample_knn6: for each sampled particle (sample: device int32[s], original
+ * indices drawn by the caller) its 6 nearest other particles among the n
+ * particles of the last p3t_build_tree (one cluster; positions of that build),
+ * by exact FP64 squared distance (dx*dx + dy*dy) + dz*dz, ties broken by the
+ * smaller original index, ascending: nn_idx device int32[s*6] (original
+ * indices; -1 where fewer than 6 exist), nn_d2 device double[s*6] (inf there).
+ * Uses a scratch buffer of the context (allocated on first use, ~72 bytes per
+ * sampled particle and chunk).  Errors: P3T_ERR_ORDER without a one-cluster
+ * tree of these n particles; a sample index outside [0, n) latches
+ * P3T_ERR_INVALID_INPUT (its row is left unset).
+ *
+ * p3t_core_quantities: from those neighbours (device arrays in original order
+ * x, y, z, m of n particles): rho[t] = 3 (mass of the 5 nearest) / (4 pi r_6^3)
+ * per sampled particle, then out (device double[6]) = {density centre x, y, z,
+ * core radius sqrt(sum rho^2 |x - x_d|^2 / sum rho^2), core density
+ * sum rho^2 / sum rho, number of particles within the core radius}; a sampled
+ * particle with fewer than 6 neighbours (n < 7) gets rho = 0.  Requires
+ * a context that has built a tree (its metadata block holds a counter).
+ * Both calls are asynchronous on the context's stream. */
+int p3t_sample_knn6(p3t_ctx *c, int64_t n, int64_t s, const int32_t *sample, int32_t *nn_idx,
+                    double *nn_d2);
+int p3t_core_quantities(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                        const double *m, int64_t s, const int32_t *sample, const int32_t *nn_idx,
+                        const double *nn_d2, double *rho, double *out);
+
 /* Number of exact FP64 decisions the FP32 filters have handed over (opening
  * and box tests that fell inside their error bands) since the last build;
  * host int64.  A diagnostic of the filters' efficiency: the results do not

@@ -276,8 +276,9 @@ void orc_knn(int64_t n, const double *x, const double *y, const double *z, int k
  *   r_core  = sqrt(sum rho_t^2 |x_t - x_d|^2 / sum rho_t^2)
  *   rho_core = sum rho_t^2 / sum rho_t
  *   n_core  = #{ all particles j : |x_j - x_d|^2 < r_core^2 }
- * Sums run over the sample in its order.  out = {x_d, y_d, z_d, r_core,
- * rho_core, n_core}; rho (s values) may be NULL. */
+ * Sums run over the sample in its order.  A sampled particle without 6
+ * neighbours (a system of fewer than 7 particles) gets rho = 0.  out = {x_d,
+ * y_d, z_d, r_core, rho_core, n_core}; rho (s values) may be NULL. */
 void orc_core_quantities(int64_t n, const double *x, const double *y, const double *z,
                          const double *m, int64_t s, const int32_t *sample, const int32_t *idx6,
                          const double *d26, double *rho, double *out)
@@ -287,8 +288,9 @@ void orc_core_quantities(int64_t n, const double *x, const double *y, const doub
     double *r = (double *)malloc(sizeof(double) * (size_t)(s > 0 ? s : 1));
     for (int64_t t = 0; t < s; t++) {
         double mass = 0.0;
-        for (int q = 0; q < 5; q++) mass += m[idx6[6 * t + q]];
-        double r6 = sqrt(d26[6 * t + 5]);
+        for (int q = 0; q < 5; q++)
+            if (idx6[6 * t + q] >= 0) mass += m[idx6[6 * t + q]];
+        double r6 = sqrt(d26[6 * t + 5]); /* inf without a 6th neighbour: rho = 0 */
         r[t] = 3.0 * mass / (4.0 * pi * (r6 * r6 * r6));
         int64_t i = sample[t];
         w += r[t];

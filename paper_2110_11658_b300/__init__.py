@@ -41,6 +41,7 @@ EXPORTED = [
     "p3t_set_debug", "p3t_error_string", "p3t_morton_order_noalloc",
     "p3t_graph_capture", "p3t_graph_launch", "p3t_graph_destroy", "p3t_reserve", "p3t_scratch_bytes",
     "p3t_batch_move", "p3t_batch_scatter_neighbours", "p3t_filter_fallbacks", "p3t_irregular",
+    "p3t_sample_knn6", "p3t_core_quantities",
 ]
 P3T_NOALLOC_MAX_N = 65536
 
@@ -106,6 +107,8 @@ _sig = {
     "p3t_reserve": [_vp, _i64, C.c_int32],
     "p3t_filter_fallbacks": [_vp, C.POINTER(_i64)],
     "p3t_irregular": [_vp, _i64] + [_vp] * 15,
+    "p3t_sample_knn6": [_vp, _i64, _i64, _vp, _vp, _vp],
+    "p3t_core_quantities": [_vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp],
     "p3t_scratch_bytes": [C.POINTER(p3t_params), _i64, C.c_int32, C.POINTER(_i64)],
     "p3t_batch_move": [_vp, C.c_int32, _i64, _vp, _vp, C.c_int32, C.POINTER(p3t_seg_array), C.c_int32],
     "p3t_batch_scatter_neighbours": [_vp, C.c_int32, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
@@ -372,6 +375,33 @@ class Context:
         _check(_lib.p3t_irregular(self._h, n, _ptr(offsets, t.int64, n + 1, "offsets"), _ptr(idx, t.int32, None, "idx"),
                                   *args, *outs), "p3t_irregular")
         return f, jerk
+
+    def sample_knn6(self, sample, n=None):
+        """6 nearest neighbours of the sampled particles (p3t_sample_knn6) among the
+        particles of the last build: (idx (s, 6) int32, d2 (s, 6) float64) CUDA tensors."""
+        t = self._torch
+        n = self.n if n is None else n
+        s = sample.numel()
+        idx = t.empty(s, 6, dtype=t.int32, device=sample.device)
+        d2 = t.empty(s, 6, dtype=t.float64, device=sample.device)
+        _check(_lib.p3t_sample_knn6(self._h, n, s, _ptr(sample, t.int32, s, "sample"), idx.data_ptr(),
+                                    d2.data_ptr()), "p3t_sample_knn6")
+        return idx, d2
+
+    def core_quantities(self, x, y, z, m, sample, idx6, d26):
+        """Core quantities from the sample's 6 nearest neighbours (p3t_core_quantities):
+        (rho (s,) CUDA tensor, dict of centre, r_core, rho_core, n_core)."""
+        t = self._torch
+        n, s = x.numel(), sample.numel()
+        rho = t.empty(s, dtype=t.float64, device=x.device)
+        out = t.empty(6, dtype=t.float64, device=x.device)
+        _check(_lib.p3t_core_quantities(self._h, n, *[_ptr(a, t.float64, n, nm) for a, nm in zip((x, y, z, m), "xyzm")],
+                                        s, _ptr(sample, t.int32, s, "sample"), _ptr(idx6, t.int32, 6 * s, "idx6"),
+                                        _ptr(d26, t.float64, 6 * s, "d26"), rho.data_ptr(), out.data_ptr()),
+               "p3t_core_quantities")
+        self.check()
+        o = out.cpu().numpy()
+        return rho, {"centre": o[:3].copy(), "r_core": float(o[3]), "rho_core": float(o[4]), "n_core": int(o[5])}
 
     def filter_fallbacks(self) -> int:
         """FP64 decisions taken by the FP32 filters since the last build (diagnostic)."""

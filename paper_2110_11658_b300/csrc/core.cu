@@ -1,0 +1,335 @@
+// Core quantities from a sample's nearest neighbours (Sec. 4: a random sample
+// of min(N, sqrt(5000 N)) particles, a brute-force search for each sampled
+// particle's 6 nearest neighbours, and the density estimator and
+// density-weighted averages of Casertano & Hut, which the paper cites).
+//
+// Search: every sampled particle against every particle of the built tree
+// (one cluster).  Blocks pair 128 sampled particles with one chunk of
+// candidates in key order, staged through shared memory.  Each candidate is
+// first tested in FP32 on double-single coordinates relative to the frame
+// centre (the tree's hi/lo splits): a candidate whose FP32 squared distance
+// exceeds an upper bound of the current 6th distance cannot enter the list;
+// the others are decided with the exact FP64 distance (dx*dx + dy*dy) + dz*dz
+// and inserted by (distance, original index).  A second kernel merges the
+// chunks' lists.  The result is unique, so it equals the oracle's bit for bit.
+#include <cstdint>
+#include <cmath>
+
+#include "p3t_internal.cuh"
+
+namespace p3t {
+
+constexpr int kKnn = 6;
+constexpr int kKnnThreads = 128;
+constexpr int kKnnTile = 256;
+
+struct KnnArgs {
+    Tree T;
+    int n, s;
+    const int32_t *sample;
+    int chunk;             // candidates per chunk
+    int n_chunks;
+    double *part_d2;       // [s][n_chunks][6]
+    int32_t *part_idx;
+};
+
+// (d, i) < (e, j) in the order of the lists: distance, then original index
+__device__ __forceinline__ bool knn_less(double d, int i, double e, int j)
+{
+    return d < e || (d == e && i < j);
+}
+
+__device__ __forceinline__ void knn_insert(double (&bd)[kKnn], int (&bi)[kKnn], double d, int i)
+{
+    if (!knn_less(d, i, bd[kKnn - 1], bi[kKnn - 1])) return;
+    bd[kKnn - 1] = d, bi[kKnn - 1] = i;
+#pragma unroll
+    for (int q = kKnn - 1; q > 0; q--) {
+        if (knn_less(bd[q], bi[q], bd[q - 1], bi[q - 1])) {
+            const double td = bd[q];
+            const int ti = bi[q];
+            bd[q] = bd[q - 1], bi[q] = bi[q - 1];
+            bd[q - 1] = td, bi[q - 1] = ti;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kKnnThreads) knn_chunk_kernel(KnnArgs a)
+{
+    __shared__ float4 sh[kKnnTile], sl[kKnnTile];
+    const Tree &T = a.T;
+    const int t = blockIdx.x * kKnnThreads + threadIdx.x;
+    const int c = blockIdx.y;
+    bool active = t < a.s;
+    int me = -1, km = 0;
+    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+    double4_32a p = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    if (active) {
+        me = a.sample[t];
+        if ((unsigned)me >= (unsigned)a.n) {  // not a particle: no list
+            if (c == 0) latch_error(T.meta, P3T_ERR_INVALID_INPUT);
+            active = false;
+            me = -1;
+        } else {
+            km = T.inv[me];
+            h = T.ph[km], l = T.pl[km];
+            p = T.sp[km];
+        }
+    }
+    // the frame term of the FP32 band: after the double-single difference every
+    // coordinate carries <= 2^-47 R; 2^-40 R^2 covers its share of any squared
+    // distance within the frame with a wide margin
+    const float Rf = (float)T.cl[0].frame[3];
+    const float band_abs = Rf * Rf * 9.094947e-13f + 1e-37f;
+    double bd[kKnn];
+    int bi[kKnn];
+    // upper bound of the 6th distance: the 6th nearest among the 32 particles next
+    // to this one in key order (spatial neighbours); no nearer-than-true neighbour
+    // is lost, since the true 6th distance is at most this one
+    double bound = INFINITY;
+    if (active) {
+#pragma unroll
+        for (int q = 0; q < kKnn; q++) bd[q] = INFINITY, bi[q] = 0x7fffffff;
+        const int lo = max(0, km - 16), hi = min(a.n, km + 17);
+        for (int kj = lo; kj < hi; kj++) {
+            if (kj == km) continue;
+            const double4_32a pj = T.sp[kj];
+            const double ex = dsub(pj.x, p.x), ey = dsub(pj.y, p.y), ez = dsub(pj.z, p.z);
+            knn_insert(bd, bi, dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)), kj);
+        }
+        bound = bd[kKnn - 1];
+    }
+#pragma unroll
+    for (int q = 0; q < kKnn; q++) bd[q] = INFINITY, bi[q] = 0x7fffffff;
+    // FP32 squared distances above this cannot enter the list
+    float thr = bound < INFINITY ? (float)bound * (1.f + 32.f * kFp32U) + band_abs : INFINITY;
+    const int k0 = c * a.chunk, k1 = min(a.n, k0 + a.chunk);
+    for (int base = k0; base < k1; base += kKnnTile) {
+        const int nt = min(kKnnTile, k1 - base);
+        __syncthreads();
+        for (int q = threadIdx.x; q < nt; q += kKnnThreads) {
+            sh[q] = T.ph[base + q];
+            sl[q] = T.pl[base + q];
+        }
+        __syncthreads();
+        if (!active) continue;
+#pragma unroll 4
+        for (int q = 0; q < nt; q++) {
+            const float4 ch = sh[q], cl = sl[q];
+            const float dx = (ch.x - h.x) + (cl.x - l.x);
+            const float dy = (ch.y - h.y) + (cl.y - l.y);
+            const float dz = (ch.z - h.z) + (cl.z - l.z);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 <= thr) {  // may enter the list: decide exactly
+                const int kj = base + q;
+                const int oj = T.perm[kj];
+                if (oj != me) {
+                    const double4_32a pj = T.sp[kj];
+                    const double ex = dsub(pj.x, p.x), ey = dsub(pj.y, p.y), ez = dsub(pj.z, p.z);
+                    const double d2 = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez));
+                    knn_insert(bd, bi, d2, oj);
+                    // |FP32 - exact| of a squared distance <= 8u (relative) + the
+                    // frame term; 32u and twice the frame term leave a margin
+                    const double lim = fmin(bd[kKnn - 1], bound);
+                    thr = lim < INFINITY ? (float)lim * (1.f + 32.f * kFp32U) + band_abs : INFINITY;
+                }
+            }
+        }
+    }
+    if (active) {
+        const size_t o = ((size_t)t * a.n_chunks + c) * kKnn;
+#pragma unroll
+        for (int q = 0; q < kKnn; q++) a.part_d2[o + q] = bd[q], a.part_idx[o + q] = bi[q];
+    }
+}
+
+__global__ void knn_merge_kernel(KnnArgs a, int32_t *nn_idx, double *nn_d2)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < a.s; t += gridDim.x * blockDim.x) {
+        double bd[kKnn];
+        int bi[kKnn];
+#pragma unroll
+        for (int q = 0; q < kKnn; q++) bd[q] = INFINITY, bi[q] = 0x7fffffff;
+        for (int c = 0; c < a.n_chunks; c++) {
+            const size_t o = ((size_t)t * a.n_chunks + c) * kKnn;
+            for (int q = 0; q < kKnn; q++) knn_insert(bd, bi, a.part_d2[o + q], a.part_idx[o + q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kKnn; q++) {
+            const bool found = bd[q] < INFINITY;
+            nn_idx[(size_t)t * kKnn + q] = found ? bi[q] : -1;
+            nn_d2[(size_t)t * kKnn + q] = bd[q];
+        }
+    }
+}
+
+// ---- core quantities (one block, fixed reduction order) ---------------------
+constexpr int kCoreThreads = 1024;
+
+__device__ double block_sum_d(double v, double *sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[32] = s;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+struct CoreArgs {
+    int n, s;
+    const double *x, *y, *z, *m;
+    const int32_t *sample, *idx6;
+    const double *d26;
+    double *rho, *out;
+    unsigned long long *count;
+    Meta *meta;
+};
+
+__global__ void __launch_bounds__(kCoreThreads) core_sums_kernel(CoreArgs a)
+{
+    __shared__ double sh[33];
+    const double four_pi_3 = 4.0 * 3.14159265358979323846 / 3.0;
+    double w = 0.0, w2 = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+    bool bad = false;
+    for (int t = threadIdx.x; t < a.s; t += blockDim.x) {
+        double mass = 0.0;
+        for (int q = 0; q < 5; q++) {
+            const int j = a.idx6[6 * t + q];
+            if (j == -1) continue;  // fewer than 6 neighbours: d2 = inf, rho = 0
+            if ((unsigned)j >= (unsigned)a.n) {
+                bad = true;
+                continue;
+            }
+            mass = dadd(mass, a.m[j]);
+        }
+        const double r6 = dsqrt(a.d26[6 * t + 5]);
+        const double r = ddiv(mass, dmul(four_pi_3, dmul(dmul(r6, r6), r6)));
+        const int i = a.sample[t];
+        if ((unsigned)i >= (unsigned)a.n) {  // not a particle: weight 0
+            bad = true;
+            a.rho[t] = 0.0;
+            continue;
+        }
+        a.rho[t] = r;
+        w = dadd(w, r), w2 = dadd(w2, dmul(r, r));
+        cx = dadd(cx, dmul(r, a.x[i])), cy = dadd(cy, dmul(r, a.y[i])), cz = dadd(cz, dmul(r, a.z[i]));
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) latch_error(a.meta, P3T_ERR_INVALID_INPUT);
+    w = block_sum_d(w, sh);
+    w2 = block_sum_d(w2, sh);
+    cx = ddiv(block_sum_d(cx, sh), w);
+    cy = ddiv(block_sum_d(cy, sh), w);
+    cz = ddiv(block_sum_d(cz, sh), w);
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < a.s; t += blockDim.x) {
+        const int i = a.sample[t];
+        if ((unsigned)i >= (unsigned)a.n) continue;
+        const double dx = dsub(a.x[i], cx), dy = dsub(a.y[i], cy), dz = dsub(a.z[i], cz);
+        const double r = a.rho[t];
+        acc = dadd(acc, dmul(dmul(r, r), dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz))));
+    }
+    acc = block_sum_d(acc, sh);
+    if (threadIdx.x == 0) {
+        a.out[0] = cx, a.out[1] = cy, a.out[2] = cz;
+        a.out[3] = dsqrt(ddiv(acc, w2));
+        a.out[4] = ddiv(w2, w);
+        *a.count = 0ULL;
+    }
+}
+
+__global__ void core_count_kernel(CoreArgs a)
+{
+    const double cx = a.out[0], cy = a.out[1], cz = a.out[2], rc = a.out[3];
+    const double rc2 = dmul(rc, rc);
+    unsigned int cnt = 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < a.n; j += gridDim.x * blockDim.x) {
+        const double dx = dsub(a.x[j], cx), dy = dsub(a.y[j], cy), dz = dsub(a.z[j], cz);
+        cnt += dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz)) < rc2;
+    }
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.count, (unsigned long long)cnt);
+}
+
+__global__ void core_finish_kernel(CoreArgs a)
+{
+    a.out[5] = (double)*a.count;
+}
+
+}  // namespace p3t
+
+using namespace p3t;
+
+extern "C" {
+
+int p3t_sample_knn6(p3t_ctx *c, int64_t n, int64_t s, const int32_t *sample, int32_t *nn_idx,
+                    double *nn_d2)
+{
+    if (!c || !sample || !nn_idx || !nn_d2 || n <= 0 || s <= 0 || s > n) return P3T_ERR_INVALID_ARG;
+    if (!c->built || c->n != n || c->tree.n_clusters != 1) return P3T_ERR_ORDER;
+    // chunks so that the grid covers the GPU about four times over
+    const int sblocks = (int)((s + kKnnThreads - 1) / kKnnThreads);
+    int chunks = (4 * 4 * c->sm_count + sblocks - 1) / sblocks;
+    if (chunks < 1) chunks = 1;
+    if (chunks > 64) chunks = 64;
+    const size_t need = (size_t)s * chunks * kKnn * (sizeof(double) + sizeof(int32_t));
+    if (c->knn_bytes < need) {
+        if (c->knn_buf) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->knn_buf);
+            c->knn_buf = nullptr;
+            c->knn_bytes = 0;
+        }
+        if (cudaMalloc(&c->knn_buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return P3T_ERR_OOM;
+        }
+        c->knn_bytes = need;
+    }
+    KnnArgs a;
+    a.T = c->tree;
+    a.n = (int)n;
+    a.s = (int)s;
+    a.sample = sample;
+    a.n_chunks = chunks;
+    a.chunk = (int)((n + chunks - 1) / chunks);
+    a.part_d2 = (double *)c->knn_buf;
+    a.part_idx = (int32_t *)((char *)c->knn_buf + (size_t)s * chunks * kKnn * sizeof(double));
+    dim3 grid(sblocks, chunks);
+    knn_chunk_kernel<<<grid, kKnnThreads, 0, c->stream>>>(a);
+    knn_merge_kernel<<<(int)((s + 255) / 256), 256, 0, c->stream>>>(a, nn_idx, nn_d2);
+    return check_launch(c);
+}
+
+int p3t_core_quantities(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                        const double *m, int64_t s, const int32_t *sample, const int32_t *nn_idx,
+                        const double *nn_d2, double *rho, double *out)
+{
+    if (!c || !x || !y || !z || !m || !sample || !nn_idx || !nn_d2 || !rho || !out || n <= 0 ||
+        s <= 0 || n >= (1LL << 31) - 1 || s >= (1LL << 31) - 1)
+        return P3T_ERR_INVALID_ARG;
+    if (!c->meta) return P3T_ERR_ORDER;
+    CoreArgs a;
+    a.n = (int)n, a.s = (int)s;
+    a.x = x, a.y = y, a.z = z, a.m = m;
+    a.sample = sample, a.idx6 = nn_idx, a.d26 = nn_d2;
+    a.rho = rho, a.out = out;
+    a.count = &c->meta->core_count;
+    a.meta = c->meta;
+    core_sums_kernel<<<1, kCoreThreads, 0, c->stream>>>(a);
+    const long long want = (n + 255) / 256;
+    core_count_kernel<<<(int)(want < 8LL * c->sm_count ? want : 8LL * c->sm_count), 256, 0, c->stream>>>(a);
+    core_finish_kernel<<<1, 1, 0, c->stream>>>(a);
+    return check_launch(c);
+}
+
+}  // extern "C"

@@ -215,6 +215,7 @@ int p3t_destroy(p3t_ctx *c)
     if (c->host_stage) cudaFree(c->host_stage);
     if (c->clusters) cudaFree(c->clusters);
     if (c->irr_buf) cudaFree(c->irr_buf);
+    if (c->knn_buf) cudaFree(c->knn_buf);
     delete c;
     return P3T_OK;
 }

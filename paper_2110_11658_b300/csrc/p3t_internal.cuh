@@ -62,6 +62,7 @@ struct Meta {
     unsigned int tickets[32];      // work-distribution counters (reset per launch)
     long long nbr_total;
     long long fallback_tests;      // FP64 decisions taken after an undecided FP32 filter
+    unsigned long long core_count; // particles within the core radius (core quantities)
 };
 
 // ---- one cluster of a (possibly batched) build -----------------------------------
@@ -345,6 +346,8 @@ struct p3t_ctx {
     unsigned long long gen;           // bumped whenever blob or clusters move
     void *irr_buf;                    // double-single states of p3t_irregular (mixed)
     size_t irr_bytes;
+    void *knn_buf;                    // per-chunk lists of p3t_sample_knn6
+    size_t knn_bytes;
 };
 
 namespace p3t {
