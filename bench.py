@@ -60,6 +60,9 @@ def parse_args(argv=None):
     ap.add_argument("--group-size", type=int, default=32)
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--leaf-cap", type=int, default=16)
+    ap.add_argument("--r-buff", type=float, default=0.0,
+                    help="neighbour buffer: r_list = r_out + r_buff (Eq. 20; 'paper' value 3 tau sigma "
+                         "is passed as a negative number: -1 = one times the rule)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
@@ -277,6 +280,10 @@ def run_b300(args, rank, local, world):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     c, w = workload(args.n, 20211022 + rank)
+    if args.r_buff != 0.0:
+        import synth
+        rb = args.r_buff if args.r_buff > 0 else -args.r_buff * synth.paper_run_params(args.n)["r_buff"]
+        w["r_list"] = w["r_out"] + rb
     prm = p3t.Params(theta=w["theta"], r_in=w["r_in"], r_out=w["r_out"], r_list=w["r_list"],
                      leaf_cap=args.leaf_cap, group_size=args.group_size, tile=args.tile,
                      precision=p3t.P3T_FP32_MIXED, quadrupole=1)

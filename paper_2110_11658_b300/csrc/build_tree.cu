@@ -90,7 +90,7 @@ __global__ void cluster_params_kernel(Cluster *cl, int C, const double *__restri
     K.rout2_f = (float)K.rout2_d;
     K.rl2_f = (float)K.rl2_d;
     K.rl_f = (float)rl;
-    K.counted = rl > 0.0 && rl <= ro;
+    K.counted = rl > 0.0;  // the mixed walk counts every list radius (shell ranges beyond r_out)
 }
 
 // cluster of every particle from the offsets (validated: 0 = seg[0] < ... < seg[C] = n)

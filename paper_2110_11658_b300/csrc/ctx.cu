@@ -234,7 +234,7 @@ int p3t_reserve(p3t_ctx *c, int64_t n, int32_t n_clusters)
 {
     if (!c || n <= 0 || n >= (1LL << 31) - 1 || n_clusters < 1 || n_clusters > n)
         return P3T_ERR_INVALID_ARG;
-    if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 29)) return P3T_ERR_INVALID_ARG;
+    if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 28)) return P3T_ERR_INVALID_ARG;
     return reserve(c, n, n_clusters);
 }
 
@@ -255,7 +255,7 @@ static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *se
     if (!c || !x || !y || !z || !m) return P3T_ERR_INVALID_ARG;
     if (n <= 0 || n >= (1LL << 31) - 1) return P3T_ERR_INVALID_ARG;
     if (n_clusters < 1 || n_clusters > n) return P3T_ERR_INVALID_ARG;
-    if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 29)) return P3T_ERR_INVALID_ARG;
+    if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 28)) return P3T_ERR_INVALID_ARG;
     int e = reserve(c, n, n_clusters);
     if (e) return e;
     c->built = 0;

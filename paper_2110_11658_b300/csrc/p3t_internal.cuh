@@ -198,6 +198,43 @@ __device__ __forceinline__ int pop_batch(int *stk, int &sp)
     return lane < take ? kfirst + (lane - kexcl) : -1;
 }
 
+// The far-force walk's stack entries may carry a flag in bit 31 (ranges visited
+// only for the neighbour count); node indices then stay below 2^28.
+constexpr unsigned kRangeFlag = 0x80000000u;
+__device__ __forceinline__ int pack_range_f(int first, int count, bool flag)
+{
+    return (int)(((unsigned)first << 3) | (unsigned)(count - 1) | (flag ? kRangeFlag : 0u));
+}
+
+// pop_batch for flagged entries: also returns this lane's entry flag.
+__device__ __forceinline__ int pop_batch_f(int *stk, int &sp, bool &flag)
+{
+    const unsigned full_mask = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int e = lane < sp ? stk[sp - 1 - lane] : 0;
+    const int first_e = (int)(((unsigned)e >> 3) & 0x0fffffffu);
+    const int cnt = lane < sp ? (e & 7) + 1 : 0;
+    const unsigned b0 = __ballot_sync(full_mask, cnt & 1), b1 = __ballot_sync(full_mask, cnt & 2),
+                   b2 = __ballot_sync(full_mask, cnt & 4), b3 = __ballot_sync(full_mask, cnt & 8);
+    const int excl = __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt) + 8 * __popc(b3 & lt);
+    const int total = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2) + 8 * __popc(b3);
+    const int take = total < 32 ? total : 32;
+    const bool starts = cnt > 0 && excl < take;
+    const unsigned smask = __reduce_or_sync(full_mask, starts ? (1u << excl) : 0u);
+    const unsigned consumed = __ballot_sync(full_mask, cnt > 0 && excl + cnt <= take);
+    if (starts && excl + cnt > take)
+        stk[sp - 1 - lane] = pack_range_f(first_e + (take - excl), cnt - (take - excl), e < 0);
+    const unsigned le = lane == 31 ? full_mask : ((2u << lane) - 1u);
+    const int k = (__popc(smask & le) - 1) & 31;
+    const int kraw = __shfl_sync(full_mask, e, k);
+    const int kexcl = __shfl_sync(full_mask, excl, k);
+    sp -= __popc(consumed);
+    __syncwarp();
+    flag = lane < take && kraw < 0;
+    return lane < take ? (int)(((unsigned)kraw >> 3) & 0x0fffffffu) + (lane - kexcl) : -1;
+}
+
 // ---- block-wide exclusive scan (blockDim.x a multiple of 32, <= 1024) --------------
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T v)

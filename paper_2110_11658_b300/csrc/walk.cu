@@ -29,11 +29,16 @@
 // run in FP32 and each tile's partial sum is added to the running sum with
 // Kahan compensation.  The FP64 form does everything in FP64.
 //
-// When 0 < r_list <= r_out the particle loop also counts, per target, the
-// neighbours of Sec. 2.3 (pairs in opened leaves with |r| < r_list; every pair
-// within r_out of a group particle is in an opened leaf), with the same FP32
-// band + exact FP64 decision as the neighbour kernels, so p3t_neighbours can
-// skip its counting pass.
+// In the mixed form the particle loop also counts, per target, the neighbours
+// of Sec. 2.3 (pairs with |r| < r_list), with the same FP32 band + exact FP64
+// decision as the neighbour kernels, so p3t_neighbours can skip its counting
+// pass.  Every pair within r_out of a group particle lies in a leaf the walk
+// opens.  For r_list > r_out (the buffer radius r_out + r_buff of Eq. 20) a
+// cell the force accepts may still hold neighbours: its children are pushed as
+// flagged, neighbour-only ranges, tested by the r_list box test alone, and the
+// particles of such leaves are staged with mass 0, so they are counted and add
+// exactly nothing to the force.  The force and its interaction counts do not
+// depend on r_list.
 #include <cstdint>
 #include <type_traits>
 
@@ -601,9 +606,10 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
                 else
                     hi = mid;
             }
-            const int j = W.lq[lo].x + (pos - W.lqo[lo]);
+            const int lx = W.lq[lo].x;  // bit 31: neighbour-only leaf (staged with mass 0)
+            const int j = (lx & 0x7fffffff) + (pos - W.lqo[lo]);
             const float4 r = ds_rel(P.T.ph[j], P.T.pl[j], F);
-            pb[0] = r.x, pb[2] = r.y, pb[4] = r.z, pb[6] = r.w;
+            pb[0] = r.x, pb[2] = r.y, pb[4] = r.z, pb[6] = lx < 0 ? 0.f : r.w;
             if (NBR) W.pj[lane] = j;
         }
         __syncwarp();
@@ -647,7 +653,7 @@ __device__ __forceinline__ void eval_parts_any(const WarpSmem<Real> &W, const Wa
         eval_parts<Real, TPL, POT, NBR>(W, P, K, nleaves, nparts, F, px, py, pz, A, NC);
 }
 
-template <typename Real, int TPL, bool POT, bool QUAD, bool NBR>
+template <typename Real, int TPL, bool POT, bool QUAD, bool NBR, bool SHELL>
 __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3) walk_kernel(WalkArgs P)
 {
     extern __shared__ __align__(16) char smem[];
@@ -686,8 +692,11 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         const double rout2_d = K.rout2_d;
         const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && rout2_f > 1e-20f && rout2_f < 1e30f;
         const bool count_here = NBR && K.counted;
+        const bool shell = SHELL && count_here && K.rl2_d > rout2_d;  // neighbours beyond r_out
+        const float rl2_f = K.rl2_f;
         const float k_rel = 8.f * kU, k_abs = 8.f * kU * Rf, k_sq = 16.f * kU * kU * Rf * Rf;
         const Band bb_band = fp32_band(Rf, rout2_f);  // the box-box test against r_out
+        const Band bl_band = fp32_band(Rf, rl2_f);    // and against r_list (shell)
         GroupFrame F;
         F.cx = dmul(0.5, dadd(glo.x, ghi.x));
         F.cy = dmul(0.5, dadd(glo.y, ghi.y));
@@ -742,7 +751,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         typename std::conditional<kMixed, AccX2<TPL>, Acc<double, TPL>>::type A;
         A.zero_all();
         int sp = 1;
-        if (lane == 0) W.stk[0] = pack_range(cid, 1);
+        if (lane == 0) W.stk[0] = pack_range_f(cid, 1, false);
         __syncwarp();
         int cb = 0, lqn = 0, lqp = 0;
         long long ncell = 0, npart = 0;
@@ -753,11 +762,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                 if (lane == 0) latch_error(meta, P3T_ERR_INTERNAL);
                 break;
             }
-            // ---- pop up to 32 nodes, one per lane
-            const int node = pop_batch(W.stk, sp);
+            // ---- pop up to 32 nodes, one per lane (flagged: neighbour-only range)
+            bool nbr_only = false;
+            int node;
+            if constexpr (SHELL)
+                node = pop_batch_f(W.stk, sp, nbr_only);
+            else
+                node = pop_batch(W.stk, sp);
 
             // ---- opening test (test and staging data come in one load batch)
-            bool open = false, is_leaf = false;
+            bool open = false, is_leaf = false, in_shell = false;
             int cinfo = 0, ccount = 0;
             float4 ra, rd, rq0, rq1;  // node record: COM hi / lo + M / quadrupole
             if (node >= 0) {
@@ -793,7 +807,25 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                         dec_b = fabsf(db) > fmaf(bb_band.a, e2, bb_band.b);
                         in_b = db < 0.f;
                     }
-                    if ((dec_m && in_m) || (dec_b && in_b)) {
+                    if (SHELL && nbr_only) {
+                        // neighbour-only range: the box test against r_list alone
+                        bool dec_l = false, in_l = false;
+                        if (filter_ok) {
+                            const float ux = fmaxf(fmaxf(b.x - ghx, glx - c.x), 0.f);
+                            const float uy = fmaxf(fmaxf(b.y - ghy, gly - c.y), 0.f);
+                            const float uz = fmaxf(fmaxf(b.z - ghz, glz - c.z), 0.f);
+                            const float e2 = ux * ux + uy * uy + uz * uz;
+                            const float dl = e2 - rl2_f;
+                            dec_l = fabsf(dl) > fmaf(bl_band.a, e2, bl_band.b);
+                            in_l = dl < 0.f;
+                        }
+                        if (!dec_l) {
+                            nfallback += filter_ok;
+                            const double4_32a cl = T.lo[node], ch = T.hi[node];
+                            in_l = dist2_box_box(T.glo[g], T.ghi[g], cl, ch) < T.cl[cid].rl2_d;
+                        }
+                        open = in_l;
+                    } else if ((dec_m && in_m) || (dec_b && in_b)) {
                         open = true;
                     } else if (dec_m && dec_b) {
                         open = false;
@@ -806,6 +838,25 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                         open = dist2_point_box(cm.x, cm.y, cm.z, bl, bh) < cl.w ||
                                dist2_box_box(bl, bh, cl, ch) < T.cl[cid].rout2_d;
                     }
+                    if (SHELL && shell && !nbr_only && !open) {
+                        // a cell the force accepts may still hold neighbours (r_list > r_out)
+                        bool dec_l = false, in_l = false;
+                        if (filter_ok) {
+                            const float ux = fmaxf(fmaxf(b.x - ghx, glx - c.x), 0.f);
+                            const float uy = fmaxf(fmaxf(b.y - ghy, gly - c.y), 0.f);
+                            const float uz = fmaxf(fmaxf(b.z - ghz, glz - c.z), 0.f);
+                            const float e2 = ux * ux + uy * uy + uz * uz;
+                            const float dl = e2 - rl2_f;
+                            dec_l = fabsf(dl) > fmaf(bl_band.a, e2, bl_band.b);
+                            in_l = dl < 0.f;
+                        }
+                        if (!dec_l) {
+                            nfallback += filter_ok;
+                            const double4_32a cl = T.lo[node], ch = T.hi[node];
+                            in_l = dist2_box_box(T.glo[g], T.ghi[g], cl, ch) < T.cl[cid].rl2_d;
+                        }
+                        in_shell = in_l;
+                    }
                 } else {
                     const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
                     const float4 *rec = T.wn + (size_t)kWalkRecord * node;
@@ -816,9 +867,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                 }
                 is_leaf = cinfo < 0;
             }
-            const bool accept = node >= 0 && !open;
-            const bool open_int = node >= 0 && open && !is_leaf;
-            const bool open_leaf = node >= 0 && open && is_leaf;
+            // force: accepted cells and opened nodes of force ranges; neighbour count
+            // only: flagged ranges that pass the r_list test and accepted shell cells
+            const bool accept = node >= 0 && !open && !nbr_only;
+            const bool go_nbr = node >= 0 && ((nbr_only && open) || in_shell);
+            const bool open_int = node >= 0 && ((open && !nbr_only) || go_nbr) && !is_leaf;
+            const bool open_leaf = node >= 0 && ((open && !nbr_only) || go_nbr) && is_leaf;
             // consistency of the child / particle ranges before following them
             const bool bad = (open_int && (ccount < 1 || ccount > 8 || cinfo + ccount > nn)) ||
                              (open_leaf && (ccount < 1 || -1 - cinfo + ccount > T.n));
@@ -835,7 +889,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                 sp = 0;
                 break;
             }
-            if (open_int) W.stk[sp + __popc(pm >> lane >> 1)] = pack_range(cinfo, ccount);
+            if (open_int) W.stk[sp + __popc(pm >> lane >> 1)] = pack_range_f(cinfo, ccount, go_nbr);
             sp += npush;
 
             // ---- queue accepted cells
@@ -874,13 +928,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
             cb += na;
             ncell += na;
 
-            // ---- queue opened leaves
+            // ---- queue opened leaves (neighbour-only ones flagged in bit 31 of .x)
             const unsigned lm = __ballot_sync(0xffffffffu, open_leaf);
-            if (open_leaf) W.lq[lqn + __popc(lm & lt)] = make_int2(-1 - cinfo, ccount);
+            if (open_leaf)
+                W.lq[lqn + __popc(lm & lt)] =
+                    make_int2((int)((unsigned)(-1 - cinfo) | (go_nbr ? kRangeFlag : 0u)), ccount);
             lqn += __popc(lm);
             const int lc = (int)__reduce_add_sync(0xffffffffu, open_leaf ? (unsigned)ccount : 0u);
             lqp += lc;
-            npart += lc;
+            npart += shell ? (int)__reduce_add_sync(0xffffffffu, open_leaf && !go_nbr ? (unsigned)ccount : 0u)
+                           : lc;
 
             if (cb >= tile) {
                 eval_cells_any<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
@@ -928,10 +985,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
     }
 }
 
-template <typename Real, int TPL, bool POT, bool QUAD, bool NBR>
+template <typename Real, int TPL, bool POT, bool QUAD, bool NBR, bool SHELL>
 static int launch_walk(p3t_ctx *c, const WalkArgs &a)
 {
-    auto kern = walk_kernel<Real, TPL, POT, QUAD, NBR>;
+    auto kern = walk_kernel<Real, TPL, POT, QUAD, NBR, SHELL>;
     const size_t smem = kWalkWarps * WarpSmem<Real>::bytes(a.tile);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
@@ -945,23 +1002,23 @@ static int launch_walk(p3t_ctx *c, const WalkArgs &a)
     return check_launch(c);
 }
 
-template <typename Real, int TPL, bool NBR>
+template <typename Real, int TPL, bool NBR, bool SHELL>
 static int dispatch_pq(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
 {
     if (pot)
-        return quad ? launch_walk<Real, TPL, true, true, NBR>(c, a)
-                    : launch_walk<Real, TPL, true, false, NBR>(c, a);
-    return quad ? launch_walk<Real, TPL, false, true, NBR>(c, a)
-                : launch_walk<Real, TPL, false, false, NBR>(c, a);
+        return quad ? launch_walk<Real, TPL, true, true, NBR, SHELL>(c, a)
+                    : launch_walk<Real, TPL, true, false, NBR, SHELL>(c, a);
+    return quad ? launch_walk<Real, TPL, false, true, NBR, SHELL>(c, a)
+                : launch_walk<Real, TPL, false, false, NBR, SHELL>(c, a);
 }
 
-template <typename Real, bool NBR>
+template <typename Real, bool NBR, bool SHELL = false>
 static int dispatch_tpl(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
 {
     const int G = c->prm.group_size;
-    if (G <= 32) return dispatch_pq<Real, 1, NBR>(c, a, pot, quad);
-    if (G <= 64) return dispatch_pq<Real, 2, NBR>(c, a, pot, quad);
-    return dispatch_pq<Real, 4, NBR>(c, a, pot, quad);
+    if (G <= 32) return dispatch_pq<Real, 1, NBR, SHELL>(c, a, pot, quad);
+    if (G <= 64) return dispatch_pq<Real, 2, NBR, SHELL>(c, a, pot, quad);
+    return dispatch_pq<Real, 4, NBR, SHELL>(c, a, pot, quad);
 }
 
 int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc, int64_t *np)
@@ -987,19 +1044,23 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     a.rl2_d = P.r_list * P.r_list;
     a.rl_f = (float)P.r_list;
     a.rl2_f = (float)a.rl2_d;
-    // count neighbours in the walk for the clusters whose neighbour pairs all lie in
-    // opened leaves (0 < r_list <= r_out); with the context's parameters the host
-    // knows whether that holds, with a per-cluster table the walk decides per group
-    const bool fuse_nbr = c->built_precision == P3T_FP32_MIXED &&
-                          (!c->uniform_params || (P.r_list > 0.0 && P.r_list <= P.r_out));
+    // the mixed walk counts the neighbours of every cluster with a list radius
+    // (beyond r_out through neighbour-only ranges); with a per-cluster table the
+    // walk decides per group
+    const bool fuse_nbr = c->built_precision == P3T_FP32_MIXED && (!c->uniform_params || P.r_list > 0.0);
     a.nbr_count = fuse_nbr ? c->nbr_count : nullptr;
     if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
         return P3T_ERR_CUDA;
     const bool quad = P.quadrupole != 0;
     const bool want_pot = pot != nullptr;
     int e;
+    // neighbour-only ranges are needed when a list radius exceeds r_out (with a
+    // per-cluster table the host cannot tell, so they are compiled in)
+    const bool shell = fuse_nbr && (!c->uniform_params || P.r_list > P.r_out);
     if (c->built_precision == P3T_FP64)
         e = dispatch_tpl<double, false>(c, a, want_pot, quad);
+    else if (shell)
+        e = dispatch_tpl<float, true, true>(c, a, want_pot, quad);
     else if (fuse_nbr)
         e = dispatch_tpl<float, true>(c, a, want_pot, quad);
     else
