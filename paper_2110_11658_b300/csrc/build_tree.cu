@@ -406,7 +406,6 @@ __global__ void topo_root_kernel(Tree T, int n, int leaf_cap, int G)
     T.topo[c] = make_int4((int)first, cnt, -1, 0);
     T.level[c] = 0;
     T.parent[c] = -1;
-    T.ready[c] = 0;
     if (cnt <= leaf_cap) T.leaves[atomicAdd(&T.meta->n_leaves, 1)] = c;
     flag_groups(T.gflag, (int)first, cnt, true, cnt <= leaf_cap, G);
 }
@@ -478,7 +477,6 @@ __global__ void __launch_bounds__(kBuildThreads)
                         T.topo[c] = make_int4(bnd[o], cnt, -1, 0);
                         T.level[c] = l + 1;
                         T.parent[c] = node;
-                        T.ready[c] = 0;
                         bool leaf = cnt <= leaf_cap || l + 1 >= kLevels;
                         if (leaf) T.leaves[atomicAdd(&M->n_leaves, 1)] = c;
                         flag_groups(T.gflag, bnd[o], cnt, big, leaf, G);

@@ -62,7 +62,6 @@ static size_t scratch_plan(p3t_ctx *c, long long N, int L, char *base)
     put(&T.topo, 16 * (size_t)NN);
     put(&T.level, 4 * (size_t)NN);
     put(&T.parent, 4 * (size_t)NN);
-    put(&T.ready, 4 * (size_t)NN);
     put(&T.comM, 32 * (size_t)NN);
     put(&T.lo, 32 * (size_t)NN);
     put(&T.hi, 32 * (size_t)NN);

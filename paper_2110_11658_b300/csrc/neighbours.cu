@@ -5,10 +5,10 @@
 // Passes, one warp per walk group:
 //   count  walk opening every cell whose box lies within r_list of the group
 //          box, test each target against the particles of the opened leaves
-//          (skipped when the far-force walk already counted: r_list <= r_out)
+//          (skipped for the clusters the mixed far-force walk already counted)
 //   scan   counts -> int64 row offsets (look-back scan)
 //   fill   the same walk, writing original indices; then each row is sorted
-//          in registers (warp-wide bitonic network).
+//          (bitonic networks by row-length class, see below).
 // The pair test is defined in FP64 as r2 = (dx*dx + dy*dy) + dz*dz < r_list^2.
 // It is first taken in FP32 on coordinates relative to the group centre
 // (double-single differences); a pair inside the FP32 error band is re-tested
@@ -28,9 +28,7 @@ constexpr int kNbrLeafQ = 96;  // flush threshold 64 + up to 32 leaves from one 
 constexpr float kUn = 5.9604644775390625e-8f;
 
 struct NbrArgs {
-    Tree T;
-    double rl2_d;
-    float rl_f, rl2_f;
+    Tree T;  // list radii and frames come from the tree's cluster table
     int32_t *count;        // per particle, original order
     const int64_t *offs;   // row offsets (fill pass)
     int32_t *idx;          // entries (fill pass)
@@ -495,9 +493,6 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
     const int n = c->n;
     NbrArgs a;
     a.T = c->tree;
-    a.rl2_d = c->prm.r_list * c->prm.r_list;
-    a.rl_f = (float)c->prm.r_list;
-    a.rl2_f = (float)a.rl2_d;
     a.count = c->nbr_count;
     a.offs = offsets;
     a.idx = idx;

@@ -94,7 +94,6 @@ struct Tree {
     int4 *topo;
     int32_t *level;
     int32_t *parent;
-    int32_t *ready;
     double4_32a *comM;
     double4_32a *lo;
     double4_32a *hi;

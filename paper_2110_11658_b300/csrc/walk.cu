@@ -59,11 +59,7 @@ constexpr int kMinBlocksTpl1 = 6;            // resident blocks per SM at TPL = 
 // consumed; so at most 32 ranges per level are live: 32 * 22 in total.
 
 struct WalkArgs {
-    Tree T;
-    float inv_dr_f, rin_dr_f;   // x = r * inv_dr - r_in * inv_dr
-    double inv_dr_d, r_in_d;
-    double rout2_d;
-    float rout2_f;
+    Tree T;  // every radius and frame comes from the tree's cluster table
     int tile;
     void *ax, *ay, *az;
     double *pot;
@@ -71,8 +67,6 @@ struct WalkArgs {
     long long *grp_cells, *grp_parts;
     unsigned int *ticket;
     int32_t *nbr_count;          // fused neighbour count (original order) or null
-    double rl2_d;
-    float rl_f, rl2_f;
 };
 
 template <typename Real>
@@ -1026,13 +1020,6 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     const p3t_params &P = c->prm;
     WalkArgs a;
     a.T = c->tree;
-    const double dr = P.r_out - P.r_in;
-    a.inv_dr_d = 1.0 / dr;
-    a.r_in_d = P.r_in;
-    a.inv_dr_f = (float)a.inv_dr_d;
-    a.rin_dr_f = (float)(P.r_in * a.inv_dr_d);
-    a.rout2_d = P.r_out * P.r_out;
-    a.rout2_f = (float)a.rout2_d;
     a.tile = P.tile;
     a.ax = ax, a.ay = ay, a.az = az;
     a.pot = pot;
@@ -1041,9 +1028,6 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     a.grp_cells = c->debug ? (long long *)c->grp_cells : nullptr;
     a.grp_parts = c->debug ? (long long *)c->grp_parts : nullptr;
     a.ticket = &c->meta->tickets[22];
-    a.rl2_d = P.r_list * P.r_list;
-    a.rl_f = (float)P.r_list;
-    a.rl2_f = (float)a.rl2_d;
     // the mixed walk counts the neighbours of every cluster with a list radius
     // (beyond r_out through neighbour-only ranges); with a per-cluster table the
     // walk decides per group
