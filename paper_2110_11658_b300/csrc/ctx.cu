@@ -55,6 +55,7 @@ static size_t scratch_plan(p3t_ctx *c, long long N, int L, char *base)
     put(&T.glo, 32 * (size_t)N);
     put(&T.ghi, 32 * (size_t)N);
     put(&c->nbr_count, 4 * (size_t)N);
+    put(&c->row_list, 4 * (size_t)N);
     put(&c->grp_cells, 8 * (size_t)N);
     put(&c->grp_parts, 8 * (size_t)N);
     put(&c->sort_hist, 4 * 256 * (size_t)sort_blocks);

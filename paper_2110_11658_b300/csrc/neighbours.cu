@@ -14,6 +14,7 @@
 // (double-single differences); a pair inside the FP32 error band is re-tested
 // with the exact FP64 operations, so the lists equal the FP64 definition bit
 // for bit.
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 #include <type_traits>
@@ -301,21 +302,102 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 }
 
 // ---- per-row ascending sort --------------------------------------------------
-// One warp per row.  Rows of up to 128 entries sit in registers (element
-// e = 32 r + lane in register r) and a bitonic network sorts them: partners 32
-// apart or more are in the same lane, closer ones are exchanged by shuffles.
-// Rows of up to 512 entries use the same in-register network with 8 or 16
-// registers per lane.  Longer rows are sorted by a loop-based network in which every
-// compare-exchange puts the smaller value at the lower index (each merge stage
-// starts by comparing mirrored positions of a block), so a row of any length
-// sorts in place as if padded with +infinity: a pair whose upper index is past
-// the end never moves.  Rows of up to kSmemRow entries are sorted in shared
-// memory, longer ones directly in global memory.  The size classes run as
-// separate launches: one kernel holding the fully unrolled networks of every
-// size overflowed the instruction cache.
+// Rows are distinct indices in [0, n), so the sorted row is unique and any
+// correct sort writes the same bytes.  The rows are first binned by length into
+// per-class lists (two cheap passes over the row offsets), then each class is
+// sorted by its own launch, one warp per listed row, so that no launch scans the
+// rows of other classes and only one class's code is resident in the
+// instruction cache:
+//   (1, 512]      bitonic network in registers, K = 1, 2, 4, 8, 16 entries per
+//                 lane (element e = 32 r + lane in register r; partners 32 apart
+//                 or more are in the same lane, closer ones are exchanged by
+//                 shuffles)
+//   (512, 2048]   loop-based bitonic network (below) in shared memory
+//   > 2048        the same network in global memory.
+// The loop network puts the smaller value at the lower index in every
+// compare-exchange (each merge stage starts by comparing mirrored positions of a
+// block), so a row of any length sorts in place as if padded with +infinity: a
+// pair whose upper index is past the end never moves.  (An LSD radix sort in
+// shared memory, ranks from ballots, was slower than these networks for every
+// class of the 10^6-particle Plummer workload.)
+constexpr int kRowClasses = 8;
+// class c holds the rows with kClassLen[c] < len <= kClassLen[c + 1]
+__constant__ int kClassLenDev[kRowClasses + 1] = {1, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
+constexpr int kClassLen[kRowClasses + 1] = {1, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
 constexpr int kSortWarps = 4;
-constexpr int kRegRow = 512;    // longest row sorted in registers (16 per lane)
-constexpr int kSmemRow = 2048;  // longest row sorted in shared memory
+
+__device__ __forceinline__ int row_class(int len)
+{
+    int c = 0;
+#pragma unroll
+    for (int k = 1; k < kRowClasses; k++) c += len > kClassLenDev[k];
+    return len > 1 ? c : -1;
+}
+
+// counts of the classes -> Meta.row_class[0 .. 7]
+__global__ void row_class_count_kernel(int n, const int64_t *__restrict__ offs, long long capacity,
+                                       Meta *meta)
+{
+    __shared__ int cnt[kRowClasses];
+    if (threadIdx.x < kRowClasses) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    if (offs[n] <= capacity) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const int c = row_class((int)(offs[i + 1] - offs[i]));
+            if (c >= 0) atomicAdd(&cnt[c], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kRowClasses && cnt[threadIdx.x])
+        atomicAdd(&meta->row_class[threadIdx.x], cnt[threadIdx.x]);
+}
+
+// row ids -> list, class c at [sum of the counts below c, + count c) (in any
+// order inside a class); cursors in Meta.row_class[8 .. 15]
+__global__ void row_class_fill_kernel(int n, const int64_t *__restrict__ offs, long long capacity,
+                                      Meta *meta, int32_t *list)
+{
+    __shared__ int cnt[kRowClasses], base[kRowClasses];
+    if (offs[n] > capacity) return;
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        if (threadIdx.x < kRowClasses) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        const int i = i0 + threadIdx.x;
+        const int c = i < n ? row_class((int)(offs[i + 1] - offs[i])) : -1;
+        const int rank = c >= 0 ? atomicAdd(&cnt[c], 1) : 0;
+        __syncthreads();
+        if (threadIdx.x < kRowClasses) {
+            int start = 0;
+            for (int q = 0; q < (int)threadIdx.x; q++) start += meta->row_class[q];
+            base[threadIdx.x] =
+                start + (cnt[threadIdx.x] ? atomicAdd(&meta->row_class[kRowClasses + threadIdx.x],
+                                                      cnt[threadIdx.x])
+                                          : 0);
+        }
+        __syncthreads();
+        if (c >= 0) list[base[c] + rank] = i;
+        __syncthreads();
+    }
+}
+
+// The rows of class C, one warp each: f(row pointer, length).
+template <int C, typename F>
+__device__ __forceinline__ void for_class_rows(const Meta *meta, const int32_t *list,
+                                               const int64_t *offs, int32_t *idx, F &&f)
+{
+    int start = 0;
+#pragma unroll
+    for (int q = 0; q < C; q++) start += meta->row_class[q];
+    const int count = meta->row_class[C];
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < count;
+         k += (gridDim.x * blockDim.x) >> 5) {
+        const int i = list[start + k];
+        const long long o = offs[i];
+        f(idx + o, (int)(offs[i + 1] - o));
+        __syncwarp();
+    }
+}
 
 template <int K>
 __device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len)
@@ -398,69 +480,74 @@ __device__ void warp_sort_mem(int32_t *a, int len)
     }
 }
 
-// Rows whose length lies in (lo, hi], one warp per row.  Each size class is its
-// own launch so that only one register network is resident in the instruction
-// cache at a time.
-template <int K>
+template <int C, int K>
 __global__ void __launch_bounds__(kSortWarps * 32)
-    row_sort_reg_kernel(int n, const int64_t *__restrict__ offs, int32_t *idx, long long capacity)
+    row_sort_reg_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
+                        int32_t *idx)
 {
-    if (offs[n] > capacity) return;
-    constexpr int lo = K == 1 ? 1 : 16 * K, hi = 32 * K;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
-         i += (gridDim.x * blockDim.x) >> 5) {
-        const long long o = offs[i];
-        const int len = (int)(offs[i + 1] - o);
-        if (len > lo && len <= hi) warp_bitonic_row<K>(idx + o, len);
-        __syncwarp();
-    }
+    for_class_rows<C>(meta, list, offs, idx, [](int32_t *row, int len) { warp_bitonic_row<K>(row, len); });
 }
 
-// Rows of up to 128 entries (three small networks in one launch).
+// rows of class C sorted by the loop network in shared memory
+template <int C>
 __global__ void __launch_bounds__(kSortWarps * 32)
-    row_sort_small_kernel(int n, const int64_t *__restrict__ offs, int32_t *idx, long long capacity)
+    row_sort_smem_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
+                         int32_t *idx)
 {
-    if (offs[n] > capacity) return;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
-         i += (gridDim.x * blockDim.x) >> 5) {
-        const long long o = offs[i];
-        const int len = (int)(offs[i + 1] - o);
-        if (len <= 1 || len > 128) continue;
-        int32_t *row = idx + o;
-        if (len <= 32)
-            warp_bitonic_row<1>(row, len);
-        else if (len <= 64)
-            warp_bitonic_row<2>(row, len);
-        else
-            warp_bitonic_row<4>(row, len);
-        __syncwarp();
-    }
-}
-
-// Rows longer than kRegRow: shared memory up to kSmemRow, global memory beyond.
-__global__ void __launch_bounds__(kSortWarps * 32)
-    row_sort_mem_kernel(int n, const int64_t *__restrict__ offs, int32_t *idx, long long capacity)
-{
-    __shared__ int32_t sbuf[kSortWarps][kSmemRow];
+    __shared__ int32_t sbuf[kSortWarps][kClassLen[C + 1]];
     const int lane = threadIdx.x & 31;
     int32_t *sb = sbuf[threadIdx.x >> 5];
-    if (offs[n] > capacity) return;
-    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n;
-         i += (gridDim.x * blockDim.x) >> 5) {
-        const long long o = offs[i];
-        const int len = (int)(offs[i + 1] - o);
-        if (len <= kRegRow) continue;
-        int32_t *row = idx + o;
-        if (len <= kSmemRow) {
-            for (int e = lane; e < len; e += 32) sb[e] = row[e];
-            __syncwarp();
-            warp_sort_mem(sb, len);
-            for (int e = lane; e < len; e += 32) row[e] = sb[e];
-        } else {
-            warp_sort_mem(row, len);
-        }
+    for_class_rows<C>(meta, list, offs, idx, [&](int32_t *row, int len) {
+        for (int e = lane; e < len; e += 32) sb[e] = row[e];
         __syncwarp();
+        warp_sort_mem(sb, len);
+        for (int e = lane; e < len; e += 32) row[e] = sb[e];
+    });
+}
+
+// rows of class C sorted by the loop network in global memory
+template <int C>
+__global__ void __launch_bounds__(kSortWarps * 32)
+    row_sort_global_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
+                           int32_t *idx)
+{
+    for_class_rows<C>(meta, list, offs, idx, [](int32_t *row, int len) { warp_sort_mem(row, len); });
+}
+
+template <typename Kern>
+static int launch_sort(p3t_ctx *c, Kern kern, const int64_t *offsets, int32_t *idx)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSortWarps * 32, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return P3T_ERR_CUDA;
+    kern<<<per_sm * c->sm_count, kSortWarps * 32, 0, c->stream>>>(c->meta, c->row_list, offsets, idx);
+    return check_launch(c);
+}
+
+// Sorts every row of the filled lists (offsets[n] <= capacity; otherwise nothing).
+static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long capacity)
+{
+    cudaStream_t s = c->stream;
+    const int n = c->n;
+    if (cudaMemsetAsync(c->meta->row_class, 0, sizeof(c->meta->row_class), s) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    const int grid = (int)std::min<long long>(((long long)n + 255) / 256, 4LL * c->sm_count);
+    row_class_count_kernel<<<grid, 256, 0, s>>>(n, offsets, capacity, c->meta);
+    row_class_fill_kernel<<<grid, 256, 0, s>>>(n, offsets, capacity, c->meta, c->row_list);
+    int e = check_launch(c);
+    if (e) return e;
+    if ((e = launch_sort(c, row_sort_reg_kernel<0, 1>, offsets, idx))) return e;
+    if ((e = launch_sort(c, row_sort_reg_kernel<1, 2>, offsets, idx))) return e;
+    if ((e = launch_sort(c, row_sort_reg_kernel<2, 4>, offsets, idx))) return e;
+    if (n > kClassLen[3] + 1) {  // longer rows need more than 128 distinct indices
+        if ((e = launch_sort(c, row_sort_reg_kernel<3, 8>, offsets, idx))) return e;
+        if ((e = launch_sort(c, row_sort_reg_kernel<4, 16>, offsets, idx))) return e;
+        if ((e = launch_sort(c, row_sort_smem_kernel<5>, offsets, idx))) return e;
+        if ((e = launch_sort(c, row_sort_global_kernel<6>, offsets, idx))) return e;
     }
+    return P3T_OK;
 }
 
 template <int TPL, bool FILL>
@@ -532,12 +619,7 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
     if (capacity == 0) return P3T_OK;
     e = dispatch_nbr<true>(c, a);
     if (e) return e;
-    const int grid = 8 * c->sm_count;
-    row_sort_small_kernel<<<grid, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
-    row_sort_reg_kernel<8><<<grid, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
-    row_sort_reg_kernel<16><<<grid, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
-    row_sort_mem_kernel<<<grid, kSortWarps * 32, 0, s>>>(n, offsets, idx, capacity);
-    return check_launch(c);
+    return sort_rows(c, offsets, idx, capacity);
 }
 
 }  // namespace p3t

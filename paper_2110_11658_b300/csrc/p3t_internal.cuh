@@ -63,6 +63,7 @@ struct Meta {
     long long nbr_total;
     long long fallback_tests;      // FP64 decisions taken after an undecided FP32 filter
     unsigned long long core_count; // particles within the core radius (core quantities)
+    int row_class[16];             // neighbour rows by length class: counts, fill cursors
 };
 
 // ---- one cluster of a (possibly batched) build -----------------------------------
@@ -374,6 +375,7 @@ struct p3t_ctx {
     int32_t *sort_hist;               // 256 * sort blocks
     unsigned long long *scan_status;  // look-back status words
     int32_t *nbr_count;               // per particle (original order)
+    int32_t *row_list;                // neighbour rows binned by length class
     int64_t *grp_cells, *grp_parts;   // per group debug counts
     void *blob;                       // single allocation backing everything above
     size_t blob_bytes;
