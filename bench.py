@@ -36,12 +36,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# DRAM bytes of one walk_kernel launch per particle, from the ncu capture summarised
-# in profiles/walk_kernel_plummer_kroupa_n262144.md (17.25 MB at N = 2^18; the
-# traffic grows with N).  Valid only for the kernel sources it was measured on:
+# DRAM bytes of one walk_kernel launch per particle, from the ncu capture of the
+# 10^6-particle Plummer walk summarised in profiles/walk_kernel_plummer_kroupa_n1e6.md
+# (73.95 MB read + 11.51 MB written; 65.8 B per particle at N = 2^18, so the figure
+# holds for N = 10^6 only).  Valid only for the kernel sources it was measured on:
 # if they change, the roofline's traffic is reported as null until re-measured.
-WALK_TRAFFIC = {"sources": {"walk.cu": "e4b071658d0b0e22", "p3t_internal.cuh": "1846c913bb5c5164"},
-                "bytes_per_particle": 17250816 / 262144}
+WALK_TRAFFIC = {"sources": {"walk.cu": "10b996333d99d67b", "p3t_internal.cuh": "74a3aebf000683be"},
+                "n": 1000000, "bytes": 73951232 + 11510272}
 
 N_DEFAULT = 1_000_000
 THETA = 0.4
@@ -208,7 +209,7 @@ def walk_traffic(n):
         with open(os.path.join(csrc, name), "rb") as fh:
             if hashlib.sha256(fh.read()).hexdigest()[:16] != want:
                 return None
-    return WALK_TRAFFIC["bytes_per_particle"] * n
+    return WALK_TRAFFIC["bytes"] if n == WALK_TRAFFIC["n"] else None
 
 
 def fp32_peak_tflops(sm_count, sm_max_mhz):
