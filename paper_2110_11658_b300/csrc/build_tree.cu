@@ -25,8 +25,8 @@
 namespace p3t {
 
 constexpr int kBuildThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kBuildThreads * kSortItems;
+constexpr int kSortTile = kSortTileItems;
+constexpr int kSortItems = kSortTile / kBuildThreads;
 constexpr unsigned long long kQMax = (1ULL << 21) - 1;
 
 int topo_status_stride(long long n);
@@ -310,17 +310,36 @@ __global__ void __launch_bounds__(kBuildThreads)
     gofs[tid] = hist_off[tid * nblocks + blockIdx.x];
 #pragma unroll
     for (int w = 0; w < W; w++) wcnt[w][tid] = 0;
+    // every item of the tile is loaded before the ranking rounds
+    const long long base = (long long)blockIdx.x * kSortTile;
+    uint64_t key[kSortItems];
+    int32_t val[kSortItems];
+    int dig[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++) {
+        const long long i = base + r * kBuildThreads + tid;
+        const bool valid = i < n;
+        key[r] = valid ? kin[i] : 0;
+        val[r] = valid ? vin[i] : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kSortItems; r++)
+        dig[r] = base + r * kBuildThreads + tid < n ? sort_digit(key[r], val[r], shift, cid) : 0;
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    const long long base = (long long)blockIdx.x * kSortTile;
+#pragma unroll
     for (int r = 0; r < kSortItems; r++) {
-        long long i = base + r * kBuildThreads + tid;
-        bool valid = i < n;
-        uint64_t key = valid ? kin[i] : 0;
-        int32_t val = valid ? vin[i] : 0;
-        int d = valid ? sort_digit(key, val, shift, cid) : 256;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int wrank = __popc(peers & lt);
+        const bool valid = base + r * kBuildThreads + tid < n;
+        const int d = dig[r];
+        // lanes of this warp holding the same digit: one ballot per digit bit
+        unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            const bool bit = (d >> b) & 1;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
+        const int wrank = __popc(peers & lt);
         if (valid && wrank == 0) wcnt[warp][d] = __popc(peers);
         __syncthreads();
         {
@@ -336,9 +355,9 @@ __global__ void __launch_bounds__(kBuildThreads)
         }
         __syncthreads();
         if (valid) {
-            int pos = pofs[warp][d] + wrank;
-            kout[pos] = key;
-            vout[pos] = val;
+            const int pos = pofs[warp][d] + wrank;
+            kout[pos] = key[r];
+            vout[pos] = val[r];
         }
     }
 }
@@ -410,19 +429,6 @@ __global__ void topo_root_kernel(Tree T, int n, int leaf_cap, int G)
     flag_groups(T.gflag, (int)first, cnt, true, cnt <= leaf_cap, G);
 }
 
-__device__ __forceinline__ int lower_bound_key(const uint64_t *__restrict__ keys, int lo, int hi,
-                                               uint64_t target)
-{
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (keys[mid] < target)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return lo;
-}
-
 __global__ void __launch_bounds__(kBuildThreads)
     topo_level_kernel(Tree T, int l, int leaf_cap, int G, unsigned long long *status,
                       unsigned int *ticket)
@@ -453,9 +459,21 @@ __global__ void __launch_bounds__(kBuildThreads)
             const uint64_t pfx = T.keys[b] >> (shift + 3);
             bnd[0] = b;
             bnd[8] = e;
+            // the 7 octant boundaries: lower bounds of ((pfx << 3) | o) << shift in
+            // keys[b, e), searched in lockstep (branchless halving with a common
+            // length, so the 7 loads of a step are independent)
+            uint64_t tgt[8];
+            int at[8];
 #pragma unroll
-            for (int o = 1; o < 8; o++)
-                bnd[o] = lower_bound_key(T.keys, bnd[o - 1], e, ((pfx << 3) | (uint64_t)o) << shift);
+            for (int o = 1; o < 8; o++) tgt[o] = ((pfx << 3) | (uint64_t)o) << shift, at[o] = b;
+            for (int len = e - b; len > 1;) {
+                const int half = len >> 1;
+#pragma unroll
+                for (int o = 1; o < 8; o++) at[o] = T.keys[at[o] + half] < tgt[o] ? at[o] + half : at[o];
+                len -= half;
+            }
+#pragma unroll
+            for (int o = 1; o < 8; o++) bnd[o] = at[o] + (T.keys[at[o]] < tgt[o] ? 1 : 0);
 #pragma unroll
             for (int o = 0; o < 8; o++) nch += bnd[o + 1] > bnd[o];
         }
@@ -645,13 +663,24 @@ __device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
     double M = 0.0, S[3] = {0, 0, 0}, lo[3], hi[3], com[3];
     EncBox box;
     box.reset();
-    for (int i = b; i < e; i++) {
-        double4_32a p = T.sp[i];
-        M = dadd(M, p.w);
-        S[0] = dadd(S[0], dmul(p.w, p.x));
-        S[1] = dadd(S[1], dmul(p.w, p.y));
-        S[2] = dadd(S[2], dmul(p.w, p.z));
-        box.add(p.x, p.y, p.z);
+    // chunks of 8 particles: the loads of a chunk are issued before its
+    // (sequential, fixed-order) sums
+    for (int i0 = b; i0 < e; i0 += 8) {
+        double4_32a pc[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (i0 + u < e) pc[u] = T.sp[i0 + u];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            if (i0 + u < e) {
+                const double4_32a &p = pc[u];
+                M = dadd(M, p.w);
+                S[0] = dadd(S[0], dmul(p.w, p.x));
+                S[1] = dadd(S[1], dmul(p.w, p.y));
+                S[2] = dadd(S[2], dmul(p.w, p.z));
+                box.add(p.x, p.y, p.z);
+            }
+        }
     }
     box.get(lo, hi);
     for (int d = 0; d < 3; d++) com[d] = M > 0.0 ? ddiv(S[d], M) : dmul(0.5, dadd(lo[d], hi[d]));
@@ -679,6 +708,7 @@ __device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
         ds_split(dsub(com[1], O[1]), chy, cly);
         ds_split(dsub(com[2], O[2]), chz, clz);
         float Q[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 8
         for (int i = b; i < e; i++) {
             const float4 h = T.ph[i], l = T.pl[i];
             const float m = h.w;
@@ -713,26 +743,37 @@ __device__ void internal_moments(Tree &T, int k, int4 tp, double theta)
     double M = 0.0, S[3] = {0, 0, 0}, lo[3], hi[3], com[3];
     EncBox box;
     box.reset();
-    for (int c = c0; c < c1; c++) {
-        double4_32a cm = ldcg_d4(&T.comM[c]);
-        double4_32a cl = ldcg_d4(&T.lo[c]);
-        double4_32a ch = ldcg_d4(&T.hi[c]);
-        M = dadd(M, cm.w);
-        S[0] = dadd(S[0], dmul(cm.w, cm.x));
-        S[1] = dadd(S[1], dmul(cm.w, cm.y));
-        S[2] = dadd(S[2], dmul(cm.w, cm.z));
-        box.add_box(cl, ch);
+    // at most 8 children: every child's record is loaded before the
+    // (sequential, octant-order) sums
+    const int nc = c1 - c0;
+    double4_32a cm[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+        if (i < nc) cm[i] = ldcg_d4(&T.comM[c0 + i]);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        if (i < nc) {
+            const double4_32a cl = ldcg_d4(&T.lo[c0 + i]);
+            const double4_32a ch = ldcg_d4(&T.hi[c0 + i]);
+            M = dadd(M, cm[i].w);
+            S[0] = dadd(S[0], dmul(cm[i].w, cm[i].x));
+            S[1] = dadd(S[1], dmul(cm[i].w, cm[i].y));
+            S[2] = dadd(S[2], dmul(cm[i].w, cm[i].z));
+            box.add_box(cl, ch);
+        }
     }
     box.get(lo, hi);
     for (int d = 0; d < 3; d++) com[d] = M > 0.0 ? ddiv(S[d], M) : dmul(0.5, dadd(lo[d], hi[d]));
     double q[6];
     if (Q64) {
         double Q[6] = {0, 0, 0, 0, 0, 0};
-        for (int c = c0; c < c1; c++) {
-            double4_32a cm = ldcg_d4(&T.comM[c]);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            if (i >= nc) break;
+            const int c = c0 + i;
             const double *Qc = T.q64 + 6 * (size_t)c;
-            double Mc = cm.w;
-            double dx = dsub(cm.x, com[0]), dy = dsub(cm.y, com[1]), dz = dsub(cm.z, com[2]);
+            double Mc = cm[i].w;
+            double dx = dsub(cm[i].x, com[0]), dy = dsub(cm[i].y, com[1]), dz = dsub(cm[i].z, com[2]);
             double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
             Q[0] = dadd(Q[0], dadd(__ldcg(Qc + 0), dmul(Mc, dsub(dmul(dmul(3.0, dx), dx), d2))));
             Q[1] = dadd(Q[1], dadd(__ldcg(Qc + 1), dmul(Mc, dmul(dmul(3.0, dx), dy))));
@@ -744,13 +785,15 @@ __device__ void internal_moments(Tree &T, int k, int4 tp, double theta)
         for (int a = 0; a < 6; a++) q[a] = Q[a];
     } else {
         float Q[6] = {0, 0, 0, 0, 0, 0};
-        for (int c = c0; c < c1; c++) {
-            double4_32a cm = ldcg_d4(&T.comM[c]);
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            if (i >= nc) break;
+            const int c = c0 + i;
             const float *Qc = T.q32 + 6 * (size_t)c;
-            float Mc = (float)cm.w;
-            float dx = __double2float_rn(dsub(cm.x, com[0]));
-            float dy = __double2float_rn(dsub(cm.y, com[1]));
-            float dz = __double2float_rn(dsub(cm.z, com[2]));
+            float Mc = (float)cm[i].w;
+            float dx = __double2float_rn(dsub(cm[i].x, com[0]));
+            float dy = __double2float_rn(dsub(cm[i].y, com[1]));
+            float dz = __double2float_rn(dsub(cm[i].z, com[2]));
             float d2 = dx * dx + dy * dy + dz * dz;
             Q[0] += __ldcg(Qc + 0) + Mc * (3.f * dx * dx - d2);
             Q[1] += __ldcg(Qc + 1) + Mc * (3.f * dx * dy);

@@ -28,7 +28,7 @@ int topo_status_stride(long long n) { return (int)(n / 256 + 4); }
 static size_t scratch_plan(p3t_ctx *c, long long N, int L, char *base)
 {
     const long long NN = node_capacity(N, L);
-    const long long sort_blocks = (N + 4095) / 4096;
+    const long long sort_blocks = (N + kSortTileItems - 1) / kSortTileItems;
     const long long scan_words = N / 256 + 64 + 256 * sort_blocks / 256;
     const long long topo_words = (long long)kMaxLevelSlots * topo_status_stride(N);
     Tree &T = c->tree;

@@ -45,7 +45,7 @@ __global__ void sort_scatter_kernel(int n, const uint64_t *__restrict__ kin,
 namespace {
 
 constexpr int kMaxN = P3T_NOALLOC_MAX_N;
-constexpr int kTile = 4096;                       // items per sort block
+constexpr int kTile = kSortTileItems;             // items per sort block
 constexpr int kMaxBlocks = (kMaxN + kTile - 1) / kTile;
 constexpr size_t kClusterOff = (sizeof(Meta) + 15) / 16 * 16;                     // Cluster after Meta
 constexpr size_t kMetaBytes = (kClusterOff + sizeof(Cluster) + 255) / 256 * 256;

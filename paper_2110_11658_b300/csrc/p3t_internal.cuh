@@ -50,6 +50,9 @@ __host__ __device__ inline Band fp32_band(float R, float r2)
                 (k_rel * r2 * 1.0001f + 0.8661f * k_abs * r + k_sq) * 1.001f};
 }
 
+// ---- key sort: items per block of the radix-sort passes (256 threads x 4) -----
+constexpr int kSortTileItems = 1024;
+
 // ---- device metadata block (one per context) -------------------------------
 struct Meta {
     int err;                       // first latched error code (0 = none)
