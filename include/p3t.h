@@ -154,11 +154,13 @@ int p3t_drift(p3t_ctx *c, int64_t n, double dt, double *x, double *y, double *z,
 
 /* One whole regular step from HOST memory, the paper's REGF + RKICK boundary
  * (Sec. 2.4, Eq. 12): copy x, y, z, m, vx, vy, vz (host double[n]) to the
- * device, build, far force, neighbours, kick, and copy back a_far (host
+ * device, build, neighbours, far force, kick, and copy back a_far (host
  * float or double[n] per precision, SoA ax/ay/az), the kicked velocities
  * (in place in vx, vy, vz) and the neighbour lists (host int64 offsets[n+1],
- * int32 idx[capacity]).  Synchronises.  Page-locked host memory gives full
- * copy bandwidth.  *total receives the neighbour count; P3T_ERR_CAPACITY as
+ * int32 idx[capacity]).  The lists are copied on a second stream of the
+ * context while the far force runs; the call synchronises both streams
+ * before it returns.  Page-locked host memory gives full copy bandwidth
+ * (and is needed for the copy to overlap the far force).  *total receives the neighbour count; P3T_ERR_CAPACITY as
  * in p3t_neighbours (velocities are then kicked but idx is not written). */
 int p3t_step_host(p3t_ctx *c, int64_t n, double dt, const double *x, const double *y,
                   const double *z, const double *m, double *vx, double *vy, double *vz, void *ax,

@@ -213,6 +213,11 @@ int p3t_destroy(p3t_ctx *c)
     cudaStreamSynchronize(c->stream);
     if (c->blob) cudaFree(c->blob);
     if (c->host_stage) cudaFree(c->host_stage);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->lists_ready) cudaEventDestroy(c->lists_ready);
     if (c->clusters) cudaFree(c->clusters);
     if (c->irr_buf) cudaFree(c->irr_buf);
     if (c->knn_buf) cudaFree(c->knn_buf);

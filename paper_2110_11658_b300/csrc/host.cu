@@ -1,7 +1,8 @@
 // p3t_step_host: one regular step from and to host memory -- the boundary of
 // the paper's REGF (host arrays in; regular force and neighbour lists out,
 // Sec. 2.4) followed by RKICK (Eq. 12).  Device staging buffers are owned by
-// the context and grow on demand.
+// the context and grow on demand.  The neighbour lists are built before the
+// far force and copied back on a second stream during the walk.
 #include <cstring>
 
 #include "p3t_internal.cuh"
@@ -50,25 +51,49 @@ extern "C" int p3t_step_host(p3t_ctx *c, int64_t n, double dt, const double *x, 
     for (int k = 0; k < 7; k++)
         if (cudaMemcpyAsync(din[k], hin[k], 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
             return P3T_ERR_CUDA;
+    if (!c->copy_stream) {
+        if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            c->copy_stream = nullptr;
+            return P3T_ERR_CUDA;
+        }
+        if (cudaEventCreateWithFlags(&c->lists_ready, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            c->lists_ready = nullptr;
+            return P3T_ERR_CUDA;
+        }
+    }
+    // neighbour lists first (their count pass replaces the count inside the
+    // walk), so that their copy to the host runs on a second stream while the
+    // far-force walk computes
     int e = p3t_build_tree(c, n, dx, dy, dz, dm);
-    if (e) return e;
-    e = p3t_far_force(c, dax, day, daz, nullptr, nullptr, nullptr);
     if (e) return e;
     int ne = p3t_neighbours(c, doffs, didx, capacity, total);
     if (ne && ne != P3T_ERR_CAPACITY) return ne;
-    e = p3t_kick(c, dt, dax, day, daz, dvx, dvy, dvz);
-    if (e) return e;
+    if (cudaEventRecord(c->lists_ready, s) != cudaSuccess ||
+        cudaStreamWaitEvent(c->copy_stream, c->lists_ready, 0) != cudaSuccess ||
+        cudaMemcpyAsync(offsets, doffs, 8 * (n + 1), cudaMemcpyDeviceToHost, c->copy_stream) !=
+            cudaSuccess)
+        return P3T_ERR_CUDA;
+    if (!ne && *total > 0 &&
+        cudaMemcpyAsync(idx, didx, 4 * (size_t)*total, cudaMemcpyDeviceToHost, c->copy_stream) !=
+            cudaSuccess)
+        return P3T_ERR_CUDA;
+    e = p3t_far_force(c, dax, day, daz, nullptr, nullptr, nullptr);
+    if (e == P3T_OK) e = p3t_kick(c, dt, dax, day, daz, dvx, dvy, dvz);
+    if (e) {
+        cudaStreamSynchronize(c->copy_stream);
+        return e;
+    }
     void *hout[6] = {ax, ay, az, vx, vy, vz};
     const void *dout[6] = {dax, day, daz, dvx, dvy, dvz};
     const size_t osz[6] = {asz, asz, asz, 8, 8, 8};
     for (int k = 0; k < 6; k++)
-        if (cudaMemcpyAsync(hout[k], dout[k], osz[k] * n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        if (cudaMemcpyAsync(hout[k], dout[k], osz[k] * n, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+            cudaStreamSynchronize(c->copy_stream);
             return P3T_ERR_CUDA;
-    if (cudaMemcpyAsync(offsets, doffs, 8 * (n + 1), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return P3T_ERR_CUDA;
-    if (!ne && *total > 0 &&
-        cudaMemcpyAsync(idx, didx, 4 * (size_t)*total, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return P3T_ERR_CUDA;
+        }
+    if (cudaStreamSynchronize(c->copy_stream) != cudaSuccess) return P3T_ERR_CUDA;
     e = p3t_status(c);
     if (e) return e;
     return ne;

@@ -1030,8 +1030,10 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     a.ticket = &c->meta->tickets[22];
     // the mixed walk counts the neighbours of every cluster with a list radius
     // (beyond r_out through neighbour-only ranges); with a per-cluster table the
-    // walk decides per group
-    const bool fuse_nbr = c->built_precision == P3T_FP32_MIXED && (!c->uniform_params || P.r_list > 0.0);
+    // walk decides per group.  Counts already taken for this tree (p3t_neighbours
+    // ran first) are not taken again.
+    const bool fuse_nbr = !c->counts_valid && c->built_precision == P3T_FP32_MIXED &&
+                          (!c->uniform_params || P.r_list > 0.0);
     a.nbr_count = fuse_nbr ? c->nbr_count : nullptr;
     if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
         return P3T_ERR_CUDA;
