@@ -126,6 +126,16 @@ __device__ __forceinline__ double dec_double(unsigned long long e)
     unsigned long long u = (e >> 63) ? (e ^ 0x8000000000000000ULL) : ~e;
     return __longlong_as_double((long long)u);
 }
+// isfinite(v) and (for a finite v) v >= 0, tested on the bits (no FP64 instruction)
+__device__ __forceinline__ bool finite_bits(double v)
+{
+    return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ULL) != 0x7ff0000000000000ULL;
+}
+__device__ __forceinline__ bool nonneg_bits(double v)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) == 0 || u == 0x8000000000000000ULL;  // -0 >= 0
+}
 
 // Per-cluster bounding box (exact, order-preserving integer min/max) and input
 // validation.  Each warp keeps running minima and maxima for its current cluster
@@ -173,7 +183,8 @@ __global__ void __launch_bounds__(kBuildThreads)
         if (i < n) {
             const double p[3] = {x[i], y[i], z[i]};
             const double mi = m[i];
-            ok = isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]) && isfinite(mi) && mi >= 0.0;
+            ok = finite_bits(p[0]) && finite_bits(p[1]) && finite_bits(p[2]) && finite_bits(mi) &&
+                 nonneg_bits(mi);
             bad |= !ok;
             c = cid ? cid[i] : 0;
             if (ok)
@@ -532,9 +543,6 @@ __global__ void __launch_bounds__(kBuildThreads)
     if (i < n && gflag[i]) grp[gidx[i]].x = i;
 }
 
-__device__ __forceinline__ double upd_min(double lo, double p) { return p < lo ? p : lo; }
-__device__ __forceinline__ double upd_max(double hi, double p) { return p > hi ? p : hi; }
-
 // Exact box bounds on the integer pipes: min/max of the order-preserving
 // encodings (no FP64 instruction).  Equal to the FP64 min/max except that -0
 // orders below +0, which changes no distance, extent or centre computed later.
@@ -578,22 +586,27 @@ __global__ void __launch_bounds__(kBuildThreads) group_finish_kernel(Tree T, int
          g += (gridDim.x * blockDim.x) >> 5) {
         const int first = T.grp[g].x;
         const int end = g + 1 < ng ? T.grp[g + 1].x : n;
-        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        // min/max of the order-preserving encodings on the integer pipes (the FP64
+        // pipe is slow); equal to the FP64 min/max up to the sign of a zero
+        EncBox box;
+        box.reset();
         for (int i = first + lane; i < end; i += 32) {
-            double4_32a p = T.sp[i];
-            lo[0] = upd_min(lo[0], p.x), hi[0] = upd_max(hi[0], p.x);
-            lo[1] = upd_min(lo[1], p.y), hi[1] = upd_max(hi[1], p.y);
-            lo[2] = upd_min(lo[2], p.z), hi[2] = upd_max(hi[2], p.z);
+            const double4_32a p = T.sp[i];
+            box.add(p.x, p.y, p.z);
         }
 #pragma unroll
         for (int d = 0; d < 3; d++) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                lo[d] = upd_min(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-                hi[d] = upd_max(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+                const unsigned long long a = __shfl_xor_sync(0xffffffffu, box.lo[d], o);
+                const unsigned long long b = __shfl_xor_sync(0xffffffffu, box.hi[d], o);
+                box.lo[d] = a < box.lo[d] ? a : box.lo[d];
+                box.hi[d] = b > box.hi[d] ? b : box.hi[d];
             }
         }
         if (lane == 0) {
+            double lo[3], hi[3];
+            box.get(lo, hi);
             T.grp[g].y = end - first;
             T.glo[g] = make_double4_32a(lo[0], lo[1], lo[2], 0.0);
             T.ghi[g] = make_double4_32a(hi[0], hi[1], hi[2], 0.0);
