@@ -97,13 +97,13 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         // at 1e30 so that no FP32 test counts it (its rare FP64 path checks si < 0)
         float px[TPL], py[TPL], pz[TPL];
         int si[TPL], cnt[TPL], me[TPL];
-        long long base[TPL];
+        int32_t *wp[TPL];  // fill: next entry of the target's row
         float A = 0.f;
 #pragma unroll
         for (int t = 0; t < TPL; t++) {
             int s = gr.x + lane + 32 * t;
             cnt[t] = 0;
-            base[t] = 0;
+            wp[t] = P.idx;
             if (s < gr.x + gr.y) {
                 const float4 h = T.ph[s], l = T.pl[s];
                 px[t] = (h.x - fhx) + (l.x - flx);
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 si[t] = s;
                 A = fmaxf(A, fmaxf(fabsf(px[t]), fmaxf(fabsf(py[t]), fabsf(pz[t]))));
                 me[t] = T.perm[s];
-                if (FILL) base[t] = P.offs[me[t]];
+                if (FILL) wp[t] = P.idx + P.offs[me[t]];
             } else {
                 px[t] = py[t] = pz[t] = 1e30f;
                 si[t] = -1;
@@ -174,10 +174,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                     }
                 }
                 if (FILL) {
-                    if (in0) P.idx[base[t] + cnt[t]] = o0;
-                    cnt[t] += in0;
-                    if (in1) P.idx[base[t] + cnt[t]] = o1;
-                    cnt[t] += in1;
+                    if (in0) *wp[t] = o0;
+                    wp[t] += in0;
+                    if (in1) *wp[t] = o1;
+                    wp[t] += in1;
                 } else {
                     cnt[t] += (int)in0 + (int)in1;
                 }
