@@ -309,9 +309,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 // rows of other classes and only one class's code is resident in the
 // instruction cache:
 //   (1, 512]      bitonic network in registers, K = 1, 2, 4, 8, 16 entries per
-//                 lane (element e = 32 r + lane in register r; partners 32 apart
-//                 or more are in the same lane, closer ones are exchanged by
-//                 shuffles)
+//                 lane: up to 128 in the strided layout (element e = 32 r + lane
+//                 in register r; partners 32 apart or more are in the same lane,
+//                 closer ones are exchanged by shuffles), above in the transposed
+//                 layout (warp_bitonic_row_t)
 //   (512, 2048]   loop-based bitonic network (below) in shared memory
 //   > 2048        the same network in global memory.
 // The loop network puts the smaller value at the lower index in every
@@ -325,6 +326,9 @@ constexpr int kRowClasses = 8;
 __constant__ int kClassLenDev[kRowClasses + 1] = {1, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
 constexpr int kClassLen[kRowClasses + 1] = {1, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
 constexpr int kSortWarps = 4;
+// bit c set: class c uses the transposed register network (faster for
+// (128, 512], slower for (64, 128] on the 10^6-particle Plummer rows)
+constexpr unsigned kTransposed = (1u << 3) | (1u << 4);
 
 __device__ __forceinline__ int row_class(int len)
 {
@@ -444,6 +448,69 @@ __device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len)
     }
 }
 
+// The same network in the transposed layout: lane holds the K consecutive
+// elements e = K lane + r, so the stages with partners less than K apart are
+// compare-exchanges between registers and only the wider ones need shuffles.
+// Descending blocks are handled by complementing their values (~v reverses the
+// order of int32), so that every compare-exchange is ascending; the complement
+// pattern changes once per merge level.  The row passes through shared memory
+// (sb: 32 K + K words, index e + e / 32 keeps both access patterns free of bank
+// conflicts) so that the global loads and stores stay coalesced.
+template <int K>
+__device__ __forceinline__ void warp_bitonic_row_t(int32_t *row, int len, int32_t *sb)
+{
+    constexpr int N = 32 * K;
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < N; e += 32) sb[e + (e >> 5)] = e < len ? row[e] : INT_MAX;
+    __syncwarp();
+    int v[K];
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        const int e = K * lane + r;
+        v[r] = sb[e + (e >> 5)] ^ ((e & 2) ? -1 : 0);
+    }
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+        if (k > 2) {
+#pragma unroll
+            for (int r = 0; r < K; r++) {
+                const int e = K * lane + r;
+                v[r] ^= ((e & k) ? -1 : 0) ^ ((e & (k >> 1)) ? -1 : 0);
+            }
+        }
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j < K) {
+#pragma unroll
+                for (int r = 0; r < K; r++) {
+                    const int r2 = r ^ j;
+                    if (r2 > r) {
+                        const int a = v[r], b = v[r2];
+                        v[r] = min(a, b);
+                        v[r2] = max(a, b);
+                    }
+                }
+            } else {
+                const int lj = j / K;
+                const bool lower = (lane & lj) == 0;
+#pragma unroll
+                for (int r = 0; r < K; r++) {
+                    const int p = __shfl_xor_sync(0xffffffffu, v[r], lj);
+                    v[r] = lower ? min(v[r], p) : max(v[r], p);
+                }
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        const int e = K * lane + r;
+        sb[e + (e >> 5)] = v[r];  // level N has no descending block: v is the value
+    }
+    __syncwarp();
+    for (int e = lane; e < len; e += 32) row[e] = sb[e + (e >> 5)];
+}
+
 // ascending compare-exchange of a[i] and a[h] (i < h), skipped past the end
 __device__ __forceinline__ void cmpx(int32_t *a, int i, int h, int len)
 {
@@ -486,6 +553,17 @@ __global__ void __launch_bounds__(kSortWarps * 32)
                         int32_t *idx)
 {
     for_class_rows<C>(meta, list, offs, idx, [](int32_t *row, int len) { warp_bitonic_row<K>(row, len); });
+}
+
+template <int C, int K>
+__global__ void __launch_bounds__(kSortWarps * 32)
+    row_sort_tr_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
+                       int32_t *idx)
+{
+    __shared__ int32_t sbuf[kSortWarps][33 * K];
+    int32_t *sb = sbuf[threadIdx.x >> 5];
+    for_class_rows<C>(meta, list, offs, idx,
+                      [&](int32_t *row, int len) { warp_bitonic_row_t<K>(row, len, sb); });
 }
 
 // rows of class C sorted by the loop network in shared memory
@@ -540,10 +618,22 @@ static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long
     if (e) return e;
     if ((e = launch_sort(c, row_sort_reg_kernel<0, 1>, offsets, idx))) return e;
     if ((e = launch_sort(c, row_sort_reg_kernel<1, 2>, offsets, idx))) return e;
-    if ((e = launch_sort(c, row_sort_reg_kernel<2, 4>, offsets, idx))) return e;
+    if (kTransposed & (1u << 2))
+        e = launch_sort(c, row_sort_tr_kernel<2, 4>, offsets, idx);
+    else
+        e = launch_sort(c, row_sort_reg_kernel<2, 4>, offsets, idx);
+    if (e) return e;
     if (n > kClassLen[3] + 1) {  // longer rows need more than 128 distinct indices
-        if ((e = launch_sort(c, row_sort_reg_kernel<3, 8>, offsets, idx))) return e;
-        if ((e = launch_sort(c, row_sort_reg_kernel<4, 16>, offsets, idx))) return e;
+        if (kTransposed & (1u << 3))
+            e = launch_sort(c, row_sort_tr_kernel<3, 8>, offsets, idx);
+        else
+            e = launch_sort(c, row_sort_reg_kernel<3, 8>, offsets, idx);
+        if (e) return e;
+        if (kTransposed & (1u << 4))
+            e = launch_sort(c, row_sort_tr_kernel<4, 16>, offsets, idx);
+        else
+            e = launch_sort(c, row_sort_reg_kernel<4, 16>, offsets, idx);
+        if (e) return e;
         if ((e = launch_sort(c, row_sort_smem_kernel<5>, offsets, idx))) return e;
         if ((e = launch_sort(c, row_sort_global_kernel<6>, offsets, idx))) return e;
     }
