@@ -218,6 +218,7 @@ int p3t_destroy(p3t_ctx *c)
         cudaStreamDestroy(c->copy_stream);
     }
     if (c->lists_ready) cudaEventDestroy(c->lists_ready);
+    if (c->v_ready) cudaEventDestroy(c->v_ready);
     if (c->clusters) cudaFree(c->clusters);
     if (c->irr_buf) cudaFree(c->irr_buf);
     if (c->knn_buf) cudaFree(c->knn_buf);

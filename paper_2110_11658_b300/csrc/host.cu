@@ -1,8 +1,9 @@
 // p3t_step_host: one regular step from and to host memory -- the boundary of
 // the paper's REGF (host arrays in; regular force and neighbour lists out,
 // Sec. 2.4) followed by RKICK (Eq. 12).  Device staging buffers are owned by
-// the context and grow on demand.  The neighbour lists are built before the
-// far force and copied back on a second stream during the walk.
+// the context and grow on demand.  A second stream of the context uploads the
+// velocities during the build and copies the neighbour lists (built before the
+// far force) back during the walk.
 #include <cstring>
 
 #include "p3t_internal.cuh"
@@ -46,43 +47,59 @@ extern "C" int p3t_step_host(p3t_ctx *c, int64_t n, double dt, const double *x, 
     void *dax = take(asz * n), *day = take(asz * n), *daz = take(asz * n);
     int64_t *doffs = (int64_t *)take(8 * (n + 1));
     int32_t *didx = capacity > 0 ? (int32_t *)take(4 * capacity) : nullptr;
-    const double *hin[7] = {x, y, z, m, vx, vy, vz};
-    double *din[7] = {dx, dy, dz, dm, dvx, dvy, dvz};
-    for (int k = 0; k < 7; k++)
-        if (cudaMemcpyAsync(din[k], hin[k], 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess)
-            return P3T_ERR_CUDA;
     if (!c->copy_stream) {
         if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
             c->copy_stream = nullptr;
             return P3T_ERR_CUDA;
         }
-        if (cudaEventCreateWithFlags(&c->lists_ready, cudaEventDisableTiming) != cudaSuccess) {
+        if (cudaEventCreateWithFlags(&c->lists_ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->v_ready, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
-            c->lists_ready = nullptr;
             return P3T_ERR_CUDA;
         }
+    }
+    cudaStream_t cs = c->copy_stream;
+    // positions and masses on the compute stream; the velocities, which only the
+    // kick reads, on the copy stream while the tree is built
+    const double *hin[7] = {x, y, z, m, vx, vy, vz};
+    double *din[7] = {dx, dy, dz, dm, dvx, dvy, dvz};
+    for (int k = 0; k < 7; k++)
+        if (cudaMemcpyAsync(din[k], hin[k], 8 * n, cudaMemcpyHostToDevice, k < 4 ? s : cs) !=
+            cudaSuccess) {
+            cudaStreamSynchronize(cs);
+            return P3T_ERR_CUDA;
+        }
+    if (cudaEventRecord(c->v_ready, cs) != cudaSuccess) {
+        cudaStreamSynchronize(cs);
+        return P3T_ERR_CUDA;
     }
     // neighbour lists first (their count pass replaces the count inside the
     // walk), so that their copy to the host runs on a second stream while the
     // far-force walk computes
     int e = p3t_build_tree(c, n, dx, dy, dz, dm);
-    if (e) return e;
+    if (e) {
+        cudaStreamSynchronize(cs);
+        return e;
+    }
     int ne = p3t_neighbours(c, doffs, didx, capacity, total);
-    if (ne && ne != P3T_ERR_CAPACITY) return ne;
+    if (ne && ne != P3T_ERR_CAPACITY) {
+        cudaStreamSynchronize(cs);
+        return ne;
+    }
     if (cudaEventRecord(c->lists_ready, s) != cudaSuccess ||
-        cudaStreamWaitEvent(c->copy_stream, c->lists_ready, 0) != cudaSuccess ||
-        cudaMemcpyAsync(offsets, doffs, 8 * (n + 1), cudaMemcpyDeviceToHost, c->copy_stream) !=
-            cudaSuccess)
+        cudaStreamWaitEvent(cs, c->lists_ready, 0) != cudaSuccess ||
+        cudaMemcpyAsync(offsets, doffs, 8 * (n + 1), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        (!ne && *total > 0 &&
+         cudaMemcpyAsync(idx, didx, 4 * (size_t)*total, cudaMemcpyDeviceToHost, cs) != cudaSuccess)) {
+        cudaStreamSynchronize(cs);
         return P3T_ERR_CUDA;
-    if (!ne && *total > 0 &&
-        cudaMemcpyAsync(idx, didx, 4 * (size_t)*total, cudaMemcpyDeviceToHost, c->copy_stream) !=
-            cudaSuccess)
-        return P3T_ERR_CUDA;
+    }
     e = p3t_far_force(c, dax, day, daz, nullptr, nullptr, nullptr);
+    if (e == P3T_OK && cudaStreamWaitEvent(s, c->v_ready, 0) != cudaSuccess) e = P3T_ERR_CUDA;
     if (e == P3T_OK) e = p3t_kick(c, dt, dax, day, daz, dvx, dvy, dvz);
     if (e) {
-        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamSynchronize(cs);
         return e;
     }
     void *hout[6] = {ax, ay, az, vx, vy, vz};
@@ -90,10 +107,10 @@ extern "C" int p3t_step_host(p3t_ctx *c, int64_t n, double dt, const double *x, 
     const size_t osz[6] = {asz, asz, asz, 8, 8, 8};
     for (int k = 0; k < 6; k++)
         if (cudaMemcpyAsync(hout[k], dout[k], osz[k] * n, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
-            cudaStreamSynchronize(c->copy_stream);
+            cudaStreamSynchronize(cs);
             return P3T_ERR_CUDA;
         }
-    if (cudaStreamSynchronize(c->copy_stream) != cudaSuccess) return P3T_ERR_CUDA;
+    if (cudaStreamSynchronize(cs) != cudaSuccess) return P3T_ERR_CUDA;
     e = p3t_status(c);
     if (e) return e;
     return ne;

@@ -384,8 +384,9 @@ struct p3t_ctx {
     size_t blob_bytes;
     void *host_stage;                 // device staging of p3t_step_host
     size_t host_stage_bytes;
-    cudaStream_t copy_stream;         // p3t_step_host: neighbour-list copy beside the far force
-    cudaEvent_t lists_ready;
+    cudaStream_t copy_stream;         // p3t_step_host: velocity upload and neighbour-list
+    cudaEvent_t lists_ready;          // copy beside the build and the far force
+    cudaEvent_t v_ready;
     unsigned long long gen;           // bumped whenever blob or clusters move
     void *irr_buf;                    // double-single states of p3t_irregular (mixed)
     size_t irr_bytes;
