@@ -130,7 +130,15 @@ int p3t_far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t
  * offsets: device int64[n + 1], row i is idx[offsets[i] .. offsets[i+1]);
  * idx: device int32[capacity].  *total (host) receives the number of entries.
  * Synchronises the stream once to read the total.  If total > capacity the
- * call returns P3T_ERR_CAPACITY with *total and offsets set and idx untouched. */
+ * call returns P3T_ERR_CAPACITY with *total and offsets set and idx untouched.
+ * Row mode: when this call follows p3t_far_force on the same tree (mixed
+ * precision, group_size <= 32), it also sizes a context-owned scratch of
+ * row_cap int32 entries per particle (row_cap = 8 x the mean row length, in
+ * multiples of 32, in [64, 4096]); the following far-force walks then write
+ * each neighbour they test into it, and the next lists of the same tree only
+ * sort those rows (a row longer than row_cap is rebuilt by a second walk of
+ * its group).  The lists are the same either way; a failed allocation of the
+ * scratch leaves row mode off. */
 int p3t_neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *total);
 
 /* As p3t_neighbours without the synchronisation: *total_dev is a device
@@ -258,6 +266,13 @@ int p3t_core_quantities(p3t_ctx *c, int64_t n, const double *x, const double *y,
  * host int64.  A diagnostic of the filters' efficiency: the results do not
  * depend on it.  Synchronises the context's stream. */
 int p3t_filter_fallbacks(p3t_ctx *c, int64_t *count);
+
+/* Row mode of the neighbour lists (see p3t_neighbours), host values, no
+ * synchronisation: *row_cap = entries per row the next far-force walks write
+ * (0: row mode off); *rows_valid = 1 if the last walk on the current tree
+ * wrote its rows, so that the next lists only sort them.  Either pointer may
+ * be NULL. */
+int p3t_row_mode(p3t_ctx *c, int32_t *row_cap, int32_t *rows_valid);
 
 /* 1: record per-group counts in the walk (slightly slower); 0: off (default). */
 int p3t_set_debug(p3t_ctx *c, int on);

@@ -41,7 +41,7 @@ EXPORTED = [
     "p3t_set_debug", "p3t_error_string", "p3t_morton_order_noalloc",
     "p3t_graph_capture", "p3t_graph_launch", "p3t_graph_destroy", "p3t_reserve", "p3t_scratch_bytes",
     "p3t_batch_move", "p3t_batch_scatter_neighbours", "p3t_filter_fallbacks", "p3t_irregular",
-    "p3t_sample_knn6", "p3t_core_quantities",
+    "p3t_sample_knn6", "p3t_core_quantities", "p3t_row_mode",
 ]
 P3T_NOALLOC_MAX_N = 65536
 
@@ -106,6 +106,7 @@ _sig = {
     "p3t_graph_destroy": [_vp],
     "p3t_reserve": [_vp, _i64, C.c_int32],
     "p3t_filter_fallbacks": [_vp, C.POINTER(_i64)],
+    "p3t_row_mode": [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "p3t_irregular": [_vp, _i64] + [_vp] * 15,
     "p3t_sample_knn6": [_vp, _i64, _i64, _vp, _vp, _vp],
     "p3t_core_quantities": [_vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp],
@@ -408,6 +409,12 @@ class Context:
         v = C.c_int64(0)
         _check(_lib.p3t_filter_fallbacks(self._h, C.byref(v)), "p3t_filter_fallbacks")
         return v.value
+
+    def row_mode(self):
+        """(row_cap, rows_valid) of the neighbour lists' row mode (host values)."""
+        cap, valid = C.c_int32(0), C.c_int32(0)
+        _check(_lib.p3t_row_mode(self._h, C.byref(cap), C.byref(valid)), "p3t_row_mode")
+        return cap.value, valid.value
 
     def group_counts(self):
         t = self._torch

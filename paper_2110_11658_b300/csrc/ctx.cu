@@ -213,6 +213,7 @@ int p3t_destroy(p3t_ctx *c)
     cudaStreamSynchronize(c->stream);
     if (c->blob) cudaFree(c->blob);
     if (c->host_stage) cudaFree(c->host_stage);
+    if (c->row_scratch) cudaFree(c->row_scratch);
     if (c->copy_stream) {
         cudaStreamSynchronize(c->copy_stream);
         cudaStreamDestroy(c->copy_stream);
@@ -267,6 +268,7 @@ static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *se
     c->built = 0;
     c->counts_valid = 0;
     c->walk_counted = 0;
+    c->rows_valid = 0;
     c->uniform_params = cprm == nullptr;
     e = build_tree(c, (int)n, n_clusters, seg, cprm, x, y, z, m);
     if (e) return e;
@@ -408,6 +410,14 @@ int p3t_irregular(p3t_ctx *c, int64_t n, const int64_t *offsets, const int32_t *
         return P3T_ERR_INVALID_ARG;
     if (!c->built || !c->meta || c->n != n) return P3T_ERR_ORDER;  // a tree of these n particles
     return irregular(c, (int)n, offsets, idx, x, y, z, m, vx, vy, vz, fx, fy, fz, jx, jy, jz);
+}
+
+int p3t_row_mode(p3t_ctx *c, int32_t *row_cap, int32_t *rows_valid)
+{
+    if (!c) return P3T_ERR_INVALID_ARG;
+    if (row_cap) *row_cap = c->row_cap;
+    if (rows_valid) *rows_valid = c->rows_valid;
+    return P3T_OK;
 }
 
 int p3t_filter_fallbacks(p3t_ctx *c, int64_t *count)

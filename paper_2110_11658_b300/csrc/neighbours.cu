@@ -36,6 +36,7 @@ struct NbrArgs {
     long long capacity;
     int skip_counted;      // count pass: skip clusters whose neighbours the walk counted
     unsigned int *ticket;
+    int row_cap;           // fill pass in row mode: only groups with a row longer than this
 };
 
 struct NbrSmem {
@@ -118,6 +119,12 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 si[t] = -1;
                 me[t] = -1;
             }
+        }
+        if (FILL && P.row_cap > 0) {  // row mode: the walk wrote every row of at most row_cap
+            bool longer = false;
+#pragma unroll
+            for (int t = 0; t < TPL; t++) longer |= si[t] >= 0 && P.count[me[t]] > P.row_cap;
+            if (!__any_sync(0xffffffffu, longer)) continue;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) A = fmaxf(A, __shfl_xor_sync(0xffffffffu, A, o));
@@ -323,8 +330,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 // class of the 10^6-particle Plummer workload.)
 constexpr int kRowClasses = 8;
 // class c holds the rows with kClassLen[c] < len <= kClassLen[c + 1]
-__constant__ int kClassLenDev[kRowClasses + 1] = {1, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
-constexpr int kClassLen[kRowClasses + 1] = {1, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
+__constant__ int kClassLenDev[kRowClasses + 1] = {0, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
+constexpr int kClassLen[kRowClasses + 1] = {0, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
 constexpr int kSortWarps = 4;
 // bit c set: class c uses the transposed register network (faster for
 // (128, 512], slower for (64, 128] on the 10^6-particle Plummer rows)
@@ -335,7 +342,7 @@ __device__ __forceinline__ int row_class(int len)
     int c = 0;
 #pragma unroll
     for (int k = 1; k < kRowClasses; k++) c += len > kClassLenDev[k];
-    return len > 1 ? c : -1;
+    return len > 0 ? c : -1;
 }
 
 // counts of the classes -> Meta.row_class[0 .. 7]
@@ -385,10 +392,30 @@ __global__ void row_class_fill_kernel(int n, const int64_t *__restrict__ offs, l
     }
 }
 
-// The rows of class C, one warp each: f(row pointer, length).
+// Where the entries of row i come from: the row itself in idx (filled by the
+// fill pass), or, in row mode, the far-force walk's scratch row of the target
+// (cap entries per particle in key order, holding key-order source positions)
+// when the row has at most cap entries.
+struct RowSrc {
+    const int32_t *rows;  // null: every row is in idx
+    const int32_t *inv;   // original -> key order
+    const int32_t *perm;  // key order -> original
+    int cap;
+};
+
+// Entry e of one row as an original index.
+struct RowLoad {
+    const int32_t *sr;  // scratch row, or null
+    const int32_t *perm;
+    const int32_t *row;
+    __device__ __forceinline__ int operator()(int e) const { return sr ? perm[sr[e]] : row[e]; }
+};
+
+// The rows of class C, one warp each: f(row pointer in idx, length, loader).
 template <int C, typename F>
 __device__ __forceinline__ void for_class_rows(const Meta *meta, const int32_t *list,
-                                               const int64_t *offs, int32_t *idx, F &&f)
+                                               const int64_t *offs, int32_t *idx, RowSrc src,
+                                               F &&f)
 {
     int start = 0;
 #pragma unroll
@@ -398,20 +425,25 @@ __device__ __forceinline__ void for_class_rows(const Meta *meta, const int32_t *
          k += (gridDim.x * blockDim.x) >> 5) {
         const int i = list[start + k];
         const long long o = offs[i];
-        f(idx + o, (int)(offs[i + 1] - o));
+        const int len = (int)(offs[i + 1] - o);
+        RowLoad ld;
+        ld.sr = src.rows && len <= src.cap ? src.rows + (size_t)src.inv[i] * src.cap : nullptr;
+        ld.perm = src.perm;
+        ld.row = idx + o;
+        f(idx + o, len, ld);
         __syncwarp();
     }
 }
 
 template <int K>
-__device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len)
+__device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len, const RowLoad &ld)
 {
     const int lane = threadIdx.x & 31;
     int v[K];
 #pragma unroll
     for (int r = 0; r < K; r++) {
         int e = 32 * r + lane;
-        v[r] = e < len ? row[e] : INT_MAX;
+        v[r] = e < len ? ld(e) : INT_MAX;
     }
 #pragma unroll
     for (int k = 2; k <= 32 * K; k <<= 1) {
@@ -457,11 +489,12 @@ __device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len)
 // (sb: 32 K + K words, index e + e / 32 keeps both access patterns free of bank
 // conflicts) so that the global loads and stores stay coalesced.
 template <int K>
-__device__ __forceinline__ void warp_bitonic_row_t(int32_t *row, int len, int32_t *sb)
+__device__ __forceinline__ void warp_bitonic_row_t(int32_t *row, int len, int32_t *sb,
+                                                   const RowLoad &ld)
 {
     constexpr int N = 32 * K;
     const int lane = threadIdx.x & 31;
-    for (int e = lane; e < N; e += 32) sb[e + (e >> 5)] = e < len ? row[e] : INT_MAX;
+    for (int e = lane; e < N; e += 32) sb[e + (e >> 5)] = e < len ? ld(e) : INT_MAX;
     __syncwarp();
     int v[K];
 #pragma unroll
@@ -550,62 +583,76 @@ __device__ void warp_sort_mem(int32_t *a, int len)
 template <int C, int K>
 __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_reg_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
-                        int32_t *idx)
+                        int32_t *idx, RowSrc src)
 {
-    for_class_rows<C>(meta, list, offs, idx, [](int32_t *row, int len) { warp_bitonic_row<K>(row, len); });
+    for_class_rows<C>(meta, list, offs, idx, src, [](int32_t *row, int len, const RowLoad &ld) {
+        warp_bitonic_row<K>(row, len, ld);
+    });
 }
 
 template <int C, int K>
 __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_tr_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
-                       int32_t *idx)
+                       int32_t *idx, RowSrc src)
 {
     __shared__ int32_t sbuf[kSortWarps][33 * K];
     int32_t *sb = sbuf[threadIdx.x >> 5];
-    for_class_rows<C>(meta, list, offs, idx,
-                      [&](int32_t *row, int len) { warp_bitonic_row_t<K>(row, len, sb); });
+    for_class_rows<C>(meta, list, offs, idx, src, [&](int32_t *row, int len, const RowLoad &ld) {
+        warp_bitonic_row_t<K>(row, len, sb, ld);
+    });
 }
 
 // rows of class C sorted by the loop network in shared memory
 template <int C>
 __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_smem_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
-                         int32_t *idx)
+                         int32_t *idx, RowSrc src)
 {
     __shared__ int32_t sbuf[kSortWarps][kClassLen[C + 1]];
     const int lane = threadIdx.x & 31;
     int32_t *sb = sbuf[threadIdx.x >> 5];
-    for_class_rows<C>(meta, list, offs, idx, [&](int32_t *row, int len) {
-        for (int e = lane; e < len; e += 32) sb[e] = row[e];
+    for_class_rows<C>(meta, list, offs, idx, src, [&](int32_t *row, int len, const RowLoad &ld) {
+        for (int e = lane; e < len; e += 32) sb[e] = ld(e);
         __syncwarp();
         warp_sort_mem(sb, len);
         for (int e = lane; e < len; e += 32) row[e] = sb[e];
     });
 }
 
-// rows of class C sorted by the loop network in global memory
+// rows of class C sorted by the loop network in global memory (a scratch row is
+// first copied into place)
 template <int C>
 __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_global_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
-                           int32_t *idx)
+                           int32_t *idx, RowSrc src)
 {
-    for_class_rows<C>(meta, list, offs, idx, [](int32_t *row, int len) { warp_sort_mem(row, len); });
+    const int lane = threadIdx.x & 31;
+    for_class_rows<C>(meta, list, offs, idx, src, [&](int32_t *row, int len, const RowLoad &ld) {
+        if (ld.sr) {
+            for (int e = lane; e < len; e += 32) row[e] = ld(e);
+            __syncwarp();
+        }
+        warp_sort_mem(row, len);
+    });
 }
 
 template <typename Kern>
-static int launch_sort(p3t_ctx *c, Kern kern, const int64_t *offsets, int32_t *idx)
+static int launch_sort(p3t_ctx *c, Kern kern, const int64_t *offsets, int32_t *idx, RowSrc src)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSortWarps * 32, 0) !=
             cudaSuccess ||
         per_sm < 1)
         return P3T_ERR_CUDA;
-    kern<<<per_sm * c->sm_count, kSortWarps * 32, 0, c->stream>>>(c->meta, c->row_list, offsets, idx);
+    kern<<<per_sm * c->sm_count, kSortWarps * 32, 0, c->stream>>>(c->meta, c->row_list, offsets, idx,
+                                                                 src);
     return check_launch(c);
 }
 
-// Sorts every row of the filled lists (offsets[n] <= capacity; otherwise nothing).
-static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long capacity)
+// Sorts every row of the filled lists (offsets[n] <= capacity; otherwise nothing),
+// reading rows of at most src.cap entries from the walk's scratch in row mode.
+static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long capacity,
+                     RowSrc src)
 {
     cudaStream_t s = c->stream;
     const int n = c->n;
@@ -616,26 +663,26 @@ static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long
     row_class_fill_kernel<<<grid, 256, 0, s>>>(n, offsets, capacity, c->meta, c->row_list);
     int e = check_launch(c);
     if (e) return e;
-    if ((e = launch_sort(c, row_sort_reg_kernel<0, 1>, offsets, idx))) return e;
-    if ((e = launch_sort(c, row_sort_reg_kernel<1, 2>, offsets, idx))) return e;
+    if ((e = launch_sort(c, row_sort_reg_kernel<0, 1>, offsets, idx, src))) return e;
+    if ((e = launch_sort(c, row_sort_reg_kernel<1, 2>, offsets, idx, src))) return e;
     if (kTransposed & (1u << 2))
-        e = launch_sort(c, row_sort_tr_kernel<2, 4>, offsets, idx);
+        e = launch_sort(c, row_sort_tr_kernel<2, 4>, offsets, idx, src);
     else
-        e = launch_sort(c, row_sort_reg_kernel<2, 4>, offsets, idx);
+        e = launch_sort(c, row_sort_reg_kernel<2, 4>, offsets, idx, src);
     if (e) return e;
     if (n > kClassLen[3] + 1) {  // longer rows need more than 128 distinct indices
         if (kTransposed & (1u << 3))
-            e = launch_sort(c, row_sort_tr_kernel<3, 8>, offsets, idx);
+            e = launch_sort(c, row_sort_tr_kernel<3, 8>, offsets, idx, src);
         else
-            e = launch_sort(c, row_sort_reg_kernel<3, 8>, offsets, idx);
+            e = launch_sort(c, row_sort_reg_kernel<3, 8>, offsets, idx, src);
         if (e) return e;
         if (kTransposed & (1u << 4))
-            e = launch_sort(c, row_sort_tr_kernel<4, 16>, offsets, idx);
+            e = launch_sort(c, row_sort_tr_kernel<4, 16>, offsets, idx, src);
         else
-            e = launch_sort(c, row_sort_reg_kernel<4, 16>, offsets, idx);
+            e = launch_sort(c, row_sort_reg_kernel<4, 16>, offsets, idx, src);
         if (e) return e;
-        if ((e = launch_sort(c, row_sort_smem_kernel<5>, offsets, idx))) return e;
-        if ((e = launch_sort(c, row_sort_global_kernel<6>, offsets, idx))) return e;
+        if ((e = launch_sort(c, row_sort_smem_kernel<5>, offsets, idx, src))) return e;
+        if ((e = launch_sort(c, row_sort_global_kernel<6>, offsets, idx, src))) return e;
     }
     return P3T_OK;
 }
@@ -663,6 +710,40 @@ static int dispatch_nbr(p3t_ctx *c, const NbrArgs &a)
     return launch_nbr<4, FILL>(c, a);
 }
 
+// Row mode (the far-force walk writes each neighbour it counts into a scratch row
+// of row_cap entries per particle, so that the lists need no second walk) pays off
+// when the walk runs before the lists.  The synchronous lists size the scratch for
+// the following walks: row_cap = 8 x the mean row length in multiples of 32, in
+// [64, 4096]; a row longer than that is filled by the fill pass for its group.  A
+// failed allocation leaves row mode off.  Reallocating drops the rows of the
+// current tree (rows_valid), which the fill pass then rebuilds.
+static void size_row_scratch(p3t_ctx *c, long long total)
+{
+    if (!c->walk_counted || c->built_precision != P3T_FP32_MIXED || c->prm.group_size > 32 ||
+        c->n <= 0)
+        return;
+    const long long mean = (total + c->n - 1) / c->n;
+    const long long cap = std::max(64LL, std::min(4096LL, (8 * mean + 31) / 32 * 32));
+    const size_t need = (size_t)c->cap_n * (size_t)cap;
+    if (need > c->row_scratch_entries) {
+        cudaStreamSynchronize(c->stream);
+        if (c->row_scratch) cudaFree(c->row_scratch);
+        c->row_scratch = nullptr;
+        c->row_scratch_entries = 0;
+        c->rows_valid = 0;
+        c->row_cap = 0;
+        c->gen++;  // graphs captured with the old scratch refuse to launch
+        void *p = nullptr;
+        if (cudaMalloc(&p, need * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        c->row_scratch = (int32_t *)p;
+        c->row_scratch_entries = need;
+    }
+    c->row_cap = (int)cap;
+}
+
 int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, int64_t *total_dev,
                bool sync, int64_t *total_host)
 {
@@ -675,6 +756,7 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
     a.idx = idx;
     a.capacity = capacity;
     a.ticket = &c->meta->tickets[23];
+    a.row_cap = 0;
     int e;
     a.skip_counted = c->walk_counted;
     if (!c->counts_valid) {  // the far-force walk did not count every cluster
@@ -692,6 +774,7 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
             cudaStreamSynchronize(s) != cudaSuccess)
             return P3T_ERR_CUDA;
         *total_host = tot;
+        size_row_scratch(c, tot);
         int err = 0;
         if (cudaMemcpy(&err, &c->meta->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
             return P3T_ERR_CUDA;
@@ -707,9 +790,14 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
             return P3T_ERR_CUDA;
     }
     if (capacity == 0) return P3T_OK;
+    RowSrc src{nullptr, nullptr, nullptr, 0};
+    if (c->rows_valid) {  // the walk wrote the rows: fill only groups with a longer row
+        a.row_cap = c->rows_cap_used;
+        src = RowSrc{c->row_scratch, c->tree.inv, c->tree.perm, c->rows_cap_used};
+    }
     e = dispatch_nbr<true>(c, a);
     if (e) return e;
-    return sort_rows(c, offsets, idx, capacity);
+    return sort_rows(c, offsets, idx, capacity, src);
 }
 
 }  // namespace p3t

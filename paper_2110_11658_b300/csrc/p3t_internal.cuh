@@ -365,6 +365,7 @@ struct p3t_ctx {
     int built;
     int built_precision;
     int counts_valid;  // neighbour counts of the current tree already in nbr_count
+    int rows_valid;    // the walk wrote the rows of the current tree into row_scratch
     int walk_counted;  // the far-force walk counted the neighbours of clusters with `counted`
     int uniform_params;  // every cluster uses the context's parameters
     int cap_clusters;
@@ -379,6 +380,10 @@ struct p3t_ctx {
     unsigned long long *scan_status;  // look-back status words
     int32_t *nbr_count;               // per particle (original order)
     int32_t *row_list;                // neighbour rows binned by length class
+    int32_t *row_scratch;             // row mode: neighbour rows written by the far-force walk
+    size_t row_scratch_entries;       // (row_cap entries per particle, key order)
+    int row_cap;                      // entries per row for the next walks (0: row mode off)
+    int rows_cap_used;                // entries per row of the rows in the scratch
     int64_t *grp_cells, *grp_parts;   // per group debug counts
     void *blob;                       // single allocation backing everything above
     size_t blob_bytes;
@@ -399,18 +404,21 @@ namespace p3t {
 // graph restores the state of its captured step when it is launched.
 struct HostState {
     int n, built, built_precision, counts_valid, walk_counted, uniform_params;
+    int rows_valid, rows_cap_used;
     Tree tree;
 };
 inline HostState save_state(const p3t_ctx *c)
 {
-    return HostState{c->n, c->built, c->built_precision, c->counts_valid, c->walk_counted,
-                     c->uniform_params, c->tree};
+    return HostState{c->n,           c->built,          c->built_precision,
+                     c->counts_valid, c->walk_counted,  c->uniform_params,
+                     c->rows_valid,  c->rows_cap_used, c->tree};
 }
 inline void restore_state(p3t_ctx *c, const HostState &h)
 {
     c->n = h.n, c->built = h.built, c->built_precision = h.built_precision;
     c->counts_valid = h.counts_valid, c->walk_counted = h.walk_counted;
     c->uniform_params = h.uniform_params, c->tree = h.tree;
+    c->rows_valid = h.rows_valid, c->rows_cap_used = h.rows_cap_used;
 }
 }  // namespace p3t
 

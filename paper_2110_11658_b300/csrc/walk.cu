@@ -67,6 +67,8 @@ struct WalkArgs {
     long long *grp_cells, *grp_parts;
     unsigned int *ticket;
     int32_t *nbr_count;          // fused neighbour count (original order) or null
+    int32_t *rows;               // row mode: rows of row_cap entries per target (key order)
+    int row_cap;
 };
 
 template <typename Real>
@@ -326,6 +328,13 @@ template <int TPL>
 struct NbrCount {
     int si[TPL];   // target positions in key order (-1: empty slot)
     int cnt[TPL];
+    // row mode: the target's row of `cap` entries in the row scratch (key-order
+    // source positions, the target itself left out; entries past cap are dropped
+    // while cnt keeps counting)
+    int32_t *row[TPL];
+    int wc[TPL];
+    unsigned hit[TPL];  // neighbours among the 32 staged sources (bit = staging slot)
+    int cap;
     float lo, hi;  // r2 < lo: neighbour; r2 > hi: not; otherwise decide in FP64
     // |r2 - mid| <= rad covers [lo, hi] (the rare undecided band) with a 2x margin,
     // so rounding of mid and of r2 - mid cannot leave a band pair out
@@ -343,7 +352,7 @@ struct NbrCount {
     }
 };
 
-template <typename Real, int TPL, bool POT, bool NBR>
+template <typename Real, int TPL, bool POT, int NBR>
 __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkArgs &P,
                                            const Cluster &K, int nleaves, int nparts,
                                            const GroupFrame &F, const Real (&px)[TPL],
@@ -505,7 +514,7 @@ __device__ __forceinline__ void eval_cells_x2(const WarpSmem<float> &W, int ncel
 }
 
 // One pair of staged particles (k: pair index) against this lane's targets.
-template <int TPL, bool POT, bool NBR, bool TAIL>
+template <int TPL, bool POT, int NBR, bool TAIL>
 __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &T, const Cluster &K,
                                           const float4 *pq, int k, int ns, float inv_dr, float nrin_dr,
                                           const float2 (&NPX)[TPL], const float2 (&NPY)[TPL],
@@ -545,7 +554,7 @@ __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &
             // counts at once, inside it (rare) is decided with the FP64 operations; the
             // pair with itself is counted (r2 = 0) and removed at the end
             const bool yreal = !TAIL || 2 * k + 1 < ns;
-            NC.cnt[t] += (r2.x < NC.lo) + (yreal && r2.y < NC.lo);
+            bool in0 = r2.x < NC.lo, in1 = yreal && r2.y < NC.lo;
             const float2 d = fadd2(r2, f2(-NC.mid));
             if (fminf(fabsf(d.x), fabsf(d.y)) <= NC.rad) {
 #pragma unroll
@@ -555,16 +564,24 @@ __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &
                         const int sj = W.pj[2 * k + e];
                         const double4_32a a = T.sp[NC.si[t] < 0 ? sj : NC.si[t]], b = T.sp[sj];
                         const double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
-                        NC.cnt[t] += dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < K.rl2_d;
+                        const bool in = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < K.rl2_d;
+                        if (e)
+                            in1 = in;
+                        else
+                            in0 = in;
                     }
                 }
             }
+            if constexpr (NBR == 2)  // rows written once per staged chunk (write_rows)
+                NC.hit[t] |= ((unsigned)in0 | ((unsigned)in1 << 1)) << (2 * k);
+            else
+                NC.cnt[t] += (int)in0 + (int)in1;
         }
     }
 }
 
 // Mixed form, two staged particles at a time; same terms as eval_parts.
-template <int TPL, bool POT, bool NBR>
+template <int TPL, bool POT, int NBR>
 __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const WalkArgs &P,
                                               const Cluster &K, int nleaves, int nparts,
                                               const GroupFrame &F, const float (&px)[TPL],
@@ -619,6 +636,25 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
             part_pair<TPL, POT, NBR, false>(W, P.T, K, pq, k, ns, inv_dr, nrin_dr, NPX, NPY, NPZ, A, NC);
         if (ns & 1)  // the last pair holds the zero-mass pad
             part_pair<TPL, POT, NBR, true>(W, P.T, K, pq, nfull, ns, inv_dr, nrin_dr, NPX, NPY, NPZ, A, NC);
+        if constexpr (NBR == 2) {
+            // the chunk's neighbours of each target: counted (the target itself
+            // included, removed at the end) and appended to its row but for itself;
+            // entries past the row's capacity are dropped
+#pragma unroll
+            for (int t = 0; t < TPL; t++) {
+                unsigned h = NC.hit[t];
+                NC.hit[t] = 0u;
+                NC.cnt[t] += __popc(h);
+                while (h) {
+                    const int j = W.pj[__ffs(h) - 1];
+                    h &= h - 1u;
+                    if (j != NC.si[t]) {
+                        if (NC.wc[t] < NC.cap) NC.row[t][NC.wc[t]] = j;
+                        NC.wc[t]++;
+                    }
+                }
+            }
+        }
         __syncwarp();
     }
     A.fold();
@@ -635,7 +671,7 @@ __device__ __forceinline__ void eval_cells_any(const WarpSmem<Real> &W, int ncel
         eval_cells<Real, TPL, POT, QUAD>(W, ncells, px, py, pz, A);
 }
 
-template <typename Real, int TPL, bool POT, bool NBR, typename AccT>
+template <typename Real, int TPL, bool POT, int NBR, typename AccT>
 __device__ __forceinline__ void eval_parts_any(const WarpSmem<Real> &W, const WalkArgs &P, const Cluster &K,
                                                int nleaves, int nparts, const GroupFrame &F,
                                                const Real (&px)[TPL], const Real (&py)[TPL],
@@ -647,7 +683,7 @@ __device__ __forceinline__ void eval_parts_any(const WarpSmem<Real> &W, const Wa
         eval_parts<Real, TPL, POT, NBR>(W, P, K, nleaves, nparts, F, px, py, pz, A, NC);
 }
 
-template <typename Real, int TPL, bool POT, bool QUAD, bool NBR, bool SHELL>
+template <typename Real, int TPL, bool POT, bool QUAD, int NBR, bool SHELL>
 __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3) walk_kernel(WalkArgs P)
 {
     extern __shared__ __align__(16) char smem[];
@@ -711,6 +747,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
             int s = gr.x + lane + 32 * t;
             NC.cnt[t] = 0;
             NC.si[t] = -1;
+            if constexpr (NBR == 2) {
+                // an empty slot (at c_g) must write nothing: its count starts past any cap
+                NC.hit[t] = 0u;
+                NC.wc[t] = s < gr.x + gr.y ? 0 : (1 << 30);
+                NC.row[t] = P.rows + (size_t)(s < gr.x + gr.y ? s : 0) * P.row_cap;
+            }
             if (s < gr.x + gr.y) {
                 if (kMixed) {
                     float4 r = ds_rel(T.ph[s], T.pl[s], F);
@@ -735,6 +777,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
             const float A = amax * 1.0001f;
             const float band = kU * (24.f * K.rl2_f + 32.f * A * K.rl_f + 128.f * kU * Rf * K.rl_f) +
                                64.f * kU * kU * (A + 2.f * K.rl_f) * (A + 2.f * K.rl_f);
+            NC.cap = P.row_cap;
             if (!count_here)
                 NC.off();  // this cluster is counted elsewhere
             else if (filter_ok)
@@ -979,7 +1022,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
     }
 }
 
-template <typename Real, int TPL, bool POT, bool QUAD, bool NBR, bool SHELL>
+template <typename Real, int TPL, bool POT, bool QUAD, int NBR, bool SHELL>
 static int launch_walk(p3t_ctx *c, const WalkArgs &a)
 {
     auto kern = walk_kernel<Real, TPL, POT, QUAD, NBR, SHELL>;
@@ -996,7 +1039,7 @@ static int launch_walk(p3t_ctx *c, const WalkArgs &a)
     return check_launch(c);
 }
 
-template <typename Real, int TPL, bool NBR, bool SHELL>
+template <typename Real, int TPL, int NBR, bool SHELL>
 static int dispatch_pq(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
 {
     if (pot)
@@ -1006,10 +1049,11 @@ static int dispatch_pq(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
                 : launch_walk<Real, TPL, false, false, NBR, SHELL>(c, a);
 }
 
-template <typename Real, bool NBR, bool SHELL = false>
+template <typename Real, int NBR, bool SHELL = false>
 static int dispatch_tpl(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
 {
     const int G = c->prm.group_size;
+    if constexpr (NBR == 2) return dispatch_pq<Real, 1, 2, SHELL>(c, a, pot, quad);  // G <= 32
     if (G <= 32) return dispatch_pq<Real, 1, NBR, SHELL>(c, a, pot, quad);
     if (G <= 64) return dispatch_pq<Real, 2, NBR, SHELL>(c, a, pot, quad);
     return dispatch_pq<Real, 4, NBR, SHELL>(c, a, pot, quad);
@@ -1035,6 +1079,12 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     const bool fuse_nbr = !c->counts_valid && c->built_precision == P3T_FP32_MIXED &&
                           (!c->uniform_params || P.r_list > 0.0);
     a.nbr_count = fuse_nbr ? c->nbr_count : nullptr;
+    // row mode: the walk also writes each neighbour it counts into the row scratch,
+    // so that p3t_neighbours only sorts (one warp per group of 32 targets)
+    const bool rows = fuse_nbr && P.group_size <= 32 && c->row_cap > 0 &&
+                      c->row_scratch_entries >= (size_t)c->n * (size_t)c->row_cap;
+    a.rows = rows ? c->row_scratch : nullptr;
+    a.row_cap = rows ? c->row_cap : 0;
     if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
         return P3T_ERR_CUDA;
     const bool quad = P.quadrupole != 0;
@@ -1044,15 +1094,19 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     // per-cluster table the host cannot tell, so they are compiled in)
     const bool shell = fuse_nbr && (!c->uniform_params || P.r_list > P.r_out);
     if (c->built_precision == P3T_FP64)
-        e = dispatch_tpl<double, false>(c, a, want_pot, quad);
+        e = dispatch_tpl<double, 0>(c, a, want_pot, quad);
     else if (shell)
-        e = dispatch_tpl<float, true, true>(c, a, want_pot, quad);
+        e = rows ? dispatch_tpl<float, 2, true>(c, a, want_pot, quad)
+                 : dispatch_tpl<float, 1, true>(c, a, want_pot, quad);
     else if (fuse_nbr)
-        e = dispatch_tpl<float, true>(c, a, want_pot, quad);
+        e = rows ? dispatch_tpl<float, 2>(c, a, want_pot, quad)
+                 : dispatch_tpl<float, 1>(c, a, want_pot, quad);
     else
-        e = dispatch_tpl<float, false>(c, a, want_pot, quad);
+        e = dispatch_tpl<float, 0>(c, a, want_pot, quad);
     if (e == P3T_OK && fuse_nbr) {
         c->walk_counted = 1;
+        c->rows_valid = rows;
+        c->rows_cap_used = a.row_cap;
         c->counts_valid = c->uniform_params;  // every cluster counted
     }
     return e;

@@ -8,11 +8,12 @@ target accuracy of the distant-force path).
 """
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import paper_2110_11658_b300 as p3t
 import synth
-from gpu_helpers import assert_tree_equal, rel_err, run_gpu
+from gpu_helpers import DEV, assert_tree_equal, rel_err, run_gpu, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -186,3 +187,46 @@ def test_long_neighbour_rows_take_every_sort_path():
     for lo, hi in ((1, 32), (32, 64), (64, 128), (128, 256), (256, 512), (512, 2048), (2048, n)):
         assert ((lens > lo) & (lens <= hi)).any(), (lo, hi)
     assert np.array_equal(g["offs"], o2) and np.array_equal(g["idx"], i2)
+
+
+def test_row_mode_lists_and_fallback():
+    # After one synchronous list of a tree that the far-force walk counted, the
+    # following walks also write each neighbour into the context's row scratch and
+    # the lists only sort those rows.  A Plummer sphere with a few neighbours per
+    # particle plus a tight clump whose rows (399) exceed the scratch rows (8 x the
+    # mean row): those rows come from the fill pass instead.  Every step's lists
+    # equal the brute force, and the forces equal those of a context that never
+    # enters row mode, bit for bit.
+    p = synth.plummer(20000, 43)
+    rng = np.random.default_rng(43)
+    q = rng.normal(size=(3, 400)) * 0.002 + 2.0
+    x, y, z = (np.concatenate([a, b]) for a, b in zip((p.x, p.y, p.z), q))
+    n = x.size
+    m = np.full(n, 1.0 / n)
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05)
+    o2, i2 = oracle.neighbours_brute(x, y, z, 0.05)
+    assert np.diff(o2).max() == 399
+    xd, yd, zd, md = to_dev(x), to_dev(y), to_dev(z), to_dev(m)
+    ctx = p3t.Context(prm)
+    a = [torch.empty(n, dtype=torch.float32, device=DEV) for _ in range(3)]
+    offs = torch.empty(n + 1, dtype=torch.int64, device=DEV)
+    idx = torch.empty(2 * len(i2) + 64, dtype=torch.int32, device=DEV)
+    for step in range(3):
+        ctx.build_tree(xd, yd, zd, md)
+        ctx.far_force(*a)
+        cap, valid = ctx.row_mode()
+        if step == 0:
+            assert cap == 0 and valid == 0
+        else:
+            assert 64 <= cap < 399 and valid == 1
+        tot = ctx.neighbours(offs, idx)
+        assert tot == len(i2)
+        assert np.array_equal(offs.cpu().numpy(), o2) and np.array_equal(idx[:tot].cpu().numpy(), i2)
+    ctx2 = p3t.Context(prm)
+    ctx2.build_tree(xd, yd, zd, md)
+    b = [torch.empty(n, dtype=torch.float32, device=DEV) for _ in range(3)]
+    ctx2.far_force(*b)
+    ctx.check()
+    ctx2.check()
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
