@@ -36,13 +36,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# DRAM bytes of one walk_kernel launch per particle, from the ncu capture of the
-# 10^6-particle Plummer walk summarised in profiles/walk_kernel_plummer_kroupa_n1e6.md
-# (73.95 MB read + 11.51 MB written; 65.8 B per particle at N = 2^18, so the figure
-# holds for N = 10^6 only).  Valid only for the kernel sources it was measured on:
-# if they change, the roofline's traffic is reported as null until re-measured.
-WALK_TRAFFIC = {"sources": {"walk.cu": "10b996333d99d67b", "p3t_internal.cuh": "74a3aebf000683be"},
-                "n": 1000000, "bytes": 73951232 + 11510272}
+# DRAM bytes of one walk_kernel launch, from the ncu capture of the 10^6-particle
+# Plummer walk summarised in profiles/walk_kernel_plummer_kroupa_n1e6.md: the walk
+# of the timed step, which also writes the neighbour rows (161.7 MB read + 473.3 MB
+# written; without the rows the counting walk moved 85.5 MB).  Valid only at that N and for the
+# kernel sources it was measured on: otherwise the roofline's traffic is null.
+WALK_TRAFFIC = {"sources": {"walk.cu": "026e769ca6d0e883", "p3t_internal.cuh": "a9a489be7027efda"},
+                "n": 1000000, "bytes": 161744640 + 473291008}
 
 N_DEFAULT = 1_000_000
 THETA = 0.4
@@ -357,6 +357,21 @@ def run_b300(args, rank, local, world):
     st = ctx.status()
     if st != p3t.P3T_OK:
         raise p3t.P3TError(st, "benchmark step")
+    row_cap, rows_valid = ctx.row_mode()
+    # the same walk without neighbour work (the lists built first, so the walk
+    # neither counts nor writes rows): the kernel's force efficiency on its own
+    fo = []
+    for _ in range(6):
+        flush.fill_(1)
+        ctx.build_tree(x, y, z, m)
+        ctx.neighbours_async(offs, idx, tot_dev)
+        f0, f1 = ev(), ev()
+        f0.record(stream)
+        ctx.far_force(*a)
+        f1.record(stream)
+        fo.append((f0, f1))
+    torch.cuda.synchronize(dev)
+    far_only_ms = dist_max(statistics.median(f0.elapsed_time(f1) for f0, f1 in fo[1:]), world, dev)
     ph = {"build": 0.0, "far": 0.0, "nbr": 0.0, "kick_drift": 0.0}
     for e0, e1, e2, e3, e4 in evs:
         ph["build"] += e0.elapsed_time(e1)
@@ -443,12 +458,18 @@ def run_b300(args, rank, local, world):
         "step_ms_p50": statistics.median(per_step),
         "step_ms_p99": per_step[min(len(per_step) - 1, int(round(0.99 * (len(per_step) - 1))))],
         "mean_neighbours": nbr_total / n,
-        "roofline": {"bound": "alu", "kernel": "walk_kernel (p3t_far_force)", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "walk_kernel (p3t_far_force, counting and writing the "
+                                              "neighbour rows)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                      "traffic": walk_traffic(n),
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
                                     % (float(peaks.get("sm_max_mhz", 2032.0)), peak_kind),
                      "flops_per_launch": FLOPS_PER_INTERACTION * inter},
+        "roofline_force_only": {"kernel": "walk_kernel after the lists (no neighbour counting or rows)",
+                                "far_ms": far_only_ms,
+                                "achieved": FLOPS_PER_INTERACTION * inter / (far_only_ms * 1e-3) / 1e12,
+                                "frac": FLOPS_PER_INTERACTION * inter / (far_only_ms * 1e-3) / 1e12 / fp32_peak},
+        "neighbour_rows": {"written_by_walk": bool(rows_valid), "row_cap": row_cap},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * KERNELS_PER_STEP,

@@ -394,21 +394,19 @@ __global__ void row_class_fill_kernel(int n, const int64_t *__restrict__ offs, l
 
 // Where the entries of row i come from: the row itself in idx (filled by the
 // fill pass), or, in row mode, the far-force walk's scratch row of the target
-// (cap entries per particle in key order, holding key-order source positions)
-// when the row has at most cap entries.
+// (cap entries per particle in key order, holding original indices) when the
+// row has at most cap entries.
 struct RowSrc {
     const int32_t *rows;  // null: every row is in idx
     const int32_t *inv;   // original -> key order
-    const int32_t *perm;  // key order -> original
     int cap;
 };
 
-// Entry e of one row as an original index.
+// Entry e of one row.
 struct RowLoad {
     const int32_t *sr;  // scratch row, or null
-    const int32_t *perm;
     const int32_t *row;
-    __device__ __forceinline__ int operator()(int e) const { return sr ? perm[sr[e]] : row[e]; }
+    __device__ __forceinline__ int operator()(int e) const { return sr ? sr[e] : row[e]; }
 };
 
 // The rows of class C, one warp each: f(row pointer in idx, length, loader).
@@ -428,7 +426,6 @@ __device__ __forceinline__ void for_class_rows(const Meta *meta, const int32_t *
         const int len = (int)(offs[i + 1] - o);
         RowLoad ld;
         ld.sr = src.rows && len <= src.cap ? src.rows + (size_t)src.inv[i] * src.cap : nullptr;
-        ld.perm = src.perm;
         ld.row = idx + o;
         f(idx + o, len, ld);
         __syncwarp();
@@ -790,10 +787,10 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
             return P3T_ERR_CUDA;
     }
     if (capacity == 0) return P3T_OK;
-    RowSrc src{nullptr, nullptr, nullptr, 0};
+    RowSrc src{nullptr, nullptr, 0};
     if (c->rows_valid) {  // the walk wrote the rows: fill only groups with a longer row
         a.row_cap = c->rows_cap_used;
-        src = RowSrc{c->row_scratch, c->tree.inv, c->tree.perm, c->rows_cap_used};
+        src = RowSrc{c->row_scratch, c->tree.inv, c->rows_cap_used};
     }
     e = dispatch_nbr<true>(c, a);
     if (e) return e;

@@ -164,6 +164,7 @@ struct WarpSmem {
     int *lqo;  // exclusive prefix of leaf counts
     R4 *pp;    // staged source particles {dx, dy, dz, m}
     int *pj;   // their positions in key order
+    int *po;   // row mode: their original indices
     static __host__ __device__ size_t bytes(int tile)
     {
         size_t cb = tile + 32;
@@ -171,7 +172,7 @@ struct WarpSmem {
         b += cb * (2 * sizeof(R4) + sizeof(R2));
         b += cb * 8 + (cb + 1) * 4;
         b = (b + 31) / 32 * 32;
-        b += 32 * sizeof(R4) + 32 * 4;
+        b += 32 * sizeof(R4) + 2 * 32 * 4;
         return (b + 127) / 128 * 128;
     }
     __device__ void carve(char *base, int tile)
@@ -194,6 +195,8 @@ struct WarpSmem {
         pp = (R4 *)p;
         p += 32 * sizeof(R4);
         pj = (int *)p;
+        p += 32 * 4;
+        po = (int *)p;
     }
 };
 
@@ -328,9 +331,9 @@ template <int TPL>
 struct NbrCount {
     int si[TPL];   // target positions in key order (-1: empty slot)
     int cnt[TPL];
-    // row mode: the target's row of `cap` entries in the row scratch (key-order
-    // source positions, the target itself left out; entries past cap are dropped
-    // while cnt keeps counting)
+    // row mode: the target's row of `cap` entries in the row scratch (original
+    // indices, the target itself left out; entries past cap are dropped while cnt
+    // keeps counting)
     int32_t *row[TPL];
     int wc[TPL];
     unsigned hit[TPL];  // neighbours among the 32 staged sources (bit = staging slot)
@@ -622,6 +625,7 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
             const float4 r = ds_rel(P.T.ph[j], P.T.pl[j], F);
             pb[0] = r.x, pb[2] = r.y, pb[4] = r.z, pb[6] = lx < 0 ? 0.f : r.w;
             if (NBR) W.pj[lane] = j;
+            if (NBR == 2) W.po[lane] = P.T.perm[j];
         }
         __syncwarp();
         if ((ns & 1) && lane == 0) {
@@ -646,10 +650,10 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
                 NC.hit[t] = 0u;
                 NC.cnt[t] += __popc(h);
                 while (h) {
-                    const int j = W.pj[__ffs(h) - 1];
+                    const int b = __ffs(h) - 1;
                     h &= h - 1u;
-                    if (j != NC.si[t]) {
-                        if (NC.wc[t] < NC.cap) NC.row[t][NC.wc[t]] = j;
+                    if (W.pj[b] != NC.si[t]) {
+                        if (NC.wc[t] < NC.cap) NC.row[t][NC.wc[t]] = W.po[b];
                         NC.wc[t]++;
                     }
                 }
