@@ -204,6 +204,9 @@ __device__ __forceinline__ int pop_batch(int *stk, int &sp)
 // The far-force walk's stack entries may carry a flag in bit 31 (ranges visited
 // only for the neighbour count); node indices then stay below 2^28.
 constexpr unsigned kRangeFlag = 0x80000000u;
+// leaf-queue entries: bit 30 marks a leaf whose box lies r_out or more from the
+// group's box (particle indices stay below the node capacity bound 2^28)
+constexpr unsigned kFarLeaf = 0x40000000u;
 __device__ __forceinline__ int pack_range_f(int first, int count, bool flag)
 {
     return (int)(((unsigned)first << 3) | (unsigned)(count - 1) | (flag ? kRangeFlag : 0u));

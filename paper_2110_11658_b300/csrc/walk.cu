@@ -519,7 +519,8 @@ __device__ __forceinline__ void eval_cells_x2(const WarpSmem<float> &W, int ncel
 // One pair of staged particles (k: pair index) against this lane's targets.
 template <int TPL, bool POT, int NBR, bool TAIL>
 __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &T, const Cluster &K,
-                                          const float4 *pq, int k, int ns, float inv_dr, float nrin_dr,
+                                          const float4 *pq, int k, int ns, unsigned cm, float inv_dr,
+                                          float nrin_dr,
                                           const float2 (&NPX)[TPL], const float2 (&NPY)[TPL],
                                           const float2 (&NPZ)[TPL], AccX2<TPL> &A, NbrCount<TPL> &NC)
 {
@@ -552,7 +553,7 @@ __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &
             A.p[t][3].x -= r2.x > 0.f ? Mj.x * ri.x : 0.f;
             A.p[t][3].y -= r2.y > 0.f ? Mj.y * ri.y : 0.f;
         }
-        if (NBR) {
+        if (NBR && ((cm >> (2 * k)) & 3u)) {  // (a pair from leaves beyond r_out holds none)
             // neighbour iff |x_j - x_i|^2 < r_list^2 in FP64: below the band in FP32
             // counts at once, inside it (rare) is decided with the FP64 operations; the
             // pair with itself is counted (r2 = 0) and removed at the end
@@ -611,6 +612,7 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
     for (int c0 = 0; c0 < nparts; c0 += 32) {
         int pos = c0 + lane;
         const int ns = min(32, nparts - c0);
+        bool cand = false;  // may be a neighbour of a target of the group
         if (pos < nparts) {
             int lo = 0, hi = nleaves;  // last leaf with lqo <= pos
             while (hi - lo > 1) {
@@ -620,8 +622,10 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
                 else
                     hi = mid;
             }
-            const int lx = W.lq[lo].x;  // bit 31: neighbour-only leaf (staged with mass 0)
-            const int j = (lx & 0x7fffffff) + (pos - W.lqo[lo]);
+            // bit 31: neighbour-only leaf (staged with mass 0); bit 30: leaf beyond r_out
+            const int lx = W.lq[lo].x;
+            const int j = (lx & 0x3fffffff) + (pos - W.lqo[lo]);
+            cand = (lx & (int)kFarLeaf) == 0;
             const float4 r = ds_rel(P.T.ph[j], P.T.pl[j], F);
             pb[0] = r.x, pb[2] = r.y, pb[4] = r.z, pb[6] = lx < 0 ? 0.f : r.w;
             if (NBR) W.pj[lane] = j;
@@ -634,12 +638,14 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
             b[1] = b[0], b[3] = b[2], b[5] = b[4], b[7] = 0.f;
         }
         __syncwarp();
+        const unsigned cm = __ballot_sync(0xffffffffu, cand);  // slots to test as neighbours
         const int nfull = ns >> 1;
 #pragma unroll kPartPairUnroll
         for (int k = 0; k < nfull; k++)
-            part_pair<TPL, POT, NBR, false>(W, P.T, K, pq, k, ns, inv_dr, nrin_dr, NPX, NPY, NPZ, A, NC);
+            part_pair<TPL, POT, NBR, false>(W, P.T, K, pq, k, ns, cm, inv_dr, nrin_dr, NPX, NPY, NPZ, A, NC);
         if (ns & 1)  // the last pair holds the zero-mass pad
-            part_pair<TPL, POT, NBR, true>(W, P.T, K, pq, nfull, ns, inv_dr, nrin_dr, NPX, NPY, NPZ, A, NC);
+            part_pair<TPL, POT, NBR, true>(W, P.T, K, pq, nfull, ns, cm, inv_dr, nrin_dr, NPX, NPY, NPZ, A,
+                                           NC);
         if constexpr (NBR == 2) {
             // the chunk's neighbours of each target: counted (the target itself
             // included, removed at the end) and appended to its row but for itself;
@@ -813,6 +819,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
 
             // ---- opening test (test and staging data come in one load batch)
             bool open = false, is_leaf = false, in_shell = false;
+            bool beyond = false;  // box certainly r_out or more from the group box: no neighbour
             int cinfo = 0, ccount = 0;
             float4 ra, rd, rq0, rq1;  // node record: COM hi / lo + M / quadrupole
             if (node >= 0) {
@@ -848,6 +855,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                         dec_b = fabsf(db) > fmaf(bb_band.a, e2, bb_band.b);
                         in_b = db < 0.f;
                     }
+                    // (with r_list > r_out a force leaf beyond r_out may still hold neighbours)
+                    beyond = !SHELL && dec_b && !in_b;
                     if (SHELL && nbr_only) {
                         // neighbour-only range: the box test against r_list alone
                         bool dec_l = false, in_l = false;
@@ -973,7 +982,9 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
             const unsigned lm = __ballot_sync(0xffffffffu, open_leaf);
             if (open_leaf)
                 W.lq[lqn + __popc(lm & lt)] =
-                    make_int2((int)((unsigned)(-1 - cinfo) | (go_nbr ? kRangeFlag : 0u)), ccount);
+                    make_int2((int)((unsigned)(-1 - cinfo) | (go_nbr ? kRangeFlag : 0u) |
+                                    (beyond ? kFarLeaf : 0u)),
+                              ccount);
             lqn += __popc(lm);
             const int lc = (int)__reduce_add_sync(0xffffffffu, open_leaf ? (unsigned)ccount : 0u);
             lqp += lc;
