@@ -131,14 +131,14 @@ int p3t_far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t
  * idx: device int32[capacity].  *total (host) receives the number of entries.
  * Synchronises the stream once to read the total.  If total > capacity the
  * call returns P3T_ERR_CAPACITY with *total and offsets set and idx untouched.
- * Row mode: when this call follows p3t_far_force on the same tree (mixed
- * precision, group_size <= 32), it also sizes a context-owned scratch of
- * row_cap int32 entries per particle (row_cap = 8 x the mean row length, in
- * multiples of 32, in [64, 4096]); the following far-force walks then write
- * each neighbour they test into it, and the next lists of the same tree only
- * sort those rows (a row longer than row_cap is rebuilt by a second walk of
- * its group).  The lists are the same either way; a failed allocation of the
- * scratch leaves row mode off. */
+ * Row mode (mixed precision, group_size <= 32): this call also sizes a
+ * context-owned scratch of row_cap int32 entries per particle (row_cap = 8 x
+ * the mean row length, in multiples of 32, in [64, 4096]); for the following
+ * trees the pass that counts the neighbours (the far-force walk, or the lists'
+ * own count pass when they come first) writes each neighbour into it, and the
+ * lists only sort those rows (a row longer than row_cap is rebuilt by a second
+ * walk of its group).  The lists are the same either way; a failed allocation
+ * of the scratch leaves row mode off. */
 int p3t_neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *total);
 
 /* As p3t_neighbours without the synchronisation: *total_dev is a device

@@ -37,6 +37,8 @@ struct NbrArgs {
     int skip_counted;      // count pass: skip clusters whose neighbours the walk counted
     unsigned int *ticket;
     int row_cap;           // fill pass in row mode: only groups with a row longer than this
+    int32_t *rows;         // count pass in row mode: rows of rows_cap entries per target
+    int rows_cap;          // (key order, original indices; see the far-force walk)
 };
 
 struct NbrSmem {
@@ -47,7 +49,7 @@ struct NbrSmem {
     int pj[32];     // their positions in key order
 };
 
-template <int TPL, bool FILL>
+template <int TPL, bool FILL, bool ROWS = false>
 __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 {
     __shared__ NbrSmem sm[kNbrWarps];
@@ -99,12 +101,22 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         float px[TPL], py[TPL], pz[TPL];
         int si[TPL], cnt[TPL], me[TPL];
         int32_t *wp[TPL];  // fill: next entry of the target's row
+        // count pass in row mode: neighbours among the staged chunk (bit = slot), the
+        // target's scratch row and its entries (an empty slot writes nothing)
+        unsigned hit[TPL];
+        int32_t *rrow[TPL];
+        int rwc[TPL];
         float A = 0.f;
 #pragma unroll
         for (int t = 0; t < TPL; t++) {
             int s = gr.x + lane + 32 * t;
             cnt[t] = 0;
             wp[t] = P.idx;
+            if (ROWS) {
+                hit[t] = 0u;
+                rrow[t] = P.rows + (size_t)(s < gr.x + gr.y ? s : 0) * P.rows_cap;
+                rwc[t] = s < gr.x + gr.y ? 0 : (1 << 30);
+            }
             if (s < gr.x + gr.y) {
                 const float4 h = T.ph[s], l = T.pl[s];
                 px[t] = (h.x - fhx) + (l.x - flx);
@@ -185,6 +197,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                     wp[t] += in0;
                     if (in1) *wp[t] = o1;
                     wp[t] += in1;
+                } else if (ROWS) {
+                    hit[t] |= ((unsigned)in0 | ((unsigned)in1 << 1)) << (2 * k);
                 } else {
                     cnt[t] += (int)in0 + (int)in1;
                 }
@@ -294,6 +308,21 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 #pragma unroll 2
                 for (int k = 0; k < nfull; k++) test_pair(k, ns, std::false_type());
                 if (ns & 1) test_pair(nfull, ns, std::true_type());
+                if (ROWS) {  // count the chunk's neighbours and append them to the rows
+                    const int *po = reinterpret_cast<const int *>(W.pp);
+#pragma unroll
+                    for (int t = 0; t < TPL; t++) {
+                        unsigned h = hit[t];
+                        hit[t] = 0u;
+                        cnt[t] += __popc(h);
+                        while (h) {
+                            const int b = __ffs(h) - 1;
+                            h &= h - 1u;
+                            if (rwc[t] < P.rows_cap) rrow[t][rwc[t]] = po[8 * (b >> 1) + 6 + (b & 1)];
+                            rwc[t]++;
+                        }
+                    }
+                }
                 __syncwarp();
             }
             lqn = lqp = 0;
@@ -684,17 +713,17 @@ static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long
     return P3T_OK;
 }
 
-template <int TPL, bool FILL>
+template <int TPL, bool FILL, bool ROWS = false>
 static int launch_nbr(p3t_ctx *c, const NbrArgs &a)
 {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nbr_kernel<TPL, FILL>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, nbr_kernel<TPL, FILL, ROWS>,
                                                       kNbrWarps * 32, 0) != cudaSuccess ||
         per_sm < 1)
         return P3T_ERR_CUDA;
     if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
         return P3T_ERR_CUDA;
-    nbr_kernel<TPL, FILL><<<per_sm * c->sm_count, kNbrWarps * 32, 0, c->stream>>>(a);
+    nbr_kernel<TPL, FILL, ROWS><<<per_sm * c->sm_count, kNbrWarps * 32, 0, c->stream>>>(a);
     return check_launch(c);
 }
 
@@ -707,18 +736,17 @@ static int dispatch_nbr(p3t_ctx *c, const NbrArgs &a)
     return launch_nbr<4, FILL>(c, a);
 }
 
-// Row mode (the far-force walk writes each neighbour it counts into a scratch row
-// of row_cap entries per particle, so that the lists need no second walk) pays off
-// when the walk runs before the lists.  The synchronous lists size the scratch for
-// the following walks: row_cap = 8 x the mean row length in multiples of 32, in
-// [64, 4096]; a row longer than that is filled by the fill pass for its group.  A
-// failed allocation leaves row mode off.  Reallocating drops the rows of the
-// current tree (rows_valid), which the fill pass then rebuilds.
+// Row mode: the pass that counts the neighbours (the far-force walk, or the
+// count pass when the lists come first) also writes each neighbour into a
+// scratch row of row_cap entries per particle, so that the lists need no fill
+// walk.  The synchronous lists size the scratch for the following trees: row_cap
+// = 8 x the mean row length in multiples of 32, in [64, 4096]; a row longer than
+// that is filled by the fill pass for its group.  A failed allocation leaves row
+// mode off.  Reallocating drops the rows of the current tree (rows_valid), which
+// the fill pass then rebuilds.
 static void size_row_scratch(p3t_ctx *c, long long total)
 {
-    if (!c->walk_counted || c->built_precision != P3T_FP32_MIXED || c->prm.group_size > 32 ||
-        c->n <= 0)
-        return;
+    if (c->built_precision != P3T_FP32_MIXED || c->prm.group_size > 32 || c->n <= 0) return;
     const long long mean = (total + c->n - 1) / c->n;
     const long long cap = std::max(64LL, std::min(4096LL, (8 * mean + 31) / 32 * 32));
     const size_t need = (size_t)c->cap_n * (size_t)cap;
@@ -754,12 +782,28 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
     a.capacity = capacity;
     a.ticket = &c->meta->tickets[23];
     a.row_cap = 0;
+    a.rows = nullptr;
+    a.rows_cap = 0;
     int e;
     a.skip_counted = c->walk_counted;
     if (!c->counts_valid) {  // the far-force walk did not count every cluster
-        e = dispatch_nbr<false>(c, a);
+        // row mode in the count pass: when the walk counted nothing (the lists come
+        // before the far force), or wrote the rows of what it counted
+        const int cap = c->walk_counted ? (c->rows_valid ? c->rows_cap_used : 0) : c->row_cap;
+        const bool rows = cap > 0 && c->prm.group_size <= 32 &&
+                          c->built_precision == P3T_FP32_MIXED &&
+                          c->row_scratch_entries >= (size_t)n * (size_t)cap;
+        if (rows) {
+            a.rows = c->row_scratch;
+            a.rows_cap = cap;
+            e = launch_nbr<1, false, true>(c, a);
+        } else {
+            e = dispatch_nbr<false>(c, a);
+        }
         if (e) return e;
         c->counts_valid = 1;
+        c->rows_valid = rows;
+        c->rows_cap_used = rows ? cap : 0;
     }
     e = scan_excl_i32_to_i64(c->nbr_count, offsets, n, offsets + n, c->scan_status,
                              &c->meta->tickets[29], c->meta, s);

@@ -230,3 +230,38 @@ def test_row_mode_lists_and_fallback():
     ctx2.check()
     for u, v in zip(a, b):
         assert torch.equal(u, v)
+
+
+def test_row_mode_in_host_step():
+    # p3t_step_host builds the lists before the far force, so its count pass
+    # writes the rows from the second step on; lists (with rows beyond the scratch
+    # row) equal the brute force every step, accelerations and velocities equal a
+    # first step (no row mode) of a fresh context
+    p = synth.plummer(20000, 47)
+    rng = np.random.default_rng(47)
+    q = rng.normal(size=(3, 400)) * 0.002 - 2.0
+    x, y, z = (np.concatenate([a, b]) for a, b in zip((p.x, p.y, p.z), q))
+    n = x.size
+    m = np.full(n, 1.0 / n)
+    v = [np.concatenate([a, np.zeros(400)]) for a in (p.vx, p.vy, p.vz)]
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05)
+    o2, i2 = oracle.neighbours_brute(x, y, z, 0.05)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+
+    def host_step(ctx):
+        hv = [pin(a) for a in v]
+        ha = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(3)]
+        ho = torch.empty(n + 1, dtype=torch.int64).pin_memory()
+        hi = torch.empty(2 * len(i2) + 64, dtype=torch.int32).pin_memory()
+        tot = ctx.step_host(1.0 / 512, pin(x), pin(y), pin(z), pin(m), *hv, *ha, ho, hi)
+        return tot, ho.numpy(), hi[:tot].numpy(), [t.numpy() for t in ha], [t.numpy() for t in hv]
+
+    ref = host_step(p3t.Context(prm))
+    ctx = p3t.Context(prm)
+    for step in range(3):
+        tot, offs, idx, acc, vel = host_step(ctx)
+        cap, valid = ctx.row_mode()
+        assert (valid == 1) == (step > 0) and cap > 0
+        assert tot == len(i2) and np.array_equal(offs, o2) and np.array_equal(idx, i2)
+        for u, w in zip(acc + vel, ref[3] + ref[4]):
+            assert np.array_equal(u, w)
