@@ -308,6 +308,10 @@ int p3t_scratch_bytes(const p3t_params *p, int64_t n, int32_t n_clusters, int64_
  *   ax, ay, az, pot, n_cell, n_part: as p3t_far_force.
  *   offsets, idx, capacity, total: as p3t_neighbours_async; offsets null: no lists.
  *   drift_dt: x += drift_dt * v after the kick; 0: no drift.
+ *   events: five optional cudaEvent_t handles (null entries skipped), recorded
+ *     into the graph as event nodes at the start of the step, after the build,
+ *     after the far force, after the lists and at the end, so that one launch
+ *     can be timed phase by phase (cudaEventElapsedTime after it completes).
  * p3t_graph_capture sizes the context's scratch for the step first, then
  * records the step on a private stream, so nothing runs or allocates during
  * capture; the graph is launched on the context's stream.  The context's
@@ -339,6 +343,7 @@ typedef struct {
     int64_t *total;
     double kick_dt;
     double drift_dt;
+    void *events[5];
 } p3t_step_args;
 int p3t_graph_capture(p3t_ctx *c, const p3t_step_args *a, p3t_graph **out);
 int p3t_graph_launch(p3t_graph *g);

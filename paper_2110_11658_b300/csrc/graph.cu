@@ -16,18 +16,31 @@ struct p3t_graph {
     HostState after;         // host-side state the captured step leaves
 };
 
+// an event node of the graph (the step's phase boundaries), if the caller gave one
+static int mark(p3t_ctx *c, const p3t_step_args *a, int k)
+{
+    if (!a->events[k]) return P3T_OK;
+    return cudaEventRecordWithFlags((cudaEvent_t)a->events[k], c->stream, cudaEventRecordExternal) ==
+                   cudaSuccess
+               ? P3T_OK
+               : P3T_ERR_CUDA;
+}
+
 static int record_step(p3t_ctx *c, const p3t_step_args *a)
 {
-    int e = a->seg_offsets ? p3t_build_tree_batch(c, a->n_clusters, a->n, a->seg_offsets,
-                                                  a->cluster_params, a->x, a->y, a->z, a->m)
-                           : p3t_build_tree(c, a->n, a->x, a->y, a->z, a->m);
+    int e = mark(c, a, 0);
     if (e) return e;
+    e = a->seg_offsets ? p3t_build_tree_batch(c, a->n_clusters, a->n, a->seg_offsets,
+                                              a->cluster_params, a->x, a->y, a->z, a->m)
+                       : p3t_build_tree(c, a->n, a->x, a->y, a->z, a->m);
+    if (e || (e = mark(c, a, 1))) return e;
     e = p3t_far_force(c, a->ax, a->ay, a->az, a->pot, a->n_cell, a->n_part);
-    if (e) return e;
+    if (e || (e = mark(c, a, 2))) return e;
     if (a->offsets) {
         e = p3t_neighbours_async(c, a->offsets, a->idx, a->capacity, a->total);
         if (e) return e;
     }
+    if ((e = mark(c, a, 3))) return e;
     if (a->vx) {
         e = p3t_kick(c, a->kick_dt, a->ax, a->ay, a->az, a->vx, a->vy, a->vz);
         if (e) return e;
@@ -36,7 +49,7 @@ static int record_step(p3t_ctx *c, const p3t_step_args *a)
             if (e) return e;
         }
     }
-    return P3T_OK;
+    return mark(c, a, 4);
 }
 
 extern "C" {
@@ -81,6 +94,8 @@ int p3t_graph_capture(p3t_ctx *c, const p3t_step_args *a, p3t_graph **out)
     g->after = save_state(c);
     restore_state(c, before);  // nothing of the captured step has run yet
     if (!e && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) e = P3T_ERR_CUDA;
+    // upload now, so that the first launch does not pay for it
+    if (!e && cudaGraphUpload(g->exec, c->stream) != cudaSuccess) e = P3T_ERR_CUDA;
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cap);
     if (e) {
