@@ -116,3 +116,29 @@ def test_graph_refuses_launch_after_scratch_moved():
     assert e.value.code == p3t.P3T_ERR_ORDER
     ctx.check()
     ctx.close()
+
+
+def test_graph_phase_events():
+    # events recorded as graph nodes time one launch phase by phase: every phase
+    # non-negative, the phases summing to the whole step; the step's results are
+    # those of the eager step
+    c = synth.plummer(20000, 61)
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05)
+    se, sg = _state(c), _state(c)
+    be, bg = _buffers(c.n, torch.float32, 16 * c.n), _buffers(c.n, torch.float32, 16 * c.n)
+    ce, cg = p3t.Context(prm), p3t.Context(prm)
+    _eager_step(ce, se, be)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    g = cg.capture_step(sg["x"], sg["y"], sg["z"], sg["m"], *bg["a"], vx=sg["vx"], vy=sg["vy"], vz=sg["vz"],
+                        kick_dt=DT, drift_dt=DT, n_cell=bg["nc"], n_part=bg["np"], offsets=bg["offs"],
+                        idx=bg["idx"], total=bg["tot"], events=ev)
+    g.launch()
+    torch.cuda.synchronize()
+    ce.check()
+    cg.check()
+    _compare(_snapshot(se, be), _snapshot(sg, bg))
+    phases = [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+    assert all(p >= 0.0 for p in phases) and phases[1] > 0.0
+    assert abs(sum(phases) - ev[0].elapsed_time(ev[4])) < 1e-3
+    cg.close()
+    ce.close()
