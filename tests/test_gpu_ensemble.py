@@ -134,3 +134,37 @@ def test_batch_with_per_cluster_parameters(precision):
     ctx.build_tree_batch(torch.from_numpy(seg).to(DEV), to_dev(all_.x), to_dev(all_.y), to_dev(all_.z),
                          to_dev(all_.m), cluster_params=torch.from_numpy(bad).to(DEV))
     assert ctx.status() == p3t.P3T_ERR_INVALID_INPUT
+
+
+def test_batch_row_mode_over_steps():
+    # the same per-cluster batch stepped three times on one context: from the
+    # second step the walk writes the rows (a cluster beyond r_out through the
+    # shell ranges, one without neighbours); every step's lists equal each
+    # cluster's brute force
+    cl = _ensemble()
+    all_, seg = _concat(cl)
+    rows = []
+    for k, c in enumerate(cl):
+        rc = synth.paper_run_params(max(c.n, 64))["r_cut"]
+        r_list = rc if k not in (3, 5) else (1.5 * rc if k == 3 else 0.0)
+        rows.append([(0.3, 0.5, 0.7)[k % 3], 0.1 * rc, rc, r_list])
+    cprm = np.array(rows, dtype=np.float64)
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, group_size=32)
+    ctx = p3t.Context(prm)
+    n = all_.n
+    args = (torch.from_numpy(seg).to(DEV), to_dev(all_.x), to_dev(all_.y), to_dev(all_.z), to_dev(all_.m))
+    a = [torch.empty(n, dtype=ctx.acc_dtype, device=DEV) for _ in range(3)]
+    offs = torch.empty(n + 1, dtype=torch.int64, device=DEV)
+    idx = torch.empty(50 * n, dtype=torch.int32, device=DEV)
+    ref = [oracle.neighbours_brute(c.x, c.y, c.z, cprm[k, 3]) for k, c in enumerate(cl)]
+    for step in range(3):
+        ctx.build_tree_batch(*args, cluster_params=torch.from_numpy(cprm).to(DEV))
+        ctx.far_force(*a)
+        assert ctx.row_mode()[1] == (1 if step > 0 else 0)
+        tot = ctx.neighbours(offs, idx)
+        ctx.check()
+        ob, ib = offs.cpu().numpy(), idx[:tot].cpu().numpy()
+        for k, (o2, i2) in enumerate(ref):
+            s0, s1 = seg[k], seg[k + 1]
+            assert np.array_equal(ob[s0:s1 + 1] - ob[s0], o2)
+            assert np.array_equal(ib[ob[s0]:ob[s1]] - s0, i2)
