@@ -38,11 +38,11 @@ if ROOT not in sys.path:
 
 # DRAM bytes of one walk_kernel launch, from the ncu capture of the 10^6-particle
 # Plummer walk summarised in profiles/walk_kernel_plummer_kroupa_n1e6.md: the walk
-# of the timed step, which also writes the neighbour rows (163.3 MB read + 472.8 MB
+# of the timed step, which also writes the neighbour rows (163.1 MB read + 473.0 MB
 # written; without the rows the counting walk moved 85.5 MB).  Valid only at that N and for the
 # kernel sources it was measured on: otherwise the roofline's traffic is null.
-WALK_TRAFFIC = {"sources": {"walk.cu": "294f2d27506acf73", "p3t_internal.cuh": "11c36aaef7364619"},
-                "n": 1000000, "bytes": 163299840 + 472801792}
+WALK_TRAFFIC = {"sources": {"walk.cu": "6af7099f7838618b", "p3t_internal.cuh": "11c36aaef7364619"},
+                "n": 1000000, "bytes": 163064832 + 472987648}
 
 N_DEFAULT = 1_000_000
 THETA = 0.4
