@@ -10,14 +10,15 @@
 // contribute nothing.
 //
 // One warp per target row; lanes take every 32nd entry and their partial sums
-// are reduced by shuffles in FP64.  Targets are visited in key order (the
-// built tree's), so warps running together share their neighbours in the
-// caches.  The FP64 form repeats the oracle's operations per pair (no
-// contraction).  The mixed form first splits every position (relative to its
-// cluster's frame centre O) and velocity into double-single FP32 pairs (hi +
-// lo, made in FP64 once per particle and stored in key order, so a row's
-// neighbours sit close together), then forms each difference as
-// (hi_j - hi_i) + (lo_j - lo_i) and evaluates the pair in FP32: no FP64
+// are reduced by shuffles (in FP64 for the FP64 form, in FP32 for the mixed
+// one).  Targets are visited in key order (the built tree's), so warps running
+// together share their neighbours in the caches.  The FP64 form repeats the
+// oracle's operations per pair (no contraction).  The mixed form first splits
+// every position (relative to its cluster's frame centre O) and velocity into
+// double-single FP32 pairs (hi + lo, made in FP64 once per particle and stored
+// in original order, so that a row's entries index them directly), then forms
+// each difference as (hi_j - hi_i) + (lo_j - lo_i) and evaluates the pair in
+// FP32, with the changeover's FP32 constants from the cluster table: no FP64
 // instruction per pair, and each difference within 2^-23 of its own size plus
 // 2^-46 of the cluster size (the relative error of a term is ~1e-7).
 #include <cstdint>
@@ -28,7 +29,7 @@ namespace p3t {
 
 constexpr int kIrrWarps = 8;
 
-// double-single state of one particle (mixed form), key order
+// double-single state of one particle (mixed form)
 struct DsState {
     float4 ph;  // {hi of x - O, m}
     float4 pl;  // {lo of x - O, 0}
@@ -43,17 +44,17 @@ struct IrrArgs {
     const double *x, *y, *z, *m, *vx, *vy, *vz;
     double *fx, *fy, *fz, *jx, *jy, *jz;
     const int32_t *order;   // targets in this order (key order) or null
-    const int32_t *inv;     // original -> key order (per-cluster radii) or null
+    const int32_t *inv;     // original -> key order (FP64 form's per-cluster radii)
     const int32_t *cid_s;   // cluster of each particle, key order
     const Cluster *cl;      // per-cluster radii (null: r_in, r_out below)
     const Cluster *cl_frame;  // cluster table (frame centres of the split)
     double r_in, r_out;
     Meta *meta;
-    DsState *ds;            // mixed form: per-particle splits, key order
+    DsState *ds;            // mixed form: per-particle splits, original order
 };
 
 // mixed form: split position (relative to the cluster's frame centre) and
-// velocity of every particle into hi + lo FP32 pairs, key order
+// velocity of every particle into hi + lo FP32 pairs, stored in original order
 __global__ void __launch_bounds__(256) irregular_split_kernel(IrrArgs a)
 {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < a.n; k += gridDim.x * blockDim.x) {
@@ -68,11 +69,17 @@ __global__ void __launch_bounds__(256) irregular_split_kernel(IrrArgs a)
         ds_split(a.vz[i], s.vh.z, s.vl.z);
         s.ph.w = (float)a.m[i];
         s.pl.w = s.vh.w = s.vl.w = 0.f;
-        a.ds[k] = s;
+        a.ds[i] = s;  // original order: a row's entries index it directly
     }
 }
 
 __device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -88,23 +95,26 @@ __global__ void __launch_bounds__(kIrrWarps * 32) irregular_kernel(IrrArgs a)
     for (int k = blockIdx.x * kIrrWarps + (threadIdx.x >> 5); k < a.n; k += nw) {
         const int i = a.order ? a.order[k] : k;
         double r_in = a.r_in, r_out = a.r_out;
-        if (a.cl) {
+        if (!MIXED && a.cl) {
             const Cluster &K = a.cl[a.cid_s[a.inv[i]]];
             r_in = K.r_in, r_out = K.r_out;
         }
-        const double dr = dsub(r_out, r_in);
+        const double dr = MIXED ? 0.0 : dsub(r_out, r_in);
         double xi = 0.0, yi = 0.0, zi = 0.0, uxi = 0.0, uyi = 0.0, uzi = 0.0;
         DsState si;
+        float inv_dr_f = 0.f, rin_dr_f = 0.f;
         if (MIXED) {
-            si = a.ds[k];
+            // target k of key order: its split state and its cluster's FP32 constants of
+            // the changeover, 1/(r_out - r_in) and r_in/(r_out - r_in) (no FP64 per row)
+            si = a.ds[i];
+            const Cluster &K = a.cl_frame[a.cid_s[k]];
+            inv_dr_f = K.inv_dr_f, rin_dr_f = K.rin_dr_f;
         } else {
             xi = a.x[i], yi = a.y[i], zi = a.z[i];
             uxi = a.vx[i], uyi = a.vy[i], uzi = a.vz[i];
         }
         const long long o0 = a.offs[i], o1 = a.offs[i + 1];
         double F[3] = {0.0, 0.0, 0.0}, J[3] = {0.0, 0.0, 0.0};
-        // mixed form: FP32 constants of the changeover
-        const float inv_dr_f = (float)(1.0 / dr), rin_dr_f = (float)(r_in / dr);
         float Ff[3] = {0.f, 0.f, 0.f}, Jf[3] = {0.f, 0.f, 0.f};
         for (long long e = o0 + lane; e < o1; e += 32) {
             const int j = a.idx[e];
@@ -113,7 +123,7 @@ __global__ void __launch_bounds__(kIrrWarps * 32) irregular_kernel(IrrArgs a)
                 continue;
             }
             if (MIXED) {
-                const DsState sj = a.ds[a.inv[j]];
+                const DsState sj = a.ds[j];
                 const float dx = (sj.ph.x - si.ph.x) + (sj.pl.x - si.pl.x);
                 const float dy = (sj.ph.y - si.ph.y) + (sj.pl.y - si.pl.y);
                 const float dz = (sj.ph.z - si.ph.z) + (sj.pl.z - si.pl.z);
@@ -183,14 +193,22 @@ __global__ void __launch_bounds__(kIrrWarps * 32) irregular_kernel(IrrArgs a)
             }
         }
         if (MIXED) {
+            // the lanes' FP32 partial sums summed in FP32; lane q < 6 widens and stores
+            // component q (one FP64-pipe conversion per row)
 #pragma unroll
-            for (int q = 0; q < 3; q++) F[q] = (double)Ff[q], J[q] = (double)Jf[q];
-        }
+            for (int q = 0; q < 3; q++) Ff[q] = warp_sum_f(Ff[q]), Jf[q] = warp_sum_f(Jf[q]);
+            const float v = lane == 0 ? Ff[0] : lane == 1 ? Ff[1] : lane == 2 ? Ff[2]
+                          : lane == 3 ? Jf[0] : lane == 4 ? Jf[1] : Jf[2];
+            double *out = lane == 0 ? a.fx : lane == 1 ? a.fy : lane == 2 ? a.fz
+                        : lane == 3 ? a.jx : lane == 4 ? a.jy : a.jz;
+            if (lane < 6) out[i] = (double)v;
+        } else {
 #pragma unroll
-        for (int q = 0; q < 3; q++) F[q] = warp_sum_d(F[q]), J[q] = warp_sum_d(J[q]);
-        if (lane == 0) {
-            a.fx[i] = F[0], a.fy[i] = F[1], a.fz[i] = F[2];
-            a.jx[i] = J[0], a.jy[i] = J[1], a.jz[i] = J[2];
+            for (int q = 0; q < 3; q++) F[q] = warp_sum_d(F[q]), J[q] = warp_sum_d(J[q]);
+            if (lane == 0) {
+                a.fx[i] = F[0], a.fy[i] = F[1], a.fz[i] = F[2];
+                a.jx[i] = J[0], a.jy[i] = J[1], a.jz[i] = J[2];
+            }
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) latch_error(a.meta, P3T_ERR_INVALID_INPUT);
