@@ -7,8 +7,10 @@
 // (one cluster).  Blocks pair 128 sampled particles with one chunk of
 // candidates in key order, staged through shared memory.  Each candidate is
 // first tested in FP32 on double-single coordinates relative to the frame
-// centre (the tree's hi/lo splits): a candidate whose FP32 squared distance
-// exceeds an upper bound of the current 6th distance cannot enter the list;
+// centre (the hi parts of the tree's splits, two candidates per packed FP32x2
+// instruction): a candidate whose FP32 squared distance exceeds an upper bound
+// of the current 6th distance, widened by the filter's error, cannot enter the
+// list;
 // the others are decided with the exact FP64 distance (dx*dx + dy*dy) + dz*dz
 // and inserted by (distance, original index).  A second kernel merges the
 // chunks' lists.  The result is unique, so it equals the oracle's bit for bit.
@@ -54,15 +56,31 @@ __device__ __forceinline__ void knn_insert(double (&bd)[kKnn], int (&bi)[kKnn], 
     }
 }
 
+// FP32 filter threshold for candidates that may enter a list whose 6th squared
+// distance is at most lim.  The test uses only the hi parts of the splits: every
+// coordinate difference is then within 2u R (both roundings to FP32, u = 2^-24,
+// R the frame's half-size) plus u of itself of the exact one, so a candidate at
+// exact distance r has an FP32 squared distance of at most
+// ((1 + u) r + sqrt(3) 2u R)^2 (1 + 3u) (triangle inequality over the three
+// coordinates); thr covers that with sqrt(lim) (1 + 8u) + 4u R and (1 + 32u).
+__device__ __forceinline__ float knn_threshold(double lim, float eR)
+{
+    if (!(lim < INFINITY)) return INFINITY;
+    const float s = sqrtf((float)lim) * (1.f + 8.f * kFp32U) + eR;
+    return s * s * (1.f + 32.f * kFp32U);
+}
+
 __global__ void __launch_bounds__(kKnnThreads) knn_chunk_kernel(KnnArgs a)
 {
-    __shared__ float4 sh[kKnnTile], sl[kKnnTile];
+    // candidates in pairs (hi parts relative to the frame centre): {x0 x1 y0 y1}, {z0 z1}
+    __shared__ float4 sxy[kKnnTile / 2];
+    __shared__ float2 sz[kKnnTile / 2];
     const Tree &T = a.T;
     const int t = blockIdx.x * kKnnThreads + threadIdx.x;
     const int c = blockIdx.y;
     bool active = t < a.s;
     int me = -1, km = 0;
-    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+    float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
     double4_32a p = make_double4_32a(0.0, 0.0, 0.0, 0.0);
     if (active) {
         me = a.sample[t];
@@ -72,15 +90,11 @@ __global__ void __launch_bounds__(kKnnThreads) knn_chunk_kernel(KnnArgs a)
             me = -1;
         } else {
             km = T.inv[me];
-            h = T.ph[km], l = T.pl[km];
+            h = T.ph[km];
             p = T.sp[km];
         }
     }
-    // the frame term of the FP32 band: after the double-single difference every
-    // coordinate carries <= 2^-47 R; 2^-40 R^2 covers its share of any squared
-    // distance within the frame with a wide margin
-    const float Rf = (float)T.cl[0].frame[3];
-    const float band_abs = Rf * Rf * 9.094947e-13f + 1e-37f;
+    const float eR = 4.f * kFp32U * (float)T.cl[0].frame[3];
     double bd[kKnn];
     int bi[kKnn];
     // upper bound of the 6th distance: the 6th nearest among the 32 particles next
@@ -102,36 +116,45 @@ __global__ void __launch_bounds__(kKnnThreads) knn_chunk_kernel(KnnArgs a)
 #pragma unroll
     for (int q = 0; q < kKnn; q++) bd[q] = INFINITY, bi[q] = 0x7fffffff;
     // FP32 squared distances above this cannot enter the list
-    float thr = bound < INFINITY ? (float)bound * (1.f + 32.f * kFp32U) + band_abs : INFINITY;
+    float thr = knn_threshold(bound, eR);
+    const float2 NX = make_float2(-h.x, -h.x), NY = make_float2(-h.y, -h.y), NZ = make_float2(-h.z, -h.z);
     const int k0 = c * a.chunk, k1 = min(a.n, k0 + a.chunk);
     for (int base = k0; base < k1; base += kKnnTile) {
         const int nt = min(kKnnTile, k1 - base);
+        const int np = (nt + 1) >> 1;
         __syncthreads();
-        for (int q = threadIdx.x; q < nt; q += kKnnThreads) {
-            sh[q] = T.ph[base + q];
-            sl[q] = T.pl[base + q];
+        for (int q = threadIdx.x; q < np; q += kKnnThreads) {
+            const float4 a0 = T.ph[base + 2 * q];
+            // an odd tail's partner sits far away: never within any threshold
+            const float4 a1 = 2 * q + 1 < nt ? T.ph[base + 2 * q + 1] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            sxy[q] = make_float4(a0.x, a1.x, a0.y, a1.y);
+            sz[q] = make_float2(a0.z, a1.z);
         }
         __syncthreads();
         if (!active) continue;
 #pragma unroll 4
-        for (int q = 0; q < nt; q++) {
-            const float4 ch = sh[q], cl = sl[q];
-            const float dx = (ch.x - h.x) + (cl.x - l.x);
-            const float dy = (ch.y - h.y) + (cl.y - l.y);
-            const float dz = (ch.z - h.z) + (cl.z - l.z);
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 <= thr) {  // may enter the list: decide exactly
-                const int kj = base + q;
-                const int oj = T.perm[kj];
-                if (oj != me) {
-                    const double4_32a pj = T.sp[kj];
-                    const double ex = dsub(pj.x, p.x), ey = dsub(pj.y, p.y), ez = dsub(pj.z, p.z);
-                    const double d2 = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez));
-                    knn_insert(bd, bi, d2, oj);
-                    // |FP32 - exact| of a squared distance <= 8u (relative) + the
-                    // frame term; 32u and twice the frame term leave a margin
-                    const double lim = fmin(bd[kKnn - 1], bound);
-                    thr = lim < INFINITY ? (float)lim * (1.f + 32.f * kFp32U) + band_abs : INFINITY;
+        for (int q = 0; q < np; q++) {
+            const float4 xy = sxy[q];
+            const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), NX);
+            const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), NY);
+            const float2 dz = __fadd2_rn(sz[q], NZ);
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            if (fminf(r2.x, r2.y) <= thr) {  // one of the two may enter the list: decide exactly
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const int kj = base + 2 * q + e;
+                    if ((e ? r2.y : r2.x) <= thr && 2 * q + e < nt) {
+                        const int oj = T.perm[kj];
+                        if (oj != me) {
+                            const double4_32a pj = T.sp[kj];
+                            const double ex = dsub(pj.x, p.x), ey = dsub(pj.y, p.y), ez = dsub(pj.z, p.z);
+                            const double d2 = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez));
+                            knn_insert(bd, bi, d2, oj);
+                            thr = knn_threshold(fmin(bd[kKnn - 1], bound), eR);
+                        }
+                    }
                 }
             }
         }
