@@ -614,6 +614,29 @@ __global__ void __launch_bounds__(kBuildThreads) group_finish_kernel(Tree T, int
     }
 }
 
+// the FP32 frame quantities of every group, one thread per group: the mixed walks
+// and the neighbour passes load them instead of deriving them on the FP64 pipe
+// per warp (same operations as those walks used: c_g = (lo + hi) / 2, its
+// double-single split relative to the cluster's frame centre O, the box - O)
+__global__ void __launch_bounds__(kBuildThreads) group_frames_kernel(Tree T)
+{
+    const int ng = T.meta->n_groups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        const double4_32a glo = T.glo[g], ghi = T.ghi[g];
+        const double *O = T.cl[T.cid_s[T.grp[g].x]].frame;
+        float hx, hy, hz, lx, ly, lz;
+        ds_split(dsub(dmul(0.5, dadd(glo.x, ghi.x)), O[0]), hx, lx);
+        ds_split(dsub(dmul(0.5, dadd(glo.y, ghi.y)), O[1]), hy, ly);
+        ds_split(dsub(dmul(0.5, dadd(glo.z, ghi.z)), O[2]), hz, lz);
+        T.gfr[3 * (size_t)g] = make_float4(hx, hy, hz, lx);
+        T.gfr[3 * (size_t)g + 1] = make_float4(ly, lz, __double2float_rn(dsub(glo.x, O[0])),
+                                               __double2float_rn(dsub(glo.y, O[1])));
+        T.gfr[3 * (size_t)g + 2] =
+            make_float4(__double2float_rn(dsub(glo.z, O[2])), __double2float_rn(dsub(ghi.x, O[0])),
+                        __double2float_rn(dsub(ghi.y, O[1])), __double2float_rn(dsub(ghi.z, O[2])));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // moments (rule 6) and the opening radius (rule 8)
 
@@ -915,6 +938,7 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     if (e) return e;
     group_first_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, T.gflag, T.gidx, T.grp);
     group_finish_kernel<<<persistent, kBuildThreads, 0, s>>>(T, n);
+    group_frames_kernel<<<persistent, kBuildThreads, 0, s>>>(T);
 
     // moments: leaves, then levels 20 .. 0 (a level without internal nodes exits at once)
     const bool q64 = P.precision == P3T_FP64;

@@ -78,24 +78,25 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         const Cluster &K = T.cl[cid];
         // counting: clusters the far-force walk already counted are skipped
         if (!FILL && P.skip_counted && K.counted) continue;
-        const double *fr = K.frame;
-        const double Ox = fr[0], Oy = fr[1], Oz = fr[2];
-        const float Rf = (float)fr[3] * 1.0001f;
+        if (FILL && P.row_cap > 0) {  // row mode: every row of at most row_cap is written
+            bool longer = false;
+#pragma unroll
+            for (int t = 0; t < TPL; t++) {
+                const int s = gr.x + lane + 32 * t;
+                longer |= s < gr.x + gr.y && P.count[T.perm[s]] > P.row_cap;
+            }
+            if (!__any_sync(0xffffffffu, longer)) continue;
+        }
+        const float Rf = (float)K.frame[3] * 1.0001f;
         const float rl_f = K.rl_f, rl2_f = K.rl2_f;
         const double rl2_d = K.rl2_d;
         const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && rl2_f > 1e-20f && rl2_f < 1e30f;
         const Band bl_band = fp32_band(Rf, rl2_f);  // box-box test against r_list
-        const double cgx = dmul(0.5, dadd(glo.x, ghi.x));
-        const double cgy = dmul(0.5, dadd(glo.y, ghi.y));
-        const double cgz = dmul(0.5, dadd(glo.z, ghi.z));
-        float fhx, fhy, fhz, flx, fly, flz;  // double-single split of c_g - O
-        ds_split(dsub(cgx, Ox), fhx, flx);
-        ds_split(dsub(cgy, Oy), fhy, fly);
-        ds_split(dsub(cgz, Oz), fhz, flz);
-        const float glx = __double2float_rn(dsub(glo.x, Ox)), gly = __double2float_rn(dsub(glo.y, Oy)),
-                    glz = __double2float_rn(dsub(glo.z, Oz));
-        const float ghx = __double2float_rn(dsub(ghi.x, Ox)), ghy = __double2float_rn(dsub(ghi.y, Oy)),
-                    ghz = __double2float_rn(dsub(ghi.z, Oz));
+        // double-single split of c_g - O and the box - O, made once per build
+        const float4 g0 = T.gfr[3 * (size_t)g], g1 = T.gfr[3 * (size_t)g + 1],
+                     g2 = T.gfr[3 * (size_t)g + 2];
+        const float fhx = g0.x, fhy = g0.y, fhz = g0.z, flx = g0.w, fly = g1.x, flz = g1.y;
+        const float glx = g1.z, gly = g1.w, glz = g2.x, ghx = g2.y, ghy = g2.z, ghz = g2.w;
         // targets: coordinates relative to c_g, original index `me`; an empty slot sits
         // at 1e30 so that no FP32 test counts it (its rare FP64 path checks si < 0)
         float px[TPL], py[TPL], pz[TPL];
@@ -131,12 +132,6 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 si[t] = -1;
                 me[t] = -1;
             }
-        }
-        if (FILL && P.row_cap > 0) {  // row mode: the walk wrote every row of at most row_cap
-            bool longer = false;
-#pragma unroll
-            for (int t = 0; t < TPL; t++) longer |= si[t] >= 0 && P.count[me[t]] > P.row_cap;
-            if (!__any_sync(0xffffffffu, longer)) continue;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) A = fmaxf(A, __shfl_xor_sync(0xffffffffu, A, o));

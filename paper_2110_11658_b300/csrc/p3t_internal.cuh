@@ -106,6 +106,9 @@ struct Tree {
     float4 *wn;    // kWalkRecord float4 per node
     int2 *grp;
     double4_32a *glo, *ghi;
+    // per group, three float4 made once per build (mixed walks): the double-single
+    // split of c_g - O {hx hy hz lx} {ly lz, box lo - O: x y} {z, box hi - O: x y z}
+    float4 *gfr;
     unsigned char *gflag;  // group-start flags, particle order
     int32_t *gidx;         // scan of gflag
     int32_t *leaves;       // leaf node indices, in creation order (moments work list)

@@ -718,7 +718,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ng) break;
         const int2 gr = T.grp[g];
-        const double4_32a glo = T.glo[g], ghi = T.ghi[g];
+        double4_32a glo, ghi;  // the FP64 form's group box (the mixed form reloads it when needed)
+        if constexpr (!kMixed) glo = T.glo[g], ghi = T.ghi[g];
         // the group's cluster: its frame O, its root (node cid) and the filter bands
         // (|FP32 - FP64| of a squared distance <= k_rel (d2 + r2) + k_abs |t|_1 +
         // k_sq, about twice the derived bound, every coordinate relative to O being
@@ -740,17 +741,26 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         const Band bb_band = fp32_band(Rf, rout2_f);  // the box-box test against r_out
         const Band bl_band = fp32_band(Rf, rl2_f);    // and against r_list (shell)
         GroupFrame F;
-        F.cx = dmul(0.5, dadd(glo.x, ghi.x));
-        F.cy = dmul(0.5, dadd(glo.y, ghi.y));
-        F.cz = dmul(0.5, dadd(glo.z, ghi.z));
-        ds_split(dsub(F.cx, Ox), F.hx, F.lx);
-        ds_split(dsub(F.cy, Oy), F.hy, F.ly);
-        ds_split(dsub(F.cz, Oz), F.hz, F.lz);
-        // group box relative to O for the FP32 filter
-        const float glx = __double2float_rn(dsub(glo.x, Ox)), gly = __double2float_rn(dsub(glo.y, Oy)),
-                    glz = __double2float_rn(dsub(glo.z, Oz));
-        const float ghx = __double2float_rn(dsub(ghi.x, Ox)), ghy = __double2float_rn(dsub(ghi.y, Oy)),
-                    ghz = __double2float_rn(dsub(ghi.z, Oz));
+        float glx, gly, glz, ghx, ghy, ghz;  // group box relative to O for the FP32 filter
+        if constexpr (kMixed) {
+            // c_g's double-single split and the box, made once per build (group_frames_kernel)
+            const float4 g0 = T.gfr[3 * (size_t)g], g1 = T.gfr[3 * (size_t)g + 1],
+                         g2 = T.gfr[3 * (size_t)g + 2];
+            F.cx = F.cy = F.cz = 0.0;  // (the mixed form works relative to O)
+            F.hx = g0.x, F.hy = g0.y, F.hz = g0.z, F.lx = g0.w, F.ly = g1.x, F.lz = g1.y;
+            glx = g1.z, gly = g1.w, glz = g2.x, ghx = g2.y, ghy = g2.z, ghz = g2.w;
+        } else {
+            F.cx = dmul(0.5, dadd(glo.x, ghi.x));
+            F.cy = dmul(0.5, dadd(glo.y, ghi.y));
+            F.cz = dmul(0.5, dadd(glo.z, ghi.z));
+            ds_split(dsub(F.cx, Ox), F.hx, F.lx);
+            ds_split(dsub(F.cy, Oy), F.hy, F.ly);
+            ds_split(dsub(F.cz, Oz), F.hz, F.lz);
+            glx = __double2float_rn(dsub(glo.x, Ox)), gly = __double2float_rn(dsub(glo.y, Oy));
+            glz = __double2float_rn(dsub(glo.z, Oz));
+            ghx = __double2float_rn(dsub(ghi.x, Ox)), ghy = __double2float_rn(dsub(ghi.y, Oy));
+            ghz = __double2float_rn(dsub(ghi.z, Oz));
+        }
         Real px[TPL], py[TPL], pz[TPL];
         NbrCount<TPL> NC;
         float amax = 0.f;
