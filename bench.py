@@ -492,8 +492,8 @@ def run_b300(args, rank, local, world):
 # bbox, cube, keys (6) + radix sort 8 x (histogram, scan, scatter) + gather + topology
 # root, 21 levels, finish + group scan, first, finish, frames + moments leaves and 21
 # levels; far force 1 (it also counts the neighbours); neighbours = offsets scan, fill,
-# row binning by length (count, list) and seven row-sort size classes; kick 1; drift 1
-KERNELS_PER_STEP = (6 + 8 * 3 + 1 + (1 + 21 + 1) + 4 + (1 + 21)) + 1 + (2 + 2 + 7) + 1 + 1
+# row binning by length (count, list) and eight row-sort size classes; kick 1; drift 1
+KERNELS_PER_STEP = (6 + 8 * 3 + 1 + (1 + 21 + 1) + 4 + (1 + 21)) + 1 + (2 + 2 + 8) + 1 + 1
 
 
 def run_reference(args, rank, world):

@@ -339,12 +339,12 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 // sorted by its own launch, one warp per listed row, so that no launch scans the
 // rows of other classes and only one class's code is resident in the
 // instruction cache:
-//   (1, 512]      bitonic network in registers, K = 1, 2, 4, 8, 16 entries per
-//                 lane: up to 128 in the strided layout (element e = 32 r + lane
-//                 in register r; partners 32 apart or more are in the same lane,
-//                 closer ones are exchanged by shuffles), above in the transposed
-//                 layout (warp_bitonic_row_t)
-//   (512, 2048]   loop-based bitonic network (below) in shared memory
+//   (1, 1024]     bitonic network in registers, K = 1, 2, 4, 8, 16, 32 entries
+//                 per lane: up to 128 in the strided layout (element e = 32 r +
+//                 lane in register r; partners 32 apart or more are in the same
+//                 lane, closer ones are exchanged by shuffles), above in the
+//                 transposed layout (warp_bitonic_row_t)
+//   (1024, 2048]  loop-based bitonic network (below) in shared memory
 //   > 2048        the same network in global memory.
 // The loop network puts the smaller value at the lower index in every
 // compare-exchange (each merge stage starts by comparing mirrored positions of a
@@ -354,12 +354,13 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 // class of the 10^6-particle Plummer workload.)
 constexpr int kRowClasses = 8;
 // class c holds the rows with kClassLen[c] < len <= kClassLen[c + 1]
-__constant__ int kClassLenDev[kRowClasses + 1] = {0, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
-constexpr int kClassLen[kRowClasses + 1] = {0, 32, 64, 128, 256, 512, 2048, INT_MAX, INT_MAX};
+__constant__ int kClassLenDev[kRowClasses + 1] = {0, 32, 64, 128, 256, 512, 1024, 2048, INT_MAX};
+constexpr int kClassLen[kRowClasses + 1] = {0, 32, 64, 128, 256, 512, 1024, 2048, INT_MAX};
 constexpr int kSortWarps = 4;
+constexpr int kRowLoadBatch = 8;  // global loads a lane issues before storing any
 // bit c set: class c uses the transposed register network (faster for
-// (128, 512], slower for (64, 128] on the 10^6-particle Plummer rows)
-constexpr unsigned kTransposed = (1u << 3) | (1u << 4);
+// (128, 1024], slower for (64, 128] on the 10^6-particle Plummer rows)
+constexpr unsigned kTransposed = (1u << 3) | (1u << 4) | (1u << 5);
 
 __device__ __forceinline__ int row_class(int len)
 {
@@ -426,11 +427,11 @@ struct RowSrc {
     int cap;
 };
 
-// Entry e of one row.
+// Where one row's entries are read from: its scratch row, else its place in idx.
 struct RowLoad {
     const int32_t *sr;  // scratch row, or null
     const int32_t *row;
-    __device__ __forceinline__ int operator()(int e) const { return sr ? sr[e] : row[e]; }
+    __device__ __forceinline__ const int32_t *base() const { return sr ? sr : row; }
 };
 
 // The rows of class C, one warp each: f(row pointer in idx, length, loader).
@@ -460,11 +461,12 @@ template <int K>
 __device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len, const RowLoad &ld)
 {
     const int lane = threadIdx.x & 31;
+    const int32_t *src = ld.base();
     int v[K];
 #pragma unroll
     for (int r = 0; r < K; r++) {
         int e = 32 * r + lane;
-        v[r] = e < len ? ld(e) : INT_MAX;
+        v[r] = e < len ? src[e] : INT_MAX;
     }
 #pragma unroll
     for (int k = 2; k <= 32 * K; k <<= 1) {
@@ -508,16 +510,27 @@ __device__ __forceinline__ void warp_bitonic_row(int32_t *row, int len, const Ro
 // order of int32), so that every compare-exchange is ascending; the complement
 // pattern changes once per merge level.  The row passes through shared memory
 // (sb: 32 K + K words, index e + e / 32 keeps both access patterns free of bank
-// conflicts) so that the global loads and stores stay coalesced.
+// conflicts) so that the global loads and stores stay coalesced; all K loads of
+// a lane are issued before the first store.
 template <int K>
 __device__ __forceinline__ void warp_bitonic_row_t(int32_t *row, int len, int32_t *sb,
                                                    const RowLoad &ld)
 {
     constexpr int N = 32 * K;
     const int lane = threadIdx.x & 31;
-    for (int e = lane; e < N; e += 32) sb[e + (e >> 5)] = e < len ? ld(e) : INT_MAX;
-    __syncwarp();
+    const int32_t *src = ld.base();
     int v[K];
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        const int e = 32 * r + lane;
+        v[r] = e < len ? src[e] : INT_MAX;
+    }
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        const int e = 32 * r + lane;
+        sb[e + (e >> 5)] = v[r];
+    }
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r < K; r++) {
         const int e = K * lane + r;
@@ -562,7 +575,11 @@ __device__ __forceinline__ void warp_bitonic_row_t(int32_t *row, int len, int32_
         sb[e + (e >> 5)] = v[r];  // level N has no descending block: v is the value
     }
     __syncwarp();
-    for (int e = lane; e < len; e += 32) row[e] = sb[e + (e >> 5)];
+#pragma unroll
+    for (int r = 0; r < K; r++) {
+        const int e = 32 * r + lane;
+        if (e < len) row[e] = sb[e + (e >> 5)];
+    }
 }
 
 // ascending compare-exchange of a[i] and a[h] (i < h), skipped past the end
@@ -587,7 +604,7 @@ __device__ void warp_sort_mem(int32_t *a, int len)
     for (int k = 2; k <= P; k <<= 1) {
         const int hk = k >> 1;
         for (int i = lane; i < half; i += 32) {  // mirrored pairs within blocks of k
-            const int lo = (i / hk) * k + (i % hk);
+            const int lo = ((i & ~(hk - 1)) << 1) | (i & (hk - 1));
             cmpx(a, lo, lo ^ (k - 1), len);
         }
         __syncwarp();
@@ -633,7 +650,20 @@ __global__ void __launch_bounds__(kSortWarps * 32)
     const int lane = threadIdx.x & 31;
     int32_t *sb = sbuf[threadIdx.x >> 5];
     for_class_rows<C>(meta, list, offs, idx, src, [&](int32_t *row, int len, const RowLoad &ld) {
-        for (int e = lane; e < len; e += 32) sb[e] = ld(e);
+        const int32_t *s = ld.base();
+        for (int e0 = 0; e0 < len; e0 += 32 * kRowLoadBatch) {  // loads in flight together
+            int t[kRowLoadBatch];
+#pragma unroll
+            for (int r = 0; r < kRowLoadBatch; r++) {
+                const int e = e0 + 32 * r + lane;
+                t[r] = e < len ? s[e] : 0;
+            }
+#pragma unroll
+            for (int r = 0; r < kRowLoadBatch; r++) {
+                const int e = e0 + 32 * r + lane;
+                if (e < len) sb[e] = t[r];
+            }
+        }
         __syncwarp();
         warp_sort_mem(sb, len);
         for (int e = lane; e < len; e += 32) row[e] = sb[e];
@@ -650,7 +680,7 @@ __global__ void __launch_bounds__(kSortWarps * 32)
     const int lane = threadIdx.x & 31;
     for_class_rows<C>(meta, list, offs, idx, src, [&](int32_t *row, int len, const RowLoad &ld) {
         if (ld.sr) {
-            for (int e = lane; e < len; e += 32) row[e] = ld(e);
+            for (int e = lane; e < len; e += 32) row[e] = ld.sr[e];
             __syncwarp();
         }
         warp_sort_mem(row, len);
@@ -702,8 +732,9 @@ static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long
         else
             e = launch_sort(c, row_sort_reg_kernel<4, 16>, offsets, idx, src);
         if (e) return e;
-        if ((e = launch_sort(c, row_sort_smem_kernel<5>, offsets, idx, src))) return e;
-        if ((e = launch_sort(c, row_sort_global_kernel<6>, offsets, idx, src))) return e;
+        if ((e = launch_sort(c, row_sort_tr_kernel<5, 32>, offsets, idx, src))) return e;
+        if ((e = launch_sort(c, row_sort_smem_kernel<6>, offsets, idx, src))) return e;
+        if ((e = launch_sort(c, row_sort_global_kernel<7>, offsets, idx, src))) return e;
     }
     return P3T_OK;
 }
