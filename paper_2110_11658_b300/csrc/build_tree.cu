@@ -440,9 +440,12 @@ __global__ void topo_root_kernel(Tree T, int n, int leaf_cap, int G)
     flag_groups(T.gflag, (int)first, cnt, true, cnt <= leaf_cap, G);
 }
 
+// A level with at most kTopoWideNodes nodes splits one node per warp with a 32-way
+// search: a node of 10^6 keys takes 4 dependent load steps instead of the 20 of a
+// binary search.  status holds status_cap lookback flags (one per tile).
 __global__ void __launch_bounds__(kBuildThreads)
     topo_level_kernel(Tree T, int l, int leaf_cap, int G, unsigned long long *status,
-                      unsigned int *ticket)
+                      int status_cap, unsigned int *ticket)
 {
     __shared__ unsigned int sh_t;
     __shared__ long long sh_scan[32];
@@ -450,15 +453,23 @@ __global__ void __launch_bounds__(kBuildThreads)
     Meta *M = T.meta;
     const int nl = M->level_count[l];
     const int base = M->level_start[l];
-    const int ntiles = (nl + kBuildThreads - 1) / kBuildThreads;
+    const bool wide = nl <= kTopoWideNodes;  // uniform over the launch
+    const int per_tile = wide ? kBuildThreads / 32 : kBuildThreads;
+    const int ntiles = (nl + per_tile - 1) / per_tile;
     const int shift = 63 - 3 * (l + 1);
+    const int lane = threadIdx.x & 31;
+    if (ntiles > status_cap) {  // more tiles than flags (cannot happen for nl <= n)
+        if (threadIdx.x == 0) latch_error(M, P3T_ERR_INTERNAL);
+        return;
+    }
     while (true) {
         if (threadIdx.x == 0) sh_t = atomicAdd(ticket, 1u);
         __syncthreads();
         const int t = (int)sh_t;
         __syncthreads();
         if (t >= ntiles) break;
-        const int node = base + t * kBuildThreads + threadIdx.x;
+        // wide: warp w of the block holds node t * 8 + w (every lane), else one node a thread
+        const int node = base + t * per_tile + (wide ? (int)(threadIdx.x >> 5) : (int)threadIdx.x);
         const bool mine = node < base + nl;
         int bnd[9];
         int nch = 0;
@@ -471,48 +482,98 @@ __global__ void __launch_bounds__(kBuildThreads)
             bnd[0] = b;
             bnd[8] = e;
             // the 7 octant boundaries: lower bounds of ((pfx << 3) | o) << shift in
-            // keys[b, e), searched in lockstep (branchless halving with a common
-            // length, so the 7 loads of a step are independent)
+            // keys[b, e), searched in lockstep (the 7 loads of a step are independent)
             uint64_t tgt[8];
-            int at[8];
 #pragma unroll
-            for (int o = 1; o < 8; o++) tgt[o] = ((pfx << 3) | (uint64_t)o) << shift, at[o] = b;
-            for (int len = e - b; len > 1;) {
-                const int half = len >> 1;
+            for (int o = 1; o < 8; o++) tgt[o] = ((pfx << 3) | (uint64_t)o) << shift;
+            if (wide) {
+                // the lower bound lies in [lo, hi] (keys[lo - 1] < tgt <= keys[hi]);
+                // lane j probes lo + j * stride, the probes below tgt are a prefix of
+                // the lanes (keys ascending), and the range shrinks to one stride
+                int lo[8], hi[8];
 #pragma unroll
-                for (int o = 1; o < 8; o++) at[o] = T.keys[at[o] + half] < tgt[o] ? at[o] + half : at[o];
-                len -= half;
+                for (int o = 1; o < 8; o++) lo[o] = b, hi[o] = e;
+                while (true) {
+                    bool any = false;
+                    uint64_t kv[8];
+                    int st[8];
+#pragma unroll
+                    for (int o = 1; o < 8; o++) {
+                        const int len = hi[o] - lo[o];
+                        st[o] = (len + 31) >> 5;
+                        const int pj = lo[o] + lane * st[o];
+                        kv[o] = len > 0 && pj < hi[o] ? T.keys[pj] : ~0ull;
+                        any |= len > 0;
+                    }
+                    if (!any) break;
+#pragma unroll
+                    for (int o = 1; o < 8; o++) {
+                        const int k = __popc(__ballot_sync(0xffffffffu, kv[o] < tgt[o]));
+                        const int l0 = lo[o];
+                        if (hi[o] > l0) {
+                            if (k > 0) lo[o] = l0 + (k - 1) * st[o] + 1;
+                            if (l0 + k * st[o] < hi[o]) hi[o] = l0 + k * st[o];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < 8; o++) bnd[o] = lo[o];
+            } else {
+                // branchless halving with a common length
+                int at[8];
+#pragma unroll
+                for (int o = 1; o < 8; o++) at[o] = b;
+                for (int len = e - b; len > 1;) {
+                    const int half = len >> 1;
+#pragma unroll
+                    for (int o = 1; o < 8; o++)
+                        at[o] = T.keys[at[o] + half] < tgt[o] ? at[o] + half : at[o];
+                    len -= half;
+                }
+#pragma unroll
+                for (int o = 1; o < 8; o++) bnd[o] = at[o] + (T.keys[at[o]] < tgt[o] ? 1 : 0);
             }
-#pragma unroll
-            for (int o = 1; o < 8; o++) bnd[o] = at[o] + (T.keys[at[o]] < tgt[o] ? 1 : 0);
 #pragma unroll
             for (int o = 0; o < 8; o++) nch += bnd[o + 1] > bnd[o];
         }
+        const bool owner = !wide || lane == 0;  // writes the node's children
         long long tot;
-        long long ex = block_excl_scan<long long>((long long)nch, &tot, sh_scan);
+        long long ex = block_excl_scan<long long>(owner ? (long long)nch : 0LL, &tot, sh_scan);
         long long pre = lookback_prefix(status, t, tot, M, &sh_pre);
         const int child_base = base + nl + (int)(pre + ex);
-        if (split) {
-            const bool big = tp.y > kGroupNodeFactor * G;
-            if (child_base + nch > T.cap_nodes) {
-                latch_error(M, P3T_ERR_CAPACITY);
-            } else {
-                int k = 0;
+        const bool fits = child_base + nch <= T.cap_nodes;
+        if (split && owner && !fits) latch_error(M, P3T_ERR_CAPACITY);
+        const bool write = split && owner && fits;
+        // leaves appended with one atomic per warp
+        int nlf = 0;
+        if (write) {
 #pragma unroll
-                for (int o = 0; o < 8; o++) {
-                    int cnt = bnd[o + 1] - bnd[o];
-                    if (cnt > 0) {
-                        int c = child_base + k++;
-                        T.topo[c] = make_int4(bnd[o], cnt, -1, 0);
-                        T.level[c] = l + 1;
-                        T.parent[c] = node;
-                        bool leaf = cnt <= leaf_cap || l + 1 >= kLevels;
-                        if (leaf) T.leaves[atomicAdd(&M->n_leaves, 1)] = c;
-                        flag_groups(T.gflag, bnd[o], cnt, big, leaf, G);
-                    }
-                }
-                T.topo[node] = make_int4(tp.x, tp.y, child_base, nch);
+            for (int o = 0; o < 8; o++) {
+                const int cnt = bnd[o + 1] - bnd[o];
+                nlf += cnt > 0 && (cnt <= leaf_cap || l + 1 >= kLevels);
             }
+        }
+        const int inc = warp_incl_scan(nlf);
+        int lf = 0;
+        if (lane == 31 && inc > 0) lf = atomicAdd(&M->n_leaves, inc);
+        lf = __shfl_sync(0xffffffffu, lf, 31) + inc - nlf;
+        if (write) {
+            const bool big = tp.y > kGroupNodeFactor * G;
+            int k = 0;
+#pragma unroll
+            for (int o = 0; o < 8; o++) {
+                int cnt = bnd[o + 1] - bnd[o];
+                if (cnt > 0) {
+                    int c = child_base + k++;
+                    T.topo[c] = make_int4(bnd[o], cnt, -1, 0);
+                    T.level[c] = l + 1;
+                    T.parent[c] = node;
+                    bool leaf = cnt <= leaf_cap || l + 1 >= kLevels;
+                    if (leaf) T.leaves[lf++] = c;
+                    flag_groups(T.gflag, bnd[o], cnt, big, leaf, G);
+                }
+            }
+            T.topo[node] = make_int4(tp.x, tp.y, child_base, nch);
         }
         if (t == ntiles - 1 && threadIdx.x == 0) {
             M->level_start[l + 1] = base + nl;
@@ -928,7 +989,7 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     const int topo_grid = 2 * c->sm_count;
     for (int l = 0; l < kLevels; l++)
         topo_level_kernel<<<topo_grid, kBuildThreads, 0, s>>>(
-            T, l, P.leaf_cap, P.group_size, topo_status + (size_t)l * stride, &M->tickets[l]);
+            T, l, P.leaf_cap, P.group_size, topo_status + (size_t)l * stride, stride, &M->tickets[l]);
     topo_finish_kernel<<<1, 1, 0, s>>>(M, T.cap_nodes);
     if (check_launch(c)) return P3T_ERR_CUDA;
 

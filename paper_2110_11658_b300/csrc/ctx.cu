@@ -21,7 +21,15 @@ long long node_capacity(long long n, int leaf_cap)
     return n + (long long)kLevels * (n / (leaf_cap + 1)) + 1;
 }
 
-int topo_status_stride(long long n) { return (int)(n / 256 + 4); }
+// lookback flags per tree level: one per tile of the level's nodes (a level holds
+// at most n nodes; tiles of 256 nodes, or of 8 on levels of at most
+// kTopoWideNodes nodes)
+int topo_status_stride(long long n)
+{
+    const long long wide = (n < kTopoWideNodes ? n : kTopoWideNodes) / 8 + 4;
+    const long long narrow = n / 256 + 4;
+    return (int)(wide > narrow ? wide : narrow);
+}
 
 // The scratch layout of a context for n particles: every buffer, in order, each
 // 256-byte aligned.  With base == nullptr only the total is computed.

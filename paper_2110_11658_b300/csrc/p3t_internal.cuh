@@ -52,6 +52,10 @@ __host__ __device__ inline Band fp32_band(float R, float r2)
 
 // ---- key sort: items per block of the radix-sort passes (256 threads x 4) -----
 constexpr int kSortTileItems = 1024;
+// A tree level with at most this many nodes (the top of the tree: few nodes of
+// many particles) is split one node per warp, tiles of 8 nodes; deeper levels
+// one node per thread, tiles of 256.
+constexpr int kTopoWideNodes = 4096;
 
 // ---- device metadata block (one per context) -------------------------------
 struct Meta {
