@@ -904,6 +904,122 @@ __device__ void internal_moments(Tree &T, int k, int4 tp, double theta)
     write_node<Q64>(T, k, M, com, lo, hi, q, theta, tp);
 }
 
+// The internal node k of the mixed form on three lanes, lane d doing dimension
+// d of every FP64 step (the same operations in the same order as
+// internal_moments<false> + write_node<false>; M and the steps after the box are
+// repeated on the three lanes).  A warp issues about a third of the FP64
+// instructions of one node per lane for the same 32 / 3 nodes' worth of work, and
+// the chain of a level with few nodes is a third as long.  Every lane of the warp
+// calls this (the shuffles); act: the lane holds dimension d of node k.
+__device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool act, int d, int lane0)
+{
+    auto sh = [&](double v, int j) { return __shfl_sync(0xffffffffu, v, lane0 + j); };
+    auto shf = [&](float v, int j) { return __shfl_sync(0xffffffffu, v, lane0 + j); };
+    auto comp = [&](const double4_32a &v) { return d == 0 ? v.x : (d == 1 ? v.y : v.z); };
+    const int c0 = tp.z, nc = act ? tp.w : 0;
+    double M = 0.0, S = 0.0;
+    unsigned long long elo = ~0ULL, ehi = 0ULL;
+    double4_32a cm[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+        if (i < nc) cm[i] = ldcg_d4(&T.comM[c0 + i]);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        if (i < nc) {
+            const double4_32a cl = ldcg_d4(&T.lo[c0 + i]);
+            const double4_32a ch = ldcg_d4(&T.hi[c0 + i]);
+            M = dadd(M, cm[i].w);
+            S = dadd(S, dmul(cm[i].w, comp(cm[i])));
+            const unsigned long long a = enc_double(comp(cl)), b = enc_double(comp(ch));
+            elo = a < elo ? a : elo;
+            ehi = b > ehi ? b : ehi;
+        }
+    }
+    const double lo = dec_double(elo), hi = dec_double(ehi);
+    const double com = M > 0.0 ? ddiv(S, M) : dmul(0.5, dadd(lo, hi));
+    // quadrupole from the children (FP32): each lane's offsets, then all three
+    float Q[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const float dd = i < nc ? __double2float_rn(dsub(comp(cm[i]), com)) : 0.f;
+        const float dx = shf(dd, 0), dy = shf(dd, 1), dz = shf(dd, 2);
+        if (i < nc) {
+            const float *Qc = T.q32 + 6 * (size_t)(c0 + i);
+            const float Mc = (float)cm[i].w;
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            Q[0] += __ldcg(Qc + 0) + Mc * (3.f * dx * dx - d2);
+            Q[1] += __ldcg(Qc + 1) + Mc * (3.f * dx * dy);
+            Q[2] += __ldcg(Qc + 2) + Mc * (3.f * dx * dz);
+            Q[3] += __ldcg(Qc + 3) + Mc * (3.f * dy * dy - d2);
+            Q[4] += __ldcg(Qc + 4) + Mc * (3.f * dy * dz);
+            Q[5] += __ldcg(Qc + 5) + Mc * (3.f * dz * dz - d2);
+        }
+    }
+    // opening radius l/theta + delta (rule 8)
+    const double side = dsub(hi, lo);
+    const double sx = sh(side, 0), sy = sh(side, 1), sz = sh(side, 2);
+    double l = sx;
+    if (sy > l) l = sy;
+    if (sz > l) l = sz;
+    const double c = dsub(dmul(0.5, dadd(lo, hi)), com);
+    const double c2 = dmul(c, c);
+    const double cx2 = sh(c2, 0), cy2 = sh(c2, 1), cz2 = sh(c2, 2);
+    const Cluster &K = T.cl[T.cid_s[act && tp.x < T.n ? tp.x : 0]];
+    const double theta = K.theta;
+    double ro2 = INFINITY;
+    if (act) {
+        const double delta = dsqrt(dadd(dadd(cx2, cy2), cz2));
+        if (theta > 0.0) {
+            const double ro = dadd(ddiv(l, theta), delta);
+            ro2 = dmul(ro, ro);
+        }
+    }
+    // relative to the cluster's frame O: the double-single COM and the FP32 box
+    const double O = K.frame[d];
+    float ch, cl;
+    ds_split(dsub(com, O), ch, cl);
+    const float blo = __double2float_rn(dsub(lo, O)), bhi = __double2float_rn(dsub(hi, O));
+    const double cx = sh(com, 0), cy = sh(com, 1), cz = sh(com, 2);
+    const double lx = sh(lo, 0), ly = sh(lo, 1), lz = sh(lo, 2);
+    const double hx = sh(hi, 0), hy = sh(hi, 1), hz = sh(hi, 2);
+    const float chx = shf(ch, 0), chy = shf(ch, 1), chz = shf(ch, 2);
+    const float clx = shf(cl, 0), cly = shf(cl, 1), clz = shf(cl, 2);
+    const float blx = shf(blo, 0), bly = shf(blo, 1), blz = shf(blo, 2);
+    const float bhx = shf(bhi, 0), bhy = shf(bhi, 1), bhz = shf(bhi, 2);
+    if (act && d == 0) {
+        T.comM[k] = make_double4_32a(cx, cy, cz, M);
+        T.lo[k] = make_double4_32a(lx, ly, lz, ro2);
+        T.hi[k] = make_double4_32a(hx, hy, hz, 0.0);
+        float2 *q2 = reinterpret_cast<float2 *>(T.q32 + 6 * (size_t)k);
+        q2[0] = make_float2(Q[0], Q[1]);
+        q2[1] = make_float2(Q[2], Q[3]);
+        q2[2] = make_float2(Q[4], Q[5]);
+        float4 *w = T.wn + (size_t)kWalkRecord * k;
+        w[0] = make_float4(chx, chy, chz, __double2float_rn(ro2));
+        w[1] = make_float4(blx, bly, blz, __int_as_float(tp.z));
+        w[2] = make_float4(bhx, bhy, bhz, __int_as_float(tp.w));
+        w[3] = make_float4(clx, cly, clz, __double2float_rn(M));
+        w[4] = make_float4(Q[0], Q[1], Q[2], Q[3]);
+        w[5] = make_float4(Q[4], Q[5], 0.f, 0.f);
+    }
+}
+
+// internal nodes of level l in the mixed form, ten nodes a warp (three lanes each)
+__global__ void __launch_bounds__(kBuildThreads) moments_level3_kernel(Tree T, int l)
+{
+    const int b = T.meta->level_start[l], e = b + T.meta->level_count[l];
+    const int lane = threadIdx.x & 31;
+    const int slot = lane / 3, d = lane - 3 * slot;  // lanes 30, 31: slot 10, idle
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int k0 = b + 10 * warp; k0 < e; k0 += 10 * nwarps) {
+        const int k = k0 + slot;
+        const bool in = slot < 10 && k < e;
+        const int4 tp = in ? T.topo[k] : make_int4(0, 0, -1, 0);
+        internal_moments3(T, k, tp, in && tp.z >= 0, slot < 10 ? d : 0, slot < 10 ? 3 * slot : 0);
+    }
+}
+
 // leaves first (one thread per leaf), then the internal nodes level by level,
 // deepest first, each from its children in octant order; every pass keeps
 // whole warps busy (FP64 instructions cost the same for one lane as for 32)
@@ -1011,7 +1127,7 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
         if (q64)
             moments_level_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, l, P.theta);
         else
-            moments_level_kernel<false><<<persistent, kBuildThreads, 0, s>>>(T, l, P.theta);
+            moments_level3_kernel<<<persistent, kBuildThreads, 0, s>>>(T, l);
     }
     return check_launch(c);
 }
