@@ -338,6 +338,7 @@ struct NbrCount {
     int wc[TPL];
     unsigned hit[TPL];  // neighbours among the 32 staged sources (bit = staging slot)
     int cap;
+    bool beyond;   // the group's cluster lists neighbours beyond r_out (r_list > r_out)
     float lo, hi;  // r2 < lo: neighbour; r2 > hi: not; otherwise decide in FP64
     // |r2 - mid| <= rad covers [lo, hi] (the rare undecided band) with a 2x margin,
     // so rounding of mid and of r2 - mid cannot leave a band pair out
@@ -516,10 +517,49 @@ __device__ __forceinline__ void eval_cells_x2(const WarpSmem<float> &W, int ncel
     __syncwarp();
 }
 
-// One pair of staged particles (k: pair index) against this lane's targets.
-template <int TPL, bool POT, int NBR, bool TAIL>
+// The neighbour test of one pair of staged particles against target t: neighbour
+// iff |x_j - x_i|^2 < r_list^2 in FP64.  Below the band in FP32 counts at once;
+// inside it (rare), the FP64 operations decide.  The pair with itself is counted
+// (r2 = 0) and removed at the end.
+template <int TPL, int NBR, bool TAIL>
+__device__ __forceinline__ void pair_nbr(const WarpSmem<float> &W, const Tree &T, const Cluster &K, int k,
+                                         int ns, int t, float2 r2, NbrCount<TPL> &NC)
+{
+    const bool yreal = !TAIL || 2 * k + 1 < ns;
+    bool in0 = r2.x < NC.lo, in1 = yreal && r2.y < NC.lo;
+    const float2 d = fadd2(r2, f2(-NC.mid));
+    if (fminf(fabsf(d.x), fabsf(d.y)) <= NC.rad) {
+#pragma unroll
+        for (int e = 0; e < 2; e++) {
+            const float r2e = e ? r2.y : r2.x;
+            if ((e == 0 || yreal) && r2e >= NC.lo && r2e <= NC.hi) {
+                const int sj = W.pj[2 * k + e];
+                const double4_32a a = T.sp[NC.si[t] < 0 ? sj : NC.si[t]], b = T.sp[sj];
+                const double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
+                const bool in = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < K.rl2_d;
+                if (e)
+                    in1 = in;
+                else
+                    in0 = in;
+            }
+        }
+    }
+    if constexpr (NBR == 2)  // rows written once per staged chunk (write_rows)
+        NC.hit[t] |= ((unsigned)in0 | ((unsigned)in1 << 1)) << (2 * k);
+    else
+        NC.cnt[t] += (int)in0 + (int)in1;
+}
+
+// One pair of staged particles (k: pair index) against this lane's targets.  A
+// pair whose two sources come from leaves beyond r_out of the group box (or pads of
+// mass 0; a clear bit pair in wm) has r >= r_out for every target: W = 1 exactly.
+// Its sources may hold neighbours only if the cluster lists neighbours beyond r_out
+// (bits in cm).  wm and cm are ballots over the staged slots, so the branches are
+// warp-uniform.  ALL_FAR: wm = cm = 0 for the whole chunk (no branch at all).
+template <int TPL, bool POT, int NBR, bool SHELL, bool TAIL, bool ALL_FAR = false>
 __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &T, const Cluster &K,
-                                          const float4 *pq, int k, int ns, unsigned cm, float inv_dr,
+                                          const float4 *pq, int k, int ns, unsigned wm, unsigned cm,
+                                          float inv_dr,
                                           float nrin_dr,
                                           const float2 (&NPX)[TPL], const float2 (&NPY)[TPL],
                                           const float2 (&NPZ)[TPL], AccX2<TPL> &A, NbrCount<TPL> &NC)
@@ -527,6 +567,7 @@ __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &
     const float4 b0 = pq[2 * k], b1 = pq[2 * k + 1];
     const float2 X = make_float2(b0.x, b0.y), Y = make_float2(b0.z, b0.w);
     const float2 Z = make_float2(b1.x, b1.y), Mj = make_float2(b1.z, b1.w);
+    const bool far = ALL_FAR || ((wm >> (2 * k)) & 3u) == 0u;
 #pragma unroll
     for (int t = 0; t < TPL; t++) {
         // d = x_j - x_i
@@ -535,17 +576,36 @@ __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &
         r2 = ffma2(dy, dy, r2);
         r2 = ffma2(dz, dz, r2);
         const float2 ri = make_float2(rsqrtf(fmaxf(r2.x, kR2Min)), rsqrtf(fmaxf(r2.y, kR2Min)));
-        const float2 r = fmul2(r2, ri);
-        // x = (r - r_in)/(r_out - r_in) clamped to [0, 1]
-        const float2 x = make_float2(__saturatef(fmaf(r.x, inv_dr, nrin_dr)),
-                                     __saturatef(fmaf(r.y, inv_dr, nrin_dr)));
-        float2 w = ffma2(f2(-20.f), x, f2(70.f));
-        w = ffma2(w, x, f2(-84.f));
-        w = ffma2(w, x, f2(35.f));
-        const float2 x2 = fmul2(x, x);
-        const float2 Wt = fmul2(w, fmul2(x2, x2));
         const float2 ri3 = fmul2(fmul2(ri, ri), ri);
-        const float2 f = fmul2(fmul2(Mj, Wt), ri3);
+        // W(r): x = (r - r_in)/(r_out - r_in) clamped to [0, 1], x^4 (35 - 84x + 70x^2 - 20x^3)
+        auto weight = [&]() {
+            const float2 r = fmul2(r2, ri);
+            const float2 x = make_float2(__saturatef(fmaf(r.x, inv_dr, nrin_dr)),
+                                         __saturatef(fmaf(r.y, inv_dr, nrin_dr)));
+            float2 w = ffma2(f2(-20.f), x, f2(70.f));
+            w = ffma2(w, x, f2(-84.f));
+            w = ffma2(w, x, f2(35.f));
+            const float2 x2 = fmul2(x, x);
+            return fmul2(w, fmul2(x2, x2));
+        };
+        float2 f;
+        if constexpr (ALL_FAR) {
+            f = fmul2(Mj, ri3);
+        } else if constexpr (NBR == 1) {
+            // the counting walk stays straight-line (a branch per pair measured slower
+            // there): every pair's weight, then W = 1 for far pairs as in the other walks
+            const float2 fw = fmul2(fmul2(Mj, weight()), ri3);
+            const float2 f1 = fmul2(Mj, ri3);
+            f = far ? f1 : fw;
+        } else if (far) {
+            f = fmul2(Mj, ri3);
+            if constexpr (NBR == 2 && SHELL)  // neighbours beyond r_out (r_list > r_out) only
+                if ((cm >> (2 * k)) & 3u) pair_nbr<TPL, NBR, TAIL>(W, T, K, k, ns, t, r2, NC);
+        } else {
+            f = fmul2(fmul2(Mj, weight()), ri3);
+            if constexpr (NBR == 2)  // the row-mode walk tests the pairs that may hold neighbours
+                pair_nbr<TPL, NBR, TAIL>(W, T, K, k, ns, t, r2, NC);
+        }
         A.p[t][0] = ffma2(f, dx, A.p[t][0]);
         A.p[t][1] = ffma2(f, dy, A.p[t][1]);
         A.p[t][2] = ffma2(f, dz, A.p[t][2]);
@@ -553,41 +613,13 @@ __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &
             A.p[t][3].x -= r2.x > 0.f ? Mj.x * ri.x : 0.f;
             A.p[t][3].y -= r2.y > 0.f ? Mj.y * ri.y : 0.f;
         }
-        // (a pair from leaves beyond r_out holds no neighbour; the row-mode walk skips
-        // their test, the counting walk runs it straight-line, which measured faster)
-        if (NBR && (NBR == 1 || ((cm >> (2 * k)) & 3u))) {
-            // neighbour iff |x_j - x_i|^2 < r_list^2 in FP64: below the band in FP32
-            // counts at once, inside it (rare) is decided with the FP64 operations; the
-            // pair with itself is counted (r2 = 0) and removed at the end
-            const bool yreal = !TAIL || 2 * k + 1 < ns;
-            bool in0 = r2.x < NC.lo, in1 = yreal && r2.y < NC.lo;
-            const float2 d = fadd2(r2, f2(-NC.mid));
-            if (fminf(fabsf(d.x), fabsf(d.y)) <= NC.rad) {
-#pragma unroll
-                for (int e = 0; e < 2; e++) {
-                    const float r2e = e ? r2.y : r2.x;
-                    if ((e == 0 || yreal) && r2e >= NC.lo && r2e <= NC.hi) {
-                        const int sj = W.pj[2 * k + e];
-                        const double4_32a a = T.sp[NC.si[t] < 0 ? sj : NC.si[t]], b = T.sp[sj];
-                        const double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
-                        const bool in = dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)) < K.rl2_d;
-                        if (e)
-                            in1 = in;
-                        else
-                            in0 = in;
-                    }
-                }
-            }
-            if constexpr (NBR == 2)  // rows written once per staged chunk (write_rows)
-                NC.hit[t] |= ((unsigned)in0 | ((unsigned)in1 << 1)) << (2 * k);
-            else
-                NC.cnt[t] += (int)in0 + (int)in1;
-        }
+        if constexpr (NBR == 1 && !ALL_FAR)  // the counting walk tests every pair, straight-line
+            pair_nbr<TPL, NBR, TAIL>(W, T, K, k, ns, t, r2, NC);
     }
 }
 
 // Mixed form, two staged particles at a time; same terms as eval_parts.
-template <int TPL, bool POT, int NBR>
+template <int TPL, bool POT, int NBR, bool SHELL>
 __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const WalkArgs &P,
                                               const Cluster &K, int nleaves, int nparts,
                                               const GroupFrame &F, const float (&px)[TPL],
@@ -614,7 +646,8 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
     for (int c0 = 0; c0 < nparts; c0 += 32) {
         int pos = c0 + lane;
         const int ns = min(32, nparts - c0);
-        bool cand = false;  // may be a neighbour of a target of the group
+        bool wneed = false;  // not from a leaf beyond r_out: the weight W(r) is needed
+        bool cand = false;   // may be a neighbour of a target of the group
         if (pos < nparts) {
             int lo = 0, hi = nleaves;  // last leaf with lqo <= pos
             while (hi - lo > 1) {
@@ -627,7 +660,8 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
             // bit 31: neighbour-only leaf (staged with mass 0); bit 30: leaf beyond r_out
             const int lx = W.lq[lo].x;
             const int j = (lx & 0x3fffffff) + (pos - W.lqo[lo]);
-            cand = (lx & (int)kFarLeaf) == 0;
+            wneed = (lx & (int)kFarLeaf) == 0;
+            cand = wneed || (SHELL && NC.beyond);
             const float4 r = ds_rel(P.T.ph[j], P.T.pl[j], F);
             pb[0] = r.x, pb[2] = r.y, pb[4] = r.z, pb[6] = lx < 0 ? 0.f : r.w;
             if (NBR) W.pj[lane] = j;
@@ -640,14 +674,30 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
             b[1] = b[0], b[3] = b[2], b[5] = b[4], b[7] = 0.f;
         }
         __syncwarp();
-        const unsigned cm = __ballot_sync(0xffffffffu, cand);  // slots to test as neighbours
+        // slots that need the weight polynomial (a slot from a leaf beyond r_out has
+        // W = 1) and slots that may hold neighbours (the same unless the cluster
+        // lists neighbours beyond r_out)
+        const unsigned wm = __ballot_sync(0xffffffffu, wneed);
+        const unsigned cm = NBR && SHELL ? __ballot_sync(0xffffffffu, cand) : wm;
         const int nfull = ns >> 1;
+        if ((wm | cm) == 0u) {
+            // every source of the chunk from a leaf beyond r_out: W = 1, no neighbour
 #pragma unroll kPartPairUnroll
-        for (int k = 0; k < nfull; k++)
-            part_pair<TPL, POT, NBR, false>(W, P.T, K, pq, k, ns, cm, inv_dr, nrin_dr, NPX, NPY, NPZ, A, NC);
-        if (ns & 1)  // the last pair holds the zero-mass pad
-            part_pair<TPL, POT, NBR, true>(W, P.T, K, pq, nfull, ns, cm, inv_dr, nrin_dr, NPX, NPY, NPZ, A,
-                                           NC);
+            for (int k = 0; k < nfull; k++)
+                part_pair<TPL, POT, NBR, SHELL, false, true>(W, P.T, K, pq, k, ns, wm, cm, inv_dr, nrin_dr, NPX, NPY, NPZ,
+                                                      A, NC);
+            if (ns & 1)
+                part_pair<TPL, POT, NBR, SHELL, true, true>(W, P.T, K, pq, nfull, ns, wm, cm, inv_dr, nrin_dr, NPX, NPY,
+                                                     NPZ, A, NC);
+        } else {
+#pragma unroll kPartPairUnroll
+            for (int k = 0; k < nfull; k++)
+                part_pair<TPL, POT, NBR, SHELL, false>(W, P.T, K, pq, k, ns, wm, cm, inv_dr, nrin_dr, NPX, NPY, NPZ, A,
+                                                NC);
+            if (ns & 1)  // the last pair holds the zero-mass pad
+                part_pair<TPL, POT, NBR, SHELL, true>(W, P.T, K, pq, nfull, ns, wm, cm, inv_dr, nrin_dr, NPX, NPY, NPZ,
+                                               A, NC);
+        }
         if constexpr (NBR == 2) {
             // the chunk's neighbours of each target: counted (the target itself
             // included, removed at the end) and appended to its row but for itself;
@@ -683,14 +733,14 @@ __device__ __forceinline__ void eval_cells_any(const WarpSmem<Real> &W, int ncel
         eval_cells<Real, TPL, POT, QUAD>(W, ncells, px, py, pz, A);
 }
 
-template <typename Real, int TPL, bool POT, int NBR, typename AccT>
+template <typename Real, int TPL, bool POT, int NBR, bool SHELL, typename AccT>
 __device__ __forceinline__ void eval_parts_any(const WarpSmem<Real> &W, const WalkArgs &P, const Cluster &K,
                                                int nleaves, int nparts, const GroupFrame &F,
                                                const Real (&px)[TPL], const Real (&py)[TPL],
                                                const Real (&pz)[TPL], AccT &A, NbrCount<TPL> &NC)
 {
     if constexpr (sizeof(Real) == 4)
-        eval_parts_x2<TPL, POT, NBR>(W, P, K, nleaves, nparts, F, px, py, pz, A, NC);
+        eval_parts_x2<TPL, POT, NBR, SHELL>(W, P, K, nleaves, nparts, F, px, py, pz, A, NC);
     else
         eval_parts<Real, TPL, POT, NBR>(W, P, K, nleaves, nparts, F, px, py, pz, A, NC);
 }
@@ -763,6 +813,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         }
         Real px[TPL], py[TPL], pz[TPL];
         NbrCount<TPL> NC;
+        NC.beyond = false;
         float amax = 0.f;
 #pragma unroll
         for (int t = 0; t < TPL; t++) {
@@ -800,6 +851,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
             const float band = kU * (24.f * K.rl2_f + 32.f * A * K.rl_f + 128.f * kU * Rf * K.rl_f) +
                                64.f * kU * kU * (A + 2.f * K.rl_f) * (A + 2.f * K.rl_f);
             NC.cap = P.row_cap;
+            NC.beyond = shell;
             if (!count_here)
                 NC.off();  // this cluster is counted elsewhere
             else if (filter_ok)
@@ -831,7 +883,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
 
             // ---- opening test (test and staging data come in one load batch)
             bool open = false, is_leaf = false, in_shell = false;
-            bool beyond = false;  // box certainly r_out or more from the group box: no neighbour
+            bool beyond = false;  // box certainly r_out or more from the group box: W = 1
             int cinfo = 0, ccount = 0;
             float4 ra, rd, rq0, rq1;  // node record: COM hi / lo + M / quadrupole
             if (node >= 0) {
@@ -868,7 +920,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                         in_b = db < 0.f;
                     }
                     // (with r_list > r_out a force leaf beyond r_out may still hold neighbours)
-                    beyond = !SHELL && dec_b && !in_b;
+                    beyond = dec_b && !in_b;
                     if (SHELL && nbr_only) {
                         // neighbour-only range: the box test against r_list alone
                         bool dec_l = false, in_l = false;
@@ -1008,12 +1060,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                 cb = 0;
             }
             if (lqp >= tile) {
-                eval_parts_any<Real, TPL, POT, NBR>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
+                eval_parts_any<Real, TPL, POT, NBR, SHELL>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
                 lqn = lqp = 0;
             }
         }
         if (cb > 0) eval_cells_any<Real, TPL, POT, QUAD>(W, cb, px, py, pz, A);
-        if (lqp > 0) eval_parts_any<Real, TPL, POT, NBR>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
+        if (lqp > 0) eval_parts_any<Real, TPL, POT, NBR, SHELL>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
 
         // ---- results, scattered to the original order
 #pragma unroll
