@@ -242,10 +242,16 @@ int p3t_irregular(p3t_ctx *c, int64_t n, const int64_t *offsets, const int32_t *
  * by exact FP64 squared distance (dx*dx + dy*dy) + dz*dz, ties broken by the
  * smaller original index, ascending: nn_idx device int32[s*6] (original
  * indices; -1 where fewer than 6 exist), nn_d2 device double[s*6] (inf there).
- * Uses a scratch buffer of the context (allocated on first use, ~72 bytes per
- * sampled particle and chunk).  Errors: P3T_ERR_ORDER without a one-cluster
- * tree of these n particles; a sample index outside [0, n) latches
- * P3T_ERR_INVALID_INPUT (its row is left unset).
+ * The search walks the built tree, pruning nodes whose box lies beyond an
+ * upper bound of the 6th distance; the lists equal those of a brute-force
+ * search.  Errors: P3T_ERR_ORDER without a one-cluster tree of these n
+ * particles; a sample index outside [0, n) latches P3T_ERR_INVALID_INPUT (its
+ * row is left unset).
+ *
+ * p3t_sample_knn6_brute: the same lists by the paper's brute-force search,
+ * every sampled particle against every particle.  Uses a scratch buffer of the
+ * context (allocated on first use, ~72 bytes per sampled particle and chunk of
+ * candidates).  Same arguments and errors.
  *
  * p3t_core_quantities: from those neighbours (device arrays in original order
  * x, y, z, m of n particles): rho[t] = 3 (mass of the 5 nearest) / (4 pi r_6^3)
@@ -257,6 +263,8 @@ int p3t_irregular(p3t_ctx *c, int64_t n, const int64_t *offsets, const int32_t *
  * Both calls are asynchronous on the context's stream. */
 int p3t_sample_knn6(p3t_ctx *c, int64_t n, int64_t s, const int32_t *sample, int32_t *nn_idx,
                     double *nn_d2);
+int p3t_sample_knn6_brute(p3t_ctx *c, int64_t n, int64_t s, const int32_t *sample, int32_t *nn_idx,
+                          double *nn_d2);
 int p3t_core_quantities(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
                         const double *m, int64_t s, const int32_t *sample, const int32_t *nn_idx,
                         const double *nn_d2, double *rho, double *out);

@@ -41,7 +41,7 @@ EXPORTED = [
     "p3t_set_debug", "p3t_error_string", "p3t_morton_order_noalloc",
     "p3t_graph_capture", "p3t_graph_launch", "p3t_graph_destroy", "p3t_reserve", "p3t_scratch_bytes",
     "p3t_batch_move", "p3t_batch_scatter_neighbours", "p3t_filter_fallbacks", "p3t_irregular",
-    "p3t_sample_knn6", "p3t_core_quantities", "p3t_row_mode",
+    "p3t_sample_knn6", "p3t_sample_knn6_brute", "p3t_core_quantities", "p3t_row_mode",
 ]
 P3T_NOALLOC_MAX_N = 65536
 
@@ -109,6 +109,7 @@ _sig = {
     "p3t_row_mode": [_vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "p3t_irregular": [_vp, _i64] + [_vp] * 15,
     "p3t_sample_knn6": [_vp, _i64, _i64, _vp, _vp, _vp],
+    "p3t_sample_knn6_brute": [_vp, _i64, _i64, _vp, _vp, _vp],
     "p3t_core_quantities": [_vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp],
     "p3t_scratch_bytes": [C.POINTER(p3t_params), _i64, C.c_int32, C.POINTER(_i64)],
     "p3t_batch_move": [_vp, C.c_int32, _i64, _vp, _vp, C.c_int32, C.POINTER(p3t_seg_array), C.c_int32],
@@ -377,16 +378,19 @@ class Context:
                                   *args, *outs), "p3t_irregular")
         return f, jerk
 
-    def sample_knn6(self, sample, n=None):
-        """6 nearest neighbours of the sampled particles (p3t_sample_knn6) among the
-        particles of the last build: (idx (s, 6) int32, d2 (s, 6) float64) CUDA tensors."""
+    def sample_knn6(self, sample, n=None, brute=False):
+        """6 nearest neighbours of the sampled particles among the particles of the
+        last build: (idx (s, 6) int32, d2 (s, 6) float64) CUDA tensors.  The tree
+        search (p3t_sample_knn6), or with brute=True the brute-force search
+        (p3t_sample_knn6_brute); the lists are the same."""
         t = self._torch
         n = self.n if n is None else n
         s = sample.numel()
         idx = t.empty(s, 6, dtype=t.int32, device=sample.device)
         d2 = t.empty(s, 6, dtype=t.float64, device=sample.device)
-        _check(_lib.p3t_sample_knn6(self._h, n, s, _ptr(sample, t.int32, s, "sample"), idx.data_ptr(),
-                                    d2.data_ptr()), "p3t_sample_knn6")
+        name = "p3t_sample_knn6_brute" if brute else "p3t_sample_knn6"
+        _check(getattr(_lib, name)(self._h, n, s, _ptr(sample, t.int32, s, "sample"), idx.data_ptr(),
+                                   d2.data_ptr()), name)
         return idx, d2
 
     def core_quantities(self, x, y, z, m, sample, idx6, d26):

@@ -3,17 +3,23 @@
 // particle's 6 nearest neighbours, and the density estimator and
 // density-weighted averages of Casertano & Hut, which the paper cites).
 //
-// Search: every sampled particle against every particle of the built tree
-// (one cluster).  Blocks pair 128 sampled particles with one chunk of
-// candidates in key order, staged through shared memory.  Each candidate is
-// first tested in FP32 on double-single coordinates relative to the frame
-// centre (the hi parts of the tree's splits, two candidates per packed FP32x2
-// instruction): a candidate whose FP32 squared distance exceeds an upper bound
-// of the current 6th distance, widened by the filter's error, cannot enter the
-// list;
-// the others are decided with the exact FP64 distance (dx*dx + dy*dy) + dz*dz
-// and inserted by (distance, original index).  A second kernel merges the
-// chunks' lists.  The result is unique, so it equals the oracle's bit for bit.
+// Search (p3t_sample_knn6): one thread per sampled particle walks the built
+// tree (one cluster) depth first.  It opens a node unless the FP32 distance from
+// the particle to the node's box exceeds the filter threshold below, and tests
+// the particles of the opened leaves.  A node whose box lies beyond an upper
+// bound of the 6th distance holds no candidate, so the result is that of the
+// brute-force search, which p3t_sample_knn6_brute performs as the paper does:
+// every sampled particle against every particle, blocks pairing 128 sampled
+// particles with one chunk of candidates in key order (staged through shared
+// memory), a second kernel merging the chunks' lists.
+//
+// Both test each candidate first in FP32 on double-single coordinates relative
+// to the frame centre (the hi parts of the tree's splits; the brute-force scan
+// takes two candidates per packed FP32x2 instruction): a candidate whose FP32
+// squared distance exceeds an upper bound of the current 6th distance, widened
+// by the filter's error, cannot enter the list.  The others are decided with the
+// exact FP64 distance (dx*dx + dy*dy) + dz*dz and inserted by (distance,
+// original index).  The result is unique, so it equals the oracle's bit for bit.
 #include <cstdint>
 #include <cmath>
 
@@ -186,6 +192,92 @@ __global__ void knn_merge_kernel(KnnArgs a, int32_t *nn_idx, double *nn_d2)
     }
 }
 
+// The 6 nearest neighbours of sampled particle t by a depth-first walk of the
+// tree.  A point-box test in FP32 on the walk record's box (relative to the
+// frame centre) and the hi part of the particle's split has the same error as
+// the candidates' filter (each coordinate difference within 2u R + u of itself
+// of the exact one; max(., 0) adds none), so a node whose FP32 box distance
+// exceeds the threshold holds no particle within the bound.
+constexpr int kKnnStack = 192;  // 7 open siblings a level over 22 levels, and the root
+__global__ void __launch_bounds__(kKnnThreads) knn_tree_kernel(Tree T, int n, int s,
+                                                               const int32_t *sample,
+                                                               int32_t *nn_idx, double *nn_d2)
+{
+    const int t = blockIdx.x * kKnnThreads + threadIdx.x;
+    if (t >= s) return;
+    const int me = sample[t];
+    if ((unsigned)me >= (unsigned)n) {  // not a particle: no list
+        latch_error(T.meta, P3T_ERR_INVALID_INPUT);
+        return;
+    }
+    const int km = T.inv[me];
+    const float4 h = T.ph[km];
+    const double4_32a p = T.sp[km];
+    const float eR = 4.f * kFp32U * (float)T.cl[0].frame[3];
+    double bd[kKnn];
+    int bi[kKnn];
+    // upper bound of the 6th distance from the 32 particles next in key order
+#pragma unroll
+    for (int q = 0; q < kKnn; q++) bd[q] = INFINITY, bi[q] = 0x7fffffff;
+    {
+        const int lo = max(0, km - 16), hi = min(n, km + 17);
+        for (int kj = lo; kj < hi; kj++) {
+            if (kj == km) continue;
+            const double4_32a pj = T.sp[kj];
+            const double ex = dsub(pj.x, p.x), ey = dsub(pj.y, p.y), ez = dsub(pj.z, p.z);
+            knn_insert(bd, bi, dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)), kj);
+        }
+    }
+    const double bound = bd[kKnn - 1];
+#pragma unroll
+    for (int q = 0; q < kKnn; q++) bd[q] = INFINITY, bi[q] = 0x7fffffff;
+    float thr = knn_threshold(bound, eR);
+    int stk[kKnnStack];
+    int sp = 0;
+    stk[sp++] = 0;  // the root of the one cluster
+    const int nn = T.meta->n_nodes;
+    while (sp > 0) {
+        const int node = stk[--sp];
+        const float4 *w = T.wn + (size_t)kWalkRecord * node;
+        const float4 b = w[1], c = w[2];  // box lo - O and child / particle start; box hi - O and count
+        const float tx = fmaxf(fmaxf(b.x - h.x, h.x - c.x), 0.f);
+        const float ty = fmaxf(fmaxf(b.y - h.y, h.y - c.y), 0.f);
+        const float tz = fmaxf(fmaxf(b.z - h.z, h.z - c.z), 0.f);
+        if (tx * tx + ty * ty + tz * tz > thr) continue;
+        const int info = __float_as_int(b.w), cnt = __float_as_int(c.w);
+        if (info < 0) {  // leaf: particles [-1 - info, + cnt) in key order
+            const int k0 = -1 - info;
+            if (cnt < 1 || k0 + cnt > n) {
+                latch_error(T.meta, P3T_ERR_INTERNAL);
+                break;
+            }
+            for (int kj = k0; kj < k0 + cnt; kj++) {
+                const float4 hj = T.ph[kj];
+                const float dx = hj.x - h.x, dy = hj.y - h.y, dz = hj.z - h.z;
+                if (dx * dx + dy * dy + dz * dz > thr) continue;
+                const int oj = T.perm[kj];
+                if (oj == me) continue;
+                const double4_32a pj = T.sp[kj];
+                const double ex = dsub(pj.x, p.x), ey = dsub(pj.y, p.y), ez = dsub(pj.z, p.z);
+                knn_insert(bd, bi, dadd(dadd(dmul(ex, ex), dmul(ey, ey)), dmul(ez, ez)), oj);
+                thr = knn_threshold(fmin(bd[kKnn - 1], bound), eR);
+            }
+        } else {
+            if (cnt < 1 || cnt > 8 || info + cnt > nn || sp + cnt > kKnnStack) {
+                latch_error(T.meta, P3T_ERR_INTERNAL);
+                break;
+            }
+            for (int q = cnt - 1; q >= 0; q--) stk[sp++] = info + q;  // octant 0 on top
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kKnn; q++) {
+        const bool found = bd[q] < INFINITY;
+        nn_idx[(size_t)t * kKnn + q] = found ? bi[q] : -1;
+        nn_d2[(size_t)t * kKnn + q] = bd[q];
+    }
+}
+
 // ---- core quantities (one block, fixed reduction order) ---------------------
 constexpr int kCoreThreads = 1024;
 
@@ -296,6 +388,16 @@ extern "C" {
 
 int p3t_sample_knn6(p3t_ctx *c, int64_t n, int64_t s, const int32_t *sample, int32_t *nn_idx,
                     double *nn_d2)
+{
+    if (!c || !sample || !nn_idx || !nn_d2 || n <= 0 || s <= 0 || s > n) return P3T_ERR_INVALID_ARG;
+    if (!c->built || c->n != n || c->tree.n_clusters != 1) return P3T_ERR_ORDER;
+    knn_tree_kernel<<<(int)((s + kKnnThreads - 1) / kKnnThreads), kKnnThreads, 0, c->stream>>>(
+        c->tree, (int)n, (int)s, sample, nn_idx, nn_d2);
+    return check_launch(c);
+}
+
+int p3t_sample_knn6_brute(p3t_ctx *c, int64_t n, int64_t s, const int32_t *sample, int32_t *nn_idx,
+                          double *nn_d2)
 {
     if (!c || !sample || !nn_idx || !nn_d2 || n <= 0 || s <= 0 || s > n) return P3T_ERR_INVALID_ARG;
     if (!c->built || c->n != n || c->tree.n_clusters != 1) return P3T_ERR_ORDER;
