@@ -555,8 +555,9 @@ __device__ __forceinline__ void pair_nbr(const WarpSmem<float> &W, const Tree &T
 // mass 0; a clear bit pair in wm) has r >= r_out for every target: W = 1 exactly.
 // Its sources may hold neighbours only if the cluster lists neighbours beyond r_out
 // (bits in cm).  wm and cm are ballots over the staged slots, so the branches are
-// warp-uniform.  ALL_FAR: wm = cm = 0 for the whole chunk (no branch at all).
-template <int TPL, bool POT, int NBR, bool SHELL, bool TAIL, bool ALL_FAR = false>
+// warp-uniform.  ALL_FAR: wm = cm = 0 for the whole chunk; ALL_NEAR: every slot of
+// the chunk needs W (no branch at all in either).
+template <int TPL, bool POT, int NBR, bool SHELL, bool TAIL, bool ALL_FAR = false, bool ALL_NEAR = false>
 __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &T, const Cluster &K,
                                           const float4 *pq, int k, int ns, unsigned wm, unsigned cm,
                                           float inv_dr,
@@ -567,7 +568,7 @@ __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &
     const float4 b0 = pq[2 * k], b1 = pq[2 * k + 1];
     const float2 X = make_float2(b0.x, b0.y), Y = make_float2(b0.z, b0.w);
     const float2 Z = make_float2(b1.x, b1.y), Mj = make_float2(b1.z, b1.w);
-    const bool far = ALL_FAR || ((wm >> (2 * k)) & 3u) == 0u;
+    const bool far = ALL_FAR || (!ALL_NEAR && ((wm >> (2 * k)) & 3u) == 0u);
 #pragma unroll
     for (int t = 0; t < TPL; t++) {
         // d = x_j - x_i
@@ -591,7 +592,7 @@ __device__ __forceinline__ void part_pair(const WarpSmem<float> &W, const Tree &
         float2 f;
         if constexpr (ALL_FAR) {
             f = fmul2(Mj, ri3);
-        } else if constexpr (NBR == 1) {
+        } else if constexpr (NBR == 1 && !ALL_NEAR) {
             // the counting walk stays straight-line (a branch per pair measured slower
             // there): every pair's weight, then W = 1 for far pairs as in the other walks
             const float2 fw = fmul2(fmul2(Mj, weight()), ri3);
@@ -680,7 +681,36 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
         const unsigned wm = __ballot_sync(0xffffffffu, wneed);
         const unsigned cm = NBR && SHELL ? __ballot_sync(0xffffffffu, cand) : wm;
         const int nfull = ns >> 1;
-        if ((wm | cm) == 0u) {
+        if constexpr (NBR == 0) {
+            // the force-only walk (no neighbour work, fewer live registers): deeper
+            // unrolling and a branch-free loop for chunks of near sources too
+            const unsigned all = ns == 32 ? 0xffffffffu : (1u << ns) - 1u;
+            if (wm == 0u) {
+#pragma unroll 4
+                for (int k = 0; k < nfull; k++)
+                    part_pair<TPL, POT, NBR, SHELL, false, true>(W, P.T, K, pq, k, ns, wm, cm, inv_dr, nrin_dr, NPX,
+                                                                 NPY, NPZ, A, NC);
+                if (ns & 1)
+                    part_pair<TPL, POT, NBR, SHELL, true, true>(W, P.T, K, pq, nfull, ns, wm, cm, inv_dr, nrin_dr,
+                                                                NPX, NPY, NPZ, A, NC);
+            } else if (wm == all) {
+#pragma unroll 4
+                for (int k = 0; k < nfull; k++)
+                    part_pair<TPL, POT, NBR, SHELL, false, false, true>(W, P.T, K, pq, k, ns, wm, cm, inv_dr,
+                                                                        nrin_dr, NPX, NPY, NPZ, A, NC);
+                if (ns & 1)
+                    part_pair<TPL, POT, NBR, SHELL, true, false, true>(W, P.T, K, pq, nfull, ns, wm, cm, inv_dr,
+                                                                       nrin_dr, NPX, NPY, NPZ, A, NC);
+            } else {
+#pragma unroll 4
+                for (int k = 0; k < nfull; k++)
+                    part_pair<TPL, POT, NBR, SHELL, false>(W, P.T, K, pq, k, ns, wm, cm, inv_dr, nrin_dr, NPX, NPY,
+                                                           NPZ, A, NC);
+                if (ns & 1)
+                    part_pair<TPL, POT, NBR, SHELL, true>(W, P.T, K, pq, nfull, ns, wm, cm, inv_dr, nrin_dr, NPX,
+                                                          NPY, NPZ, A, NC);
+            }
+        } else if ((wm | cm) == 0u) {
             // every source of the chunk from a leaf beyond r_out: W = 1, no neighbour
 #pragma unroll kPartPairUnroll
             for (int k = 0; k < nfull; k++)
