@@ -671,6 +671,11 @@ def ensemble_run(args):
 
     def batched_graph(cfg, st):
         ctx = p3t.Context(params(cfg), stream)
+        # one synchronous list first, as in the single-cluster step: it sizes the
+        # row scratch, so the captured walks write the neighbour rows (row mode)
+        ctx.build_tree_batch(seg, st["x"], st["y"], st["z"], st["m"], cluster_params=cprm)
+        ctx.far_force(*buf["a"])
+        ctx.neighbours(buf["offs"], buf["idx"])
         g = ctx.capture_step(st["x"], st["y"], st["z"], st["m"], *buf["a"], seg_offsets=seg, cluster_params=cprm,
                              vx=st["vx"], vy=st["vy"], vz=st["vz"], kick_dt=DT, drift_dt=DT,
                              n_cell=buf["nc"], n_part=buf["np"], offsets=buf["offs"], idx=buf["idx"],
@@ -705,6 +710,7 @@ def ensemble_run(args):
     ctx.check()
     inter = (int(buf["nc"].item()) + int(buf["np"].item())) / steps
     nbr_total = int(buf["tot"].item())
+    row_cap, rows_valid = ctx.row_mode()
     # far force alone (eager, same context and tree) for the walk's roofline
     far_ts = _events_ms(stream, lambda: ctx.far_force(*buf["a"]), steps, flush)
     ctx.check()
@@ -720,6 +726,9 @@ def ensemble_run(args):
         ctx.kick(DT, *buf["a"], st["vx"], st["vy"], st["vz"])
         ctx.drift(DT, st["x"], st["y"], st["z"], st["vx"], st["vy"], st["vz"])
 
+    ctx.build_tree_batch(seg, st["x"], st["y"], st["z"], st["m"], cluster_params=cprm)
+    ctx.far_force(*buf["a"])
+    ctx.neighbours(buf["offs"], buf["idx"])  # sizes the row scratch (row mode)
     for _ in range(2):
         eager()
     out["batched_eager"] = _dist(_events_ms(stream, eager, steps, flush))
@@ -738,6 +747,9 @@ def ensemble_run(args):
         offs = torch.empty(c.n + 1, dtype=torch.int64, device=dev)
         idx = buf["idx"][16 * s0:16 * s1]
         tot = torch.zeros(1, dtype=torch.int64, device=dev)
+        cx.build_tree(v["x"], v["y"], v["z"], v["m"])
+        cx.far_force(*a)
+        cx.neighbours(offs, idx)  # sizes the row scratch (row mode)
         per.append((cx, v, a, offs, idx, tot))
 
     def sequential():
@@ -787,6 +799,7 @@ def ensemble_run(args):
                      "speedup_vs_sequential_graph": out["sequential_graph"]["mean"] / step_ms,
                      "tuner_table": table},
         "far_ms": far_ms, "interactions_per_particle": inter / n, "mean_neighbours": nbr_total / n,
+        "neighbour_rows": {"written_by_walk": bool(rows_valid), "row_cap": row_cap},
         "fp32_pct_of_peak": 100.0 * achieved / fp32_peak,
         "roofline": {"bound": "alu", "kernel": "walk_kernel (batched far force)", "achieved": achieved,
                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,

@@ -242,6 +242,7 @@ class Slot:
         self.h_status = torch.zeros(1, dtype=torch.int32).pin_memory()
         self.done = torch.cuda.Event()
         self.batch = None
+        self.sized = False  # the first batch's lists are synchronous: they size the row scratch
 
     def launch(self, arena: Arena, batch: Batch):
         import numpy as np
@@ -273,7 +274,20 @@ class Slot:
         ctx = self.ctx
         ctx.build_tree_batch(boff_d, st["x"], st["y"], st["z"], st["m"], cluster_params=self.d_prm[:c])
         ctx.far_force(*a)
-        ctx.neighbours_async(self.offs[:nb + 1], self.idx, self.tot)
+        if self.sized:
+            ctx.neighbours_async(self.offs[:nb + 1], self.idx, self.tot)
+        else:
+            # once per slot (a host sync): sizes the row scratch, so that the
+            # following batches' walks write the neighbour rows (row mode)
+            try:
+                total = ctx.neighbours(self.offs[:nb + 1], self.idx)
+            except p3t.P3TError as e:  # reported by the scatter's status, as in the async form
+                if e.code != p3t.P3T_ERR_CAPACITY:
+                    raise
+                total = e.total
+            with torch.cuda.stream(s):
+                self.tot.fill_(total)
+            self.sized = True
         ctx.kick(self.dt, *a, st["vx"], st["vy"], st["vz"])
         ctx.drift(self.dt, st["x"], st["y"], st["z"], st["vx"], st["vy"], st["vz"])
         back = [(arena.state[k], self.st[k]) for k in ("x", "y", "z", "vx", "vy", "vz")]
