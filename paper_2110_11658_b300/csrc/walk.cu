@@ -331,13 +331,11 @@ template <int TPL>
 struct NbrCount {
     int si[TPL];   // target positions in key order (-1: empty slot)
     int cnt[TPL];
-    // row mode: the target's row of `cap` entries in the row scratch (original
-    // indices, the target itself left out; entries past cap are dropped while cnt
-    // keeps counting)
-    int32_t *row[TPL];
+    // row mode: wc entries written to the target's row of row_cap entries in the
+    // row scratch, at rows + si * row_cap (original indices, the target itself left
+    // out; entries past row_cap are dropped while cnt keeps counting)
     int wc[TPL];
     unsigned hit[TPL];  // neighbours among the 32 staged sources (bit = staging slot)
-    int cap;
     bool beyond;   // the group's cluster lists neighbours beyond r_out (r_list > r_out)
     float lo, hi;  // r2 < lo: neighbour; r2 > hi: not; otherwise decide in FP64
     // |r2 - mid| <= rad covers [lo, hi] (the rare undecided band) with a 2x margin,
@@ -741,7 +739,8 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
                     const int b = __ffs(h) - 1;
                     h &= h - 1u;
                     if (W.pj[b] != NC.si[t]) {
-                        if (NC.wc[t] < NC.cap) NC.row[t][NC.wc[t]] = W.po[b];
+                        if (NC.wc[t] < P.row_cap)
+                            P.rows[(size_t)NC.si[t] * P.row_cap + NC.wc[t]] = W.po[b];
                         NC.wc[t]++;
                     }
                 }
@@ -854,7 +853,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
                 // an empty slot (at c_g) must write nothing: its count starts past any cap
                 NC.hit[t] = 0u;
                 NC.wc[t] = s < gr.x + gr.y ? 0 : (1 << 30);
-                NC.row[t] = P.rows + (size_t)(s < gr.x + gr.y ? s : 0) * P.row_cap;
             }
             if (s < gr.x + gr.y) {
                 if (kMixed) {
@@ -880,7 +878,6 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
             const float A = amax * 1.0001f;
             const float band = kU * (24.f * K.rl2_f + 32.f * A * K.rl_f + 128.f * kU * Rf * K.rl_f) +
                                64.f * kU * kU * (A + 2.f * K.rl_f) * (A + 2.f * K.rl_f);
-            NC.cap = P.row_cap;
             NC.beyond = shell;
             if (!count_here)
                 NC.off();  // this cluster is counted elsewhere
