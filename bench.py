@@ -41,8 +41,8 @@ if ROOT not in sys.path:
 # of the timed step, which also writes the neighbour rows (163.1 MB read + 473.0 MB
 # written; without the rows the counting walk moved 85.5 MB).  Valid only at that N and for the
 # kernel sources it was measured on: otherwise the roofline's traffic is null.
-WALK_TRAFFIC = {"sources": {"walk.cu": "a2b3fd13fd619816", "p3t_internal.cuh": "7f55f9317b085d0a"},
-                "n": 1000000, "bytes": 167937536 + 477390848}
+WALK_TRAFFIC = {"sources": {"walk.cu": "44a0159a01d02876", "p3t_internal.cuh": "7f55f9317b085d0a"},
+                "n": 1000000, "bytes": 170160384 + 478669056}
 
 N_DEFAULT = 1_000_000
 THETA = 0.4
