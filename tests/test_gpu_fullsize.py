@@ -111,3 +111,33 @@ def test_fullsize_irregular_force_and_jerk(c2):
     assert np.median(ef) <= 1e-6 and np.median(ej) <= 1e-6
     big = sj > 1e-3 * np.median(sj[sj > 0])
     assert ej[big].max() <= 1e-4, ej[big].max()
+
+
+def test_fullsize_row_mode_step_as_timed(c2):
+    # the kernel variant the benchmark times: after one synchronous list (the
+    # sizing step), the walk writes the neighbour rows (row mode) and computes no
+    # potential; its lists must equal the ones checked above in full, and its
+    # forces the fixture's (the same FP32 arithmetic in another kernel variant)
+    c, w = c2["c"], c2["w"]
+    prm = p3t.Params(theta=w["theta"], r_in=w["r_in"], r_out=w["r_out"], r_list=w["r_list"],
+                     leaf_cap=16, group_size=32, tile=64, precision=p3t.P3T_FP32_MIXED)
+    ctx = p3t.Context(prm)
+    d = [to_dev(getattr(c, k)) for k in "xyzm"]
+    a = [torch.empty(c.n, dtype=torch.float32, device=DEV) for _ in range(3)]
+    offs = torch.empty(c.n + 1, dtype=torch.int64, device=DEV)
+    idx = torch.empty(130 * c.n, dtype=torch.int32, device=DEV)
+    ctx.build_tree(*d)
+    ctx.far_force(*a)
+    ctx.neighbours(offs, idx)
+    ctx.build_tree(*d)
+    ctx.far_force(*a)
+    cap, valid = ctx.row_mode()
+    assert cap > 0 and valid == 1
+    total = ctx.neighbours(offs, idx)
+    ctx.check()
+    assert total == len(c2["idx"])
+    assert np.array_equal(offs.cpu().numpy(), c2["offs"])
+    assert np.array_equal(idx[:total].cpu().numpy(), c2["idx"])
+    e = rel_err(torch.stack(a, 1).double().cpu().numpy(), c2["a"])
+    assert np.median(e) <= 1e-7 and e.max() <= 1e-5, (np.median(e), e.max())
+    ctx.close()
