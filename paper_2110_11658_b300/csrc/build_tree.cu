@@ -698,6 +698,70 @@ __global__ void __launch_bounds__(kBuildThreads) group_frames_kernel(Tree T)
     }
 }
 
+// The order in which the walks take the groups: by the size of the group box
+// (the FP32 exponent and two mantissa bits of its longest side), smallest first.
+// Small boxes hold the densest groups, which carry the most particle terms, so
+// the persistent walk starts them first and its tail holds light groups.  Inside
+// a bin the order is arbitrary; no result depends on it (groups are independent).
+constexpr int kGroupBins = 256;
+__device__ __forceinline__ int group_bin(const Tree &T, int g)
+{
+    const float4 g1 = T.gfr[3 * (size_t)g + 1], g2 = T.gfr[3 * (size_t)g + 2];
+    const float side = fmaxf(fmaxf(fmaxf(g2.y - g1.z, g2.z - g1.w), g2.w - g2.x), 0.f);
+    const int b = (int)(__float_as_uint(side) >> 21) - (int)(__float_as_uint(1e-12f) >> 21);
+    return min(max(b, 0), kGroupBins - 1);
+}
+
+__global__ void __launch_bounds__(kBuildThreads) group_bins_kernel(Tree T)
+{
+    __shared__ int cnt[kGroupBins];
+    for (int b = threadIdx.x; b < kGroupBins; b += blockDim.x) cnt[b] = 0;
+    __syncthreads();
+    const int ng = T.meta->n_groups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        atomicAdd(&cnt[group_bin(T, g)], 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kGroupBins; b += blockDim.x)
+        if (cnt[b]) atomicAdd(&T.gbins[b], cnt[b]);
+}
+
+// exclusive scan of the bin counts into the cursors (one block of kGroupBins threads)
+__global__ void __launch_bounds__(kGroupBins) group_bins_scan_kernel(Tree T)
+{
+    __shared__ int sh[kGroupBins];
+    const int b = threadIdx.x;
+    sh[b] = T.gbins[b];
+    __syncthreads();
+    for (int o = 1; o < kGroupBins; o <<= 1) {
+        const int v = b >= o ? sh[b - o] : 0;
+        __syncthreads();
+        sh[b] += v;
+        __syncthreads();
+    }
+    T.gbins[kGroupBins + b] = sh[b] - T.gbins[b];
+}
+
+// one slot per group: ranks inside a block's chunk from shared counters, one
+// global reservation per (chunk, bin)
+__global__ void __launch_bounds__(kBuildThreads) group_order_kernel(Tree T)
+{
+    __shared__ int cnt[kGroupBins], base[kGroupBins];
+    const int ng = T.meta->n_groups;
+    for (int g0 = blockIdx.x * blockDim.x; g0 < ng; g0 += gridDim.x * blockDim.x) {
+        for (int b = threadIdx.x; b < kGroupBins; b += blockDim.x) cnt[b] = 0;
+        __syncthreads();
+        const int g = g0 + threadIdx.x;
+        const int bin = g < ng ? group_bin(T, g) : -1;
+        const int rank = bin >= 0 ? atomicAdd(&cnt[bin], 1) : 0;
+        __syncthreads();
+        for (int b = threadIdx.x; b < kGroupBins; b += blockDim.x)
+            if (cnt[b]) base[b] = atomicAdd(&T.gbins[kGroupBins + b], cnt[b]);
+        __syncthreads();
+        if (bin >= 0) T.gorder[base[bin] + rank] = g;
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // moments (rule 6) and the opening radius (rule 8)
 
@@ -1116,6 +1180,13 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     group_first_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, T.gflag, T.gidx, T.grp);
     group_finish_kernel<<<persistent, kBuildThreads, 0, s>>>(T, n);
     group_frames_kernel<<<persistent, kBuildThreads, 0, s>>>(T);
+    if (cudaMemsetAsync(T.gbins, 0, sizeof(int32_t) * 2 * kGroupBins, s) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    // few blocks: the bins take one global atomic per block and bin
+    const int order_grid = std::min(64, persistent);
+    group_bins_kernel<<<order_grid, kBuildThreads, 0, s>>>(T);
+    group_bins_scan_kernel<<<1, kGroupBins, 0, s>>>(T);
+    group_order_kernel<<<order_grid, kBuildThreads, 0, s>>>(T);
 
     // moments: leaves, then levels 20 .. 0 (a level without internal nodes exits at once)
     const bool q64 = P.precision == P3T_FP64;

@@ -796,6 +796,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, TPL == 1 ? kMinBlocksTpl1 : 3
         if (lane == 0) g = (int)atomicAdd(P.ticket, 1u);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ng) break;
+        g = T.gorder[g];  // smallest group boxes first (made by the build)
         const int2 gr = T.grp[g];
         double4_32a glo, ghi;  // the FP64 form's group box (the mixed form reloads it when needed)
         if constexpr (!kMixed) glo = T.glo[g], ghi = T.ghi[g];
