@@ -41,8 +41,8 @@ if ROOT not in sys.path:
 # of the timed step, which also writes the neighbour rows (163.1 MB read + 473.0 MB
 # written; without the rows the counting walk moved 85.5 MB).  Valid only at that N and for the
 # kernel sources it was measured on: otherwise the roofline's traffic is null.
-WALK_TRAFFIC = {"sources": {"walk.cu": "44a0159a01d02876", "p3t_internal.cuh": "7f55f9317b085d0a"},
-                "n": 1000000, "bytes": 170160384 + 478669056}
+WALK_TRAFFIC = {"sources": {"walk.cu": "d3b8e31d5980a380", "p3t_internal.cuh": "fe31a037aff42001"},
+                "n": 1000000, "bytes": 285850624 + 509234944}
 
 N_DEFAULT = 1_000_000
 THETA = 0.4
