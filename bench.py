@@ -36,11 +36,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# DRAM bytes of one walk_kernel launch, from the ncu capture of the 10^6-particle
-# Plummer walk summarised in profiles/walk_kernel_plummer_kroupa_n1e6.md: the walk
-# of the timed step, which also writes the neighbour rows (163.1 MB read + 473.0 MB
-# written; without the rows the counting walk moved 85.5 MB).  Valid only at that N and for the
-# kernel sources it was measured on: otherwise the roofline's traffic is null.
+# DRAM bytes (read + written) of one walk_kernel launch, from an ncu capture of the
+# 10^6-particle Plummer walk of the timed step, which also writes the neighbour rows.
+# Valid only at that N and for the kernel sources it was measured on (their hashes):
+# otherwise the roofline's traffic is null.
 WALK_TRAFFIC = {"sources": {"walk.cu": "d3b8e31d5980a380", "p3t_internal.cuh": "fe31a037aff42001"},
                 "n": 1000000, "bytes": 285850624 + 509234944}
 
@@ -78,6 +77,9 @@ def parse_args(argv=None):
     ap.add_argument("--requests", type=int, default=10000, help="serve256: requests in the timed stream")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve256: mean arrival rate (requests/s)")
     ap.add_argument("--no-tune", action="store_true", help="ensemble64: use --group-size/--tile/--leaf-cap")
+    ap.add_argument("--no-ensemble", action="store_true",
+                    help="plummer1m: leave out the short ensemble64 summary (p50/p99) of the line")
+    ap.add_argument("--ens-steps", type=int, default=20, help="timed steps of the short ensemble summary")
     ap.add_argument("--samples", type=int, default=8192, help="direct-sum targets (king2m)")
     return ap.parse_args(argv)
 
@@ -449,13 +451,9 @@ def run_b300(args, rank, local, world):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "plummer_kroupa_n%d_theta%.1f_nbr100" % (n, THETA), "n": n, "theta": THETA,
-                   "r_out": w["r_out"], "r_in": w["r_in"], "r_list": w["r_list"], "leaf_cap": args.leaf_cap,
-                   "group_size": args.group_size, "tile": args.tile, "dt": DT, "quadrupole": True,
-                   "precision": "fp32 interactions, fp64 coordinates, compensated sums",
-                   "step": "build_tree + far_force + neighbours + kick + drift, one CUDA graph launch",
-                   "l2": "256 MB buffer written between timed steps (L2 is 126 MB)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": bench_config(n, w, args, world),
+        "precision": "fp32 interactions, fp64 coordinates, compensated sums",
+        "step": "build_tree + far_force + neighbours + kick + drift, one CUDA graph launch",
         "far_force_evals_per_s": total_particles / (far_ms * 1e-3),
         "interactions_per_s": inter / (far_ms * 1e-3) * world,
         "interactions_per_particle": inter / n,
@@ -485,7 +483,21 @@ def run_b300(args, rank, local, world):
         "wall_s_timed": wall,
     }
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_ensemble:
+        # the metric's ensemble p50/p99: the 64-cluster batched step, a few graph launches
+        del x, y, z, m, vx, vy, vz, a, offs, idx, flush
+        torch.cuda.empty_cache()
+        line["ensemble"] = ensemble_run(args, short=True)
     return line
+
+
+def bench_config(n, w, args, world):
+    """The workload of the throughput line, identical in both arms."""
+    return {"workload": "plummer_kroupa_n%d_theta%.1f_nbr100" % (n, THETA), "n": n, "theta": THETA,
+            "r_out": w["r_out"], "r_in": w["r_in"], "r_list": w["r_list"], "leaf_cap": args.leaf_cap,
+            "group_size": args.group_size, "tile": args.tile, "dt": DT, "quadrupole": True,
+            "l2": "256 MB buffer written between timed steps (L2 is 126 MB)",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 # kernels launched by one step: build = metadata, cluster table, cluster parameters,
@@ -520,9 +532,9 @@ def run_reference(args, rank, world):
         "value": value, "unit": "particles/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "plummer_kroupa_n%d_theta%.1f_nbr100" % (c.n, THETA), "n": c.n, "theta": THETA,
-                   "r_out": w["r_out"], "r_in": w["r_in"], "r_list": w["r_list"], "leaf_cap": args.leaf_cap,
-                   "group_size": args.group_size, "dt": DT, "quadrupole": True},
+        "config": bench_config(c.n, w, args, world),
+        "precision": "fp64 throughout (the oracle)",
+        "step": "oracle tree build + far force + neighbour lists + kick, a bounded sample scaled to N",
         "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -630,13 +642,21 @@ def _dist(ts):
             "min": float(a.min()), "max": float(a.max()), "steps": len(ts)}
 
 
-def ensemble_run(args):
+# the launch shape the autotuner picks for this ensemble (G, list tile, leaf capacity)
+ENS_TUNED = {"group_size": 32, "tile": 64, "leaf_cap": 16}
+
+
+def ensemble_run(args, short=False):
     """64 independent clusters (alternately Plummer and King W0 = 5), N log-uniform in
     [1e4, 5e5] (~7.8e6 in total), equal masses, theta = 0.4, per-cluster r_out by the
     paper's rule.  One step = batched build + far force + neighbour lists + kick + drift,
     captured once into a CUDA graph (one persistent walk launch for every cluster), with
     the launch shape picked by the autotuner.  Compared with the same step run one
-    cluster at a time (eager calls, and one graph per cluster)."""
+    cluster at a time (eager calls, and one graph per cluster).
+
+    short: the summary the throughput benchmark attaches to its line: the tuned shape
+    (ENS_TUNED) without a search, `args.ens_steps` timed steps of the batched graph and of
+    one graph per cluster, no eager forms."""
     import numpy as np
     import torch
 
@@ -684,7 +704,9 @@ def ensemble_run(args):
         return g, ctx
 
     tune_state = {k: v.clone() for k, v in init.items()}
-    if args.no_tune:
+    if short:
+        best, table = dict(ENS_TUNED), []
+    elif args.no_tune:
         best = {"group_size": args.group_size, "tile": args.tile, "leaf_cap": args.leaf_cap}
         table = []
     else:
@@ -693,7 +715,7 @@ def ensemble_run(args):
         best, table = res.best, [{"cfg": c, "ms": ms} for c, ms in res.table]
     del tune_state
 
-    steps = max(3, args.steps)
+    steps = max(3, args.ens_steps if short else args.steps)
     out = {}
     # (a) batched, graph-captured
     st = {k: v.clone() for k, v in init.items()}
@@ -716,6 +738,19 @@ def ensemble_run(args):
     far_ts = _events_ms(stream, lambda: ctx.far_force(*buf["a"]), steps, flush)
     ctx.check()
     ctx.close()
+    if short:
+        del g
+        per_s = _sequential_graph_ms(cl, segn, rows, init, buf, params(best), stream, dev, steps, flush)
+        b = out["batched_graph"]
+        return {"workload": "ensemble64_plummer_king5_n1e4-5e5", "n_clusters": len(cl), "particles": n,
+                "shape": best, "steps": steps, "step_ms_p50": b["p50"], "step_ms_p99": b["p99"],
+                "step_ms_mean": b["mean"], "particles_per_s": n / (b["mean"] * 1e-3),
+                "one_cluster_at_a_time_ms_mean": per_s["mean"], "one_cluster_at_a_time_ms_p99": per_s["p99"],
+                "speedup_vs_one_at_a_time": per_s["mean"] / b["mean"],
+                "far_ms": float(np.median(far_ts)), "interactions_per_particle": inter / n,
+                "step": "batched build + far force + neighbours + kick + drift, one CUDA graph launch; "
+                        "one at a time = one graph per cluster, 64 launches",
+                "clocks": clk}
     # (b) batched, eager calls
     st = {k: v.clone() for k, v in init.items()}
     ctx = p3t.Context(params(best), stream)
@@ -808,6 +843,47 @@ def ensemble_run(args):
                                     % (float(peaks.get("sm_max_mhz", 2032.0)), peak_kind)},
         "gpu_launches": None, "clocks": clk,
     }
+
+
+def _sequential_graph_ms(cl, segn, rows, init, buf, prm0, stream, dev, steps, flush):
+    """The ensemble step one cluster at a time: a context and a captured graph per
+    cluster (its own r_out), the 64 graphs launched back to back; step times in ms."""
+    import copy
+
+    import torch
+
+    import paper_2110_11658_b300 as p3t
+    st = {k: v.clone() for k, v in init.items()}
+    per = []
+    for k, c in enumerate(cl):
+        s0, s1 = int(segn[k]), int(segn[k + 1])
+        prm = copy.copy(prm0)
+        prm.r_in, prm.r_out, prm.r_list = rows[k][1], rows[k][2], rows[k][3]
+        cx = p3t.Context(prm, stream)
+        v = {q: st[q][s0:s1] for q in st}
+        a = [buf["a"][i][s0:s1] for i in range(3)]
+        offs = torch.empty(c.n + 1, dtype=torch.int64, device=dev)
+        idx = buf["idx"][16 * s0:16 * s1]
+        tot = torch.zeros(1, dtype=torch.int64, device=dev)
+        cx.build_tree(v["x"], v["y"], v["z"], v["m"])
+        cx.far_force(*a)
+        cx.neighbours(offs, idx)  # sizes the row scratch (row mode)
+        g = cx.capture_step(v["x"], v["y"], v["z"], v["m"], *a, vx=v["vx"], vy=v["vy"], vz=v["vz"],
+                            kick_dt=DT, drift_dt=DT, offsets=offs, idx=idx, total=tot)
+        per.append((cx, g))
+
+    def launch_all():
+        for _, g in per:
+            g.launch()
+
+    for _ in range(2):
+        launch_all()
+    res = _dist(_events_ms(stream, launch_all, steps, flush))
+    for cx, g in per:
+        cx.check()
+        g.close()
+        cx.close()
+    return res
 
 
 # ---------------------------------------------------------------------------- serving

@@ -285,6 +285,27 @@ int p3t_row_mode(p3t_ctx *c, int32_t *row_cap, int32_t *rows_valid);
 /* 1: record per-group counts in the walk (slightly slower); 0: off (default). */
 int p3t_set_debug(p3t_ctx *c, int on);
 
+/* Bounded device-side waits (the look-back of the device-wide prefix sums in
+ * the sort, the topology, the groups and the neighbour offsets; no part of the
+ * paper's method, a guard that keeps every kernel finite): a wait that has
+ * polled `polls` times without its predecessor publishing gives up, latches
+ * P3T_ERR_TIMEOUT (returned by the next synchronising call, e.g. p3t_status)
+ * and lets the kernel finish with a partial result.  polls = 0 restores the
+ * default, 2^22 polls (about 1.1 s of backoff sleeps).  Synchronises the
+ * context's stream when the device block already exists.  Errors:
+ * P3T_ERR_INVALID_ARG (polls < 0), P3T_ERR_CUDA. */
+int p3t_set_spin_limit(p3t_ctx *c, int64_t polls);
+
+/* Test hook for the bounded waits: runs one exclusive prefix sum over n
+ * entries of the context's neighbour-count buffer in which tile 0's work item is
+ * never handed out, so the tiles after it wait on a status word that nothing
+ * writes until their spin limit (p3t_set_spin_limit) runs out.  Synchronises
+ * and returns the context's status: P3T_ERR_TIMEOUT is the expected outcome,
+ * read and cleared like any latched error, after which the context is usable.
+ * Needs scratch for n particles (p3t_reserve or a build; else P3T_ERR_ORDER);
+ * invalidates the cached neighbour counts (the next p3t_neighbours recounts). */
+int p3t_debug_stalled_scan(p3t_ctx *c, int64_t n);
+
 /* Static description of an error code. */
 const char *p3t_error_string(int code);
 
@@ -414,9 +435,11 @@ int p3t_batch_scatter_neighbours(void *cuda_stream, int32_t n_seg, int64_t n_bat
  * GPU that loads the library until the process exits); n above that returns
  * P3T_ERR_CAPACITY, n <= 0 or a null pointer P3T_ERR_INVALID_ARG.
  * The first call on a device looks up the array's device address on the
- * current device; make that first call before any stream capture.  The call
- * runs on `cuda_stream`, synchronises it, and returns P3T_ERR_INVALID_INPUT
- * for non-finite or negative inputs as p3t_build_tree would.  Every call
+ * current device; make that first call before any stream capture.  Every
+ * call, the first and each later one, runs on `cuda_stream` and ends by
+ * synchronising it to read its status; it returns P3T_ERR_INVALID_INPUT for
+ * non-finite or negative inputs as p3t_build_tree would, and a latched error
+ * never carries over into the next call.  Every call
  * shares the one array: calls that overlap on a GPU (other streams or host
  * threads at the same time) race on it. */
 #define P3T_NOALLOC_MAX_N 65536

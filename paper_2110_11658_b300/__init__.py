@@ -42,6 +42,7 @@ EXPORTED = [
     "p3t_graph_capture", "p3t_graph_launch", "p3t_graph_destroy", "p3t_reserve", "p3t_scratch_bytes",
     "p3t_batch_move", "p3t_batch_scatter_neighbours", "p3t_filter_fallbacks", "p3t_irregular",
     "p3t_sample_knn6", "p3t_sample_knn6_brute", "p3t_core_quantities", "p3t_row_mode",
+    "p3t_set_spin_limit", "p3t_debug_stalled_scan",
 ]
 P3T_NOALLOC_MAX_N = 65536
 
@@ -99,6 +100,8 @@ _sig = {
     "p3t_export_tree": [_vp] + [_vp] * 15,
     "p3t_group_counts": [_vp, _vp, _vp],
     "p3t_set_debug": [_vp, C.c_int],
+    "p3t_set_spin_limit": [_vp, _i64],
+    "p3t_debug_stalled_scan": [_vp, _i64],
     "p3t_error_string": [C.c_int],
     "p3t_morton_order_noalloc": [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "p3t_graph_capture": [_vp, C.POINTER(p3t_step_args), C.POINTER(_vp)],
@@ -243,6 +246,9 @@ class Context:
     def reserve(self, n: int, n_clusters: int = 1):
         """Size the scratch for n particles in n_clusters clusters now (p3t_reserve)."""
         _check(_lib.p3t_reserve(self._h, int(n), int(n_clusters)), "p3t_reserve")
+
+    def set_spin_limit(self, polls: int):
+        _check(_lib.p3t_set_spin_limit(self._h, int(polls)), "p3t_set_spin_limit")
 
     def set_debug(self, on: bool):
         _check(_lib.p3t_set_debug(self._h, int(bool(on))), "p3t_set_debug")

@@ -119,6 +119,10 @@ int ensure_capacity(p3t_ctx *c, long long n)
     c->tree.meta = c->meta;
     c->tree.cap_nodes = (int)need_nodes;
     if (cudaMemsetAsync(c->meta, 0, sizeof(Meta), c->stream) != cudaSuccess) return P3T_ERR_CUDA;
+    if (c->spin_limit &&
+        cudaMemcpyAsync(&c->meta->spin_limit, &c->spin_limit, sizeof(long long),
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+        return P3T_ERR_CUDA;
     return P3T_OK;
 }
 
@@ -449,6 +453,31 @@ int p3t_set_debug(p3t_ctx *c, int on)
     if (!c) return P3T_ERR_INVALID_ARG;
     c->debug = on ? 1 : 0;
     return P3T_OK;
+}
+
+int p3t_set_spin_limit(p3t_ctx *c, int64_t polls)
+{
+    if (!c || polls < 0) return P3T_ERR_INVALID_ARG;
+    c->spin_limit = polls;
+    if (!c->meta) return P3T_OK;  // written into the device block when it is allocated
+    if (cudaMemcpyAsync(&c->meta->spin_limit, &c->spin_limit, sizeof(long long),
+                        cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return P3T_ERR_CUDA;
+    }
+    return P3T_OK;
+}
+
+int p3t_debug_stalled_scan(p3t_ctx *c, int64_t n)
+{
+    if (!c || n <= 0) return P3T_ERR_INVALID_ARG;
+    if (!c->meta || n > c->cap_n) return P3T_ERR_ORDER;
+    c->counts_valid = 0;  // the scan runs over the neighbour-count buffer
+    int e = scan_stalled((int)n, c->nbr_count, c->row_list, c->scan_status, &c->meta->tickets[30],
+                         c->meta, c->stream);
+    if (e) return e;
+    return p3t_status(c);
 }
 
 const char *p3t_error_string(int code)

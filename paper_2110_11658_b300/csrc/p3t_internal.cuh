@@ -24,7 +24,10 @@ namespace p3t {
 
 constexpr int kLevels = 21;          // key bits per axis = tree depth
 constexpr int kMaxLevelSlots = 24;   // per-level bookkeeping arrays
-constexpr long long kSpinLimit = 1LL << 24;  // bounded waits: ~1 s with backoff
+// Bounded waits: polls before a wait gives up and latches P3T_ERR_TIMEOUT (a
+// context may set its own limit, Meta::spin_limit).  The first 64 polls sleep
+// 32 ns, the rest 256 ns, so 2^22 polls take about 1.1 s.
+constexpr long long kSpinLimit = 1LL << 22;
 constexpr int kWalkRecord = 6;               // float4 per node in Tree::wn
 constexpr float kFp32U = 5.9604644775390625e-8f;  // 2^-24, FP32 unit round-off
 
@@ -71,6 +74,7 @@ struct Meta {
     long long fallback_tests;      // FP64 decisions taken after an undecided FP32 filter
     unsigned long long core_count; // particles within the core radius (core quantities)
     int row_class[16];             // neighbour rows by length class: counts, fill cursors
+    long long spin_limit;          // polls of a bounded wait (0: kSpinLimit)
 };
 
 // ---- one cluster of a (possibly batched) build -----------------------------------
@@ -288,7 +292,7 @@ __device__ __forceinline__ T block_excl_scan(T v, T *total, T *sh)
 // status[t]: bits 62-63 = flag (0 none, 1 aggregate, 2 inclusive prefix), bits
 // 0-61 = value.  Called by ALL threads of the block holding ticket t with the
 // block aggregate; returns the exclusive prefix of the block.  The wait on a
-// predecessor is bounded: after kSpinLimit polls the error is latched and the
+// predecessor is bounded: after Meta::spin_limit polls the error is latched and the
 // partial prefix is used, so the kernel always terminates.
 constexpr unsigned long long kFlagAgg = 1ULL << 62, kFlagPre = 2ULL << 62,
                              kValMask = (1ULL << 62) - 1;
@@ -305,6 +309,7 @@ __device__ __forceinline__ long long lookback_prefix(unsigned long long *status,
         } else {
             if (lane == 0) st_relaxed(&status[t], kFlagAgg | (unsigned long long)aggregate);
             int j = t - 1;  // this lane inspects j - lane
+            const long long limit = meta->spin_limit > 0 ? meta->spin_limit : kSpinLimit;
             long long spins = 0;
             while (true) {
                 int idx = j - lane;
@@ -312,7 +317,7 @@ __device__ __forceinline__ long long lookback_prefix(unsigned long long *status,
                 unsigned long long flag = s & ~kValMask;
                 // wait until every inspected predecessor published something
                 if (__any_sync(0xffffffffu, flag == 0)) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > limit) {
                         if (lane == 0) latch_error(meta, P3T_ERR_TIMEOUT);
                         break;
                     }
@@ -383,6 +388,7 @@ struct p3t_ctx {
     int cap_clusters;
     p3t::Cluster *clusters;  // per-cluster table (separate allocation)
     int pending_err;  // host-side latched error
+    long long spin_limit;  // polls of a bounded device wait (0: the default)
     // device memory
     p3t::Meta *meta;
     p3t::Tree tree;
@@ -441,6 +447,8 @@ int irregular(p3t_ctx *c, int n, const int64_t *offs, const int32_t *idx, const 
               const double *vy, const double *vz, double *fx, double *fy, double *fz, double *jx,
               double *jy, double *jz);
 int reserve(p3t_ctx *c, long long n, int n_clusters);
+int scan_stalled(int n, const int32_t *in, int32_t *out, unsigned long long *status,
+                 unsigned int *ticket, Meta *meta, cudaStream_t s);
 int check_launch(p3t_ctx *c);
 int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *cprm,
                const double *x, const double *y, const double *z, const double *m);

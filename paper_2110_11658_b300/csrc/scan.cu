@@ -85,4 +85,26 @@ int scan_excl_i32_to_i32(const int32_t *in, int32_t *out, int n, unsigned long l
     return run_scan<int32_t, int32_t>(in, out, n, (int32_t *)nullptr, status, ticket, meta, s);
 }
 
+__global__ void set_ticket_kernel(unsigned int *ticket, unsigned int v) { *ticket = v; }
+
+// The scan above with tile 0's ticket never handed out: the block holding tile
+// 1 (and every tile whose look-back window of 32 reaches tile 0) waits on a
+// predecessor that never publishes, so its bounded wait runs out, latches
+// P3T_ERR_TIMEOUT and goes on with a partial prefix; later tiles find those
+// published prefixes and finish.  The last of the ntiles blocks takes ticket
+// ntiles, past the last tile: it reads nothing, writes no output and publishes
+// status word ntiles (the status array holds ntiles + 2 words).
+int scan_stalled(int n, const int32_t *in, int32_t *out, unsigned long long *status,
+                 unsigned int *ticket, Meta *meta, cudaStream_t s)
+{
+    if (n <= 0) return P3T_ERR_INVALID_ARG;
+    const int ntiles = (n + kScanTile - 1) / kScanTile;
+    if (cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (ntiles + 1), s) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    set_ticket_kernel<<<1, 1, 0, s>>>(ticket, 1u);
+    scan_kernel<int32_t, int32_t><<<ntiles, kScanThreads, 0, s>>>(in, out, n, (int32_t *)nullptr,
+                                                                   status, ticket, meta);
+    return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
 }  // namespace p3t

@@ -106,3 +106,31 @@ def test_kick_and_drift_exact():
     ctx.drift(0.01, *x, *v)
     ctx.check()
     assert np.array_equal(x[0].cpu().numpy(), c.x + 0.01 * ref[0])
+
+
+def test_bounded_wait_runs_out_and_returns_a_status():
+    # a prefix sum whose first tile is never handed out: the look-back waits of the
+    # tiles after it poll a status word that nothing writes, give up after the
+    # context's spin limit, latch P3T_ERR_TIMEOUT and finish; the context stays usable
+    ctx = p3t.Context(p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05))
+    ctx.reserve(20000)
+    assert p3t.p3t_debug_stalled_scan(ctx.handle, 0) == p3t.P3T_ERR_INVALID_ARG
+    assert p3t.p3t_debug_stalled_scan(ctx.handle, 10 ** 6) == p3t.P3T_ERR_ORDER  # beyond the scratch
+    assert p3t.p3t_set_spin_limit(ctx.handle, -1) == p3t.P3T_ERR_INVALID_ARG
+    ctx.set_spin_limit(2000)
+    for n in (5000, 20000):  # 3 and 10 tiles of the scan
+        assert p3t.p3t_debug_stalled_scan(ctx.handle, n) == p3t.P3T_ERR_TIMEOUT
+        assert ctx.status() == p3t.P3T_OK  # read once, cleared
+    ctx.set_spin_limit(0)  # the default again
+    c = synth.plummer(4096, synth.BASE_SEED)
+    g = run_gpu(c, ctx.params, nbr=True)
+    ctx.build_tree(to_dev(c.x), to_dev(c.y), to_dev(c.z), to_dev(c.m))
+    a = [torch.empty(c.n, dtype=torch.float32, device=DEV) for _ in range(3)]
+    ctx.far_force(*a)
+    offs = torch.empty(c.n + 1, dtype=torch.int64, device=DEV)
+    idx = torch.empty(8 * c.n, dtype=torch.int32, device=DEV)
+    tot = ctx.neighbours(offs, idx)
+    ctx.check()
+    assert np.array_equal(torch.stack(a, 1).double().cpu().numpy(), g["a"])
+    assert np.array_equal(offs.cpu().numpy(), g["offs"]) and np.array_equal(idx[:tot].cpu().numpy(), g["idx"])
+    ctx.close()

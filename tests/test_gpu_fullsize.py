@@ -4,8 +4,9 @@ Plummer sphere, N = 10^6, Kroupa masses, theta = 0.4, r_out for ~100 mean
 neighbours, r_in = 0.1 r_out, leaf_cap 16, G = 32, tile 64, mixed precision.
 The oracle builds the whole tree (bit-exact comparison of keys, permutation,
 topology and groups) and evaluates forces, interaction counts and neighbour
-rows for a seeded sample of groups; a sample of targets is also checked
-against the FP64 direct sum.
+rows of every group, once; both walk variants (the first walk, with the
+potential, and the row-mode walk the benchmark times) are compared with it in
+full; a sample of targets is also checked against the FP64 direct sum.
 """
 import numpy as np
 import pytest
@@ -45,7 +46,10 @@ def c2():
            "f_irr": fi.T.cpu().numpy(), "j_irr": ji.T.cpu().numpy()}
     ctx.check()
     ctx.close()
-    out["oracle"] = oracle.Tree(c.x, c.y, c.z, c.m, w["theta"], w["r_out"], leaf_cap=16, group_size=32)
+    t = oracle.Tree(c.x, c.y, c.z, c.m, w["theta"], w["r_out"], leaf_cap=16, group_size=32)
+    out["oracle"] = t
+    out["ref_far"] = t.far(w["r_in"])  # every group
+    _, out["ref_offs"], out["ref_idx"] = t.neighbours(w["r_list"])
     return out
 
 
@@ -58,25 +62,26 @@ def test_fullsize_tree_bit_exact(c2):
         assert np.array_equal(g[k], ref[k]), k
 
 
-def test_fullsize_sampled_groups_forces_counts_neighbours(c2):
-    t = c2["oracle"]
-    rng = np.random.default_rng(8)
-    sel = np.sort(rng.choice(t.n_groups, 128, replace=False))
-    f = t.far(c2["w"]["r_in"], groups=sel)
-    assert np.array_equal(c2["g_cells"][sel], f["n_cell"])
-    assert np.array_equal(c2["g_parts"][sel], f["n_part"])
-    rows = ~np.isnan(f["a"][:, 0])
-    e = rel_err(c2["a"][rows], f["a"][rows])
+def _assert_matches_oracle(c2, a, g_cells, g_parts, offs, idx):
+    """Every group's interaction counts and every neighbour row equal the
+    oracle's; forces within median 1e-5 and 99th percentile 1e-4."""
+    f = c2["ref_far"]
+    assert np.array_equal(g_cells, f["n_cell"])
+    assert np.array_equal(g_parts, f["n_part"])
+    e = rel_err(a, f["a"])
     assert np.median(e) <= 1e-5 and np.percentile(e, 99) <= 1e-4, (np.median(e), np.percentile(e, 99))
-    ep = np.abs(c2["pot"][rows] - f["pot"][rows]) / np.abs(f["pot"][rows])
+    assert np.array_equal(offs, c2["ref_offs"])
+    assert np.array_equal(idx, c2["ref_idx"])
+
+
+def test_fullsize_all_groups_forces_counts_neighbours(c2):
+    _assert_matches_oracle(c2, c2["a"], c2["g_cells"], c2["g_parts"], c2["offs"], c2["idx"])
+    f = c2["ref_far"]
+    ep = np.abs(c2["pot"] - f["pot"]) / np.abs(f["pot"])
     assert np.median(ep) <= 1e-6
-    counts, offs, idx = t.neighbours(c2["w"]["r_list"], groups=sel)
-    mine = np.nonzero(counts >= 0)[0]
-    go, gi = c2["offs"], c2["idx"]
-    for i in mine:
-        assert np.array_equal(gi[go[i]:go[i + 1]], idx[offs[i]:offs[i + 1]]), i
     # mean neighbour number near the target of the workload (~100)
-    assert 90 < go[-1] / len(go) < 115
+    go = c2["offs"]
+    assert 90 < go[-1] / (len(go) - 1) < 115
 
 
 def test_fullsize_against_direct_sum(c2):
@@ -116,8 +121,9 @@ def test_fullsize_irregular_force_and_jerk(c2):
 def test_fullsize_row_mode_step_as_timed(c2):
     # the kernel variant the benchmark times: after one synchronous list (the
     # sizing step), the walk writes the neighbour rows (row mode) and computes no
-    # potential; its lists must equal the ones checked above in full, and its
-    # forces the fixture's (the same FP32 arithmetic in another kernel variant)
+    # potential; every group's counts, every row and the forces against the
+    # oracle, and the forces against the fixture's (the same FP32 arithmetic in
+    # another kernel variant)
     c, w = c2["c"], c2["w"]
     prm = p3t.Params(theta=w["theta"], r_in=w["r_in"], r_out=w["r_out"], r_list=w["r_list"],
                      leaf_cap=16, group_size=32, tile=64, precision=p3t.P3T_FP32_MIXED)
@@ -129,15 +135,17 @@ def test_fullsize_row_mode_step_as_timed(c2):
     ctx.build_tree(*d)
     ctx.far_force(*a)
     ctx.neighbours(offs, idx)
+    ctx.set_debug(True)  # per-group counts: a store per group, the same kernel variant
     ctx.build_tree(*d)
     ctx.far_force(*a)
     cap, valid = ctx.row_mode()
     assert cap > 0 and valid == 1
     total = ctx.neighbours(offs, idx)
+    gc, gp = ctx.group_counts()
     ctx.check()
-    assert total == len(c2["idx"])
-    assert np.array_equal(offs.cpu().numpy(), c2["offs"])
-    assert np.array_equal(idx[:total].cpu().numpy(), c2["idx"])
-    e = rel_err(torch.stack(a, 1).double().cpu().numpy(), c2["a"])
+    got = torch.stack(a, 1).double().cpu().numpy()
+    _assert_matches_oracle(c2, got, gc.cpu().numpy(), gp.cpu().numpy(), offs.cpu().numpy(),
+                           idx[:total].cpu().numpy())
+    e = rel_err(got, c2["a"])
     assert np.median(e) <= 1e-7 and e.max() <= 1e-5, (np.median(e), e.max())
     ctx.close()

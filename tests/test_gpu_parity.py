@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 import torch
 
+import opening_cases
 import oracle
 import paper_2110_11658_b300 as p3t
 import synth
@@ -267,3 +268,26 @@ def test_row_mode_in_host_step():
         assert tot == len(i2) and np.array_equal(offs, o2) and np.array_equal(idx, i2)
         for u, w in zip(acc + vel, ref[3] + ref[4]):
             assert np.array_equal(u, w)
+
+
+@pytest.mark.parametrize("case", opening_cases.CASES, ids=[c[0] for c in opening_cases.CASES])
+@pytest.mark.parametrize("precision", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_opening_rule_decision_by_decision(case, precision):
+    # the hand-built pairs that pin the oracle's opening rule one decision at a
+    # time, several of them exactly on a threshold: the GPU's decisions (the
+    # mixed form's FP32 filter falls back to FP64 inside its error band) give the
+    # same per-group counts as the oracle and as the hand-worked table
+    cid, theta, r_out, X, sx, sy, gy, opened, why = case
+    x, y, z, m = opening_cases.particles(X, sx, sy, gy)
+    c = synth.Cluster(x=x, y=y, z=z, m=m, vx=np.zeros_like(x), vy=np.zeros_like(x), vz=np.zeros_like(x))
+    prm = p3t.Params(theta=theta, r_in=0.1 * r_out, r_out=r_out, r_list=r_out,
+                     leaf_cap=opening_cases.LEAF_CAP, group_size=opening_cases.GROUP_SIZE,
+                     precision=precision)
+    g = run_gpu(c, prm, pot=False, nbr=False)
+    t = oracle.Tree(x, y, z, m, theta, r_out, leaf_cap=opening_cases.LEAF_CAP,
+                    group_size=opening_cases.GROUP_SIZE)
+    f = t.far(0.1 * r_out)
+    assert np.array_equal(g["g_cells"], f["n_cell"])
+    assert np.array_equal(g["g_parts"], f["n_part"])
+    grp = int(np.nonzero(g["tree"]["g_first"] == 0)[0][0])
+    assert (int(g["g_cells"][grp]), int(g["g_parts"][grp])) == opening_cases.expected_counts(opened), why

@@ -11,6 +11,7 @@ import math
 import numpy as np
 import pytest
 
+import opening_cases
 import oracle
 import synth
 
@@ -265,3 +266,25 @@ def test_sampled_groups_match_full_walk():
     assert np.array_equal(part["a"][rows], full["a"][rows])
     assert np.array_equal(part["n_cell"], full["n_cell"][sel])
     assert math.isfinite(full["a"].sum())
+
+
+@pytest.mark.parametrize("case", opening_cases.CASES, ids=[c[0] for c in opening_cases.CASES])
+def test_opening_rule_decision_by_decision(case):
+    # one hand-built group/cell pair per case, on one side of a threshold of the
+    # opening rule or exactly on it; the expected decision is worked out by hand
+    # in the case table, with the mistake that would flip it
+    cid, theta, r_out, X, sx, sy, gy, opened, why = case
+    x, y, z, m = opening_cases.particles(X, sx, sy, gy)
+    t = oracle.Tree(x, y, z, m, theta, r_out, leaf_cap=opening_cases.LEAF_CAP,
+                    group_size=opening_cases.GROUP_SIZE)
+    d = t.export()
+    # the layout the table assumes: the root's children are the group's leaf,
+    # the cell's leaf and the ballast's branch, in that order
+    kids = list(range(d["child"][0], d["child"][0] + d["nchild"][0]))
+    assert [d["count"][k] for k in kids] == [2, 2, opening_cases.BALLAST]
+    assert d["nchild"][kids[0]] == 0 and d["nchild"][kids[1]] == 0
+    assert d["perm"][:4].tolist() == [0, 1, 2, 3]
+    g = int(np.nonzero(d["g_first"] == 0)[0][0])
+    assert d["g_count"][g] == 2
+    f = t.far(0.1 * r_out, groups=[g])
+    assert (int(f["n_cell"][0]), int(f["n_part"][0])) == opening_cases.expected_counts(opened), why

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2110_11658_b300 as p3t
 import synth
 
@@ -54,6 +55,10 @@ def test_noalloc_equals_build_tree_on_consecutive_calls():
         rk, rp = _regular(c)
         assert np.array_equal(keys, rk)
         assert np.array_equal(perm, rp)
+        # and directly against the oracle's keys, stably ordered by (key, index)
+        ok = oracle.morton_keys(c.x, c.y, c.z)
+        order = np.lexsort((np.arange(c.n), ok))
+        assert np.array_equal(perm, order) and np.array_equal(keys, ok[order])
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
@@ -71,3 +76,18 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     assert code == p3t.P3T_OK
     rk, rp = _regular(c)
     assert np.array_equal(keys2, rk) and np.array_equal(perm2, rp)
+
+
+def test_noalloc_invalid_input_does_not_carry_over():
+    # a NaN position is reported; the next valid call on the same shared array
+    # starts clean and returns the regular build's keys and permutation
+    torch.cuda.set_device(DEV)
+    bad = synth.plummer(3000, 104)
+    bad.x[1234] = np.nan
+    code, _, _ = _noalloc(bad)
+    assert code == p3t.P3T_ERR_INVALID_INPUT
+    good = synth.plummer(3000, 105)
+    code, keys, perm = _noalloc(good)
+    assert code == p3t.P3T_OK
+    rk, rp = _regular(good)
+    assert np.array_equal(keys, rk) and np.array_equal(perm, rp)
