@@ -58,6 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--group-size", type=int, default=32)
+    ap.add_argument("--threads-per-group", type=int, default=32,
+                    help="32: one warp per group; 64 or 128: one thread per target (G <= threads)")
     ap.add_argument("--tile", type=int, default=64)
     ap.add_argument("--leaf-cap", type=int, default=16)
     ap.add_argument("--r-buff", type=float, default=0.0,
@@ -289,7 +291,7 @@ def run_b300(args, rank, local, world):
         w["r_list"] = w["r_out"] + rb
     prm = p3t.Params(theta=w["theta"], r_in=w["r_in"], r_out=w["r_out"], r_list=w["r_list"],
                      leaf_cap=args.leaf_cap, group_size=args.group_size, tile=args.tile,
-                     precision=p3t.P3T_FP32_MIXED, quadrupole=1)
+                     threads_per_group=args.threads_per_group, precision=p3t.P3T_FP32_MIXED, quadrupole=1)
     stream = torch.cuda.current_stream(dev)
     ctx = p3t.Context(prm, stream)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
@@ -495,7 +497,8 @@ def bench_config(n, w, args, world):
     """The workload of the throughput line, identical in both arms."""
     return {"workload": "plummer_kroupa_n%d_theta%.1f_nbr100" % (n, THETA), "n": n, "theta": THETA,
             "r_out": w["r_out"], "r_in": w["r_in"], "r_list": w["r_list"], "leaf_cap": args.leaf_cap,
-            "group_size": args.group_size, "tile": args.tile, "dt": DT, "quadrupole": True,
+            "group_size": args.group_size, "threads_per_group": args.threads_per_group, "tile": args.tile,
+            "dt": DT, "quadrupole": True,
             "l2": "256 MB buffer written between timed steps (L2 is 126 MB)",
             "parallelism": "replicas" if world > 1 else "single"}
 
@@ -643,7 +646,7 @@ def _dist(ts):
 
 
 # the launch shape the autotuner picks for this ensemble (G, list tile, leaf capacity)
-ENS_TUNED = {"group_size": 32, "tile": 64, "leaf_cap": 16}
+ENS_TUNED = {"group_size": 32, "threads_per_group": 32, "tile": 64, "leaf_cap": 16}
 
 
 def ensemble_run(args, short=False):
@@ -688,7 +691,7 @@ def ensemble_run(args, short=False):
     def params(cfg):
         return p3t.Params(theta=ENS_THETA, r_in=rows[0][1], r_out=rows[0][2], r_list=rows[0][3],
                           leaf_cap=cfg["leaf_cap"], group_size=cfg["group_size"], tile=cfg["tile"],
-                          precision=p3t.P3T_FP32_MIXED)
+                          threads_per_group=cfg.get("threads_per_group", 32), precision=p3t.P3T_FP32_MIXED)
 
     def batched_graph(cfg, st):
         ctx = p3t.Context(params(cfg), stream)
@@ -707,7 +710,8 @@ def ensemble_run(args, short=False):
     if short:
         best, table = dict(ENS_TUNED), []
     elif args.no_tune:
-        best = {"group_size": args.group_size, "tile": args.tile, "leaf_cap": args.leaf_cap}
+        best = {"group_size": args.group_size, "threads_per_group": args.threads_per_group, "tile": args.tile,
+                "leaf_cap": args.leaf_cap}
         table = []
     else:
         res = autotune.Tuner(autotune.time_graph_step(lambda cfg: batched_graph(cfg, tune_state), steps=3),

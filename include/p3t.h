@@ -55,7 +55,10 @@ extern "C" {
  *  group_size   G, the largest particle group that walks the tree together (32, 64 or 128).
  *  tile         interaction-list tile: a group evaluates its buffered cells and
  *               particles once `tile` of them are queued (32..256, multiple of 32).
- *  threads_per_group  threads that evaluate one group (32).
+ *  threads_per_group  threads that evaluate one group: 32 (one warp; a lane holds
+ *               G/32 targets when G > 32), 64 or 128 (2 or 4 warps, one target per
+ *               thread, G <= threads_per_group: the first warp walks the tree for the
+ *               group and every warp evaluates the queued cells and particles).
  *  precision    P3T_FP32_MIXED or P3T_FP64.
  *  quadrupole   1: monopole + quadrupole cell terms; 0: monopole only. */
 typedef struct {

@@ -1,14 +1,17 @@
 """Autotuner of the walk's launch shape for a workload (ensemble or single cluster).
 
 The tuned knobs are the walk group size G (targets that share one interaction
-list: one warp, G/32 targets per lane), the list tile (interaction-list
-entries queued in shared memory before they are evaluated) and the leaf
-capacity L of the octree.  G and L change the group and leaf boxes and so the
+list), the threads per group (one warp with G/32 targets per lane, or G
+threads in G/32 warps with one target each, the first warp walking the tree),
+the list tile (interaction-list entries queued in shared memory before they
+are evaluated) and the leaf capacity L of the octree.  G and L change the group and leaf boxes and so the
 interaction lists themselves: a tuned configuration is part of the result's
 identity, and the oracle reproduces a result given the same G and L.
 
-The search runs in two stages to bound its cost: G x tile at the default leaf
-capacity, then L at the best (G, tile).  Every candidate is timed by a
+The search runs in two stages to bound its cost: G x threads per group x tile
+at the default leaf capacity, then L at the best (G, threads, tile).  The
+threads per group change only how the same lists are evaluated, not the
+results.  Every candidate is timed by a
 caller-supplied function (normally a graph-captured step of the real
 workload, see ``time_graph_step``) as the median of a few repeats.  Results
 can be cached in a JSON file, keyed by a workload signature.
@@ -24,13 +27,21 @@ from dataclasses import dataclass, field
 GROUP_SIZES = (32, 64, 128)
 TILES = (32, 64, 128, 256)
 LEAF_CAPS = (8, 16, 32)
-DEFAULT = {"group_size": 32, "tile": 64, "leaf_cap": 16}
+DEFAULT = {"group_size": 32, "threads_per_group": 32, "tile": 64, "leaf_cap": 16}
+
+
+def thread_counts(g: int):
+    """Threads per group worth trying for G: one warp, or one thread per target."""
+    return (32,) if g <= 32 else (32, 32 * ((g + 31) // 32))
 
 
 def valid(cfg: dict) -> bool:
-    """Launch shapes p3t_create accepts (tile a multiple of 32 in [32, 256], G <= 128)."""
+    """Launch shapes p3t_create accepts (tile a multiple of 32 in [32, 256], G <= 128,
+    32, 64 or 128 threads per group with G <= threads beyond one warp)."""
     g, t, leaf = cfg["group_size"], cfg["tile"], cfg["leaf_cap"]
-    return 1 <= g <= 128 and 32 <= t <= 256 and t % 32 == 0 and 1 <= leaf <= (1 << 20)
+    tpg = cfg.get("threads_per_group", 32)
+    return (1 <= g <= 128 and 32 <= t <= 256 and t % 32 == 0 and 1 <= leaf <= (1 << 20)
+            and tpg in (32, 64, 128) and (tpg == 32 or g <= tpg))
 
 
 def workload_key(device: str, sizes, precision: int, theta, extra: str = "") -> str:
@@ -50,7 +61,7 @@ class Result:
 
 
 class Tuner:
-    """Two-stage search over (G, tile) then leaf capacity.
+    """Two-stage search over (G, threads per group, tile) then leaf capacity.
 
     time_fn(cfg) -> milliseconds of one step with that configuration; it is
     called `repeats` times per candidate and the median is kept.
@@ -89,8 +100,8 @@ class Tuner:
             if hit is not None:
                 return Result(hit["best"], hit["best_ms"], [(c, ms) for c, ms in hit["table"]], cached=True)
         table = []
-        stage1 = [{"group_size": g, "tile": t, "leaf_cap": DEFAULT["leaf_cap"]}
-                  for g in self.group_sizes for t in self.tiles]
+        stage1 = [{"group_size": g, "threads_per_group": w, "tile": t, "leaf_cap": DEFAULT["leaf_cap"]}
+                  for g in self.group_sizes for w in thread_counts(g) for t in self.tiles]
         for cfg in stage1:
             if valid(cfg):
                 table.append((cfg, self._measure(cfg)))

@@ -172,7 +172,9 @@ static int validate_params(const p3t_params *p)
     if (p->leaf_cap < 1 || p->leaf_cap > (1 << 20)) return P3T_ERR_INVALID_ARG;
     if (p->group_size < 1 || p->group_size > 128) return P3T_ERR_INVALID_ARG;
     if (p->tile < 32 || p->tile > 256 || p->tile % 32) return P3T_ERR_INVALID_ARG;
-    if (p->threads_per_group != 32) return P3T_ERR_INVALID_ARG;
+    if (p->threads_per_group != 32 && p->threads_per_group != 64 && p->threads_per_group != 128)
+        return P3T_ERR_INVALID_ARG;
+    if (p->threads_per_group > 32 && p->group_size > p->threads_per_group) return P3T_ERR_INVALID_ARG;
     if (p->precision != P3T_FP32_MIXED && p->precision != P3T_FP64) return P3T_ERR_INVALID_ARG;
     if (p->quadrupole != 0 && p->quadrupole != 1) return P3T_ERR_INVALID_ARG;
     return P3T_OK;

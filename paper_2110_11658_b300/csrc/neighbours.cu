@@ -772,7 +772,9 @@ static int dispatch_nbr(p3t_ctx *c, const NbrArgs &a)
 // the fill pass then rebuilds.
 static void size_row_scratch(p3t_ctx *c, long long total)
 {
-    if (c->built_precision != P3T_FP32_MIXED || c->prm.group_size > 32 || c->n <= 0) return;
+    // (rows need one target per lane in the walk: G <= threads per group)
+    if (c->built_precision != P3T_FP32_MIXED || c->prm.group_size > c->prm.threads_per_group || c->n <= 0)
+        return;
     const long long mean = (total + c->n - 1) / c->n;
     const long long cap = std::max(64LL, std::min(4096LL, (8 * mean + 31) / 32 * 32));
     const size_t need = (size_t)c->cap_n * (size_t)cap;

@@ -47,13 +47,23 @@ def test_error_strings_and_defaults():
 
 @pytest.mark.parametrize("field,value", [("theta", -0.1), ("r_in", 0.06), ("r_out", 0.0),
                                          ("leaf_cap", 0), ("group_size", 129), ("tile", 48),
-                                         ("threads_per_group", 64), ("precision", 5),
+                                         ("threads_per_group", 96), ("threads_per_group", 16),
+                                         ("precision", 5),
                                          ("quadrupole", 2), ("r_list", -1.0)])
 def test_create_rejects_bad_params_without_gpu(field, value):
     import paper_2110_11658_b300 as p3t
     prm = p3t.Params()
     setattr(prm, field, value)
     cp = prm.to_c()
+    h = C.c_void_p()
+    assert p3t.p3t_create(C.byref(h), C.byref(cp), None) == p3t.P3T_ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_more_targets_than_threads_is_rejected():
+    # beyond one warp a group has one thread per target: G <= threads_per_group
+    import paper_2110_11658_b300 as p3t
+    cp = p3t.Params(group_size=128, threads_per_group=64).to_c()
     h = C.c_void_p()
     assert p3t.p3t_create(C.byref(h), C.byref(cp), None) == p3t.P3T_ERR_INVALID_ARG
     assert not h.value

@@ -7,20 +7,32 @@ from paper_2110_11658_b300 import autotune
 
 
 def _cost(cfg):
-    # a separable cost with its minimum at G = 64, tile = 128, leaf_cap = 8
-    return abs(cfg["group_size"] - 64) / 32 + abs(cfg["tile"] - 128) / 64 + abs(cfg["leaf_cap"] - 8) / 8 + 1.0
+    # a separable cost with its minimum at G = 64 on two warps, tile = 128, leaf_cap = 8
+    return (abs(cfg["group_size"] - 64) / 32 + abs(cfg["tile"] - 128) / 64 + abs(cfg["leaf_cap"] - 8) / 8
+            + (0.0 if cfg["threads_per_group"] == 64 else 0.5) + 1.0)
 
 
 def test_tuner_finds_minimum_in_two_stages():
     calls = []
     tuner = autotune.Tuner(lambda c: calls.append(c) or _cost(c), repeats=1)
     res = tuner.tune()
-    assert res.best == {"group_size": 64, "tile": 128, "leaf_cap": 8}
+    assert res.best == {"group_size": 64, "threads_per_group": 64, "tile": 128, "leaf_cap": 8}
     assert res.best_ms == pytest.approx(1.0)
-    # stage 1: 3 x 4 shapes at leaf_cap 16; stage 2: the two other leaf capacities
-    assert len(calls) == 12 + 2
-    assert all(c["leaf_cap"] == 16 for c in calls[:12])
-    assert {c["leaf_cap"] for c in calls[12:]} == {8, 32}
+    # stage 1: (G, threads) in (32, 32), (64, 32), (64, 64), (128, 32), (128, 128) x 4 tiles
+    # at leaf_cap 16; stage 2: the two other leaf capacities
+    assert len(calls) == 20 + 2
+    assert all(c["leaf_cap"] == 16 for c in calls[:20])
+    assert {(c["group_size"], c["threads_per_group"]) for c in calls[:20]} == {
+        (32, 32), (64, 32), (64, 64), (128, 32), (128, 128)}
+    assert {c["leaf_cap"] for c in calls[20:]} == {8, 32}
+
+
+def test_threads_per_group_validity():
+    ok = {"group_size": 64, "threads_per_group": 64, "tile": 64, "leaf_cap": 16}
+    assert autotune.valid(ok)
+    assert not autotune.valid(dict(ok, threads_per_group=96))
+    assert not autotune.valid(dict(ok, group_size=128))  # more targets than threads
+    assert autotune.valid(dict(ok, group_size=128, threads_per_group=32))  # 4 per lane
 
 
 def test_tuner_takes_median_of_repeats():
@@ -35,7 +47,7 @@ def test_tuner_skips_invalid_shapes():
     tuner = autotune.Tuner(lambda c: seen.append(c) or 1.0, repeats=1, group_sizes=(32, 256),
                            tiles=(64, 512), leaf_caps=(16,))
     tuner.tune()
-    assert seen == [{"group_size": 32, "tile": 64, "leaf_cap": 16}]
+    assert seen == [{"group_size": 32, "threads_per_group": 32, "tile": 64, "leaf_cap": 16}]
     with pytest.raises(ValueError):
         autotune.Tuner(lambda c: 1.0, group_sizes=(256,), tiles=(64,)).tune()
 

@@ -39,11 +39,15 @@ def _concat(cl):
     return synth.Cluster(*(cat(a) for a in ("x", "y", "z", "m", "vx", "vy", "vz"))), seg
 
 
+@pytest.mark.parametrize("shape", [(32, 32), (64, 64), (128, 128)], ids=["G32", "G64x64thr", "G128x128thr"])
 @pytest.mark.parametrize("precision", [p3t.P3T_FP32_MIXED, p3t.P3T_FP64], ids=["mixed", "fp64"])
-def test_batch_equals_each_cluster_alone(precision):
+def test_batch_equals_each_cluster_alone(precision, shape):
+    # every launch shape the autotuner searches: G and threads per group
+    G, tpg = shape
     cl = _ensemble()
     all_, seg = _concat(cl)
-    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, group_size=32, precision=precision)
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, group_size=G, threads_per_group=tpg,
+                     precision=precision)
     ctx = p3t.Context(prm)
     x, y, z, m = to_dev(all_.x), to_dev(all_.y), to_dev(all_.z), to_dev(all_.m)
     segd = torch.from_numpy(seg).to(DEV)
@@ -74,7 +78,7 @@ def test_batch_equals_each_cluster_alone(precision):
         rows_b = ob[s0:s1 + 1] - ob[s0]
         assert np.array_equal(rows_b, g["offs"])
         assert np.array_equal(ib[ob[s0]:ob[s1]] - s0, g["idx"])
-        t = oracle.Tree(c.x, c.y, c.z, c.m, 0.5, 0.05, leaf_cap=16, group_size=32)
+        t = oracle.Tree(c.x, c.y, c.z, c.m, 0.5, 0.05, leaf_cap=16, group_size=G)
         f = t.far(0.005)
         assert np.array_equal(g["g_cells"], f["n_cell"])
     assert tot == ob[-1]

@@ -291,3 +291,65 @@ def test_opening_rule_decision_by_decision(case, precision):
     assert np.array_equal(g["g_parts"], f["n_part"])
     grp = int(np.nonzero(g["tree"]["g_first"] == 0)[0][0])
     assert (int(g["g_cells"][grp]), int(g["g_parts"][grp])) == opening_cases.expected_counts(opened), why
+
+
+@pytest.mark.parametrize("G", [64, 128])
+@pytest.mark.parametrize("precision", [FP64, MIXED], ids=["fp64", "mixed"])
+def test_threads_per_group_forms(G, precision):
+    # G threads per group (the first warp walks, every warp evaluates its own 32
+    # targets) evaluate the same tiles in the same order as one warp holding G/32
+    # targets per lane: counts and lists bit for bit, and so are the mixed form's
+    # forces (explicit FP32 intrinsics); the FP64 form's plain expressions may be
+    # contracted into FMAs differently in the two kernels (1e-13); both against
+    # the oracle's tree of the same G
+    c = synth.make("king", 20000, synth.BASE_SEED + 5, masses="kroupa")
+    base = dict(theta=0.4, r_in=0.002, r_out=0.02, r_list=0.02, leaf_cap=8, group_size=G, precision=precision)
+    one = run_gpu(c, p3t.Params(threads_per_group=32, **base), kick_dt=1.0 / 256)
+    many = run_gpu(c, p3t.Params(threads_per_group=G, **base), kick_dt=1.0 / 256)
+    exact = ("g_cells", "g_parts", "offs", "idx") + (("a", "pot", "v") if precision == MIXED else ())
+    for k in exact:
+        assert np.array_equal(one[k], many[k]), k
+    if precision == FP64:
+        assert rel_err(many["a"], one["a"]).max() < 1e-13
+        assert np.abs(many["pot"] - one["pot"]).max() < 1e-13 * np.abs(one["pot"]).max()
+    assert one["n_cell"] == many["n_cell"] and one["n_part"] == many["n_part"]
+    t = _oracle(c, 0.4, 0.02, 8, G)
+    f = t.far(0.002)
+    assert np.array_equal(many["g_cells"], f["n_cell"])
+    assert np.array_equal(many["g_parts"], f["n_part"])
+    e = rel_err(many["a"], f["a"])
+    if precision == FP64:
+        assert e.max() < 1e-10
+    else:
+        assert np.median(e) <= 1e-5 and np.percentile(e, 99) <= 1e-4
+    o2, i2 = oracle.neighbours_brute(c.x, c.y, c.z, 0.02)
+    assert np.array_equal(many["offs"], o2) and np.array_equal(many["idx"], i2)
+
+
+@pytest.mark.parametrize("G", [64, 128])
+def test_threads_per_group_row_mode(G):
+    # with one target per thread the walk also writes the neighbour rows (row mode)
+    # from the second step on; lists equal the brute force, forces the first step's
+    c = synth.plummer(30000, synth.BASE_SEED + 6, masses="kroupa")
+    prm = p3t.Params(theta=0.5, r_in=0.003, r_out=0.03, r_list=0.03, leaf_cap=16, group_size=G,
+                     threads_per_group=G)
+    ctx = p3t.Context(prm)
+    d = [to_dev(getattr(c, k)) for k in "xyzm"]
+    a = [torch.empty(c.n, dtype=torch.float32, device=DEV) for _ in range(3)]
+    offs = torch.empty(c.n + 1, dtype=torch.int64, device=DEV)
+    idx = torch.empty(64 * c.n, dtype=torch.int32, device=DEV)
+    ctx.build_tree(*d)
+    ctx.far_force(*a)
+    ctx.neighbours(offs, idx)
+    first = torch.stack(a, 1).double().cpu().numpy()
+    o2, i2 = oracle.neighbours_brute(c.x, c.y, c.z, 0.03)
+    for _ in range(2):
+        ctx.build_tree(*d)
+        ctx.far_force(*a)
+        cap, valid = ctx.row_mode()
+        assert cap > 0 and valid == 1
+        tot = ctx.neighbours(offs, idx)
+        ctx.check()
+        assert np.array_equal(offs.cpu().numpy(), o2) and np.array_equal(idx[:tot].cpu().numpy(), i2)
+        assert np.array_equal(torch.stack(a, 1).double().cpu().numpy(), first)
+    ctx.close()
