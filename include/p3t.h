@@ -449,6 +449,71 @@ int p3t_batch_scatter_neighbours(void *cuda_stream, int32_t n_seg, int64_t n_bat
 int p3t_morton_order_noalloc(int64_t n, const double *x, const double *y, const double *z,
                              const double *m, uint64_t *keys, int32_t *perm, void *cuda_stream);
 
+/* ---- one cluster over several ranks (multi-GPU domain decomposition) -------
+ * The multi-GPU force calculator the paper leaves as future work (Sec. 4):
+ * rank r holds the particles whose Morton keys (rules 1-3, on the bounding box
+ * of the whole cluster) lie in [b_r, b_r+1).  The splitters b are cell
+ * boundaries of the global octree chosen so that every cell straddling one (a
+ * "top cell") holds more than max(16 G, leaf_cap) particles; the global tree is
+ * then the top cells plus complete subtrees that each belong to one rank, and
+ * every walk group of the whole cluster lies in one rank.  Each rank builds its
+ * part (p3t_build_tree_range), ships every other rank the part of its subtrees
+ * that the receiver's domain box opens (p3t_let_export: the locally essential
+ * tree, by rule 8 with r_out, or r_list when that is larger), and joins what it
+ * receives (p3t_tree_join).  Its groups then walk the global tree: interaction
+ * lists, forces and neighbour rows equal those of one build of the whole cluster,
+ * neighbour rows holding global indices.  The caller moves the data between
+ * ranks (NCCL or any transport): every array below is device memory of this
+ * rank unless marked host.  These calls synchronise the context's stream.
+ *
+ * p3t_local_bbox: exact min xyz, max xyz (host double[6]) of n device points.
+ * p3t_key_range_counts: counts[r] (host) = number of the n points whose key, in
+ *   the cube of global_box (host double[6], the ranks' boxes reduced), lies in
+ *   [lo[r], hi[r]) (host uint64, at most 1024 intervals).
+ * p3t_partition: the n particles packed by destination rank, rank r taking the
+ *   keys in [bounds[r], bounds[r+1]) (host, n_ranks + 1 bounds, bounds[0] = 0,
+ *   bounds[n_ranks] = 2^63): every src[a] (n 8-byte elements) is copied to dst[a]
+ *   (n elements), rank 0's particles first, each rank's in their input order;
+ *   counts (host, n_ranks) receives the particles per rank.
+ * p3t_build_tree_range: the rank's tree of its n particles (all inside its key
+ *   range), on the cube and frame of global_box (host), with the n_top top cells
+ *   (host: first key and level of each, at most 256, levels < 21) split whatever
+ *   their local count and never cut into groups; gid (device int64[n], < 2^31) the
+ *   particles' global indices, which order equal keys and fill neighbour rows.
+ *   Errors as p3t_build_tree; P3T_ERR_INVALID_INPUT when a particle lies outside
+ *   global_box.
+ * p3t_let_export: after p3t_build_tree_range, the locally essential tree of this
+ *   rank's subtrees for a receiver with domain box box (host double[6]) and radius
+ *   r_halo (max(r_out, r_list)): *n_roots subtree roots first, then the opened
+ *   nodes' children level by level, as *n_nodes records of P3T_LET_NODE_BYTES, and
+ *   the *n_parts particles of opened leaves (P3T_LET_PART_BYTES each).  With
+ *   cap_nodes = 0 only the sizes are returned (P3T_ERR_CAPACITY when they exceed
+ *   the capacities, sizes still set).
+ * p3t_tree_join: after p3t_build_tree_range, the rank's tree joined with the
+ *   locally essential trees of the n_let other ranks (device buffers as exported,
+ *   with their sizes and root counts; host arrays of n_let): the top cells'
+ *   moments are formed from the joined children (rule 6), and p3t_far_force,
+ *   p3t_neighbours and p3t_kick then work on the rank's own particles, in its input
+ *   order.  The joined tree holds copies of the remote nodes and particles; the
+ *   next build returns to the rank's own tree.  P3T_ERR_INVALID_INPUT when the
+ *   subtree roots do not complete the top cells (a missing or duplicated rank). */
+#define P3T_LET_NODE_BYTES 288
+#define P3T_LET_PART_BYTES 96
+int p3t_local_bbox(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z, double *box);
+int p3t_key_range_counts(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                         const double *global_box, int32_t n_ranges, const uint64_t *lo, const uint64_t *hi,
+                         int64_t *counts);
+int p3t_partition(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                  const double *global_box, int32_t n_ranks, const uint64_t *bounds, int32_t n_arrays,
+                  const void *const *src, void *const *dst, int64_t *counts);
+int p3t_build_tree_range(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                         const double *m, const int64_t *gid, const double *global_box, int32_t n_top,
+                         const uint64_t *top_key, const int32_t *top_level);
+int p3t_let_export(p3t_ctx *c, const double *box, double r_halo, int64_t cap_nodes, void *nodes,
+                   int64_t cap_parts, void *parts, int64_t *n_nodes, int64_t *n_parts, int32_t *n_roots);
+int p3t_tree_join(p3t_ctx *c, int32_t n_let, const void *const *let_nodes, const int64_t *let_n_nodes,
+                  const int32_t *let_n_roots, const void *const *let_parts, const int64_t *let_n_parts);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,7 +43,11 @@ EXPORTED = [
     "p3t_batch_move", "p3t_batch_scatter_neighbours", "p3t_filter_fallbacks", "p3t_irregular",
     "p3t_sample_knn6", "p3t_sample_knn6_brute", "p3t_core_quantities", "p3t_row_mode",
     "p3t_set_spin_limit", "p3t_debug_stalled_scan",
+    "p3t_local_bbox", "p3t_key_range_counts", "p3t_partition", "p3t_build_tree_range", "p3t_let_export",
+    "p3t_tree_join",
 ]
+P3T_LET_NODE_BYTES = 288
+P3T_LET_PART_BYTES = 96
 P3T_NOALLOC_MAX_N = 65536
 
 
@@ -117,6 +121,17 @@ _sig = {
     "p3t_scratch_bytes": [C.POINTER(p3t_params), _i64, C.c_int32, C.POINTER(_i64)],
     "p3t_batch_move": [_vp, C.c_int32, _i64, _vp, _vp, C.c_int32, C.POINTER(p3t_seg_array), C.c_int32],
     "p3t_batch_scatter_neighbours": [_vp, C.c_int32, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "p3t_local_bbox": [_vp, _i64, _vp, _vp, _vp, C.POINTER(C.c_double)],
+    "p3t_key_range_counts": [_vp, _i64, _vp, _vp, _vp, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_uint64),
+                             C.POINTER(C.c_uint64), C.POINTER(_i64)],
+    "p3t_partition": [_vp, _i64, _vp, _vp, _vp, C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_uint64),
+                      C.c_int32, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_i64)],
+    "p3t_build_tree_range": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, C.POINTER(C.c_double), C.c_int32,
+                             C.POINTER(C.c_uint64), C.POINTER(C.c_int32)],
+    "p3t_let_export": [_vp, C.POINTER(C.c_double), C.c_double, _i64, _vp, _i64, _vp, C.POINTER(_i64),
+                       C.POINTER(_i64), C.POINTER(C.c_int32)],
+    "p3t_tree_join": [_vp, C.c_int32, C.POINTER(_vp), C.POINTER(_i64), C.POINTER(C.c_int32), C.POINTER(_vp),
+                      C.POINTER(_i64)],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -246,6 +261,84 @@ class Context:
     def reserve(self, n: int, n_clusters: int = 1):
         """Size the scratch for n particles in n_clusters clusters now (p3t_reserve)."""
         _check(_lib.p3t_reserve(self._h, int(n), int(n_clusters)), "p3t_reserve")
+
+    # ---- one cluster over several ranks (include/p3t.h; orchestration in decomp.py)
+    def local_bbox(self, x, y, z):
+        """Exact min xyz, max xyz of the n device points (p3t_local_bbox)."""
+        n = x.numel()
+        box = (C.c_double * 6)()
+        _check(_lib.p3t_local_bbox(self._h, n, _ptr(x, self._torch.float64, n, "x"), _ptr(y, self._torch.float64, n, "y"),
+                                   _ptr(z, self._torch.float64, n, "z"), box), "p3t_local_bbox")
+        return list(box)
+
+    def key_range_counts(self, x, y, z, global_box, lo, hi):
+        """Points per key interval [lo[r], hi[r]) in the cube of global_box (p3t_key_range_counts)."""
+        n = 0 if x is None else x.numel()
+        nr = len(lo)
+        clo, chi = (C.c_uint64 * nr)(*lo), (C.c_uint64 * nr)(*hi)
+        out = (C.c_int64 * nr)()
+        gb = (C.c_double * 6)(*global_box)
+        _check(_lib.p3t_key_range_counts(self._h, n, _ptr(x), _ptr(y), _ptr(z), gb, nr, clo, chi, out),
+               "p3t_key_range_counts")
+        return list(out)
+
+    def partition(self, x, y, z, global_box, bounds, arrays):
+        """The particles packed by destination rank (p3t_partition): arrays is a list of
+        8-byte-element CUDA tensors of n elements; returns (packed tensors, counts)."""
+        t = self._torch
+        n = x.numel()
+        nb = len(bounds) - 1
+        cb = (C.c_uint64 * (nb + 1))(*bounds)
+        dst = [t.empty_like(a) for a in arrays]
+        for a in arrays:
+            if a.element_size() != 8 or a.numel() != n:
+                raise ValueError("partition arrays must hold n 8-byte elements")
+        src_p = (_vp * len(arrays))(*[_ptr(a) for a in arrays])
+        dst_p = (_vp * len(arrays))(*[_ptr(a) for a in dst])
+        cnt = (C.c_int64 * nb)()
+        gb = (C.c_double * 6)(*global_box)
+        _check(_lib.p3t_partition(self._h, n, _ptr(x), _ptr(y), _ptr(z), gb, nb, cb, len(arrays), src_p, dst_p, cnt),
+               "p3t_partition")
+        return dst, list(cnt)
+
+    def build_tree_range(self, x, y, z, m, gid, global_box, top_keys, top_levels):
+        """This rank's tree of a decomposed cluster (p3t_build_tree_range)."""
+        t = self._torch
+        n = x.numel()
+        nt = len(top_keys)
+        tk = (C.c_uint64 * max(1, nt))(*top_keys)
+        tl = (C.c_int32 * max(1, nt))(*top_levels)
+        gb = (C.c_double * 6)(*global_box)
+        _check(_lib.p3t_build_tree_range(self._h, n, _ptr(x, t.float64, n, "x"), _ptr(y, t.float64, n, "y"),
+                                         _ptr(z, t.float64, n, "z"), _ptr(m, t.float64, n, "m"),
+                                         _ptr(gid, t.int64, n, "gid"), gb, nt, tk, tl), "p3t_build_tree_range")
+
+    def let_export(self, box, r_halo):
+        """The locally essential tree of this rank for a receiver with domain box `box`
+        (p3t_let_export): (node bytes, particle bytes, n_nodes, n_roots, n_parts)."""
+        t = self._torch
+        cb = (C.c_double * 6)(*box)
+        nn, npt, nr = C.c_int64(0), C.c_int64(0), C.c_int32(0)
+        code = _lib.p3t_let_export(self._h, cb, float(r_halo), 0, None, 0, None, C.byref(nn), C.byref(npt), C.byref(nr))
+        if code not in (P3T_OK, P3T_ERR_CAPACITY):
+            _check(code, "p3t_let_export")
+        nodes = t.empty(max(1, nn.value) * P3T_LET_NODE_BYTES, dtype=t.uint8, device="cuda")
+        parts = t.empty(max(1, npt.value) * P3T_LET_PART_BYTES, dtype=t.uint8, device="cuda")
+        n2, p2 = C.c_int64(0), C.c_int64(0)
+        _check(_lib.p3t_let_export(self._h, cb, float(r_halo), max(1, nn.value), _ptr(nodes), max(1, npt.value),
+                                   _ptr(parts), C.byref(n2), C.byref(p2), C.byref(nr)), "p3t_let_export")
+        return nodes, parts, n2.value, nr.value, p2.value
+
+    def tree_join(self, lets):
+        """Join the locally essential trees of the other ranks (p3t_tree_join); lets is a
+        list of (node bytes, particle bytes, n_nodes, n_roots, n_parts)."""
+        k = len(lets)
+        nodes = (_vp * max(1, k))(*[_ptr(a[0]) for a in lets])
+        parts = (_vp * max(1, k))(*[_ptr(a[1]) for a in lets])
+        nn = (C.c_int64 * max(1, k))(*[int(a[2]) for a in lets])
+        nr = (C.c_int32 * max(1, k))(*[int(a[3]) for a in lets])
+        npt = (C.c_int64 * max(1, k))(*[int(a[4]) for a in lets])
+        _check(_lib.p3t_tree_join(self._h, k, nodes, nn, nr, parts, npt), "p3t_tree_join")
 
     def set_spin_limit(self, polls: int):
         _check(_lib.p3t_set_spin_limit(self._h, int(polls)), "p3t_set_spin_limit")

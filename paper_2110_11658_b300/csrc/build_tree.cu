@@ -20,14 +20,13 @@
 // reproducible bit for bit.
 #include <cstdint>
 
-#include "p3t_internal.cuh"
+#include "build_common.cuh"
 
 namespace p3t {
 
 constexpr int kBuildThreads = 256;
 constexpr int kSortTile = kSortTileItems;
 constexpr int kSortItems = kSortTile / kBuildThreads;
-constexpr unsigned long long kQMax = (1ULL << 21) - 1;
 
 int topo_status_stride(long long n);
 
@@ -115,17 +114,6 @@ __global__ void __launch_bounds__(kBuildThreads)
     cid[i] = lo;
 }
 
-// order-preserving map of non-NaN doubles onto unsigned integers
-__device__ __forceinline__ unsigned long long enc_double(double v)
-{
-    unsigned long long u = (unsigned long long)__double_as_longlong(v);
-    return (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
-}
-__device__ __forceinline__ double dec_double(unsigned long long e)
-{
-    unsigned long long u = (e >> 63) ? (e ^ 0x8000000000000000ULL) : ~e;
-    return __longlong_as_double((long long)u);
-}
 // isfinite(v) and (for a finite v) v >= 0, tested on the bits (no FP64 instruction)
 __device__ __forceinline__ bool finite_bits(double v)
 {
@@ -241,25 +229,6 @@ __global__ void cube_kernel(Cluster *cl, int C)
     K.scale = ddiv(2097152.0, side);
     // |x - O| <= R for every particle; pad for the rounding of O
     K.frame[3] = R * (1.0 + 1e-9) + 1e-300;
-}
-
-__device__ __forceinline__ unsigned long long spread3(unsigned long long v)
-{
-    v &= 0x1fffffULL;
-    v = (v | (v << 32)) & 0x1f00000000ffffULL;
-    v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
-    v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
-    v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
-    v = (v | (v << 2)) & 0x1249249249249249ULL;
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long quantise(double v, double lo, double s)
-{
-    double t = floor(dmul(dsub(v, lo), s));
-    if (!(t >= 0.0)) return 0;  // also NaN
-    if (t > (double)kQMax) return kQMax;
-    return (unsigned long long)t;
 }
 
 __global__ void __launch_bounds__(kBuildThreads)
@@ -381,12 +350,13 @@ __global__ void __launch_bounds__(kBuildThreads)
                   const int32_t *__restrict__ perm, const int32_t *__restrict__ cid,
                   const Cluster *__restrict__ cl, double4_32a *__restrict__ sp,
                   float4 *__restrict__ ph, float4 *__restrict__ pl, int32_t *__restrict__ inv,
-                  int32_t *__restrict__ cid_s)
+                  int32_t *__restrict__ cid_s, const int64_t *__restrict__ gid, int32_t *__restrict__ rid)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     int i = perm[s];
     inv[i] = s;
+    if (gid) rid[s] = (int32_t)gid[i];
     const int c = cid ? cid[i] : 0;
     cid_s[s] = c;
     const double *O = cl[c].frame;
@@ -436,8 +406,9 @@ __global__ void topo_root_kernel(Tree T, int n, int leaf_cap, int G)
     T.topo[c] = make_int4((int)first, cnt, -1, 0);
     T.level[c] = 0;
     T.parent[c] = -1;
-    if (cnt <= leaf_cap) T.leaves[atomicAdd(&T.meta->n_leaves, 1)] = c;
-    flag_groups(T.gflag, (int)first, cnt, true, cnt <= leaf_cap, G);
+    const bool top = T.n_top > 0 && is_top_cell(T, 0, 0ULL);  // a decomposed cluster's root
+    if (cnt <= leaf_cap && !top) T.leaves[atomicAdd(&T.meta->n_leaves, 1)] = c;
+    if (!top) flag_groups(T.gflag, (int)first, cnt, true, cnt <= leaf_cap, G);
 }
 
 // A level with at most kTopoWideNodes nodes splits one node per warp with a 32-way
@@ -475,7 +446,9 @@ __global__ void __launch_bounds__(kBuildThreads)
         int nch = 0;
         int4 tp = make_int4(0, 0, -1, 0);
         if (mine) tp = T.topo[node];
-        const bool split = mine && tp.y > leaf_cap && l < kLevels;
+        // a top cell of a decomposed cluster splits whatever its local count
+        const bool top = mine && T.n_top > 0 && tp.y > 0 && is_top_cell(T, l, T.keys[tp.x] >> (63 - 3 * l));
+        const bool split = mine && (tp.y > leaf_cap || top) && l < kLevels;
         if (split) {
             const int b = tp.x, e = tp.x + tp.y;
             const uint64_t pfx = T.keys[b] >> (shift + 3);
@@ -550,7 +523,9 @@ __global__ void __launch_bounds__(kBuildThreads)
 #pragma unroll
             for (int o = 0; o < 8; o++) {
                 const int cnt = bnd[o + 1] - bnd[o];
-                nlf += cnt > 0 && (cnt <= leaf_cap || l + 1 >= kLevels);
+                const bool ctop = T.n_top > 0 && cnt > 0 &&
+                                  is_top_cell(T, l + 1, T.keys[bnd[o]] >> (63 - 3 * (l + 1)));
+                nlf += cnt > 0 && (cnt <= leaf_cap || l + 1 >= kLevels) && !ctop;
             }
         }
         const int inc = warp_incl_scan(nlf);
@@ -558,7 +533,8 @@ __global__ void __launch_bounds__(kBuildThreads)
         if (lane == 31 && inc > 0) lf = atomicAdd(&M->n_leaves, inc);
         lf = __shfl_sync(0xffffffffu, lf, 31) + inc - nlf;
         if (write) {
-            const bool big = tp.y > kGroupNodeFactor * G;
+            // a top cell holds more than 16 G particles over all ranks
+            const bool big = tp.y > kGroupNodeFactor * G || top;
             int k = 0;
 #pragma unroll
             for (int o = 0; o < 8; o++) {
@@ -568,9 +544,10 @@ __global__ void __launch_bounds__(kBuildThreads)
                     T.topo[c] = make_int4(bnd[o], cnt, -1, 0);
                     T.level[c] = l + 1;
                     T.parent[c] = node;
-                    bool leaf = cnt <= leaf_cap || l + 1 >= kLevels;
+                    const bool ctop = T.n_top > 0 && is_top_cell(T, l + 1, T.keys[bnd[o]] >> (63 - 3 * (l + 1)));
+                    bool leaf = (cnt <= leaf_cap || l + 1 >= kLevels) && !ctop;
                     if (leaf) T.leaves[lf++] = c;
-                    flag_groups(T.gflag, bnd[o], cnt, big, leaf, G);
+                    if (!ctop) flag_groups(T.gflag, bnd[o], cnt, big, leaf, G);
                 }
             }
             T.topo[node] = make_int4(tp.x, tp.y, child_base, nch);
@@ -603,40 +580,6 @@ __global__ void __launch_bounds__(kBuildThreads)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && gflag[i]) grp[gidx[i]].x = i;
 }
-
-// Exact box bounds on the integer pipes: min/max of the order-preserving
-// encodings (no FP64 instruction).  Equal to the FP64 min/max except that -0
-// orders below +0, which changes no distance, extent or centre computed later.
-struct EncBox {
-    unsigned long long lo[3], hi[3];
-    __device__ void reset()
-    {
-        for (int d = 0; d < 3; d++) lo[d] = ~0ULL, hi[d] = 0ULL;
-    }
-    __device__ void add(double x, double y, double z)
-    {
-        unsigned long long e[3] = {enc_double(x), enc_double(y), enc_double(z)};
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            lo[d] = e[d] < lo[d] ? e[d] : lo[d];
-            hi[d] = e[d] > hi[d] ? e[d] : hi[d];
-        }
-    }
-    __device__ void add_box(const double4_32a &l, const double4_32a &h)
-    {
-        unsigned long long a[3] = {enc_double(l.x), enc_double(l.y), enc_double(l.z)};
-        unsigned long long b[3] = {enc_double(h.x), enc_double(h.y), enc_double(h.z)};
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            lo[d] = a[d] < lo[d] ? a[d] : lo[d];
-            hi[d] = b[d] > hi[d] ? b[d] : hi[d];
-        }
-    }
-    __device__ void get(double *l, double *h) const
-    {
-        for (int d = 0; d < 3; d++) l[d] = dec_double(lo[d]), h[d] = dec_double(hi[d]);
-    }
-};
 
 // one warp per group: count and tight box (exact min/max, order-free)
 __global__ void __launch_bounds__(kBuildThreads) group_finish_kernel(Tree T, int n)
@@ -766,58 +709,6 @@ __global__ void __launch_bounds__(kBuildThreads) group_order_kernel(Tree T)
 // moments (rule 6) and the opening radius (rule 8)
 
 template <bool Q64>
-__device__ void write_node(Tree &T, int k, double M, const double com[3], const double lo[3],
-                           const double hi[3], const double *q, double, int4 tp)
-{
-    const Cluster &K = T.cl[T.cid_s[tp.x < T.n ? tp.x : 0]];
-    const double theta = K.theta;
-    // opening radius l/theta + delta
-    double l = dsub(hi[0], lo[0]);
-    if (dsub(hi[1], lo[1]) > l) l = dsub(hi[1], lo[1]);
-    if (dsub(hi[2], lo[2]) > l) l = dsub(hi[2], lo[2]);
-    double cx = dsub(dmul(0.5, dadd(lo[0], hi[0])), com[0]);
-    double cy = dsub(dmul(0.5, dadd(lo[1], hi[1])), com[1]);
-    double cz = dsub(dmul(0.5, dadd(lo[2], hi[2])), com[2]);
-    double delta = dsqrt(dadd(dadd(dmul(cx, cx), dmul(cy, cy)), dmul(cz, cz)));
-    double ro2;
-    if (theta > 0.0) {
-        double ro = dadd(ddiv(l, theta), delta);
-        ro2 = dmul(ro, ro);
-    } else {
-        ro2 = INFINITY;
-    }
-    T.comM[k] = make_double4_32a(com[0], com[1], com[2], M);
-    T.lo[k] = make_double4_32a(lo[0], lo[1], lo[2], ro2);
-    T.hi[k] = make_double4_32a(hi[0], hi[1], hi[2], 0.0);
-    if (Q64) {
-        double2 *q2 = reinterpret_cast<double2 *>(T.q64 + 6 * (size_t)k);
-        q2[0] = make_double2(q[0], q[1]);
-        q2[1] = make_double2(q[2], q[3]);
-        q2[2] = make_double2(q[4], q[5]);
-    } else {
-        float2 *q2 = reinterpret_cast<float2 *>(T.q32 + 6 * (size_t)k);
-        q2[0] = make_float2((float)q[0], (float)q[1]);
-        q2[1] = make_float2((float)q[2], (float)q[3]);
-        q2[2] = make_float2((float)q[4], (float)q[5]);
-    }
-    const double *O = K.frame;
-    const bool leaf = tp.z < 0;
-    float chx, chy, chz, clx, cly, clz;
-    ds_split(dsub(com[0], O[0]), chx, clx);
-    ds_split(dsub(com[1], O[1]), chy, cly);
-    ds_split(dsub(com[2], O[2]), chz, clz);
-    float4 *w = T.wn + (size_t)kWalkRecord * k;
-    w[0] = make_float4(chx, chy, chz, __double2float_rn(ro2));
-    w[1] = make_float4(__double2float_rn(dsub(lo[0], O[0])), __double2float_rn(dsub(lo[1], O[1])),
-                       __double2float_rn(dsub(lo[2], O[2])), __int_as_float(leaf ? -1 - tp.x : tp.z));
-    w[2] = make_float4(__double2float_rn(dsub(hi[0], O[0])), __double2float_rn(dsub(hi[1], O[1])),
-                       __double2float_rn(dsub(hi[2], O[2])), __int_as_float(leaf ? tp.y : tp.w));
-    w[3] = make_float4(clx, cly, clz, __double2float_rn(M));
-    w[4] = make_float4((float)q[0], (float)q[1], (float)q[2], (float)q[3]);
-    w[5] = make_float4((float)q[4], (float)q[5], 0.f, 0.f);
-}
-
-template <bool Q64>
 __device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
 {
     const int b = tp.x, e = tp.x + tp.y;
@@ -883,85 +774,6 @@ __device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
             Q[3] += m * (3.f * dy * dy - r2);
             Q[4] += m * (3.f * dy * dz);
             Q[5] += m * (3.f * dz * dz - r2);
-        }
-        for (int a = 0; a < 6; a++) q[a] = Q[a];
-    }
-    write_node<Q64>(T, k, M, com, lo, hi, q, theta, tp);
-}
-
-// L2-coherent load of a value written by another block in this kernel
-__device__ __forceinline__ double4_32a ldcg_d4(const double4_32a *p)
-{
-    const double2 *q = reinterpret_cast<const double2 *>(p);
-    double2 a = __ldcg(q), b = __ldcg(q + 1);
-    return make_double4_32a(a.x, a.y, b.x, b.y);
-}
-
-template <bool Q64>
-__device__ void internal_moments(Tree &T, int k, int4 tp, double theta)
-{
-    const int c0 = tp.z, c1 = tp.z + tp.w;
-    double M = 0.0, S[3] = {0, 0, 0}, lo[3], hi[3], com[3];
-    EncBox box;
-    box.reset();
-    // at most 8 children: every child's record is loaded before the
-    // (sequential, octant-order) sums
-    const int nc = c1 - c0;
-    double4_32a cm[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++)
-        if (i < nc) cm[i] = ldcg_d4(&T.comM[c0 + i]);
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        if (i < nc) {
-            const double4_32a cl = ldcg_d4(&T.lo[c0 + i]);
-            const double4_32a ch = ldcg_d4(&T.hi[c0 + i]);
-            M = dadd(M, cm[i].w);
-            S[0] = dadd(S[0], dmul(cm[i].w, cm[i].x));
-            S[1] = dadd(S[1], dmul(cm[i].w, cm[i].y));
-            S[2] = dadd(S[2], dmul(cm[i].w, cm[i].z));
-            box.add_box(cl, ch);
-        }
-    }
-    box.get(lo, hi);
-    for (int d = 0; d < 3; d++) com[d] = M > 0.0 ? ddiv(S[d], M) : dmul(0.5, dadd(lo[d], hi[d]));
-    double q[6];
-    if (Q64) {
-        double Q[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            if (i >= nc) break;
-            const int c = c0 + i;
-            const double *Qc = T.q64 + 6 * (size_t)c;
-            double Mc = cm[i].w;
-            double dx = dsub(cm[i].x, com[0]), dy = dsub(cm[i].y, com[1]), dz = dsub(cm[i].z, com[2]);
-            double d2 = dadd(dadd(dmul(dx, dx), dmul(dy, dy)), dmul(dz, dz));
-            Q[0] = dadd(Q[0], dadd(__ldcg(Qc + 0), dmul(Mc, dsub(dmul(dmul(3.0, dx), dx), d2))));
-            Q[1] = dadd(Q[1], dadd(__ldcg(Qc + 1), dmul(Mc, dmul(dmul(3.0, dx), dy))));
-            Q[2] = dadd(Q[2], dadd(__ldcg(Qc + 2), dmul(Mc, dmul(dmul(3.0, dx), dz))));
-            Q[3] = dadd(Q[3], dadd(__ldcg(Qc + 3), dmul(Mc, dsub(dmul(dmul(3.0, dy), dy), d2))));
-            Q[4] = dadd(Q[4], dadd(__ldcg(Qc + 4), dmul(Mc, dmul(dmul(3.0, dy), dz))));
-            Q[5] = dadd(Q[5], dadd(__ldcg(Qc + 5), dmul(Mc, dsub(dmul(dmul(3.0, dz), dz), d2))));
-        }
-        for (int a = 0; a < 6; a++) q[a] = Q[a];
-    } else {
-        float Q[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            if (i >= nc) break;
-            const int c = c0 + i;
-            const float *Qc = T.q32 + 6 * (size_t)c;
-            float Mc = (float)cm[i].w;
-            float dx = __double2float_rn(dsub(cm[i].x, com[0]));
-            float dy = __double2float_rn(dsub(cm[i].y, com[1]));
-            float dz = __double2float_rn(dsub(cm[i].z, com[2]));
-            float d2 = dx * dx + dy * dy + dz * dz;
-            Q[0] += __ldcg(Qc + 0) + Mc * (3.f * dx * dx - d2);
-            Q[1] += __ldcg(Qc + 1) + Mc * (3.f * dx * dy);
-            Q[2] += __ldcg(Qc + 2) + Mc * (3.f * dx * dz);
-            Q[3] += __ldcg(Qc + 3) + Mc * (3.f * dy * dy - d2);
-            Q[4] += __ldcg(Qc + 4) + Mc * (3.f * dy * dz);
-            Q[5] += __ldcg(Qc + 5) + Mc * (3.f * dz * dz - d2);
         }
         for (int a = 0; a < 6; a++) q[a] = Q[a];
     }
@@ -1108,16 +920,59 @@ __global__ void __launch_bounds__(kBuildThreads) moments_level_kernel(Tree T, in
 }
 
 // ---------------------------------------------------------------------------
+// global indices (< 2^31) as int32 digits for the range build's first sort passes
+__global__ void __launch_bounds__(kBuildThreads)
+    gid32_kernel(int n, const int64_t *__restrict__ gid, int32_t *__restrict__ g32, Meta *meta)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t v = gid[i];
+    if (v < 0 || v >= (1LL << 31)) latch_error(meta, P3T_ERR_INVALID_INPUT);
+    g32[i] = (int32_t)v;
+}
+
+// the global bounding box of a decomposed cluster in place of the rank's own (the
+// rank's particles, already validated by bbox_kernel, must lie inside it)
+__global__ void set_bbox_kernel(Cluster *cl, double lx, double ly, double lz, double hx, double hy,
+                                double hz, Meta *meta)
+{
+    Cluster &K = cl[0];
+    const double lo[3] = {lx, ly, lz}, hi[3] = {hx, hy, hz};
+    for (int d = 0; d < 3; d++) {
+        const unsigned long long a = enc_double(lo[d]), b = enc_double(hi[d]);
+        const bool empty = K.minmax[d] == ~0ULL;
+        if (!empty && (K.minmax[d] < a || K.minmax[3 + d] > b)) latch_error(meta, P3T_ERR_INVALID_INPUT);
+        K.minmax[d] = a;
+        K.minmax[3 + d] = b;
+    }
+}
+
+// The cube and frame of a decomposed cluster's global bounding box into the device
+// cluster record *cl (rule 1, as a build computes them), for the key counts and the
+// partition of particles among ranks.
+int global_frame(cudaStream_t s, const double box[6], Cluster *cl, Meta *meta)
+{
+    init_clusters_kernel<<<1, 32, 0, s>>>(cl, 1);
+    set_bbox_kernel<<<1, 1, 0, s>>>(cl, box[0], box[1], box[2], box[3], box[4], box[5], meta);
+    cube_kernel<<<1, 32, 0, s>>>(cl, 1);
+    return cudaGetLastError() == cudaSuccess ? P3T_OK : P3T_ERR_CUDA;
+}
+
 int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *cprm,
-               const double *x, const double *y, const double *z, const double *m)
+               const double *x, const double *y, const double *z, const double *m,
+               const RangeSpec *range)
 {
     cudaStream_t s = c->stream;
     Tree &T = c->tree;
     Meta *M = c->meta;
     const p3t_params &P = c->prm;
     T.n = n;
+    T.n_src = n;
     T.n_clusters = n_clusters;
     T.seg = seg;
+    T.n_top = range ? range->n_top : 0;
+    T.top_key = c->top_buf;
+    T.top_level = reinterpret_cast<const int32_t *>(c->top_buf + kMaxTopCells);
     const int32_t *cid = seg ? T.cid : nullptr;  // null: a single cluster
     const int grid_n = (n + kBuildThreads - 1) / kBuildThreads;
     const int grid_c = (n_clusters + 127) / 128;
@@ -1129,21 +984,29 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
                                                  P.r_list, M);
     if (seg) cid_kernel<<<(n > n_clusters ? grid_n : grid_c + 1), kBuildThreads, 0, s>>>(n, n_clusters, seg, T.cid, M);
     bbox_kernel<<<persistent, kBuildThreads, 0, s>>>(n, x, y, z, m, cid, T.cl, M);
+    if (range)
+        set_bbox_kernel<<<1, 1, 0, s>>>(T.cl, range->box[0], range->box[1], range->box[2], range->box[3],
+                                        range->box[4], range->box[5], M);
     cube_kernel<<<grid_c, 128, 0, s>>>(T.cl, n_clusters);
     keys_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, cid, T.cl, c->keys_buf[0], c->perm_buf[0]);
     if (check_launch(c)) return P3T_ERR_CUDA;
 
     // 8 passes of 8 bits over the key, then (batched builds) stable passes over the
-    // cluster id, so the order is (cluster, key, original index)
+    // cluster id, so the order is (cluster, key, original index).  A rank's part of
+    // a decomposed cluster sorts by the global index first (4 passes over its low 32
+    // bits), so that its order is (key, global index), as in one build of the whole.
     const int nb = (n + kSortTile - 1) / kSortTile;
     const int cid_passes = seg ? (n_clusters <= 256 ? 1 : (n_clusters <= 65536 ? 2 : 3)) : 0;
-    const int passes = 8 + cid_passes;
+    const int gid_passes = range && range->gid ? 4 : 0;
+    if (gid_passes) gid32_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, range->gid, c->rid_buf, M);
+    const int passes = gid_passes + 8 + cid_passes;
     for (int pass = 0; pass < passes; pass++) {
-        const bool by_cid = pass >= 8;
-        const int shift = by_cid ? 8 * (pass - 8) : 8 * pass;
+        const bool by_gid = pass < gid_passes;
+        const bool by_cid = pass >= gid_passes + 8;
+        const int shift = by_gid ? 8 * pass : (by_cid ? 8 * (pass - gid_passes - 8) : 8 * (pass - gid_passes));
         uint64_t *kin = c->keys_buf[pass & 1], *kout = c->keys_buf[(pass + 1) & 1];
         int32_t *vin = c->perm_buf[pass & 1], *vout = c->perm_buf[(pass + 1) & 1];
-        const int32_t *dcid = by_cid ? T.cid : nullptr;
+        const int32_t *dcid = by_cid ? T.cid : (by_gid ? c->rid_buf : nullptr);
         sort_hist_kernel<<<nb, kBuildThreads, 0, s>>>(n, kin, vin, dcid, shift, nb, c->sort_hist);
         if (check_launch(c)) return P3T_ERR_CUDA;
         int e = scan_excl_i32_to_i32(c->sort_hist, c->sort_hist, 256 * nb, c->scan_status,
@@ -1155,8 +1018,10 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     }
     T.keys = c->keys_buf[passes & 1];
     T.perm = c->perm_buf[passes & 1];
+    const int64_t *gid = range ? range->gid : nullptr;
+    T.rid = gid ? c->rid_buf : T.perm;
     gather_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, m, T.perm, cid, T.cl, T.sp, T.ph, T.pl,
-                                                    T.inv, T.cid_s);
+                                                    T.inv, T.cid_s, gid, T.rid);
 
     // topology, level by level
     unsigned long long *topo_status = c->scan_status + (n / 256 + 64 + 256 * nb / 256);

@@ -67,6 +67,8 @@ static size_t scratch_plan(p3t_ctx *c, long long N, int L, char *base)
     put(&T.gbins, 4 * 512);
     put(&c->nbr_count, 4 * (size_t)N);
     put(&c->row_list, 4 * (size_t)N);
+    put(&c->rid_buf, 4 * (size_t)N);
+    put(&c->top_buf, 12 * (size_t)kMaxTopCells);
     put(&c->grp_cells, 8 * (size_t)N);
     put(&c->grp_parts, 8 * (size_t)N);
     put(&c->sort_hist, 4 * 256 * (size_t)sort_blocks);
@@ -124,6 +126,15 @@ int ensure_capacity(p3t_ctx *c, long long n)
                         cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
         return P3T_ERR_CUDA;
     return P3T_OK;
+}
+
+// Point the tree views back at the context's own scratch (a rank's tree may
+// have been joined with remote nodes and particles in other buffers).
+void reset_tree_views(p3t_ctx *c)
+{
+    if (c->blob) scratch_plan(c, c->cap_n, c->cap_leaf, (char *)c->blob);
+    c->tree.meta = c->meta;
+    c->tree.cap_nodes = (int)c->cap_nodes;
 }
 
 // Scratch for n particles in n_clusters clusters (no work is enqueued unless
@@ -240,6 +251,8 @@ int p3t_destroy(p3t_ctx *c)
     if (c->clusters) cudaFree(c->clusters);
     if (c->irr_buf) cudaFree(c->irr_buf);
     if (c->knn_buf) cudaFree(c->knn_buf);
+    if (c->dec_buf) cudaFree(c->dec_buf);
+    if (c->join_buf) cudaFree(c->join_buf);
     delete c;
     return P3T_OK;
 }
@@ -274,7 +287,7 @@ int p3t_scratch_bytes(const p3t_params *p, int64_t n, int32_t n_clusters, int64_
 
 static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *seg,
                         const double *cprm, const double *x, const double *y, const double *z,
-                        const double *m)
+                        const double *m, const RangeSpec *range = nullptr)
 {
     if (!c || !x || !y || !z || !m) return P3T_ERR_INVALID_ARG;
     if (n <= 0 || n >= (1LL << 31) - 1) return P3T_ERR_INVALID_ARG;
@@ -282,12 +295,15 @@ static int build_common(p3t_ctx *c, int64_t n, int n_clusters, const int64_t *se
     if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 28)) return P3T_ERR_INVALID_ARG;
     int e = reserve(c, n, n_clusters);
     if (e) return e;
+    reset_tree_views(c);  // a joined tree's views point elsewhere
     c->built = 0;
     c->counts_valid = 0;
     c->walk_counted = 0;
     c->rows_valid = 0;
+    c->range_built = range != nullptr;
+    c->joined = 0;
     c->uniform_params = cprm == nullptr;
-    e = build_tree(c, (int)n, n_clusters, seg, cprm, x, y, z, m);
+    e = build_tree(c, (int)n, n_clusters, seg, cprm, x, y, z, m, range);
     if (e) return e;
     c->n = (int)n;
     c->built = 1;
@@ -299,6 +315,47 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *x, const double *y, cons
                    const double *m)
 {
     return build_common(c, n, 1, nullptr, nullptr, x, y, z, m);
+}
+
+int p3t_build_tree_range(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
+                         const double *m, const int64_t *gid, const double *global_box, int32_t n_top,
+                         const uint64_t *top_key, const int32_t *top_level)
+{
+    if (!c || !global_box || n_top < 0 || n_top > kMaxTopCells || (n_top > 0 && (!top_key || !top_level)))
+        return P3T_ERR_INVALID_ARG;
+    for (int d = 0; d < 3; d++)
+        if (!(global_box[d] <= global_box[3 + d]) || !std::isfinite(global_box[d]) ||
+            !std::isfinite(global_box[3 + d]))
+            return P3T_ERR_INVALID_ARG;
+    for (int i = 0; i < n_top; i++) {
+        const int l = top_level[i];
+        // a top cell splits: level < 21, its key the first of a level-l cell
+        if (l < 0 || l >= kLevels || (l > 0 && (top_key[i] & ((1ULL << (63 - 3 * l)) - 1))) ||
+            (l == 0 && top_key[i] != 0) || top_key[i] >= (1ULL << 63))
+            return P3T_ERR_INVALID_ARG;
+    }
+    if (!x || n <= 0 || n >= (1LL << 31) - 1) return P3T_ERR_INVALID_ARG;
+    if (node_capacity(n, c->prm.leaf_cap) >= (1LL << 28)) return P3T_ERR_INVALID_ARG;
+    int e = reserve(c, n, 1);  // the scratch the top-cell table lives in (the build reserves no more)
+    if (e) return e;
+    c->n_top = n_top;
+    memcpy(c->gbox, global_box, sizeof(c->gbox));
+    for (int i = 0; i < n_top; i++) c->top_key[i] = top_key[i], c->top_level[i] = top_level[i];
+    unsigned long long hbuf[kMaxTopCells + kMaxTopCells / 2];
+    memcpy(hbuf, top_key, sizeof(uint64_t) * n_top);
+    memcpy(reinterpret_cast<char *>(hbuf) + 8 * kMaxTopCells, top_level, sizeof(int32_t) * n_top);
+    if (n_top > 0 &&
+        (cudaMemcpyAsync(c->top_buf, hbuf, 8 * n_top, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+         cudaMemcpyAsync(reinterpret_cast<char *>(c->top_buf) + 8 * kMaxTopCells,
+                         reinterpret_cast<char *>(hbuf) + 8 * kMaxTopCells, 4 * n_top,
+                         cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+         cudaStreamSynchronize(c->stream) != cudaSuccess))
+        return P3T_ERR_CUDA;
+    RangeSpec r;
+    memcpy(r.box, global_box, sizeof(r.box));
+    r.n_top = n_top;
+    r.gid = gid;
+    return build_common(c, n, 1, nullptr, nullptr, x, y, z, m, &r);
 }
 
 int p3t_build_tree_batch(p3t_ctx *c, int32_t n_clusters, int64_t n, const int64_t *seg_offsets,

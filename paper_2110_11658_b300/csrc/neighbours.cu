@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         // targets: coordinates relative to c_g, original index `me`; an empty slot sits
         // at 1e30 so that no FP32 test counts it (its rare FP64 path checks si < 0)
         float px[TPL], py[TPL], pz[TPL];
-        int si[TPL], cnt[TPL], me[TPL];
+        int si[TPL], cnt[TPL], me[TPL];  // me: the target's row id (as its sources carry)
         int32_t *wp[TPL];  // fill: next entry of the target's row
         // count pass in row mode: neighbours among the staged chunk (bit = slot), the
         // target's scratch row and its entries (an empty slot writes nothing)
@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 pz[t] = (h.z - fhz) + (l.z - flz);
                 si[t] = s;
                 A = fmaxf(A, fmaxf(fabsf(px[t]), fmaxf(fabsf(py[t]), fabsf(pz[t]))));
-                me[t] = T.perm[s];
-                if (FILL) wp[t] = P.idx + P.offs[me[t]];
+                me[t] = T.rid[s];
+                if (FILL) wp[t] = P.idx + P.offs[T.perm[s]];
             } else {
                 px[t] = py[t] = pz[t] = 1e30f;
                 si[t] = -1;
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 const bool open_int = open && !is_leaf;
                 const bool open_leaf = open && is_leaf;
                 const bool bad = (open_int && (ccount < 1 || ccount > 8 || cinfo + ccount > nn)) ||
-                                 (open_leaf && (ccount < 1 || -1 - cinfo + ccount > T.n));
+                                 (open_leaf && (ccount < 1 || -1 - cinfo + ccount > T.n_src));
                 if (__any_sync(0xffffffffu, bad)) {
                     if (lane == 0) latch_error(meta, P3T_ERR_INTERNAL);
                     break;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                     pb[0] = (h.x - fhx) + (l.x - flx);
                     pb[2] = (h.y - fhy) + (l.y - fly);
                     pb[4] = (h.z - fhz) + (l.z - flz);
-                    pb[6] = __int_as_float(T.perm[j]);
+                    pb[6] = __int_as_float(T.rid[j]);
                     W.pj[lane] = j;
                 }
                 __syncwarp();

@@ -124,7 +124,27 @@ struct Tree {
     int32_t *leaves;       // leaf node indices, in creation order (moments work list)
     int32_t *inv;          // original index -> position in key order
     Meta *meta;
+    // the ids neighbour rows hold, key order: perm (the caller's original index) or,
+    // for a rank of a decomposed cluster, the particle's global index
+    int32_t *rid;
+    int n_src;             // particles in the source arrays (sp, ph, pl, rid): n, or more
+                           // once remote particles are joined to a rank's tree
+    // a rank's part of a decomposed cluster: cells split whatever their count (they
+    // hold particles of other ranks too) and never cut into walk groups
+    int n_top;
+    const unsigned long long *top_key;  // first key of each such cell
+    const int32_t *top_level;
 };
+
+constexpr int kMaxTopCells = 256;  // top cells of a decomposed cluster (about 21 per splitter)
+
+// node k of a range build is a top cell: level l, prefix = its first key >> (63 - 3 l)
+__device__ __forceinline__ bool is_top_cell(const Tree &T, int l, unsigned long long prefix)
+{
+    for (int i = 0; i < T.n_top; i++)
+        if (T.top_level[i] == l && (T.top_key[i] >> (63 - 3 * l)) == prefix) return true;
+    return false;
+}
 
 // ---- error latch ---------------------------------------------------------------
 __device__ __forceinline__ void latch_error(Meta *m, int code)
@@ -398,6 +418,8 @@ struct p3t_ctx {
     unsigned long long *scan_status;  // look-back status words
     int32_t *nbr_count;               // per particle (original order)
     int32_t *row_list;                // neighbour rows binned by length class
+    int32_t *rid_buf;                 // global row ids of a range build (key order)
+    unsigned long long *top_buf;      // top cells of a range build: keys, then levels
     int32_t *row_scratch;             // row mode: neighbour rows written by the far-force walk
     size_t row_scratch_entries;       // (row_cap entries per particle, key order)
     int row_cap;                      // entries per row for the next walks (0: row mode off)
@@ -415,6 +437,17 @@ struct p3t_ctx {
     size_t irr_bytes;
     void *knn_buf;                    // per-chunk lists of p3t_sample_knn6
     size_t knn_bytes;
+    // a rank's part of a decomposed cluster (decomp.cu)
+    int range_built;                  // the current tree came from p3t_build_tree_range
+    int joined;                       // ... and has been joined with remote trees
+    int n_top;                        // its top cells (host copy)
+    unsigned long long top_key[p3t::kMaxTopCells];
+    int32_t top_level[p3t::kMaxTopCells];
+    double gbox[6];                   // the global bounding box
+    void *dec_buf;                    // working memory of the decomposition calls
+    size_t dec_bytes;
+    void *join_buf;                   // the joined tree's node and particle arrays
+    size_t join_bytes;
 };
 
 namespace p3t {
@@ -450,8 +483,18 @@ int reserve(p3t_ctx *c, long long n, int n_clusters);
 int scan_stalled(int n, const int32_t *in, int32_t *out, unsigned long long *status,
                  unsigned int *ticket, Meta *meta, cudaStream_t s);
 int check_launch(p3t_ctx *c);
+// A rank's part of a decomposed cluster (p3t_build_tree_range): the global bounding
+// box (min xyz, max xyz), the ranks' top cells and the particles' global indices.
+struct RangeSpec {
+    double box[6];
+    int n_top;
+    const int64_t *gid;  // device, the caller's order (null: rows hold local indices)
+};
 int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const double *cprm,
-               const double *x, const double *y, const double *z, const double *m);
+               const double *x, const double *y, const double *z, const double *m,
+               const RangeSpec *range = nullptr);
+void reset_tree_views(p3t_ctx *c);
+int global_frame(cudaStream_t s, const double box[6], Cluster *cl, Meta *meta);
 int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc, int64_t *np);
 int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, int64_t *total_dev,
                bool sync, int64_t *total_host);

@@ -668,7 +668,7 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
             const float4 r = ds_rel(P.T.ph[j], P.T.pl[j], F);
             pb[0] = r.x, pb[2] = r.y, pb[4] = r.z, pb[6] = lx < 0 ? 0.f : r.w;
             if (NBR) W.pj[lane] = j;
-            if (NBR == 2) W.po[lane] = P.T.perm[j];
+            if (NBR == 2) W.po[lane] = P.T.rid[j];
         }
         __syncwarp();
         if ((ns & 1) && lane == 0) {
@@ -1080,7 +1080,7 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
             const bool open_leaf = node >= 0 && ((open && !nbr_only) || go_nbr) && is_leaf;
             // consistency of the child / particle ranges before following them
             const bool bad = (open_int && (ccount < 1 || ccount > 8 || cinfo + ccount > nn)) ||
-                             (open_leaf && (ccount < 1 || -1 - cinfo + ccount > T.n));
+                             (open_leaf && (ccount < 1 || -1 - cinfo + ccount > T.n_src));
             if (__any_sync(0xffffffffu, bad)) {
                 if (lane == 0) latch_error(meta, P3T_ERR_INTERNAL);
                 return false;
