@@ -68,14 +68,17 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
-    ap.add_argument("--workload", default="plummer1m", choices=["plummer1m", "king2m", "ensemble64", "serve256", "irregular1m", "core1m"],
+    ap.add_argument("--ranks", type=int, default=2, help="decomp1m: virtual ranks on one GPU (without torchrun)")
+    ap.add_argument("--workload", default="plummer1m",
+                    choices=["plummer1m", "king2m", "ensemble64", "serve256", "irregular1m", "core1m", "decomp1m"],
                     help="plummer1m: the throughput benchmark; king2m: theta sweep of the "
                          "mixed and FP64 forms against the direct sum (one line per theta); "
                          "ensemble64: 64 clusters in one graph-captured batched step, autotuned, "
                          "against one-cluster-at-a-time launches; serve256: Poisson request stream over "
                          "256 resident clusters with continuous batching (p50/p99 latency); "
                          "irregular1m: irregular force and jerk over the neighbour rows of plummer1m; "
-                         "core1m: 6 nearest neighbours of sqrt(5000 N) sampled particles and core quantities")
+                         "core1m: 6 nearest neighbours of sqrt(5000 N) sampled particles and core quantities; "
+                         "decomp1m: plummer1m decomposed over ranks (locally essential trees)")
     ap.add_argument("--requests", type=int, default=10000, help="serve256: requests in the timed stream")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve256: mean arrival rate (requests/s)")
     ap.add_argument("--no-tune", action="store_true", help="ensemble64: use --group-size/--tile/--leaf-cap")
@@ -1097,6 +1100,121 @@ def core_run(args):
     }
 
 
+def decomp_run(args):
+    """The benchmark workload (Plummer 10^6, theta 0.4, ~100 neighbours) decomposed over
+    ranks: under torchrun one rank per GPU (NCCL); otherwise --ranks virtual ranks on one
+    GPU, run one after another (what one GPU of a P-GPU run does, without the
+    transfers).  Per phase the time of the slowest rank: splitters and partition, range
+    build, locally essential trees (export), join, far force, neighbour lists; with the
+    bytes each rank receives."""
+    import numpy as np
+    import torch
+
+    import paper_2110_11658_b300 as p3t
+    from paper_2110_11658_b300 import decomp
+
+    rank, local, world = dist_init()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    c, w = workload(args.n, 20211022)
+    prm = p3t.Params(theta=w["theta"], r_in=w["r_in"], r_out=w["r_out"], r_list=w["r_list"], leaf_cap=args.leaf_cap,
+                     group_size=args.group_size, tile=args.tile, precision=p3t.P3T_FP32_MIXED)
+    if world > 1:
+        import torch.distributed as dist
+        comm = decomp.TorchComm(dist, device=dev)
+        mine = [rank]
+    else:
+        comm = decomp.LocalComm(args.ranks)
+        mine = list(range(args.ranks))
+    P = comm.size
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+
+    def fresh():
+        parts = []
+        for r in mine:
+            sel = np.arange(r, c.n, P)  # an arbitrary first distribution: every P-th particle
+            ctx = p3t.Context(prm)
+            parts.append(decomp.RankPart(ctx, t(c.x[sel]), t(c.y[sel]), t(c.z[sel]), t(c.m[sel]),
+                                         gid=t(sel.astype(np.int64))))
+        return parts
+
+    def one_step():
+        parts = fresh()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        decomp.decompose(comm, parts, prm)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        far, nbr = [], []
+        for p in parts:
+            n = p.x.numel()
+            a = [torch.empty(n, dtype=torch.float32, device=dev) for _ in range(3)]
+            offs = torch.empty(n + 1, dtype=torch.int64, device=dev)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            p.ctx.far_force(*a)
+            e1.record()
+            try:  # the list size first (a rank holding the dense core has long rows)
+                p.ctx.neighbours(offs, torch.empty(1, dtype=torch.int32, device=dev))
+                total = 0
+            except p3t.P3TError as err:
+                if err.code != p3t.P3T_ERR_CAPACITY:
+                    raise
+                total = err.total
+            idx = torch.empty(max(1, total), dtype=torch.int32, device=dev)
+            p.ctx.neighbours(offs, idx)
+            e2.record()
+            e2.synchronize()
+            far.append(e0.elapsed_time(e1))
+            nbr.append(e1.elapsed_time(e2))
+            p.ctx.check()
+        info = [p.info | {"n": p.x.numel()} for p in parts]
+        for p in parts:
+            p.ctx.close()
+        return (t1 - t0) * 1e3, far, nbr, info
+
+    for _ in range(max(1, args.warmup)):
+        one_step()
+    rows = [one_step() for _ in range(max(1, args.steps))]
+    dec_ms = statistics.median(r[0] for r in rows)
+    far = [statistics.median(r[1][i] for r in rows) for i in range(len(mine))]
+    nbr = [statistics.median(r[2][i] for r in rows) for i in range(len(mine))]
+    info = rows[-1][3]
+    far_max = dist_max(max(far), world, dev)
+    nbr_max = dist_max(max(nbr), world, dev)
+    # the same walk on one context holding the whole cluster
+    ctx = p3t.Context(prm)
+    d = [t(getattr(c, k)) for k in "xyzm"]
+    ctx.build_tree(*d)
+    a = [torch.empty(c.n, dtype=torch.float32, device=dev) for _ in range(3)]
+    ts = []
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.far_force(*a)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ctx.close()
+    single_far = statistics.median(ts[1:])
+    if rank != 0:
+        return None
+    per_rank = [{"n": i["n"], "let_nodes_in": i["let_nodes_in"], "let_parts_in": i["let_parts_in"],
+                 "let_bytes_in": i["let_nodes_in"] * p3t.P3T_LET_NODE_BYTES + i["let_parts_in"] * p3t.P3T_LET_PART_BYTES,
+                 "far_ms": f, "nbr_ms": b} for i, f, b in zip(info, far, nbr)]
+    return {
+        "metric": "decomposed far-force step: far force per rank (ms) and locally essential tree sizes",
+        "value": c.n / (far_max * 1e-3), "unit": "particles/s (far force, slowest rank)", "n_gpus": world,
+        "ranks": P, "steps": len(rows), "warmup": args.warmup, "ms_per_step": far_max, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "plummer_kroupa_n%d_theta%.1f_nbr100_ranks%d" % (c.n, THETA, P), "n": c.n,
+                   "ranks": P, "ranks_on_gpus": "one per GPU" if world > 1 else "all on one GPU, in turn"},
+        "decompose_ms": dec_ms, "far_ms_slowest": far_max, "nbr_ms_slowest": nbr_max,
+        "single_context_far_ms": single_far, "bounds": info[0]["bounds"], "top_cells": info[0]["top_cells"],
+        "per_rank": per_rank,
+    }
+
+
 def _json_default(o):
     """numpy scalars in result dictionaries."""
     if hasattr(o, "item"):
@@ -1106,6 +1224,11 @@ def _json_default(o):
 
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload == "decomp1m":
+        line = decomp_run(args)
+        if line is not None:
+            print(json.dumps(line, default=_json_default))
+        return
     if args.workload == "core1m":
         print(json.dumps(core_run(args), default=_json_default))
         return

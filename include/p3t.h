@@ -482,9 +482,15 @@ int p3t_morton_order_noalloc(int64_t n, const double *x, const double *y, const 
  *   particles' global indices, which order equal keys and fill neighbour rows.
  *   Errors as p3t_build_tree; P3T_ERR_INVALID_INPUT when a particle lies outside
  *   global_box.
+ * p3t_subtree_boxes: after p3t_build_tree_range, the exact boxes (host,
+ *   min xyz, max xyz, 6 doubles each, at most cap) of this rank's subtree roots,
+ *   the nodes below the top cells; every walk group of the rank lies in one of
+ *   them.  *n_boxes = their number (P3T_ERR_CAPACITY when above cap).
  * p3t_let_export: after p3t_build_tree_range, the locally essential tree of this
- *   rank's subtrees for a receiver with domain box box (host double[6]) and radius
- *   r_halo (max(r_out, r_list)): *n_roots subtree roots first, then the opened
+ *   rank's subtrees for a receiver whose subtree boxes are boxes (host, n_boxes x
+ *   6 doubles, at most 4096) and radius r_halo (max(r_out, r_list)): a node is
+ *   shipped opened iff rule 8 opens it for one of the boxes (so for any group of
+ *   the receiver that opens it); *n_roots subtree roots first, then the opened
  *   nodes' children level by level, as *n_nodes records of P3T_LET_NODE_BYTES, and
  *   the *n_parts particles of opened leaves (P3T_LET_PART_BYTES each).  With
  *   cap_nodes = 0 only the sizes are returned (P3T_ERR_CAPACITY when they exceed
@@ -509,7 +515,8 @@ int p3t_partition(p3t_ctx *c, int64_t n, const double *x, const double *y, const
 int p3t_build_tree_range(p3t_ctx *c, int64_t n, const double *x, const double *y, const double *z,
                          const double *m, const int64_t *gid, const double *global_box, int32_t n_top,
                          const uint64_t *top_key, const int32_t *top_level);
-int p3t_let_export(p3t_ctx *c, const double *box, double r_halo, int64_t cap_nodes, void *nodes,
+int p3t_subtree_boxes(p3t_ctx *c, int32_t cap, double *boxes, int32_t *n_boxes);
+int p3t_let_export(p3t_ctx *c, int32_t n_boxes, const double *boxes, double r_halo, int64_t cap_nodes, void *nodes,
                    int64_t cap_parts, void *parts, int64_t *n_nodes, int64_t *n_parts, int32_t *n_roots);
 int p3t_tree_join(p3t_ctx *c, int32_t n_let, const void *const *let_nodes, const int64_t *let_n_nodes,
                   const int32_t *let_n_roots, const void *const *let_parts, const int64_t *let_n_parts);

@@ -44,7 +44,7 @@ EXPORTED = [
     "p3t_sample_knn6", "p3t_sample_knn6_brute", "p3t_core_quantities", "p3t_row_mode",
     "p3t_set_spin_limit", "p3t_debug_stalled_scan",
     "p3t_local_bbox", "p3t_key_range_counts", "p3t_partition", "p3t_build_tree_range", "p3t_let_export",
-    "p3t_tree_join",
+    "p3t_tree_join", "p3t_subtree_boxes",
 ]
 P3T_LET_NODE_BYTES = 288
 P3T_LET_PART_BYTES = 96
@@ -128,7 +128,8 @@ _sig = {
                       C.c_int32, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_i64)],
     "p3t_build_tree_range": [_vp, _i64, _vp, _vp, _vp, _vp, _vp, C.POINTER(C.c_double), C.c_int32,
                              C.POINTER(C.c_uint64), C.POINTER(C.c_int32)],
-    "p3t_let_export": [_vp, C.POINTER(C.c_double), C.c_double, _i64, _vp, _i64, _vp, C.POINTER(_i64),
+    "p3t_subtree_boxes": [_vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)],
+    "p3t_let_export": [_vp, C.c_int32, C.POINTER(C.c_double), C.c_double, _i64, _vp, _i64, _vp, C.POINTER(_i64),
                        C.POINTER(_i64), C.POINTER(C.c_int32)],
     "p3t_tree_join": [_vp, C.c_int32, C.POINTER(_vp), C.POINTER(_i64), C.POINTER(C.c_int32), C.POINTER(_vp),
                       C.POINTER(_i64)],
@@ -312,20 +313,33 @@ class Context:
         _check(_lib.p3t_build_tree_range(self._h, n, _ptr(x, t.float64, n, "x"), _ptr(y, t.float64, n, "y"),
                                          _ptr(z, t.float64, n, "z"), _ptr(m, t.float64, n, "m"),
                                          _ptr(gid, t.int64, n, "gid"), gb, nt, tk, tl), "p3t_build_tree_range")
+        self.n = n
 
-    def let_export(self, box, r_halo):
-        """The locally essential tree of this rank for a receiver with domain box `box`
+    def subtree_boxes(self):
+        """Boxes of this rank's subtree roots (p3t_subtree_boxes): a list of 6-tuples."""
+        n = C.c_int32(0)
+        code = _lib.p3t_subtree_boxes(self._h, 0, None, C.byref(n))
+        if code not in (P3T_OK, P3T_ERR_CAPACITY):
+            _check(code, "p3t_subtree_boxes")
+        buf = (C.c_double * max(6, 6 * n.value))()
+        _check(_lib.p3t_subtree_boxes(self._h, n.value, buf, C.byref(n)), "p3t_subtree_boxes")
+        return [tuple(buf[6 * i:6 * i + 6]) for i in range(n.value)]
+
+    def let_export(self, boxes, r_halo):
+        """The locally essential tree of this rank for a receiver with subtree boxes `boxes`
         (p3t_let_export): (node bytes, particle bytes, n_nodes, n_roots, n_parts)."""
         t = self._torch
-        cb = (C.c_double * 6)(*box)
+        nb = len(boxes)
+        cb = (C.c_double * (6 * nb))(*[v for b in boxes for v in b])
         nn, npt, nr = C.c_int64(0), C.c_int64(0), C.c_int32(0)
-        code = _lib.p3t_let_export(self._h, cb, float(r_halo), 0, None, 0, None, C.byref(nn), C.byref(npt), C.byref(nr))
+        code = _lib.p3t_let_export(self._h, nb, cb, float(r_halo), 0, None, 0, None, C.byref(nn), C.byref(npt),
+                                   C.byref(nr))
         if code not in (P3T_OK, P3T_ERR_CAPACITY):
             _check(code, "p3t_let_export")
         nodes = t.empty(max(1, nn.value) * P3T_LET_NODE_BYTES, dtype=t.uint8, device="cuda")
         parts = t.empty(max(1, npt.value) * P3T_LET_PART_BYTES, dtype=t.uint8, device="cuda")
         n2, p2 = C.c_int64(0), C.c_int64(0)
-        _check(_lib.p3t_let_export(self._h, cb, float(r_halo), max(1, nn.value), _ptr(nodes), max(1, npt.value),
+        _check(_lib.p3t_let_export(self._h, nb, cb, float(r_halo), max(1, nn.value), _ptr(nodes), max(1, npt.value),
                                    _ptr(parts), C.byref(n2), C.byref(p2), C.byref(nr)), "p3t_let_export")
         return nodes, parts, n2.value, nr.value, p2.value
 

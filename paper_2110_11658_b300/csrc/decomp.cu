@@ -13,8 +13,9 @@
 //   p3t_partition         the particles packed by destination rank
 //   p3t_build_tree_range  (ctx.cu) the rank's tree: top cells split whatever their
 //                         count, sorted by (key, global index)
+//   p3t_subtree_boxes     the boxes of the rank's subtree roots (every group lies in one)
 //   p3t_let_export        the locally essential tree for another rank: the rank's
-//                         subtrees as the receiver's domain box sees them (rule 8 with
+//                         subtrees as the receiver's subtree boxes see them (rule 8 with
 //                         the receiver's radius), nodes and the particles of opened leaves
 //   p3t_tree_join         the rank's tree joined with the top tree and the remote
 //                         subtrees: its groups then walk the global tree, so their
@@ -32,6 +33,7 @@ namespace p3t {
 
 constexpr int kDecThreads = 256;
 constexpr int kMaxRanges = 1024;  // key intervals of one p3t_key_range_counts call
+constexpr int kMaxDomainBoxes = 4096;  // a rank's subtree roots (the receiver's boxes of a LET)
 
 // Morton key of a point in the cube of K (rules 2-3, as keys_kernel computes it)
 __device__ __forceinline__ unsigned long long key_of(double x, double y, double z, const Cluster &K)
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kDecThreads)
 // frontier, opened leaves their particles.  Pass 0 counts them (nch, npt); pass 1
 // forms the next frontier and, when `write`, the LET records and particles.
 __global__ void __launch_bounds__(kDecThreads)
-    let_level_kernel(Tree T, int nf, const int32_t *__restrict__ front, double4_32a blo, double4_32a bhi,
+    let_level_kernel(Tree T, int nf, const int32_t *__restrict__ front, int nbox, const double4_32a *__restrict__ boxes,
                      double r2, int pass, int32_t *__restrict__ nch, int32_t *__restrict__ npt,
                      const int64_t *__restrict__ ch_off, const int64_t *__restrict__ pt_off, long long next_base,
                      long long part_base, int32_t *__restrict__ next, bool write, LetNode *out_nodes,
@@ -237,7 +239,12 @@ __global__ void __launch_bounds__(kDecThreads)
     const int u = front[f];
     const int4 tp = T.topo[u];
     const double4_32a cm = T.comM[u], cl = T.lo[u], ch = T.hi[u];
-    const bool open = dist2_point_box(cm.x, cm.y, cm.z, blo, bhi) < cl.w || dist2_box_box(blo, bhi, cl, ch) < r2;
+    // opened iff one of the receiver's boxes opens it (each of its groups lies in one)
+    bool open = false;
+    for (int i = 0; i < nbox && !open; i++) {
+        const double4_32a blo = boxes[2 * i], bhi = boxes[2 * i + 1];
+        open = dist2_point_box(cm.x, cm.y, cm.z, blo, bhi) < cl.w || dist2_box_box(blo, bhi, cl, ch) < r2;
+    }
     const bool leaf = tp.z < 0;
     if (pass == 0) {
         nch[f] = open && !leaf ? tp.w : 0;
@@ -290,6 +297,16 @@ __global__ void node_keys_kernel(Tree T, int n, const int32_t *__restrict__ ids,
     const int k = ids[i];
     level[i] = T.level[k];
     key[i] = T.keys[T.topo[k].x];
+}
+
+// the exact boxes (min xyz, max xyz) of the listed nodes
+__global__ void node_boxes_kernel(Tree T, int n, const int32_t *__restrict__ ids, double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double4_32a l = T.lo[ids[i]], h = T.hi[ids[i]];
+    double *o = out + 6 * (size_t)i;
+    o[0] = l.x, o[1] = l.y, o[2] = l.z, o[3] = h.x, o[4] = h.y, o[5] = h.z;
 }
 
 __global__ void __launch_bounds__(kDecThreads) top_flag_kernel(Tree T, int nn, unsigned char *flag)
@@ -584,11 +601,12 @@ static int flagged_list(p3t_ctx *c, int nn, const unsigned char *flag, int32_t *
     return P3T_OK;
 }
 
-int p3t_let_export(p3t_ctx *c, const double *box, double r_halo, int64_t cap_nodes, void *nodes,
+int p3t_let_export(p3t_ctx *c, int32_t n_boxes, const double *boxes, double r_halo, int64_t cap_nodes, void *nodes,
                    int64_t cap_parts, void *parts, int64_t *n_nodes, int64_t *n_parts, int32_t *n_roots)
 {
-    if (!c || !box || !n_nodes || !n_parts || !n_roots || !(r_halo >= 0.0) || !std::isfinite(r_halo) ||
-        cap_nodes < 0 || cap_parts < 0 || (cap_nodes > 0 && !nodes) || (cap_parts > 0 && !parts))
+    if (!c || n_boxes < 1 || n_boxes > kMaxDomainBoxes || !boxes || !n_nodes || !n_parts || !n_roots ||
+        !(r_halo >= 0.0) || !std::isfinite(r_halo) || cap_nodes < 0 || cap_parts < 0 || (cap_nodes > 0 && !nodes) ||
+        (cap_parts > 0 && !parts))
         return P3T_ERR_INVALID_ARG;
     if (!c->built || !c->range_built || c->joined || c->n_top < 1) return P3T_ERR_ORDER;
     int e = p3t_status(c);
@@ -600,10 +618,24 @@ int p3t_let_export(p3t_ctx *c, const double *box, double r_halo, int64_t cap_nod
     const size_t off_p = al((size_t)nn + 16), off_a = off_p + al(4 * (size_t)nn),
                  off_b = off_a + al(4 * (size_t)nn), off_c = off_b + al(4 * (size_t)nn),
                  off_d = off_c + al(4 * (size_t)nn), off_e = off_d + al(4 * (size_t)nn),
-                 off_g = off_e + al(8 * (size_t)nn), off_t = off_g + al(8 * (size_t)nn);
-    e = dec_reserve(c, off_t + 256);
+                 off_g = off_e + al(8 * (size_t)nn), off_t = off_g + al(8 * (size_t)nn),
+                 off_x = off_t + 256;
+    e = dec_reserve(c, off_x + al(64 * (size_t)n_boxes));
     if (e) return e;
     char *b = (char *)c->dec_buf;
+    double4_32a *dbox = (double4_32a *)(b + off_x);
+    {
+        std::vector<double4_32a> hb(2 * (size_t)n_boxes);
+        for (int i = 0; i < n_boxes; i++) {
+            const double *q = boxes + 6 * (size_t)i;
+            hb[2 * i] = make_double4_32a(q[0], q[1], q[2], 0.0);
+            hb[2 * i + 1] = make_double4_32a(q[3], q[4], q[5], 0.0);
+        }
+        if (cudaMemcpyAsync(dbox, hb.data(), 64 * (size_t)n_boxes, cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return P3T_ERR_CUDA;
+    }
     unsigned char *flag = (unsigned char *)b;
     int32_t *pos = (int32_t *)(b + off_p);
     int32_t *front = (int32_t *)(b + off_a), *next = (int32_t *)(b + off_b);
@@ -618,15 +650,13 @@ int p3t_let_export(p3t_ctx *c, const double *box, double r_halo, int64_t cap_nod
     e = flagged_list(c, nn, flag, pos, front, tot, &nf);
     if (e) return e;
     *n_roots = nf;
-    const double4_32a blo = make_double4_32a(box[0], box[1], box[2], 0.0);
-    const double4_32a bhi = make_double4_32a(box[3], box[4], box[5], 0.0);
     const double r2 = r_halo * r_halo;
     const bool q64 = c->built_precision == P3T_FP64;
     long long node_base = 0, part_base = 0;
     bool fits = cap_nodes > 0;
     while (nf > 0) {
         const int gf = (nf + kDecThreads - 1) / kDecThreads;
-        let_level_kernel<<<gf, kDecThreads, 0, s>>>(T, nf, front, blo, bhi, r2, 0, nch, npt, nullptr, nullptr, 0, 0,
+        let_level_kernel<<<gf, kDecThreads, 0, s>>>(T, nf, front, n_boxes, dbox, r2, 0, nch, npt, nullptr, nullptr, 0, 0,
                                                     nullptr, false, nullptr, 0, nullptr, q64);
         e = scan_excl_i32_to_i64(nch, cho, nf, tot64, c->scan_status, &c->meta->tickets[28], c->meta, s);
         if (e) return e;
@@ -638,7 +668,7 @@ int p3t_let_export(p3t_ctx *c, const double *box, double r_halo, int64_t cap_nod
             return P3T_ERR_CUDA;
         if (t2[0] > nn) return P3T_ERR_INTERNAL;  // a frontier holds distinct nodes
         fits = fits && node_base + nf <= cap_nodes && part_base + t2[1] <= cap_parts;
-        let_level_kernel<<<gf, kDecThreads, 0, s>>>(T, nf, front, blo, bhi, r2, 1, nullptr, nullptr, cho, pto,
+        let_level_kernel<<<gf, kDecThreads, 0, s>>>(T, nf, front, n_boxes, dbox, r2, 1, nullptr, nullptr, cho, pto,
                                                     node_base + nf, part_base, next, fits, (LetNode *)nodes,
                                                     node_base, (LetPart *)parts, q64);
         node_base += nf;
@@ -651,6 +681,38 @@ int p3t_let_export(p3t_ctx *c, const double *box, double r_halo, int64_t cap_nod
     e = sync_status(c);
     if (e) return e;
     return fits ? P3T_OK : P3T_ERR_CAPACITY;
+}
+
+int p3t_subtree_boxes(p3t_ctx *c, int32_t cap, double *boxes, int32_t *n_boxes)
+{
+    if (!c || !n_boxes || cap < 0 || (cap > 0 && !boxes)) return P3T_ERR_INVALID_ARG;
+    if (!c->built || !c->range_built || c->joined || c->n_top < 1) return P3T_ERR_ORDER;
+    int e = p3t_status(c);
+    if (e) return e;
+    int nn = 0;
+    if (cudaMemcpy(&nn, &c->meta->n_nodes, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return P3T_ERR_CUDA;
+    const size_t off_p = al((size_t)nn + 16), off_r = off_p + al(4 * (size_t)nn), off_t = off_r + al(4 * (size_t)nn),
+                 off_o = off_t + 256;
+    e = dec_reserve(c, off_o + al(64 * (size_t)kMaxDomainBoxes));
+    if (e) return e;
+    char *b = (char *)c->dec_buf;
+    unsigned char *flag = (unsigned char *)b;
+    int32_t *pos = (int32_t *)(b + off_p), *ids = (int32_t *)(b + off_r), *tot = (int32_t *)(b + off_t);
+    double *out = (double *)(b + off_o);
+    root_flag_kernel<<<(nn + kDecThreads - 1) / kDecThreads, kDecThreads, 0, c->stream>>>(c->tree, nn, flag);
+    int cnt = 0;
+    e = flagged_list(c, nn, flag, pos, ids, tot, &cnt);
+    if (e) return e;
+    *n_boxes = cnt;
+    if (cnt > cap) return P3T_ERR_CAPACITY;
+    if (cnt > kMaxDomainBoxes) return P3T_ERR_INTERNAL;
+    if (cnt > 0) {
+        node_boxes_kernel<<<(cnt + 255) / 256, 256, 0, c->stream>>>(c->tree, cnt, ids, out);
+        if (cudaMemcpyAsync(boxes, out, 48 * (size_t)cnt, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            return P3T_ERR_CUDA;
+    }
+    return sync_status(c);
 }
 
 int p3t_tree_join(p3t_ctx *c, int32_t n_let, const void *const *let_nodes, const int64_t *let_n_nodes,

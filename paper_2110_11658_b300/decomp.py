@@ -13,8 +13,9 @@ tree is complete subtrees owned by single ranks.  Each rank then
 
 1. builds its part of the tree (top cells forced open, order (key, global index)),
 2. sends every other rank the locally essential tree of its subtrees as that
-   rank's domain box sees them (the opening rule of Sec. 2.4 with r_out, or the
-   list radius when larger, so the neighbour halo is included),
+   rank's subtree boxes see them (the opening rule of Sec. 2.4 with r_out, or the
+   list radius when larger, so the neighbour halo is included; every group of the
+   receiver lies in one of those boxes, so the tree holds whatever any of them opens),
 3. joins what it receives: the top cells' moments follow from the joined
    children, and its groups walk the global tree.
 
@@ -263,8 +264,8 @@ def decompose(comm, parts, params):
     tops = top_cells(bounds, _global_counts(comm, parts, gbox))
     for p in parts:
         p.ctx.build_tree_range(p.x, p.y, p.z, p.m, p.gid, gbox, [k for k, _ in tops], [l for _, l in tops])
-    # 4. domain boxes, locally essential trees, joins
-    dom = comm.allgather([p.ctx.local_bbox(p.x, p.y, p.z) for p in parts])[0]
+    # 4. every rank's subtree boxes, locally essential trees, joins
+    dom = comm.allgather([p.ctx.subtree_boxes() for p in parts])[0]
     r_halo = max(params.r_out, params.r_list)
     send_n, send_p, meta = [], [], []
     for i, p in enumerate(parts):
