@@ -509,10 +509,11 @@ def bench_config(n, w, args, world):
 # kernels launched by one step: build = metadata, cluster table, cluster parameters,
 # bbox, cube, keys (6) + radix sort 8 x (histogram, scan, scatter) + gather + topology
 # root, 21 levels, finish + group scan, first, finish, frames, walk order (bins, scan,
-# scatter) + moments leaves and 21 levels; far force 1 (it also counts the neighbours);
+# scatter) + moments leaves and 21 levels; far force 3 (the rows' layout from the last
+# counts and its scan, then the walk, which also counts the neighbours and writes the rows);
 # neighbours = offsets scan, fill, row binning by length (count, list) and eight
 # row-sort size classes; kick 1; drift 1
-KERNELS_PER_STEP = (6 + 8 * 3 + 1 + (1 + 21 + 1) + 4 + 3 + (1 + 21)) + 1 + (2 + 2 + 8) + 1 + 1
+KERNELS_PER_STEP = (6 + 8 * 3 + 1 + (1 + 21 + 1) + 4 + 3 + (1 + 21)) + 3 + (2 + 2 + 8) + 1 + 1
 
 
 def run_reference(args, rank, world):

@@ -134,14 +134,16 @@ int p3t_far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t
  * idx: device int32[capacity].  *total (host) receives the number of entries.
  * Synchronises the stream once to read the total.  If total > capacity the
  * call returns P3T_ERR_CAPACITY with *total and offsets set and idx untouched.
- * Row mode (mixed precision, group_size <= 32): this call also sizes a
- * context-owned scratch of row_cap int32 entries per particle (row_cap = 8 x
- * the mean row length, in multiples of 32, in [64, 4096]); for the following
- * trees the pass that counts the neighbours (the far-force walk, or the lists'
- * own count pass when they come first) writes each neighbour into it, and the
- * lists only sort those rows (a row longer than row_cap is rebuilt by a second
- * walk of its group).  The lists are the same either way; a failed allocation
- * of the scratch leaves row mode off. */
+ * Row mode (mixed precision, one target per lane: group_size <= 32, or <=
+ * threads_per_group): this call also sizes a context-owned scratch of int32
+ * entries, about 1.3 times the lists' entries at 100 neighbours a particle;
+ * for the following trees of the same particles the pass that counts the
+ * neighbours (the far-force walk, or the lists' own count pass when they come
+ * first) writes each neighbour into its target's row there, each row having
+ * room for c + c/8 + 8 entries when its particle had c neighbours at the last
+ * count, and the lists only sort those rows (a row that outgrew its room is
+ * rebuilt by a second walk of its group).  The lists are the same either way; a
+ * failed allocation of the scratch leaves row mode off. */
 int p3t_neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *total);
 
 /* As p3t_neighbours without the synchronisation: *total_dev is a device
@@ -279,7 +281,7 @@ int p3t_core_quantities(p3t_ctx *c, int64_t n, const double *x, const double *y,
 int p3t_filter_fallbacks(p3t_ctx *c, int64_t *count);
 
 /* Row mode of the neighbour lists (see p3t_neighbours), host values, no
- * synchronisation: *row_cap = entries per row the next far-force walks write
+ * synchronisation: *row_cap = the row scratch's entries per particle, on average
  * (0: row mode off); *rows_valid = 1 if the last walk on the current tree
  * wrote its rows, so that the next lists only sort them.  Either pointer may
  * be NULL. */

@@ -68,6 +68,7 @@ static size_t scratch_plan(p3t_ctx *c, long long N, int L, char *base)
     put(&c->nbr_count, 4 * (size_t)N);
     put(&c->row_list, 4 * (size_t)N);
     put(&c->rid_buf, 4 * (size_t)N);
+    put(&c->row_off, 8 * ((size_t)N + 1));
     put(&c->top_buf, 12 * (size_t)kMaxTopCells);
     put(&c->grp_cells, 8 * (size_t)N);
     put(&c->grp_parts, 8 * (size_t)N);
@@ -117,6 +118,7 @@ int ensure_capacity(p3t_ctx *c, long long n)
     c->gen++;
     c->cap_n = n;
     c->cap_nodes = need_nodes;
+    c->counts_n = 0;  // the neighbour counts went with the old scratch
     c->cap_leaf = L;
     c->tree.meta = c->meta;
     c->tree.cap_nodes = (int)need_nodes;

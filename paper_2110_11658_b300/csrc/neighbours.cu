@@ -36,9 +36,11 @@ struct NbrArgs {
     long long capacity;
     int skip_counted;      // count pass: skip clusters whose neighbours the walk counted
     unsigned int *ticket;
-    int row_cap;           // fill pass in row mode: only groups with a row longer than this
-    int32_t *rows;         // count pass in row mode: rows of rows_cap entries per target
-    int rows_cap;          // (key order, original indices; see the far-force walk)
+    int row_cap;           // fill pass in row mode (> 0): only groups with a row longer than its span
+    int32_t *rows;         // count pass in row mode: the targets' rows (key order, laid out by
+                           // row_off; ids as the far-force walk writes them)
+    const int64_t *row_off;
+    long long row_entries;
 };
 
 struct NbrSmem {
@@ -78,12 +80,17 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         const Cluster &K = T.cl[cid];
         // counting: clusters the far-force walk already counted are skipped
         if (!FILL && P.skip_counted && K.counted) continue;
-        if (FILL && P.row_cap > 0) {  // row mode: every row of at most row_cap is written
+        if (FILL && P.row_cap > 0) {  // row mode: every row within its span is written
             bool longer = false;
 #pragma unroll
             for (int t = 0; t < TPL; t++) {
                 const int s = gr.x + lane + 32 * t;
-                longer |= s < gr.x + gr.y && P.count[T.perm[s]] > P.row_cap;
+                if (s < gr.x + gr.y) {
+                    long long lo;
+                    int cap;
+                    row_span(P.row_off, P.row_entries, s, lo, cap);
+                    longer |= P.count[T.perm[s]] > cap;
+                }
             }
             if (!__any_sync(0xffffffffu, longer)) continue;
         }
@@ -106,7 +113,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         // target's scratch row and its entries (an empty slot writes nothing)
         unsigned hit[TPL];
         int32_t *rrow[TPL];
-        int rwc[TPL];
+        int rwc[TPL], rcap[TPL];
         float A = 0.f;
 #pragma unroll
         for (int t = 0; t < TPL; t++) {
@@ -115,7 +122,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
             wp[t] = P.idx;
             if (ROWS) {
                 hit[t] = 0u;
-                rrow[t] = P.rows + (size_t)(s < gr.x + gr.y ? s : 0) * P.rows_cap;
+                long long lo = 0;
+                rcap[t] = 0;
+                if (s < gr.x + gr.y) row_span(P.row_off, P.row_entries, s, lo, rcap[t]);
+                rrow[t] = P.rows + lo;
                 rwc[t] = s < gr.x + gr.y ? 0 : (1 << 30);
             }
             if (s < gr.x + gr.y) {
@@ -313,7 +323,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                         while (h) {
                             const int b = __ffs(h) - 1;
                             h &= h - 1u;
-                            if (rwc[t] < P.rows_cap) rrow[t][rwc[t]] = po[8 * (b >> 1) + 6 + (b & 1)];
+                            if (rwc[t] < rcap[t]) rrow[t][rwc[t]] = po[8 * (b >> 1) + 6 + (b & 1)];
                             rwc[t]++;
                         }
                     }
@@ -424,7 +434,8 @@ __global__ void row_class_fill_kernel(int n, const int64_t *__restrict__ offs, l
 struct RowSrc {
     const int32_t *rows;  // null: every row is in idx
     const int32_t *inv;   // original -> key order
-    int cap;
+    const int64_t *row_off;
+    long long entries;
 };
 
 // Where one row's entries are read from: its scratch row, else its place in idx.
@@ -450,7 +461,13 @@ __device__ __forceinline__ void for_class_rows(const Meta *meta, const int32_t *
         const long long o = offs[i];
         const int len = (int)(offs[i + 1] - o);
         RowLoad ld;
-        ld.sr = src.rows && len <= src.cap ? src.rows + (size_t)src.inv[i] * src.cap : nullptr;
+        ld.sr = nullptr;
+        if (src.rows) {
+            long long lo;
+            int cap;
+            row_span(src.row_off, src.entries, src.inv[i], lo, cap);
+            if (len <= cap) ld.sr = src.rows + lo;
+        }
         ld.row = idx + o;
         f(idx + o, len, ld);
         __syncwarp();
@@ -763,21 +780,26 @@ static int dispatch_nbr(p3t_ctx *c, const NbrArgs &a)
 }
 
 // Row mode: the pass that counts the neighbours (the far-force walk, or the
-// count pass when the lists come first) also writes each neighbour into a
-// scratch row of row_cap entries per particle, so that the lists need no fill
-// walk.  The synchronous lists size the scratch for the following trees: row_cap
-// = 8 x the mean row length in multiples of 32, in [64, 4096]; a row longer than
-// that is filled by the fill pass for its group.  A failed allocation leaves row
-// mode off.  Reallocating drops the rows of the current tree (rows_valid), which
-// the fill pass then rebuilds.
+// count pass when the lists come first) also writes each neighbour into the
+// target's row of a scratch, so that the lists need no fill walk.  Each tree's
+// rows are laid out from the last counts of the same particles (row_caps_kernel:
+// c + c/8 + 8 entries for a particle that had c neighbours), and the synchronous
+// lists size the scratch once: the entries of such a layout of their counts plus
+// a sixteenth (about 1.3 times the lists' entries at 100 neighbours a particle),
+// so a row overflows only when its particle gained more than an eighth of its
+// neighbours and 8 since the counts were taken (and the rows at the end when the
+// layout as a whole grew by more than a sixteenth).  Such a row is filled by
+// the fill pass for its group.  A failed allocation leaves row mode off.
+// Reallocating drops the rows of the current tree (rows_valid), which the fill
+// pass then rebuilds.
 static void size_row_scratch(p3t_ctx *c, long long total)
 {
     // (rows need one target per lane in the walk: G <= threads per group)
     if (c->built_precision != P3T_FP32_MIXED || c->prm.group_size > c->prm.threads_per_group || c->n <= 0)
         return;
-    const long long mean = (total + c->n - 1) / c->n;
-    const long long cap = std::max(64LL, std::min(4096LL, (8 * mean + 31) / 32 * 32));
-    const size_t need = (size_t)c->cap_n * (size_t)cap;
+    const long long layout = total + total / 8 + 8LL * c->n;
+    const size_t need = (size_t)((layout + layout / 16 + 4095) / 4096 * 4096);
+    const long long cap = std::max(1LL, (long long)(need / (size_t)c->n));
     if (need > c->row_scratch_entries) {
         cudaStreamSynchronize(c->stream);
         if (c->row_scratch) cudaFree(c->row_scratch);
@@ -794,7 +816,33 @@ static void size_row_scratch(p3t_ctx *c, long long total)
         c->row_scratch = (int32_t *)p;
         c->row_scratch_entries = need;
     }
-    c->row_cap = (int)cap;
+    c->row_cap = (int)std::min(cap, (long long)INT32_MAX);
+}
+
+// capacity of each target's row (key order) from the last count of its particle
+__global__ void __launch_bounds__(256)
+    row_caps_kernel(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ count,
+                    int32_t *__restrict__ cap)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int cnt = count[perm[s]];
+    cap[s] = cnt < (1 << 24) ? cnt + (cnt >> 3) + 8 : (1 << 24);
+}
+
+// Lay out the current tree's rows in the scratch (row_off) when row mode is on and
+// the counts of these particles are known; returns whether the rows can be written.
+int prepare_rows(p3t_ctx *c)
+{
+    c->rows_cap_used = 0;
+    if (c->row_cap <= 0 || !c->row_scratch || c->counts_n != c->n || c->n <= 0) return 0;
+    const int n = c->n;
+    row_caps_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->tree.perm, c->nbr_count, c->row_list);
+    if (scan_excl_i32_to_i64(c->row_list, c->row_off, n, c->row_off + n, c->scan_status, &c->meta->tickets[26],
+                             c->meta, c->stream) != P3T_OK)
+        return 0;
+    c->rows_cap_used = 1;
+    return 1;
 }
 
 int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, int64_t *total_dev,
@@ -811,27 +859,25 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
     a.ticket = &c->meta->tickets[23];
     a.row_cap = 0;
     a.rows = nullptr;
-    a.rows_cap = 0;
+    a.row_off = c->row_off;
+    a.row_entries = (long long)c->row_scratch_entries;
     int e;
     a.skip_counted = c->walk_counted;
     if (!c->counts_valid) {  // the far-force walk did not count every cluster
         // row mode in the count pass: when the walk counted nothing (the lists come
         // before the far force), or wrote the rows of what it counted
-        const int cap = c->walk_counted ? (c->rows_valid ? c->rows_cap_used : 0) : c->row_cap;
-        const bool rows = cap > 0 && c->prm.group_size <= 32 &&
-                          c->built_precision == P3T_FP32_MIXED &&
-                          c->row_scratch_entries >= (size_t)n * (size_t)cap;
+        const bool can = c->prm.group_size <= 32 && c->built_precision == P3T_FP32_MIXED;
+        const bool rows = can && (c->walk_counted ? c->rows_valid != 0 : prepare_rows(c) != 0);
         if (rows) {
             a.rows = c->row_scratch;
-            a.rows_cap = cap;
             e = launch_nbr<1, false, true>(c, a);
         } else {
             e = dispatch_nbr<false>(c, a);
         }
         if (e) return e;
         c->counts_valid = 1;
+        c->counts_n = n;
         c->rows_valid = rows;
-        c->rows_cap_used = rows ? cap : 0;
     }
     e = scan_excl_i32_to_i64(c->nbr_count, offsets, n, offsets + n, c->scan_status,
                              &c->meta->tickets[29], c->meta, s);
@@ -859,10 +905,10 @@ int neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, long long capacity, i
             return P3T_ERR_CUDA;
     }
     if (capacity == 0) return P3T_OK;
-    RowSrc src{nullptr, nullptr, 0};
-    if (c->rows_valid) {  // the walk wrote the rows: fill only groups with a longer row
-        a.row_cap = c->rows_cap_used;
-        src = RowSrc{c->row_scratch, c->tree.inv, c->rows_cap_used};
+    RowSrc src{nullptr, nullptr, nullptr, 0};
+    if (c->rows_valid) {  // the rows were written: fill only groups with a longer row
+        a.row_cap = 1;
+        src = RowSrc{c->row_scratch, c->tree.inv, c->row_off, (long long)c->row_scratch_entries};
     }
     e = dispatch_nbr<true>(c, a);
     if (e) return e;

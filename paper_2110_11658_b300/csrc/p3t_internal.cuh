@@ -136,6 +136,15 @@ struct Tree {
     const int32_t *top_level;
 };
 
+// Row mode: target s (key order) owns scratch entries [row_off[s], row_off[s + 1])
+// clipped to the scratch; a row with more neighbours comes from the fill pass.
+__device__ __forceinline__ void row_span(const int64_t *row_off, long long entries, int s, long long &lo, int &cap)
+{
+    lo = row_off[s];
+    const long long hi = row_off[s + 1] < entries ? row_off[s + 1] : entries;
+    cap = hi > lo ? (int)(hi - lo) : 0;
+}
+
 constexpr int kMaxTopCells = 256;  // top cells of a decomposed cluster (about 21 per splitter)
 
 // node k of a range build is a top cell: level l, prefix = its first key >> (63 - 3 l)
@@ -421,9 +430,11 @@ struct p3t_ctx {
     int32_t *rid_buf;                 // global row ids of a range build (key order)
     unsigned long long *top_buf;      // top cells of a range build: keys, then levels
     int32_t *row_scratch;             // row mode: neighbour rows written by the far-force walk
-    size_t row_scratch_entries;       // (row_cap entries per particle, key order)
-    int row_cap;                      // entries per row for the next walks (0: row mode off)
-    int rows_cap_used;                // entries per row of the rows in the scratch
+    size_t row_scratch_entries;       // (rows in key order, laid out by row_off)
+    int row_cap;                      // > 0: row mode on (the scratch's mean entries per particle)
+    int rows_cap_used;                // row_off lays out the rows of the current tree
+    int64_t *row_off;                 // row mode: first scratch entry of each row, key order (n + 1)
+    long long counts_n;               // nbr_count holds every particle's count for these n particles
     int64_t *grp_cells, *grp_parts;   // per group debug counts
     void *blob;                       // single allocation backing everything above
     size_t blob_bytes;
@@ -483,6 +494,7 @@ int reserve(p3t_ctx *c, long long n, int n_clusters);
 int scan_stalled(int n, const int32_t *in, int32_t *out, unsigned long long *status,
                  unsigned int *ticket, Meta *meta, cudaStream_t s);
 int check_launch(p3t_ctx *c);
+int prepare_rows(p3t_ctx *c);
 // A rank's part of a decomposed cluster (p3t_build_tree_range): the global bounding
 // box (min xyz, max xyz), the ranks' top cells and the particles' global indices.
 struct RangeSpec {

@@ -41,10 +41,12 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     // row mode: the walk also writes each neighbour it counts into the row scratch,
     // so that p3t_neighbours only sorts (one target per lane)
     const int wpg = P.threads_per_group / 32;  // warps per group
-    const bool rows = fuse_nbr && P.group_size <= 32 * wpg && c->row_cap > 0 &&
-                      c->row_scratch_entries >= (size_t)c->n * (size_t)c->row_cap;
+    // (rows laid out from the last counts of these particles, before the walk
+    // overwrites them)
+    const bool rows = fuse_nbr && P.group_size <= 32 * wpg && prepare_rows(c);
     a.rows = rows ? c->row_scratch : nullptr;
-    a.row_cap = rows ? c->row_cap : 0;
+    a.row_off = c->row_off;
+    a.row_entries = (long long)c->row_scratch_entries;
     if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
         return P3T_ERR_CUDA;
     const bool quad = P.quadrupole != 0;
@@ -71,8 +73,8 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     if (e == P3T_OK && fuse_nbr) {
         c->walk_counted = 1;
         c->rows_valid = rows;
-        c->rows_cap_used = a.row_cap;
         c->counts_valid = c->uniform_params;  // every cluster counted
+        if (c->counts_valid) c->counts_n = c->n;
     }
     return e;
 }

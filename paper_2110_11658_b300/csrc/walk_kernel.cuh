@@ -69,8 +69,9 @@ struct WalkArgs {
     long long *grp_cells, *grp_parts;
     unsigned int *ticket;
     int32_t *nbr_count;          // fused neighbour count (original order) or null
-    int32_t *rows;               // row mode: rows of row_cap entries per target (key order)
-    int row_cap;
+    int32_t *rows;               // row mode: the targets' rows (key order), laid out by row_off
+    const int64_t *row_off;
+    long long row_entries;       // entries of the row scratch
 };
 
 template <typename Real>
@@ -333,9 +334,9 @@ template <int TPL>
 struct NbrCount {
     int si[TPL];   // target positions in key order (-1: empty slot)
     int cnt[TPL];
-    // row mode: wc entries written to the target's row of row_cap entries in the
-    // row scratch, at rows + si * row_cap (original indices, the target itself left
-    // out; entries past row_cap are dropped while cnt keeps counting)
+    // row mode: wc entries written to the target's row in the row scratch, at
+    // rows + row_off[si] (ids of the sources, the target itself left out; entries
+    // past the row's capacity are dropped while cnt keeps counting)
     int wc[TPL];
     unsigned hit[TPL];  // neighbours among the 32 staged sources (bit = staging slot)
     bool beyond;   // the group's cluster lists neighbours beyond r_out (r_list > r_out)
@@ -739,13 +740,17 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
                 unsigned h = NC.hit[t];
                 NC.hit[t] = 0u;
                 NC.cnt[t] += __popc(h);
-                while (h) {
-                    const int b = __ffs(h) - 1;
-                    h &= h - 1u;
-                    if (W.pj[b] != NC.si[t]) {
-                        if (NC.wc[t] < P.row_cap)
-                            P.rows[(size_t)NC.si[t] * P.row_cap + NC.wc[t]] = W.po[b];
-                        NC.wc[t]++;
+                if (h && NC.si[t] >= 0) {  // (an empty slot writes nothing)
+                    long long lo;
+                    int cap;
+                    row_span(P.row_off, P.row_entries, NC.si[t], lo, cap);
+                    while (h) {
+                        const int b = __ffs(h) - 1;
+                        h &= h - 1u;
+                        if (W.pj[b] != NC.si[t]) {
+                            if (NC.wc[t] < cap) P.rows[lo + NC.wc[t]] = W.po[b];
+                            NC.wc[t]++;
+                        }
                     }
                 }
             }

@@ -195,33 +195,35 @@ def test_long_neighbour_rows_take_every_sort_path():
 def test_row_mode_lists_and_fallback():
     # After one synchronous list of a tree that the far-force walk counted, the
     # following walks also write each neighbour into the context's row scratch and
-    # the lists only sort those rows.  A Plummer sphere with a few neighbours per
-    # particle plus a tight clump whose rows (399) exceed the scratch rows (8 x the
-    # mean row): those rows come from the fill pass instead.  Every step's lists
-    # equal the brute force, and the forces equal those of a context that never
-    # enters row mode, bit for bit.
+    # the lists only sort those rows.  Each row's room comes from its particle's
+    # last count (c + c/8 + 8).  A Plummer sphere plus a clump of 400 that is loose
+    # (few neighbours) on the first steps and tight (399 each) on the last: those
+    # rows overflow their room and come from the fill pass instead.  Every step's
+    # lists equal the brute force, and the forces equal those of a context that
+    # never enters row mode, bit for bit.
     p = synth.plummer(20000, 43)
     rng = np.random.default_rng(43)
-    q = rng.normal(size=(3, 400)) * 0.002 + 2.0
-    x, y, z = (np.concatenate([a, b]) for a, b in zip((p.x, p.y, p.z), q))
-    n = x.size
+    q = rng.normal(size=(3, 400))
+    n = p.n + 400
     m = np.full(n, 1.0 / n)
     prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05)
-    o2, i2 = oracle.neighbours_brute(x, y, z, 0.05)
-    assert np.diff(o2).max() == 399
-    xd, yd, zd, md = to_dev(x), to_dev(y), to_dev(z), to_dev(m)
     ctx = p3t.Context(prm)
     a = [torch.empty(n, dtype=torch.float32, device=DEV) for _ in range(3)]
     offs = torch.empty(n + 1, dtype=torch.int64, device=DEV)
-    idx = torch.empty(2 * len(i2) + 64, dtype=torch.int32, device=DEV)
-    for step in range(3):
+    idx = torch.empty(400 * 400 + 8 * n, dtype=torch.int32, device=DEV)
+    for step, scale in enumerate((0.3, 0.3, 0.002, 0.002)):
+        x, y, z = (np.concatenate([a_, b_]) for a_, b_ in zip((p.x, p.y, p.z), q * scale + 2.0))
+        o2, i2 = oracle.neighbours_brute(x, y, z, 0.05)
+        if scale < 0.01:
+            assert np.diff(o2).max() == 399
+        xd, yd, zd, md = to_dev(x), to_dev(y), to_dev(z), to_dev(m)
         ctx.build_tree(xd, yd, zd, md)
         ctx.far_force(*a)
         cap, valid = ctx.row_mode()
         if step == 0:
             assert cap == 0 and valid == 0
         else:
-            assert 64 <= cap < 399 and valid == 1
+            assert cap > 0 and valid == 1
         tot = ctx.neighbours(offs, idx)
         assert tot == len(i2)
         assert np.array_equal(offs.cpu().numpy(), o2) and np.array_equal(idx[:tot].cpu().numpy(), i2)
@@ -237,9 +239,9 @@ def test_row_mode_lists_and_fallback():
 
 def test_row_mode_in_host_step():
     # p3t_step_host builds the lists before the far force, so its count pass
-    # writes the rows from the second step on; lists (with rows beyond the scratch
-    # row) equal the brute force every step, accelerations and velocities equal a
-    # first step (no row mode) of a fresh context
+    # writes the rows from the second step on; lists (a clump's rows of 399
+    # included) equal the brute force every step, accelerations and velocities
+    # equal a first step (no row mode) of a fresh context
     p = synth.plummer(20000, 47)
     rng = np.random.default_rng(47)
     q = rng.normal(size=(3, 400)) * 0.002 - 2.0
