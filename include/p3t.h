@@ -137,12 +137,12 @@ int p3t_far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t
  * Row mode (mixed precision, one target per lane: group_size <= 32, or <=
  * threads_per_group): this call also sizes a context-owned scratch of int32
  * entries, about 1.3 times the lists' entries at 100 neighbours a particle;
- * for the following trees of the same particles the pass that counts the
- * neighbours (the far-force walk, or the lists' own count pass when they come
- * first) writes each neighbour into its target's row there, each row having
- * room for c + c/8 + 8 entries when its particle had c neighbours at the last
- * count, and the lists only sort those rows (a row that outgrew its room is
- * rebuilt by a second walk of its group).  The lists are the same either way; a
+ * for the following trees the pass that counts the neighbours (the far-force
+ * walk, or the lists' own count pass when they come first) writes each neighbour
+ * into its target's row there, each row having room for c + c/8 + 8 entries when
+ * its particle had c neighbours at the last count of the same n particles (equal
+ * rows otherwise), and the lists only sort those rows (a row that outgrew its
+ * room is rebuilt by a second walk of its group).  The lists are the same either way; a
  * failed allocation of the scratch leaves row mode off. */
 int p3t_neighbours(p3t_ctx *c, int64_t *offsets, int32_t *idx, int64_t capacity, int64_t *total);
 

@@ -830,17 +830,32 @@ __global__ void __launch_bounds__(256)
     cap[s] = cnt < (1 << 24) ? cnt + (cnt >> 3) + 8 : (1 << 24);
 }
 
-// Lay out the current tree's rows in the scratch (row_off) when row mode is on and
-// the counts of these particles are known; returns whether the rows can be written.
+// equal rows of `cap` entries (no counts of these particles yet)
+__global__ void __launch_bounds__(256) row_uniform_kernel(int n, long long cap, int64_t *__restrict__ row_off)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s <= n) row_off[s] = (long long)s * cap;
+}
+
+// Lay out the current tree's rows in the scratch (row_off) when row mode is on:
+// from the last counts of these particles when known, else in equal rows (a
+// context that steps different particle sets, such as a serving slot's batches);
+// returns whether the rows can be written.
 int prepare_rows(p3t_ctx *c)
 {
     c->rows_cap_used = 0;
-    if (c->row_cap <= 0 || !c->row_scratch || c->counts_n != c->n || c->n <= 0) return 0;
+    if (c->row_cap <= 0 || !c->row_scratch || c->n <= 0) return 0;
     const int n = c->n;
-    row_caps_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->tree.perm, c->nbr_count, c->row_list);
-    if (scan_excl_i32_to_i64(c->row_list, c->row_off, n, c->row_off + n, c->scan_status, &c->meta->tickets[26],
-                             c->meta, c->stream) != P3T_OK)
-        return 0;
+    if (c->counts_n == n) {
+        row_caps_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->tree.perm, c->nbr_count, c->row_list);
+        if (scan_excl_i32_to_i64(c->row_list, c->row_off, n, c->row_off + n, c->scan_status,
+                                 &c->meta->tickets[26], c->meta, c->stream) != P3T_OK)
+            return 0;
+    } else {
+        const long long cap = (long long)(c->row_scratch_entries / (size_t)n);
+        if (cap < 1) return 0;
+        row_uniform_kernel<<<(n + 256) / 256, 256, 0, c->stream>>>(n, cap, c->row_off);
+    }
     c->rows_cap_used = 1;
     return 1;
 }
