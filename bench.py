@@ -476,6 +476,10 @@ def run_b300(args, rank, local, world):
                      "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (%s sm_max_mhz)"
                                     % (float(peaks.get("sm_max_mhz", 2032.0)), peak_kind),
                      "flops_per_launch": FLOPS_PER_INTERACTION * inter},
+        "roofline_cells_only": {"note": "the cell (monopole + quadrupole) terms alone at 38 flops each over "
+                                        "the same timed walk; the particle terms (W-weighted pairs) left out",
+                                "achieved": FLOPS_PER_INTERACTION * ncell / (far_ms * 1e-3) / 1e12,
+                                "frac": FLOPS_PER_INTERACTION * ncell / (far_ms * 1e-3) / 1e12 / fp32_peak},
         "roofline_force_only": {"kernel": "walk_kernel after the lists (no neighbour counting or rows)",
                                 "far_ms": far_only_ms,
                                 "achieved": FLOPS_PER_INTERACTION * inter / (far_only_ms * 1e-3) / 1e12,
