@@ -120,7 +120,7 @@ __device__ void write_node(Tree &T, int k, double M, const double com[3], const 
     ds_split(dsub(com[0], O[0]), chx, clx);
     ds_split(dsub(com[1], O[1]), chy, cly);
     ds_split(dsub(com[2], O[2]), chz, clz);
-    float4 *w = T.wn + (size_t)kWalkRecord * k;
+    const auto w = wrec_at(T.wn, k);
     w[0] = make_float4(chx, chy, chz, __double2float_rn(ro2));
     w[1] = make_float4(__double2float_rn(dsub(lo[0], O[0])), __double2float_rn(dsub(lo[1], O[1])),
                        __double2float_rn(dsub(lo[2], O[2])), __int_as_float(leaf ? -1 - tp.x : tp.z));

@@ -870,7 +870,7 @@ __device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool 
         q2[0] = make_float2(Q[0], Q[1]);
         q2[1] = make_float2(Q[2], Q[3]);
         q2[2] = make_float2(Q[4], Q[5]);
-        float4 *w = T.wn + (size_t)kWalkRecord * k;
+        const auto w = wrec_at(T.wn, k);
         w[0] = make_float4(chx, chy, chz, __double2float_rn(ro2));
         w[1] = make_float4(blx, bly, blz, __int_as_float(tp.z));
         w[2] = make_float4(bhx, bhy, bhz, __int_as_float(tp.w));

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kKnnThreads) knn_tree_kernel(Tree T, int n, in
     const int nn = T.meta->n_nodes;
     while (sp > 0) {
         const int node = stk[--sp];
-        const float4 *w = T.wn + (size_t)kWalkRecord * node;
+        const auto w = wrec_at(T.wn, node);
         const float4 b = w[1], c = w[2];  // box lo - O and child / particle start; box hi - O and count
         const float tx = fmaxf(fmaxf(b.x - h.x, h.x - c.x), 0.f);
         const float ty = fmaxf(fmaxf(b.y - h.y, h.y - c.y), 0.f);

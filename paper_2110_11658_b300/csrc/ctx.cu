@@ -82,7 +82,7 @@ static size_t scratch_plan(p3t_ctx *c, long long N, int L, char *base)
     put(&T.hi, 32 * (size_t)NN);
     put(&T.q32, 24 * (size_t)NN);
     put(&T.q64, 48 * (size_t)NN);
-    put(&T.wn, 16 * (size_t)kWalkRecord * (size_t)NN);
+    put(&T.wn, 16 * wrec_words(NN));
     return off;
 }
 

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kDecThreads)
         for (int j = 0; j < tp.w; j++) next[ch_off[f] + j] = tp.z + j;
     if (!write) return;
     LetNode &o = out_nodes[node_base + f];
-    const float4 *w = T.wn + (size_t)kWalkRecord * u;
+    const auto w = wrec_at(T.wn, u);
 #pragma unroll
     for (int j = 0; j < kWalkRecord; j++) o.wn[j] = w[j];
     o.comM = cm, o.lo = cl, o.hi = ch;
@@ -362,7 +362,7 @@ struct Joined {
 __device__ __forceinline__ void put_links(const Joined &J, int k, int4 tp)
 {
     J.topo[k] = tp;
-    float4 *w = J.wn + (size_t)kWalkRecord * k;
+    const auto w = wrec_at(J.wn, k);
     const bool leaf = tp.z < 0;
     w[1].w = __int_as_float(leaf ? -1 - tp.x : tp.z);
     w[2].w = __int_as_float(leaf ? tp.y : tp.w);
@@ -387,8 +387,8 @@ __global__ void __launch_bounds__(kDecThreads)
         else
             J.q32[6 * (size_t)d + a] = T.q32[6 * (size_t)k + a];
     }
-    const float4 *w = T.wn + (size_t)kWalkRecord * k;
-    float4 *o = J.wn + (size_t)kWalkRecord * d;
+    const auto w = wrec_at(T.wn, k);
+    const auto o = wrec_at(J.wn, d);
     for (int j = 0; j < kWalkRecord; j++) o[j] = w[j];
     put_links(J, d, tp);
 }
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kDecThreads)
         else
             J.q32[6 * (size_t)d + a] = o.q32[a];
     }
-    float4 *w = J.wn + (size_t)kWalkRecord * d;
+    const auto w = wrec_at(J.wn, d);
     for (int j = 0; j < kWalkRecord; j++) w[j] = o.wn[j];
     put_links(J, d, tp);
 }
@@ -857,7 +857,7 @@ int p3t_tree_join(p3t_ctx *c, int32_t n_let, const void *const *let_nodes, const
         return o;
     };
     const size_t o_topo = slot(16 * NN), o_comM = slot(32 * NN), o_lo = slot(32 * NN), o_hi = slot(32 * NN),
-                 o_q64 = slot(48 * NN), o_q32 = slot(24 * NN), o_wn = slot(16 * kWalkRecord * NN),
+                 o_q64 = slot(48 * NN), o_q32 = slot(24 * NN), o_wn = slot(16 * wrec_words((long long)NN)),
                  o_sp = slot(32 * NP), o_ph = slot(16 * NP), o_pl = slot(16 * NP), o_rid = slot(4 * NP),
                  o_cid = slot(4 * NP);
     if (jo > c->join_bytes) {

@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 bool open = false, is_leaf = false;
                 int cinfo = 0, ccount = 0;
                 if (node >= 0) {
-                    const float4 *rec = T.wn + (size_t)kWalkRecord * node;
+                    const auto rec = wrec_at(T.wn, node);
                     const float4 b = rec[1], cc = rec[2];
                     cinfo = __float_as_int(b.w);
                     ccount = __float_as_int(cc.w);

@@ -29,6 +29,28 @@ constexpr int kMaxLevelSlots = 24;   // per-level bookkeeping arrays
 // 32 ns, the rest 256 ns, so 2^22 polls take about 1.1 s.
 constexpr long long kSpinLimit = 1LL << 22;
 constexpr int kWalkRecord = 6;               // float4 per node in Tree::wn
+// Node k's walk record, field f (0 .. kWalkRecord - 1): blocks of 32 nodes stored field
+// by field, so that a warp reading one field of consecutive nodes (the children of the
+// ranges it popped) reads consecutive 16-byte words.  Buffers hold whole blocks.
+__host__ __device__ __forceinline__ size_t wrec(int k, int f)
+{
+    return ((size_t)(k >> 5) * kWalkRecord + f) * 32 + (k & 31);
+}
+__host__ __device__ __forceinline__ size_t wrec_words(long long nodes)  // float4 of a buffer
+{
+    return (size_t)((nodes + 31) / 32) * 32 * kWalkRecord;
+}
+template <typename V>
+struct WRecRef {
+    V *base;
+    int k;
+    __host__ __device__ __forceinline__ V &operator[](int f) const { return base[wrec(k, f)]; }
+};
+template <typename V>
+__host__ __device__ __forceinline__ WRecRef<V> wrec_at(V *base, int k)
+{
+    return WRecRef<V>{base, k};
+}
 constexpr float kFp32U = 5.9604644775390625e-8f;  // 2^-24, FP32 unit round-off
 
 // Error band of an FP32 squared-distance test d2 < r2 in a cluster frame of half
@@ -111,7 +133,7 @@ struct Tree {
     double4_32a *hi;
     double *q64;   // 6 per node (FP64 form)
     float *q32;    // 6 per node (mixed form)
-    float4 *wn;    // kWalkRecord float4 per node
+    float4 *wn;    // kWalkRecord float4 per node (layout: wrec)
     int2 *grp;
     double4_32a *glo, *ghi;
     // per group, three float4 made once per build (mixed walks): the double-single

@@ -984,7 +984,7 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
             float4 ra, rd, rq0, rq1;  // node record: COM hi / lo + M / quadrupole
             if (node >= 0) {
                 if (kMixed) {
-                    const float4 *rec = T.wn + (size_t)kWalkRecord * node;
+                    const auto rec = wrec_at(T.wn, node);
                     ra = rec[0];
                     const float4 b = rec[1], c = rec[2];
                     rd = rec[3];
@@ -1069,7 +1069,7 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
                     }
                 } else {
                     const double4_32a cm = T.comM[node], cl = T.lo[node], ch = T.hi[node];
-                    const float4 *rec = T.wn + (size_t)kWalkRecord * node;
+                    const auto rec = wrec_at(T.wn, node);
                     cinfo = __float_as_int(rec[1].w);
                     ccount = __float_as_int(rec[2].w);
                     open = dist2_point_box(cm.x, cm.y, cm.z, glo, ghi) < cl.w ||
