@@ -1038,20 +1038,26 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     topo_finish_kernel<<<1, 1, 0, s>>>(M, T.cap_nodes);
     if (check_launch(c)) return P3T_ERR_CUDA;
 
-    // groups
+    // groups, on the side stream beside the moments: both only read the topology
+    // (the stream joins again before the build returns)
+    const bool fork = c->side_stream != nullptr;
+    const cudaStream_t gs = fork ? c->side_stream : s;
+    if (fork && (cudaEventRecord(c->fork_ev, s) != cudaSuccess || cudaStreamWaitEvent(gs, c->fork_ev, 0) != cudaSuccess))
+        return P3T_ERR_CUDA;
     int e = scan_excl_u8_to_i32(T.gflag, T.gidx, n, &M->n_groups, c->scan_status, &M->tickets[30],
-                                M, s);
+                                M, gs);
     if (e) return e;
-    group_first_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, T.gflag, T.gidx, T.grp);
-    group_finish_kernel<<<persistent, kBuildThreads, 0, s>>>(T, n);
-    group_frames_kernel<<<persistent, kBuildThreads, 0, s>>>(T);
-    if (cudaMemsetAsync(T.gbins, 0, sizeof(int32_t) * 2 * kGroupBins, s) != cudaSuccess)
+    group_first_kernel<<<grid_n, kBuildThreads, 0, gs>>>(n, T.gflag, T.gidx, T.grp);
+    group_finish_kernel<<<persistent, kBuildThreads, 0, gs>>>(T, n);
+    group_frames_kernel<<<persistent, kBuildThreads, 0, gs>>>(T);
+    if (cudaMemsetAsync(T.gbins, 0, sizeof(int32_t) * 2 * kGroupBins, gs) != cudaSuccess)
         return P3T_ERR_CUDA;
     // few blocks: the bins take one global atomic per block and bin
     const int order_grid = std::min(64, persistent);
-    group_bins_kernel<<<order_grid, kBuildThreads, 0, s>>>(T);
-    group_bins_scan_kernel<<<1, kGroupBins, 0, s>>>(T);
-    group_order_kernel<<<order_grid, kBuildThreads, 0, s>>>(T);
+    group_bins_kernel<<<order_grid, kBuildThreads, 0, gs>>>(T);
+    group_bins_scan_kernel<<<1, kGroupBins, 0, gs>>>(T);
+    group_order_kernel<<<order_grid, kBuildThreads, 0, gs>>>(T);
+    if (fork && cudaEventRecord(c->join_ev, gs) != cudaSuccess) return P3T_ERR_CUDA;
 
     // moments: leaves, then levels 20 .. 0 (a level without internal nodes exits at once)
     const bool q64 = P.precision == P3T_FP64;
@@ -1065,6 +1071,7 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
         else
             moments_level3_kernel<<<persistent, kBuildThreads, 0, s>>>(T, l);
     }
+    if (fork && cudaStreamWaitEvent(s, c->join_ev, 0) != cudaSuccess) return P3T_ERR_CUDA;
     return check_launch(c);
 }
 

@@ -233,6 +233,15 @@ int p3t_create(p3t_ctx **out, const p3t_params *p, void *cuda_stream)
         delete c;
         return P3T_ERR_CUDA;
     }
+    // a second stream for the build's group pass (without it the pass runs in line)
+    if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->side_stream) cudaStreamDestroy(c->side_stream);
+        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+        c->side_stream = nullptr, c->fork_ev = c->join_ev = nullptr;
+    }
     *out = c;
     return P3T_OK;
 }
@@ -250,6 +259,12 @@ int p3t_destroy(p3t_ctx *c)
     }
     if (c->lists_ready) cudaEventDestroy(c->lists_ready);
     if (c->v_ready) cudaEventDestroy(c->v_ready);
+    if (c->side_stream) {
+        cudaStreamSynchronize(c->side_stream);
+        cudaStreamDestroy(c->side_stream);
+    }
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
     if (c->clusters) cudaFree(c->clusters);
     if (c->irr_buf) cudaFree(c->irr_buf);
     if (c->knn_buf) cudaFree(c->knn_buf);

@@ -462,6 +462,8 @@ struct p3t_ctx {
     size_t blob_bytes;
     void *host_stage;                 // device staging of p3t_step_host
     size_t host_stage_bytes;
+    cudaStream_t side_stream;         // the build's groups, beside its moments (null: in line)
+    cudaEvent_t fork_ev, join_ev;
     cudaStream_t copy_stream;         // p3t_step_host: velocity upload and neighbour-list
     cudaEvent_t lists_ready;          // copy beside the build and the far force
     cudaEvent_t v_ready;
