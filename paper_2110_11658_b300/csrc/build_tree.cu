@@ -46,6 +46,7 @@ __global__ void init_meta_kernel(Meta *m)
         m->n_leaves = 0;
         m->depth = 0;
         m->fallback_tests = 0;
+        m->uncounted = 0;
     }
 }
 
@@ -90,6 +91,7 @@ __global__ void cluster_params_kernel(Cluster *cl, int C, const double *__restri
     K.rl2_f = (float)K.rl2_d;
     K.rl_f = (float)rl;
     K.counted = rl > 0.0;  // the mixed walk counts every list radius (shell ranges beyond r_out)
+    if (!K.counted) atomicAdd(&meta->uncounted, 1);
 }
 
 // cluster of every particle from the offsets (validated: 0 = seg[0] < ... < seg[C] = n)

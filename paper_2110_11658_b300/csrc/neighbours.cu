@@ -68,6 +68,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         if (blockIdx.x == 0 && threadIdx.x == 0) latch_error(meta, P3T_ERR_CAPACITY);
         return;
     }
+    // nothing to do: row mode with every row within its room, or a count pass after a
+    // walk that counted every cluster
+    if (FILL && P.row_cap > 0 && meta->row_over == 0) return;
+    if (!FILL && P.skip_counted && meta->uncounted == 0) return;
 
     while (true) {
         int g = 0;
@@ -338,6 +342,11 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
             for (int t = 0; t < TPL; t++)
                 if (si[t] >= 0) P.count[T.perm[si[t]]] = cnt[t];
         }
+        if (ROWS) {
+#pragma unroll
+            for (int t = 0; t < TPL; t++)
+                if (si[t] >= 0 && rwc[t] > rcap[t]) meta->row_over = 1;
+        }
         __syncwarp();
     }
 }
@@ -346,10 +355,12 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 // Rows are distinct indices in [0, n), so the sorted row is unique and any
 // correct sort writes the same bytes.  The rows are first binned by length into
 // per-class lists (two cheap passes over the row offsets), then each class is
-// sorted by its own launch, one warp per listed row, so that no launch scans the
-// rows of other classes and only one class's code is resident in the
-// instruction cache:
-//   (1, 1024]     bitonic network in registers, K = 1, 2, 4, 8, 16, 32 entries
+// sorted by its own launch, one warp per listed row (one thread for the
+// shortest), so that no launch scans the rows of other classes and only one
+// class's code is resident in the instruction cache:
+//   [1, 4]        a 5-comparator network in one thread's registers (a row of
+//                 one entry is only copied, from the walk's scratch in row mode)
+//   (4, 1024]     bitonic network in registers, K = 1, 2, 4, 8, 16, 32 entries
 //                 per lane: up to 128 in the strided layout (element e = 32 r +
 //                 lane in register r; partners 32 apart or more are in the same
 //                 lane, closer ones are exchanged by shuffles), above in the
@@ -362,15 +373,16 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
 // pair whose upper index is past the end never moves.  (An LSD radix sort in
 // shared memory, ranks from ballots, was slower than these networks for every
 // class of the 10^6-particle Plummer workload.)
-constexpr int kRowClasses = 8;
+constexpr int kRowClasses = 9;
 // class c holds the rows with kClassLen[c] < len <= kClassLen[c + 1]
-__constant__ int kClassLenDev[kRowClasses + 1] = {0, 32, 64, 128, 256, 512, 1024, 2048, INT_MAX};
-constexpr int kClassLen[kRowClasses + 1] = {0, 32, 64, 128, 256, 512, 1024, 2048, INT_MAX};
+__constant__ int kClassLenDev[kRowClasses + 1] = {0, 4, 32, 64, 128, 256, 512, 1024, 2048, INT_MAX};
+constexpr int kClassLen[kRowClasses + 1] = {0, 4, 32, 64, 128, 256, 512, 1024, 2048, INT_MAX};
+static_assert(2 * kRowClasses <= (int)(sizeof(Meta::row_class) / sizeof(int)), "class counters and cursors");
 constexpr int kSortWarps = 4;
 constexpr int kRowLoadBatch = 8;  // global loads a lane issues before storing any
 // bit c set: class c uses the transposed register network (faster for
 // (128, 1024], slower for (64, 128] on the 10^6-particle Plummer rows)
-constexpr unsigned kTransposed = (1u << 3) | (1u << 4) | (1u << 5);
+constexpr unsigned kTransposed = (1u << 4) | (1u << 5) | (1u << 6);
 
 __device__ __forceinline__ int row_class(int len)
 {
@@ -635,6 +647,49 @@ __device__ void warp_sort_mem(int32_t *a, int len)
     }
 }
 
+// ascending compare-exchange of two registers
+__device__ __forceinline__ void cx2(int &a, int &b)
+{
+    const int lo = min(a, b), hi = max(a, b);
+    a = lo, b = hi;
+}
+
+// rows of class C (at most 4 entries), one thread each: a 5-comparator network
+template <int C>
+__global__ void __launch_bounds__(kSortWarps * 32)
+    row_sort_tiny_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
+                         int32_t *idx, RowSrc src)
+{
+    static_assert(kClassLen[C + 1] == 4, "four entries per row");
+    int start = 0;
+#pragma unroll
+    for (int q = 0; q < C; q++) start += meta->row_class[q];
+    const int count = meta->row_class[C];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const int i = list[start + k];
+        const long long o = offs[i];
+        const int len = (int)(offs[i + 1] - o);
+        const int32_t *s = idx + o;
+        if (src.rows) {
+            long long lo;
+            int cap;
+            row_span(src.row_off, src.entries, src.inv[i], lo, cap);
+            if (len <= cap) s = src.rows + lo;
+        }
+        int v0 = s[0], v1 = len > 1 ? s[1] : INT_MAX, v2 = len > 2 ? s[2] : INT_MAX, v3 = len > 3 ? s[3] : INT_MAX;
+        cx2(v0, v1);
+        cx2(v2, v3);
+        cx2(v0, v2);
+        cx2(v1, v3);
+        cx2(v1, v2);
+        int32_t *row = idx + o;
+        row[0] = v0;
+        if (len > 1) row[1] = v1;
+        if (len > 2) row[2] = v2;
+        if (len > 3) row[3] = v3;
+    }
+}
+
 template <int C, int K>
 __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_reg_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
@@ -731,27 +786,28 @@ static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long
     row_class_fill_kernel<<<grid, 256, 0, s>>>(n, offsets, capacity, c->meta, c->row_list);
     int e = check_launch(c);
     if (e) return e;
-    if ((e = launch_sort(c, row_sort_reg_kernel<0, 1>, offsets, idx, src))) return e;
-    if ((e = launch_sort(c, row_sort_reg_kernel<1, 2>, offsets, idx, src))) return e;
-    if (kTransposed & (1u << 2))
-        e = launch_sort(c, row_sort_tr_kernel<2, 4>, offsets, idx, src);
+    if ((e = launch_sort(c, row_sort_tiny_kernel<0>, offsets, idx, src))) return e;
+    if ((e = launch_sort(c, row_sort_reg_kernel<1, 1>, offsets, idx, src))) return e;
+    if ((e = launch_sort(c, row_sort_reg_kernel<2, 2>, offsets, idx, src))) return e;
+    if (kTransposed & (1u << 3))
+        e = launch_sort(c, row_sort_tr_kernel<3, 4>, offsets, idx, src);
     else
-        e = launch_sort(c, row_sort_reg_kernel<2, 4>, offsets, idx, src);
+        e = launch_sort(c, row_sort_reg_kernel<3, 4>, offsets, idx, src);
     if (e) return e;
-    if (n > kClassLen[3] + 1) {  // longer rows need more than 128 distinct indices
-        if (kTransposed & (1u << 3))
-            e = launch_sort(c, row_sort_tr_kernel<3, 8>, offsets, idx, src);
-        else
-            e = launch_sort(c, row_sort_reg_kernel<3, 8>, offsets, idx, src);
-        if (e) return e;
+    if (n > kClassLen[4] + 1) {  // longer rows need more than 128 distinct indices
         if (kTransposed & (1u << 4))
-            e = launch_sort(c, row_sort_tr_kernel<4, 16>, offsets, idx, src);
+            e = launch_sort(c, row_sort_tr_kernel<4, 8>, offsets, idx, src);
         else
-            e = launch_sort(c, row_sort_reg_kernel<4, 16>, offsets, idx, src);
+            e = launch_sort(c, row_sort_reg_kernel<4, 8>, offsets, idx, src);
         if (e) return e;
-        if ((e = launch_sort(c, row_sort_tr_kernel<5, 32>, offsets, idx, src))) return e;
-        if ((e = launch_sort(c, row_sort_smem_kernel<6>, offsets, idx, src))) return e;
-        if ((e = launch_sort(c, row_sort_global_kernel<7>, offsets, idx, src))) return e;
+        if (kTransposed & (1u << 5))
+            e = launch_sort(c, row_sort_tr_kernel<5, 16>, offsets, idx, src);
+        else
+            e = launch_sort(c, row_sort_reg_kernel<5, 16>, offsets, idx, src);
+        if (e) return e;
+        if ((e = launch_sort(c, row_sort_tr_kernel<6, 32>, offsets, idx, src))) return e;
+        if ((e = launch_sort(c, row_sort_smem_kernel<7>, offsets, idx, src))) return e;
+        if ((e = launch_sort(c, row_sort_global_kernel<8>, offsets, idx, src))) return e;
     }
     return P3T_OK;
 }
@@ -845,6 +901,7 @@ int prepare_rows(p3t_ctx *c)
 {
     c->rows_cap_used = 0;
     if (c->row_cap <= 0 || !c->row_scratch || c->n <= 0) return 0;
+    if (cudaMemsetAsync(&c->meta->row_over, 0, sizeof(int), c->stream) != cudaSuccess) return 0;
     const int n = c->n;
     if (c->counts_n == n) {
         row_caps_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->tree.perm, c->nbr_count, c->row_list);

@@ -95,7 +95,9 @@ struct Meta {
     long long nbr_total;
     long long fallback_tests;      // FP64 decisions taken after an undecided FP32 filter
     unsigned long long core_count; // particles within the core radius (core quantities)
-    int row_class[16];             // neighbour rows by length class: counts, fill cursors
+    int row_class[20];             // neighbour rows by length class: counts, fill cursors
+    int uncounted;                 // clusters whose neighbours the mixed walk does not count
+    int row_over;                  // row mode: a row outgrew its room since the rows were laid out
     long long spin_limit;          // polls of a bounded wait (0: kSpinLimit)
 };
 

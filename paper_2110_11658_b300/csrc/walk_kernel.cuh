@@ -1236,6 +1236,12 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
                     if (POT) P.pot[o] = (double)A.s[t][3];
                 }
                 if (count_here) P.nbr_count[o] = NC.cnt[t] - 1;  // minus the pair with itself
+                if constexpr (NBR == 2) {  // a row that outgrew its room: the fill pass rebuilds it
+                    long long lo;
+                    int cap;
+                    row_span(P.row_off, P.row_entries, s, lo, cap);
+                    if (NC.wc[t] > cap) meta->row_over = 1;
+                }
             }
         }
         if (walker) {

@@ -170,9 +170,10 @@ def test_extreme_scales_switch_filters_off_or_on(scale):
 
 def test_long_neighbour_rows_take_every_sort_path():
     # short rows (Plummer) and tight clumps whose rows fill every length class of
-    # the row sort: (1, 32], (32, 64], (64, 128] and (128, 256], (256, 512],
-    # (512, 1024] (register networks, strided and transposed), (1024, 2048] (shared
-    # memory) and > 2048 (global memory); every row must equal the brute force
+    # the row sort: [1, 4] (one thread a row), (4, 32], (32, 64], (64, 128] and
+    # (128, 256], (256, 512], (512, 1024] (register networks, strided and
+    # transposed), (1024, 2048] (shared memory) and > 2048 (global memory); every
+    # row must equal the brute force
     p = synth.plummer(3000, 41)
     rng = np.random.default_rng(41)
     xs, ys, zs = [p.x], [p.y], [p.z]
@@ -186,8 +187,8 @@ def test_long_neighbour_rows_take_every_sort_path():
     g = run_gpu(c, p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05), pot=False)
     o2, i2 = oracle.neighbours_brute(x, y, z, 0.05)
     lens = np.diff(o2)
-    for lo, hi in ((1, 32), (32, 64), (64, 128), (128, 256), (256, 512), (512, 1024), (1024, 2048),
-                   (2048, n)):
+    for lo, hi in ((0, 1), (1, 4), (4, 32), (32, 64), (64, 128), (128, 256), (256, 512), (512, 1024),
+                   (1024, 2048), (2048, n)):
         assert ((lens > lo) & (lens <= hi)).any(), (lo, hi)
     assert np.array_equal(g["offs"], o2) and np.array_equal(g["idx"], i2)
 
