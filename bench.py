@@ -653,8 +653,9 @@ def _dist(ts):
             "min": float(a.min()), "max": float(a.max()), "steps": len(ts)}
 
 
-# the launch shape the autotuner picks for this ensemble (G, list tile, leaf capacity)
-ENS_TUNED = {"group_size": 32, "threads_per_group": 32, "tile": 64, "leaf_cap": 16}
+# the launch shape the autotuner picks for this ensemble (G, threads per group, list tile, leaf
+# capacity, and the lists before the far force)
+ENS_TUNED = {"group_size": 32, "threads_per_group": 32, "tile": 64, "leaf_cap": 16, "lists_first": 1}
 
 
 def ensemble_run(args, short=False):
@@ -711,7 +712,7 @@ def ensemble_run(args, short=False):
         g = ctx.capture_step(st["x"], st["y"], st["z"], st["m"], *buf["a"], seg_offsets=seg, cluster_params=cprm,
                              vx=st["vx"], vy=st["vy"], vz=st["vz"], kick_dt=DT, drift_dt=DT,
                              n_cell=buf["nc"], n_part=buf["np"], offsets=buf["offs"], idx=buf["idx"],
-                             total=buf["tot"])
+                             total=buf["tot"], lists_first=bool(cfg.get("lists_first", 0)))
         return g, ctx
 
     tune_state = {k: v.clone() for k, v in init.items()}
@@ -719,7 +720,7 @@ def ensemble_run(args, short=False):
         best, table = dict(ENS_TUNED), []
     elif args.no_tune:
         best = {"group_size": args.group_size, "threads_per_group": args.threads_per_group, "tile": args.tile,
-                "leaf_cap": args.leaf_cap}
+                "leaf_cap": args.leaf_cap, "lists_first": 0}
         table = []
     else:
         res = autotune.Tuner(autotune.time_graph_step(lambda cfg: batched_graph(cfg, tune_state), steps=3),
@@ -752,7 +753,8 @@ def ensemble_run(args, short=False):
     ctx.close()
     if short:
         del g
-        per_s = _sequential_graph_ms(cl, segn, rows, init, buf, params(best), stream, dev, steps, flush)
+        per_s = _sequential_graph_ms(cl, segn, rows, init, buf, params(best), stream, dev, steps, flush,
+                                     bool(best.get("lists_first", 0)))
         b = out["batched_graph"]
         return {"workload": "ensemble64_plummer_king5_n1e4-5e5", "n_clusters": len(cl), "particles": n,
                 "shape": best, "steps": steps, "step_ms_p50": b["p50"], "step_ms_p99": b["p99"],
@@ -767,10 +769,16 @@ def ensemble_run(args, short=False):
     st = {k: v.clone() for k, v in init.items()}
     ctx = p3t.Context(params(best), stream)
 
+    lists_first = bool(best.get("lists_first", 0))
+
     def eager():
         ctx.build_tree_batch(seg, st["x"], st["y"], st["z"], st["m"], cluster_params=cprm)
-        ctx.far_force(*buf["a"])
-        ctx.neighbours_async(buf["offs"], buf["idx"], buf["tot"])
+        if lists_first:
+            ctx.neighbours_async(buf["offs"], buf["idx"], buf["tot"])
+            ctx.far_force(*buf["a"])
+        else:
+            ctx.far_force(*buf["a"])
+            ctx.neighbours_async(buf["offs"], buf["idx"], buf["tot"])
         ctx.kick(DT, *buf["a"], st["vx"], st["vy"], st["vz"])
         ctx.drift(DT, st["x"], st["y"], st["z"], st["vx"], st["vy"], st["vz"])
 
@@ -803,8 +811,12 @@ def ensemble_run(args, short=False):
     def sequential():
         for cx, v, a, offs, idx, tot in per:
             cx.build_tree(v["x"], v["y"], v["z"], v["m"])
-            cx.far_force(*a)
-            cx.neighbours_async(offs, idx, tot)
+            if lists_first:
+                cx.neighbours_async(offs, idx, tot)
+                cx.far_force(*a)
+            else:
+                cx.far_force(*a)
+                cx.neighbours_async(offs, idx, tot)
             cx.kick(DT, *a, v["vx"], v["vy"], v["vz"])
             cx.drift(DT, v["x"], v["y"], v["z"], v["vx"], v["vy"], v["vz"])
 
@@ -812,7 +824,7 @@ def ensemble_run(args, short=False):
         sequential()
     out["sequential_eager"] = _dist(_events_ms(stream, sequential, steps, flush))
     graphs = [cx.capture_step(v["x"], v["y"], v["z"], v["m"], *a, vx=v["vx"], vy=v["vy"], vz=v["vz"],
-                              kick_dt=DT, drift_dt=DT, offsets=offs, idx=idx, total=tot)
+                              kick_dt=DT, drift_dt=DT, offsets=offs, idx=idx, total=tot, lists_first=lists_first)
               for cx, v, a, offs, idx, tot in per]
 
     def sequential_graphs():
@@ -857,7 +869,7 @@ def ensemble_run(args, short=False):
     }
 
 
-def _sequential_graph_ms(cl, segn, rows, init, buf, prm0, stream, dev, steps, flush):
+def _sequential_graph_ms(cl, segn, rows, init, buf, prm0, stream, dev, steps, flush, lists_first=False):
     """The ensemble step one cluster at a time: a context and a captured graph per
     cluster (its own r_out), the 64 graphs launched back to back; step times in ms."""
     import copy
@@ -881,7 +893,7 @@ def _sequential_graph_ms(cl, segn, rows, init, buf, prm0, stream, dev, steps, fl
         cx.far_force(*a)
         cx.neighbours(offs, idx)  # sizes the row scratch (row mode)
         g = cx.capture_step(v["x"], v["y"], v["z"], v["m"], *a, vx=v["vx"], vy=v["vy"], vz=v["vz"],
-                            kick_dt=DT, drift_dt=DT, offsets=offs, idx=idx, total=tot)
+                            kick_dt=DT, drift_dt=DT, offsets=offs, idx=idx, total=tot, lists_first=lists_first)
         per.append((cx, g))
 
     def launch_all():

@@ -344,8 +344,17 @@ int p3t_scratch_bytes(const p3t_params *p, int64_t n, int32_t n_clusters, int64_
  *   drift_dt: x += drift_dt * v after the kick; 0: no drift.
  *   events: five optional cudaEvent_t handles (null entries skipped), recorded
  *     into the graph as event nodes at the start of the step, after the build,
- *     after the far force, after the lists and at the end, so that one launch
- *     can be timed phase by phase (cudaEventElapsedTime after it completes).
+ *     after the far force, after the lists and at the end (lists_first: after the
+ *     lists, then after the far force), so that one launch can be timed phase by
+ *     phase (cudaEventElapsedTime after it completes).
+ *   lists_first: 0, the far force before the lists (its walk counts the
+ *     neighbours and, in row mode, writes their rows); 1, the lists first (their
+ *     own count pass, then a far force that computes forces only), which is
+ *     faster when the rows are short.  Both orders give the same lists, and
+ *     the same forces bit for bit unless a cluster lists neighbours beyond its
+ *     r_out (then to rounding: the counting walk stages that cluster's
+ *     neighbour-only sources with mass 0, which changes how the pair sums are
+ *     split).
  * p3t_graph_capture sizes the context's scratch for the step first, then
  * records the step on a private stream, so nothing runs or allocates during
  * capture; the graph is launched on the context's stream.  The context's
@@ -378,6 +387,7 @@ typedef struct {
     double kick_dt;
     double drift_dt;
     void *events[5];
+    int32_t lists_first;
 } p3t_step_args;
 int p3t_graph_capture(p3t_ctx *c, const p3t_step_args *a, p3t_graph **out);
 int p3t_graph_launch(p3t_graph *g);

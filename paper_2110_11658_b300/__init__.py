@@ -65,7 +65,7 @@ class p3t_step_args(C.Structure):
                 ("ax", C.c_void_p), ("ay", C.c_void_p), ("az", C.c_void_p), ("pot", C.c_void_p),
                 ("n_cell", C.c_void_p), ("n_part", C.c_void_p), ("offsets", C.c_void_p), ("idx", C.c_void_p),
                 ("capacity", C.c_int64), ("total", C.c_void_p), ("kick_dt", C.c_double),
-                ("drift_dt", C.c_double), ("events", C.c_void_p * 5)]
+                ("drift_dt", C.c_double), ("events", C.c_void_p * 5), ("lists_first", C.c_int32)]
 
 
 class p3t_seg_array(C.Structure):
@@ -544,11 +544,13 @@ class Context:
 
     def capture_step(self, x, y, z, m, ax, ay, az, seg_offsets=None, cluster_params=None, vx=None, vy=None,
                      vz=None, kick_dt=0.0, drift_dt=0.0, pot=None, n_cell=None, n_part=None, offsets=None,
-                     idx=None, total=None, capacity=None, events=None):
+                     idx=None, total=None, capacity=None, events=None, lists_first=False):
         """Record one step (build, far force, neighbour lists, kick, drift) into a CUDA graph
         (p3t_graph_capture).  The tensors are baked in: replays reuse them.  events: up to
         five torch.cuda.Event (timing) or None, recorded as graph nodes at the step's start,
-        after the build, the far force and the lists, and at its end."""
+        after the build, the far force and the lists (lists_first: the lists, then the far
+        force), and at its end.  lists_first: the lists before the far force (faster for
+        short rows; same results)."""
         t = self._torch
         n = x.numel()
         nc = 1 if seg_offsets is None else seg_offsets.numel() - 1
@@ -564,6 +566,7 @@ class Context:
             _ptr(n_part, t.int64, 1, "n_part"), _ptr(offsets, t.int64, n + 1, "offsets"),
             _ptr(idx, t.int32, cap, "idx"), cap, _ptr(total, t.int64, 1, "total"), float(kick_dt),
             float(drift_dt))
+        a.lists_first = 1 if lists_first else 0
         for k, ev in enumerate(list(events or [])[:5]):
             if ev is not None:
                 if not ev.cuda_event:  # torch creates the event on its first record

@@ -8,10 +8,13 @@ are evaluated) and the leaf capacity L of the octree.  G and L change the group 
 interaction lists themselves: a tuned configuration is part of the result's
 identity, and the oracle reproduces a result given the same G and L.
 
-The search runs in two stages to bound its cost: G x threads per group x tile
-at the default leaf capacity, then L at the best (G, threads, tile).  The
-threads per group change only how the same lists are evaluated, not the
-results.  Every candidate is timed by a
+The search runs in three stages to bound its cost: G x threads per group x tile
+at the default leaf capacity, then L at the best (G, threads, tile), then the
+order of a step's far force and neighbour lists at the best shape (the walk
+counting the neighbours, or the lists' own count pass first and a force-only
+walk: the second pays when the rows are short).  The threads per group and the
+order change only how the same lists and forces are computed, not the results.
+Every candidate is timed by a
 caller-supplied function (normally a graph-captured step of the real
 workload, see ``time_graph_step``) as the median of a few repeats.  Results
 can be cached in a JSON file, keyed by a workload signature.
@@ -27,7 +30,8 @@ from dataclasses import dataclass, field
 GROUP_SIZES = (32, 64, 128)
 TILES = (32, 64, 128, 256)
 LEAF_CAPS = (8, 16, 32)
-DEFAULT = {"group_size": 32, "threads_per_group": 32, "tile": 64, "leaf_cap": 16}
+ORDERS = (0, 1)  # lists_first: the far force before the lists (0) or after them (1)
+DEFAULT = {"group_size": 32, "threads_per_group": 32, "tile": 64, "leaf_cap": 16, "lists_first": 0}
 
 
 def thread_counts(g: int):
@@ -41,7 +45,7 @@ def valid(cfg: dict) -> bool:
     g, t, leaf = cfg["group_size"], cfg["tile"], cfg["leaf_cap"]
     tpg = cfg.get("threads_per_group", 32)
     return (1 <= g <= 128 and 32 <= t <= 256 and t % 32 == 0 and 1 <= leaf <= (1 << 20)
-            and tpg in (32, 64, 128) and (tpg == 32 or g <= tpg))
+            and tpg in (32, 64, 128) and (tpg == 32 or g <= tpg) and cfg.get("lists_first", 0) in (0, 1))
 
 
 def workload_key(device: str, sizes, precision: int, theta, extra: str = "") -> str:
@@ -61,18 +65,20 @@ class Result:
 
 
 class Tuner:
-    """Two-stage search over (G, threads per group, tile) then leaf capacity.
+    """Three-stage search over (G, threads per group, tile), then leaf capacity,
+    then the order of far force and lists.
 
     time_fn(cfg) -> milliseconds of one step with that configuration; it is
     called `repeats` times per candidate and the median is kept.
     """
 
     def __init__(self, time_fn, repeats: int = 3, cache_path: str | None = None,
-                 group_sizes=GROUP_SIZES, tiles=TILES, leaf_caps=LEAF_CAPS):
+                 group_sizes=GROUP_SIZES, tiles=TILES, leaf_caps=LEAF_CAPS, orders=ORDERS):
         self.time_fn = time_fn
         self.repeats = max(1, int(repeats))
         self.cache_path = cache_path
         self.group_sizes, self.tiles, self.leaf_caps = tuple(group_sizes), tuple(tiles), tuple(leaf_caps)
+        self.orders = tuple(orders)
 
     def _load(self) -> dict:
         if self.cache_path and os.path.exists(self.cache_path):
@@ -100,7 +106,8 @@ class Tuner:
             if hit is not None:
                 return Result(hit["best"], hit["best_ms"], [(c, ms) for c, ms in hit["table"]], cached=True)
         table = []
-        stage1 = [{"group_size": g, "threads_per_group": w, "tile": t, "leaf_cap": DEFAULT["leaf_cap"]}
+        stage1 = [{"group_size": g, "threads_per_group": w, "tile": t, "leaf_cap": DEFAULT["leaf_cap"],
+                   "lists_first": DEFAULT["lists_first"]}
                   for g in self.group_sizes for w in thread_counts(g) for t in self.tiles]
         for cfg in stage1:
             if valid(cfg):
@@ -110,6 +117,11 @@ class Tuner:
         best, _ = min(table, key=lambda e: e[1])
         for leaf in self.leaf_caps:
             cfg = dict(best, leaf_cap=leaf)
+            if valid(cfg) and all(cfg != c for c, _ in table):
+                table.append((cfg, self._measure(cfg)))
+        best, _ = min(table, key=lambda e: e[1])
+        for order in self.orders:
+            cfg = dict(best, lists_first=order)
             if valid(cfg) and all(cfg != c for c, _ in table):
                 table.append((cfg, self._measure(cfg)))
         best, best_ms = min(table, key=lambda e: e[1])

@@ -34,13 +34,15 @@ static int record_step(p3t_ctx *c, const p3t_step_args *a)
                                               a->cluster_params, a->x, a->y, a->z, a->m)
                        : p3t_build_tree(c, a->n, a->x, a->y, a->z, a->m);
     if (e || (e = mark(c, a, 1))) return e;
-    e = p3t_far_force(c, a->ax, a->ay, a->az, a->pot, a->n_cell, a->n_part);
-    if (e || (e = mark(c, a, 2))) return e;
-    if (a->offsets) {
-        e = p3t_neighbours_async(c, a->offsets, a->idx, a->capacity, a->total);
-        if (e) return e;
+    // the far force and the lists, in the order asked for
+    for (int ph = 0; ph < 2; ph++) {
+        if ((ph == 0) == (a->lists_first == 0)) {
+            e = p3t_far_force(c, a->ax, a->ay, a->az, a->pot, a->n_cell, a->n_part);
+        } else if (a->offsets) {
+            e = p3t_neighbours_async(c, a->offsets, a->idx, a->capacity, a->total);
+        }
+        if (e || (e = mark(c, a, 2 + ph))) return e;
     }
-    if ((e = mark(c, a, 3))) return e;
     if (a->vx) {
         e = p3t_kick(c, a->kick_dt, a->ax, a->ay, a->az, a->vx, a->vy, a->vz);
         if (e) return e;
@@ -68,6 +70,7 @@ int p3t_graph_capture(p3t_ctx *c, const p3t_step_args *a, p3t_graph **out)
     if (a->drift_dt != 0.0 && (!kick || !std::isfinite(a->drift_dt))) return P3T_ERR_INVALID_ARG;
     if (a->offsets && (!a->total || a->capacity < 0 || (a->capacity > 0 && !a->idx)))
         return P3T_ERR_INVALID_ARG;
+    if (a->lists_first != 0 && a->lists_first != 1) return P3T_ERR_INVALID_ARG;
     // scratch first: nothing may allocate while the stream is being captured
     int e = reserve(c, a->n, a->n_clusters);
     if (e) return e;
