@@ -212,7 +212,7 @@ class Slot:
 
     STAGING_BYTES_PER_PARTICLE = 7 * 8 + 3 * 4 + 8  # state, accelerations, row offsets (+ entries)
 
-    def __init__(self, index, params, budget, max_clusters, nbr_cap, dt, device):
+    def __init__(self, index, params, budget, max_clusters, nbr_cap, dt, device, lists_first=True):
         import torch
 
         import paper_2110_11658_b300 as p3t
@@ -243,6 +243,9 @@ class Slot:
         self.done = torch.cuda.Event()
         self.batch = None
         self.sized = False  # the first batch's lists are synchronous: they size the row scratch
+        # the lists before the far force: their own count pass, then a force-only walk
+        # (faster for the short rows of the paper's r_cut; the same results)
+        self.lists_first = lists_first
 
     def launch(self, arena: Arena, batch: Batch):
         import numpy as np
@@ -273,12 +276,14 @@ class Slot:
         a = [v[:nb] for v in self.acc]
         ctx = self.ctx
         ctx.build_tree_batch(boff_d, st["x"], st["y"], st["z"], st["m"], cluster_params=self.d_prm[:c])
-        ctx.far_force(*a)
+        if not self.lists_first:
+            ctx.far_force(*a)
         if self.sized:
             ctx.neighbours_async(self.offs[:nb + 1], self.idx, self.tot)
         else:
             # once per slot (a host sync): sizes the row scratch, so that the
-            # following batches' walks write the neighbour rows (row mode)
+            # following batches' passes that count the neighbours also write their
+            # rows (row mode)
             try:
                 total = ctx.neighbours(self.offs[:nb + 1], self.idx)
             except p3t.P3TError as e:  # reported by the scatter's status, as in the async form
@@ -288,6 +293,8 @@ class Slot:
             with torch.cuda.stream(s):
                 self.tot.fill_(total)
             self.sized = True
+        if self.lists_first:
+            ctx.far_force(*a)
         ctx.kick(self.dt, *a, st["vx"], st["vy"], st["vz"])
         ctx.drift(self.dt, st["x"], st["y"], st["z"], st["vx"], st["vy"], st["vz"])
         back = [(arena.state[k], self.st[k]) for k in ("x", "y", "z", "vx", "vy", "vz")]
@@ -326,7 +333,8 @@ class Server:
 
     def __init__(self, arena: Arena, n_slots: int = 2, budget: int | None = None, max_clusters: int = 256,
                  nbr_cap: int = 16, dt: float = 1.0 / 512, leaf_cap: int = 16, group_size: int = 32,
-                 tile: int = 64, hbm_budget: int | None = None, batch_factor: float = 8.0):
+                 tile: int = 64, hbm_budget: int | None = None, batch_factor: float = 8.0,
+                 lists_first: bool = True):
         import paper_2110_11658_b300 as p3t
         self.arena = arena
         prm = p3t.Params(theta=float(arena.params[0, 0]), r_in=float(arena.params[0, 1]),
@@ -345,7 +353,8 @@ class Server:
         self.bytes_per_slot = int(per_particle * budget)
         self.sched = Scheduler(arena.sizes, n_slots, budget, max_clusters)
         arena.torch.cuda.synchronize(arena.device)  # the arena was filled on another stream
-        self.slots = [Slot(i, prm, budget, max_clusters, nbr_cap, dt, arena.device) for i in range(n_slots)]
+        self.slots = [Slot(i, prm, budget, max_clusters, nbr_cap, dt, arena.device, lists_first)
+                      for i in range(n_slots)]
         self.batches = []
 
     def close(self):
