@@ -647,8 +647,12 @@ __global__ void __launch_bounds__(kBuildThreads) group_frames_kernel(Tree T)
 // (the FP32 exponent and two mantissa bits of its longest side), smallest first.
 // Small boxes hold the densest groups, which carry the most particle terms, so
 // the persistent walk starts them first and its tail holds light groups.  Inside
-// a bin the order is arbitrary; no result depends on it (groups are independent).
+// a bin the groups keep their key order (a stable counting sort over chunks of
+// kOrderChunk groups), so that the groups walked at the same time lie close
+// together and share node records and sources in L2.  No result depends on the
+// order (groups are independent).
 constexpr int kGroupBins = 256;
+constexpr int kOrderChunk = 1024;  // groups of one block's chunk, 4 per thread
 __device__ __forceinline__ int group_bin(const Tree &T, int g)
 {
     const float4 g1 = T.gfr[3 * (size_t)g + 1], g2 = T.gfr[3 * (size_t)g + 2];
@@ -657,52 +661,59 @@ __device__ __forceinline__ int group_bin(const Tree &T, int g)
     return min(max(b, 0), kGroupBins - 1);
 }
 
-__global__ void __launch_bounds__(kBuildThreads) group_bins_kernel(Tree T)
+// bin counts of every chunk: hist[bin * nchunks + chunk] (one block per chunk; chunks
+// past the groups count nothing)
+__global__ void __launch_bounds__(kBuildThreads) group_bins_kernel(Tree T, int32_t *hist, int nchunks)
 {
+    static_assert(kBuildThreads == kGroupBins, "one thread per bin");
     __shared__ int cnt[kGroupBins];
-    for (int b = threadIdx.x; b < kGroupBins; b += blockDim.x) cnt[b] = 0;
+    cnt[threadIdx.x] = 0;
     __syncthreads();
     const int ng = T.meta->n_groups;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+    const int g0 = blockIdx.x * kOrderChunk;
+    for (int g = g0 + threadIdx.x; g < min(ng, g0 + kOrderChunk); g += kBuildThreads)
         atomicAdd(&cnt[group_bin(T, g)], 1);
     __syncthreads();
-    for (int b = threadIdx.x; b < kGroupBins; b += blockDim.x)
-        if (cnt[b]) atomicAdd(&T.gbins[b], cnt[b]);
+    hist[threadIdx.x * nchunks + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// exclusive scan of the bin counts into the cursors (one block of kGroupBins threads)
-__global__ void __launch_bounds__(kGroupBins) group_bins_scan_kernel(Tree T)
+// stable placement: a chunk's groups of one bin go to that bin's offset for the chunk
+// (hist, scanned bin-major), in the order of their index
+__global__ void __launch_bounds__(kBuildThreads)
+    group_order_kernel(Tree T, const int32_t *__restrict__ hist, int nchunks)
 {
-    __shared__ int sh[kGroupBins];
-    const int b = threadIdx.x;
-    sh[b] = T.gbins[b];
-    __syncthreads();
-    for (int o = 1; o < kGroupBins; o <<= 1) {
-        const int v = b >= o ? sh[b - o] : 0;
-        __syncthreads();
-        sh[b] += v;
-        __syncthreads();
-    }
-    T.gbins[kGroupBins + b] = sh[b] - T.gbins[b];
-}
-
-// one slot per group: ranks inside a block's chunk from shared counters, one
-// global reservation per (chunk, bin)
-__global__ void __launch_bounds__(kBuildThreads) group_order_kernel(Tree T)
-{
-    __shared__ int cnt[kGroupBins], base[kGroupBins];
+    constexpr int W = kBuildThreads / 32;
+    __shared__ int base[kGroupBins];
+    __shared__ int wcnt[W][kGroupBins];
+    __shared__ int pofs[W][kGroupBins];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
     const int ng = T.meta->n_groups;
-    for (int g0 = blockIdx.x * blockDim.x; g0 < ng; g0 += gridDim.x * blockDim.x) {
-        for (int b = threadIdx.x; b < kGroupBins; b += blockDim.x) cnt[b] = 0;
+    base[tid] = hist[tid * nchunks + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < W; w++) wcnt[w][tid] = 0;
+    __syncthreads();
+#pragma unroll 1
+    for (int r = 0; r < kOrderChunk / kBuildThreads; r++) {
+        const int g = blockIdx.x * kOrderChunk + r * kBuildThreads + tid;
+        const bool valid = g < ng;
+        const int bin = valid ? group_bin(T, g) : kGroupBins;  // (kGroupBins: no group)
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        const int wrank = __popc(peers & lt);
+        if (valid && wrank == 0) wcnt[warp][bin] = __popc(peers);
         __syncthreads();
-        const int g = g0 + threadIdx.x;
-        const int bin = g < ng ? group_bin(T, g) : -1;
-        const int rank = bin >= 0 ? atomicAdd(&cnt[bin], 1) : 0;
+        {
+            int s = base[tid];
+#pragma unroll
+            for (int w = 0; w < W; w++) {
+                pofs[w][tid] = s;
+                s += wcnt[w][tid];
+                wcnt[w][tid] = 0;
+            }
+            base[tid] = s;
+        }
         __syncthreads();
-        for (int b = threadIdx.x; b < kGroupBins; b += blockDim.x)
-            if (cnt[b]) base[b] = atomicAdd(&T.gbins[kGroupBins + b], cnt[b]);
-        __syncthreads();
-        if (bin >= 0) T.gorder[base[bin] + rank] = g;
+        if (valid) T.gorder[pofs[warp][bin] + wrank] = g;
         __syncthreads();
     }
 }
@@ -1052,13 +1063,14 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     group_first_kernel<<<grid_n, kBuildThreads, 0, gs>>>(n, T.gflag, T.gidx, T.grp);
     group_finish_kernel<<<persistent, kBuildThreads, 0, gs>>>(T, n);
     group_frames_kernel<<<persistent, kBuildThreads, 0, gs>>>(T);
-    if (cudaMemsetAsync(T.gbins, 0, sizeof(int32_t) * 2 * kGroupBins, gs) != cudaSuccess)
-        return P3T_ERR_CUDA;
-    // few blocks: the bins take one global atomic per block and bin
-    const int order_grid = std::min(64, persistent);
-    group_bins_kernel<<<order_grid, kBuildThreads, 0, gs>>>(T);
-    group_bins_scan_kernel<<<1, kGroupBins, 0, gs>>>(T);
-    group_order_kernel<<<order_grid, kBuildThreads, 0, gs>>>(T);
+    // the walk order: a stable counting sort of the groups by box size (chunks sized
+    // for the largest group count, n; the sort's histogram and scan buffers, free now)
+    const int nchunks = (n + kOrderChunk - 1) / kOrderChunk;
+    group_bins_kernel<<<nchunks, kBuildThreads, 0, gs>>>(T, c->sort_hist, nchunks);
+    if ((e = scan_excl_i32_to_i32(c->sort_hist, c->sort_hist, kGroupBins * nchunks, c->scan_status,
+                                  &M->tickets[31], M, gs)))
+        return e;
+    group_order_kernel<<<nchunks, kBuildThreads, 0, gs>>>(T, c->sort_hist, nchunks);
     if (fork && cudaEventRecord(c->join_ev, gs) != cudaSuccess) return P3T_ERR_CUDA;
 
     // moments: leaves, then levels 20 .. 0 (a level without internal nodes exits at once)

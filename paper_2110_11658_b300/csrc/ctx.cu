@@ -64,7 +64,6 @@ static size_t scratch_plan(p3t_ctx *c, long long N, int L, char *base)
     put(&T.ghi, 32 * (size_t)N);
     put(&T.gfr, 48 * (size_t)N);
     put(&T.gorder, 4 * (size_t)N);
-    put(&T.gbins, 4 * 512);
     put(&c->nbr_count, 4 * (size_t)N);
     put(&c->row_list, 4 * (size_t)N);
     put(&c->rid_buf, 4 * (size_t)N);

@@ -142,7 +142,6 @@ struct Tree {
     // split of c_g - O {hx hy hz lx} {ly lz, box lo - O: x y} {z, box hi - O: x y z}
     float4 *gfr;
     int32_t *gorder;       // the walks' order of the groups (smallest boxes first)
-    int32_t *gbins;        // 2 x 256: group counts by box size, then cursors
     unsigned char *gflag;  // group-start flags, particle order
     int32_t *gidx;         // scan of gflag
     int32_t *leaves;       // leaf node indices, in creation order (moments work list)
