@@ -37,8 +37,13 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def _compile(src: str) -> str:
+def _compile(src: str, force: bool = False) -> str:
     obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+    # an object newer than its source and every header is reused
+    headers = [p for p in _deps() if not p.endswith(".cu")]
+    if not force and os.path.exists(obj) and all(os.path.getmtime(p) <= os.path.getmtime(obj)
+                                                 for p in [src] + headers):
+        return obj
     cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -52,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(_compile, srcs))
+        objs = list(ex.map(lambda src: _compile(src, force), srcs))
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [NVCC, *ARCH, "-shared", *objs, "-o", tmp]  # cudart linked statically
     r = subprocess.run(cmd, capture_output=True, text=True)

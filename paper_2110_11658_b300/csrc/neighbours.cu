@@ -47,8 +47,10 @@ struct NbrSmem {
     int stk[kNbrStack];
     int2 lq[kNbrLeafQ];
     int lqo[kNbrLeafQ + 1];
-    float4 pp[32];  // 16 pairs of staged sources (pair layout)
-    int pj[32];     // their positions in key order
+    // staged sources in the pair layout: slots [0, 32) are tested as one chunk of
+    // 16 pairs, [32, 64) take what a candidate chunk adds beyond 32
+    float4 pp[64];
+    int pj[64];  // their positions in key order
 };
 
 template <int TPL, bool FILL, bool ROWS = false>
@@ -160,6 +162,15 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         const float in_hi = pair_filter ? rl2_f + tpair : INFINITY;
         // |r2 - in_mid| <= in_rad covers [in_lo, in_hi] with a 2x margin (infinite: filter off)
         const float in_mid = 0.5f * in_lo + 0.5f * in_hi, in_rad = in_hi - in_lo;
+        // Source filter: a source whose distance to the group box is r_list or more
+        // (with a margin) is nobody's neighbour and is not staged.  The box relative
+        // to c_g and the source offsets carry at most ~8 u R error per coordinate
+        // (u = 2^-24), so d > r_list (1 + 1e-5) + 32 u R in FP32 implies an exact
+        // distance above r_list, far outside the FP64 test's rounding.
+        const float bxl = (glx - fhx) - flx, byl = (gly - fhy) - fly, bzl = (glz - fhz) - flz;
+        const float bxh = (ghx - fhx) - flx, byh = (ghy - fhy) - fly, bzh = (ghz - fhz) - flz;
+        const float thr = rl_f * 1.00001f + 32.f * kUn * Rf;
+        const float src_thr2 = pair_filter ? thr * thr : INFINITY;
         float2 NPX[TPL], NPY[TPL], NPZ[TPL];
 #pragma unroll
         for (int t = 0; t < TPL; t++)
@@ -217,7 +228,32 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
         int sp = 1;
         if (lane == 0) W.stk[0] = pack_range(cid, 1);
         __syncwarp();
+        // the staged sources [0, ns) against the targets (ns <= 32; an odd ns is padded
+        // by the caller), then, in row mode, their neighbours appended to the rows
+        auto test_chunk = [&](int ns) {
+            const int nfull = ns >> 1;
+#pragma unroll 2
+            for (int k = 0; k < nfull; k++) test_pair(k, ns, std::false_type());
+            if (ns & 1) test_pair(nfull, ns, std::true_type());
+            if (ROWS) {  // count the chunk's neighbours and append them to the rows
+                const int *po = reinterpret_cast<const int *>(W.pp);
+#pragma unroll
+                for (int t = 0; t < TPL; t++) {
+                    unsigned h = hit[t];
+                    hit[t] = 0u;
+                    cnt[t] += __popc(h);
+                    while (h) {
+                        const int b = __ffs(h) - 1;
+                        h &= h - 1u;
+                        if (rwc[t] < rcap[t]) rrow[t][rwc[t]] = po[8 * (b >> 1) + 6 + (b & 1)];
+                        rwc[t]++;
+                    }
+                }
+            }
+            __syncwarp();
+        };
         int lqn = 0, lqp = 0;
+        int nst = 0;  // staged sources waiting for a full chunk (< 32 between chunks)
         int iters = 0;  // a valid walk pops every node at most once
         while (true) {
             if (++iters > nn + 2) {
@@ -272,70 +308,82 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 lqp += (int)__reduce_add_sync(0xffffffffu, open_leaf ? (unsigned)ccount : 0u);
                 if (lqp < 64 && sp > 0) continue;
             }
-            if (lqp == 0) break;
-            // ---- test the targets against the queued leaves' particles
-            __syncwarp();
-            {
-                int carry = 0;
-                for (int b0 = 0; b0 < lqn; b0 += 32) {
-                    int i = b0 + lane;
-                    int v = i < lqn ? W.lq[i].y : 0;
-                    int inc = warp_incl_scan(v);
-                    if (i < lqn) W.lqo[i] = carry + inc - v;
-                    carry += __shfl_sync(0xffffffffu, inc, 31);
-                }
-            }
-            __syncwarp();
-            for (int c0 = 0; c0 < lqp; c0 += 32) {
-                int pos = c0 + lane;
-                if (pos < lqp) {
-                    int lo = 0, hi = lqn;
-                    while (hi - lo > 1) {
-                        int mid = (lo + hi) >> 1;
-                        if (W.lqo[mid] <= pos)
-                            lo = mid;
-                        else
-                            hi = mid;
+            if (lqp > 0) {
+                // ---- stage the queued leaves' particles that pass the source filter
+                __syncwarp();
+                {
+                    int carry = 0;
+                    for (int b0 = 0; b0 < lqn; b0 += 32) {
+                        int i = b0 + lane;
+                        int v = i < lqn ? W.lq[i].y : 0;
+                        int inc = warp_incl_scan(v);
+                        if (i < lqn) W.lqo[i] = carry + inc - v;
+                        carry += __shfl_sync(0xffffffffu, inc, 31);
                     }
-                    int j = W.lq[lo].x + (pos - W.lqo[lo]);
-                    const float4 h = T.ph[j], l = T.pl[j];
-                    pb[0] = (h.x - fhx) + (l.x - flx);
-                    pb[2] = (h.y - fhy) + (l.y - fly);
-                    pb[4] = (h.z - fhz) + (l.z - flz);
-                    pb[6] = __int_as_float(T.rid[j]);
-                    W.pj[lane] = j;
                 }
                 __syncwarp();
-                const int ns = min(32, lqp - c0);
-                if ((ns & 1) && lane == 0) {  // pad: far away, never a neighbour
-                    float *b = reinterpret_cast<float *>(W.pp) + 8 * (ns >> 1);
-                    b[1] = b[3] = b[5] = 1e30f;
-                    b[7] = __int_as_float(-1);
-                }
-                __syncwarp();
-                const int nfull = ns >> 1;
-#pragma unroll 2
-                for (int k = 0; k < nfull; k++) test_pair(k, ns, std::false_type());
-                if (ns & 1) test_pair(nfull, ns, std::true_type());
-                if (ROWS) {  // count the chunk's neighbours and append them to the rows
-                    const int *po = reinterpret_cast<const int *>(W.pp);
-#pragma unroll
-                    for (int t = 0; t < TPL; t++) {
-                        unsigned h = hit[t];
-                        hit[t] = 0u;
-                        cnt[t] += __popc(h);
-                        while (h) {
-                            const int b = __ffs(h) - 1;
-                            h &= h - 1u;
-                            if (rwc[t] < rcap[t]) rrow[t][rwc[t]] = po[8 * (b >> 1) + 6 + (b & 1)];
-                            rwc[t]++;
+                for (int c0 = 0; c0 < lqp; c0 += 32) {
+                    const int pos = c0 + lane;
+                    bool keep = false;
+                    float rx = 0.f, ry = 0.f, rz = 0.f;
+                    int j = 0;
+                    if (pos < lqp) {
+                        int lo = 0, hi = lqn;
+                        while (hi - lo > 1) {
+                            int mid = (lo + hi) >> 1;
+                            if (W.lqo[mid] <= pos)
+                                lo = mid;
+                            else
+                                hi = mid;
                         }
+                        j = W.lq[lo].x + (pos - W.lqo[lo]);
+                        const float4 h = T.ph[j], l = T.pl[j];
+                        rx = (h.x - fhx) + (l.x - flx);
+                        ry = (h.y - fhy) + (l.y - fly);
+                        rz = (h.z - fhz) + (l.z - flz);
+                        const float tx = fmaxf(fmaxf(bxl - rx, rx - bxh), 0.f);
+                        const float ty = fmaxf(fmaxf(byl - ry, ry - byh), 0.f);
+                        const float tz = fmaxf(fmaxf(bzl - rz, rz - bzh), 0.f);
+                        keep = !(tx * tx + ty * ty + tz * tz > src_thr2);
+                    }
+                    const unsigned km = __ballot_sync(0xffffffffu, keep);
+                    if (keep) {
+                        const int sl = nst + __popc(km & lt);  // < 64
+                        float *b = reinterpret_cast<float *>(W.pp) + 8 * (sl >> 1) + (sl & 1);
+                        b[0] = rx, b[2] = ry, b[4] = rz, b[6] = __int_as_float(T.rid[j]);
+                        W.pj[sl] = j;
+                    }
+                    nst += __popc(km);
+                    if (nst >= 32) {
+                        __syncwarp();
+                        test_chunk(32);
+                        // the staged sources beyond the chunk move down to slots [0, nst - 32)
+                        const int rem = nst - 32;
+                        if (lane < rem) {
+                            const float *src = reinterpret_cast<const float *>(W.pp) + 8 * ((32 + lane) >> 1) + (lane & 1);
+                            float *dst = reinterpret_cast<float *>(W.pp) + 8 * (lane >> 1) + (lane & 1);
+                            const float v0 = src[0], v1 = src[2], v2 = src[4], v3 = src[6];
+                            const int pjv = W.pj[32 + lane];
+                            dst[0] = v0, dst[2] = v1, dst[4] = v2, dst[6] = v3;
+                            W.pj[lane] = pjv;
+                        }
+                        __syncwarp();
+                        nst = rem;
                     }
                 }
-                __syncwarp();
+                lqn = lqp = 0;
             }
-            lqn = lqp = 0;
             if (sp == 0) break;
+        }
+        if (nst > 0) {  // the last staged sources
+            __syncwarp();
+            if ((nst & 1) && lane == 0) {  // pad: far away, never a neighbour
+                float *b = reinterpret_cast<float *>(W.pp) + 8 * (nst >> 1);
+                b[1] = b[3] = b[5] = 1e30f;
+                b[7] = __int_as_float(-1);
+            }
+            __syncwarp();
+            test_chunk(nst);
         }
         if (!FILL) {
 #pragma unroll

@@ -99,6 +99,7 @@ struct Meta {
     int uncounted;                 // clusters whose neighbours the mixed walk does not count
     int row_over;                  // row mode: a row outgrew its room since the rows were laid out
     long long spin_limit;          // polls of a bounded wait (0: kSpinLimit)
+    int cell_forms[2];             // clusters whose groups take the r^-5 / the r^-3 cell term
 };
 
 // ---- one cluster of a (possibly batched) build -----------------------------------
@@ -112,6 +113,7 @@ struct Cluster {
     double rout2_d, rl2_d, inv_dr_d;        // r_out^2, r_list^2, 1/(r_out - r_in)
     float rout2_f, rl2_f, rl_f, inv_dr_f, rin_dr_f;
     int counted;                   // 1: the mixed far-force walk counts its neighbours
+    int fast_cells;                // 1: the r^-5 cell term stays in the FP32 range (walk)
 };
 
 // ---- tree view passed by value to kernels ------------------------------------

@@ -1,21 +1,36 @@
 // Far-force entry (p3t_far_force): picks the walk variant of walk_kernel.cuh for
-// the context's precision, parameters and neighbour state.  Walks with one warp per
-// group are instantiated here, those with 2 and 4 warps per group in walk_wpg.cu.
+// the context's precision, parameters and neighbour state.  The FP64 walk with one
+// warp per group is instantiated here, the mixed walks in walk_f1.cu / walk_f2.cu
+// (the two cell forms) and those with 2 and 4 warps per group in walk_wpg*.cu.
 #include "walk_kernel.cuh"
 
 namespace p3t {
 
-extern template int dispatch_walk_wpg<2>(p3t_ctx *, const WalkArgs &, bool, int, bool, bool, bool);
-extern template int dispatch_walk_wpg<4>(p3t_ctx *, const WalkArgs &, bool, int, bool, bool, bool);
-
-template <typename Real, int NBR, bool SHELL = false>
-static int dispatch_tpl(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
+// Which clusters may take the r^-5 cell term (eval_cells_x2): r_out >= 1e-7, frame
+// half-size R <= 1e6 and cluster mass (the root record's) <= 1e15, all finite.  One
+// block; the counts of both kinds go to Meta.cell_forms: the r^-5 walk runs when no
+// cluster is outside that range, the r^-3 walk otherwise (for every cluster, so that
+// the form is one per launch).
+__global__ void __launch_bounds__(256) cell_forms_kernel(Tree T)
 {
-    const int G = c->prm.group_size;
-    if constexpr (NBR == 2) return dispatch_pq<Real, 1, 2, SHELL, 1>(c, a, pot, quad);  // G <= 32
-    if (G <= 32) return dispatch_pq<Real, 1, NBR, SHELL, 1>(c, a, pot, quad);
-    if (G <= 64) return dispatch_pq<Real, 2, NBR, SHELL, 1>(c, a, pot, quad);
-    return dispatch_pq<Real, 4, NBR, SHELL, 1>(c, a, pot, quad);
+    __shared__ int cnt[2];
+    if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int nf = 0, ns = 0;
+    for (int c = threadIdx.x; c < T.n_clusters; c += blockDim.x) {
+        Cluster &K = T.cl[c];
+        const float R = (float)K.frame[3];
+        const float M = T.wn[wrec(c, 3)].w;
+        const bool fast = K.rout2_f >= 1e-14f && K.rout2_f < 1e30f && R >= 0.f && R <= 1e6f &&
+                          M >= 0.f && M <= 1e15f;
+        K.fast_cells = fast;
+        nf += fast;
+        ns += !fast;
+    }
+    if (nf) atomicAdd(&cnt[0], nf);
+    if (ns) atomicAdd(&cnt[1], ns);
+    __syncthreads();
+    if (threadIdx.x < 2) T.meta->cell_forms[threadIdx.x] = cnt[threadIdx.x];
 }
 
 int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc, int64_t *np)
@@ -55,21 +70,25 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     // neighbour-only ranges are needed when a list radius exceeds r_out (with a
     // per-cluster table the host cannot tell, so they are compiled in)
     const bool shell = fuse_nbr && (!c->uniform_params || P.r_list > P.r_out);
-    if (wpg > 1) {
-        const bool fp64 = c->built_precision == P3T_FP64;
-        const int nbr = fp64 || !fuse_nbr ? 0 : (rows ? 2 : 1);
-        e = wpg == 2 ? dispatch_walk_wpg<2>(c, a, fp64, nbr, shell, want_pot, quad)
-                     : dispatch_walk_wpg<4>(c, a, fp64, nbr, shell, want_pot, quad);
-    } else if (c->built_precision == P3T_FP64)
-        e = dispatch_tpl<double, 0>(c, a, want_pot, quad);
-    else if (shell)
-        e = rows ? dispatch_tpl<float, 2, true>(c, a, want_pot, quad)
-                 : dispatch_tpl<float, 1, true>(c, a, want_pot, quad);
-    else if (fuse_nbr)
-        e = rows ? dispatch_tpl<float, 2>(c, a, want_pot, quad)
-                 : dispatch_tpl<float, 1>(c, a, want_pot, quad);
-    else
-        e = dispatch_tpl<float, 0>(c, a, want_pot, quad);
+    if (c->built_precision == P3T_FP64) {
+        e = wpg == 1 ? dispatch_tpl<double, 0, false, 0>(c, a, want_pot, quad)
+                     : (wpg == 2 ? dispatch_walk_wpg<2, 0>(c, a, 0, false, want_pot, quad)
+                                 : dispatch_walk_wpg<4, 0>(c, a, 0, false, want_pot, quad));
+    } else {
+        // the r^-5 walk, then the r^-3 walk: one of the two finds its form chosen
+        // (cell_forms_kernel) and walks every group, the other returns at once
+        const int nbr = !fuse_nbr ? 0 : (rows ? 2 : 1);
+        cell_forms_kernel<<<1, 256, 0, c->stream>>>(c->tree);
+        e = check_launch(c);
+        if (!e) e = mixed_walk<1>(c, a, wpg, nbr, shell, want_pot, quad);
+        if (!e) {
+            WalkArgs b = a;
+            b.ticket = &c->meta->tickets[24];
+            e = cudaMemsetAsync(b.ticket, 0, sizeof(unsigned int), c->stream) == cudaSuccess
+                    ? mixed_walk<2>(c, b, wpg, nbr, shell, want_pot, quad)
+                    : P3T_ERR_CUDA;
+        }
+    }
     if (e == P3T_OK && fuse_nbr) {
         c->walk_counted = 1;
         c->rows_valid = rows;

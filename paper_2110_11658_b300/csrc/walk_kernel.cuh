@@ -51,7 +51,10 @@ namespace p3t {
 constexpr int kWalkWarps = 4;                // warps per block
 constexpr int kStackCap = 32 * 22 + 64;      // ranges per warp; see the bound below
 constexpr float kU = 5.9604644775390625e-8f;  // 2^-24, FP32 unit round-off
-constexpr int kCellPairUnroll = 2;           // pairs of cells per unrolled iteration
+// pairs of cells per unrolled iteration: 4 in the force-only walk, 2 where the neighbour
+// state holds registers
+template <int NBR>
+__host__ __device__ constexpr int cell_pair_unroll() { return NBR == 0 ? 4 : 2; }
 constexpr int kPartPairUnroll = 2;           // pairs of particles per unrolled iteration
 constexpr int kMinBlocksTpl1 = 6;            // resident blocks per SM at TPL = 1 (80 registers)
 
@@ -453,7 +456,14 @@ __device__ __forceinline__ void eval_parts(const WarpSmem<Real> &W, const WalkAr
 // Mixed form, two queued cells at a time (layout above); same terms as eval_cells.
 // PAD: pad an odd count here (one warp per group); with several warps per group the
 // walking warp pads the queue once before they all read it.
-template <int TPL, bool POT, bool QUAD, bool PAD>
+// FAST: the quadrupole term as r^-5 [(-M r^2 - 5/2 (r.Q.r)/r^2) r + Q r], one packed
+// operation fewer per pair of cells than the r^-3 form below.  r^-5 and the products
+// stay inside the FP32 range (no overflow, no flush to zero) for r_out >= 1e-7, a
+// frame half-size R <= 1e6 and a cluster mass <= 1e15, which the walk checks per
+// group (every accepted cell lies at r >= r_out from each target of the group, and
+// r <= 2 sqrt(3) R); otherwise the r^-3 form runs, which keeps every intermediate
+// within r^-3.
+template <int TPL, bool POT, bool QUAD, bool PAD, int UNROLL, bool FAST>
 __device__ __forceinline__ void eval_cells_x2(const WarpSmem<float> &W, int ncells, const float (&px)[TPL],
                                               const float (&py)[TPL], const float (&pz)[TPL],
                                               AccX2<TPL> &A)
@@ -471,7 +481,7 @@ __device__ __forceinline__ void eval_cells_x2(const WarpSmem<float> &W, int ncel
 #pragma unroll
     for (int t = 0; t < TPL; t++) PX[t] = f2(px[t]), PY[t] = f2(py[t]), PZ[t] = f2(pz[t]);
     const int npairs = (ncells + 1) >> 1;
-#pragma unroll kCellPairUnroll
+#pragma unroll UNROLL
     for (int k = 0; k < npairs; k++) {
         const float4 a0 = cq[5 * k], a1 = cq[5 * k + 1];
         const float2 NX = make_float2(a0.x, a0.y), NY = make_float2(a0.z, a0.w);
@@ -493,7 +503,21 @@ __device__ __forceinline__ void eval_cells_x2(const WarpSmem<float> &W, int ncel
             const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
             const float2 q = fmul2(ri, ri);
             const float2 ri3 = fmul2(ri, q);
-            if (QUAD) {
+            if (QUAD && FAST) {
+                float2 qx = fmul2(Qxx, rx), qy = fmul2(Qxy, rx), qz = fmul2(Qxz, rx);
+                qx = ffma2(Qxy, ry, qx), qy = ffma2(Qyy, ry, qy), qz = ffma2(Qyz, ry, qz);
+                qx = ffma2(Qxz, rz, qx), qy = ffma2(Qyz, rz, qy), qz = ffma2(Qzz, rz, qz);
+                float2 rqr = fmul2(rx, qx);
+                rqr = ffma2(ry, qy, rqr);
+                rqr = ffma2(rz, qz, rqr);
+                const float2 w = fmul2(rqr, q);                         // r.Q.r / r^2
+                const float2 sc = ffma2(NM, r2, fmul2(f2(-2.5f), w));  // -M r^2 - 5/2 r.Q.r / r^2
+                const float2 ri5 = fmul2(ri3, q);
+                A.p[t][0] = ffma2(ri5, ffma2(sc, rx, qx), A.p[t][0]);
+                A.p[t][1] = ffma2(ri5, ffma2(sc, ry, qy), A.p[t][1]);
+                A.p[t][2] = ffma2(ri5, ffma2(sc, rz, qz), A.p[t][2]);
+                if (POT) A.p[t][3] = ffma2(ri, ffma2(f2(-0.5f), fmul2(w, q), NM), A.p[t][3]);
+            } else if (QUAD) {
                 float2 qx = fmul2(Qxx, rx), qy = fmul2(Qxy, rx), qz = fmul2(Qxz, rx);
                 qx = ffma2(Qxy, ry, qx), qy = ffma2(Qyy, ry, qy), qz = ffma2(Qyz, ry, qz);
                 qx = ffma2(Qxz, rz, qx), qy = ffma2(Qyz, rz, qy), qz = ffma2(Qzz, rz, qz);
@@ -761,14 +785,15 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
 }
 
 // the mixed form evaluates pairs of sources, the FP64 form one at a time
-template <typename Real, int TPL, bool POT, bool QUAD, bool PAD, typename AccT>
+template <typename Real, int TPL, bool POT, bool QUAD, bool PAD, int NBR, bool FAST, typename AccT>
 __device__ __forceinline__ void eval_cells_any(const WarpSmem<Real> &W, int ncells, const Real (&px)[TPL],
                                                const Real (&py)[TPL], const Real (&pz)[TPL], AccT &A)
 {
-    if constexpr (sizeof(Real) == 4)
-        eval_cells_x2<TPL, POT, QUAD, PAD>(W, ncells, px, py, pz, A);
-    else
+    if constexpr (sizeof(Real) == 4) {
+        eval_cells_x2<TPL, POT, QUAD, PAD, cell_pair_unroll<NBR>(), FAST>(W, ncells, px, py, pz, A);
+    } else {
         eval_cells<Real, TPL, POT, QUAD>(W, ncells, px, py, pz, A);
+    }
 }
 
 template <typename Real, int TPL, bool POT, int NBR, bool SHELL, typename AccT>
@@ -812,12 +837,16 @@ constexpr int walk_block_threads()
 // Every warp executes the same sequence of barriers: the round loop ends on the
 // flag the walking warp writes before a round's first barrier and nobody changes
 // before its second.
-template <typename Real, int TPL, bool POT, bool QUAD, int NBR, bool SHELL, int WPG>
+// FORM: 0 the FP64 form; a mixed walk is launched twice, 1 with the r^-5 cell term,
+// which does the work when every cluster of the tree fits that form (fast_cells),
+// and 2 with the r^-3 term, which does it otherwise; the other launch returns at once.
+template <typename Real, int TPL, bool POT, bool QUAD, int NBR, bool SHELL, int WPG, int FORM = 0>
 __global__ void __launch_bounds__(walk_block_threads<WPG>(),
                                   TPL == 1 ? kMinBlocksTpl1 * kWalkWarps / (WPG == 1 ? kWalkWarps : WPG) : 3)
     walk_kernel(WalkArgs P)
 {
     static_assert(WPG == 1 || TPL == 1, "several warps per group hold one target per lane");
+    static_assert(FORM == 0 || sizeof(Real) == 4, "cell forms: mixed walks");
     extern __shared__ __align__(16) char smem[];
     using R4 = typename Vec4<Real>::T;
     using R2 = typename Vec4<Real>::T2;
@@ -841,6 +870,8 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
     const int ng = meta->n_groups;
     const int nn = meta->n_nodes;
     const int tile = P.tile;
+    // the r^-5 launch runs when every cluster fits that form, the r^-3 launch otherwise
+    if (FORM != 0 && (meta->cell_forms[1] == 0) != (FORM == 1)) return;
 
     while (true) {
         int g = 0;
@@ -871,6 +902,9 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
         const float rout2_f = K.rout2_f;
         const double rout2_d = K.rout2_d;
         const bool filter_ok = Rf > 1e-6f && Rf < 1e12f && rout2_f > 1e-20f && rout2_f < 1e30f;
+        // FORM 1 / 2: this launch takes only the groups of clusters whose cell term
+        // stays / does not stay in the FP32 range in the r^-5 form (cell_forms_kernel)
+        constexpr bool fast_cells = kMixed && FORM == 1;
         const bool count_here = NBR && K.counted;
         const bool shell = SHELL && count_here && K.rl2_d > rout2_d;  // neighbours beyond r_out
         const float rl2_f = K.rl2_f;
@@ -1157,7 +1191,7 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
             while (sp > 0) {
                 if (!walk_batch()) break;
                 if (cb >= tile) {
-                    eval_cells_any<Real, TPL, POT, QUAD, true>(W, cb, px, py, pz, A);
+                    eval_cells_any<Real, TPL, POT, QUAD, true, NBR, fast_cells>(W, cb, px, py, pz, A);
                     cb = 0;
                 }
                 if (lqp >= tile) {
@@ -1165,7 +1199,7 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
                     lqn = lqp = 0;
                 }
             }
-            if (cb > 0) eval_cells_any<Real, TPL, POT, QUAD, true>(W, cb, px, py, pz, A);
+            if (cb > 0) eval_cells_any<Real, TPL, POT, QUAD, true, NBR, fast_cells>(W, cb, px, py, pz, A);
             if (lqp > 0) eval_parts_any<Real, TPL, POT, NBR, SHELL>(W, P, K, lqn, lqp, F, px, py, pz, A, NC);
         } else {
             // evaluation rounds: the walking warp fills the queues up to a tile, then
@@ -1206,7 +1240,7 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
 #pragma unroll 1
                 for (int pass = 0; pass < 2; pass++) {  // one call site each (code size)
                     if ((pass == 0) != parts_first) {
-                        if (ec > 0) eval_cells_any<Real, TPL, POT, QUAD, false>(W, ec, px, py, pz, A);
+                        if (ec > 0) eval_cells_any<Real, TPL, POT, QUAD, false, NBR, fast_cells>(W, ec, px, py, pz, A);
                     } else if (ep > 0) {
                         eval_parts_any<Real, TPL, POT, NBR, SHELL>(W, P, K, el, ep, F, px, py, pz, A, NC);
                     }
@@ -1268,10 +1302,10 @@ inline size_t walk_smem_bytes(int tile, bool fp64, int wpg)
     return wpg == 1 ? kWalkWarps * w : wpg * w + sizeof(GroupCtl);
 }
 
-template <typename Real, int TPL, bool POT, bool QUAD, int NBR, bool SHELL, int WPG>
+template <typename Real, int TPL, bool POT, bool QUAD, int NBR, bool SHELL, int WPG, int FORM>
 static int launch_walk(p3t_ctx *c, const WalkArgs &a)
 {
-    auto kern = walk_kernel<Real, TPL, POT, QUAD, NBR, SHELL, WPG>;
+    auto kern = walk_kernel<Real, TPL, POT, QUAD, NBR, SHELL, WPG, FORM>;
     const size_t smem = walk_smem_bytes(a.tile, sizeof(Real) == 8, WPG);
     constexpr int threads = walk_block_threads<WPG>();
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -1285,28 +1319,72 @@ static int launch_walk(p3t_ctx *c, const WalkArgs &a)
     return check_launch(c);
 }
 
-template <typename Real, int TPL, int NBR, bool SHELL, int WPG>
+template <typename Real, int TPL, int NBR, bool SHELL, int WPG, int FORM>
 static int dispatch_pq(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
 {
     if (pot)
-        return quad ? launch_walk<Real, TPL, true, true, NBR, SHELL, WPG>(c, a)
-                    : launch_walk<Real, TPL, true, false, NBR, SHELL, WPG>(c, a);
-    return quad ? launch_walk<Real, TPL, false, true, NBR, SHELL, WPG>(c, a)
-                : launch_walk<Real, TPL, false, false, NBR, SHELL, WPG>(c, a);
+        return quad ? launch_walk<Real, TPL, true, true, NBR, SHELL, WPG, FORM>(c, a)
+                    : launch_walk<Real, TPL, true, false, NBR, SHELL, WPG, FORM>(c, a);
+    return quad ? launch_walk<Real, TPL, false, true, NBR, SHELL, WPG, FORM>(c, a)
+                : launch_walk<Real, TPL, false, false, NBR, SHELL, WPG, FORM>(c, a);
 }
 
 // The variants of one warps-per-group count: precision, neighbour work (0 none,
 // 1 count, 2 count and rows), neighbour-only ranges (shell), potential, quadrupole.
-template <int WPG>
-int dispatch_walk_wpg(p3t_ctx *c, const WalkArgs &a, bool fp64, int nbr, bool shell, bool pot, bool quad)
+// FORM 0 is the FP64 form, 1 and 2 the mixed form's two launches.
+template <int WPG, int FORM>
+int dispatch_walk_wpg(p3t_ctx *c, const WalkArgs &a, int nbr, bool shell, bool pot, bool quad)
 {
-    if (fp64) return dispatch_pq<double, 1, 0, false, WPG>(c, a, pot, quad);
-    if (shell)
-        return nbr == 2 ? dispatch_pq<float, 1, 2, true, WPG>(c, a, pot, quad)
-                        : dispatch_pq<float, 1, 1, true, WPG>(c, a, pot, quad);
-    if (nbr == 2) return dispatch_pq<float, 1, 2, false, WPG>(c, a, pot, quad);
-    if (nbr == 1) return dispatch_pq<float, 1, 1, false, WPG>(c, a, pot, quad);
-    return dispatch_pq<float, 1, 0, false, WPG>(c, a, pot, quad);
+    if constexpr (FORM == 0) {
+        return dispatch_pq<double, 1, 0, false, WPG, 0>(c, a, pot, quad);
+    } else {
+        if (shell)
+            return nbr == 2 ? dispatch_pq<float, 1, 2, true, WPG, FORM>(c, a, pot, quad)
+                            : dispatch_pq<float, 1, 1, true, WPG, FORM>(c, a, pot, quad);
+        if (nbr == 2) return dispatch_pq<float, 1, 2, false, WPG, FORM>(c, a, pot, quad);
+        if (nbr == 1) return dispatch_pq<float, 1, 1, false, WPG, FORM>(c, a, pot, quad);
+        return dispatch_pq<float, 1, 0, false, WPG, FORM>(c, a, pot, quad);
+    }
 }
+
+// One warp per group: TPL targets per lane for groups of up to 32 TPL particles.
+template <typename Real, int NBR, bool SHELL, int FORM>
+int dispatch_tpl(p3t_ctx *c, const WalkArgs &a, bool pot, bool quad)
+{
+    const int G = c->prm.group_size;
+    if constexpr (NBR == 2) return dispatch_pq<Real, 1, 2, SHELL, 1, FORM>(c, a, pot, quad);  // G <= 32
+    if (G <= 32) return dispatch_pq<Real, 1, NBR, SHELL, 1, FORM>(c, a, pot, quad);
+    if (G <= 64) return dispatch_pq<Real, 2, NBR, SHELL, 1, FORM>(c, a, pot, quad);
+    return dispatch_pq<Real, 4, NBR, SHELL, 1, FORM>(c, a, pot, quad);
+}
+
+// One launch of the mixed walk with cell form FORM (1 or 2) for the context's warps per
+// group and neighbour work (0 none, 1 count, 2 count and rows; shell: neighbour-only
+// ranges).  Instantiated in walk_f1.cu and walk_f2.cu, the several-warp variants in
+// walk_wpg.cu, so that the translation units compile in parallel.
+template <int FORM>
+int mixed_walk(p3t_ctx *c, const WalkArgs &a, int wpg, int nbr, bool shell, bool pot, bool quad)
+{
+    if (wpg > 1)
+        return wpg == 2 ? dispatch_walk_wpg<2, FORM>(c, a, nbr, shell, pot, quad)
+                        : dispatch_walk_wpg<4, FORM>(c, a, nbr, shell, pot, quad);
+    if (shell)
+        return nbr == 2 ? dispatch_tpl<float, 2, true, FORM>(c, a, pot, quad)
+                        : dispatch_tpl<float, 1, true, FORM>(c, a, pot, quad);
+    if (nbr == 2) return dispatch_tpl<float, 2, false, FORM>(c, a, pot, quad);
+    if (nbr == 1) return dispatch_tpl<float, 1, false, FORM>(c, a, pot, quad);
+    return dispatch_tpl<float, 0, false, FORM>(c, a, pot, quad);
+}
+
+#define P3T_WPG_DECL(W, F) extern template int dispatch_walk_wpg<W, F>(p3t_ctx *, const WalkArgs &, int, bool, bool, bool);
+P3T_WPG_DECL(2, 0)
+P3T_WPG_DECL(2, 1)
+P3T_WPG_DECL(2, 2)
+P3T_WPG_DECL(4, 0)
+P3T_WPG_DECL(4, 1)
+P3T_WPG_DECL(4, 2)
+#undef P3T_WPG_DECL
+extern template int mixed_walk<1>(p3t_ctx *, const WalkArgs &, int, int, bool, bool, bool);
+extern template int mixed_walk<2>(p3t_ctx *, const WalkArgs &, int, int, bool, bool, bool);
 
 }  // namespace p3t
