@@ -192,15 +192,17 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                 float2 r2 = __fmul2_rn(dx, dx);
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dz, dz, r2);
-                bool in0 = r2.x < in_lo && o0 != me[t];
-                bool in1 = r2.y < in_lo && o1 != me[t];
+                // (the pair of a target with itself is counted here, r2 = 0, and taken off
+                // at the end; the fill pass leaves it out at once)
+                bool in0 = r2.x < in_lo && (!FILL || o0 != me[t]);
+                bool in1 = r2.y < in_lo && (!FILL || o1 != me[t]);
                 const float2 d = __fadd2_rn(r2, make_float2(-in_mid, -in_mid));
                 if (fminf(fabsf(d.x), fabsf(d.y)) <= in_rad) {  // an undecided pair (rare)
 #pragma unroll
                     for (int e = 0; e < 2; e++) {
                         const float r2e = e ? r2.y : r2.x;
                         const int oe = e ? o1 : o0;
-                        if (si[t] >= 0 && (!kTail || e == 0 || 2 * k + 1 < ns) && oe != me[t] &&
+                        if (si[t] >= 0 && (!kTail || e == 0 || 2 * k + 1 < ns) && (!FILL || oe != me[t]) &&
                             r2e >= in_lo && r2e <= in_hi) {
                             const double4_32a a = T.sp[si[t]], b = T.sp[W.pj[2 * k + e]];
                             double ex = dsub(b.x, a.x), ey = dsub(b.y, a.y), ez = dsub(b.z, a.z);
@@ -242,11 +244,23 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
                     unsigned h = hit[t];
                     hit[t] = 0u;
                     cnt[t] += __popc(h);
+                    // two hits an iteration, their loads issued together; the target
+                    // itself is left out
                     while (h) {
-                        const int b = __ffs(h) - 1;
+                        const int b0 = __ffs(h) - 1;
                         h &= h - 1u;
-                        if (rwc[t] < rcap[t]) rrow[t][rwc[t]] = po[8 * (b >> 1) + 6 + (b & 1)];
-                        rwc[t]++;
+                        const bool two = h != 0u;
+                        const int b1 = two ? __ffs(h) - 1 : b0;
+                        h &= h - 1u;
+                        const int o0 = po[8 * (b0 >> 1) + 6 + (b0 & 1)], o1 = po[8 * (b1 >> 1) + 6 + (b1 & 1)];
+                        if (o0 != me[t]) {
+                            if (rwc[t] < rcap[t]) rrow[t][rwc[t]] = o0;
+                            rwc[t]++;
+                        }
+                        if (two && o1 != me[t]) {
+                            if (rwc[t] < rcap[t]) rrow[t][rwc[t]] = o1;
+                            rwc[t]++;
+                        }
                     }
                 }
             }
@@ -386,9 +400,12 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
             test_chunk(nst);
         }
         if (!FILL) {
+            // each target met itself once (its leaf is opened and it passes the source
+            // filter) and counted itself iff 0 < r_list^2
+            const int self = rl2_d > 0.0 ? 1 : 0;
 #pragma unroll
             for (int t = 0; t < TPL; t++)
-                if (si[t] >= 0) P.count[T.perm[si[t]]] = cnt[t];
+                if (si[t] >= 0) P.count[T.perm[si[t]]] = cnt[t] - self;
         }
         if (ROWS) {
 #pragma unroll

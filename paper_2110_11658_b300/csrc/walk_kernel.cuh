@@ -171,6 +171,9 @@ struct WarpSmem {
     R4 *pp;    // staged source particles {dx, dy, dz, m}
     int *pj;   // their positions in key order
     int *po;   // row mode: their original indices
+    // mixed form: the group box relative to c_g {lo xyz, hi x} {hi yz, t2, -}, t2 the
+    // squared distance beyond which a source is r_out or more from the whole box
+    float4 *gb;
     static __host__ __device__ size_t bytes(int tile)
     {
         size_t cb = tile + 32;
@@ -178,7 +181,7 @@ struct WarpSmem {
         b += cb * (2 * sizeof(R4) + sizeof(R2));
         b += cb * 8 + (cb + 1) * 4;
         b = (b + 31) / 32 * 32;
-        b += 32 * sizeof(R4) + 2 * 32 * 4;
+        b += 32 * sizeof(R4) + 2 * 32 * 4 + 2 * sizeof(float4);
         return (b + 127) / 128 * 128;
     }
     __device__ void carve(char *base, int tile)
@@ -203,6 +206,8 @@ struct WarpSmem {
         pj = (int *)p;
         p += 32 * 4;
         po = (int *)p;
+        p += 32 * 4;
+        gb = (float4 *)p;
     }
 };
 
@@ -689,8 +694,18 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
             const int lx = W.lq[lo].x;
             const int j = (lx & 0x3fffffff) + (pos - W.lqo[lo]);
             wneed = (lx & (int)kFarLeaf) == 0;
-            cand = wneed || (SHELL && NC.beyond);
             const float4 r = ds_rel(P.T.ph[j], P.T.pl[j], F);
+            if (wneed) {
+                // a source r_out or more from the whole group box (FP32 with a margin
+                // that covers its rounding) has W = 1 with every target, like the
+                // sources of a leaf beyond r_out
+                const float4 b0 = W.gb[0], b1 = W.gb[1];
+                const float tx = fmaxf(fmaxf(b0.x - r.x, r.x - b0.w), 0.f);
+                const float ty = fmaxf(fmaxf(b0.y - r.y, r.y - b1.x), 0.f);
+                const float tz = fmaxf(fmaxf(b0.z - r.z, r.z - b1.y), 0.f);
+                wneed = !(tx * tx + ty * ty + tz * tz > b1.z);
+            }
+            cand = wneed || (SHELL && NC.beyond);
             pb[0] = r.x, pb[2] = r.y, pb[4] = r.z, pb[6] = lx < 0 ? 0.f : r.w;
             if (NBR) W.pj[lane] = j;
             if (NBR == 2) W.po[lane] = P.T.rid[j];
@@ -768,11 +783,20 @@ __device__ __forceinline__ void eval_parts_x2(const WarpSmem<float> &W, const Wa
                     long long lo;
                     int cap;
                     row_span(P.row_off, P.row_entries, NC.si[t], lo, cap);
+                    // two hits an iteration, their loads issued together
                     while (h) {
-                        const int b = __ffs(h) - 1;
+                        const int b0 = __ffs(h) - 1;
                         h &= h - 1u;
-                        if (W.pj[b] != NC.si[t]) {
-                            if (NC.wc[t] < cap) P.rows[lo + NC.wc[t]] = W.po[b];
+                        const bool two = h != 0u;
+                        const int b1 = two ? __ffs(h) - 1 : b0;
+                        h &= h - 1u;
+                        const int j0 = W.pj[b0], j1 = W.pj[b1], o0 = W.po[b0], o1 = W.po[b1];
+                        if (j0 != NC.si[t]) {
+                            if (NC.wc[t] < cap) P.rows[lo + NC.wc[t]] = o0;
+                            NC.wc[t]++;
+                        }
+                        if (two && j1 != NC.si[t]) {
+                            if (NC.wc[t] < cap) P.rows[lo + NC.wc[t]] = o1;
                             NC.wc[t]++;
                         }
                     }
@@ -931,6 +955,17 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
             glz = __double2float_rn(dsub(glo.z, Oz));
             ghx = __double2float_rn(dsub(ghi.x, Ox)), ghy = __double2float_rn(dsub(ghi.y, Oy));
             ghz = __double2float_rn(dsub(ghi.z, Oz));
+        }
+        if constexpr (kMixed) {
+            if (lane == 0) {
+                // the source test of eval_parts_x2: box - c_g carries <= ~6 u R per
+                // coordinate and a source offset about as much, so a distance above
+                // r_out (1 + 1e-5) + 32 u R in FP32 is above r_out exactly
+                const float t = sqrtf(rout2_f) * 1.00001f + 32.f * kU * Rf;
+                W.gb[0] = make_float4((glx - F.hx) - F.lx, (gly - F.hy) - F.ly, (glz - F.hz) - F.lz,
+                                      (ghx - F.hx) - F.lx);
+                W.gb[1] = make_float4((ghy - F.hy) - F.ly, (ghz - F.hz) - F.lz, filter_ok ? t * t : INFINITY, 0.f);
+            }
         }
         Real px[TPL], py[TPL], pz[TPL];
         NbrCount<TPL> NC;
