@@ -56,7 +56,8 @@ constexpr float kU = 5.9604644775390625e-8f;  // 2^-24, FP32 unit round-off
 template <int NBR>
 __host__ __device__ constexpr int cell_pair_unroll() { return NBR == 0 ? 4 : 2; }
 constexpr int kPartPairUnroll = 2;           // pairs of particles per unrolled iteration
-constexpr int kMinBlocksTpl1 = 6;            // resident blocks per SM at TPL = 1 (80 registers)
+constexpr int kMinBlocksTpl1 = 6;            // resident blocks per SM at TPL = 1 (80 registers; 5 for
+                                             // the row-mode walk, whose neighbour state needs more)
 
 // Stack bound: children ranges are pushed so that the stack stays sorted by
 // level (deepest on top).  Ranges of level l are created only while popping
@@ -866,7 +867,7 @@ constexpr int walk_block_threads()
 // and 2 with the r^-3 term, which does it otherwise; the other launch returns at once.
 template <typename Real, int TPL, bool POT, bool QUAD, int NBR, bool SHELL, int WPG, int FORM = 0>
 __global__ void __launch_bounds__(walk_block_threads<WPG>(),
-                                  TPL == 1 ? kMinBlocksTpl1 * kWalkWarps / (WPG == 1 ? kWalkWarps : WPG) : 3)
+                                  TPL == 1 ? (NBR == 2 ? 5 : kMinBlocksTpl1) * kWalkWarps / (WPG == 1 ? kWalkWarps : WPG) : 3)
     walk_kernel(WalkArgs P)
 {
     static_assert(WPG == 1 || TPL == 1, "several warps per group hold one target per lane");
