@@ -356,3 +356,27 @@ def test_threads_per_group_row_mode(G):
         assert np.array_equal(offs.cpu().numpy(), o2) and np.array_equal(idx[:tot].cpu().numpy(), i2)
         assert np.array_equal(torch.stack(a, 1).double().cpu().numpy(), first)
     ctx.close()
+
+
+def test_cell_forms_agree():
+    # The mixed walk evaluates cells in the r^-5 form when every cluster's r_out,
+    # frame and mass keep it inside FP32, else in the r^-3 form.  Masses scaled by
+    # 2^54 (total 1.8e16, past the 1e15 bound) select the r^-3 form; the scaling
+    # is exact in both forms, so the two runs must give the same lists and forces
+    # that agree to FP32 rounding, each within the oracle tolerance.
+    c = synth.plummer(20000, 61, masses="kroupa")
+    prm = p3t.Params(theta=0.4, r_in=0.004, r_out=0.04, r_list=0.04, group_size=32)
+    fast = run_gpu(c, prm, pot=False)
+    s = 2.0 ** 54
+    heavy = synth.Cluster(c.x, c.y, c.z, c.m * s, c.vx, c.vy, c.vz)
+    slow = run_gpu(heavy, prm, pot=False)
+    assert np.array_equal(fast["g_cells"], slow["g_cells"]) and np.array_equal(fast["g_parts"], slow["g_parts"])
+    assert np.array_equal(fast["offs"], slow["offs"]) and np.array_equal(fast["idx"], slow["idx"])
+    a3 = slow["a"] / s
+    e = rel_err(fast["a"], a3)
+    assert np.median(e) < 1e-6 and e.max() < 1e-4, (np.median(e), e.max())
+    assert not np.array_equal(fast["a"], a3)  # two different operation sequences ran
+    f = _oracle(c, 0.4, 0.04, 16, 32).far(0.004)
+    for a in (fast["a"], a3):
+        err = rel_err(a, f["a"])
+        assert np.median(err) <= 1e-5 and np.percentile(err, 99) <= 1e-4
