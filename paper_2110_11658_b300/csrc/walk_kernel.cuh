@@ -28,6 +28,10 @@
 // 2^-23 of its magnitude without any FP64 instruction in the walk; interactions
 // run in FP32 and each tile's partial sum is added to the running sum with
 // Kahan compensation.  The FP64 form does everything in FP64.
+// The mixed form's cell term takes the r^-5 form when every cluster of the tree
+// keeps r^-5 and its products inside FP32, else the r^-3 form (eval_cells_x2; the
+// far force launches the walk once per form, one of the two launches finding no
+// work).
 //
 // In the mixed form the particle loop also counts, per target, the neighbours
 // of Sec. 2.3 (pairs with |r| < r_list), with the same FP32 band + exact FP64
