@@ -106,7 +106,11 @@ int p3t_build_tree(p3t_ctx *c, int64_t n, const double *x, const double *y, cons
  * exactly as p3t_build_tree would build it alone with its parameters, so every
  * later call (far force, neighbours, kick) gives each cluster the same result,
  * bit for bit, as a build of that cluster alone; neighbour lists never cross
- * clusters.  Original indices in outputs refer to the concatenated order.  No
+ * clusters.  (One exception: the mixed far force evaluates cells in the r^-5 form
+ * when every cluster of the tree has r_out >= 1e-7, a frame half-size <= 1e6 and
+ * a mass <= 1e15, else in the r^-3 form; a batch holding a cluster outside those
+ * bounds gives the others forces equal to their builds alone to FP32 rounding,
+ * lists still bit for bit.)  Original indices in outputs refer to the concatenated order.  No
  * host synchronisation: a whole step can be captured in a CUDA graph once the
  * context's scratch has been sized by an earlier build of the same n. */
 int p3t_build_tree_batch(p3t_ctx *c, int32_t n_clusters, int64_t n, const int64_t *seg_offsets,

@@ -172,3 +172,40 @@ def test_batch_row_mode_over_steps():
             s0, s1 = seg[k], seg[k + 1]
             assert np.array_equal(ob[s0:s1 + 1] - ob[s0], o2)
             assert np.array_equal(ib[ob[s0]:ob[s1]] - s0, i2)
+
+
+def test_batch_with_a_cluster_outside_the_r5_range():
+    # One cluster whose mass (scaled by 2^54, past 1e15) puts it outside the r^-5 cell
+    # term's FP32 range makes the whole batch take the r^-3 term: the other cluster's
+    # lists stay bit-identical to its build alone (r^-5), its forces agree to FP32
+    # rounding, and both clusters match the oracle.
+    a_c = synth.plummer(3000, 71, masses="kroupa")
+    b_c = synth.plummer(2000, 72, masses="kroupa")
+    s = 2.0 ** 54
+    b_c = synth.Cluster(b_c.x + 10.0, b_c.y, b_c.z, b_c.m * s, b_c.vx, b_c.vy, b_c.vz)
+    all_, seg = _concat([a_c, b_c])
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, group_size=32)
+    ctx = p3t.Context(prm)
+    ctx.build_tree_batch(torch.from_numpy(seg).to(DEV), to_dev(all_.x), to_dev(all_.y), to_dev(all_.z),
+                         to_dev(all_.m))
+    n = all_.n
+    a = [torch.empty(n, dtype=torch.float32, device=DEV) for _ in range(3)]
+    ctx.far_force(*a)
+    offs = torch.empty(n + 1, dtype=torch.int64, device=DEV)
+    idx = torch.empty(50 * n, dtype=torch.int32, device=DEV)
+    tot = ctx.neighbours(offs, idx)
+    ctx.check()
+    ab = torch.stack(a, 1).double().cpu().numpy()
+    ob, ib = offs.cpu().numpy(), idx[:tot].cpu().numpy()
+    alone = run_gpu(a_c, prm, pot=False)
+    s0, s1 = seg[0], seg[1]
+    assert np.array_equal(ob[s0:s1 + 1] - ob[s0], alone["offs"])
+    assert np.array_equal(ib[ob[s0]:ob[s1]], alone["idx"])
+    e = np.linalg.norm(ab[s0:s1] - alone["a"], axis=1) / np.linalg.norm(alone["a"], axis=1)
+    assert np.median(e) < 1e-6 and e.max() < 1e-4
+    for k, (c, scale) in enumerate(((a_c, 1.0), (b_c, s))):
+        t = oracle.Tree(c.x, c.y, c.z, c.m, 0.5, 0.05, leaf_cap=16, group_size=32)
+        ref = t.far(0.005)["a"]
+        got = ab[seg[k]:seg[k + 1]]
+        err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert np.median(err) <= 1e-5 and np.percentile(err, 99) <= 1e-4, (k, np.median(err), np.percentile(err, 99))
