@@ -241,6 +241,12 @@ int p3t_create(p3t_ctx **out, const p3t_params *p, void *cuda_stream)
         if (c->fork_ev) cudaEventDestroy(c->fork_ev);
         c->side_stream = nullptr, c->fork_ev = c->join_ev = nullptr;
     }
+    if (c->side_stream && (cudaStreamCreateWithFlags(&c->side_stream2, cudaStreamNonBlocking) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&c->join_ev2, cudaEventDisableTiming) != cudaSuccess)) {
+        cudaGetLastError();
+        if (c->side_stream2) cudaStreamDestroy(c->side_stream2);
+        c->side_stream2 = nullptr, c->join_ev2 = nullptr;
+    }
     *out = c;
     return P3T_OK;
 }
@@ -264,6 +270,11 @@ int p3t_destroy(p3t_ctx *c)
     }
     if (c->fork_ev) cudaEventDestroy(c->fork_ev);
     if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->side_stream2) {
+        cudaStreamSynchronize(c->side_stream2);
+        cudaStreamDestroy(c->side_stream2);
+    }
+    if (c->join_ev2) cudaEventDestroy(c->join_ev2);
     if (c->clusters) cudaFree(c->clusters);
     if (c->irr_buf) cudaFree(c->irr_buf);
     if (c->knn_buf) cudaFree(c->knn_buf);

@@ -825,15 +825,15 @@ __global__ void __launch_bounds__(kSortWarps * 32)
 }
 
 template <typename Kern>
-static int launch_sort(p3t_ctx *c, Kern kern, const int64_t *offsets, int32_t *idx, RowSrc src)
+static int launch_sort(p3t_ctx *c, Kern kern, const int64_t *offsets, int32_t *idx, RowSrc src,
+                       cudaStream_t st)
 {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSortWarps * 32, 0) !=
             cudaSuccess ||
         per_sm < 1)
         return P3T_ERR_CUDA;
-    kern<<<per_sm * c->sm_count, kSortWarps * 32, 0, c->stream>>>(c->meta, c->row_list, offsets, idx,
-                                                                 src);
+    kern<<<per_sm * c->sm_count, kSortWarps * 32, 0, st>>>(c->meta, c->row_list, offsets, idx, src);
     return check_launch(c);
 }
 
@@ -851,29 +851,50 @@ static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long
     row_class_fill_kernel<<<grid, 256, 0, s>>>(n, offsets, capacity, c->meta, c->row_list);
     int e = check_launch(c);
     if (e) return e;
-    if ((e = launch_sort(c, row_sort_tiny_kernel<0>, offsets, idx, src))) return e;
-    if ((e = launch_sort(c, row_sort_reg_kernel<1, 1>, offsets, idx, src))) return e;
-    if ((e = launch_sort(c, row_sort_reg_kernel<2, 2>, offsets, idx, src))) return e;
-    if (kTransposed & (1u << 3))
-        e = launch_sort(c, row_sort_tr_kernel<3, 4>, offsets, idx, src);
-    else
-        e = launch_sort(c, row_sort_reg_kernel<3, 4>, offsets, idx, src);
-    if (e) return e;
-    if (n > kClassLen[4] + 1) {  // longer rows need more than 128 distinct indices
-        if (kTransposed & (1u << 4))
-            e = launch_sort(c, row_sort_tr_kernel<4, 8>, offsets, idx, src);
+    // the length classes sort disjoint rows: the longest class on the context's stream,
+    // the other classes on two side streams beside it (joined before returning, also
+    // after a failed launch, so that a captured stream is always joined)
+    const bool fork = c->side_stream != nullptr;
+    const cudaStream_t s1 = fork ? c->side_stream : s;
+    const cudaStream_t s2 = c->side_stream2 ? c->side_stream2 : s1;
+    if (fork && (cudaEventRecord(c->fork_ev, s) != cudaSuccess || cudaStreamWaitEvent(s1, c->fork_ev, 0) != cudaSuccess ||
+                 cudaStreamWaitEvent(s2, c->fork_ev, 0) != cudaSuccess))
+        return P3T_ERR_CUDA;
+    auto run = [&]() -> int {
+        int e2;
+        if ((e2 = launch_sort(c, row_sort_tiny_kernel<0>, offsets, idx, src, s2))) return e2;
+        if ((e2 = launch_sort(c, row_sort_reg_kernel<1, 1>, offsets, idx, src, s2))) return e2;
+        if ((e2 = launch_sort(c, row_sort_reg_kernel<2, 2>, offsets, idx, src, s2))) return e2;
+        if (kTransposed & (1u << 3))
+            e2 = launch_sort(c, row_sort_tr_kernel<3, 4>, offsets, idx, src, s2);
         else
-            e = launch_sort(c, row_sort_reg_kernel<4, 8>, offsets, idx, src);
-        if (e) return e;
-        if (kTransposed & (1u << 5))
-            e = launch_sort(c, row_sort_tr_kernel<5, 16>, offsets, idx, src);
-        else
-            e = launch_sort(c, row_sort_reg_kernel<5, 16>, offsets, idx, src);
-        if (e) return e;
-        if ((e = launch_sort(c, row_sort_tr_kernel<6, 32>, offsets, idx, src))) return e;
-        if ((e = launch_sort(c, row_sort_smem_kernel<7>, offsets, idx, src))) return e;
-        if ((e = launch_sort(c, row_sort_global_kernel<8>, offsets, idx, src))) return e;
+            e2 = launch_sort(c, row_sort_reg_kernel<3, 4>, offsets, idx, src, s2);
+        if (e2) return e2;
+        if (n > kClassLen[4] + 1) {  // longer rows need more than 128 distinct indices
+            if (kTransposed & (1u << 4))
+                e2 = launch_sort(c, row_sort_tr_kernel<4, 8>, offsets, idx, src, s1);
+            else
+                e2 = launch_sort(c, row_sort_reg_kernel<4, 8>, offsets, idx, src, s1);
+            if (e2) return e2;
+            if (kTransposed & (1u << 5))
+                e2 = launch_sort(c, row_sort_tr_kernel<5, 16>, offsets, idx, src, s);
+            else
+                e2 = launch_sort(c, row_sort_reg_kernel<5, 16>, offsets, idx, src, s);
+            if (e2) return e2;
+            if ((e2 = launch_sort(c, row_sort_tr_kernel<6, 32>, offsets, idx, src, s1))) return e2;
+            if ((e2 = launch_sort(c, row_sort_smem_kernel<7>, offsets, idx, src, s1))) return e2;
+            if ((e2 = launch_sort(c, row_sort_global_kernel<8>, offsets, idx, src, s1))) return e2;
+        }
+        return P3T_OK;
+    };
+    e = run();
+    if (fork) {
+        const bool ok = cudaEventRecord(c->join_ev, s1) == cudaSuccess && cudaStreamWaitEvent(s, c->join_ev, 0) == cudaSuccess &&
+                        (s2 == s1 || (cudaEventRecord(c->join_ev2, s2) == cudaSuccess &&
+                                      cudaStreamWaitEvent(s, c->join_ev2, 0) == cudaSuccess));
+        if (!ok && !e) e = P3T_ERR_CUDA;
     }
+    if (e) return e;
     return P3T_OK;
 }
 

@@ -467,6 +467,8 @@ struct p3t_ctx {
     size_t host_stage_bytes;
     cudaStream_t side_stream;         // the build's groups, beside its moments (null: in line)
     cudaEvent_t fork_ev, join_ev;
+    cudaStream_t side_stream2;        // the row sort's third branch (null: on side_stream)
+    cudaEvent_t join_ev2;
     cudaStream_t copy_stream;         // p3t_step_host: velocity upload and neighbour-list
     cudaEvent_t lists_ready;          // copy beside the build and the far force
     cudaEvent_t v_ready;
