@@ -1033,8 +1033,15 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     T.perm = c->perm_buf[passes & 1];
     const int64_t *gid = range ? range->gid : nullptr;
     T.rid = gid ? c->rid_buf : T.perm;
-    gather_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, m, T.perm, cid, T.cl, T.sp, T.ph, T.pl,
-                                                    T.inv, T.cid_s, gid, T.rid);
+    // the gather on the side stream beside the topology, which reads only the keys (the
+    // moments and the groups wait for it)
+    const bool gfork = c->side_stream != nullptr && c->join_ev2 != nullptr;
+    const cudaStream_t gts = gfork ? c->side_stream : s;
+    if (gfork && (cudaEventRecord(c->fork_ev, s) != cudaSuccess || cudaStreamWaitEvent(gts, c->fork_ev, 0) != cudaSuccess))
+        return P3T_ERR_CUDA;
+    gather_kernel<<<grid_n, kBuildThreads, 0, gts>>>(n, x, y, z, m, T.perm, cid, T.cl, T.sp, T.ph, T.pl,
+                                                      T.inv, T.cid_s, gid, T.rid);
+    if (gfork && cudaEventRecord(c->join_ev2, gts) != cudaSuccess) return P3T_ERR_CUDA;
 
     // topology, level by level
     unsigned long long *topo_status = c->scan_status + (n / 256 + 64 + 256 * nb / 256);
@@ -1050,6 +1057,7 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
             T, l, P.leaf_cap, P.group_size, topo_status + (size_t)l * stride, stride, &M->tickets[l]);
     topo_finish_kernel<<<1, 1, 0, s>>>(M, T.cap_nodes);
     if (check_launch(c)) return P3T_ERR_CUDA;
+    if (gfork && cudaStreamWaitEvent(s, c->join_ev2, 0) != cudaSuccess) return P3T_ERR_CUDA;  // the gather
 
     // groups, on the side stream beside the moments: both only read the topology
     // (the stream joins again before the build returns)
