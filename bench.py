@@ -40,7 +40,7 @@ if ROOT not in sys.path:
 # 10^6-particle Plummer walk of the timed step, which also writes the neighbour rows.
 # Valid only at that N and for the kernel sources it was measured on (their hashes):
 # otherwise the roofline's traffic is null.
-WALK_TRAFFIC = {"sources": {"walk.cu": "d468b674e174d09e", "walk_f1.cu": "2881d95896a10898", "walk_kernel.cuh": "5c61d53f45a3fb26", "p3t_internal.cuh": "7050717df5117a2f"},
+WALK_TRAFFIC = {"sources": {"walk.cu": "d468b674e174d09e", "walk_f1.cu": "2881d95896a10898", "walk_kernel.cuh": "5c61d53f45a3fb26", "p3t_internal.cuh": "e3c22a891e7bcdf2"},
                 "n": 1000000, "bytes": 299048704 + 504167168}
 
 N_DEFAULT = 1_000_000
