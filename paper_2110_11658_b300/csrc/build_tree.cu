@@ -7,10 +7,12 @@
 //             into a 63-bit Morton key (bit 3k+2 <- q_x, 3k+1 <- q_y, 3k <- q_z)
 //   sort      stable LSD radix sort of (key, index), 8 passes of 8 bits
 //   gather    particles in key order as double4_32a {x, y, z, m}
-//   topology  canonical octree level by level (a node at level l is split iff
-//             it holds more than leaf_cap particles and l < 21; children are
-//             the non-empty octants, numbered breadth first via a look-back
-//             scan per level); walk-group starts are flagged on the way
+//   topology  canonical octree (a node at level l is split iff it holds more
+//             than leaf_cap particles and l < 21; children are the non-empty
+//             octants, numbered breadth first): from each particle's first and
+//             last levels and one scan of per-tile node counts, or level by level
+//             with a look-back scan per level for a rank's range build; walk-group
+//             starts are flagged on the way
 //   groups    flags -> scan -> ranges, tight FP64 boxes
 //   moments   bottom-up: each leaf sums its particles in key order, the last
 //             child to finish combines its parent's children in octant order
@@ -561,6 +563,239 @@ __global__ void __launch_bounds__(kBuildThreads)
     }
 }
 
+// ---- the same topology without a launch per level (one cluster or a batch; not a
+// rank's range build, whose top cells split whatever their count) ----------------------
+// Particle i starts the cells of every level above the levels its key shares with
+// particle i - 1 (all of them when i starts its cluster).  A level-l cell holds more
+// than L particles iff some L + 1 consecutive particles inside it share the cell's
+// prefix, and every cell containing i holds such a window containing i, so with
+// M(i) = the largest number of levels shared by keys j and j + L over the windows
+// [j, j + L] of i's cluster that contain i, the cells containing i down to level
+// lam(i) = min(M(i) + 1, 21) exist (their ancestors are split) and the one at lam(i)
+// is a leaf.  So i starts the nodes of levels shared(i) + 1 .. lam(i), a node is
+// split iff its level is below lam of its first particle, and breadth-first order is
+// (level, first particle): a count of each level's nodes per tile of particles and one
+// scan give every node its index.
+constexpr int kFlatLevels = kLevels + 1;  // levels 0 .. 21
+
+__device__ __forceinline__ int shared_levels(uint64_t a, uint64_t b)
+{
+    const uint64_t x = a ^ b;
+    if (x == 0) return kLevels;
+    const int eq = __clzll((long long)x) - 1;  // equal key bits below the unused bit 63
+    return eq / 3 < kLevels ? eq / 3 : kLevels;
+}
+
+// cluster bounds [cs, ce) of particle i (key order; batched clusters are contiguous)
+__device__ __forceinline__ void cluster_bounds(const Tree &T, int n, int i, int &cs, int &ce)
+{
+    if (!T.seg) {
+        cs = 0;
+        ce = n;
+        return;
+    }
+    int lo = 0, hi = T.n_clusters;  // the last c with seg[c] <= i
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (T.seg[mid] <= i)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    // (clamped so that invalid offsets, latched by the cluster-id pass, stay in bounds)
+    const long long a = T.seg[lo], b = T.seg[lo + 1];
+    cs = (int)(a < 0 ? 0 : (a > i ? i : a));
+    ce = (int)(b > n ? n : (b <= i ? i + 1 : b));
+}
+
+// per particle: packed (shared + 1) | lam << 8; per tile of kBuildThreads particles and
+// level: the nodes the tile's particles start (cnt[l * ntiles + tile])
+constexpr int kFlatMaxLeaf = 128;  // leaf capacities above this take the level launches
+__global__ void __launch_bounds__(kBuildThreads)
+    topo_flat_count_kernel(Tree T, int n, int leaf_cap, int ntiles, int32_t *__restrict__ packed,
+                           int32_t *__restrict__ cnt)
+{
+    __shared__ uint64_t sk[kBuildThreads + 2 * kFlatMaxLeaf];
+    __shared__ int sw[kBuildThreads + kFlatMaxLeaf];
+    __shared__ int lc[kFlatLevels];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int t0 = blockIdx.x * kBuildThreads;
+    const int L = leaf_cap;
+    if (tid < kFlatLevels) lc[tid] = 0;
+    // keys [t0 - L, t0 + kBuildThreads + L)
+    for (int q = tid; q < kBuildThreads + 2 * L; q += kBuildThreads) {
+        const int j = t0 - L + q;
+        sk[q] = j >= 0 && j < n ? T.keys[j] : 0ULL;
+    }
+    __syncthreads();
+    // w(j) for the window starts j in [t0 - L, t0 + kBuildThreads): the levels keys j
+    // and j + L share (the windows that cross a cluster's bounds are skipped below)
+    for (int q = tid; q < kBuildThreads + L; q += kBuildThreads) {
+        const int j = t0 - L + q;
+        sw[q] = j >= 0 && j + L < n ? shared_levels(sk[q], sk[q + L]) : -1;
+    }
+    __syncthreads();
+    const int i = t0 + tid;
+    int sh = 0, lam = -1;
+    if (i < n) {
+        int cs, ce;
+        cluster_bounds(T, n, i, cs, ce);
+        sh = i == cs ? -1 : shared_levels(sk[tid + L - 1], sk[tid + L]);
+        const int j0 = i - L > cs ? i - L : cs, j1 = i < ce - 1 - L ? i : ce - 1 - L;
+        int m = -1;
+        for (int j = j0; j <= j1; j++) {
+            const int w = sw[j - t0 + L];
+            m = w > m ? w : m;
+        }
+        lam = m + 1 < kLevels ? m + 1 : kLevels;
+        packed[i] = (sh + 1) | (lam << 8);
+    }
+#pragma unroll 1
+    for (int l = 0; l < kFlatLevels; l++) {
+        const unsigned b = __ballot_sync(0xffffffffu, i < n && sh < l && l <= lam);
+        if (lane == 0 && b) atomicAdd(&lc[l], __popc(b));
+    }
+    __syncthreads();
+    if (tid < kFlatLevels) cnt[tid * ntiles + blockIdx.x] = lc[tid];
+    if (blockIdx.x == 0 && tid == 0) cnt[kFlatLevels * ntiles] = 0;  // the scan's total
+}
+
+// every node's index from the scanned counts (level, then first particle): node
+// (l, i) gets first i, its level, and its first child (l + 1, i) when it is split;
+// leaves join the moments' work list
+__global__ void __launch_bounds__(kBuildThreads)
+    topo_flat_emit_kernel(Tree T, int n, int ntiles, const int32_t *__restrict__ packed,
+                          const int32_t *__restrict__ base)
+{
+    constexpr int W = kBuildThreads / 32;
+    __shared__ int wc[kFlatLevels][W];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int i = blockIdx.x * kBuildThreads + tid;
+    int sh = 0, lam = -1;
+    if (i < n) {
+        const int pk = packed[i];
+        sh = (pk & 0xff) - 1;
+        lam = pk >> 8;
+    }
+#pragma unroll 1
+    for (int l = 0; l < kFlatLevels; l++) {
+        const unsigned b = __ballot_sync(0xffffffffu, i < n && sh < l && l <= lam);
+        if (lane == 0) wc[l][warp] = __popc(b);
+    }
+    __syncthreads();
+    const int cap = T.cap_nodes;
+    int next = -1, leaf_id = -1;  // node (l + 1, i); node (lam, i) if i starts it
+#pragma unroll 1
+    for (int l = kFlatLevels - 1; l >= 0; l--) {  // deepest first: the child is known
+        const bool mine = i < n && sh < l && l <= lam;
+        const unsigned b = __ballot_sync(0xffffffffu, mine);
+        if (!mine) continue;
+        int id = base[l * ntiles + blockIdx.x] + __popc(b & lt);
+        for (int w = 0; w < warp; w++) id += wc[l][w];
+        if (id < cap) {  // (more nodes than the capacity are latched by the meta pass)
+            T.topo[id] = make_int4(i, 0, l < lam ? next : -1, 0);
+            T.level[id] = l;
+        }
+        if (l == lam) leaf_id = id;
+        next = id;
+    }
+    const bool leaf = leaf_id >= 0 && leaf_id < cap;
+    const unsigned lb = __ballot_sync(0xffffffffu, leaf);
+    if (lb) {
+        const int lead = __ffs(lb) - 1;
+        int at = 0;
+        if (lane == lead) at = atomicAdd(&T.meta->n_leaves, __popc(lb));
+        at = __shfl_sync(0xffffffffu, at, lead);
+        if (leaf) T.leaves[at + __popc(lb & lt)] = leaf_id;
+    }
+}
+
+// per node: its particle count (the end of its cell: an exponential then a binary
+// search over the keys for the first key outside the cell's prefix, within the
+// cluster), its children (the next nodes of level l + 1 whose first particles lie in
+// the cell, at most 8), the children's parent, and the walk-group starts of the
+// children (whose counts are the gaps between their first particles) and of the roots
+__global__ void __launch_bounds__(kBuildThreads) topo_flat_finish_kernel(Tree T, int n, int G)
+{
+    const Meta *M = T.meta;
+    const int nn = M->n_nodes < T.cap_nodes ? M->n_nodes : T.cap_nodes;
+    int *tpw = reinterpret_cast<int *>(T.topo);  // the emit pass wrote x (first) and z (child)
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
+        const int i = tpw[4 * (size_t)k], child = tpw[4 * (size_t)k + 2];
+        const int l = T.level[k];
+        int cs, ce;
+        cluster_bounds(T, n, i, cs, ce);
+        int end = ce;
+        if (l > 0) {
+            // first j in (i, ce) whose key leaves the level-l cell of key i, else ce
+            const uint64_t ki = T.keys[i];
+            const int sft = 63 - 3 * l;
+            const uint64_t pfx = ki >> sft;
+            int lo = i, step = 1;  // keys[lo] inside; probe lo + step
+            while (lo + step < ce && (T.keys[lo + step] >> sft) == pfx) {
+                lo += step;
+                step <<= 1;
+            }
+            int hi = lo + step < ce ? lo + step : ce;  // keys[hi] outside, or hi == ce
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if ((T.keys[mid] >> sft) == pfx)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            end = hi;
+        }
+        const int count = end - i;
+        tpw[4 * (size_t)k + 1] = count;
+        if (l == 0) {
+            T.parent[k] = -1;
+            flag_groups(T.gflag, i, count, true, child < 0, G);
+        }
+        int nch = 0;
+        if (child >= 0) {
+            const int lend = M->level_start[l + 1] + M->level_count[l + 1];
+            const int cend = lend < T.cap_nodes ? lend : T.cap_nodes;
+            const bool big = count > kGroupNodeFactor * G;
+            // the level's first particles ascend, so the children are the run of nodes
+            // from child on whose first particles lie below end
+            int f[8];
+#pragma unroll
+            for (int o = 0; o < 8; o++) {
+                f[o] = child + o < cend ? tpw[4 * (size_t)(child + o)] : end;
+                nch += f[o] < end;
+            }
+#pragma unroll
+            for (int o = 0; o < 8; o++) {
+                if (o >= nch) break;
+                const int c = child + o;
+                const int cnt = (o + 1 < nch ? f[o + 1] : end) - f[o];
+                T.parent[c] = k;
+                flag_groups(T.gflag, f[o], cnt, big, tpw[4 * (size_t)c + 2] < 0, G);
+            }
+        }
+        tpw[4 * (size_t)k + 3] = nch;
+    }
+}
+
+// the level starts and counts and the node total from the scanned counts
+__global__ void topo_flat_meta_kernel(Meta *M, const int32_t *__restrict__ base, int ntiles, int cap_nodes)
+{
+    const int total = base[kFlatLevels * ntiles];
+    int depth = 0;
+    for (int l = 0; l < kFlatLevels; l++) {
+        const int b = base[l * ntiles];
+        const int e = l + 1 < kFlatLevels ? base[(l + 1) * ntiles] : total;
+        M->level_start[l] = b;
+        M->level_count[l] = e - b;
+        if (e > b) depth = l;
+    }
+    if (total > cap_nodes) latch_error(M, P3T_ERR_CAPACITY);
+    M->n_nodes = total;
+    M->depth = depth;
+}
+
 __global__ void topo_finish_kernel(Meta *M, int cap_nodes)
 {
     int total = 0, depth = 0;
@@ -1043,19 +1278,38 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
                                                       T.inv, T.cid_s, gid, T.rid);
     if (gfork && cudaEventRecord(c->join_ev2, gts) != cudaSuccess) return P3T_ERR_CUDA;
 
-    // topology, level by level
-    unsigned long long *topo_status = c->scan_status + (n / 256 + 64 + 256 * nb / 256);
-    const int stride = topo_status_stride(n);
-    if (cudaMemsetAsync(topo_status, 0, sizeof(unsigned long long) * stride * kMaxLevelSlots, s) !=
-            cudaSuccess ||
-        cudaMemsetAsync(T.gflag, 0, n, s) != cudaSuccess)
-        return P3T_ERR_CUDA;
-    topo_root_kernel<<<grid_c, 128, 0, s>>>(T, n, P.leaf_cap, P.group_size);
-    const int topo_grid = 2 * c->sm_count;
-    for (int l = 0; l < kLevels; l++)
-        topo_level_kernel<<<topo_grid, kBuildThreads, 0, s>>>(
-            T, l, P.leaf_cap, P.group_size, topo_status + (size_t)l * stride, stride, &M->tickets[l]);
-    topo_finish_kernel<<<1, 1, 0, s>>>(M, T.cap_nodes);
+    // topology: in one flat pass over the particles (per-particle levels, a scan of
+    // the per-tile node counts, the nodes, their counts and children), or level by
+    // level for a rank's range build (its top cells split whatever their count) and
+    // for leaf capacities past the flat pass's window
+    if (cudaMemsetAsync(T.gflag, 0, n, s) != cudaSuccess) return P3T_ERR_CUDA;
+    if (!range && P.leaf_cap <= kFlatMaxLeaf) {
+        // per-particle levels in the group index buffer and per-tile counts in the sort
+        // histogram (both free until the groups): 22 ceil(n / 256) + 1 <= 256 ceil(n / 1024)
+        const int ntiles = grid_n;
+        const int ncnt = kFlatLevels * ntiles + 1;
+        topo_flat_count_kernel<<<ntiles, kBuildThreads, 0, s>>>(T, n, P.leaf_cap, ntiles, T.gidx,
+                                                                c->sort_hist);
+        if (check_launch(c)) return P3T_ERR_CUDA;
+        int e = scan_excl_i32_to_i32(c->sort_hist, c->sort_hist, ncnt, c->scan_status, &M->tickets[31],
+                                     M, s);
+        if (e) return e;
+        topo_flat_meta_kernel<<<1, 1, 0, s>>>(M, c->sort_hist, ntiles, T.cap_nodes);
+        topo_flat_emit_kernel<<<ntiles, kBuildThreads, 0, s>>>(T, n, ntiles, T.gidx, c->sort_hist);
+        topo_flat_finish_kernel<<<persistent, kBuildThreads, 0, s>>>(T, n, P.group_size);
+    } else {
+        unsigned long long *topo_status = c->scan_status + (n / 256 + 64 + 256 * nb / 256);
+        const int stride = topo_status_stride(n);
+        if (cudaMemsetAsync(topo_status, 0, sizeof(unsigned long long) * stride * kMaxLevelSlots, s) !=
+            cudaSuccess)
+            return P3T_ERR_CUDA;
+        topo_root_kernel<<<grid_c, 128, 0, s>>>(T, n, P.leaf_cap, P.group_size);
+        const int topo_grid = 2 * c->sm_count;
+        for (int l = 0; l < kLevels; l++)
+            topo_level_kernel<<<topo_grid, kBuildThreads, 0, s>>>(
+                T, l, P.leaf_cap, P.group_size, topo_status + (size_t)l * stride, stride, &M->tickets[l]);
+        topo_finish_kernel<<<1, 1, 0, s>>>(M, T.cap_nodes);
+    }
     if (check_launch(c)) return P3T_ERR_CUDA;
     if (gfork && cudaStreamWaitEvent(s, c->join_ev2, 0) != cudaSuccess) return P3T_ERR_CUDA;  // the gather
 
