@@ -188,16 +188,22 @@ __device__ void internal_moments(Tree &T, int k, int4 tp, double theta)
         }
         for (int a = 0; a < 6; a++) q[a] = Q[a];
     } else {
+        // offsets from the double-single COMs relative to the cluster's frame O (the
+        // children's records and the node's own split)
+        const double *O = T.cl[T.cid_s[tp.x < T.n ? tp.x : 0]].frame;
+        float ch[3], cl[3];
+        for (int d = 0; d < 3; d++) ds_split(dsub(com[d], O[d]), ch[d], cl[d]);
         float Q[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             if (i >= nc) break;
             const int c = c0 + i;
             const float *Qc = T.q32 + 6 * (size_t)c;
-            float Mc = (float)cm[i].w;
-            float dx = __double2float_rn(dsub(cm[i].x, com[0]));
-            float dy = __double2float_rn(dsub(cm[i].y, com[1]));
-            float dz = __double2float_rn(dsub(cm[i].z, com[2]));
+            const float4 w0 = __ldcg(&T.wn[wrec(c, 0)]), w3 = __ldcg(&T.wn[wrec(c, 3)]);
+            const float Mc = w3.w;
+            const float dx = (w0.x - ch[0]) + (w3.x - cl[0]);
+            const float dy = (w0.y - ch[1]) + (w3.y - cl[1]);
+            const float dz = (w0.z - ch[2]) + (w3.z - cl[2]);
             float d2 = dx * dx + dy * dy + dz * dz;
             Q[0] += __ldcg(Qc + 0) + Mc * (3.f * dx * dx - d2);
             Q[1] += __ldcg(Qc + 1) + Mc * (3.f * dx * dy);

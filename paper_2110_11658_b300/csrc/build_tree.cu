@@ -768,11 +768,12 @@ __global__ void __launch_bounds__(kBuildThreads) topo_flat_finish_kernel(Tree T,
             }
 #pragma unroll
             for (int o = 0; o < 8; o++) {
-                if (o >= nch) break;
-                const int c = child + o;
-                const int cnt = (o + 1 < nch ? f[o + 1] : end) - f[o];
-                T.parent[c] = k;
-                flag_groups(T.gflag, f[o], cnt, big, tpw[4 * (size_t)c + 2] < 0, G);
+                if (o < nch) {
+                    const int c = child + o;
+                    const int cnt = (o < 7 && o + 1 < nch ? f[o < 7 ? o + 1 : 7] : end) - f[o];
+                    T.parent[c] = k;
+                    flag_groups(T.gflag, f[o], cnt, big, tpw[4 * (size_t)c + 2] < 0, G);
+                }
             }
         }
         tpw[4 * (size_t)k + 3] = nch;
@@ -1028,6 +1029,159 @@ __device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
     write_node<Q64>(T, k, M, com, lo, hi, q, theta, tp);
 }
 
+// A mixed-form leaf's records from its sums: the steps of write_node<false> with the
+// FP32 quadrupole and the double-single COM (relative to the frame O) passed in
+__device__ __forceinline__ void write_leaf_mixed(Tree &T, int k, int4 tp, double M, const double com[3],
+                                                 const double lo[3], const double hi[3], const float Q[6],
+                                                 const float ch[3], const float cl[3], const Cluster &K)
+{
+    const double theta = K.theta;
+    double l = dsub(hi[0], lo[0]);
+    if (dsub(hi[1], lo[1]) > l) l = dsub(hi[1], lo[1]);
+    if (dsub(hi[2], lo[2]) > l) l = dsub(hi[2], lo[2]);
+    const double cx = dsub(dmul(0.5, dadd(lo[0], hi[0])), com[0]);
+    const double cy = dsub(dmul(0.5, dadd(lo[1], hi[1])), com[1]);
+    const double cz = dsub(dmul(0.5, dadd(lo[2], hi[2])), com[2]);
+    const double delta = dsqrt(dadd(dadd(dmul(cx, cx), dmul(cy, cy)), dmul(cz, cz)));
+    double ro2 = INFINITY;
+    if (theta > 0.0) {
+        const double ro = dadd(ddiv(l, theta), delta);
+        ro2 = dmul(ro, ro);
+    }
+    T.comM[k] = make_double4_32a(com[0], com[1], com[2], M);
+    T.lo[k] = make_double4_32a(lo[0], lo[1], lo[2], ro2);
+    T.hi[k] = make_double4_32a(hi[0], hi[1], hi[2], 0.0);
+    float2 *q2 = reinterpret_cast<float2 *>(T.q32 + 6 * (size_t)k);
+    q2[0] = make_float2(Q[0], Q[1]);
+    q2[1] = make_float2(Q[2], Q[3]);
+    q2[2] = make_float2(Q[4], Q[5]);
+    const double *O = K.frame;
+    const auto w = wrec_at(T.wn, k);
+    w[0] = make_float4(ch[0], ch[1], ch[2], __double2float_rn(ro2));
+    w[1] = make_float4(__double2float_rn(dsub(lo[0], O[0])), __double2float_rn(dsub(lo[1], O[1])),
+                       __double2float_rn(dsub(lo[2], O[2])), __int_as_float(-1 - tp.x));
+    w[2] = make_float4(__double2float_rn(dsub(hi[0], O[0])), __double2float_rn(dsub(hi[1], O[1])),
+                       __double2float_rn(dsub(hi[2], O[2])), __int_as_float(tp.y));
+    w[3] = make_float4(cl[0], cl[1], cl[2], __double2float_rn(M));
+    w[4] = make_float4(Q[0], Q[1], Q[2], Q[3]);
+    w[5] = make_float4(Q[4], Q[5], 0.f, 0.f);
+}
+
+// A mixed-form leaf (k >= 0) from its FP64 sums: COM, FP32 quadrupole on offsets from
+// the double-single splits (x - O) - (com - O), records
+__device__ __forceinline__ void leaf_finish_mixed(Tree &T, int k, int4 tp, double M, const double S[3],
+                                                  const EncBox &box)
+{
+    if (k < 0) return;
+    double lo[3], hi[3], com[3];
+    box.get(lo, hi);
+    for (int d = 0; d < 3; d++) com[d] = M > 0.0 ? ddiv(S[d], M) : dmul(0.5, dadd(lo[d], hi[d]));
+    const Cluster &K = T.cl[T.cid_s[tp.x < T.n ? tp.x : 0]];
+    float ch[3], cl[3];
+    for (int d = 0; d < 3; d++) ds_split(dsub(com[d], K.frame[d]), ch[d], cl[d]);
+    float Q[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int i = tp.x; i < tp.x + tp.y; i++) {
+        const float4 h = T.ph[i], l = T.pl[i];
+        const float m = h.w;
+        const float dx = (h.x - ch[0]) + (l.x - cl[0]);
+        const float dy = (h.y - ch[1]) + (l.y - cl[1]);
+        const float dz = (h.z - ch[2]) + (l.z - cl[2]);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        Q[0] += m * (3.f * dx * dx - r2);
+        Q[1] += m * (3.f * dx * dy);
+        Q[2] += m * (3.f * dx * dz);
+        Q[3] += m * (3.f * dy * dy - r2);
+        Q[4] += m * (3.f * dy * dz);
+        Q[5] += m * (3.f * dz * dz - r2);
+    }
+    write_leaf_mixed(T, k, tp, M, com, lo, hi, Q, ch, cl, K);
+}
+
+// Two mixed-form leaves on one lane (ka, kb; -1: none), their particles taken as one
+// stream for the FP64 sums: the sums of each leaf stay sequential in key order (the
+// same operations as leaf_moments<false>), and a lane's FP64 steps are the two
+// leaves' total
+__device__ __forceinline__ void leaf_pair_mixed(Tree &T, int ka, int kb)
+{
+    const int4 ta = ka >= 0 ? T.topo[ka] : make_int4(0, 0, -1, 0);
+    const int4 tb = kb >= 0 ? T.topo[kb] : make_int4(0, 0, -1, 0);
+    const int na = ta.y, tot = ta.y + tb.y;
+    double M = 0.0, S[3] = {0, 0, 0}, Ma = 0.0, Sa[3] = {0, 0, 0};
+    EncBox box, boxa;
+    box.reset();
+    boxa.reset();
+    for (int p0 = 0; p0 < tot; p0 += 4) {
+        double4_32a pc[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int p = p0 + u;
+            if (p < tot) pc[u] = T.sp[p < na ? ta.x + p : tb.x + (p - na)];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int p = p0 + u;
+            if (p < tot) {
+                if (p == na) {  // leaf a done: its sums aside, b starts from zero
+                    Ma = M;
+                    Sa[0] = S[0], Sa[1] = S[1], Sa[2] = S[2];
+                    boxa = box;
+                    M = 0.0;
+                    S[0] = S[1] = S[2] = 0.0;
+                    box.reset();
+                }
+                const double4_32a &q = pc[u];
+                M = dadd(M, q.w);
+                S[0] = dadd(S[0], dmul(q.w, q.x));
+                S[1] = dadd(S[1], dmul(q.w, q.y));
+                S[2] = dadd(S[2], dmul(q.w, q.z));
+                box.add(q.x, q.y, q.z);
+            }
+        }
+    }
+    if (tot == na) {  // no particles of b: the running sums are a's
+        Ma = M;
+        Sa[0] = S[0], Sa[1] = S[1], Sa[2] = S[2];
+        boxa = box;
+    }
+    leaf_finish_mixed(T, ka, ta, Ma, Sa, boxa);
+    leaf_finish_mixed(T, kb, tb, M, S, box);
+}
+
+// The mixed-form leaves, 64 a warp: sorted by particle count (a counting sort over
+// the warp) and paired smallest with largest, so that the warp's FP64 steps follow
+// its largest pair rather than its largest leaf twice
+constexpr int kLeafClasses = 18;  // counts 0 .. 16, and 17 for every larger count
+__global__ void __launch_bounds__(kBuildThreads) moments_leaf_pair_kernel(Tree T)
+{
+    __shared__ int sl[kBuildThreads / 32][64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nl = T.meta->n_leaves;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int l0 = 64 * gw; l0 < nl; l0 += 64 * nw) {
+        const int ka = l0 + lane < nl ? T.leaves[l0 + lane] : -1;
+        const int kb = l0 + 32 + lane < nl ? T.leaves[l0 + 32 + lane] : -1;
+        const int na = ka >= 0 ? T.topo[ka].y : 0, nb = kb >= 0 ? T.topo[kb].y : 0;
+        const int va = na < kLeafClasses - 1 ? na : kLeafClasses - 1;
+        const int vb = nb < kLeafClasses - 1 ? nb : kLeafClasses - 1;
+        int base = 0, ra = 0, rb = 0;
+#pragma unroll 1
+        for (int v = 0; v < kLeafClasses; v++) {
+            const unsigned ba = __ballot_sync(0xffffffffu, va == v), bb = __ballot_sync(0xffffffffu, vb == v);
+            if (va == v) ra = base + __popc(ba & lt);
+            if (vb == v) rb = base + __popc(ba) + __popc(bb & lt);
+            base += __popc(ba) + __popc(bb);
+        }
+        sl[warp][ra] = ka;
+        sl[warp][rb] = kb;
+        __syncwarp();
+        const int k0 = sl[warp][lane], k1 = sl[warp][63 - lane];
+        __syncwarp();
+        leaf_pair_mixed(T, k0, k1);
+    }
+}
+
 // The internal node k of the mixed form on three lanes, lane d doing dimension
 // d of every FP64 step (the same operations in the same order as
 // internal_moments<false> + write_node<false>; M and the steps after the box are
@@ -1061,15 +1215,26 @@ __device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool 
     }
     const double lo = dec_double(elo), hi = dec_double(ehi);
     const double com = M > 0.0 ? ddiv(S, M) : dmul(0.5, dadd(lo, hi));
-    // quadrupole from the children (FP32): each lane's offsets, then all three
+    // relative to the cluster's frame O: the double-single COM
+    const Cluster &K = T.cl[T.cid_s[act && tp.x < T.n ? tp.x : 0]];
+    const double O = K.frame[d];
+    float ch, cl;
+    ds_split(dsub(com, O), ch, cl);
+    // quadrupole from the children (FP32): each lane's offsets from the double-single
+    // COMs of its dimension (the children's records), then all three
+    auto compf = [&](const float4 &v) { return d == 0 ? v.x : (d == 1 ? v.y : v.z); };
     float Q[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-        const float dd = i < nc ? __double2float_rn(dsub(comp(cm[i]), com)) : 0.f;
+        float dd = 0.f, Mc = 0.f;
+        if (i < nc) {
+            const float4 w0 = __ldcg(&T.wn[wrec(c0 + i, 0)]), w3 = __ldcg(&T.wn[wrec(c0 + i, 3)]);
+            dd = (compf(w0) - ch) + (compf(w3) - cl);
+            Mc = w3.w;
+        }
         const float dx = shf(dd, 0), dy = shf(dd, 1), dz = shf(dd, 2);
         if (i < nc) {
             const float *Qc = T.q32 + 6 * (size_t)(c0 + i);
-            const float Mc = (float)cm[i].w;
             const float d2 = dx * dx + dy * dy + dz * dz;
             Q[0] += __ldcg(Qc + 0) + Mc * (3.f * dx * dx - d2);
             Q[1] += __ldcg(Qc + 1) + Mc * (3.f * dx * dy);
@@ -1088,7 +1253,6 @@ __device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool 
     const double c = dsub(dmul(0.5, dadd(lo, hi)), com);
     const double c2 = dmul(c, c);
     const double cx2 = sh(c2, 0), cy2 = sh(c2, 1), cz2 = sh(c2, 2);
-    const Cluster &K = T.cl[T.cid_s[act && tp.x < T.n ? tp.x : 0]];
     const double theta = K.theta;
     double ro2 = INFINITY;
     if (act) {
@@ -1098,10 +1262,7 @@ __device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool 
             ro2 = dmul(ro, ro);
         }
     }
-    // relative to the cluster's frame O: the double-single COM and the FP32 box
-    const double O = K.frame[d];
-    float ch, cl;
-    ds_split(dsub(com, O), ch, cl);
+    // the FP32 box relative to O
     const float blo = __double2float_rn(dsub(lo, O)), bhi = __double2float_rn(dsub(hi, O));
     const double cx = sh(com, 0), cy = sh(com, 1), cz = sh(com, 2);
     const double lx = sh(lo, 0), ly = sh(lo, 1), lz = sh(lo, 2);
@@ -1340,7 +1501,7 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     if (q64)
         moments_leaf_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
     else
-        moments_leaf_kernel<false><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
+        moments_leaf_pair_kernel<<<persistent, kBuildThreads, 0, s>>>(T);
     for (int l = kLevels - 1; l >= 0; l--) {
         if (q64)
             moments_level_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, l, P.theta);
