@@ -54,6 +54,7 @@ __global__ void init_meta_kernel(Meta *m)
 
 __global__ void init_clusters_kernel(Cluster *cl, int C)
 {
+    pdl_wait();
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
         for (int d = 0; d < 3; d++) {
             cl[c].minmax[d] = ~0ULL;   // running minimum
@@ -67,6 +68,7 @@ __global__ void cluster_params_kernel(Cluster *cl, int C, const double *__restri
                                       double theta, double r_in, double r_out, double r_list,
                                       Meta *meta)
 {
+    pdl_wait();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     double th = theta, ri = r_in, ro = r_out, rl = r_list;
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(kBuildThreads)
                 const double *__restrict__ z, const double *__restrict__ m,
                 const int32_t *__restrict__ cid, Cluster *cl, Meta *meta)
 {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     bool bad = false;
     int cur = -1;  // cluster of the running extrema (warp-uniform)
@@ -210,6 +213,7 @@ __global__ void __launch_bounds__(kBuildThreads)
 // rule 1 per cluster: the bounding cube, and the frame of the FP32 walk filter
 __global__ void cube_kernel(Cluster *cl, int C)
 {
+    pdl_wait();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     Cluster &K = cl[c];
@@ -241,6 +245,7 @@ __global__ void __launch_bounds__(kBuildThreads)
                 const Cluster *__restrict__ cl, uint64_t *__restrict__ keys,
                 int32_t *__restrict__ perm)
 {
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const Cluster &K = cl[cid ? cid[i] : 0];
@@ -265,9 +270,12 @@ __device__ __forceinline__ int sort_digit(uint64_t key, int32_t val, int shift,
 __global__ void __launch_bounds__(kBuildThreads)
     sort_hist_kernel(int n, const uint64_t *__restrict__ keys, const int32_t *__restrict__ vals,
                      const int32_t *__restrict__ cid, int shift, int nblocks,
-                     int32_t *__restrict__ hist)
+                     int32_t *__restrict__ hist, unsigned long long *scan_status, int scan_words,
+                     unsigned int *scan_ticket)
 {
+    pdl_wait();
     __shared__ int cnt[256];
+    if (blockIdx.x == 0) clear_scan_state(scan_status, scan_words, scan_ticket);  // the digit scan's
     cnt[threadIdx.x] = 0;
     __syncthreads();
     const long long base = (long long)blockIdx.x * kSortTile;
@@ -286,6 +294,7 @@ __global__ void __launch_bounds__(kBuildThreads)
                         const int32_t *__restrict__ cid, int shift, int nblocks,
                         const int32_t *__restrict__ hist_off)
 {
+    pdl_wait();
     constexpr int W = kBuildThreads / 32;
     __shared__ int gofs[256];
     __shared__ int wcnt[W][256];
@@ -613,8 +622,11 @@ __device__ __forceinline__ void cluster_bounds(const Tree &T, int n, int i, int 
 constexpr int kFlatMaxLeaf = 128;  // leaf capacities above this take the level launches
 __global__ void __launch_bounds__(kBuildThreads)
     topo_flat_count_kernel(Tree T, int n, int leaf_cap, int ntiles, int32_t *__restrict__ packed,
-                           int32_t *__restrict__ cnt)
+                           int32_t *__restrict__ cnt, unsigned long long *scan_status, int scan_words,
+                           unsigned int *scan_ticket)
 {
+    pdl_wait();
+    if (blockIdx.x == 0) clear_scan_state(scan_status, scan_words, scan_ticket);  // the count scan's
     __shared__ uint64_t sk[kBuildThreads + 2 * kFlatMaxLeaf];
     __shared__ int sw[kBuildThreads + kFlatMaxLeaf];
     __shared__ int lc[kFlatLevels];
@@ -667,6 +679,7 @@ __global__ void __launch_bounds__(kBuildThreads)
     topo_flat_emit_kernel(Tree T, int n, int ntiles, const int32_t *__restrict__ packed,
                           const int32_t *__restrict__ base)
 {
+    pdl_wait();
     constexpr int W = kBuildThreads / 32;
     __shared__ int wc[kFlatLevels][W];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -718,6 +731,7 @@ __global__ void __launch_bounds__(kBuildThreads)
 // children (whose counts are the gaps between their first particles) and of the roots
 __global__ void __launch_bounds__(kBuildThreads) topo_flat_finish_kernel(Tree T, int n, int G)
 {
+    pdl_wait();
     const Meta *M = T.meta;
     const int nn = M->n_nodes < T.cap_nodes ? M->n_nodes : T.cap_nodes;
     int *tpw = reinterpret_cast<int *>(T.topo);  // the emit pass wrote x (first) and z (child)
@@ -783,6 +797,7 @@ __global__ void __launch_bounds__(kBuildThreads) topo_flat_finish_kernel(Tree T,
 // the level starts and counts and the node total from the scanned counts
 __global__ void topo_flat_meta_kernel(Meta *M, const int32_t *__restrict__ base, int ntiles, int cap_nodes)
 {
+    pdl_wait();
     const int total = base[kFlatLevels * ntiles];
     int depth = 0;
     for (int l = 0; l < kFlatLevels; l++) {
@@ -1154,6 +1169,7 @@ __device__ __forceinline__ void leaf_pair_mixed(Tree &T, int ka, int kb)
 constexpr int kLeafClasses = 18;  // counts 0 .. 16, and 17 for every larger count
 __global__ void __launch_bounds__(kBuildThreads) moments_leaf_pair_kernel(Tree T)
 {
+    pdl_wait();
     __shared__ int sl[kBuildThreads / 32][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -1292,6 +1308,7 @@ __device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool 
 // internal nodes of level l in the mixed form, ten nodes a warp (three lanes each)
 __global__ void __launch_bounds__(kBuildThreads) moments_level3_kernel(Tree T, int l)
 {
+    pdl_wait();
     const int b = T.meta->level_start[l], e = b + T.meta->level_count[l];
     const int lane = threadIdx.x & 31;
     const int slot = lane / 3, d = lane - 3 * slot;  // lanes 30, 31: slot 10, idle
@@ -1388,17 +1405,22 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     const int persistent = 4 * c->sm_count;
 
     init_meta_kernel<<<1, 64, 0, s>>>(M);
-    init_clusters_kernel<<<grid_c, 128, 0, s>>>(T.cl, n_clusters);
-    cluster_params_kernel<<<grid_c, 128, 0, s>>>(T.cl, n_clusters, cprm, P.theta, P.r_in, P.r_out,
-                                                 P.r_list, M);
+    // the kernels of one build follow one another on the stream with programmatic
+    // dependent launches (each waits for the one before it; their launches overlap)
+    bool ok = launch_pdl(init_clusters_kernel, dim3(grid_c), dim3(128), s, T.cl, n_clusters) == cudaSuccess &&
+              launch_pdl(cluster_params_kernel, dim3(grid_c), dim3(128), s, T.cl, n_clusters, cprm, P.theta,
+                         P.r_in, P.r_out, P.r_list, M) == cudaSuccess;
     if (seg) cid_kernel<<<(n > n_clusters ? grid_n : grid_c + 1), kBuildThreads, 0, s>>>(n, n_clusters, seg, T.cid, M);
-    bbox_kernel<<<persistent, kBuildThreads, 0, s>>>(n, x, y, z, m, cid, T.cl, M);
+    ok = ok && launch_pdl(bbox_kernel, dim3(persistent), dim3(kBuildThreads), s, n, x, y, z, m, cid, T.cl, M) ==
+                   cudaSuccess;
     if (range)
         set_bbox_kernel<<<1, 1, 0, s>>>(T.cl, range->box[0], range->box[1], range->box[2], range->box[3],
                                         range->box[4], range->box[5], M);
-    cube_kernel<<<grid_c, 128, 0, s>>>(T.cl, n_clusters);
-    keys_kernel<<<grid_n, kBuildThreads, 0, s>>>(n, x, y, z, cid, T.cl, c->keys_buf[0], c->perm_buf[0]);
-    if (check_launch(c)) return P3T_ERR_CUDA;
+    ok = ok &&
+         launch_pdl(cube_kernel, dim3(grid_c), dim3(128), s, T.cl, n_clusters) == cudaSuccess &&
+         launch_pdl(keys_kernel, dim3(grid_n), dim3(kBuildThreads), s, n, x, y, z, cid, (const Cluster *)T.cl,
+                    c->keys_buf[0], c->perm_buf[0]) == cudaSuccess;
+    if (!ok || check_launch(c)) return P3T_ERR_CUDA;
 
     // 8 passes of 8 bits over the key, then (batched builds) stable passes over the
     // cluster id, so the order is (cluster, key, original index).  A rank's part of
@@ -1416,14 +1438,17 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
         uint64_t *kin = c->keys_buf[pass & 1], *kout = c->keys_buf[(pass + 1) & 1];
         int32_t *vin = c->perm_buf[pass & 1], *vout = c->perm_buf[(pass + 1) & 1];
         const int32_t *dcid = by_cid ? T.cid : (by_gid ? c->rid_buf : nullptr);
-        sort_hist_kernel<<<nb, kBuildThreads, 0, s>>>(n, kin, vin, dcid, shift, nb, c->sort_hist);
-        if (check_launch(c)) return P3T_ERR_CUDA;
-        int e = scan_excl_i32_to_i32(c->sort_hist, c->sort_hist, 256 * nb, c->scan_status,
-                                     &M->tickets[31], M, s);
+        if (launch_pdl(sort_hist_kernel, dim3(nb), dim3(kBuildThreads), s, n, (const uint64_t *)kin,
+                       (const int32_t *)vin, dcid, shift, nb, c->sort_hist, c->scan_status,
+                       scan_status_words(256 * nb), &M->tickets[31]) != cudaSuccess)
+            return P3T_ERR_CUDA;
+        int e = scan_excl_i32_to_i32_cleared(c->sort_hist, c->sort_hist, 256 * nb, c->scan_status,
+                                             &M->tickets[31], M, s);
         if (e) return e;
-        sort_scatter_kernel<<<nb, kBuildThreads, 0, s>>>(n, kin, vin, kout, vout, dcid, shift, nb,
-                                                         c->sort_hist);
-        if (check_launch(c)) return P3T_ERR_CUDA;
+        if (launch_pdl(sort_scatter_kernel, dim3(nb), dim3(kBuildThreads), s, n, (const uint64_t *)kin,
+                       (const int32_t *)vin, kout, vout, dcid, shift, nb, (const int32_t *)c->sort_hist) !=
+            cudaSuccess)
+            return P3T_ERR_CUDA;
     }
     T.keys = c->keys_buf[passes & 1];
     T.perm = c->perm_buf[passes & 1];
@@ -1449,15 +1474,20 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
         // histogram (both free until the groups): 22 ceil(n / 256) + 1 <= 256 ceil(n / 1024)
         const int ntiles = grid_n;
         const int ncnt = kFlatLevels * ntiles + 1;
-        topo_flat_count_kernel<<<ntiles, kBuildThreads, 0, s>>>(T, n, P.leaf_cap, ntiles, T.gidx,
-                                                                c->sort_hist);
-        if (check_launch(c)) return P3T_ERR_CUDA;
-        int e = scan_excl_i32_to_i32(c->sort_hist, c->sort_hist, ncnt, c->scan_status, &M->tickets[31],
-                                     M, s);
+        if (launch_pdl(topo_flat_count_kernel, dim3(ntiles), dim3(kBuildThreads), s, T, n, P.leaf_cap, ntiles,
+                       T.gidx, c->sort_hist, c->scan_status, scan_status_words(ncnt), &M->tickets[31]) !=
+            cudaSuccess)
+            return P3T_ERR_CUDA;
+        int e = scan_excl_i32_to_i32_cleared(c->sort_hist, c->sort_hist, ncnt, c->scan_status,
+                                             &M->tickets[31], M, s);
         if (e) return e;
-        topo_flat_meta_kernel<<<1, 1, 0, s>>>(M, c->sort_hist, ntiles, T.cap_nodes);
-        topo_flat_emit_kernel<<<ntiles, kBuildThreads, 0, s>>>(T, n, ntiles, T.gidx, c->sort_hist);
-        topo_flat_finish_kernel<<<persistent, kBuildThreads, 0, s>>>(T, n, P.group_size);
+        if (launch_pdl(topo_flat_meta_kernel, dim3(1), dim3(1), s, M, (const int32_t *)c->sort_hist, ntiles,
+                       T.cap_nodes) != cudaSuccess ||
+            launch_pdl(topo_flat_emit_kernel, dim3(ntiles), dim3(kBuildThreads), s, T, n, ntiles,
+                       (const int32_t *)T.gidx, (const int32_t *)c->sort_hist) != cudaSuccess ||
+            launch_pdl(topo_flat_finish_kernel, dim3(persistent), dim3(kBuildThreads), s, T, n, P.group_size) !=
+                cudaSuccess)
+            return P3T_ERR_CUDA;
     } else {
         unsigned long long *topo_status = c->scan_status + (n / 256 + 64 + 256 * nb / 256);
         const int stride = topo_status_stride(n);
@@ -1500,13 +1530,13 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     const bool q64 = P.precision == P3T_FP64;
     if (q64)
         moments_leaf_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
-    else
-        moments_leaf_pair_kernel<<<persistent, kBuildThreads, 0, s>>>(T);
+    else if (launch_pdl(moments_leaf_pair_kernel, dim3(persistent), dim3(kBuildThreads), s, T) != cudaSuccess)
+        return P3T_ERR_CUDA;
     for (int l = kLevels - 1; l >= 0; l--) {
         if (q64)
             moments_level_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, l, P.theta);
-        else
-            moments_level3_kernel<<<persistent, kBuildThreads, 0, s>>>(T, l);
+        else if (launch_pdl(moments_level3_kernel, dim3(persistent), dim3(kBuildThreads), s, T, l) != cudaSuccess)
+            return P3T_ERR_CUDA;
     }
     if (fork && cudaStreamWaitEvent(s, c->join_ev, 0) != cudaSuccess) return P3T_ERR_CUDA;
     return check_launch(c);

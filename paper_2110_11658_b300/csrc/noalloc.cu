@@ -36,7 +36,8 @@ __global__ void keys_kernel(int n, const double *__restrict__ x, const double *_
                             int32_t *__restrict__ perm);
 __global__ void sort_hist_kernel(int n, const uint64_t *__restrict__ keys,
                                  const int32_t *__restrict__ vals, const int32_t *__restrict__ cid,
-                                 int shift, int nblocks, int32_t *__restrict__ hist);
+                                 int shift, int nblocks, int32_t *__restrict__ hist,
+                                 unsigned long long *scan_status, int scan_words, unsigned int *scan_ticket);
 __global__ void sort_scatter_kernel(int n, const uint64_t *__restrict__ kin,
                                     const int32_t *__restrict__ vin, uint64_t *__restrict__ kout,
                                     int32_t *__restrict__ vout, const int32_t *__restrict__ cid,
@@ -128,8 +129,9 @@ extern "C" int p3t_morton_order_noalloc(int64_t n, const double *x, const double
     int32_t *pb[2] = {perm, perm_alt};
     for (int pass = 0; pass < 8; pass++) {
         const int shift = 8 * pass;
-        sort_hist_kernel<<<nb, 256, 0, s>>>(N, kb[pass & 1], pb[pass & 1], nullptr, shift, nb, hist);
-        e = scan_excl_i32_to_i32(hist, hist, 256 * nb, status, &meta->tickets[31], meta, s);
+        sort_hist_kernel<<<nb, 256, 0, s>>>(N, kb[pass & 1], pb[pass & 1], nullptr, shift, nb, hist, status,
+                                            scan_status_words(256 * nb), &meta->tickets[31]);
+        e = scan_excl_i32_to_i32_cleared(hist, hist, 256 * nb, status, &meta->tickets[31], meta, s);
         if (e) return e;
         sort_scatter_kernel<<<nb, 256, 0, s>>>(N, kb[pass & 1], pb[pass & 1], kb[(pass + 1) & 1],
                                                pb[(pass + 1) & 1], nullptr, shift, nb, hist);

@@ -181,6 +181,30 @@ __device__ __forceinline__ bool is_top_cell(const Tree &T, int l, unsigned long 
 }
 
 // ---- error latch ---------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with launch_pdl may be scheduled
+// while the kernel before it on the stream drains; it calls pdl_wait() before its
+// first memory access, which returns once that kernel has completed and its writes
+// are visible (a no-op for a kernel launched the ordinary way).  What overlaps is
+// the launch latency alone.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                                     Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 __device__ __forceinline__ void latch_error(Meta *m, int code)
 {
     atomicCAS(&m->err, 0, code);
@@ -416,6 +440,14 @@ int scan_excl_i32_to_i64(const int32_t *in, int64_t *out, int n, int64_t *total_
 int scan_excl_i32_to_i32(const int32_t *in, int32_t *out, int n, unsigned long long *status,
                          unsigned int *ticket, Meta *meta, cudaStream_t s);
 int scan_status_words(int n);  // status array length for an n-element scan
+int scan_excl_i32_to_i32_cleared(const int32_t *in, int32_t *out, int n, unsigned long long *status,
+                                 unsigned int *ticket, Meta *meta, cudaStream_t s);
+// clears a scan's status words and ticket (one block of a kernel that runs before it)
+__device__ __forceinline__ void clear_scan_state(unsigned long long *status, int nwords, unsigned int *ticket)
+{
+    for (int t = threadIdx.x; t < nwords; t += blockDim.x) status[t] = 0ULL;
+    if (threadIdx.x == 0) *ticket = 0u;
+}
 
 }  // namespace p3t
 

@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(kScanThreads)
     __shared__ unsigned int sh_t;
     __shared__ long long sh_scan[32];
     __shared__ long long sh_pre;
+    pdl_wait();
     if (threadIdx.x == 0) sh_t = atomicAdd(ticket, 1u);
     __syncthreads();
     const int t = (int)sh_t;
@@ -83,6 +84,20 @@ int scan_excl_i32_to_i32(const int32_t *in, int32_t *out, int n, unsigned long l
                          unsigned int *ticket, Meta *meta, cudaStream_t s)
 {
     return run_scan<int32_t, int32_t>(in, out, n, (int32_t *)nullptr, status, ticket, meta, s);
+}
+
+// The same scan with its status words and ticket already cleared by the kernel
+// before it on the stream (scan_status_words(n) words and the ticket), which saves
+// the two clearing steps between them
+int scan_excl_i32_to_i32_cleared(const int32_t *in, int32_t *out, int n, unsigned long long *status,
+                                 unsigned int *ticket, Meta *meta, cudaStream_t s)
+{
+    if (n <= 0) return P3T_OK;
+    const int ntiles = (n + kScanTile - 1) / kScanTile;
+    return launch_pdl(scan_kernel<int32_t, int32_t>, dim3(ntiles), dim3(kScanThreads), s, in, out, n,
+                      (int32_t *)nullptr, status, ticket, meta) == cudaSuccess
+               ? P3T_OK
+               : P3T_ERR_CUDA;
 }
 
 __global__ void set_ticket_kernel(unsigned int *ticket, unsigned int v) { *ticket = v; }
