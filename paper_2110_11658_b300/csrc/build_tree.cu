@@ -1201,30 +1201,50 @@ __global__ void __launch_bounds__(kBuildThreads) moments_leaf_pair_kernel(Tree T
 // The internal node k of the mixed form on three lanes, lane d doing dimension
 // d of every FP64 step (the same operations in the same order as
 // internal_moments<false> + write_node<false>; M and the steps after the box are
-// repeated on the three lanes).  A warp issues about a third of the FP64
-// instructions of one node per lane for the same 32 / 3 nodes' worth of work, and
-// the chain of a level with few nodes is a third as long.  Every lane of the warp
-// calls this (the shuffles); act: the lane holds dimension d of node k.
+// repeated on the three lanes, and lane d sums quadrupole components 2d and 2d + 1).
+// A warp issues about a third of the FP64 instructions of one node per lane for the
+// same 32 / 3 nodes' worth of work.  Every load comes first, so that a node's
+// latency is one round of loads and its chain of FP64 steps (65 to 670 cycles each
+// on this part), which sets the time of the levels with few nodes.  Every lane of
+// the warp calls this (the shuffles); act: the lane holds dimension d of node k.
 __device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool act, int d, int lane0)
 {
     auto sh = [&](double v, int j) { return __shfl_sync(0xffffffffu, v, lane0 + j); };
     auto shf = [&](float v, int j) { return __shfl_sync(0xffffffffu, v, lane0 + j); };
-    auto comp = [&](const double4_32a &v) { return d == 0 ? v.x : (d == 1 ? v.y : v.z); };
     const int c0 = tp.z, nc = act ? tp.w : 0;
-    double M = 0.0, S = 0.0;
-    unsigned long long elo = ~0ULL, ehi = 0ULL;
-    double4_32a cm[8];
-#pragma unroll
-    for (int i = 0; i < 8; i++)
-        if (i < nc) cm[i] = ldcg_d4(&T.comM[c0 + i]);
+    const Cluster &K = T.cl[T.cid_s[act && tp.x < T.n ? tp.x : 0]];
+    // the children's mass, COM, box and double-single COM in dimension d, FP32 mass
+    // and quadrupole components 2d, 2d + 1
+    double cw[8], cc[8], cl0[8], ch0[8];
+    float wh[8], wl[8], wm[8], qa[8], qb[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         if (i < nc) {
-            const double4_32a cl = ldcg_d4(&T.lo[c0 + i]);
-            const double4_32a ch = ldcg_d4(&T.hi[c0 + i]);
-            M = dadd(M, cm[i].w);
-            S = dadd(S, dmul(cm[i].w, comp(cm[i])));
-            const unsigned long long a = enc_double(comp(cl)), b = enc_double(comp(ch));
+            const int c = c0 + i;
+            const double *cm = reinterpret_cast<const double *>(&T.comM[c]);
+            cw[i] = __ldcg(cm + 3);
+            cc[i] = __ldcg(cm + d);
+            cl0[i] = __ldcg(reinterpret_cast<const double *>(&T.lo[c]) + d);
+            ch0[i] = __ldcg(reinterpret_cast<const double *>(&T.hi[c]) + d);
+            const float *w0 = reinterpret_cast<const float *>(&T.wn[wrec(c, 0)]);
+            const float *w3 = reinterpret_cast<const float *>(&T.wn[wrec(c, 3)]);
+            wh[i] = __ldcg(w0 + d);
+            wl[i] = __ldcg(w3 + d);
+            wm[i] = __ldcg(w3 + 3);
+            const float *Qc = T.q32 + 6 * (size_t)c + 2 * d;
+            qa[i] = __ldcg(Qc);
+            qb[i] = __ldcg(Qc + 1);
+        }
+    }
+    const double O = K.frame[d], theta = K.theta;
+    double M = 0.0, S = 0.0;
+    unsigned long long elo = ~0ULL, ehi = 0ULL;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        if (i < nc) {
+            M = dadd(M, cw[i]);
+            S = dadd(S, dmul(cw[i], cc[i]));
+            const unsigned long long a = enc_double(cl0[i]), b = enc_double(ch0[i]);
             elo = a < elo ? a : elo;
             ehi = b > ehi ? b : ehi;
         }
@@ -1232,32 +1252,28 @@ __device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool 
     const double lo = dec_double(elo), hi = dec_double(ehi);
     const double com = M > 0.0 ? ddiv(S, M) : dmul(0.5, dadd(lo, hi));
     // relative to the cluster's frame O: the double-single COM
-    const Cluster &K = T.cl[T.cid_s[act && tp.x < T.n ? tp.x : 0]];
-    const double O = K.frame[d];
     float ch, cl;
     ds_split(dsub(com, O), ch, cl);
     // quadrupole from the children (FP32): each lane's offsets from the double-single
-    // COMs of its dimension (the children's records), then all three
-    auto compf = [&](const float4 &v) { return d == 0 ? v.x : (d == 1 ? v.y : v.z); };
-    float Q[6] = {0, 0, 0, 0, 0, 0};
+    // COMs of its dimension, then all three
+    float Qa = 0.f, Qb = 0.f;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-        float dd = 0.f, Mc = 0.f;
-        if (i < nc) {
-            const float4 w0 = __ldcg(&T.wn[wrec(c0 + i, 0)]), w3 = __ldcg(&T.wn[wrec(c0 + i, 3)]);
-            dd = (compf(w0) - ch) + (compf(w3) - cl);
-            Mc = w3.w;
-        }
+        const float dd = i < nc ? (wh[i] - ch) + (wl[i] - cl) : 0.f;
         const float dx = shf(dd, 0), dy = shf(dd, 1), dz = shf(dd, 2);
         if (i < nc) {
-            const float *Qc = T.q32 + 6 * (size_t)(c0 + i);
+            const float Mc = wm[i];
             const float d2 = dx * dx + dy * dy + dz * dz;
-            Q[0] += __ldcg(Qc + 0) + Mc * (3.f * dx * dx - d2);
-            Q[1] += __ldcg(Qc + 1) + Mc * (3.f * dx * dy);
-            Q[2] += __ldcg(Qc + 2) + Mc * (3.f * dx * dz);
-            Q[3] += __ldcg(Qc + 3) + Mc * (3.f * dy * dy - d2);
-            Q[4] += __ldcg(Qc + 4) + Mc * (3.f * dy * dz);
-            Q[5] += __ldcg(Qc + 5) + Mc * (3.f * dz * dz - d2);
+            if (d == 0) {
+                Qa += qa[i] + Mc * (3.f * dx * dx - d2);
+                Qb += qb[i] + Mc * (3.f * dx * dy);
+            } else if (d == 1) {
+                Qa += qa[i] + Mc * (3.f * dx * dz);
+                Qb += qb[i] + Mc * (3.f * dy * dy - d2);
+            } else {
+                Qa += qa[i] + Mc * (3.f * dy * dz);
+                Qb += qb[i] + Mc * (3.f * dz * dz - d2);
+            }
         }
     }
     // opening radius l/theta + delta (rule 8)
@@ -1269,7 +1285,6 @@ __device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool 
     const double c = dsub(dmul(0.5, dadd(lo, hi)), com);
     const double c2 = dmul(c, c);
     const double cx2 = sh(c2, 0), cy2 = sh(c2, 1), cz2 = sh(c2, 2);
-    const double theta = K.theta;
     double ro2 = INFINITY;
     if (act) {
         const double delta = dsqrt(dadd(dadd(cx2, cy2), cz2));
@@ -1278,30 +1293,40 @@ __device__ __forceinline__ void internal_moments3(Tree &T, int k, int4 tp, bool 
             ro2 = dmul(ro, ro);
         }
     }
-    // the FP32 box relative to O
-    const float blo = __double2float_rn(dsub(lo, O)), bhi = __double2float_rn(dsub(hi, O));
-    const double cx = sh(com, 0), cy = sh(com, 1), cz = sh(com, 2);
-    const double lx = sh(lo, 0), ly = sh(lo, 1), lz = sh(lo, 2);
-    const double hx = sh(hi, 0), hy = sh(hi, 1), hz = sh(hi, 2);
-    const float chx = shf(ch, 0), chy = shf(ch, 1), chz = shf(ch, 2);
-    const float clx = shf(cl, 0), cly = shf(cl, 1), clz = shf(cl, 2);
-    const float blx = shf(blo, 0), bly = shf(blo, 1), blz = shf(blo, 2);
-    const float bhx = shf(bhi, 0), bhy = shf(bhi, 1), bhz = shf(bhi, 2);
-    if (act && d == 0) {
-        T.comM[k] = make_double4_32a(cx, cy, cz, M);
-        T.lo[k] = make_double4_32a(lx, ly, lz, ro2);
-        T.hi[k] = make_double4_32a(hx, hy, hz, 0.0);
-        float2 *q2 = reinterpret_cast<float2 *>(T.q32 + 6 * (size_t)k);
-        q2[0] = make_float2(Q[0], Q[1]);
-        q2[1] = make_float2(Q[2], Q[3]);
-        q2[2] = make_float2(Q[4], Q[5]);
-        const auto w = wrec_at(T.wn, k);
-        w[0] = make_float4(chx, chy, chz, __double2float_rn(ro2));
-        w[1] = make_float4(blx, bly, blz, __int_as_float(tp.z));
-        w[2] = make_float4(bhx, bhy, bhz, __int_as_float(tp.w));
-        w[3] = make_float4(clx, cly, clz, __double2float_rn(M));
-        w[4] = make_float4(Q[0], Q[1], Q[2], Q[3]);
-        w[5] = make_float4(Q[4], Q[5], 0.f, 0.f);
+    // records: lane d writes its dimension (and its quadrupole components), lane 0
+    // the rest; the FP32 box relative to O
+    if (act) {
+        double *cm = reinterpret_cast<double *>(&T.comM[k]);
+        double *bl = reinterpret_cast<double *>(&T.lo[k]);
+        double *bh = reinterpret_cast<double *>(&T.hi[k]);
+        cm[d] = com;
+        bl[d] = lo;
+        bh[d] = hi;
+        reinterpret_cast<float2 *>(T.q32 + 6 * (size_t)k)[d] = make_float2(Qa, Qb);
+        float *w0 = reinterpret_cast<float *>(&T.wn[wrec(k, 0)]);
+        float *w1 = reinterpret_cast<float *>(&T.wn[wrec(k, 1)]);
+        float *w2 = reinterpret_cast<float *>(&T.wn[wrec(k, 2)]);
+        float *w3 = reinterpret_cast<float *>(&T.wn[wrec(k, 3)]);
+        float *w4 = reinterpret_cast<float *>(&T.wn[wrec(k, 4)]);  // w4, w5: Q0 .. Q5, 0, 0
+        w0[d] = ch;
+        w1[d] = __double2float_rn(dsub(lo, O));
+        w2[d] = __double2float_rn(dsub(hi, O));
+        w3[d] = cl;
+        if (d < 2) {
+            reinterpret_cast<float2 *>(w4)[d] = make_float2(Qa, Qb);
+        } else {
+            float *w5 = reinterpret_cast<float *>(&T.wn[wrec(k, 5)]);
+            *reinterpret_cast<float4 *>(w5) = make_float4(Qa, Qb, 0.f, 0.f);
+        }
+        if (d == 0) {
+            cm[3] = M;
+            bl[3] = ro2;
+            bh[3] = 0.0;
+            w0[3] = __double2float_rn(ro2);
+            w1[3] = __int_as_float(tp.z);
+            w2[3] = __int_as_float(tp.w);
+            w3[3] = __double2float_rn(M);
+        }
     }
 }
 
@@ -1535,7 +1560,8 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     for (int l = kLevels - 1; l >= 0; l--) {
         if (q64)
             moments_level_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, l, P.theta);
-        else if (launch_pdl(moments_level3_kernel, dim3(persistent), dim3(kBuildThreads), s, T, l) != cudaSuccess)
+        else if (launch_pdl(moments_level3_kernel, dim3(2 * persistent), dim3(kBuildThreads / 2), s, T, l) !=
+                 cudaSuccess)  // (blocks of 128 threads: three resident per SM at 160 registers)
             return P3T_ERR_CUDA;
     }
     if (fork && cudaStreamWaitEvent(s, c->join_ev, 0) != cudaSuccess) return P3T_ERR_CUDA;
