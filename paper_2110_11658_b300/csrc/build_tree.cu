@@ -1048,7 +1048,8 @@ __device__ void leaf_moments(Tree &T, int k, int4 tp, double theta)
 // FP32 quadrupole and the double-single COM (relative to the frame O) passed in
 __device__ __forceinline__ void write_leaf_mixed(Tree &T, int k, int4 tp, double M, const double com[3],
                                                  const double lo[3], const double hi[3], const float Q[6],
-                                                 const float ch[3], const float cl[3], const Cluster &K)
+                                                 const float ch[3], const float cl[3], const float blo[3],
+                                                 const float bhi[3], const Cluster &K)
 {
     const double theta = K.theta;
     double l = dsub(hi[0], lo[0]);
@@ -1070,13 +1071,10 @@ __device__ __forceinline__ void write_leaf_mixed(Tree &T, int k, int4 tp, double
     q2[0] = make_float2(Q[0], Q[1]);
     q2[1] = make_float2(Q[2], Q[3]);
     q2[2] = make_float2(Q[4], Q[5]);
-    const double *O = K.frame;
     const auto w = wrec_at(T.wn, k);
     w[0] = make_float4(ch[0], ch[1], ch[2], __double2float_rn(ro2));
-    w[1] = make_float4(__double2float_rn(dsub(lo[0], O[0])), __double2float_rn(dsub(lo[1], O[1])),
-                       __double2float_rn(dsub(lo[2], O[2])), __int_as_float(-1 - tp.x));
-    w[2] = make_float4(__double2float_rn(dsub(hi[0], O[0])), __double2float_rn(dsub(hi[1], O[1])),
-                       __double2float_rn(dsub(hi[2], O[2])), __int_as_float(tp.y));
+    w[1] = make_float4(blo[0], blo[1], blo[2], __int_as_float(-1 - tp.x));
+    w[2] = make_float4(bhi[0], bhi[1], bhi[2], __int_as_float(tp.y));
     w[3] = make_float4(cl[0], cl[1], cl[2], __double2float_rn(M));
     w[4] = make_float4(Q[0], Q[1], Q[2], Q[3]);
     w[5] = make_float4(Q[4], Q[5], 0.f, 0.f);
@@ -1094,10 +1092,15 @@ __device__ __forceinline__ void leaf_finish_mixed(Tree &T, int k, int4 tp, doubl
     const Cluster &K = T.cl[T.cid_s[tp.x < T.n ? tp.x : 0]];
     float ch[3], cl[3];
     for (int d = 0; d < 3; d++) ds_split(dsub(com[d], K.frame[d]), ch[d], cl[d]);
-    float Q[6] = {0, 0, 0, 0, 0, 0};
+    // the FP32 box relative to O: RN(RN(x - O)) rises with x, so the min and max of the
+    // particles' high parts are the rounded min and max of x - O (the box the FP64 path
+    // would round), without the FP64 steps
+    float Q[6] = {0, 0, 0, 0, 0, 0}, blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
 #pragma unroll 4
     for (int i = tp.x; i < tp.x + tp.y; i++) {
         const float4 h = T.ph[i], l = T.pl[i];
+        blo[0] = fminf(blo[0], h.x), blo[1] = fminf(blo[1], h.y), blo[2] = fminf(blo[2], h.z);
+        bhi[0] = fmaxf(bhi[0], h.x), bhi[1] = fmaxf(bhi[1], h.y), bhi[2] = fmaxf(bhi[2], h.z);
         const float m = h.w;
         const float dx = (h.x - ch[0]) + (l.x - cl[0]);
         const float dy = (h.y - ch[1]) + (l.y - cl[1]);
@@ -1110,7 +1113,7 @@ __device__ __forceinline__ void leaf_finish_mixed(Tree &T, int k, int4 tp, doubl
         Q[4] += m * (3.f * dy * dz);
         Q[5] += m * (3.f * dz * dz - r2);
     }
-    write_leaf_mixed(T, k, tp, M, com, lo, hi, Q, ch, cl, K);
+    write_leaf_mixed(T, k, tp, M, com, lo, hi, Q, ch, cl, blo, bhi, K);
 }
 
 // Two mixed-form leaves on one lane (ka, kb; -1: none), their particles taken as one
