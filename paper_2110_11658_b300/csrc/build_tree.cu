@@ -648,6 +648,7 @@ __global__ void __launch_bounds__(kBuildThreads)
     }
     __syncthreads();
     const int i = t0 + tid;
+    if (i < n) T.gflag[i] = 0;  // (the finish pass flags the walk groups)
     int sh = 0, lam = -1;
     if (i < n) {
         int cs, ce;
@@ -1496,8 +1497,9 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     // the per-tile node counts, the nodes, their counts and children), or level by
     // level for a rank's range build (its top cells split whatever their count) and
     // for leaf capacities past the flat pass's window
-    if (cudaMemsetAsync(T.gflag, 0, n, s) != cudaSuccess) return P3T_ERR_CUDA;
-    if (!range && P.leaf_cap <= kFlatMaxLeaf) {
+    const bool flat = !range && P.leaf_cap <= kFlatMaxLeaf;
+    if (!flat && cudaMemsetAsync(T.gflag, 0, n, s) != cudaSuccess) return P3T_ERR_CUDA;
+    if (flat) {
         // per-particle levels in the group index buffer and per-tile counts in the sort
         // histogram (both free until the groups): 22 ceil(n / 256) + 1 <= 256 ceil(n / 1024)
         const int ntiles = grid_n;

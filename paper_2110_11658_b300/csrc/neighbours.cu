@@ -964,8 +964,13 @@ static void size_row_scratch(p3t_ctx *c, long long total)
 // capacity of each target's row (key order) from the last count of its particle
 __global__ void __launch_bounds__(256)
     row_caps_kernel(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ count,
-                    int32_t *__restrict__ cap)
+                    int32_t *__restrict__ cap, int *row_over, unsigned long long *scan_status, int scan_words,
+                    unsigned int *scan_ticket)
 {
+    if (blockIdx.x == 0) {  // the layout's overflow flag and its scan's state
+        clear_scan_state(scan_status, scan_words, scan_ticket);
+        if (threadIdx.x == 0) *row_over = 0;
+    }
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int cnt = count[perm[s]];
@@ -973,9 +978,11 @@ __global__ void __launch_bounds__(256)
 }
 
 // equal rows of `cap` entries (no counts of these particles yet)
-__global__ void __launch_bounds__(256) row_uniform_kernel(int n, long long cap, int64_t *__restrict__ row_off)
+__global__ void __launch_bounds__(256) row_uniform_kernel(int n, long long cap, int64_t *__restrict__ row_off,
+                                                          int *row_over)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) *row_over = 0;
     if (s <= n) row_off[s] = (long long)s * cap;
 }
 
@@ -987,17 +994,18 @@ int prepare_rows(p3t_ctx *c)
 {
     c->rows_cap_used = 0;
     if (c->row_cap <= 0 || !c->row_scratch || c->n <= 0) return 0;
-    if (cudaMemsetAsync(&c->meta->row_over, 0, sizeof(int), c->stream) != cudaSuccess) return 0;
     const int n = c->n;
     if (c->counts_n == n) {
-        row_caps_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->tree.perm, c->nbr_count, c->row_list);
-        if (scan_excl_i32_to_i64(c->row_list, c->row_off, n, c->row_off + n, c->scan_status,
-                                 &c->meta->tickets[26], c->meta, c->stream) != P3T_OK)
+        row_caps_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->tree.perm, c->nbr_count, c->row_list,
+                                                               &c->meta->row_over, c->scan_status,
+                                                               scan_status_words(n), &c->meta->tickets[26]);
+        if (scan_excl_i32_to_i64_cleared(c->row_list, c->row_off, n, c->row_off + n, c->scan_status,
+                                         &c->meta->tickets[26], c->meta, c->stream) != P3T_OK)
             return 0;
     } else {
         const long long cap = (long long)(c->row_scratch_entries / (size_t)n);
         if (cap < 1) return 0;
-        row_uniform_kernel<<<(n + 256) / 256, 256, 0, c->stream>>>(n, cap, c->row_off);
+        row_uniform_kernel<<<(n + 256) / 256, 256, 0, c->stream>>>(n, cap, c->row_off, &c->meta->row_over);
     }
     c->rows_cap_used = 1;
     return 1;

@@ -442,6 +442,8 @@ int scan_excl_i32_to_i32(const int32_t *in, int32_t *out, int n, unsigned long l
 int scan_status_words(int n);  // status array length for an n-element scan
 int scan_excl_i32_to_i32_cleared(const int32_t *in, int32_t *out, int n, unsigned long long *status,
                                  unsigned int *ticket, Meta *meta, cudaStream_t s);
+int scan_excl_i32_to_i64_cleared(const int32_t *in, int64_t *out, int n, int64_t *total_dev,
+                                 unsigned long long *status, unsigned int *ticket, Meta *meta, cudaStream_t s);
 // clears a scan's status words and ticket (one block of a kernel that runs before it)
 __device__ __forceinline__ void clear_scan_state(unsigned long long *status, int nwords, unsigned int *ticket)
 {

@@ -100,6 +100,17 @@ int scan_excl_i32_to_i32_cleared(const int32_t *in, int32_t *out, int n, unsigne
                : P3T_ERR_CUDA;
 }
 
+int scan_excl_i32_to_i64_cleared(const int32_t *in, int64_t *out, int n, int64_t *total_dev,
+                                 unsigned long long *status, unsigned int *ticket, Meta *meta, cudaStream_t s)
+{
+    if (n <= 0) return P3T_ERR_INVALID_ARG;
+    const int ntiles = (n + kScanTile - 1) / kScanTile;
+    return launch_pdl(scan_kernel<int32_t, int64_t>, dim3(ntiles), dim3(kScanThreads), s, in, out, n, total_dev,
+                      status, ticket, meta) == cudaSuccess
+               ? P3T_OK
+               : P3T_ERR_CUDA;
+}
+
 __global__ void set_ticket_kernel(unsigned int *ticket, unsigned int v) { *ticket = v; }
 
 // The scan above with tile 0's ticket never handed out: the block holding tile

@@ -11,10 +11,11 @@ namespace p3t {
 // block; the counts of both kinds go to Meta.cell_forms: the r^-5 walk runs when no
 // cluster is outside that range, the r^-3 walk otherwise (for every cluster, so that
 // the form is one per launch).
-__global__ void __launch_bounds__(256) cell_forms_kernel(Tree T)
+__global__ void __launch_bounds__(256) cell_forms_kernel(Tree T, unsigned int *ticket1, unsigned int *ticket2)
 {
     __shared__ int cnt[2];
     if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) *ticket1 = 0u, *ticket2 = 0u;  // the two walks' group tickets
     __syncthreads();
     int nf = 0, ns = 0;
     for (int c = threadIdx.x; c < T.n_clusters; c += blockDim.x) {
@@ -62,8 +63,6 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     a.rows = rows ? c->row_scratch : nullptr;
     a.row_off = c->row_off;
     a.row_entries = (long long)c->row_scratch_entries;
-    if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess)
-        return P3T_ERR_CUDA;
     const bool quad = P.quadrupole != 0;
     const bool want_pot = pot != nullptr;
     int e;
@@ -71,6 +70,7 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
     // per-cluster table the host cannot tell, so they are compiled in)
     const bool shell = fuse_nbr && (!c->uniform_params || P.r_list > P.r_out);
     if (c->built_precision == P3T_FP64) {
+        if (cudaMemsetAsync(a.ticket, 0, sizeof(unsigned int), c->stream) != cudaSuccess) return P3T_ERR_CUDA;
         e = wpg == 1 ? dispatch_tpl<double, 0, false, 0>(c, a, want_pot, quad)
                      : (wpg == 2 ? dispatch_walk_wpg<2, 0>(c, a, 0, false, want_pot, quad)
                                  : dispatch_walk_wpg<4, 0>(c, a, 0, false, want_pot, quad));
@@ -78,16 +78,12 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
         // the r^-5 walk, then the r^-3 walk: one of the two finds its form chosen
         // (cell_forms_kernel) and walks every group, the other returns at once
         const int nbr = !fuse_nbr ? 0 : (rows ? 2 : 1);
-        cell_forms_kernel<<<1, 256, 0, c->stream>>>(c->tree);
+        WalkArgs b = a;
+        b.ticket = &c->meta->tickets[24];
+        cell_forms_kernel<<<1, 256, 0, c->stream>>>(c->tree, a.ticket, b.ticket);
         e = check_launch(c);
         if (!e) e = mixed_walk<1>(c, a, wpg, nbr, shell, want_pot, quad);
-        if (!e) {
-            WalkArgs b = a;
-            b.ticket = &c->meta->tickets[24];
-            e = cudaMemsetAsync(b.ticket, 0, sizeof(unsigned int), c->stream) == cudaSuccess
-                    ? mixed_walk<2>(c, b, wpg, nbr, shell, want_pot, quad)
-                    : P3T_ERR_CUDA;
-        }
+        if (!e) e = mixed_walk<2>(c, b, wpg, nbr, shell, want_pot, quad);
     }
     if (e == P3T_OK && fuse_nbr) {
         c->walk_counted = 1;
