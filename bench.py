@@ -40,8 +40,8 @@ if ROOT not in sys.path:
 # 10^6-particle Plummer walk of the timed step, which also writes the neighbour rows.
 # Valid only at that N and for the kernel sources it was measured on (their hashes):
 # otherwise the roofline's traffic is null.
-WALK_TRAFFIC = {"sources": {"walk.cu": "d468b674e174d09e", "walk_f1.cu": "2881d95896a10898", "walk_kernel.cuh": "5c61d53f45a3fb26", "p3t_internal.cuh": "e3c22a891e7bcdf2"},
-                "n": 1000000, "bytes": 299048704 + 504167168}
+WALK_TRAFFIC = {"sources": {"walk.cu": "258642409f61014f", "walk_f1.cu": "2881d95896a10898", "walk_kernel.cuh": "5c61d53f45a3fb26", "p3t_internal.cuh": "806545f59ff0c51a"},
+                "n": 1000000, "bytes": 303516416 + 507997696}
 
 N_DEFAULT = 1_000_000
 THETA = 0.4
@@ -512,13 +512,14 @@ def bench_config(n, w, args, world):
 
 # kernels launched by one step: build = metadata, cluster table, cluster parameters,
 # bbox, cube, keys (6) + radix sort 8 x (histogram, scan, scatter) + gather + topology
-# root, 21 levels, finish + group scan, first, finish, frames, walk order (bins, scan,
-# scatter) + moments leaves and 21 levels; far force 5 (the rows' layout from the last
-# counts and its scan, the cell-form flags, then the walk in its two cell forms, one of
-# which returns at once; the walk also counts the neighbours and writes the rows);
-# neighbours = offsets scan, fill, row binning by length (count, list) and nine
-# row-sort size classes; kick 1; drift 1 (103, as the ncu launch list of the step shows)
-KERNELS_PER_STEP = (6 + 8 * 3 + 1 + (1 + 21 + 1) + 4 + 3 + (1 + 21)) + 5 + (2 + 2 + 9) + 1 + 1
+# (per-particle levels, their scan, level table, nodes, counts and children) + group
+# scan, first, finish, frames, walk order (bins, scan, scatter) + moments leaves and 21
+# levels; far force 5 (the rows' layout from the last counts and its scan, the
+# cell-form flags, then the walk in its two cell forms, one of which returns at once;
+# the walk also counts the neighbours and writes the rows); neighbours = offsets scan,
+# fill, row binning by length (count, list) and nine row-sort size classes; kick 1;
+# drift 1 (85, as the ncu launch list of the step shows)
+KERNELS_PER_STEP = (6 + 8 * 3 + 1 + 5 + 4 + 3 + (1 + 21)) + 5 + (2 + 2 + 9) + 1 + 1
 
 
 def run_reference(args, rank, world):
