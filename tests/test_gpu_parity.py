@@ -380,3 +380,21 @@ def test_cell_forms_agree():
     for a in (fast["a"], a3):
         err = rel_err(a, f["a"])
         assert np.median(err) <= 1e-5 and np.percentile(err, 99) <= 1e-4
+
+
+@pytest.mark.parametrize("leaf", [2, 128, 129, 300])
+def test_topology_flat_and_level_forms(leaf):
+    """The topology is built flat (per-particle first and last levels, one scan) for
+    leaf capacities up to 128 and level by level above: both give the oracle's tree
+    node for node, with a clump of duplicates (level-21 leaves) in the mix."""
+    c = synth.plummer(30000, 31, masses="kroupa")
+    c.x[:400] = c.x[7]
+    c.y[:400] = c.y[7]
+    c.z[:400] = c.z[7]
+    prm = p3t.Params(theta=0.5, r_in=0.003, r_out=0.03, r_list=0.03, leaf_cap=leaf, group_size=32)
+    g = run_gpu(c, prm, pot=False, nbr=False)
+    t = oracle.Tree(c.x, c.y, c.z, c.m, 0.5, 0.03, leaf_cap=leaf, group_size=32)
+    assert_tree_equal(g["tree"], t.export(), fp64_moments=False)
+    f = t.far(0.003)
+    assert np.array_equal(g["g_cells"], f["n_cell"])
+    assert np.array_equal(g["g_parts"], f["n_part"])
