@@ -9,6 +9,7 @@ __global__ void __launch_bounds__(256)
                 const A *__restrict__ az, double *__restrict__ vx, double *__restrict__ vy,
                 double *__restrict__ vz)
 {
+    pdl_wait();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         // v + h*a with the product and the sum each rounded (no contraction)
         vx[i] = dadd(vx[i], dmul(h, (double)ax[i]));
@@ -22,6 +23,7 @@ __global__ void __launch_bounds__(256)
                  double *__restrict__ z, const double *__restrict__ vx,
                  const double *__restrict__ vy, const double *__restrict__ vz)
 {
+    pdl_wait();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         x[i] = dadd(x[i], dmul(dt, vx[i]));
         y[i] = dadd(y[i], dmul(dt, vy[i]));
@@ -35,12 +37,13 @@ int kick(p3t_ctx *c, double dt, const void *ax, const void *ay, const void *az, 
     const double h = 0.5 * dt;
     const int n = c->n;
     const int grid = (n + 255) / 256 < 8 * c->sm_count ? (n + 255) / 256 : 8 * c->sm_count;
-    if (c->built_precision == P3T_FP64)
-        kick_kernel<double><<<grid, 256, 0, c->stream>>>(n, h, (const double *)ax, (const double *)ay,
-                                                         (const double *)az, vx, vy, vz);
-    else
-        kick_kernel<float><<<grid, 256, 0, c->stream>>>(n, h, (const float *)ax, (const float *)ay,
-                                                        (const float *)az, vx, vy, vz);
+    const cudaError_t r =
+        c->built_precision == P3T_FP64
+            ? launch_pdl(kick_kernel<double>, dim3(grid), dim3(256), c->stream, n, h, (const double *)ax,
+                         (const double *)ay, (const double *)az, vx, vy, vz)
+            : launch_pdl(kick_kernel<float>, dim3(grid), dim3(256), c->stream, n, h, (const float *)ax,
+                         (const float *)ay, (const float *)az, vx, vy, vz);
+    if (r != cudaSuccess) return P3T_ERR_CUDA;
     return check_launch(c);
 }
 
@@ -48,7 +51,8 @@ int drift(p3t_ctx *c, int n, double dt, double *x, double *y, double *z, const d
           const double *vy, const double *vz)
 {
     const int grid = (n + 255) / 256 < 8 * c->sm_count ? (n + 255) / 256 : 8 * c->sm_count;
-    drift_kernel<<<grid, 256, 0, c->stream>>>(n, dt, x, y, z, vx, vy, vz);
+    if (launch_pdl(drift_kernel, dim3(grid), dim3(256), c->stream, n, dt, x, y, z, vx, vy, vz) != cudaSuccess)
+        return P3T_ERR_CUDA;
     return check_launch(c);
 }
 

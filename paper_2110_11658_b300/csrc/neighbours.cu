@@ -461,6 +461,7 @@ __device__ __forceinline__ int row_class(int len)
 __global__ void row_class_count_kernel(int n, const int64_t *__restrict__ offs, long long capacity,
                                        Meta *meta)
 {
+    pdl_wait();
     __shared__ int cnt[kRowClasses];
     if (threadIdx.x < kRowClasses) cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -480,6 +481,7 @@ __global__ void row_class_count_kernel(int n, const int64_t *__restrict__ offs, 
 __global__ void row_class_fill_kernel(int n, const int64_t *__restrict__ offs, long long capacity,
                                       Meta *meta, int32_t *list)
 {
+    pdl_wait();
     __shared__ int cnt[kRowClasses], base[kRowClasses];
     if (offs[n] > capacity) return;
     const int stride = gridDim.x * blockDim.x;
@@ -725,6 +727,7 @@ __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_tiny_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
                          int32_t *idx, RowSrc src)
 {
+    pdl_wait();
     static_assert(kClassLen[C + 1] == 4, "four entries per row");
     int start = 0;
 #pragma unroll
@@ -760,6 +763,7 @@ __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_reg_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
                         int32_t *idx, RowSrc src)
 {
+    pdl_wait();
     for_class_rows<C>(meta, list, offs, idx, src, [](int32_t *row, int len, const RowLoad &ld) {
         warp_bitonic_row<K>(row, len, ld);
     });
@@ -770,6 +774,7 @@ __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_tr_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
                        int32_t *idx, RowSrc src)
 {
+    pdl_wait();
     __shared__ int32_t sbuf[kSortWarps][33 * K];
     int32_t *sb = sbuf[threadIdx.x >> 5];
     for_class_rows<C>(meta, list, offs, idx, src, [&](int32_t *row, int len, const RowLoad &ld) {
@@ -783,6 +788,7 @@ __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_smem_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
                          int32_t *idx, RowSrc src)
 {
+    pdl_wait();
     __shared__ int32_t sbuf[kSortWarps][kClassLen[C + 1]];
     const int lane = threadIdx.x & 31;
     int32_t *sb = sbuf[threadIdx.x >> 5];
@@ -814,6 +820,7 @@ __global__ void __launch_bounds__(kSortWarps * 32)
     row_sort_global_kernel(const Meta *meta, const int32_t *list, const int64_t *__restrict__ offs,
                            int32_t *idx, RowSrc src)
 {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     for_class_rows<C>(meta, list, offs, idx, src, [&](int32_t *row, int len, const RowLoad &ld) {
         if (ld.sr) {
@@ -833,7 +840,9 @@ static int launch_sort(p3t_ctx *c, Kern kern, const int64_t *offsets, int32_t *i
             cudaSuccess ||
         per_sm < 1)
         return P3T_ERR_CUDA;
-    kern<<<per_sm * c->sm_count, kSortWarps * 32, 0, st>>>(c->meta, c->row_list, offsets, idx, src);
+    if (launch_pdl(kern, dim3(per_sm * c->sm_count), dim3(kSortWarps * 32), st, (const Meta *)c->meta,
+                   (const int32_t *)c->row_list, offsets, idx, src) != cudaSuccess)
+        return P3T_ERR_CUDA;
     return check_launch(c);
 }
 
@@ -847,8 +856,10 @@ static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long
     if (cudaMemsetAsync(c->meta->row_class, 0, sizeof(c->meta->row_class), s) != cudaSuccess)
         return P3T_ERR_CUDA;
     const int grid = (int)std::min<long long>(((long long)n + 255) / 256, 4LL * c->sm_count);
-    row_class_count_kernel<<<grid, 256, 0, s>>>(n, offsets, capacity, c->meta);
-    row_class_fill_kernel<<<grid, 256, 0, s>>>(n, offsets, capacity, c->meta, c->row_list);
+    if (launch_pdl(row_class_count_kernel, dim3(grid), dim3(256), s, n, offsets, capacity, c->meta) != cudaSuccess ||
+        launch_pdl(row_class_fill_kernel, dim3(grid), dim3(256), s, n, offsets, capacity, c->meta, c->row_list) !=
+            cudaSuccess)
+        return P3T_ERR_CUDA;
     int e = check_launch(c);
     if (e) return e;
     // the length classes sort disjoint rows: the longest class on the context's stream,
@@ -967,6 +978,7 @@ __global__ void __launch_bounds__(256)
                     int32_t *__restrict__ cap, int *row_over, unsigned long long *scan_status, int scan_words,
                     unsigned int *scan_ticket)
 {
+    pdl_wait();
     if (blockIdx.x == 0) {  // the layout's overflow flag and its scan's state
         clear_scan_state(scan_status, scan_words, scan_ticket);
         if (threadIdx.x == 0) *row_over = 0;
@@ -996,9 +1008,10 @@ int prepare_rows(p3t_ctx *c)
     if (c->row_cap <= 0 || !c->row_scratch || c->n <= 0) return 0;
     const int n = c->n;
     if (c->counts_n == n) {
-        row_caps_kernel<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->tree.perm, c->nbr_count, c->row_list,
-                                                               &c->meta->row_over, c->scan_status,
-                                                               scan_status_words(n), &c->meta->tickets[26]);
+        if (launch_pdl(row_caps_kernel, dim3((n + 255) / 256), dim3(256), c->stream, n, (const int32_t *)c->tree.perm,
+                       (const int32_t *)c->nbr_count, c->row_list, &c->meta->row_over, c->scan_status,
+                       scan_status_words(n), &c->meta->tickets[26]) != cudaSuccess)
+            return 0;
         if (scan_excl_i32_to_i64_cleared(c->row_list, c->row_off, n, c->row_off + n, c->scan_status,
                                          &c->meta->tickets[26], c->meta, c->stream) != P3T_OK)
             return 0;

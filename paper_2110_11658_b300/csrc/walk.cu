@@ -13,6 +13,7 @@ namespace p3t {
 // the form is one per launch).
 __global__ void __launch_bounds__(256) cell_forms_kernel(Tree T, unsigned int *ticket1, unsigned int *ticket2)
 {
+    pdl_wait();
     __shared__ int cnt[2];
     if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) *ticket1 = 0u, *ticket2 = 0u;  // the two walks' group tickets
@@ -80,8 +81,9 @@ int far_force(p3t_ctx *c, void *ax, void *ay, void *az, double *pot, int64_t *nc
         const int nbr = !fuse_nbr ? 0 : (rows ? 2 : 1);
         WalkArgs b = a;
         b.ticket = &c->meta->tickets[24];
-        cell_forms_kernel<<<1, 256, 0, c->stream>>>(c->tree, a.ticket, b.ticket);
-        e = check_launch(c);
+        e = launch_pdl(cell_forms_kernel, dim3(1), dim3(256), c->stream, c->tree, a.ticket, b.ticket) == cudaSuccess
+                ? check_launch(c)
+                : P3T_ERR_CUDA;
         if (!e) e = mixed_walk<1>(c, a, wpg, nbr, shell, want_pot, quad);
         if (!e) e = mixed_walk<2>(c, b, wpg, nbr, shell, want_pot, quad);
     }

@@ -874,6 +874,7 @@ __global__ void __launch_bounds__(walk_block_threads<WPG>(),
                                   TPL == 1 ? (NBR == 2 ? 5 : kMinBlocksTpl1) * kWalkWarps / (WPG == 1 ? kWalkWarps : WPG) : 3)
     walk_kernel(WalkArgs P)
 {
+    pdl_wait();
     static_assert(WPG == 1 || TPL == 1, "several warps per group hold one target per lane");
     static_assert(FORM == 0 || sizeof(Real) == 4, "cell forms: mixed walks");
     extern __shared__ __align__(16) char smem[];
@@ -1355,7 +1356,8 @@ static int launch_walk(p3t_ctx *c, const WalkArgs &a)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
         per_sm < 1)
         return P3T_ERR_CUDA;
-    kern<<<per_sm * c->sm_count, threads, smem, c->stream>>>(a);
+    if (launch_pdl_smem(kern, dim3(per_sm * c->sm_count), dim3(threads), smem, c->stream, a) != cudaSuccess)
+        return P3T_ERR_CUDA;
     return check_launch(c);
 }
 
