@@ -40,8 +40,8 @@ if ROOT not in sys.path:
 # 10^6-particle Plummer walk of the timed step, which also writes the neighbour rows.
 # Valid only at that N and for the kernel sources it was measured on (their hashes):
 # otherwise the roofline's traffic is null.
-WALK_TRAFFIC = {"sources": {"walk.cu": "258642409f61014f", "walk_f1.cu": "2881d95896a10898", "walk_kernel.cuh": "5c61d53f45a3fb26", "p3t_internal.cuh": "806545f59ff0c51a"},
-                "n": 1000000, "bytes": 303516416 + 507997696}
+WALK_TRAFFIC = {"sources": {"walk.cu": "9623c7c1f07c3515", "walk_f1.cu": "2881d95896a10898", "walk_kernel.cuh": "93d2e360329e8c2b", "p3t_internal.cuh": "1b7baccf169f4625"},
+                "n": 1000000, "bytes": 302835968 + 506728192}
 
 N_DEFAULT = 1_000_000
 THETA = 0.4
