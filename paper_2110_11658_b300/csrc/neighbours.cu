@@ -64,6 +64,10 @@ __global__ void __launch_bounds__(kNbrWarps * 32) nbr_kernel(NbrArgs P)
     Meta *meta = T.meta;
     const int ng = meta->n_groups;
     const int nn = meta->n_nodes;
+    // the fill pass runs right before the rows' length classes are counted: it clears
+    // their counters (block 0, before any return)
+    if (FILL && blockIdx.x == 0 && threadIdx.x < (int)(sizeof(meta->row_class) / sizeof(int)))
+        meta->row_class[threadIdx.x] = 0;
     bool allowed = true;
     if (FILL) allowed = P.offs[T.n] <= P.capacity;
     if (FILL && !allowed) {
@@ -853,8 +857,7 @@ static int sort_rows(p3t_ctx *c, const int64_t *offsets, int32_t *idx, long long
 {
     cudaStream_t s = c->stream;
     const int n = c->n;
-    if (cudaMemsetAsync(c->meta->row_class, 0, sizeof(c->meta->row_class), s) != cudaSuccess)
-        return P3T_ERR_CUDA;
+    // (Meta.row_class was cleared by the fill pass launched just before)
     const int grid = (int)std::min<long long>(((long long)n + 255) / 256, 4LL * c->sm_count);
     if (launch_pdl(row_class_count_kernel, dim3(grid), dim3(256), s, n, offsets, capacity, c->meta) != cudaSuccess ||
         launch_pdl(row_class_fill_kernel, dim3(grid), dim3(256), s, n, offsets, capacity, c->meta, c->row_list) !=
