@@ -209,3 +209,32 @@ def test_batch_with_a_cluster_outside_the_r5_range():
         got = ab[seg[k]:seg[k + 1]]
         err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
         assert np.median(err) <= 1e-5 and np.percentile(err, 99) <= 1e-4, (k, np.median(err), np.percentile(err, 99))
+
+
+@pytest.mark.parametrize("leaf", [1, 128])
+def test_batch_flat_topology_leaf_caps(leaf):
+    """The flat topology of a batched build at both ends of its window (leaf capacity 1
+    and 128), with a cluster of coincident points (one level-21 leaf): each cluster's
+    forces equal its build alone bit for bit, and its walk counts the oracle's."""
+    cl = _ensemble()[:6]
+    n0 = 300
+    cl.append(synth.Cluster(np.full(n0, 40.0), np.full(n0, -2.0), np.full(n0, 0.5), np.full(n0, 1.0 / n0),
+                            *(np.zeros(n0) for _ in range(3))))
+    all_, seg = _concat(cl)
+    prm = p3t.Params(theta=0.5, r_in=0.005, r_out=0.05, r_list=0.05, leaf_cap=leaf, group_size=32)
+    ctx = p3t.Context(prm)
+    x, y, z, m = to_dev(all_.x), to_dev(all_.y), to_dev(all_.z), to_dev(all_.m)
+    ctx.build_tree_batch(torch.from_numpy(seg).to(DEV), x, y, z, m)
+    n = all_.n
+    a = [torch.empty(n, dtype=ctx.acc_dtype, device=DEV) for _ in range(3)]
+    ctx.far_force(*a)
+    ctx.check()
+    ab = torch.stack(a, 1).double().cpu().numpy()
+    for k, c in enumerate(cl):
+        s0, s1 = seg[k], seg[k + 1]
+        g = run_gpu(c, prm, pot=False, nbr=False)
+        assert np.array_equal(ab[s0:s1], g["a"])
+        t = oracle.Tree(c.x, c.y, c.z, c.m, 0.5, 0.05, leaf_cap=leaf, group_size=32)
+        f = t.far(0.005)
+        assert np.array_equal(g["g_cells"], f["n_cell"])
+        assert np.array_equal(g["g_parts"], f["n_part"])
