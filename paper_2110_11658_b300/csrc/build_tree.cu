@@ -1560,13 +1560,28 @@ int build_tree(p3t_ctx *c, int n, int n_clusters, const int64_t *seg, const doub
     const bool q64 = P.precision == P3T_FP64;
     if (q64)
         moments_leaf_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, P.theta);
-    else if (launch_pdl(moments_leaf_pair_kernel, dim3(persistent), dim3(kBuildThreads), s, T) != cudaSuccess)
+    else {
+        int leaf_blocks = 0;  // one resident wave (a grid-stride loop over the leaves)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&leaf_blocks, moments_leaf_pair_kernel, kBuildThreads, 0) !=
+                cudaSuccess ||
+            leaf_blocks < 1 ||
+            launch_pdl(moments_leaf_pair_kernel, dim3(leaf_blocks * c->sm_count), dim3(kBuildThreads), s, T) !=
+                cudaSuccess)
+            return P3T_ERR_CUDA;
+    }
+    // the mixed form's level passes: blocks of 128 threads, as many as fit on the SMs at
+    // once (a level's nodes are taken ten a warp in one sweep of the resident grid; a
+    // level without internal nodes costs the launch of that grid alone)
+    int lvl_blocks = 0;
+    if (!q64 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lvl_blocks, moments_level3_kernel,
+                                                               kBuildThreads / 2, 0) != cudaSuccess ||
+                 lvl_blocks < 1))
         return P3T_ERR_CUDA;
     for (int l = kLevels - 1; l >= 0; l--) {
         if (q64)
             moments_level_kernel<true><<<persistent, kBuildThreads, 0, s>>>(T, l, P.theta);
-        else if (launch_pdl(moments_level3_kernel, dim3(2 * persistent), dim3(kBuildThreads / 2), s, T, l) !=
-                 cudaSuccess)  // (blocks of 128 threads: three resident per SM at 160 registers)
+        else if (launch_pdl(moments_level3_kernel, dim3(lvl_blocks * c->sm_count), dim3(kBuildThreads / 2), s, T,
+                            l) != cudaSuccess)
             return P3T_ERR_CUDA;
     }
     if (fork && cudaStreamWaitEvent(s, c->join_ev, 0) != cudaSuccess) return P3T_ERR_CUDA;
